@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the DysonNet / ABACUS local estimator on GB300.
+
+Workload (one step): the long-range transverse-field Ising chain N = 128
+(H = sum_{i<j} r^-3 sz sz + sum sx, open), a DysonNet of 4 layers x 32
+channels x 32 S4 modes (w = 2) in FP32, 4096 uniform random configurations:
+the local energy of every configuration, i.e. one forward pass, the output
+and interlayer link tensors, and the ABACUS log-amplitude ratio of all 128
+single flips of every configuration (524,288 ratios per step).
+
+Reported: flip ratios/s of the whole step (value), the same through the C ABI
+with host buffers (e2e), the ABACUS kernel alone, the full-forward recompute of
+every flipped configuration on the GPU, per-kernel device time from the
+library's CUDA-event tracing, the roofline of the dominant kernel, and the
+CPU FP64 oracle on a bounded sample (cpu_baseline).  `--impl reference` times
+the oracle alone on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ABACUS flip ratios/s vs full-forward recompute on GB300; p50/p99 serve latency"
+WORKLOAD = "lr-TFIM N=128 open, DysonNet L=4 d=32 s=32 w=2 FP32, 4096 samples x 128 single flips"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+# FP32 FFMA issue rate of GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA per clock.
+SMS, FP32_LANES = 152, 128
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-i", str(self.gpu)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(cfg, params, spins_np, n_samples: int):
+    """The FP64 oracle (full recompute per flip) on the first n_samples configurations."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    oracle.build()
+    sub = spins_np[:n_samples]
+    oracle.eloc(cfg["desc"], params, cfg["ham"], sub[:1])       # warm (kernel taps, page-in)
+    t0 = time.perf_counter()
+    oracle.eloc(cfg["desc"], params, cfg["ham"], sub)
+    dt = time.perf_counter() - t0
+    flips = n_samples * cfg["N"]
+    return {"value": flips / dt, "unit": "flip ratios/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle", "sample": f"local energy of the first {n_samples} configurations of the workload "
+                                        f"({flips} ratios, full FP64 recompute per flip, OpenMP over samples)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import synth
+    cfg = synth.CONFIGS["c2"]
+    params = synth.make_params(cfg)
+    spins_np = synth.make_spins(cfg, B=max(args.ref_samples, 1))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    oracle.build()
+    sub = spins_np[:args.ref_samples]
+    for _ in range(args.warmup):
+        oracle.eloc(cfg["desc"], params, cfg["ham"], sub)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.eloc(cfg["desc"], params, cfg["ham"], sub)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    flips = args.ref_samples * cfg["N"]
+    value = flips / dt
+    sample = (f"each step: local energy of the first {args.ref_samples} configurations of the workload "
+              f"({flips} ratios, FP64 full recompute per flip)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "flip ratios/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded sample on the host cores)"},
+            "cpu_baseline": {"value": value, "unit": "flip ratios/s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "flip ratios/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def link_conv_flops(N, L, d, B):
+    """FLOPs of the full-field convolutions of the link build in one step:
+    a probe from source layer m crosses full convolutions at layers m+2..L-1."""
+    total = 0
+    for m in range(0, L - 1):
+        probes = B * N * (1 if m == 0 else d)
+        hops = max(0, (L - 1) - (m + 2) + 1)
+        total += probes * hops * 2 * N * N * d
+    return total
+
+
+def abacus_unique_bytes(N, L, d, dout, w, P, B, tb=4):
+    """Algorithmic bytes of one ABACUS launch over all single flips of B samples:
+    every cache value the flips read, counted once (per-sample caches are
+    shared by that sample's N flips), plus the float64 outputs."""
+    W = 2 * w + 1
+    Rk, Rl = W - 1, w
+    per_sample = (2 * L * N * d                 # y, chi
+                  + L * dout * N * d            # rho
+                  + N * dout                    # t
+                  + (L - 1) * N * (2 * Rl + 1) * d   # ell
+                  + P * N * (2 * Rk + 1) * d * d)    # K
+    return B * (per_sample * tb + N) + B * N * 8
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--samples", type=int, default=4096)
+    ap.add_argument("--ref-samples", type=int, default=8)
+    ap.add_argument("--cpu-samples", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recompute", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2603_11189_gb300 import build as B_
+    if rank == 0 and B_.needs_build():
+        import __graft_entry__
+        __graft_entry__.build()
+    if world > 1:
+        tdist.barrier()
+    from paper_2603_11189_gb300 import dysonnet as dn
+    import synth
+
+    cfg = synth.CONFIGS["c2"]
+    desc = cfg["desc"]
+    N, Bs = cfg["N"], args.samples
+    params = synth.make_params(cfg)
+    spins_np = synth.make_spins(cfg, B=Bs)
+    model = dn.Model(desc, params)
+    spins = torch.from_numpy(spins_np).cuda()
+    eloc = torch.empty(Bs, dtype=torch.float64, device="cuda")
+    ham = cfg["ham"]
+    lib = dn._lib()
+    lib.dn_launch_count.restype = ctypes_ll()
+
+    def step():
+        model.local_energy(ham, spins, prec="fp32", out=eloc)
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    sampler.start()
+    lib.dn_profile_enable(1)
+    launches0 = lib.dn_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    barrier()
+    launches = lib.dn_launch_count() - launches0
+    lib.dn_profile_enable(0)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    flips_step = Bs * N
+    value = world * flips_step / (ms_max / 1e3)
+
+    prof = read_profile(lib)
+    assert np.all(np.isfinite(eloc.cpu().numpy())), "non-finite local energies"
+
+    # End to end through the C ABI with host buffers (pinned): H2D spins, D2H energies.
+    spins_host = torch.from_numpy(spins_np).pin_memory()
+    eloc_host = torch.empty(Bs, dtype=torch.float64).pin_memory()
+    spins_dev2 = torch.empty_like(spins)
+
+    def e2e_step():
+        spins_dev2.copy_(spins_host, non_blocking=True)
+        model.local_energy(ham, spins_dev2, prec="fp32", out=eloc)
+        eloc_host.copy_(eloc, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    ev0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    ev1.record()
+    barrier()
+    e2e_ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    e2e_value = world * flips_step / (float(t.item()) / 1e3)
+
+    # ABACUS kernel alone and the GPU full-forward recompute of every flipped configuration.
+    ab_ms = sum(v[1] for k, v in prof.items() if k.endswith("k_abacus")) / args.steps
+    build_ms = sum(v[1] for k, v in prof.items() if "/forward/" in k + "/" or "/adjoint/" in k or "/links/" in k) \
+        / args.steps
+    recompute = None
+    if not args.no_recompute:
+        sample_np, sites_np = synth.single_flips(Bs, N)
+        sample, sites = torch.from_numpy(sample_np).cuda(), torch.from_numpy(sites_np).cuda()
+        out = torch.empty(Bs * N, dtype=torch.float64, device="cuda")
+        model.recompute_flip_ratios(spins, sample, sites, prec="fp32", out=out)
+        barrier()
+        ev0.record()
+        reps = 2
+        for _ in range(reps):
+            model.recompute_flip_ratios(spins, sample, sites, prec="fp32", out=out)
+        ev1.record()
+        barrier()
+        rms = ev0.elapsed_time(ev1) / reps
+        recompute = {"value": flips_step / (rms / 1e3), "unit": "flip ratios/s", "ms": rms,
+                     "speedup_of_abacus_step": (flips_step / (ms / 1e3)) / (flips_step / (rms / 1e3))}
+
+    peaks, src = _peaks()
+    roof = roofline(prof, args.steps, desc, N, Bs, peaks, src, clocks)
+    kernels = sorted(((k, v[0], v[1]) for k, v in prof.items()), key=lambda x: -x[2])
+    total_k = sum(k[2] for k in kernels) or 1.0
+    line = {
+        "metric": METRIC, "value": value, "unit": "flip ratios/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded splitmix64 weights and spins)",
+        "config": {"workload": WORKLOAD, "N": N, "L": desc.L, "d": desc.d, "s": desc.s, "w": desc.w,
+                   "samples_per_gpu": Bs, "flips_per_sample": N, "precision": "fp32", "parallelism": f"replicas{world}",
+                   "l2": "working set > L2: the per-step caches (tens of GB) are written and read once per step"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "flip ratios/s", "h2d_bytes_per_step": int(spins_np.nbytes),
+                "d2h_bytes_per_step": int(Bs * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "abacus_kernel": {"value": flips_step / (ab_ms / 1e3) if ab_ms else None, "unit": "flip ratios/s",
+                          "ms_per_step": ab_ms},
+        "cache_build_ms_per_step": build_ms,
+        "recompute": recompute,
+        "kernels": [{"name": k, "launches": n // args.steps, "ms_per_step": v / args.steps,
+                     "share": v / total_k} for k, n, v in kernels[:8]],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, params, spins_np, args.cpu_samples)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    model.close()
+    if world > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    return 0
+
+
+def ctypes_ll():
+    import ctypes
+    return ctypes.c_longlong
+
+
+def read_profile(lib):
+    import ctypes
+    lib.dn_profile_count.restype = ctypes.c_int
+    out = {}
+    buf = ctypes.create_string_buffer(256)
+    n_l, ms = ctypes.c_longlong(), ctypes.c_double()
+    for i in range(lib.dn_profile_count()):
+        if lib.dn_profile_get(i, buf, 256, ctypes.byref(n_l), ctypes.byref(ms)) == 0 and n_l.value > 0:
+            out[buf.value.decode()] = (n_l.value, ms.value)
+    return out
+
+
+def roofline(prof, steps, desc, N, Bs, peaks, src, clocks):
+    """Roofline of the kernel with the largest device time in the step."""
+    if not prof:
+        return None
+    name, (launches, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_s = tot_ms / launches / 1e3
+    P = (desc.L - 1) * (desc.L - 2) // 2
+    if name.endswith("k_abacus"):
+        # Bs samples per local-energy call are split into chunks; bytes scale with the flips.
+        total_bytes = abacus_unique_bytes(N, desc.L, desc.d, desc.dout, desc.w, P, Bs) * steps
+        per_launch = total_bytes / launches
+        ach = per_launch / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "peak_source": src}
+    if name.endswith("links/k_conv"):
+        flops = link_conv_flops(N, desc.L, desc.d, Bs) * steps
+        per_launch = flops / launches
+        ach = per_launch / avg_s / 1e12
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": f"FP32 FMA issue rate, 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz"}
+    return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "ms_per_launch": avg_s * 1e3}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

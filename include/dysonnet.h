@@ -1,0 +1,205 @@
+/*
+ * dysonnet.h -- C ABI of the GB300 DysonNet / ABACUS local-estimator library.
+ *
+ * The library evaluates, for a batch of spin configurations sigma in {+1,-1}^N,
+ * the DysonNet log-amplitude (Sec. "DysonNet", Eq. wavefunc), fills the per-
+ * sample caches that ABACUS needs (link tensors T and L, Eqs. Tl and Lmn),
+ * and computes log psi(sigma') - log psi(sigma) for local updates sigma' by
+ * the slice-local recurrence of Alg. 1 (Eqs. recur_step and recur_out), whose
+ * exactness is Theorem 1.  The local energy of Eq. local-estimator is built on
+ * top of it for the long-range transverse-field Ising chain (Sec.
+ * "Benchmarking") and the J1-J2 Heisenberg chain (Eq. j1j2_hamiltonian).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named *_dev are caller-owned CUDA device memory on the current
+ *    device; *_host pointers are host memory.  Arrays are C-contiguous.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered and asynchronous: results are valid once the stream has
+ *    reached them.  Host-side argument checks happen before anything is
+ *    enqueued; a failing check returns DN_EINVAL and enqueues nothing.
+ *  - Invalid data that only the device can see (a spin that is not +-1, a site
+ *    out of range, a flip set wider than the cache allows) never causes an
+ *    out-of-bounds access: the affected output is set to NaN and a sticky flag
+ *    is raised, reported by dn_cache_check() (or by the next call on the cache).
+ *  - dn_model and dn_cache are opaque and library-owned.  Device memory they
+ *    hold comes from the allocator installed with dn_set_allocator() (default:
+ *    cudaMallocAsync/cudaFreeAsync on the call's stream).  A failed allocation
+ *    returns DN_ENOMEM and leaves no partial object behind.
+ *  - A model may be used by one host thread at a time.
+ *  - No C++ exception, abort() or exit() crosses this interface.
+ */
+#ifndef DYSONNET_H
+#define DYSONNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DN_OK = 0,
+    DN_EINVAL = 1,        /* bad argument (checked on the host) or bad device data (sticky flag) */
+    DN_ENOMEM = 2,        /* the allocator refused a request */
+    DN_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    DN_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    DN_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} dn_status;
+
+/* Arithmetic of the network and of the caches.  Every precision generates the
+ * S4 kernel taps in FP64 and accumulates the pooled readout and the final
+ * log cosh difference in FP64. */
+typedef enum {
+    DN_FP64 = 0,   /* everything in double */
+    DN_FP32 = 1    /* activations, caches and link contractions in float */
+} dn_precision;
+
+/* N-agnostic hyper-parameters (Sec. "Implementation of DysonNet", App.
+ * "Details on the implementation of the DysonNet block"):
+ *   L layers of h' = D(sigma) G h with d channels; diagonal S4 kernels with s
+ *   complex modes per channel; window half-width w (W = 2w+1) of the local
+ *   vertex; d_h hidden units of the per-site MLP; d_out readout units.
+ *   periodic = 1: ring (circulant kernels, wrapped windows); 0: open chain.
+ *   f_kind = 0: log psi = sum_k log cosh Omega_k (Eq. wavefunc);
+ *   f_kind = 1: log psi = sum_k Omega_k (the Jastrow limit of App. power-law). */
+typedef struct {
+    int L, d, s, w, d_h, d_out;
+    int periodic;
+    int f_kind;
+} dn_model_desc;
+
+/* Hamiltonian for local_energy().
+ *   kind 0, long-range TFIM:  H = (J/N_a) sum_{i<j} r_ij^-alpha sz_i sz_j + h sum_i sx_i
+ *           r_ij = |i-j| (open) or min(|i-j|, N-|i-j|) (periodic);
+ *           N_a = 1, or the Kac factor 2 sum_{r=1}^{N/2} r^-alpha when kac = 1.
+ *           (The paper's form -J'/N_a sum_{i!=j} ... - h' sum sx is J = -2J', h = -h'.)
+ *   kind 1, J1-J2 chain: H = J1 sum_i S_i.S_{i+1} + J2 sum_i S_i.S_{i+2}, S = sigma/2,
+ *           sums over i = 0..N-1 with wrap-around when periodic = 1, else up to N-1-b.
+ *           Requires N >= 3. */
+typedef struct {
+    int kind;
+    double J, alpha, h;
+    double J1, J2;
+    int periodic, kac;
+} dn_hamiltonian;
+
+typedef struct dn_model dn_model;
+typedef struct dn_cache dn_cache;
+
+/* Allocator hook.  alloc(bytes, stream, ctx) returns device memory or NULL;
+ * free(ptr, bytes, stream, ctx) releases it.  Passing NULL for both restores
+ * the default.  Applies to allocations made after the call. */
+typedef void *(*dn_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*dn_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+dn_status dn_set_allocator(dn_alloc_fn alloc, dn_free_fn free_fn, void *ctx);
+
+/* Human-readable name of a status. */
+const char *dn_status_string(dn_status s);
+
+/* Create a model from the flat FP64 parameter vector params_host[n_params].
+ * Layout (W = 2w+1; matrices row-major, output index first):
+ *   S4 block (8 d s + d values): lam_re[d][s] lam_im[d][s] (continuous-time
+ *     diagonal state matrix, Re < 0), log_dt[d], b_re[d][s] b_im[d][s],
+ *     cf_re[d][s] cf_im[d][s] (forward output), cb_re[d][s] cb_im[d][s]
+ *     (backward output);
+ *   for l = 1..L: S4 block | kappa[W][d_h] (window weight at offset r is row
+ *     r+w) | beta[d_h] | W1[d_h][d_h] | b1[d_h] | W2[d][d_h] | b2[d] | U[d][d] | V[d][d];
+ *   then: readout S4 block (G^f) | A[d][d_out] | e[d].
+ * The parameters are copied; the caller keeps ownership of params_host.
+ * DN_EINVAL if a size is non-positive, w < 0, n_params does not match the
+ * layout, or d > 128, d_h > 128, d_out > 8, s > 256, L > 12. */
+dn_status dn_model_create(const dn_model_desc *desc, const double *params_host, size_t n_params,
+                          dn_model **model_out);
+void dn_model_destroy(dn_model *model);
+
+/* Device bytes a cache for (N, batch, precision, max_cluster) will hold; 0 on
+ * bad arguments.  Used to admit work against a memory budget. */
+size_t dn_cache_bytes(const dn_model *model, int N, int batch, dn_precision prec, int max_cluster);
+
+/* One full DysonNet forward pass over B configurations and the construction
+ * of the ABACUS caches (Eqs. wavefunc, Tl, Lmn; App. "Efficient construction
+ * of link tensors"):
+ *   spins_dev [B][N] int8, each +1 or -1;
+ *   max_cluster in {1, 2, 3}: the flip sets the cache must serve -- single
+ *     sites (1), pairs at separation 1 (2) or separations 1 and 2 (3); the
+ *     slice width is W_F = 2w + max_cluster;
+ *   logpsi_dev [B] float64 (may be NULL): log psi(sigma).
+ * On DN_OK *cache_out owns the caches; destroy with dn_cache_destroy().
+ * Errors: DN_EINVAL (N < 1, B < 1, null pointers, max_cluster out of range,
+ * periodic with N < 2 W_F - 1), DN_ENOMEM, DN_ECUDA. */
+dn_status dysonnet_forward_cache(dn_model *model, int N, const int8_t *spins_dev, int B,
+                                 dn_precision prec, int max_cluster, void *stream,
+                                 dn_cache **cache_out, double *logpsi_dev);
+
+/* ABACUS (Alg. 1; Eqs. recur_step, recur_out; Theorem 1): for F flip sets
+ *   sample_dev [F] int32: index of the cached configuration (0 <= b < B);
+ *   sites_dev [F][2] int32: flipped sites; sites[f][1] = -1 for a single flip;
+ *     a pair must be distinct and at ring/chain separation <= max_cluster - 1;
+ *     sites[f][0] = -1 marks an empty entry (output 0);
+ *   dlogpsi_dev [F] float64: log psi(sigma') - log psi(sigma).
+ * Cost per flip is independent of N.  Entries with invalid sites get NaN and
+ * raise the cache's sticky flag.  Errors: DN_EINVAL, DN_ECUDA. */
+dn_status abacus_flip_ratios(const dn_cache *cache, const int32_t *sample_dev, const int32_t *sites_dev,
+                             int F, double *dlogpsi_dev, void *stream);
+
+/* Local energy E_loc(sigma) = sum_sigma' <sigma|H|sigma'> psi(sigma')/psi(sigma)
+ * (Eq. local-estimator) for B configurations, every ratio by ABACUS:
+ *   eloc_dev [B] float64.  Builds and frees its own caches (in chunks of
+ *   samples bounded by an internal memory budget).
+ * Errors: DN_EINVAL, DN_ENOMEM, DN_ECUDA. */
+dn_status local_energy(dn_model *model, const dn_hamiltonian *ham, int N, const int8_t *spins_dev, int B,
+                       dn_precision prec, void *stream, double *eloc_dev);
+
+/* Full-forward baseline: log psi for B configurations, recomputing the whole
+ * network (Eq. wavefunc).  logpsi_dev [B] float64; Omega_dev [B][d_out]
+ * float64 (may be NULL). */
+dn_status dn_full_forward(dn_model *model, int N, const int8_t *spins_dev, int B, dn_precision prec,
+                          void *stream, double *logpsi_dev, double *Omega_dev);
+
+/* The computation ABACUS replaces (Sec. "ABACUS", discussion of runtime):
+ * log psi(sigma') - log psi(sigma) for each flip set by building every
+ * flipped configuration on the device and recomputing the whole network.
+ * Same flip-set format as abacus_flip_ratios(); spins_dev [B][N]. */
+dn_status dn_recompute_flip_ratios(dn_model *model, int N, const int8_t *spins_dev, int B,
+                                   const int32_t *sample_dev, const int32_t *sites_dev, int F,
+                                   dn_precision prec, void *stream, double *dlogpsi_dev);
+
+/* Wait for `stream`, then report the cache's sticky device flag:
+ * DN_OK, DN_EINVAL (invalid spins or flip sites were seen), DN_ECUDA. */
+dn_status dn_cache_check(const dn_cache *cache, void *stream);
+
+/* Read-only view of one cache array (device pointer owned by the cache):
+ * name is one of "spins" (int8 [B][N]), "chi" and "y" ([B][L][N][d]),
+ * "rho" ([B][L][d_out][N][d]: output links, Eq. Tl with A folded in),
+ * "t" ([B][N][d_out]), "ell" ([B][L-1][N][2Rl+1][d]: response at layer l of
+ * the embedding at site i+o-Rl, Rl = W_F-1-w), "K" ([B][P][N][2Rk+1][d][d]:
+ * links L^(l,m) of Eq. Lmn on the band |i-k| <= Rk = W_F-1, stored
+ * [i][o][c_in][c_out] with k = i+o-Rk, pairs ordered (l,m) = (3,1), (4,1),
+ * (4,2), ...), "Omega" (f64 [B][d_out]) or "logpsi" (f64 [B]).  Elements are
+ * float64 for DN_FP64 caches and float32 for DN_FP32 caches.  Band entries
+ * whose partner site lies off an open chain are unspecified.
+ * DN_EINVAL for an unknown name. */
+dn_status dn_cache_tensor(const dn_cache *cache, const char *name, void **dev_ptr, size_t *count, int *elem_bytes);
+
+/* Shape of a cache: N, B, precision, max_cluster (any pointer may be NULL). */
+dn_status dn_cache_info(const dn_cache *cache, int *N, int *B, int *prec, int *max_cluster);
+
+/* Tracing.  dn_launch_count(): kernels launched by the library since load.
+ * dn_profile_enable(1) starts recording a pair of CUDA events around every
+ * kernel launch (on its stream), grouped by kernel name; dn_profile_enable(0)
+ * stops.  dn_profile_count() is the number of kernel names seen;
+ * dn_profile_get(i, ...) synchronises the device and returns name i, its
+ * launches and total device milliseconds since tracing was last enabled. */
+long long dn_launch_count(void);
+dn_status dn_profile_enable(int on);
+int dn_profile_count(void);
+dn_status dn_profile_get(int i, char *name, size_t name_len, long long *launches, double *total_ms);
+
+/* Release a cache (stream-ordered on the stream of the call that built it). */
+void dn_cache_destroy(dn_cache *cache);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DYSONNET_H */

@@ -1,0 +1,449 @@
+// ABACUS local update (Alg. 1; Eqs. recur_step and recur_out; Theorem 1) and
+// the local estimator (Eq. local-estimator) on sm_103a.
+//
+// One CTA per flip set F (one site, or two sites at separation <= max_cluster-1)
+// on the slice S = [first - w, last + w] (width wf <= W_F).  For l = 1..L:
+//   p_i   = sum_{k in S} g^(l)_{i-k} s^(l-1)_k                 (M~ s, slice Toeplitz)
+//         + sum_{j in F} dsigma_j ell^(l)_{i,j}                (background-propagated
+//                                                                embedding change, l >= 2)
+//         + sum_{m=1}^{l-2} sum_{k in S} L^(l,m)_{i,k} s^(m)_k  (Eq. Lmn links)
+//   s^(l)_i = U (dchi^(l)_i * (y^(l)_i + V p_i))     [= dD (h~_0 + ...) of Eq. recur_step]
+//   dOmega += rho^(l)_i . s^(l)_i                     [T^(l) of Eq. recur_out]
+// with s^(0)_j = e dsigma_j; dOmega also collects the flip's unscattered
+// contribution sum_j t_j dsigma_j.  Output: sum_k f(Omega_k + dOmega_k) - f(Omega_k).
+#include <math.h>
+
+#include "dn_internal.cuh"
+
+namespace dn {
+
+template <typename T>
+__device__ __forceinline__ T gelu_ab(T x);
+template <>
+__device__ __forceinline__ double gelu_ab<double>(double x) {
+    return 0.5 * x * (1.0 + erf(x * 0.70710678118654752440));
+}
+template <>
+__device__ __forceinline__ float gelu_ab<float>(float x) {
+    return 0.5f * x * (1.0f + erff(x * 0.70710678f));
+}
+
+__device__ __forceinline__ double log_cosh_ab(double x) {
+    const double a = fabs(x);
+    return a + log1p(exp(-2.0 * a)) - 0.69314718055994530942;
+}
+
+template <typename T>
+struct AbArgs {
+    Geom g;
+    int B, WF, Rk, Rl, P, max_cluster, f_kind;
+    const int8_t *spins;
+    const T *chi, *y, *rho, *t, *ell, *K, *taps;
+    const double *Omega;
+    unsigned *flag;
+    Weights<T> w;
+};
+
+constexpr int kAbThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_t *__restrict__ sample,
+                                                       const int32_t *__restrict__ sites, int F,
+                                                       double *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Geom &g = a.g;
+    const int N = g.N, d = g.d, dh = g.dh, L = g.L, WF = a.WF, dout = g.dout, wd = g.w;
+    T *S = reinterpret_cast<T *>(smraw);          // [L+1][WF][d]
+    T *p = S + (size_t)(L + 1) * WF * d;          // [WF][d]
+    T *gz = p + (size_t)WF * d;                   // [WF][d]
+    T *phi = gz + (size_t)WF * d;                 // [WF][dh]
+    T *act = phi + (size_t)WF * dh;               // [WF][dh]
+    double *red = reinterpret_cast<double *>(smraw + ((((size_t)(L + 3) * WF * d + 2 * (size_t)WF * dh) * sizeof(T) + 7) & ~(size_t)7));
+    __shared__ int info[8];
+    __shared__ int pos[16];
+    const int tid = threadIdx.x;
+    const long long f = blockIdx.x;
+    if (tid == 0) {
+        int status = 0, b = sample[f], j0 = sites[2 * f], j1 = sites[2 * f + 1];
+        int first = j0, sep = 0;
+        if (j0 == -1) {
+            status = 1;
+        } else if (b < 0 || b >= a.B || j0 < 0 || j0 >= N) {
+            status = 2;
+        } else if (j1 != -1) {
+            if (j1 < 0 || j1 >= N || j1 == j0) {
+                status = 2;
+            } else if (g.periodic) {
+                const int dd = ((j1 - j0) % N + N) % N;
+                sep = dd < N - dd ? dd : N - dd;
+                first = (dd == sep) ? j0 : j1;
+            } else {
+                sep = j1 > j0 ? j1 - j0 : j0 - j1;
+                first = j0 < j1 ? j0 : j1;
+            }
+            if (status == 0 && sep > a.max_cluster - 1) status = 2;
+        }
+        info[0] = status;
+        info[1] = b;
+        info[2] = j0;
+        info[3] = j1;
+        info[4] = first - wd;   // slice start
+        info[5] = g.W + sep;    // slice width
+    }
+    __syncthreads();
+    const int status = info[0];
+    if (status == 1) {
+        if (tid == 0) out[f] = 0.0;
+        return;
+    }
+    if (status == 2) {
+        if (tid == 0) {
+            out[f] = nan("");
+            atomicOr(a.flag, 2u);
+        }
+        return;
+    }
+    const long long b = info[1];
+    const int j0 = info[2], j1 = info[3], start = info[4], wf = info[5];
+    const int8_t *sp = a.spins + b * N;
+    if (tid < wf) {
+        int i = start + tid;
+        if (g.periodic) i = ((i % N) + N) % N;
+        else if (i < 0 || i >= N) i = -1;
+        pos[tid] = i;
+    }
+    const int nflip = j1 >= 0 ? 2 : 1;
+    const int jf[2] = {j0, j1};
+    const T ds[2] = {(T)(-2 * sp[j0]), j1 >= 0 ? (T)(-2 * sp[j1]) : (T)0};
+    __syncthreads();
+
+    // Band offset k - i mapped to (-(WF-1), WF-1].
+    auto offs = [&](int k, int i) -> int {
+        int dl = k - i;
+        if (g.periodic) {
+            dl = ((dl % N) + N) % N;
+            if (dl > WF - 1) dl -= N;
+        }
+        return dl;
+    };
+    auto tap = [&](int l, int r, int c) -> T {
+        int row;
+        if (g.periodic) {
+            r = ((r % N) + N) % N;
+            row = r;
+        } else {
+            row = r + N - 1;
+        }
+        return a.taps[((long long)(l - 1) * g.R + row) * d + c];
+    };
+    auto spin_new = [&](int j) -> T {
+        if (g.periodic) j = ((j % N) + N) % N;
+        else if (j < 0 || j >= N) return (T)0;
+        T v = (T)sp[j];
+        if (j == j0 || (j1 >= 0 && j == j1)) v = -v;
+        return v;
+    };
+
+    double dom[kMaxDout];
+    for (int k = 0; k < dout; ++k) dom[k] = 0.0;
+    const long long nRk = 2 * a.Rk + 1, nRl = 2 * a.Rl + 1;
+    const long long dd = (long long)d * d;
+
+    for (int l = 1; l <= L; ++l) {
+        // (1) p = propagated change reaching the slice at layer l
+        for (int idx = tid; idx < wf * d; idx += blockDim.x) {
+            const int t = idx / d, c = idx % d;
+            const int i = pos[t];
+            T acc = 0;
+            if (i >= 0) {
+                if (l == 1) {
+                    for (int q = 0; q < nflip; ++q) acc += tap(1, i - jf[q], c) * a.w.e[c] * ds[q];
+                } else {
+                    const T *Sp = S + (size_t)(l - 1) * WF * d;
+                    for (int t2 = 0; t2 < wf; ++t2) {
+                        const int k = pos[t2];
+                        if (k >= 0) acc += tap(l, i - k, c) * Sp[t2 * d + c];
+                    }
+                    const T *el = a.ell + (((b * (L - 1) + (l - 2)) * N + i) * nRl) * d;
+                    for (int q = 0; q < nflip; ++q) acc += ds[q] * el[(offs(jf[q], i) + a.Rl) * d + c];
+                    for (int m = 1; m <= l - 2; ++m) {
+                        const T *Kr = a.K + ((b * a.P + pair_index(l, m)) * N + i) * nRk * dd + c;
+                        const T *Sm = S + (size_t)m * WF * d;
+                        for (int t2 = 0; t2 < wf; ++t2) {
+                            const int k = pos[t2];
+                            if (k < 0) continue;
+                            const T *Kb = Kr + (long long)(offs(k, i) + a.Rk) * dd;
+                            const T *sv = Sm + t2 * d;
+#pragma unroll 8
+                            for (int c2 = 0; c2 < d; ++c2) acc += Kb[(long long)c2 * d] * sv[c2];
+                        }
+                    }
+                }
+            }
+            p[idx] = acc;
+        }
+        // (2) phi' on the slice with the flipped spins
+        const T *kap = a.w.kappa + (long long)(l - 1) * g.W * dh;
+        const T *beta = a.w.beta + (long long)(l - 1) * dh;
+        for (int idx = tid; idx < wf * dh; idx += blockDim.x) {
+            const int t = idx / dh, e = idx % dh;
+            T acc = 0;
+            if (pos[t] >= 0) {
+                acc = beta[e];
+                const int i = start + t;
+                for (int r = -wd; r <= wd; ++r) acc += kap[(r + wd) * dh + e] * spin_new(i + r);
+            }
+            phi[idx] = acc;
+        }
+        __syncthreads();
+        const T *W1T = a.w.W1T + (long long)(l - 1) * dh * dh;
+        const T *b1 = a.w.b1 + (long long)(l - 1) * dh;
+        for (int idx = tid; idx < wf * dh; idx += blockDim.x) {
+            const int t = idx / dh, e = idx % dh;
+            T acc = b1[e];
+            for (int f2 = 0; f2 < dh; ++f2) acc += W1T[f2 * dh + e] * phi[t * dh + f2];
+            act[idx] = gelu_ab<T>(acc);
+        }
+        __syncthreads();
+        // (3) gz = dchi * (y + V p)
+        const T *W2T = a.w.W2T + (long long)(l - 1) * dh * d;
+        const T *b2 = a.w.b2 + (long long)(l - 1) * d;
+        const T *VT = a.w.VT + (long long)(l - 1) * dd;
+        for (int idx = tid; idx < wf * d; idx += blockDim.x) {
+            const int t = idx / d, c = idx % d;
+            const int i = pos[t];
+            T val = 0;
+            if (i >= 0) {
+                T chin = b2[c];
+                for (int e = 0; e < dh; ++e) chin += W2T[e * d + c] * act[t * dh + e];
+                const long long ci = ((b * L + (l - 1)) * N + i) * d + c;
+                const T dchi = chin - a.chi[ci];
+                T z = a.y[ci];
+                for (int c2 = 0; c2 < d; ++c2) z += VT[c2 * d + c] * p[t * d + c2];
+                val = dchi * z;
+            }
+            gz[idx] = val;
+        }
+        __syncthreads();
+        // (4) s^(l) = U gz ; dOmega += rho^(l) . s^(l)
+        const T *UT = a.w.UT + (long long)(l - 1) * dd;
+        T *Sl = S + (size_t)l * WF * d;
+        for (int idx = tid; idx < wf * d; idx += blockDim.x) {
+            const int t = idx / d, c = idx % d;
+            const int i = pos[t];
+            T sv = 0;
+            if (i >= 0) {
+                for (int c2 = 0; c2 < d; ++c2) sv += UT[c2 * d + c] * gz[t * d + c2];
+                for (int k = 0; k < dout; ++k)
+                    dom[k] += (double)a.rho[(((b * L + (l - 1)) * dout + k) * N + i) * d + c] * (double)sv;
+            }
+            Sl[idx] = sv;
+        }
+        __syncthreads();
+    }
+    // Block reduction of dOmega.
+    for (int k = 0; k < dout; ++k) red[k * blockDim.x + tid] = dom[k];
+    __syncthreads();
+    if (tid < dout) {
+        const int k = tid;
+        double sum = 0.0;
+        for (int q = 0; q < (int)blockDim.x; ++q) sum += red[k * blockDim.x + q];
+        for (int q = 0; q < nflip; ++q) sum += (double)a.t[(b * N + jf[q]) * dout + k] * (double)ds[q];
+        red[k * blockDim.x] = sum;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double res = 0.0;
+        for (int k = 0; k < dout; ++k) {
+            const double om = a.Omega[b * dout + k];
+            const double dk = red[k * blockDim.x];
+            res += a.f_kind == 0 ? (log_cosh_ab(om + dk) - log_cosh_ab(om)) : dk;
+        }
+        out[f] = res;
+    }
+}
+
+template <typename T>
+cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
+                          const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    AbArgs<T> a;
+    a.g = geom_of(m, c->N);
+    a.B = c->B;
+    a.WF = c->WF;
+    a.Rk = c->Rk;
+    a.Rl = c->Rl;
+    a.P = c->P;
+    a.max_cluster = c->max_cluster;
+    a.f_kind = m->desc.f_kind;
+    a.spins = c->spins;
+    a.chi = static_cast<const T *>(c->chi);
+    a.y = static_cast<const T *>(c->y);
+    a.rho = static_cast<const T *>(c->rho);
+    a.t = static_cast<const T *>(c->t);
+    a.ell = static_cast<const T *>(c->ell);
+    a.K = static_cast<const T *>(c->K);
+    a.taps = pl.taps;
+    a.Omega = c->Omega;
+    a.flag = c->flag;
+    a.w = w;
+    const Geom &g = a.g;
+    const size_t tsz = ((size_t)(g.L + 3) * c->WF * g.d + 2 * (size_t)c->WF * g.dh) * sizeof(T);
+    const size_t smem = ((tsz + 7) & ~(size_t)7) + (size_t)kMaxDout * kAbThreads * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_abacus<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_abacus", st);
+        k_abacus<T><<<F, kAbThreads, smem, st>>>(a, sample, sites, F, out);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_abacus<double>(const dn_model *, const Plan<double> &, const Weights<double> &,
+                                           const dn_cache *, const int32_t *, const int32_t *, int, double *,
+                                           cudaStream_t);
+template cudaError_t launch_abacus<float>(const dn_model *, const Plan<float> &, const Weights<float> &,
+                                          const dn_cache *, const int32_t *, const int32_t *, int, double *,
+                                          cudaStream_t);
+
+// ------------------------------------------------------ local estimator ----
+// Connected flip sets.  kind 0 (TFIM): every single site, f = b N + i.
+// kind 1 (J1-J2): pairs (i, i+1) then (i, i+2), f = b 2N + (bond-1) N + i;
+// aligned pairs and pairs past an open end are empty entries.
+__global__ void k_make_flips(int kind, int N, int B, int periodic, const int8_t *__restrict__ spins,
+                             int32_t *__restrict__ sample, int32_t *__restrict__ sites) {
+    const long long per = kind == 0 ? N : 2 * N;
+    const long long F = per * B;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < F; f += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(f / per);
+        const int r = (int)(f % per);
+        sample[f] = b;
+        if (kind == 0) {
+            sites[2 * f] = r;
+            sites[2 * f + 1] = -1;
+        } else {
+            const int bond = r / N + 1, i = r % N;
+            int j = i + bond;
+            bool ok = true;
+            if (periodic) j %= N;
+            else if (j >= N) ok = false;
+            if (ok && spins[(long long)b * N + i] == spins[(long long)b * N + j]) ok = false;
+            sites[2 * f] = ok ? i : -1;
+            sites[2 * f + 1] = ok ? j : -1;
+        }
+    }
+}
+
+cudaError_t launch_make_flips(int kind, int N, int B, int periodic, const int8_t *spins, int32_t *sample,
+                              int32_t *sites, cudaStream_t st) {
+    {
+        ProfScope _ps("k_make_flips", st);
+        k_make_flips<<<1024, 256, 0, st>>>(kind, N, B, periodic, spins, sample, sites);
+    }
+    return cudaGetLastError();
+}
+
+// E_loc(b) = <sigma|H|sigma> + sum over connected sigma' of H_{sigma sigma'} exp(dlogpsi).
+// coupling[r] = J r^-alpha / N_a (TFIM, r = 1..N-1).
+__global__ void k_eloc_reduce(dn_hamiltonian H, int N, int B, const int8_t *__restrict__ spins,
+                              const double *__restrict__ coupling, const double *__restrict__ dlogpsi,
+                              double *__restrict__ eloc) {
+    __shared__ double red[256];
+    const int b = blockIdx.x;
+    const int8_t *sp = spins + (long long)b * N;
+    double acc = 0.0;
+    if (H.kind == 0) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            double row = 0.0;
+            for (int j = i + 1; j < N; ++j) {
+                int r = j - i;
+                if (H.periodic && N - r < r) r = N - r;
+                row += coupling[r] * sp[j];
+            }
+            acc += row * sp[i];
+        }
+        for (int i = threadIdx.x; i < N; i += blockDim.x) acc += H.h * exp(dlogpsi[(long long)b * N + i]);
+    } else {
+        for (int q = threadIdx.x; q < 2 * N; q += blockDim.x) {
+            const int bond = q / N + 1, i = q % N;
+            const double Jb = bond == 1 ? H.J1 : H.J2;
+            int j = i + bond;
+            if (H.periodic) j %= N;
+            else if (j >= N) continue;
+            acc += 0.25 * Jb * sp[i] * sp[j];
+            if (sp[i] != sp[j]) acc += 0.5 * Jb * exp(dlogpsi[(long long)b * 2 * N + q]);
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < (int)blockDim.x; ++q) s += red[q];
+        eloc[b] = s;
+    }
+}
+
+cudaError_t launch_eloc_reduce(const dn_hamiltonian &H, int N, int B, const int8_t *spins, const double *coupling,
+                               const double *dlogpsi, double *eloc, cudaStream_t st) {
+    {
+        ProfScope _ps("k_eloc_reduce", st);
+        k_eloc_reduce<<<B, 256, 0, st>>>(H, N, B, spins, coupling, dlogpsi, eloc);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- full-recompute baseline --
+__global__ void k_expand_flips(int N, const int8_t *__restrict__ spins, const int32_t *__restrict__ sample,
+                               const int32_t *__restrict__ sites, int F, int B, int8_t *__restrict__ out,
+                               unsigned *__restrict__ flag) {
+    const long long f = blockIdx.x;
+    if (f >= F) return;
+    const int b = sample[f], j0 = sites[2 * f], j1 = sites[2 * f + 1];
+    const bool bad = (b < 0 || b >= B) || (j0 < -1 || j0 >= N) || (j1 < -1 || j1 >= N) || (j0 == -1 && j1 != -1) ||
+                     (j0 >= 0 && j0 == j1);
+    if (bad && threadIdx.x == 0) atomicOr(flag, 2u);
+    const int8_t *src = spins + (long long)(bad ? 0 : b) * N;
+    int8_t *dst = out + f * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        int8_t v = src[i];
+        if (!bad && (i == j0 || i == j1)) v = (int8_t)(-v);
+        dst[i] = v;
+    }
+}
+
+cudaError_t launch_expand_flips(int N, const int8_t *spins, const int32_t *sample, const int32_t *sites, int F,
+                                int B, int8_t *out, unsigned *flag, cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    {
+        ProfScope _ps("k_expand_flips", st);
+        k_expand_flips<<<F, 128, 0, st>>>(N, spins, sample, sites, F, B, out, flag);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void k_sub_base(const double *__restrict__ lp_flip, const double *__restrict__ lp_base,
+                           const int32_t *__restrict__ sample, const int32_t *__restrict__ sites, int F, int B, int N,
+                           double *__restrict__ out) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    const int b = sample[f], j0 = sites[2 * f], j1 = sites[2 * f + 1];
+    const bool bad = (b < 0 || b >= B) || (j0 < -1 || j0 >= N) || (j1 < -1 || j1 >= N) || (j0 == -1 && j1 != -1) ||
+                     (j0 >= 0 && j0 == j1);
+    if (bad) {
+        out[f] = nan("");
+        return;
+    }
+    out[f] = j0 == -1 ? 0.0 : lp_flip[f] - lp_base[b];
+}
+
+cudaError_t launch_sub_base(const double *lp_flip, const double *lp_base, const int32_t *sample, const int32_t *sites,
+                            int F, int B, int N, double *out, cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    {
+        ProfScope _ps("k_sub_base", st);
+        k_sub_base<<<(F + 255) / 256, 256, 0, st>>>(lp_flip, lp_base, sample, sites, F, B, N, out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dn

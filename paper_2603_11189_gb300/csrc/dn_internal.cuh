@@ -1,0 +1,221 @@
+// Internal declarations of the DysonNet / ABACUS CUDA library (sm_103a).
+//
+// Data layout in HBM (per cache, B samples, T = double or float):
+//   spins  int8 [B][N]
+//   chi    T    [B][L][N][d]        local vertex spectrum chi^(l)_i (Eq. Dpractical)
+//   y      T    [B][L][N][d]        pre-gate channel mix y = V u0, u0 = G h0 (slice
+//                                   activations h~_0 of Eq. recur_step)
+//   rho    T    [B][L][dout][N][d]  output links T^(l) with A folded in (Eq. Tl)
+//   t      T    [B][N][dout]        embedding output link e . rho^(0)
+//   ell    T    [B][L-1][N][2Rl+1][d]      ell^(l)_{i, i+o-Rl}: background response
+//                                          at layer l to the embedding of site i+o-Rl
+//   K      T    [B][P][N][2Rk+1][d][d]     links L^(l,m) (Eq. Lmn) on the band
+//                                          |i-k| <= Rk, stored [i][o][c_in][c_out]
+//   Omega  f64  [B][dout], logpsi f64 [B], flag u32
+// with W_F = 2w + max_cluster, Rk = W_F - 1, Rl = W_F - 1 - w and
+// P = (L-1)(L-2)/2 layer pairs (l, m), 1 <= m <= l-2, indexed (l-3)(l-2)/2 + m-1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <vector>
+
+#include "dysonnet.h"
+
+namespace dn {
+
+constexpr int kMaxD = 128;
+constexpr int kMaxDh = 128;
+constexpr int kMaxDout = 8;
+constexpr int kMaxL = 12;
+
+// Device copies of the layer weights.  Matrices come in both orientations:
+// M[out][in] and MT[in][out] (MT puts the output index fastest, so a warp whose
+// lanes own consecutive outputs reads consecutive addresses).
+template <typename T>
+struct Weights {
+    T *kappa = nullptr;  // [L][W][dh]
+    T *beta = nullptr;   // [L][dh]
+    T *W1T = nullptr;    // [L][dh_in][dh_out]
+    T *b1 = nullptr;     // [L][dh]
+    T *W2T = nullptr;    // [L][dh][d]
+    T *b2 = nullptr;     // [L][d]
+    T *U = nullptr, *UT = nullptr, *V = nullptr, *VT = nullptr;  // [L][d][d]
+    T *A = nullptr;      // [d][dout]
+    T *e = nullptr;      // [d]
+    void *block = nullptr;
+    size_t bytes = 0;
+};
+
+// Weights-only tables for one chain length N (S4 kernel taps in FP64, cast).
+template <typename T>
+struct Plan {
+    int N = 0, R = 0;
+    T *taps = nullptr;        // [L][R][d], row r + N - 1 (open) or r (periodic)
+    T *omega = nullptr;       // [N][d] pooling weights (1/N) sum_k g^f_{k-i}
+    double *taps64 = nullptr; // [L+1][R][d]
+    double *omega64 = nullptr;
+    void *block = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace dn
+
+struct dn_model {
+    dn_model_desc desc;
+    int W = 0;
+    size_t nparams = 0;
+    std::vector<double> params;
+    double *params_dev = nullptr;
+    double *A64 = nullptr;  // [d][dout]
+    long long s4_size = 0, layer_size = 0;
+    dn::Weights<double> w64;
+    dn::Weights<float> w32;
+    std::map<int, dn::Plan<double>> plan64;
+    std::map<int, dn::Plan<float>> plan32;
+    bool weights_ready[2] = {false, false};
+};
+
+struct dn_cache {
+    dn_model *model = nullptr;
+    int N = 0, B = 0, prec = 0, max_cluster = 1;
+    int WF = 0, Rk = 0, Rl = 0, P = 0;
+    cudaStream_t stream = nullptr;
+    void *block = nullptr;
+    size_t bytes = 0;
+    int8_t *spins = nullptr;
+    void *chi = nullptr, *y = nullptr, *rho = nullptr, *t = nullptr, *ell = nullptr, *K = nullptr;
+    double *Omega = nullptr, *logpsi = nullptr;
+    unsigned *flag = nullptr;
+};
+
+namespace dn {
+
+// ------------------------------------------------------------------ memory --
+void *dev_alloc(size_t bytes, cudaStream_t stream);
+void dev_free(void *p, size_t bytes, cudaStream_t stream);
+
+// Bump allocator inside one device block, 256-byte aligned sub-arrays.
+struct Carve {
+    size_t off = 0;
+    template <typename X>
+    size_t take(size_t count) {
+        size_t o = (off + 255) & ~size_t(255);
+        off = o + count * sizeof(X);
+        return o;
+    }
+};
+
+// ---------------------------------------------------------------- tracing --
+// RAII scope around one kernel launch: counts it and, while tracing is on,
+// records CUDA events before and after it on the launch stream.
+class ProfScope {
+   public:
+    ProfScope(const char *name, cudaStream_t st);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+
+   private:
+    cudaStream_t st_;
+    int tag_ = -1;
+    cudaEvent_t start_ = nullptr;
+};
+
+// Names the enclosing stage of a call ("forward", "links", ...); launches
+// inside are traced as "stage/kernel" (stages nest).
+class ProfPhase {
+   public:
+    explicit ProfPhase(const char *name);
+    ~ProfPhase();
+    ProfPhase(const ProfPhase &) = delete;
+    ProfPhase &operator=(const ProfPhase &) = delete;
+};
+
+// --------------------------------------------------------------- geometry --
+struct Geom {
+    int N, L, d, dh, dout, w, W, periodic, R;
+};
+
+inline Geom geom_of(const dn_model *m, int N) {
+    Geom g;
+    g.N = N; g.L = m->desc.L; g.d = m->desc.d; g.dh = m->desc.d_h; g.dout = m->desc.d_out;
+    g.w = m->desc.w; g.W = 2 * m->desc.w + 1; g.periodic = m->desc.periodic;
+    g.R = g.periodic ? N : 2 * N - 1;
+    return g;
+}
+
+__host__ __device__ inline int pair_index(int l, int m) { return (l - 3) * (l - 2) / 2 + (m - 1); }
+
+// Generic addressing of a batch of [N][d] fields: field f lives at
+// base + (f / inner) * outer + (f % inner) * stride_inner.
+template <typename T>
+struct Fields {
+    T *base;
+    long long outer, stride_inner;
+    int inner;
+    __host__ __device__ T *at(long long f) const {
+        return base + (f / inner) * outer + (f % inner) * stride_inner;
+    }
+};
+
+// ---------------------------------------------------------------- kernels --
+// Launchers (forward.cu).
+cudaError_t launch_taps(const dn_model *m, int N, double *taps64, double *omega64, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cast(const double *src, T *dst, long long n, cudaStream_t st);
+cudaError_t launch_check_spins(const int8_t *spins, long long n, int8_t *copy, unsigned *flag, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, int B, T *chi,
+                       cudaStream_t st);
+
+// u = G x (transpose: G^T x) per channel.  x from `in` fields, or, when
+// spins != nullptr, x_j = e * sigma_j of sample f.  With add_Aw the output is
+// A[:, k] * omega + G^T x for field f = (b, k) (adjoint recursion).
+template <typename T>
+cudaError_t launch_conv(const Geom &g, const T *taps_l, Fields<T> in, const int8_t *spins, const T *e,
+                        Fields<T> out, long long F, bool transpose, const T *A, const T *omega, cudaStream_t st);
+
+// Site-wise vertex: forward  h = U (chi * (V u)), optionally storing y = V u and
+// the pooled sum_i omega_i h_i (FP64) per field; adjoint z = V^T (chi * (U^T x)).
+// Field f (global index f0 + f) uses the vertex of sample (f0 + f) / fields_per_sample.
+template <typename T>
+cudaError_t launch_mix(const Geom &g, int l, const Weights<T> &w, const T *chi, long long chi_stride,
+                       long long fields_per_sample, long long f0, Fields<T> in, Fields<T> out, Fields<T> yout,
+                       const T *omega, double *pooled, long long pooled_stride, long long F, bool adjoint,
+                       cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_pool0(const Geom &g, const int8_t *spins, const T *e, const T *omega, int B, double *pooled,
+                         long long pooled_stride, cudaStream_t st);
+cudaError_t launch_readout(const Geom &g, int f_kind, const double *A64, const double *pooled, int npool, int B,
+                           const int8_t *spins, double *Omega, double *logpsi, cudaStream_t st);
+template <typename T>
+cudaError_t launch_rho_init(const Geom &g, const T *A, const T *omega, Fields<T> out, long long F, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tlink(const Geom &g, const T *rho0, const T *e, int B, T *t, cudaStream_t st);
+
+// Links (links.cu): build ell and K for every sample of a cache, in batches of
+// probes that fit the scratch buffer.
+template <typename T>
+cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, dn_cache *c, T *scratch,
+                        size_t scratch_elems, cudaStream_t st);
+size_t links_scratch_elems(const dn_model *m, int N, int nb_max);
+
+// ABACUS (abacus.cu).
+template <typename T>
+cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
+                          const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st);
+cudaError_t launch_make_flips(int kind, int N, int B, int periodic, const int8_t *spins, int32_t *sample,
+                              int32_t *sites, cudaStream_t st);
+cudaError_t launch_eloc_reduce(const dn_hamiltonian &H, int N, int B, const int8_t *spins, const double *coupling,
+                               const double *dlogpsi, double *eloc, cudaStream_t st);
+cudaError_t launch_expand_flips(int N, const int8_t *spins, const int32_t *sample, const int32_t *sites, int F,
+                                int B, int8_t *out, unsigned *flag, cudaStream_t st);
+cudaError_t launch_sub_base(const double *lp_flip, const double *lp_base, const int32_t *sample, const int32_t *sites,
+                            int F, int B, int N, double *out, cudaStream_t st);
+
+}  // namespace dn

@@ -1,0 +1,492 @@
+// DysonNet forward pass and adjoint (output links) on sm_103a.
+//
+//  k_taps     S4 kernel generation in FP64 (App. "Details on the implementation
+//             of the DysonNet block", Eq. discretization; periodic chains use
+//             the closed-form circulant sum of the open kernel's images).
+//  k_omega    pooling weights of P_M G^f (Eq. wavefunc): omega_i = (1/N) sum_k g^f_{k-i}.
+//  k_chi      chi^(l)_i = W2 GELU(W1 phi^(l)_i + b1) + b2, phi from the spin window
+//             (Eq. Dpractical, local vertex of width W = 2w+1).
+//  k_conv     u = G x, channel-diagonal Toeplitz/circulant convolution (the
+//             Green's-function mixer of the DysonNet block definition), or its
+//             transpose for the adjoint.
+//  k_mix      h = U (chi * (V u)) per site (D_j = U diag(chi_j) V), with the
+//             pooled readout accumulated in FP64; or the adjoint V^T chi U^T.
+//  k_readout  Omega = A^T sum_l pooled_l, log psi = sum_k f(Omega_k).
+#include <math.h>
+
+#include "dn_internal.cuh"
+
+namespace dn {
+
+template <typename T>
+__device__ __forceinline__ T gelu(T x);
+template <>
+__device__ __forceinline__ double gelu<double>(double x) {
+    return 0.5 * x * (1.0 + erf(x * 0.70710678118654752440));
+}
+template <>
+__device__ __forceinline__ float gelu<float>(float x) {
+    return 0.5f * x * (1.0f + erff(x * 0.70710678f));
+}
+
+// ------------------------------------------------------------------ taps --
+__global__ void k_taps(const double *__restrict__ params, int L, int d, int s, long long layer_size,
+                       long long final_off, int N, int periodic, int R, double *__restrict__ out) {
+    const int ri = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y, blk = blockIdx.z;
+    if (ri >= R) return;
+    const double *p = params + (blk < L ? (long long)blk * layer_size : final_off);
+    const long long ds = (long long)d * s;
+    const double *lre = p, *lim = p + ds, *logdt = p + 2 * ds;
+    const double *bre = logdt + d, *bim = bre + ds;
+    const double *cfre = bim + ds, *cfim = cfre + ds, *cbre = cfim + ds, *cbim = cbre + ds;
+    const double dt = exp(logdt[c]);
+    double acc = 0.0;
+    for (int n = 0; n < s; ++n) {
+        const long long k = (long long)c * s + n;
+        // lam_bar = (1 + dt/2 Lam) / (1 - dt/2 Lam), B_bar = dt B / (1 - dt/2 Lam)
+        const double ar = 0.5 * dt * lre[k], ai = 0.5 * dt * lim[k];
+        const double dr = 1.0 - ar, di = -ai, dd = dr * dr + di * di;
+        const double lr = ((1.0 + ar) * dr + ai * di) / dd;
+        const double li = (ai * dr - (1.0 + ar) * di) / dd;
+        const double br = dt * bre[k], bi = dt * bim[k];
+        const double bbr = (br * dr + bi * di) / dd, bbi = (bi * dr - br * di) / dd;
+        const double lnrho = 0.5 * log(lr * lr + li * li), th = atan2(li, lr);
+        if (!periodic) {
+            const int r = ri - (N - 1);
+            const int q = r < 0 ? -r : r;
+            double sn, cs;
+            sincos(q * th, &sn, &cs);
+            const double mag = exp(q * lnrho);
+            const double cr = r >= 0 ? cfre[k] : cbre[k], ci = r >= 0 ? cfim[k] : cbim[k];
+            const double tr = cr * bbr - ci * bbi, ti = cr * bbi + ci * bbr;   // C B_bar
+            acc += tr * (mag * cs) - ti * (mag * sn);                         // Re(C B_bar lam^q)
+        } else {
+            const int r = ri;
+            double s1, c1, s2, c2, sN, cN;
+            sincos(r * th, &s1, &c1);
+            sincos((N - r) * th, &s2, &c2);
+            sincos(N * th, &sN, &cN);
+            const double m1 = exp(r * lnrho), m2 = exp((N - r) * lnrho), mN = exp(N * lnrho);
+            // Cf lam^r + Cb lam^(N-r)
+            const double nr = cfre[k] * m1 * c1 - cfim[k] * m1 * s1 + cbre[k] * m2 * c2 - cbim[k] * m2 * s2;
+            const double ni = cfre[k] * m1 * s1 + cfim[k] * m1 * c1 + cbre[k] * m2 * s2 + cbim[k] * m2 * c2;
+            const double tr = nr * bbr - ni * bbi, ti = nr * bbi + ni * bbr;
+            const double er = 1.0 - mN * cN, ei = -mN * sN, ee = er * er + ei * ei;
+            acc += (tr * er + ti * ei) / ee;                                  // Re(t / (1 - lam^N))
+        }
+    }
+    out[((long long)blk * R + ri) * d + c] = acc;
+}
+
+__global__ void k_omega(const double *__restrict__ gf, int N, int d, int periodic, double *__restrict__ omega) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * d) return;
+    const int i = idx / d, c = idx % d;
+    double acc = 0.0;
+    for (int k = 0; k < N; ++k) {
+        const int r = k - i;
+        const int row = periodic ? (r < 0 ? r + N : r) : r + N - 1;
+        acc += gf[(long long)row * d + c];
+    }
+    omega[idx] = acc / N;
+}
+
+cudaError_t launch_taps(const dn_model *m, int N, double *taps64, double *omega64, cudaStream_t st) {
+    const int L = m->desc.L, d = m->desc.d, s = m->desc.s, periodic = m->desc.periodic;
+    const int R = periodic ? N : 2 * N - 1;
+    dim3 grid((R + 127) / 128, d, L + 1);
+    {
+        ProfScope _ps("k_taps", st);
+        k_taps<<<grid, 128, 0, st>>>(m->params_dev, L, d, s, m->layer_size, (long long)L * m->layer_size, N, periodic,
+                                     R, taps64);
+    }
+    {
+        ProfScope _ps("k_omega", st);
+        k_omega<<<(N * d + 127) / 128, 128, 0, st>>>(taps64 + (long long)L * R * d, N, d, periodic, omega64);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_cast(const double *__restrict__ src, T *__restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
+}
+
+template <typename T>
+cudaError_t launch_cast(const double *src, T *dst, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    {
+        ProfScope _ps("k_cast", st);
+        k_cast<T><<<blocks, 256, 0, st>>>(src, dst, n);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void k_check_spins(const int8_t *__restrict__ spins, long long n, int8_t *__restrict__ copy,
+                              unsigned *__restrict__ flag) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int8_t v = spins[i];
+        if (copy) copy[i] = v;
+        if (v != 1 && v != -1) atomicOr(flag, 1u);
+    }
+}
+
+cudaError_t launch_check_spins(const int8_t *spins, long long n, int8_t *copy, unsigned *flag, cudaStream_t st) {
+    const int blocks = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
+    {
+        ProfScope _ps("k_check_spins", st);
+        k_check_spins<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(spins, n, copy, flag);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- chi --
+constexpr int kChiTile = 16;
+
+template <typename T>
+__global__ void k_chi(Geom g, Weights<T> w, const int8_t *__restrict__ spins, int B, T *__restrict__ chi) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
+    T *phi = reinterpret_cast<T *>(smraw);
+    T *act = phi + kChiTile * dh;
+    const int ntile = (N + kChiTile - 1) / kChiTile;
+    const long long blk = blockIdx.x;
+    const int tile = (int)(blk % ntile);
+    const long long rest = blk / ntile;
+    const int l = (int)(rest % L);
+    const long long b = rest / L;
+    const int i0 = tile * kChiTile;
+    const int ns = min(kChiTile, N - i0);
+    const int8_t *sp = spins + b * N;
+    const T *kap = w.kappa + (long long)l * W * dh;
+    const T *beta = w.beta + (long long)l * dh;
+    const T *W1T = w.W1T + (long long)l * dh * dh;
+    const T *b1 = w.b1 + (long long)l * dh;
+    const T *W2T = w.W2T + (long long)l * dh * d;
+    const T *b2 = w.b2 + (long long)l * d;
+    for (int idx = threadIdx.x; idx < ns * dh; idx += blockDim.x) {
+        const int t = idx / dh, e = idx % dh, i = i0 + t;
+        T acc = beta[e];
+        for (int r = -wd; r <= wd; ++r) {
+            int j = i + r;
+            T sv;
+            if (g.periodic) {
+                j = ((j % N) + N) % N;
+                sv = (T)sp[j];
+            } else {
+                sv = (j >= 0 && j < N) ? (T)sp[j] : (T)0;
+            }
+            acc += kap[(r + wd) * dh + e] * sv;
+        }
+        phi[t * dh + e] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ns * dh; idx += blockDim.x) {
+        const int t = idx / dh, e = idx % dh;
+        T acc = b1[e];
+        for (int f = 0; f < dh; ++f) acc += W1T[f * dh + e] * phi[t * dh + f];
+        act[t * dh + e] = gelu<T>(acc);
+    }
+    __syncthreads();
+    T *dst = chi + ((b * L + l) * N + i0) * d;
+    for (int idx = threadIdx.x; idx < ns * d; idx += blockDim.x) {
+        const int t = idx / d, c = idx % d;
+        T acc = b2[c];
+        for (int e = 0; e < dh; ++e) acc += W2T[e * d + c] * act[t * dh + e];
+        dst[(long long)t * d + c] = acc;
+    }
+}
+
+template <typename T>
+cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, int B, T *chi, cudaStream_t st) {
+    const int ntile = (g.N + kChiTile - 1) / kChiTile;
+    const long long blocks = (long long)B * g.L * ntile;
+    const size_t smem = 2 * kChiTile * g.dh * sizeof(T);
+    {
+        ProfScope _ps("k_chi", st);
+        k_chi<T><<<(unsigned)blocks, 128, smem, st>>>(g, w, spins, B, chi);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ conv --
+// One CTA per (field, channel tile).  Shared memory holds the taps of the
+// channel tile extended to offsets r in (-N, N) and the field's channels.
+template <typename T>
+__global__ void k_conv(Geom g, const T *__restrict__ taps_l, Fields<T> in, const int8_t *__restrict__ spins,
+                       const T *__restrict__ e, Fields<T> out, int CT, int transpose, const T *__restrict__ A,
+                       const T *__restrict__ omega) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d;
+    T *gx = reinterpret_cast<T *>(smraw);     // [2N-1][CT]
+    T *x = gx + (2 * N - 1) * CT;             // [N][CT]
+    const int nct = d / CT;
+    const long long f = blockIdx.x / nct;
+    const int c0 = (int)(blockIdx.x % nct) * CT;
+    for (int idx = threadIdx.x; idx < (2 * N - 1) * CT; idx += blockDim.x) {
+        const int q = idx / CT, c = idx % CT;
+        int r = q - (N - 1);
+        if (transpose) r = -r;
+        const int row = g.periodic ? (r < 0 ? r + N : r) : r + N - 1;
+        gx[idx] = taps_l[(long long)row * d + c0 + c];
+    }
+    if (spins) {
+        const int8_t *sp = spins + f * N;
+        for (int idx = threadIdx.x; idx < N * CT; idx += blockDim.x) {
+            const int j = idx / CT, c = idx % CT;
+            x[idx] = e[c0 + c] * (T)sp[j];
+        }
+    } else {
+        const T *src = in.at(f);
+        for (int idx = threadIdx.x; idx < N * CT; idx += blockDim.x) {
+            const int j = idx / CT, c = idx % CT;
+            x[idx] = src[(long long)j * d + c0 + c];
+        }
+    }
+    __syncthreads();
+    T *dst = out.at(f);
+    const int kk = A ? (int)(f % g.dout) : 0;
+    for (int idx = threadIdx.x; idx < N * CT; idx += blockDim.x) {
+        const int i = idx / CT, c = idx % CT;
+        const T *gp = gx + (i + N - 1) * CT + c;     // gx[(i - j) + N - 1] = gp[-j * CT]
+        T acc = 0;
+        for (int j = 0; j < N; ++j) acc += gp[-j * CT] * x[j * CT + c];
+        if (A) acc += A[(c0 + c) * g.dout + kk] * omega[(long long)i * d + c0 + c];
+        dst[(long long)i * d + c0 + c] = acc;
+    }
+}
+
+template <typename T>
+static int conv_tile(const Geom &g, size_t *smem) {
+    // Largest divisor of d (<= 32) whose taps + field tile fit in 200 KB.
+    int best = 1;
+    for (int ct = 1; ct <= 32 && ct <= g.d; ++ct) {
+        if (g.d % ct) continue;
+        size_t bytes = (size_t)(3 * g.N - 1) * ct * sizeof(T);
+        if (bytes <= 200 * 1024) best = ct;
+    }
+    *smem = (size_t)(3 * g.N - 1) * best * sizeof(T);
+    return best;
+}
+
+template <typename T>
+cudaError_t launch_conv(const Geom &g, const T *taps_l, Fields<T> in, const int8_t *spins, const T *e, Fields<T> out,
+                        long long F, bool transpose, const T *A, const T *omega, cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    size_t smem;
+    const int CT = conv_tile<T>(g, &smem);
+    if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
+    cudaError_t err = cudaFuncSetAttribute(k_conv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const long long blocks = F * (g.d / CT);
+    {
+        ProfScope _ps("k_conv", st);
+        k_conv<T><<<(unsigned)blocks, 256, smem, st>>>(g, taps_l, in, spins, e, out, CT, transpose ? 1 : 0, A, omega);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- mix --
+// One CTA per field; the CTA walks the sites in row tiles of TS = blockDim/d.
+// Thread (tr, a) owns output channel a of row tr of the tile.
+template <typename T>
+__global__ void k_mix(Geom g, int l, Weights<T> w, const T *__restrict__ chi, long long chi_stride, long long fps,
+                      long long f0, Fields<T> in, Fields<T> out, Fields<T> yout, const T *__restrict__ omega,
+                      double *__restrict__ pooled, long long pooled_stride, int adjoint) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d;
+    const int TS = blockDim.x / d;
+    const int a = threadIdx.x % d, tr = threadIdx.x / d;
+    const bool lane_ok = tr < TS;
+    T *xs = reinterpret_cast<T *>(smraw);   // [TS][d]
+    T *ts = xs + TS * d;                    // [TS][d]
+    double *red = reinterpret_cast<double *>(smraw + ((2 * (size_t)TS * d * sizeof(T) + 7) & ~(size_t)7));
+    const long long f = blockIdx.x;
+    const long long b = (f0 + f) / fps;
+    const T *chib = chi + b * chi_stride + (long long)(l - 1) * N * d;
+    const long long dd = (long long)d * d, lo = (long long)(l - 1) * dd;
+    // m1t[in][out], m2t[in][out]: forward M1 = V, M2 = U; adjoint M1 = U^T, M2 = V^T.
+    const T *m1t = adjoint ? w.U + lo : w.VT + lo;
+    const T *m2t = adjoint ? w.V + lo : w.UT + lo;
+    const T *src = in.at(f);
+    T *dst = out.at(f);
+    T *ydst = yout.base ? yout.at(f) : nullptr;
+    double pacc = 0.0;
+    for (int i0 = 0; i0 < N; i0 += TS) {
+        const int i = i0 + tr;
+        const bool act = lane_ok && i < N;
+        if (act) xs[tr * d + a] = src[(long long)i * d + a];
+        __syncthreads();
+        T yv = 0;
+        if (act) {
+            for (int bb = 0; bb < d; ++bb) yv += m1t[bb * d + a] * xs[tr * d + bb];
+            if (ydst) ydst[(long long)i * d + a] = yv;
+            ts[tr * d + a] = chib[(long long)i * d + a] * yv;
+        }
+        __syncthreads();
+        if (act) {
+            T hv = 0;
+            for (int bb = 0; bb < d; ++bb) hv += m2t[bb * d + a] * ts[tr * d + bb];
+            dst[(long long)i * d + a] = hv;
+            if (pooled) pacc += (double)omega[(long long)i * d + a] * (double)hv;
+        }
+        __syncthreads();
+    }
+    if (pooled) {
+        if (lane_ok) red[tr * d + a] = pacc;
+        __syncthreads();
+        if (tr == 0) {
+            double sum = 0.0;
+            for (int q = 0; q < TS; ++q) sum += red[q * d + a];
+            pooled[f * pooled_stride + a] = sum;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_mix(const Geom &g, int l, const Weights<T> &w, const T *chi, long long chi_stride,
+                          long long fields_per_sample, long long f0, Fields<T> in, Fields<T> out, Fields<T> yout,
+                          const T *omega, double *pooled, long long pooled_stride, long long F, bool adjoint,
+                          cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    int TS = 256 / g.d;
+    if (TS < 1) TS = 1;
+    const int threads = TS * g.d;
+    const size_t smem = 2 * (size_t)TS * g.d * sizeof(T) + 8 + (size_t)TS * g.d * sizeof(double);
+    {
+        ProfScope _ps("k_mix", st);
+        k_mix<T><<<(unsigned)F, threads, smem, st>>>(g, l, w, chi, chi_stride, fields_per_sample, f0, in, out, yout,
+                                                     omega, pooled, pooled_stride, adjoint ? 1 : 0);
+    }
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- readout --
+template <typename T>
+__global__ void k_pool0(Geom g, const int8_t *__restrict__ spins, const T *__restrict__ e,
+                        const T *__restrict__ omega, double *__restrict__ pooled, long long pooled_stride) {
+    const long long b = blockIdx.x;
+    const int N = g.N, d = g.d;
+    const int8_t *sp = spins + b * N;
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < N; ++i) acc += (double)omega[(long long)i * d + c] * (double)sp[i];
+        pooled[b * pooled_stride + c] = acc * (double)e[c];
+    }
+}
+
+template <typename T>
+cudaError_t launch_pool0(const Geom &g, const int8_t *spins, const T *e, const T *omega, int B, double *pooled,
+                         long long pooled_stride, cudaStream_t st) {
+    {
+        ProfScope _ps("k_pool0", st);
+        k_pool0<T><<<B, 64, 0, st>>>(g, spins, e, omega, pooled, pooled_stride);
+    }
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ double log_cosh(double x) {
+    const double a = fabs(x);
+    return a + log1p(exp(-2.0 * a)) - 0.69314718055994530942;
+}
+
+__global__ void k_readout(Geom g, int f_kind, const double *__restrict__ A64, const double *__restrict__ pooled,
+                          int npool, int B, const int8_t *__restrict__ spins, double *__restrict__ Omega,
+                          double *__restrict__ logpsi) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int d = g.d, dout = g.dout;
+    bool bad = false;
+    if (spins) {
+        const int8_t *sp = spins + (long long)b * g.N;
+        for (int i = 0; i < g.N; ++i) bad |= (sp[i] != 1 && sp[i] != -1);
+    }
+    double lp = 0.0;
+    for (int k = 0; k < dout; ++k) {
+        double acc = 0.0;
+        for (int c = 0; c < d; ++c) {
+            double pc = 0.0;
+            for (int q = 0; q < npool; ++q) pc += pooled[((long long)b * npool + q) * d + c];
+            acc += A64[c * dout + k] * pc;
+        }
+        if (bad) acc = nan("");
+        if (Omega) Omega[(long long)b * dout + k] = acc;
+        lp += f_kind == 0 ? log_cosh(acc) : acc;
+    }
+    if (logpsi) logpsi[b] = lp;
+}
+
+cudaError_t launch_readout(const Geom &g, int f_kind, const double *A64, const double *pooled, int npool, int B,
+                                 const int8_t *spins, double *Omega, double *logpsi, cudaStream_t st) {
+    {
+        ProfScope _ps("k_readout", st);
+        k_readout<<<(B + 127) / 128, 128, 0, st>>>(g, f_kind, A64, pooled, npool, B, spins, Omega, logpsi);
+    }
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- adjoint --
+template <typename T>
+__global__ void k_rho_init(Geom g, const T *__restrict__ A, const T *__restrict__ omega, Fields<T> out) {
+    const long long f = blockIdx.x;
+    const int k = (int)(f % g.dout);
+    T *dst = out.at(f);
+    for (int idx = threadIdx.x; idx < g.N * g.d; idx += blockDim.x) {
+        const int c = idx % g.d;
+        dst[idx] = A[c * g.dout + k] * omega[idx];
+    }
+}
+
+template <typename T>
+cudaError_t launch_rho_init(const Geom &g, const T *A, const T *omega, Fields<T> out, long long F, cudaStream_t st) {
+    {
+        ProfScope _ps("k_rho_init", st);
+        k_rho_init<T><<<(unsigned)F, 256, 0, st>>>(g, A, omega, out);
+    }
+    return cudaGetLastError();
+}
+
+// t[b][i][k] = e . rho^(0)[b][k][i][:]
+template <typename T>
+__global__ void k_tlink(Geom g, const T *__restrict__ rho0, const T *__restrict__ e, T *__restrict__ t) {
+    const long long b = blockIdx.x;
+    const int N = g.N, d = g.d, dout = g.dout;
+    for (int idx = threadIdx.x; idx < N * dout; idx += blockDim.x) {
+        const int i = idx / dout, k = idx % dout;
+        const T *r = rho0 + ((b * dout + k) * N + i) * d;
+        T acc = 0;
+        for (int c = 0; c < d; ++c) acc += e[c] * r[c];
+        t[(b * N + i) * dout + k] = acc;
+    }
+}
+
+template <typename T>
+cudaError_t launch_tlink(const Geom &g, const T *rho0, const T *e, int B, T *t, cudaStream_t st) {
+    {
+        ProfScope _ps("k_tlink", st);
+        k_tlink<T><<<B, 128, 0, st>>>(g, rho0, e, t);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- instantiations --
+#define DN_INST(T)                                                                                                    \
+    template cudaError_t launch_cast<T>(const double *, T *, long long, cudaStream_t);                               \
+    template cudaError_t launch_chi<T>(const Geom &, const Weights<T> &, const int8_t *, int, T *, cudaStream_t);    \
+    template cudaError_t launch_conv<T>(const Geom &, const T *, Fields<T>, const int8_t *, const T *, Fields<T>,     \
+                                        long long, bool, const T *, const T *, cudaStream_t);                        \
+    template cudaError_t launch_mix<T>(const Geom &, int, const Weights<T> &, const T *, long long, long long,     \
+                                          long long, Fields<T>, Fields<T>, Fields<T>, const T *, double *, long long, \
+                                          long long, bool, cudaStream_t);                                            \
+    template cudaError_t launch_pool0<T>(const Geom &, const int8_t *, const T *, const T *, int, double *,          \
+                                         long long, cudaStream_t);                                                   \
+    template cudaError_t launch_rho_init<T>(const Geom &, const T *, const T *, Fields<T>, long long, cudaStream_t); \
+    template cudaError_t launch_tlink<T>(const Geom &, const T *, const T *, int, T *, cudaStream_t);
+
+DN_INST(double)
+DN_INST(float)
+
+}  // namespace dn

@@ -1,0 +1,273 @@
+"""Thin Python binding of libdysonnet.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module converts
+torch tensors to raw pointers and status codes to exceptions.  It raises if
+the library is missing or no CUDA device is present: there is no CPU path.
+
+Names follow the C ABI in include/dysonnet.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+DN_OK, DN_EINVAL, DN_ENOMEM, DN_ECUDA, DN_ETIMEOUT, DN_EUNSUPPORTED = range(6)
+DN_FP64, DN_FP32 = 0, 1
+PRECISIONS = {"fp64": DN_FP64, "fp32": DN_FP32, torch.float64: DN_FP64, torch.float32: DN_FP32}
+
+
+class DysonNetError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib().dn_status_string(status).decode()}")
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("L", "d", "s", "w", "d_h", "d_out", "periodic", "f_kind")]
+
+
+class Hamiltonian(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("J", ctypes.c_double), ("alpha", ctypes.c_double), ("h", ctypes.c_double),
+                ("J1", ctypes.c_double), ("J2", ctypes.c_double), ("periodic", ctypes.c_int), ("kac", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_L = None
+_torch_alloc_installed = False
+_keep = []
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    global _L
+    if _L is not None:
+        return _L
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdysonnet.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, sz, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
+    sig = {
+        "dn_status_string": (ctypes.c_char_p, [i32]),
+        "dn_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
+        "dn_model_create": (i32, [ctypes.POINTER(ModelDesc), vp, sz, ctypes.POINTER(vp)]),
+        "dn_model_destroy": (None, [vp]),
+        "dn_cache_bytes": (sz, [vp, i32, i32, i32, i32]),
+        "dysonnet_forward_cache": (i32, [vp, i32, vp, i32, i32, i32, vp, ctypes.POINTER(vp), vp]),
+        "abacus_flip_ratios": (i32, [vp, vp, vp, i32, vp, vp]),
+        "local_energy": (i32, [vp, ctypes.POINTER(Hamiltonian), i32, vp, i32, i32, vp, vp]),
+        "dn_full_forward": (i32, [vp, i32, vp, i32, i32, vp, vp, vp]),
+        "dn_recompute_flip_ratios": (i32, [vp, i32, vp, i32, vp, vp, i32, i32, vp, vp]),
+        "dn_cache_check": (i32, [vp, vp]),
+        "dn_cache_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(i32)]),
+        "dn_cache_tensor": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(vp), ctypes.POINTER(sz),
+                                  ctypes.POINTER(i32)]),
+        "dn_cache_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _L = L
+    return L
+
+
+def exported_symbols():
+    """Names the binding expects from the library (all declared in dysonnet.h)."""
+    return ["dn_status_string", "dn_set_allocator", "dn_model_create", "dn_model_destroy", "dn_cache_bytes",
+            "dysonnet_forward_cache", "abacus_flip_ratios", "local_energy", "dn_full_forward",
+            "dn_recompute_flip_ratios", "dn_cache_check", "dn_cache_info", "dn_cache_tensor", "dn_cache_destroy"]
+
+
+def _check(status: int, what: str):
+    if status != DN_OK:
+        raise DysonNetError(status, what)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def install_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_alloc_installed
+    if _torch_alloc_installed:
+        return
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _keep.extend([a, f])
+    _check(_lib().dn_set_allocator(a, f, None), "dn_set_allocator")
+    _torch_alloc_installed = True
+
+
+def set_allocator(alloc_py, free_py):
+    """Install Python allocation callbacks (alloc(nbytes, stream) -> ptr or 0;
+    free(ptr, nbytes, stream)); pass None, None for the library default."""
+    global _torch_alloc_installed
+    if alloc_py is None:
+        _check(_lib().dn_set_allocator(ALLOC_FN(), FREE_FN(), None), "dn_set_allocator")
+        _torch_alloc_installed = False
+        return
+    a = ALLOC_FN(lambda n, s, c: alloc_py(int(n), int(s or 0)) or None)
+    f = FREE_FN(lambda p, n, s, c: free_py(int(p), int(n), int(s or 0)))
+    _keep.extend([a, f])
+    _check(_lib().dn_set_allocator(a, f, None), "dn_set_allocator")
+    _torch_alloc_installed = False
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("the DysonNet library needs a CUDA device; there is no CPU fallback")
+
+
+class Model:
+    """A DysonNet model held by the library (weights copied at creation)."""
+
+    def __init__(self, desc, params: np.ndarray, use_torch_allocator: bool = True):
+        _require_cuda()
+        if use_torch_allocator:
+            install_torch_allocator()
+        self.desc = desc
+        self._d = ModelDesc(desc.L, desc.d, desc.s, desc.w, desc.dh, desc.dout, desc.periodic, desc.fkind)
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(_lib().dn_model_create(ctypes.byref(self._d), p.ctypes.data_as(ctypes.c_void_p), p.size,
+                                      ctypes.byref(h)), "dn_model_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib().dn_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cache_bytes(self, N: int, batch: int, prec="fp32", max_cluster: int = 1) -> int:
+        return int(_lib().dn_cache_bytes(self._h, N, batch, PRECISIONS[prec], max_cluster))
+
+    def forward_cache(self, spins: torch.Tensor, prec="fp32", max_cluster: int = 1, stream=None,
+                      logpsi: torch.Tensor | None = None) -> "Cache":
+        """dysonnet_forward_cache: spins int8 [B][N] on the device."""
+        B, N = spins.shape
+        h = ctypes.c_void_p()
+        _check(_lib().dysonnet_forward_cache(self._h, N, _ptr(spins), B, PRECISIONS[prec], max_cluster,
+                                             _stream(stream), ctypes.byref(h), _ptr(logpsi)),
+               "dysonnet_forward_cache")
+        return Cache(self, h, spins)
+
+    def local_energy(self, ham: dict, spins: torch.Tensor, prec="fp32", stream=None,
+                     out: torch.Tensor | None = None) -> torch.Tensor:
+        B, N = spins.shape
+        if out is None:
+            out = torch.empty(B, dtype=torch.float64, device=spins.device)
+        H = Hamiltonian(int(ham.get("kind", 0)), float(ham.get("J", 0.0)), float(ham.get("alpha", 0.0)),
+                        float(ham.get("h", 0.0)), float(ham.get("J1", 0.0)), float(ham.get("J2", 0.0)),
+                        int(ham.get("periodic", 0)), int(ham.get("kac", 0)))
+        _check(_lib().local_energy(self._h, ctypes.byref(H), N, _ptr(spins), B, PRECISIONS[prec], _stream(stream),
+                                   _ptr(out)), "local_energy")
+        return out
+
+    def full_forward(self, spins: torch.Tensor, prec="fp32", stream=None, with_omega=False):
+        B, N = spins.shape
+        lp = torch.empty(B, dtype=torch.float64, device=spins.device)
+        om = torch.empty((B, self.desc.dout), dtype=torch.float64, device=spins.device) if with_omega else None
+        _check(_lib().dn_full_forward(self._h, N, _ptr(spins), B, PRECISIONS[prec], _stream(stream), _ptr(lp),
+                                      _ptr(om)), "dn_full_forward")
+        return (lp, om) if with_omega else lp
+
+    def recompute_flip_ratios(self, spins: torch.Tensor, sample: torch.Tensor, sites: torch.Tensor, prec="fp32",
+                              stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+        B, N = spins.shape
+        F = sample.shape[0]
+        if out is None:
+            out = torch.empty(F, dtype=torch.float64, device=spins.device)
+        _check(_lib().dn_recompute_flip_ratios(self._h, N, _ptr(spins), B, _ptr(sample), _ptr(sites), F,
+                                               PRECISIONS[prec], _stream(stream), _ptr(out)),
+               "dn_recompute_flip_ratios")
+        return out
+
+
+class Cache:
+    """Per-sample ABACUS caches built by dysonnet_forward_cache."""
+
+    def __init__(self, model: Model, handle, spins):
+        self.model, self._h = model, handle
+        self.N, self.B = spins.shape[1], spins.shape[0]
+
+    def flip_ratios(self, sample: torch.Tensor, sites: torch.Tensor, stream=None,
+                    out: torch.Tensor | None = None) -> torch.Tensor:
+        """abacus_flip_ratios: sample int32 [F], sites int32 [F][2] (-1 = unused)."""
+        F = sample.shape[0]
+        if out is None:
+            out = torch.empty(F, dtype=torch.float64, device=sample.device)
+        _check(_lib().abacus_flip_ratios(self._h, _ptr(sample), _ptr(sites), F, _ptr(out), _stream(stream)),
+               "abacus_flip_ratios")
+        return out
+
+    def check(self, stream=None) -> int:
+        return int(_lib().dn_cache_check(self._h, _stream(stream)))
+
+    def tensor(self, name: str) -> torch.Tensor:
+        """Copy of one cache array (inspection and debugging)."""
+        ptr, cnt, eb = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_int()
+        _check(_lib().dn_cache_tensor(self._h, name.encode(), ctypes.byref(ptr), ctypes.byref(cnt), ctypes.byref(eb)),
+               "dn_cache_tensor")
+        typestr = {1: "|i1", 4: "<f4", 8: "<f8"}[eb.value]
+        if cnt.value == 0:
+            return torch.empty(0, dtype={1: torch.int8, 4: torch.float32, 8: torch.float64}[eb.value], device="cuda")
+        torch.cuda.current_stream().synchronize()
+        return _device_view(ptr.value, cnt.value, typestr).clone()
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            _lib().dn_cache_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _device_view(ptr: int, count: int, typestr: str) -> torch.Tensor:
+    """Non-owning torch view of library-owned device memory."""
+
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, True), "version": 3}
+
+    return torch.as_tensor(_Arr(), device="cuda")

@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 oracle.
+
+Tolerances (relative error rel = |x - x_ref| / max(|x_ref|, 1e-3 (1 + |log psi_ref|))):
+  FP64 path <= 1e-10;  FP32 path <= 1e-4  (log-amplitude ratios).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import ModelDesc
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def dn():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_11189_gb300 import dysonnet
+    return dysonnet
+
+
+def rel_err(got, ref, lp_ref):
+    den = np.maximum(np.abs(ref), 1e-3 * (1.0 + np.abs(lp_ref)))
+    return np.abs(got - ref) / den
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_flips(dn, desc, params, spins_np, sample_np, sites_np, prec, max_cluster=1):
+    model = dn.Model(desc, params)
+    spins = cuda(spins_np)
+    lp = torch.empty(spins_np.shape[0], dtype=torch.float64, device="cuda")
+    cache = model.forward_cache(spins, prec=prec, max_cluster=max_cluster, logpsi=lp)
+    out = cache.flip_ratios(cuda(sample_np), cuda(sites_np)).cpu().numpy()
+    status = cache.check()
+    cache.destroy()
+    model.close()
+    return out, lp.cpu().numpy(), status
+
+
+def check_case(dn, desc, params, spins_np, sample_np, sites_np, prec, max_cluster=1):
+    got, lp_got, status = run_flips(dn, desc, params, spins_np, sample_np, sites_np, prec, max_cluster)
+    assert status == dn.DN_OK
+    ref = oracle.dlogpsi(desc, params, spins_np, sample_np, sites_np)
+    lp_ref, _ = oracle.logpsi(desc, params, spins_np)
+    e_lp = np.abs(lp_got - lp_ref) / np.maximum(1.0, np.abs(lp_ref))
+    e = rel_err(got, ref, lp_ref[sample_np])
+    assert e_lp.max() <= TOL[prec], f"log psi max rel err {e_lp.max():.3e}"
+    assert e.max() <= TOL[prec], f"dlogpsi max rel err {e.max():.3e} at flip {int(e.argmax())}"
+    return e.max()
+
+
+# ------------------------------------------------------------ workloads --
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_c1_workload_all_flips(dn, prec):
+    """N=16, 2 layers x 8 channels, 64 samples x all 16 single flips."""
+    cfg = synth.CONFIGS["c1"]
+    desc, params = cfg["desc"], synth.make_params(cfg)
+    spins = synth.make_spins(cfg)
+    sample, sites = synth.single_flips(cfg["B"], cfg["N"])
+    check_case(dn, desc, params, spins, sample, sites, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_c2_model_small_batch(dn, prec):
+    """The N=128, 4 x 32 x 32 model on 3 samples x all 128 flips (spans many
+    tiles; exercises all three interlayer links)."""
+    cfg = synth.CONFIGS["c2"]
+    desc, params = cfg["desc"], synth.make_params(cfg)
+    spins = synth.make_spins(cfg, B=3)
+    sample, sites = synth.single_flips(3, cfg["N"])
+    check_case(dn, desc, params, spins, sample, sites, prec)
+
+
+# ------------------------------------------------------- shapes & edges --
+
+CASES = [
+    # L, d, s, w, dh, dout, periodic, N, max_cluster
+    (1, 4, 3, 1, 5, 2, 0, 9, 1),
+    (2, 3, 4, 2, 3, 1, 1, 11, 1),
+    (3, 5, 2, 1, 4, 2, 0, 13, 3),
+    (4, 6, 3, 2, 6, 2, 1, 17, 2),
+    (5, 4, 3, 1, 3, 3, 1, 11, 3),
+    (6, 3, 2, 0, 2, 2, 0, 10, 3),
+    (3, 33, 5, 2, 17, 2, 0, 37, 2),    # ragged channel tiles
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shapes_single_and_pair_flips(dn, case, prec):
+    L, d, s, w, dh, dout, periodic, N, mc = case
+    desc = ModelDesc(L=L, d=d, s=s, w=w, dh=dh, dout=dout, periodic=periodic)
+    params = synth.init_params(desc, 100 + L * 7 + d, a_scale=6.0)
+    B = 3
+    spins = synth.spins_uniform(B, N, 31 + L)
+    sample, sites = synth.random_flips(B, N, 60, seed=L + d, pair_frac=0.6 if mc > 1 else 0.0,
+                                       max_sep=max(1, mc - 1), periodic=bool(periodic))
+    # chain ends and the wrap-around pair
+    extra_s = [0, 1, 2]
+    extra = [[0, -1], [N - 1, -1], [N - 2, N - 1] if mc > 1 else [N - 2, -1]]
+    if periodic and mc > 1:
+        extra_s.append(0)
+        extra.append([N - 1, 0])
+    sample = np.concatenate([sample, extra_s]).astype(np.int32)
+    sites = np.concatenate([sites, extra]).astype(np.int32)
+    check_case(dn, desc, params, spins, sample, sites, prec, max_cluster=mc)
+
+
+def test_tiny_chains(dn):
+    """N = 1 and N = 2 open chains (slices clipped on both sides), B = 1."""
+    for N in (1, 2, 3):
+        desc = ModelDesc(L=3, d=2, s=2, w=2, dh=2, dout=2, periodic=0)
+        params = synth.init_params(desc, 5 + N, a_scale=4.0)
+        spins = synth.spins_uniform(1, N, N)
+        sample, sites = synth.single_flips(1, N)
+        check_case(dn, desc, params, spins, sample, sites, "fp64")
+
+
+def test_empty_and_invalid_flips(dn):
+    desc = ModelDesc(L=3, d=4, s=3, w=1, dh=4, dout=2, periodic=0)
+    params = synth.init_params(desc, 8, a_scale=4.0)
+    N, B = 12, 2
+    spins = synth.spins_uniform(B, N, 3)
+    sample = np.array([0, 1, 0, 5, 1, 0, 1], dtype=np.int32)
+    sites = np.array([[-1, -1], [3, -1], [N, -1], [2, -1], [4, 4], [1, 4], [2, 3]], dtype=np.int32)
+    got, _, status = run_flips(dn, desc, params, spins, sample, sites, "fp64", max_cluster=2)
+    assert status == dn.DN_EINVAL
+    assert got[0] == 0.0
+    assert np.isnan(got[2]) and np.isnan(got[3]) and np.isnan(got[4]) and np.isnan(got[5])
+    ref = oracle.dlogpsi(desc, params, spins, sample[[1, 6]], sites[[1, 6]])
+    np.testing.assert_allclose(got[[1, 6]], ref, rtol=1e-10, atol=1e-12)
+
+
+def test_invalid_spins_give_nan(dn):
+    desc = ModelDesc(L=2, d=4, s=3, w=1, dh=4, dout=2)
+    params = synth.init_params(desc, 9)
+    spins = synth.spins_uniform(3, 8, 1)
+    spins[1, 4] = 0
+    model = dn.Model(desc, params)
+    lp = torch.empty(3, dtype=torch.float64, device="cuda")
+    cache = model.forward_cache(cuda(spins), prec="fp64", logpsi=lp)
+    assert cache.check() == dn.DN_EINVAL
+    lpn = lp.cpu().numpy()
+    assert np.isnan(lpn[1]) and np.isfinite(lpn[0]) and np.isfinite(lpn[2])
+    cache.destroy()
+    model.close()
+
+
+def test_zero_flips_and_bad_arguments(dn):
+    desc = ModelDesc(L=2, d=4, s=3, w=2, dh=4, dout=2, periodic=1)
+    params = synth.init_params(desc, 10)
+    model = dn.Model(desc, params)
+    spins = cuda(synth.spins_uniform(2, 9, 1))
+    cache = model.forward_cache(spins, prec="fp64")
+    empty = torch.empty(0, dtype=torch.int32, device="cuda")
+    out = cache.flip_ratios(empty, empty.reshape(0, 2))
+    assert out.numel() == 0
+    cache.destroy()
+    # periodic ring too short for the slice (N < 2 W_F - 1)
+    with pytest.raises(dn.DysonNetError) as ei:
+        model.forward_cache(cuda(synth.spins_uniform(2, 8, 1)), prec="fp64")
+    assert ei.value.status == dn.DN_EINVAL
+    with pytest.raises(dn.DysonNetError):
+        model.forward_cache(spins, prec="fp64", max_cluster=4)
+    model.close()
+
+
+def test_allocation_failure_is_reported(dn):
+    """A budget allocator that refuses large requests makes the cache build
+    return DN_ENOMEM and leaves the library usable."""
+    desc = synth.CONFIGS["c2"]["desc"]
+    params = synth.make_params(synth.CONFIGS["c2"])
+    model = dn.Model(desc, params)
+    spins = cuda(synth.spins_uniform(4, 128, 2))
+    keep = {}
+
+    def alloc(n, stream):
+        if n > (1 << 20):
+            return 0
+        t = torch.empty(n, dtype=torch.uint8, device="cuda")
+        keep[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def free(p, n, stream):
+        keep.pop(p, None)
+
+    try:
+        dn.set_allocator(alloc, free)
+        with pytest.raises(dn.DysonNetError) as ei:
+            model.forward_cache(spins, prec="fp32")
+        assert ei.value.status == dn.DN_ENOMEM
+    finally:
+        dn.set_allocator(None, None)
+        dn.install_torch_allocator()
+    cache = model.forward_cache(spins, prec="fp32")
+    assert cache.check() == dn.DN_OK
+    cache.destroy()
+    model.close()
+
+
+# ------------------------------------------------ local energy & baseline --
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_local_energy_tfim(dn, prec):
+    cfg = synth.CONFIGS["c1"]
+    desc, params = cfg["desc"], synth.make_params(cfg)
+    spins = synth.make_spins(cfg, B=16)
+    model = dn.Model(desc, params)
+    got = model.local_energy(cfg["ham"], cuda(spins), prec=prec).cpu().numpy()
+    ref = oracle.eloc(desc, params, cfg["ham"], spins)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))) <= tol
+    model.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_local_energy_j1j2_ring(dn, prec):
+    desc = ModelDesc(L=4, d=6, s=4, w=2, dh=6, dout=2, periodic=1)
+    params = synth.init_params(desc, 77, a_scale=6.0)
+    ham = dict(kind=1, J1=1.0, J2=0.5, periodic=1)
+    spins = synth.spins_zero_magnetisation(6, 14, 5)
+    model = dn.Model(desc, params)
+    got = model.local_energy(ham, cuda(spins), prec=prec).cpu().numpy()
+    ref = oracle.eloc(desc, params, ham, spins)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    assert np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))) <= tol
+    model.close()
+
+
+def test_local_energy_tfim_ring_kac(dn):
+    desc = ModelDesc(L=3, d=4, s=3, w=1, dh=4, dout=2, periodic=1)
+    params = synth.init_params(desc, 78, a_scale=5.0)
+    ham = dict(kind=0, J=-1.5, alpha=2.0, h=0.7, periodic=1, kac=1)
+    spins = synth.spins_uniform(5, 12, 6)
+    model = dn.Model(desc, params)
+    got = model.local_energy(ham, cuda(spins), prec="fp64").cpu().numpy()
+    ref = oracle.eloc(desc, params, ham, spins)
+    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-10)
+    model.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_forward_and_recompute_baseline(dn, prec):
+    desc = ModelDesc(L=3, d=5, s=3, w=1, dh=4, dout=2, periodic=0)
+    params = synth.init_params(desc, 90, a_scale=6.0)
+    spins = synth.spins_uniform(4, 15, 4)
+    sample, sites = synth.random_flips(4, 15, 40, seed=3, pair_frac=0.5)
+    model = dn.Model(desc, params)
+    lp, om = model.full_forward(cuda(spins), prec=prec, with_omega=True)
+    lp_ref, om_ref = oracle.logpsi(desc, params, spins)
+    tol = TOL[prec]
+    assert np.max(np.abs(lp.cpu().numpy() - lp_ref) / np.maximum(1, np.abs(lp_ref))) <= tol
+    assert np.max(np.abs(om.cpu().numpy() - om_ref) / np.maximum(1, np.abs(om_ref))) <= tol
+    got = model.recompute_flip_ratios(cuda(spins), cuda(sample), cuda(sites), prec=prec).cpu().numpy()
+    ref = oracle.dlogpsi(desc, params, spins, sample, sites)
+    assert rel_err(got, ref, lp_ref[sample]).max() <= (1e-10 if prec == "fp64" else 1e-3)
+    model.close()
+
+
+def test_jastrow_limit_identity_readout(dn):
+    """f = identity readout (the Jastrow test limit) through the GPU path."""
+    desc = ModelDesc(L=2, d=3, s=3, w=1, dh=3, dout=1, periodic=1, fkind=1)
+    params = synth.init_params(desc, 12, a_scale=2.0)
+    spins = synth.spins_uniform(3, 9, 2)
+    sample, sites = synth.single_flips(3, 9)
+    check_case(dn, desc, params, spins, sample, sites, "fp64")
