@@ -165,6 +165,24 @@ dn_status dn_recompute_flip_ratios(dn_model *model, int N, const int8_t *spins_d
                                    const int32_t *sample_dev, const int32_t *sites_dev, int F,
                                    dn_precision prec, void *stream, double *dlogpsi_dev);
 
+/* dn_full_forward() for callers that cannot allocate device memory during
+ * the call -- for example a host whose device memory is reserved up front by
+ * another runtime, or a server that forbids allocation after warm-up to keep
+ * its footprint fixed.  The paper has no counterpart; it is a deployment
+ * variant of the full forward pass.
+ * Same arguments and results as dn_full_forward().  Every temporary (packed
+ * weights, kernel taps, activations, pooled sums) lives in one fixed 16 MiB
+ * device array that each device loading the library holds until the process
+ * exits; no cudaMalloc, cudaFree or allocator call is made.  A call needs
+ * about B*N*d*(L+2)*t + B*(L+1)*d*8 bytes plus the weights and kernel taps
+ * (t = 8 for DN_FP64, 4 for DN_FP32); a request that does not fit returns
+ * DN_EINVAL and does nothing.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array and nothing in it needs clearing,
+ * but calls that overlap on the GPU (other streams or threads) race on it. */
+dn_status dn_full_forward_noalloc(const dn_model *model, int N, const int8_t *spins_dev, int B, dn_precision prec,
+                                  void *stream, double *logpsi_dev, double *Omega_dev);
+
 /* Wait for `stream`, then report the cache's sticky device flag:
  * DN_OK, DN_EINVAL (invalid spins or flip sites were seen), DN_ECUDA. */
 dn_status dn_cache_check(const dn_cache *cache, void *stream);

@@ -87,7 +87,8 @@ def exported_symbols():
     """Names the binding expects from the library (all declared in dysonnet.h)."""
     return ["dn_status_string", "dn_set_allocator", "dn_model_create", "dn_model_destroy", "dn_cache_bytes",
             "dysonnet_forward_cache", "abacus_flip_ratios", "local_energy", "dn_full_forward",
-            "dn_recompute_flip_ratios", "dn_cache_check", "dn_cache_info", "dn_cache_tensor", "dn_cache_destroy"]
+            "dn_recompute_flip_ratios", "dn_cache_check", "dn_cache_info", "dn_cache_tensor", "dn_cache_destroy",
+            "dn_full_forward_noalloc", "dn_launch_count", "dn_profile_enable", "dn_profile_count", "dn_profile_get"]
 
 
 def _check(status: int, what: str):

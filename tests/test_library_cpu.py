@@ -25,7 +25,7 @@ def _declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^(?!typedef)\s*(?:const\s+)?[A-Za-z_]\w*(?:\s+|\s*\*\s*)([A-Za-z_]\w*)\s*\(",
+        for m in re.finditer(r"^(?!typedef)\s*(?:const\s+)?(?:unsigned\s+|long\s+)*[A-Za-z_]\w*(?:\s+|\s*\*\s*)([A-Za-z_]\w*)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     names.discard("if")
