@@ -143,6 +143,16 @@ dn_status dysonnet_forward_cache(dn_model *model, int N, const int8_t *spins_dev
 dn_status abacus_flip_ratios(const dn_cache *cache, const int32_t *sample_dev, const int32_t *sites_dev,
                              int F, double *dlogpsi_dev, void *stream);
 
+/* ABACUS for every single flip of every cached configuration (the connected
+ * configurations of a transverse field, Sec. "Benchmarking"):
+ *   dlogpsi_dev [B][N] float64: entry (b, j) = log psi(sigma_b with site j
+ *   flipped) - log psi(sigma_b).
+ * Same results as abacus_flip_ratios() on the list of all single flips; the
+ * flips of a configuration are processed in groups of consecutive sites so that
+ * each link block is read from memory once per group.
+ * Errors: DN_EINVAL, DN_ECUDA. */
+dn_status abacus_single_flip_ratios(const dn_cache *cache, double *dlogpsi_dev, void *stream);
+
 /* Local energy E_loc(sigma) = sum_sigma' <sigma|H|sigma'> psi(sigma')/psi(sigma)
  * (Eq. local-estimator) for B configurations, every ratio by ABACUS:
  *   eloc_dev [B] float64.  Builds and frees its own caches (in chunks of
@@ -193,7 +203,7 @@ dn_status dn_cache_check(const dn_cache *cache, void *stream);
  * "t" ([B][N][d_out]), "ell" ([B][L-1][N][2Rl+1][d]: response at layer l of
  * the embedding at site i+o-Rl, Rl = W_F-1-w), "K" ([B][P][N][2Rk+1][d][d]:
  * links L^(l,m) of Eq. Lmn on the band |i-k| <= Rk = W_F-1, stored
- * [i][o][c_in][c_out] with k = i+o-Rk, pairs ordered (l,m) = (3,1), (4,1),
+ * [i][o][c_out][c_in] with k = i+o-Rk, pairs ordered (l,m) = (3,1), (4,1),
  * (4,2), ...), "Omega" (f64 [B][d_out]) or "logpsi" (f64 [B]).  Elements are
  * float64 for DN_FP64 caches and float32 for DN_FP32 caches.  Band entries
  * whose partner site lies off an open chain are unspecified.

@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_
     };
 
     double dom[kMaxDout];
-    for (int k = 0; k < dout; ++k) dom[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kMaxDout; ++k) dom[k] = 0.0;
     const long long nRk = 2 * a.Rk + 1, nRl = 2 * a.Rl + 1;
     const long long dd = (long long)d * d;
 
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_
                     const T *el = a.ell + (((b * (L - 1) + (l - 2)) * N + i) * nRl) * d;
                     for (int q = 0; q < nflip; ++q) acc += ds[q] * el[(offs(jf[q], i) + a.Rl) * d + c];
                     for (int m = 1; m <= l - 2; ++m) {
-                        const T *Kr = a.K + ((b * a.P + pair_index(l, m)) * N + i) * nRk * dd + c;
+                        const T *Kr = a.K + ((b * a.P + pair_index(l, m)) * N + i) * nRk * dd + (long long)c * d;
                         const T *Sm = S + (size_t)m * WF * d;
                         for (int t2 = 0; t2 < wf; ++t2) {
                             const int k = pos[t2];
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_
                             const T *Kb = Kr + (long long)(offs(k, i) + a.Rk) * dd;
                             const T *sv = Sm + t2 * d;
 #pragma unroll 8
-                            for (int c2 = 0; c2 < d; ++c2) acc += Kb[(long long)c2 * d] * sv[c2];
+                            for (int c2 = 0; c2 < d; ++c2) acc += Kb[c2] * sv[c2];
                         }
                     }
                 }
@@ -234,15 +235,18 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_
             T sv = 0;
             if (i >= 0) {
                 for (int c2 = 0; c2 < d; ++c2) sv += UT[c2 * d + c] * gz[t * d + c2];
-                for (int k = 0; k < dout; ++k)
-                    dom[k] += (double)a.rho[(((b * L + (l - 1)) * dout + k) * N + i) * d + c] * (double)sv;
+#pragma unroll
+                for (int k = 0; k < kMaxDout; ++k)
+                    if (k < dout) dom[k] += (double)a.rho[(((b * L + (l - 1)) * dout + k) * N + i) * d + c] * (double)sv;
             }
             Sl[idx] = sv;
         }
         __syncthreads();
     }
     // Block reduction of dOmega.
-    for (int k = 0; k < dout; ++k) red[k * blockDim.x + tid] = dom[k];
+#pragma unroll
+    for (int k = 0; k < kMaxDout; ++k)
+        if (k < dout) red[k * blockDim.x + tid] = dom[k];
     __syncthreads();
     if (tid < dout) {
         const int k = tid;
@@ -298,6 +302,377 @@ cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T>
     }
     return cudaGetLastError();
 }
+
+// ------------------------------------------- all single flips, by layer ----
+// The local estimator of a transverse field needs every single flip j of every
+// configuration.  The recurrence is evaluated for all of them one layer at a
+// time, each flip's slice state s^(l) kept in a scratch array between layers:
+//  k_dchi_table  dchi^(l) on every slot (flip j, slot t -> site j - w + t) for all
+//                layers: a batched per-site MLP with the flipped spin;
+//  k_ab_layer    layer l: one warp per (configuration, site i).  Site i is slot
+//                t = q of the W flips j = i + w - q.  The warp reads the link
+//                blocks L^(l,m)_{i,k} (|i-k| <= 2w) of its site once (lane = output
+//                channel, the lane's row of each block) and applies each to every
+//                flip whose slice holds both i and k; then it forms
+//                s^(l) = U (dchi * (y + V p)) for its W (flip, slot) pairs and adds
+//                rho^(l) . s^(l) to their partial dOmega;
+//  k_ab_final    dOmega_j = sum_t partial + t_j dsigma_j, and the log cosh difference.
+// Every link byte of a configuration is read once per call.
+constexpr int kLayMaxW = 9;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__ DX) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Geom &g = a.g;
+    const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
+    constexpr int RT = 64;                                  // rows per CTA
+    T *W1s = reinterpret_cast<T *>(smraw);                  // [dh][dh]  (in, out)
+    T *W2s = W1s + dh * dh;                                 // [dh][d]
+    T *ph = W2s + dh * d;                                   // [RT][dh]
+    T *ac = ph + RT * dh;                                   // [RT][dh]
+    const int l = blockIdx.y;
+    const long long rows = (long long)a.B * N * W;
+    const long long r0 = (long long)blockIdx.x * RT;
+    const T *W1T = a.w.W1T + (long long)l * dh * dh, *W2T = a.w.W2T + (long long)l * dh * d;
+    const T *b1 = a.w.b1 + (long long)l * dh, *b2 = a.w.b2 + (long long)l * d;
+    const T *kap = a.w.kappa + (long long)l * W * dh, *beta = a.w.beta + (long long)l * dh;
+    for (int q = threadIdx.x; q < dh * dh; q += blockDim.x) W1s[q] = W1T[q];
+    for (int q = threadIdx.x; q < dh * d; q += blockDim.x) W2s[q] = W2T[q];
+    for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
+        const int rr = q / dh, e = q % dh;
+        const long long r = r0 + rr;
+        T acc = 0;
+        if (r < rows) {
+            const int t = (int)(r % W), j = (int)((r / W) % N);
+            const long long b = r / ((long long)W * N);
+            const int8_t *sp = a.spins + b * N;
+            const int iu = j - wd + t;
+            const bool ok = g.periodic || (iu >= 0 && iu < N);
+            if (ok) {
+                acc = beta[e];
+                for (int o = -wd; o <= wd; ++o) {
+                    int jn = iu + o;
+                    T v;
+                    if (g.periodic) {
+                        jn = ((jn % N) + N) % N;
+                        v = (T)sp[jn];
+                    } else {
+                        v = (jn >= 0 && jn < N) ? (T)sp[jn] : (T)0;
+                    }
+                    if (jn == j) v = -v;
+                    acc += kap[(o + wd) * dh + e] * v;
+                }
+            }
+        }
+        ph[q] = acc;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
+        const int rr = q / dh, e = q % dh;
+        T acc = b1[e];
+        for (int f = 0; f < dh; ++f) acc += W1s[f * dh + e] * ph[rr * dh + f];
+        ac[q] = gelu_ab<T>(acc);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < RT * d; q += blockDim.x) {
+        const int rr = q / d, c = q % d;
+        const long long r = r0 + rr;
+        if (r >= rows) continue;
+        const int t = (int)(r % W), j = (int)((r / W) % N);
+        const long long b = r / ((long long)W * N);
+        int i = j - wd + t;
+        T v = 0;
+        if (g.periodic || (i >= 0 && i < N)) {
+            if (g.periodic) i = ((i % N) + N) % N;
+            T chin = b2[c];
+            for (int e = 0; e < dh; ++e) chin += W2s[e * d + c] * ac[rr * dh + e];
+            v = chin - a.chi[((b * L + l) * N + i) * d + c];
+        }
+        DX[((long long)l * rows + r) * d + c] = v;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T, int HD>
+__global__ void __launch_bounds__(256) k_ab_layer(AbArgs<T> a, int l, T *__restrict__ S, const T *__restrict__ DX,
+                                                  double *__restrict__ PART) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Geom &g = a.g;
+    const int N = g.N, d = g.d, L = g.L, wd = g.w, W = g.W, dout = g.dout;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long dd = (long long)d * d;
+    T *VTs = reinterpret_cast<T *>(smraw);                  // [d][d] = V^T
+    T *UTs = VTs + dd;                                      // [d][d] = U^T
+    T *wb = UTs + dd + (size_t)warp * (W * W * d + 2 * W * d);
+    T *Ss = wb;                                             // [W][W][d]  s^(m) of the warp's flips
+    T *pq = Ss + W * W * d;                                 // [W][d]
+    T *gq = pq + W * d;                                     // [W][d]
+    const long long lo = l - 1;
+    for (int q = threadIdx.x; q < dd; q += blockDim.x) {
+        VTs[q] = a.w.VT[lo * dd + q];
+        UTs[q] = a.w.UT[lo * dd + q];
+    }
+    __syncthreads();
+    const long long b = blockIdx.y;
+    const int i = blockIdx.x * 8 + warp;
+    if (i >= N) return;
+    const int8_t *sp = a.spins + b * N;
+    const long long rows = (long long)a.B * N * W;
+    const long long nRk = 2 * a.Rk + 1, nRl = 2 * a.Rl + 1;
+    // Flips served by this site: q -> j = i + w - q, slot t = q.
+    int jq[kLayMaxW];
+    T dsq[kLayMaxW];
+    unsigned valid = 0;
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) {
+        int j = i + wd - q;
+        bool ok = q < W;
+        if (g.periodic) j = ((j % N) + N) % N;
+        else ok = ok && j >= 0 && j < N;
+        jq[q] = ok ? j : 0;
+        dsq[q] = ok ? (T)(-2 * sp[j]) : (T)0;
+        if (ok) valid |= 1u << q;
+    }
+    auto tap = [&](int ll, int r, int c) -> T {
+        const int row = g.periodic ? ((r % N) + N) % N : r + N - 1;
+        return a.taps[((long long)(ll - 1) * g.R + row) * d + c];
+    };
+    auto site_ok = [&](int k) -> bool { return g.periodic || (k >= 0 && k < N); };
+    T acc[HD][kLayMaxW];
+#pragma unroll
+    for (int h = 0; h < HD; ++h)
+#pragma unroll
+        for (int q = 0; q < kLayMaxW; ++q) acc[h][q] = 0;
+    // Slice Toeplitz and embedding terms.
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) {
+        if (!((valid >> q) & 1u)) continue;
+        const int j = jq[q];
+#pragma unroll
+        for (int h = 0; h < HD; ++h) {
+            const int c = lane + 32 * h;
+            if (c >= d) continue;
+            T v;
+            if (l == 1) {
+                v = tap(1, q - wd, c) * a.w.e[c] * dsq[q];
+            } else {
+                v = 0;
+                const T *Sp = S + (lo - 1) * rows * d + (((long long)b * N + j) * W) * d + c;
+                for (int t2 = 0; t2 < W; ++t2)
+                    if (site_ok(j - wd + t2)) v += tap(l, q - t2, c) * Sp[(long long)t2 * d];
+                v += dsq[q] * a.ell[(((b * (L - 1) + (l - 2)) * N + i) * nRl + (wd - q + a.Rl)) * d + c];
+            }
+            acc[h][q] = v;
+        }
+    }
+    // Interlayer links.
+    for (int m = 1; m <= l - 2; ++m) {
+        for (int x = lane; x < W * W * d; x += 32) {
+            const int q = x / (W * d);
+            const int t2 = (x / d) % W, c2 = x % d;
+            Ss[x] = ((valid >> q) & 1u) ? S[(long long)(m - 1) * rows * d + (((long long)b * N + jq[q]) * W + t2) * d + c2]
+                                        : (T)0;
+        }
+        __syncwarp();
+        const T *Kr = a.K + ((b * a.P + pair_index(l, m)) * N + i) * nRk * dd;
+        for (int dl = -2 * wd; dl <= 2 * wd; ++dl) {
+            const int k = i + dl;
+            if (!site_ok(k)) continue;
+            const int qlo = dl < 0 ? -dl : 0, qhi = dl > 0 ? 2 * wd - dl : 2 * wd;
+            const T *Kb = Kr + (long long)(dl + a.Rk) * dd;
+#pragma unroll
+            for (int h = 0; h < HD; ++h) {
+                const int c = lane + 32 * h;
+                if (c >= d) continue;
+                const T *kr = Kb + (long long)c * d;
+                for (int c2 = 0; c2 < d; c2 += 4) {
+                    T kv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) kv[u] = (c2 + u < d) ? kr[c2 + u] : (T)0;
+#pragma unroll
+                    for (int q = 0; q < kLayMaxW; ++q) {
+                        if (q < qlo || q > qhi) continue;
+                        const T *sv = Ss + ((q * W) + (dl + q)) * d + c2;
+                        T sacc = 0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (c2 + u < d) sacc += kv[u] * sv[u];
+                        acc[h][q] += sacc;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // s^(l) = U (dchi * (y + V p)) and its contribution to dOmega.
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) {
+        if (q >= W) break;
+#pragma unroll
+        for (int h = 0; h < HD; ++h) {
+            const int c = lane + 32 * h;
+            if (c < d) pq[q * d + c] = acc[h][q];
+        }
+    }
+    __syncwarp();
+    const T *yrow = a.y + ((b * L + lo) * N + i) * d;
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) {
+        if (q >= W) break;
+        const bool ok = (valid >> q) & 1u;
+#pragma unroll
+        for (int h = 0; h < HD; ++h) {
+            const int c = lane + 32 * h;
+            if (c >= d) continue;
+            T z = yrow[c];
+            for (int c2 = 0; c2 < d; ++c2) z += VTs[c2 * d + c] * pq[q * d + c2];
+            const T dx = ok ? DX[(lo * rows + ((long long)b * N + jq[q]) * W + q) * d + c] : (T)0;
+            gq[q * d + c] = dx * z;
+        }
+    }
+    __syncwarp();
+    const T *rho = a.rho + ((b * L + lo) * dout) * (long long)N * d + (long long)i * d;
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) {
+        if (q >= W) break;
+        if (!((valid >> q) & 1u)) continue;
+        T sv[HD];
+#pragma unroll
+        for (int h = 0; h < HD; ++h) {
+            const int c = lane + 32 * h;
+            T s = 0;
+            if (c < d) {
+                for (int c2 = 0; c2 < d; ++c2) s += UTs[c2 * d + c] * gq[q * d + c2];
+                if (l < L) S[(lo * rows + ((long long)b * N + jq[q]) * W + q) * d + c] = s;
+            }
+            sv[h] = s;
+        }
+        for (int k = 0; k < dout; ++k) {
+            double v = 0.0;
+#pragma unroll
+            for (int h = 0; h < HD; ++h) {
+                const int c = lane + 32 * h;
+                if (c < d) v += (double)rho[(long long)k * N * d + c] * (double)sv[h];
+            }
+            v = warp_sum<double>(v);
+            if (lane == 0) PART[(((long long)b * N + jq[q]) * W + q) * dout + k] += v;
+        }
+    }
+}
+
+__global__ void k_ab_final(Geom g, int B, int f_kind, const int8_t *__restrict__ spins, const double *__restrict__ Omega,
+                           const double *__restrict__ PART, const void *__restrict__ tlink, int tsize,
+                           double *__restrict__ out) {
+    const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int N = g.N, W = g.W, dout = g.dout;
+    if (f >= (long long)B * N) return;
+    const long long b = f / N;
+    const int j = (int)(f % N);
+    const double ds = -2.0 * spins[b * N + j];
+    double res = 0.0;
+    for (int k = 0; k < dout; ++k) {
+        const long long ti = (b * N + j) * dout + k;
+        double s = (tsize == 8 ? static_cast<const double *>(tlink)[ti] : (double)static_cast<const float *>(tlink)[ti]) * ds;
+        for (int t = 0; t < W; ++t) s += PART[(f * W + t) * dout + k];
+        const double om = Omega[b * dout + k];
+        res += f_kind == 0 ? (log_cosh_ab(om + s) - log_cosh_ab(om)) : s;
+    }
+    out[f] = res;
+}
+
+template <typename T>
+static AbArgs<T> ab_args(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c) {
+    AbArgs<T> a;
+    a.g = geom_of(m, c->N);
+    a.B = c->B;
+    a.WF = c->WF;
+    a.Rk = c->Rk;
+    a.Rl = c->Rl;
+    a.P = c->P;
+    a.max_cluster = c->max_cluster;
+    a.f_kind = m->desc.f_kind;
+    a.spins = c->spins;
+    a.chi = static_cast<const T *>(c->chi);
+    a.y = static_cast<const T *>(c->y);
+    a.rho = static_cast<const T *>(c->rho);
+    a.t = static_cast<const T *>(c->t);
+    a.ell = static_cast<const T *>(c->ell);
+    a.K = static_cast<const T *>(c->K);
+    a.taps = pl.taps;
+    a.Omega = c->Omega;
+    a.flag = c->flag;
+    a.w = w;
+    return a;
+}
+
+size_t singles_scratch_bytes(const dn_model *m, const dn_cache *c) {
+    const size_t W = 2 * m->desc.w + 1, rows = (size_t)c->B * c->N * W;
+    const size_t tb = c->prec == DN_FP64 ? 8 : 4;
+    return 2 * (size_t)m->desc.L * rows * m->desc.d * tb + rows * m->desc.d_out * 8 + 1024;
+}
+
+template <typename T, int HD>
+static cudaError_t launch_ab_layer(const AbArgs<T> &a, int l, T *S, const T *DX, double *PART, cudaStream_t st) {
+    const Geom &g = a.g;
+    const size_t smem = (2 * (size_t)g.d * g.d + 8 * ((size_t)g.W * g.W * g.d + 2 * (size_t)g.W * g.d)) * sizeof(T);
+    cudaError_t err = cudaFuncSetAttribute(k_ab_layer<T, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((g.N + 7) / 8, a.B);
+    {
+        ProfScope _ps("k_ab_layer", st);
+        k_ab_layer<T, HD><<<grid, 256, smem, st>>>(a, l, S, DX, PART);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
+                                  void *scratch, double *out, cudaStream_t st) {
+    const Geom g = geom_of(m, c->N);
+    if (g.W > kLayMaxW || g.d > 128) return cudaErrorNotSupported;
+    const size_t lsm = (2 * (size_t)g.d * g.d + 8 * ((size_t)g.W * g.W * g.d + 2 * (size_t)g.W * g.d)) * sizeof(T);
+    const size_t tsm = ((size_t)g.dh * g.dh + (size_t)g.dh * g.d + 2 * 64 * (size_t)g.dh) * sizeof(T);
+    if (lsm > 220 * 1024 || tsm > 220 * 1024) return cudaErrorNotSupported;
+    const AbArgs<T> a = ab_args<T>(m, pl, w, c);
+    const long long rows = (long long)c->B * c->N * g.W;
+    T *DX = static_cast<T *>(scratch);
+    T *S = DX + (size_t)g.L * rows * g.d;
+    double *PART = reinterpret_cast<double *>(S + (size_t)g.L * rows * g.d);
+    cudaError_t err = cudaMemsetAsync(PART, 0, (size_t)rows * g.dout * sizeof(double), st);
+    if (err != cudaSuccess) return err;
+    if ((err = cudaFuncSetAttribute(k_dchi_table<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) !=
+        cudaSuccess)
+        return err;
+    {
+        ProfScope _ps("k_dchi_table", st);
+        k_dchi_table<T><<<dim3((unsigned)((rows + 63) / 64), g.L), 256, tsm, st>>>(a, DX);
+    }
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int hd = (g.d + 31) / 32;
+    for (int l = 1; l <= g.L; ++l) {
+        if (hd == 1) err = launch_ab_layer<T, 1>(a, l, S, DX, PART, st);
+        else if (hd == 2) err = launch_ab_layer<T, 2>(a, l, S, DX, PART, st);
+        else err = launch_ab_layer<T, 4>(a, l, S, DX, PART, st);
+        if (err != cudaSuccess) return err;
+    }
+    {
+        ProfScope _ps("k_ab_final", st);
+        k_ab_final<<<(unsigned)(((long long)c->B * c->N + 255) / 256), 256, 0, st>>>(
+            g, c->B, m->desc.f_kind, c->spins, c->Omega, PART, c->t, (int)sizeof(T), out);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_abacus_singles<double>(const dn_model *, const Plan<double> &, const Weights<double> &,
+                                                   const dn_cache *, void *, double *, cudaStream_t);
+template cudaError_t launch_abacus_singles<float>(const dn_model *, const Plan<float> &, const Weights<float> &,
+                                                  const dn_cache *, void *, double *, cudaStream_t);
 
 template cudaError_t launch_abacus<double>(const dn_model *, const Plan<double> &, const Weights<double> &,
                                            const dn_cache *, const int32_t *, const int32_t *, int, double *,

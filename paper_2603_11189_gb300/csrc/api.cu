@@ -511,6 +511,35 @@ dn_status abacus_flip_ratios(const dn_cache *c, const int32_t *sample_dev, const
     });
 }
 
+dn_status abacus_single_flip_ratios(const dn_cache *c, double *dlogpsi_dev, void *stream) {
+    if (!c || !dlogpsi_dev) return DN_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return guard([&]() -> dn_status {
+        dn::ProfPhase phase("abacus");
+        dn_model *m = c->model;
+        DevBuf scratch(dn::singles_scratch_bytes(m, c), st);
+        cudaError_t err = c->prec == DN_FP64 ? dn::launch_abacus_singles<double>(m, m->plan64.at(c->N), m->w64, c,
+                                                                                  scratch.p, dlogpsi_dev, st)
+                                             : dn::launch_abacus_singles<float>(m, m->plan32.at(c->N), m->w32, c,
+                                                                                 scratch.p, dlogpsi_dev, st);
+        if (err == cudaErrorNotSupported) {
+            // Shapes outside the grouped kernel: the general kernel on the explicit list.
+            cudaGetLastError();
+            const long long F = (long long)c->B * c->N;
+            DevBuf smp((size_t)F * sizeof(int32_t), st), sts((size_t)F * 2 * sizeof(int32_t), st);
+            ck(dn::launch_make_flips(0, c->N, c->B, 0, c->spins, smp.as<int32_t>(), sts.as<int32_t>(), st));
+            if (c->prec == DN_FP64)
+                err = dn::launch_abacus<double>(m, m->plan64.at(c->N), m->w64, c, smp.as<int32_t>(), sts.as<int32_t>(),
+                                                (int)F, dlogpsi_dev, st);
+            else
+                err = dn::launch_abacus<float>(m, m->plan32.at(c->N), m->w32, c, smp.as<int32_t>(), sts.as<int32_t>(),
+                                               (int)F, dlogpsi_dev, st);
+        }
+        ck(err);
+        return DN_OK;
+    });
+}
+
 dn_status local_energy(dn_model *m, const dn_hamiltonian *H, int N, const int8_t *spins_dev, int B,
                        dn_precision prec, void *stream, double *eloc_dev) {
     if (!m || !H || !spins_dev || !eloc_dev || B < 1 || N < 1) return DN_EINVAL;
@@ -545,14 +574,17 @@ dn_status local_energy(dn_model *m, const dn_hamiltonian *H, int N, const int8_t
             dn_cache *c = nullptr;
             dn_status s = dysonnet_forward_cache(m, N, spins_dev + (long long)b0 * N, n, prec, mc, stream, &c, nullptr);
             if (s != DN_OK) return s;
-            cudaError_t err = dn::launch_make_flips(H->kind, N, n, H->periodic, c->spins, smp.as<int32_t>(),
-                                                    sts.as<int32_t>(), st);
-            if (err == cudaSuccess) {
-                s = abacus_flip_ratios(c, smp.as<int32_t>(), sts.as<int32_t>(), n * per, dl.as<double>(), stream);
-                if (s == DN_OK)
-                    err = dn::launch_eloc_reduce(*H, N, n, c->spins, cb.as<double>(), dl.as<double>(), eloc_dev + b0,
-                                                 st);
+            cudaError_t err = cudaSuccess;
+            if (H->kind == 0) {
+                s = abacus_single_flip_ratios(c, dl.as<double>(), stream);
+            } else {
+                err = dn::launch_make_flips(H->kind, N, n, H->periodic, c->spins, smp.as<int32_t>(), sts.as<int32_t>(),
+                                            st);
+                if (err == cudaSuccess)
+                    s = abacus_flip_ratios(c, smp.as<int32_t>(), sts.as<int32_t>(), n * per, dl.as<double>(), stream);
             }
+            if (err == cudaSuccess && s == DN_OK)
+                err = dn::launch_eloc_reduce(*H, N, n, c->spins, cb.as<double>(), dl.as<double>(), eloc_dev + b0, st);
             dn_cache_destroy(c);
             if (s != DN_OK) return s;
             ck(err);

@@ -10,7 +10,8 @@
 //   ell    T    [B][L-1][N][2Rl+1][d]      ell^(l)_{i, i+o-Rl}: background response
 //                                          at layer l to the embedding of site i+o-Rl
 //   K      T    [B][P][N][2Rk+1][d][d]     links L^(l,m) (Eq. Lmn) on the band
-//                                          |i-k| <= Rk, stored [i][o][c_in][c_out]
+//                                          |i-k| <= Rk, k = i+o-Rk, each d x d block
+//                                          row-major [c_out][c_in]
 //   Omega  f64  [B][dout], logpsi f64 [B], flag u32
 // with W_F = 2w + max_cluster, Rk = W_F - 1, Rl = W_F - 1 - w and
 // P = (L-1)(L-2)/2 layer pairs (l, m), 1 <= m <= l-2, indexed (l-3)(l-2)/2 + m-1.
@@ -203,12 +204,19 @@ cudaError_t launch_tlink(const Geom &g, const T *rho0, const T *e, int B, T *t, 
 template <typename T>
 cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, dn_cache *c, T *scratch,
                         size_t scratch_elems, cudaStream_t st);
-size_t links_scratch_elems(const dn_model *m, int N, int nb_max);
+size_t links_scratch_elems(const dn_model *m, int N, int B);
 
 // ABACUS (abacus.cu).
 template <typename T>
 cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
                           const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st);
+// All N single flips of every cached configuration, out[b N + j], layer by
+// layer; scratch of singles_scratch_bytes() bytes (cudaErrorNotSupported when
+// the shape does not fit the kernels).
+size_t singles_scratch_bytes(const dn_model *m, const dn_cache *c);
+template <typename T>
+cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
+                                  void *scratch, double *out, cudaStream_t st);
 cudaError_t launch_make_flips(int kind, int N, int B, int periodic, const int8_t *spins, int32_t *sample,
                               int32_t *sites, cudaStream_t st);
 cudaError_t launch_eloc_reduce(const dn_hamiltonian &H, int N, int B, const int8_t *spins, const double *coupling,

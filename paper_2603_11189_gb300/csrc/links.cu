@@ -1,16 +1,21 @@
 // Interlayer link tensors (Eq. Lmn; App. "Exact algorithm to construct link
-// tensors", Eqs. B_def, X_def, L_def) by exact probe propagation.
+// tensors", Eqs. B_def, X_def, L_def) by exact propagation of unit sources.
 //
-// A probe is a unit source placed at the output of layer m at site k:
-//   m = 0:  the embedding e at site k            (N probes per sample);
-//   m >= 1: the unit vector e_c' at site k       (N d probes per sample).
-// It is propagated through the frozen background B^(n) = D0^(n) G^(n),
-// n = m+1, ..., and after G^(l) at every l >= m+2 its rows in the band
-// |i - k| <= R are stored:
-//   m = 0  -> ell^(l)_{i,k}       = [G^(l) X_{1,l-1} (e delta_k)]_i
-//   m >= 1 -> L^(l,m)_{i,k}[:,c'] = [G^(l) X_{m+1,l-1} (e_c' delta_k)]_i
-// The first G is the analytic kernel column g^(m+1)_{i-k}.  Only the last
-// layer's G is evaluated on the band alone.
+// A source is placed at the output of layer m at site k:
+//   m = 0:  the embedding e at site k          (P = N sources per sample, p = k);
+//   m >= 1: the unit vector e_c' at site k     (P = N d sources, p = k d + c').
+// The sources of one sample form a matrix X with rows (channel a, site n) and
+// columns p, stored channel-major [a][n][p].  Propagation through the frozen
+// background B^(n) = D0^(n) G^(n) is two GEMMs per layer:
+//   Toeplitz hop  Y[a] = T^(n)_a X[a]            T_a[i][j] = g^(n)_{i-j,a}: an
+//                                                  N x N by N x P product per channel
+//   vertex hop    X[:, i, :] = D0^(n)_i Y[:, i, :]  a d x d by d x P product per site
+// After every G^(l) with l >= m+2 the band rows |i - k| <= R of Y are stored:
+//   m = 0  -> ell^(l)_{i,k}        = [G^(l) X_{1,l-1} (e delta_k)]_i
+//   m >= 1 -> L^(l,m)_{i,k}[:, c'] = [G^(l) X_{m+1,l-1} (e_c' delta_k)]_i
+// For m >= 1 the first G is the analytic kernel column, so the first hop's
+// input X[a][n][(k,c')] = D0^(m+1)_n[a][c'] g^(m+1)_{n-k,c'} is generated inside
+// the kernel that consumes it; the last layer's G is evaluated on the band only.
 #include "dn_internal.cuh"
 
 namespace dn {
@@ -19,93 +24,426 @@ __device__ __forceinline__ int tap_row(int r, int N, int periodic) {
     return periodic ? (r < 0 ? r + N : (r >= N ? r - N : r)) : r + N - 1;
 }
 
-// u[p][i][c] = g^(m+1)_{i-k, c} * src_c  with src = e (m = 0) or e_c' (m >= 1).
-template <typename T>
-__global__ void k_probe_src(Geom g, int m, const T *__restrict__ taps, const T *__restrict__ e, long long p0,
-                            int nsrc, T *__restrict__ u) {
-    const long long pl = blockIdx.x;
-    const long long p = p0 + pl;
-    const int cp = (int)(p % nsrc);
-    const int k = (int)((p / nsrc) % g.N);
-    const int N = g.N, d = g.d;
-    T *dst = u + pl * N * d;
-    for (int idx = threadIdx.x; idx < N * d; idx += blockDim.x) {
-        const int i = idx / d, c = idx % d;
-        const T gv = taps[(long long)tap_row(i - k, N, g.periodic) * d + c];
-        dst[idx] = (m == 0) ? gv * e[c] : (c == cp ? gv : (T)0);
+// Site offset i - k reduced to (-N/2, N/2] on a ring.
+__device__ __forceinline__ int ring_delta(int dl, int N, int periodic) {
+    if (periodic) {
+        if (dl > N / 2) dl -= N;
+        else if (dl <= -((N + 1) / 2)) dl += N;
     }
+    return dl;
 }
 
+// Where band rows go: element (sample b, row i, offset o = R - (i - k), output
+// channel a, source channel c') is base[b*ss + i*rs + o*os + a*nsrc + c'].
 struct BandDst {
-    long long sample_stride, row_stride, o_stride;
-    int R;
+    long long ss, rs, os;
+    int R, nsrc;
 };
 
-// Store the band rows of full fields u (probes p0 .. p0+np) into the link array.
+// Generated first-hop input (sources at layer m >= 1): X[a][n][k d + c'] =
+// D0^(m+1)_n[a][c'] g^(m+1)_{n-k,c'}.
 template <typename T>
-__global__ void k_band_store(Geom g, const T *__restrict__ u, long long p0, int nsrc, T *__restrict__ dst,
-                             BandDst bd) {
-    const long long pl = blockIdx.x;
-    const long long p = p0 + pl;
-    const int cp = (int)(p % nsrc);
-    const long long q = p / nsrc;
-    const int k = (int)(q % g.N);
-    const long long b = q / g.N;
-    const int N = g.N, d = g.d, nrow = 2 * bd.R + 1;
-    const T *src = u + pl * N * d;
-    for (int idx = threadIdx.x; idx < nrow * d; idx += blockDim.x) {
-        const int dl = idx / d, c = idx % d;
-        const int delta = dl - bd.R;
-        int i = k + delta;
-        if (g.periodic) {
-            i = (i + N) % N;
-        } else if (i < 0 || i >= N) {
-            continue;
-        }
-        const int o = bd.R - delta;
-        dst[b * bd.sample_stride + (long long)i * bd.row_stride + (long long)o * bd.o_stride + (long long)cp * d + c] =
-            src[(long long)i * d + c];
-    }
+struct GenSrc {
+    const T *taps;   // layer m+1 taps [R][d]
+    const T *Dm;     // D0^(m+1) of sample 0 of the chunk: [n][a][c'], sample stride dm_ss
+    long long dm_ss;
+};
+
+template <typename T>
+__device__ __forceinline__ T gen_x(const GenSrc<T> &gs, int N, int d, int periodic, long long bl, int a, int n, int p) {
+    const int k = p / d, c = p - k * d;
+    return gs.Dm[bl * gs.dm_ss + ((long long)n * d + a) * d + c] * gs.taps[(long long)tap_row(n - k, N, periodic) * d + c];
 }
 
-// Band-only convolution of the last layer: link[i][o] = sum_j g_{i-j} v_j, i = k + delta.
+// ------------------------------------------------------------ site vertices --
+// Dm[b][l-1][n] = U diag(chi_n) V (row-major d x d) for layers 1..L-1.
 template <typename T>
-__global__ void k_conv_band(Geom g, const T *__restrict__ taps, const T *__restrict__ v, long long p0, int nsrc,
-                            T *__restrict__ dst, BandDst bd) {
-    const long long pl = blockIdx.x;
-    const long long p = p0 + pl;
-    const int cp = (int)(p % nsrc);
-    const long long q = p / nsrc;
-    const int k = (int)(q % g.N);
-    const long long b = q / g.N;
-    const int N = g.N, d = g.d, nrow = 2 * bd.R + 1;
-    const T *src = v + pl * N * d;
-    for (int idx = threadIdx.x; idx < nrow * d; idx += blockDim.x) {
-        const int dl = idx / d, c = idx % d;
-        const int delta = dl - bd.R;
-        int i = k + delta;
-        if (g.periodic) {
-            i = (i + N) % N;
-        } else if (i < 0 || i >= N) {
-            continue;
-        }
+__global__ void k_dmat(Geom g, Weights<T> w, const T *__restrict__ chi, long long b0, T *__restrict__ Dm) {
+    const int N = g.N, d = g.d, L = g.L;
+    const long long blk = blockIdx.x;
+    const int n = (int)(blk % N);
+    const int l = (int)((blk / N) % (L - 1)) + 1;
+    const long long bl = blk / ((long long)N * (L - 1));
+    const long long dd = (long long)d * d;
+    const T *U = w.U + (l - 1) * dd, *V = w.V + (l - 1) * dd;
+    const T *x = chi + (((b0 + bl) * L + (l - 1)) * N + n) * d;
+    T *dst = Dm + ((bl * (L - 1) + (l - 1)) * N + n) * dd;
+    for (int idx = threadIdx.x; idx < d * d; idx += blockDim.x) {
+        const int a = idx / d, c = idx % d;
         T acc = 0;
-        for (int j = 0; j < N; ++j) acc += taps[(long long)tap_row(i - j, N, g.periodic) * d + c] * src[(long long)j * d + c];
-        const int o = bd.R - delta;
-        dst[b * bd.sample_stride + (long long)i * bd.row_stride + (long long)o * bd.o_stride + (long long)cp * d + c] = acc;
+        for (int e = 0; e < d; ++e) acc += U[a * d + e] * x[e] * V[e * d + c];
+        dst[idx] = acc;
     }
 }
 
-size_t links_scratch_elems(const dn_model *m, int N, int nb_max) {
-    (void)nb_max;
-    const long long field = (long long)N * m->desc.d;
-    // Two probe batches of up to 2^14 fields, or at least one sample's worth of
-    // single-channel probes, whichever is smaller; at least 64 fields.
-    long long P = 16384;
-    const long long cap = (512ll << 20) / (2 * field * 8);   // ~512 MB at FP64
-    if (P > cap) P = cap;
-    if (P < 64) P = 64;
-    return (size_t)(2 * P * field);
+// Embedding sources through layer 1: X[b][a][n][k] = (D0^(1)_n (g^(1)_{n-k} * e))_a.
+// One CTA per (sample, site n): D0_n and the N needed tap rows are staged in
+// shared memory (rows padded to d+1 floats), then X[:, n, :] = D0_n G.
+template <typename T>
+__global__ void __launch_bounds__(256) k_embed_src(Geom g, const T *__restrict__ taps1, const T *__restrict__ e,
+                                                   const T *__restrict__ Dm, T *__restrict__ X) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d, L = g.L, dp = d + 1;
+    T *Ds = reinterpret_cast<T *>(smraw);      // [d][d]
+    T *Gs = Ds + d * d;                        // [N][d+1]
+    const long long blk = blockIdx.x;
+    const int n = (int)(blk % N);
+    const long long bl = blk / N;
+    const long long dd = (long long)d * d;
+    const T *D = Dm + ((bl * (L - 1)) * N + n) * dd;
+    for (int q = threadIdx.x; q < d * d; q += blockDim.x) Ds[q] = D[q];
+    for (int q = threadIdx.x; q < N * d; q += blockDim.x) {
+        const int k = q / d, c = q % d;
+        Gs[k * dp + c] = taps1[(long long)tap_row(n - k, N, g.periodic) * d + c] * e[c];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < d * N; idx += blockDim.x) {
+        const int a = idx / N, k = idx % N;
+        T acc = 0;
+        for (int c = 0; c < d; ++c) acc += Ds[a * d + c] * Gs[k * dp + c];
+        X[((bl * d + a) * N + n) * (long long)N + k] = acc;
+    }
+}
+
+// ------------------------------------------------------------ Toeplitz hop --
+// Y[b][a][i][p] = sum_n g_{i-n,a} X[b][a][n][p] on a 128 x 128 (i, p) tile per
+// CTA; 256 threads, each an 8 x 8 register tile (rows ty*8.., columns tx*4..
+// and 64 + tx*4..).  The Toeplitz operand is read from the channel's taps in
+// shared memory; X is staged 16 sites at a time, the next 16 sites' loads in
+// flight (in registers) while the current ones are multiplied.
+constexpr int kTgTile = 128, kTgK = 16, kTgOff = 16;
+
+template <typename T, bool GEN>
+__global__ void __launch_bounds__(256) k_tgemm(Geom g, const T *__restrict__ taps, int P, const T *__restrict__ X,
+                                               GenSrc<T> gs, T *__restrict__ Y, T *__restrict__ band, BandDst bd,
+                                               long long b0) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d;
+    T *gx = reinterpret_cast<T *>(smraw);                       // [kTgOff + 2N + kTgTile]
+    const int gx_len = kTgOff + 2 * N + kTgTile;
+    T *Bs = gx + ((gx_len + 3) & ~3);                           // [kTgK][kTgTile]
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int p0 = blockIdx.x * kTgTile;
+    const int i0 = blockIdx.y * kTgTile;
+    const long long za = blockIdx.z;
+    const int a = (int)(za % d);
+    const long long bl = za / d;
+    for (int q = tid; q < gx_len; q += blockDim.x) {
+        const int r = q - kTgOff - (N - 1);
+        T v = 0;
+        if (r > -N && r < N) v = taps[(long long)tap_row(r, N, g.periodic) * d + a];
+        gx[q] = v;
+    }
+    // This thread stages column pp of rows kr0 + 2r (r = 0..7) of every chunk.
+    const int pp = tid & (kTgTile - 1), kr0 = tid >> 7;
+    const int pl = p0 + pp;
+    const bool pok = pl < P;
+    int kq = 0, cq = 0;
+    if (GEN && pok) {
+        kq = pl / d;
+        cq = pl - kq * d;
+    }
+    const long long dd = (long long)d * d;
+    const T *dmcol = GEN ? gs.Dm + bl * gs.dm_ss + (long long)a * d + cq : nullptr;
+    const T *xcol = (!GEN && X) ? X + (bl * d + a) * (long long)N * P + pl : nullptr;
+    T st[8];
+    auto fetch = [&](int n0) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int n = n0 + kr0 + 2 * r;
+            T v = 0;
+            if (pok && n < N) {
+                if (GEN) v = dmcol[(long long)n * dd] * gs.taps[(long long)tap_row(n - kq, N, g.periodic) * d + cq];
+                else v = xcol[(long long)n * P];
+            }
+            st[r] = v;
+        }
+    };
+    T acc[8][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[q][j] = 0;
+    const int rbase = kTgOff + i0 + ty * 8 + N - 1;
+    fetch(0);
+    for (int n0 = 0; n0 < N; n0 += kTgK) {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 8; ++r) Bs[(kr0 + 2 * r) * kTgTile + pp] = st[r];
+        __syncthreads();
+        if (n0 + kTgK < N) fetch(n0 + kTgK);
+#pragma unroll 4
+        for (int kk = 0; kk < kTgK; ++kk) {
+            const int n = n0 + kk;
+            T av[8], bv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) av[q] = gx[rbase + q - n];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                bv[j] = Bs[kk * kTgTile + tx * 4 + j];
+                bv[4 + j] = Bs[kk * kTgTile + 64 + tx * 4 + j];
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[q][j] += av[q] * bv[j];
+        }
+    }
+    // Epilogue: full output and/or its band rows.
+    int kc[8], cc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int p = p0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+        kc[j] = p / bd.nsrc;
+        cc[j] = p - kc[j] * bd.nsrc;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int i = i0 + ty * 8 + q;
+        if (i >= N) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int p = p0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            if (p >= P) continue;
+            if (Y) Y[((bl * d + a) * N + i) * (long long)P + p] = acc[q][j];
+            if (band) {
+                const int dl = ring_delta(i - kc[j], N, g.periodic);
+                if (dl >= -bd.R && dl <= bd.R)
+                    band[(b0 + bl) * bd.ss + (long long)i * bd.rs + (long long)(bd.R - dl) * bd.os +
+                         (long long)a * bd.nsrc + cc[j]] = acc[q][j];
+            }
+        }
+    }
+}
+
+// -------------------------------------------------------------- vertex hop --
+// Xo[b][c][i][p] = sum_a D[b][i][c][a] Y[b][a][i][p]; one CTA per (sample,
+// site, column tile).  Fast path (d a multiple of 8, d <= 64): thread owns 8
+// output channels x 4 columns; D is staged transposed so that both operands
+// come as 16-byte shared-memory vectors.  Other d: one output per thread.
+template <typename T, bool FAST>
+__global__ void __launch_bounds__(256) k_dhop(Geom g, int P, int cols, const T *__restrict__ Dm, long long dm_ss,
+                                              const T *__restrict__ Yin, T *__restrict__ Xo) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d;
+    T *DsT = reinterpret_cast<T *>(smraw);      // [a][c] = D[c][a], rows padded to d+1
+    T *Ys = DsT + ((d * (d + 1) + 3) / 4 * 4);  // [a][cols], 16-byte aligned
+    const int p0 = blockIdx.x * cols;
+    const int i = blockIdx.y;
+    const long long bl = blockIdx.z;
+    const T *D = Dm + bl * dm_ss + (long long)i * d * d;
+    const int dp = d + 1;                       // padded rows: conflict-free transpose
+    for (int q = threadIdx.x; q < d * d; q += blockDim.x) {
+        const int c = q / d, a = q % d;
+        DsT[a * dp + c] = D[q];
+    }
+    if (sizeof(T) == 4 && P % 4 == 0 && cols % 4 == 0 && p0 + cols <= P) {
+        // 16-byte loads, several in flight per thread.
+        const int nv = d * cols / 4;
+#pragma unroll 8
+        for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+            const int a = (4 * q) / cols, pp = (4 * q) % cols;
+            const float4 v = *reinterpret_cast<const float4 *>(Yin + ((bl * d + a) * N + i) * (long long)P + p0 + pp);
+            *reinterpret_cast<float4 *>(Ys + (size_t)a * cols + pp) = v;
+        }
+    } else {
+#pragma unroll 4
+        for (int q = threadIdx.x; q < d * cols; q += blockDim.x) {
+            const int a = q / cols, pp = q % cols, p = p0 + pp;
+            Ys[q] = p < P ? Yin[((bl * d + a) * N + i) * (long long)P + p] : (T)0;
+        }
+    }
+    __syncthreads();
+    if (FAST) {
+        const int rg = d / 8, cgs = 256 / rg;
+        const int ty = threadIdx.x / cgs, tx = threadIdx.x % cgs;
+        if (ty >= rg) return;
+        T acc[8][4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[r][j] = 0;
+        for (int a = 0; a < d; ++a) {
+            T dv[8], yv[4];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) dv[r] = DsT[a * dp + ty * 8 + r];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) yv[j] = Ys[a * cols + tx * 4 + j];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[r][j] += dv[r] * yv[j];
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int c = ty * 8 + r;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = p0 + tx * 4 + j;
+                if (p < P) Xo[((bl * d + c) * N + i) * (long long)P + p] = acc[r][j];
+            }
+        }
+    } else {
+        for (int q = threadIdx.x; q < d * cols; q += blockDim.x) {
+            const int c = q / cols, pp = q % cols, p = p0 + pp;
+            if (p >= P) continue;
+            T acc = 0;
+            for (int a = 0; a < d; ++a) acc += DsT[a * dp + c] * Ys[a * cols + pp];
+            Xo[((bl * d + c) * N + i) * (long long)P + p] = acc;
+        }
+    }
+}
+
+// ------------------------------------------------------- last-layer band --
+// band[b][k+dl][R-dl][a][c'] = sum_n g^(L)_{k+dl-n,a} X[b][a][n][k nsrc + c'].
+// One warp per (sample, channel a, 32 consecutive source columns p = k nsrc + c'):
+// lane = column; it streams its column of X over n and keeps the 2R+1 taps
+// g_{k+dl-n} it needs in a register window that slides by one tap per site.
+constexpr int kBcMaxBand = 31;
+
+template <typename T, bool GEN, int NB>
+__global__ void __launch_bounds__(256) k_bandconv(Geom g, const T *__restrict__ taps, int P, const T *__restrict__ X,
+                                                  GenSrc<T> gs, T *__restrict__ band, BandDst bd, long long b0) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d, R = bd.R, ns = bd.nsrc;
+    const int pad = kBcMaxBand + 1;
+    T *gx = reinterpret_cast<T *>(smraw);       // gx[pad + r + N - 1] = g_{r,a}, zero outside (-N, N)
+    const int gx_len = 2 * N - 1 + 2 * pad;
+    const int chunks = (P + 255) / 256;         // 8 warps x 32 columns per CTA
+    const long long blk = blockIdx.x;
+    const int ch = (int)(blk % chunks);
+    const int a = (int)((blk / chunks) % d);
+    const long long bl = blk / ((long long)chunks * d);
+    for (int q = threadIdx.x; q < gx_len; q += blockDim.x) {
+        const int r = q - pad - (N - 1);
+        gx[q] = (r > -N && r < N) ? taps[(long long)tap_row(r, N, g.periodic) * d + a] : (T)0;
+    }
+    __syncthreads();
+    const int p = ch * 256 + threadIdx.x;
+    if (p >= P) return;
+    const int k = p / ns, c = p - k * ns;
+    const T *Xa = X ? X + (bl * d + a) * (long long)N * P + p : nullptr;
+    T acc[NB], win[NB];
+    // win[q] = g_{k - R + q - n} for the current n; on a ring the taps are circulant
+    // and the window index is reduced mod N by the tap table itself.
+    auto G = [&](int r) -> T {
+        if (g.periodic) r = ((r % N) + N) % N;
+        return gx[pad + r + N - 1];
+    };
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        acc[q] = 0;
+        win[q] = (q <= 2 * R) ? G(k - R + q) : (T)0;
+    }
+    for (int n = 0; n < N; ++n) {
+        const T xv = GEN ? gen_x<T>(gs, N, d, g.periodic, bl, a, n, p) : Xa[(long long)n * P];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) acc[q] += win[q] * xv;
+#pragma unroll
+        for (int q = NB - 1; q > 0; --q) win[q] = win[q - 1];
+        win[0] = G(k - R - n - 1);
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        if (q > 2 * R) break;
+        const int dl = q - R;
+        int i = k + dl;
+        if (g.periodic) i = ((i % N) + N) % N;
+        else if (i < 0 || i >= N) continue;
+        band[(b0 + bl) * bd.ss + (long long)i * bd.rs + (long long)(R - dl) * bd.os + (long long)a * ns + c] = acc[q];
+    }
+}
+
+// ------------------------------------------------------------------- host --
+static size_t links_per_sample_elems(const dn_model *m, int N) {
+    const long long d = m->desc.d, L = m->desc.L;
+    const long long P = N * d;
+    return (size_t)(2 * d * N * P + (L > 1 ? (L - 1) : 0) * N * d * d);
+}
+
+size_t links_scratch_elems(const dn_model *m, int N, int B) {
+    // Up to 6 GiB of probe fields (at 4 bytes per element), at least one sample.
+    const size_t per = links_per_sample_elems(m, N);
+    size_t nb = (size_t(6) << 30) / 4 / per;
+    if (nb < 1) nb = 1;
+    if (nb > (size_t)B) nb = (size_t)B;
+    return nb * per;
+}
+
+template <typename T>
+static cudaError_t launch_tgemm(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *Y, T *band,
+                                const BandDst &bd, long long b0, int nb, cudaStream_t st) {
+    const int gx_len = kTgOff + 2 * g.N + kTgTile;
+    const size_t smem = (((size_t)gx_len + 3) & ~size_t(3)) * sizeof(T) + (size_t)kTgK * kTgTile * sizeof(T);
+    cudaError_t err;
+    dim3 grid((P + kTgTile - 1) / kTgTile, (g.N + kTgTile - 1) / kTgTile, (unsigned)nb * g.d);
+    if (gs) {
+        err = cudaFuncSetAttribute(k_tgemm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        ProfScope _ps("k_tgemm", st);
+        k_tgemm<T, true><<<grid, 256, smem, st>>>(g, taps, P, nullptr, *gs, Y, band, bd, b0);
+    } else {
+        err = cudaFuncSetAttribute(k_tgemm<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        ProfScope _ps("k_tgemm", st);
+        k_tgemm<T, false><<<grid, 256, smem, st>>>(g, taps, P, X, GenSrc<T>{nullptr, nullptr, 0}, Y, band, bd, b0);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, bool GEN, int NB>
+static cudaError_t launch_bandconv_nb(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> &gs, T *band,
+                                      const BandDst &bd, long long b0, int nb, cudaStream_t st) {
+    const size_t smem = ((size_t)2 * g.N - 1 + 2 * (kBcMaxBand + 1)) * sizeof(T);
+    const int chunks = (P + 255) / 256;
+    const unsigned blocks = (unsigned)((long long)nb * g.d * chunks);
+    cudaError_t err = cudaFuncSetAttribute(k_bandconv<T, GEN, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_bandconv", st);
+        k_bandconv<T, GEN, NB><<<blocks, 256, smem, st>>>(g, taps, P, X, gs, band, bd, b0);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, bool GEN>
+static cudaError_t launch_bandconv_gen(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> &gs, T *band,
+                                       const BandDst &bd, long long b0, int nb, cudaStream_t st) {
+    const int nbw = 2 * bd.R + 1;
+    if (nbw <= 5) return launch_bandconv_nb<T, GEN, 5>(g, taps, P, X, gs, band, bd, b0, nb, st);
+    if (nbw <= 9) return launch_bandconv_nb<T, GEN, 9>(g, taps, P, X, gs, band, bd, b0, nb, st);
+    if (nbw <= 13) return launch_bandconv_nb<T, GEN, 13>(g, taps, P, X, gs, band, bd, b0, nb, st);
+    if (nbw <= kBcMaxBand) return launch_bandconv_nb<T, GEN, kBcMaxBand>(g, taps, P, X, gs, band, bd, b0, nb, st);
+    return cudaErrorInvalidConfiguration;
+}
+
+template <typename T>
+static cudaError_t launch_bandconv(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *band,
+                                   const BandDst &bd, long long b0, int nb, cudaStream_t st) {
+    if (gs) return launch_bandconv_gen<T, true>(g, taps, P, nullptr, *gs, band, bd, b0, nb, st);
+    return launch_bandconv_gen<T, false>(g, taps, P, X, GenSrc<T>{nullptr, nullptr, 0}, band, bd, b0, nb, st);
+}
+
+template <typename T>
+static cudaError_t launch_dhop(const Geom &g, int P, const T *Dm, long long dm_ss, const T *Y, T *Xo, int nb,
+                               cudaStream_t st) {
+    const bool fast = g.d % 8 == 0 && g.d <= 64;
+    const int cols = fast ? (256 / (g.d / 8)) * 4 : 128;
+    const size_t smem = (((size_t)g.d * (g.d + 1) + 3) / 4 * 4 + (size_t)g.d * cols) * sizeof(T);
+    dim3 grid((P + cols - 1) / cols, g.N, nb);
+    cudaError_t err;
+    if (fast) {
+        err = cudaFuncSetAttribute(k_dhop<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        ProfScope _ps("k_dhop", st);
+        k_dhop<T, true><<<grid, 256, smem, st>>>(g, P, cols, Dm, dm_ss, Y, Xo);
+    } else {
+        err = cudaFuncSetAttribute(k_dhop<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        ProfScope _ps("k_dhop", st);
+        k_dhop<T, false><<<grid, 256, smem, st>>>(g, P, cols, Dm, dm_ss, Y, Xo);
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -114,66 +452,68 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
     const Geom g = geom_of(m, c->N);
     const int N = g.N, d = g.d, L = g.L;
     if (L < 2) return cudaSuccess;
-    const long long field = (long long)N * d;
-    const long long Pmax = (long long)(scratch_elems / (2 * field));
-    if (Pmax < 1) return cudaErrorInvalidValue;
-    T *ubuf = scratch, *vbuf = scratch + Pmax * field;
+    const size_t per = links_per_sample_elems(m, N);
+    const int nb_max = (int)(scratch_elems / per);
+    if (nb_max < 1) return cudaErrorInvalidValue;
+    const long long Pm = (long long)N * d;                 // sources per sample, m >= 1
+    const long long dd = (long long)d * d;
+    const long long dm_ss = (long long)(L - 1) * N * dd;   // Dm sample stride
     const T *chi = static_cast<const T *>(c->chi);
-    const long long chi_stride = (long long)L * N * d;
     T *ell = static_cast<T *>(c->ell);
     T *K = static_cast<T *>(c->K);
     const int nRl = 2 * c->Rl + 1, nRk = 2 * c->Rk + 1;
-    Fields<T> none{nullptr, 0, 0, 1};
     cudaError_t err;
-    for (int msrc = 0; msrc <= L - 2; ++msrc) {
-        const int nsrc = msrc == 0 ? 1 : d;
-        const long long Q = (long long)c->B * N * nsrc;
-        for (long long p0 = 0; p0 < Q; p0 += Pmax) {
-            const long long np = (Q - p0 < Pmax) ? Q - p0 : Pmax;
-            Fields<T> U{ubuf, field, 0, 1}, V{vbuf, field, 0, 1};
-            {
-                ProfScope _ps("k_probe_src", st);
-                k_probe_src<T><<<(unsigned)np, 256, 0, st>>>(g, msrc, pl.taps + (long long)msrc * g.R * d, w.e, p0, nsrc,
-                                                             ubuf);
+    for (int b0 = 0; b0 < c->B; b0 += nb_max) {
+        const int nb = (c->B - b0 < nb_max) ? c->B - b0 : nb_max;
+        T *U = scratch;
+        T *F = U + (size_t)nb * d * N * Pm;
+        T *Dm = F + (size_t)nb * d * N * Pm;
+        {
+            ProfScope _ps("k_dmat", st);
+            k_dmat<T><<<(unsigned)((long long)nb * (L - 1) * N), 128, 0, st>>>(g, w, chi, b0, Dm);
+        }
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        // Embedding sources (m = 0), P = N.
+        {
+            const size_t smem = ((size_t)d * d + (size_t)N * (d + 1)) * sizeof(T);
+            if ((err = cudaFuncSetAttribute(k_embed_src<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess)
+                return err;
+            ProfScope _ps("k_embed_src", st);
+            k_embed_src<T><<<(unsigned)((long long)nb * N), 256, smem, st>>>(g, pl.taps, w.e, Dm, F);
+        }
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        for (int n = 2; n <= L; ++n) {
+            BandDst bd{(long long)(L - 1) * N * nRl * d, (long long)nRl * d, (long long)d, c->Rl, 1};
+            T *dst = ell + (long long)(n - 2) * N * nRl * d;
+            const T *taps_n = pl.taps + (long long)(n - 1) * g.R * d;
+            if (n < L) {
+                if ((err = launch_tgemm<T>(g, taps_n, N, F, nullptr, U, dst, bd, b0, nb, st)) != cudaSuccess) return err;
+                if ((err = launch_dhop<T>(g, N, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st)) != cudaSuccess)
+                    return err;
+            } else {
+                if ((err = launch_bandconv<T>(g, taps_n, N, F, nullptr, dst, bd, b0, nb, st)) != cudaSuccess) return err;
             }
-            if ((err = cudaGetLastError()) != cudaSuccess) return err;
-            err = launch_mix<T>(g, msrc + 1, w, chi, chi_stride, (long long)N * nsrc, p0, U, V, none, nullptr, nullptr,
-                                0, np, false, st);
-            if (err != cudaSuccess) return err;
+        }
+        // Interlayer sources (m >= 1), P = N d.
+        for (int msrc = 1; msrc <= L - 2; ++msrc) {
+            GenSrc<T> gs{pl.taps + (long long)msrc * g.R * d, Dm + (long long)msrc * N * dd, dm_ss};
             for (int n = msrc + 2; n <= L; ++n) {
-                BandDst bd;
-                T *dst;
-                if (msrc == 0) {
-                    bd.R = c->Rl;
-                    bd.sample_stride = (long long)(L - 1) * N * nRl * d;
-                    bd.row_stride = (long long)nRl * d;
-                    bd.o_stride = d;
-                    dst = ell + (long long)(n - 2) * N * nRl * d;
-                } else {
-                    bd.R = c->Rk;
-                    bd.sample_stride = (long long)c->P * N * nRk * d * d;
-                    bd.row_stride = (long long)nRk * d * d;
-                    bd.o_stride = (long long)d * d;
-                    dst = K + (long long)pair_index(n, msrc) * N * nRk * d * d;
-                }
+                BandDst bd{(long long)c->P * N * nRk * dd, (long long)nRk * dd, dd, c->Rk, d};
+                T *dst = K + (long long)pair_index(n, msrc) * N * nRk * dd;
                 const T *taps_n = pl.taps + (long long)(n - 1) * g.R * d;
+                const bool first = n == msrc + 2;
                 if (n < L) {
-                    err = launch_conv<T>(g, taps_n, V, nullptr, nullptr, U, np, false, nullptr, nullptr, st);
+                    err = launch_tgemm<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, U, dst, bd,
+                                          b0, nb, st);
                     if (err != cudaSuccess) return err;
-                    {
-                        ProfScope _ps("k_band_store", st);
-                        k_band_store<T><<<(unsigned)np, 256, 0, st>>>(g, ubuf, p0, nsrc, dst, bd);
-                    }
-                    if ((err = cudaGetLastError()) != cudaSuccess) return err;
-                    err = launch_mix<T>(g, n, w, chi, chi_stride, (long long)N * nsrc, p0, U, V, none, nullptr,
-                                        nullptr, 0, np, false, st);
-                    if (err != cudaSuccess) return err;
+                    if ((err = launch_dhop<T>(g, (int)Pm, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st)) !=
+                        cudaSuccess)
+                        return err;
                 } else {
-                    {
-                        ProfScope _ps("k_conv_band", st);
-                        k_conv_band<T><<<(unsigned)np, 256, 0, st>>>(g, taps_n, vbuf, p0, nsrc, dst, bd);
-                    }
-                    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+                    err = launch_bandconv<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, dst, bd,
+                                             b0, nb, st);
+                    if (err != cudaSuccess) return err;
                 }
             }
         }

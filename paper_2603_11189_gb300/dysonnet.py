@@ -65,6 +65,7 @@ def _lib():
         "dn_cache_bytes": (sz, [vp, i32, i32, i32, i32]),
         "dysonnet_forward_cache": (i32, [vp, i32, vp, i32, i32, i32, vp, ctypes.POINTER(vp), vp]),
         "abacus_flip_ratios": (i32, [vp, vp, vp, i32, vp, vp]),
+        "abacus_single_flip_ratios": (i32, [vp, vp, vp]),
         "local_energy": (i32, [vp, ctypes.POINTER(Hamiltonian), i32, vp, i32, i32, vp, vp]),
         "dn_full_forward": (i32, [vp, i32, vp, i32, i32, vp, vp, vp]),
         "dn_recompute_flip_ratios": (i32, [vp, i32, vp, i32, vp, vp, i32, i32, vp, vp]),
@@ -88,7 +89,7 @@ def exported_symbols():
     return ["dn_status_string", "dn_set_allocator", "dn_model_create", "dn_model_destroy", "dn_cache_bytes",
             "dysonnet_forward_cache", "abacus_flip_ratios", "local_energy", "dn_full_forward",
             "dn_recompute_flip_ratios", "dn_cache_check", "dn_cache_info", "dn_cache_tensor", "dn_cache_destroy",
-            "dn_full_forward_noalloc", "dn_launch_count", "dn_profile_enable", "dn_profile_count", "dn_profile_get"]
+            "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable", "dn_profile_count", "dn_profile_get"]
 
 
 def _check(status: int, what: str):
@@ -237,6 +238,13 @@ class Cache:
             out = torch.empty(F, dtype=torch.float64, device=sample.device)
         _check(_lib().abacus_flip_ratios(self._h, _ptr(sample), _ptr(sites), F, _ptr(out), _stream(stream)),
                "abacus_flip_ratios")
+        return out
+
+    def single_flip_ratios(self, stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+        """abacus_single_flip_ratios: [B][N] ratios of every single flip."""
+        if out is None:
+            out = torch.empty((self.B, self.N), dtype=torch.float64, device="cuda")
+        _check(_lib().abacus_single_flip_ratios(self._h, _ptr(out), _stream(stream)), "abacus_single_flip_ratios")
         return out
 
     def check(self, stream=None) -> int:

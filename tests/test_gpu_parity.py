@@ -80,6 +80,34 @@ def test_c2_model_small_batch(dn, prec):
     check_case(dn, desc, params, spins, sample, sites, prec)
 
 
+@pytest.mark.parametrize("case", [
+    # L, d, s, w, dh, dout, periodic, N, B, max_cluster
+    (4, 32, 32, 2, 32, 2, 0, 128, 3, 1),   # the N=128 workload model
+    (3, 5, 3, 1, 4, 2, 1, 19, 2, 1),
+    (4, 6, 3, 2, 6, 3, 0, 40, 2, 2),       # cache wider than single flips need
+    (2, 8, 4, 2, 8, 2, 0, 7, 2, 1),        # N below the flip group size
+    (5, 3, 2, 3, 3, 1, 1, 17, 2, 1),       # w = 3 on a ring
+])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_all_single_flips_grouped(dn, case, prec):
+    """abacus_single_flip_ratios (flips grouped by consecutive sites) against the oracle."""
+    L, d, s, w, dh, dout, periodic, N, B, mc = case
+    desc = ModelDesc(L=L, d=d, s=s, w=w, dh=dh, dout=dout, periodic=periodic)
+    params = synth.init_params(desc, 300 + L + d, a_scale=8.0)
+    spins = synth.spins_uniform(B, N, 17 + N)
+    model = dn.Model(desc, params)
+    cache = model.forward_cache(cuda(spins), prec=prec, max_cluster=mc)
+    got = cache.single_flip_ratios().cpu().numpy().reshape(-1)
+    assert cache.check() == dn.DN_OK
+    cache.destroy()
+    model.close()
+    sample, sites = synth.single_flips(B, N)
+    ref = oracle.dlogpsi(desc, params, spins, sample, sites)
+    lp_ref, _ = oracle.logpsi(desc, params, spins)
+    e = rel_err(got, ref, lp_ref[sample])
+    assert e.max() <= TOL[prec], f"max rel err {e.max():.3e} at {int(e.argmax())}"
+
+
 # ------------------------------------------------------- shapes & edges --
 
 CASES = [
