@@ -566,6 +566,227 @@ __global__ void __launch_bounds__(256) k_ab_layer(AbArgs<T> a, int l, T *__restr
     }
 }
 
+// Fast path of k_ab_layer for FP32 with d = 32: the link blocks of the warp's
+// site are streamed into a double-buffered shared-memory slot by the bulk-copy
+// engine (cp.async.bulk, completion on an mbarrier; every wait is bounded and a
+// timeout raises bit 4 of the cache flag).  Lane c reads 16-byte chunks of row
+// c of a block in the order (s + c) mod 8, so that the 8 lanes of a shared-memory
+// phase hit 8 different bank groups; the slice states are read in the same order.
+constexpr int kTmaWarps = 8;
+constexpr long kSpinLimit = 1L << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long it = 0; it < kSpinLimit; ++it) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_addr(mbar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(256) k_ab_layer_tma(AbArgs<float> a, int l, float *__restrict__ S,
+                                                      const float *__restrict__ DX, double *__restrict__ PART) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int d = 32;
+    const Geom &g = a.g;
+    const int N = g.N, L = g.L, wd = g.w, W = g.W, dout = g.dout;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int dd = d * d;
+    float *VTs = reinterpret_cast<float *>(smraw);                 // [d][d]
+    float *UTs = VTs + dd;                                         // [d][d]
+    float *Gs = UTs + dd;                                          // [4w+1][d] taps g^(l)_{-2w..2w}
+    const int per_warp = 2 * dd + W * W * d + 2 * W * d;
+    float *wb = Gs + (4 * wd + 1) * d + (size_t)warp * per_warp;
+    float *Kbuf = wb;                                              // [2][d][d]
+    float *Ss = Kbuf + 2 * dd;                                     // [W][W][d]
+    float *pq = Ss + W * W * d;                                    // [W][d]
+    float *gq = pq + W * d;                                        // [W][d]
+    uint64_t *mbars = reinterpret_cast<uint64_t *>(smraw + ((size_t)(2 * dd + (4 * wd + 1) * d + kTmaWarps * per_warp) *
+                                                                sizeof(float)));
+    uint64_t *mb = mbars + 2 * warp;
+    const long long lo = l - 1;
+    for (int q = threadIdx.x; q < dd; q += blockDim.x) {
+        VTs[q] = a.w.VT[lo * dd + q];
+        UTs[q] = a.w.UT[lo * dd + q];
+    }
+    for (int q = threadIdx.x; q < (4 * wd + 1) * d; q += blockDim.x) {
+        const int r = q / d - 2 * wd, c = q % d;
+        const int row = g.periodic ? ((r % N) + N) % N : (r > -N && r < N ? r + N - 1 : -1);
+        Gs[q] = row >= 0 ? a.taps[((long long)lo * g.R + row) * d + c] : 0.f;
+    }
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb + 1)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    const long long b = blockIdx.y;
+    const int i = blockIdx.x * kTmaWarps + warp;
+    if (i >= N) return;
+    const int8_t *sp = a.spins + b * N;
+    const long long rows = (long long)a.B * N * W;
+    const long long nRk = 2 * a.Rk + 1, nRl = 2 * a.Rl + 1;
+    int jq[kLayMaxW];
+    float dsq[kLayMaxW];
+    unsigned valid = 0;
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) {
+        int j = i + wd - q;
+        bool ok = q < W;
+        if (g.periodic) j = ((j % N) + N) % N;
+        else ok = ok && j >= 0 && j < N;
+        jq[q] = ok ? j : 0;
+        dsq[q] = ok ? (float)(-2 * sp[j]) : 0.f;
+        if (ok) valid |= 1u << q;
+    }
+    auto site_ok = [&](int k) -> bool { return g.periodic || (k >= 0 && k < N); };
+    // Stage s^(m) of the warp's flips: Ss[q][t2][:].
+    auto stage = [&](int m) {
+        const float *src = S + (long long)(m - 1) * rows * d;
+#pragma unroll 5
+        for (int x = lane; x < W * W * (d / 4); x += 32) {
+            const int q = x / (W * (d / 4)), t2 = (x / (d / 4)) % W, c4 = x % (d / 4);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((valid >> q) & 1u) v = *reinterpret_cast<const float4 *>(src + (((long long)b * N + jq[q]) * W + t2) * d + 4 * c4);
+            *reinterpret_cast<float4 *>(Ss + (q * W + t2) * d + 4 * c4) = v;
+        }
+        __syncwarp();
+    };
+    float acc[kLayMaxW];
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) acc[q] = 0.f;
+    const int c = lane;
+    // Slice Toeplitz and embedding terms.
+    if (l == 1) {
+#pragma unroll
+        for (int q = 0; q < kLayMaxW; ++q)
+            if ((valid >> q) & 1u) acc[q] = Gs[(q - wd + 2 * wd) * d + c] * a.w.e[c] * dsq[q];
+    } else {
+        stage(l - 1);
+        const float *el = a.ell + ((b * (L - 1) + (l - 2)) * N + i) * nRl * d;
+#pragma unroll
+        for (int q = 0; q < kLayMaxW; ++q) {
+            if (!((valid >> q) & 1u)) continue;
+            const int j = jq[q];
+            float v = dsq[q] * el[(wd - q + a.Rl) * d + c];
+            for (int t2 = 0; t2 < W; ++t2)
+                if (site_ok(j - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * Ss[(q * W + t2) * d + c];
+            acc[q] = v;
+        }
+        __syncwarp();
+    }
+    // Interlayer links: stream the site's blocks (m, dl) in order through two buffers.
+    const int nper = 4 * wd + 1;
+    const int nblk = (l - 2) > 0 ? (l - 2) * nper : 0;
+    bool timed_out = false;
+    // Copy number n goes to slot n & 1; a slot is refilled only after it has been consumed.
+    uint32_t issued_s[2] = {0u, 0u}, consumed_s[2] = {0u, 0u};
+    int issue_bi = 0, issue_cnt = 0;
+    auto blk_ok = [&](int bi) -> bool { return site_ok(i + (bi % nper) - 2 * wd); };
+    auto issue_next = [&]() {
+        while (issue_bi < nblk && !blk_ok(issue_bi)) ++issue_bi;
+        if (issue_bi >= nblk) return;
+        const int slot = issue_cnt & 1;
+        if (lane == 0) {
+            const int m = issue_bi / nper + 1, dl = issue_bi % nper - 2 * wd;
+            const float *src = a.K + (((b * a.P + pair_index(l, m)) * N + i) * nRk + (dl + a.Rk)) * (long long)dd;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_load(Kbuf + slot * dd, src, dd * sizeof(float), mb + slot);
+        }
+        issued_s[slot]++;
+        ++issue_bi;
+        ++issue_cnt;
+    };
+    issue_next();
+    issue_next();
+    int cnt = 0, cur_m = 0;
+    for (int bi = 0; bi < nblk && !timed_out; ++bi) {
+        if (!blk_ok(bi)) continue;
+        const int slot = cnt & 1;
+        ++cnt;
+        const int m = bi / nper + 1, dl = bi % nper - 2 * wd;
+        if (m != cur_m) {
+            stage(m);
+            cur_m = m;
+        }
+        if (!mbar_wait(mb + slot, consumed_s[slot] & 1u)) {
+            timed_out = true;
+            break;
+        }
+        consumed_s[slot]++;
+        const float *Kb = Kbuf + slot * dd + c * d;
+        const int qlo = dl < 0 ? -dl : 0, qhi = dl > 0 ? 2 * wd - dl : 2 * wd;
+#pragma unroll
+        for (int s = 0; s < d / 4; ++s) {
+            const int ch = (s + lane) & (d / 4 - 1);
+            const float4 kv = *reinterpret_cast<const float4 *>(Kb + 4 * ch);
+#pragma unroll
+            for (int q = 0; q < kLayMaxW; ++q) {
+                if (q < qlo || q > qhi || !((valid >> q) & 1u)) continue;
+                const float4 sv = *reinterpret_cast<const float4 *>(Ss + (q * W + (dl + q)) * d + 4 * ch);
+                acc[q] += kv.x * sv.x + kv.y * sv.y + kv.z * sv.z + kv.w * sv.w;
+            }
+        }
+        __syncwarp();
+        issue_next();
+    }
+    if (timed_out) {
+        // Let copies still in flight land before the shared memory is released.
+        if (lane == 0) atomicOr(a.flag, 4u);
+        for (int sl = 0; sl < 2; ++sl)
+            while (consumed_s[sl] < issued_s[sl]) {
+                mbar_wait(mb + sl, consumed_s[sl] & 1u);
+                consumed_s[sl]++;
+            }
+        return;
+    }
+    // s^(l) = U (dchi * (y + V p)) and its contribution to dOmega.
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q)
+        if (q < W) pq[q * d + c] = acc[q];
+    __syncwarp();
+    const float yc = a.y[((b * L + lo) * N + i) * d + c];
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) {
+        if (q >= W) break;
+        const bool ok = (valid >> q) & 1u;
+        float z = yc;
+#pragma unroll 8
+        for (int c2 = 0; c2 < d; ++c2) z += VTs[c2 * d + c] * pq[q * d + c2];
+        const float dx = ok ? DX[(lo * rows + ((long long)b * N + jq[q]) * W + q) * d + c] : 0.f;
+        gq[q * d + c] = dx * z;
+    }
+    __syncwarp();
+    const float *rho = a.rho + ((b * L + lo) * dout) * (long long)N * d + (long long)i * d;
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) {
+        if (q >= W) break;
+        if (!((valid >> q) & 1u)) continue;
+        float s = 0.f;
+#pragma unroll 8
+        for (int c2 = 0; c2 < d; ++c2) s += UTs[c2 * d + c] * gq[q * d + c2];
+        if (l < L) S[(lo * rows + ((long long)b * N + jq[q]) * W + q) * d + c] = s;
+        for (int k = 0; k < dout; ++k) {
+            double v = (double)rho[(long long)k * N * d + c] * (double)s;
+            v = warp_sum<double>(v);
+            if (lane == 0) PART[(((long long)b * N + jq[q]) * W + q) * dout + k] += v;
+        }
+    }
+}
+
 __global__ void k_ab_final(Geom g, int B, int f_kind, const int8_t *__restrict__ spins, const double *__restrict__ Omega,
                            const double *__restrict__ PART, const void *__restrict__ tlink, int tsize,
                            double *__restrict__ out) {
@@ -631,6 +852,23 @@ static cudaError_t launch_ab_layer(const AbArgs<T> &a, int l, T *S, const T *DX,
     return cudaGetLastError();
 }
 
+static cudaError_t launch_ab_layer_tma(const AbArgs<float> &a, int l, float *S, const float *DX, double *PART,
+                                       cudaStream_t st) {
+    const Geom &g = a.g;
+    const int d = 32, W = g.W;
+    const size_t per_warp = 2 * (size_t)d * d + (size_t)W * W * d + 2 * (size_t)W * d;
+    const size_t floats = 2 * (size_t)d * d + (size_t)(4 * g.w + 1) * d + kTmaWarps * per_warp;
+    const size_t smem = floats * sizeof(float) + 2 * kTmaWarps * sizeof(uint64_t);
+    cudaError_t err = cudaFuncSetAttribute(k_ab_layer_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((g.N + kTmaWarps - 1) / kTmaWarps, a.B);
+    {
+        ProfScope _ps("k_ab_layer", st);
+        k_ab_layer_tma<<<grid, 32 * kTmaWarps, smem, st>>>(a, l, S, DX, PART);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
                                   void *scratch, double *out, cudaStream_t st) {
@@ -656,7 +894,10 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int hd = (g.d + 31) / 32;
     for (int l = 1; l <= g.L; ++l) {
-        if (hd == 1) err = launch_ab_layer<T, 1>(a, l, S, DX, PART, st);
+        if (sizeof(T) == 4 && g.d == 32) err = launch_ab_layer_tma(reinterpret_cast<const AbArgs<float> &>(a), l,
+                                                                  reinterpret_cast<float *>(S),
+                                                                  reinterpret_cast<const float *>(DX), PART, st);
+        else if (hd == 1) err = launch_ab_layer<T, 1>(a, l, S, DX, PART, st);
         else if (hd == 2) err = launch_ab_layer<T, 2>(a, l, S, DX, PART, st);
         else err = launch_ab_layer<T, 4>(a, l, S, DX, PART, st);
         if (err != cudaSuccess) return err;

@@ -206,6 +206,13 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
                         size_t scratch_elems, cudaStream_t st);
 size_t links_scratch_elems(const dn_model *m, int N, int B);
 
+// Toeplitz hop of the FP32 link build on the tcgen05 tensor cores (tc_gemm.cu):
+// Y[b][a] = T_a X[b][a] (X generated from gtaps/gDm when gtaps != nullptr), band
+// rows to band (may be null).  cudaErrorNotSupported when the shape does not fit.
+cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float *X, const float *gtaps,
+                            const float *gDm, long long dm_ss, float *Y, float *band, long long bss, long long brs,
+                            long long bos, int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st);
+
 // ABACUS (abacus.cu).
 template <typename T>
 cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,

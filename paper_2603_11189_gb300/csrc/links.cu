@@ -371,8 +371,29 @@ size_t links_scratch_elems(const dn_model *m, int N, int B) {
 }
 
 template <typename T>
+static cudaError_t launch_tgemm_ffma(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *Y,
+                                     T *band, const BandDst &bd, long long b0, int nb, cudaStream_t st);
+
+// FP32: tensor cores (three BF16 products); FP64: the FMA kernel.
+template <typename T>
 static cudaError_t launch_tgemm(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *Y, T *band,
-                                const BandDst &bd, long long b0, int nb, cudaStream_t st) {
+                                const BandDst &bd, long long b0, int nb, unsigned *flag, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        cudaError_t err = launch_tgemm_tc(g, reinterpret_cast<const float *>(taps), P,
+                                          reinterpret_cast<const float *>(X),
+                                          gs ? reinterpret_cast<const float *>(gs->taps) : nullptr,
+                                          gs ? reinterpret_cast<const float *>(gs->Dm) : nullptr, gs ? gs->dm_ss : 0,
+                                          reinterpret_cast<float *>(Y), reinterpret_cast<float *>(band), bd.ss, bd.rs,
+                                          bd.os, bd.R, bd.nsrc, b0, nb, flag, st);
+        if (err != cudaErrorNotSupported) return err;
+        cudaGetLastError();
+    }
+    return launch_tgemm_ffma<T>(g, taps, P, X, gs, Y, band, bd, b0, nb, st);
+}
+
+template <typename T>
+static cudaError_t launch_tgemm_ffma(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *Y,
+                                     T *band, const BandDst &bd, long long b0, int nb, cudaStream_t st) {
     const int gx_len = kTgOff + 2 * g.N + kTgTile;
     const size_t smem = (((size_t)gx_len + 3) & ~size_t(3)) * sizeof(T) + (size_t)kTgK * kTgTile * sizeof(T);
     cudaError_t err;
@@ -488,7 +509,8 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
             T *dst = ell + (long long)(n - 2) * N * nRl * d;
             const T *taps_n = pl.taps + (long long)(n - 1) * g.R * d;
             if (n < L) {
-                if ((err = launch_tgemm<T>(g, taps_n, N, F, nullptr, U, dst, bd, b0, nb, st)) != cudaSuccess) return err;
+                if ((err = launch_tgemm<T>(g, taps_n, N, F, nullptr, U, dst, bd, b0, nb, c->flag, st)) != cudaSuccess)
+                    return err;
                 if ((err = launch_dhop<T>(g, N, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st)) != cudaSuccess)
                     return err;
             } else {
@@ -505,7 +527,7 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
                 const bool first = n == msrc + 2;
                 if (n < L) {
                     err = launch_tgemm<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, U, dst, bd,
-                                          b0, nb, st);
+                                          b0, nb, c->flag, st);
                     if (err != cudaSuccess) return err;
                     if ((err = launch_dhop<T>(g, (int)Pm, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st)) !=
                         cudaSuccess)

@@ -1,0 +1,67 @@
+"""Full-size parity: the N=128, 4 x 32 x 32 FP32 workload at the bench's size
+(4096 configurations, all 128 single flips each, through the same calls the
+bench times), with sampled outputs checked one by one against the FP64 oracle,
+and properties that hold at any size checked on all outputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dn():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_11189_gb300 import dysonnet
+    return dysonnet
+
+
+def test_bench_workload_sampled_against_oracle(dn):
+    cfg = synth.CONFIGS["c2"]
+    desc, params = cfg["desc"], synth.make_params(cfg)
+    B, N = cfg["B"], cfg["N"]
+    spins_np = synth.make_spins(cfg)
+    spins = torch.from_numpy(spins_np).cuda()
+    model = dn.Model(desc, params)
+    eloc = model.local_energy(cfg["ham"], spins, prec="fp32").cpu().numpy()
+    assert np.all(np.isfinite(eloc))
+    rng = np.random.default_rng(5)
+    # Local energies of 6 sampled configurations (each: 129 full forward passes in the oracle).
+    bs = np.sort(rng.choice(B, 6, replace=False))
+    ref = oracle.eloc(desc, params, cfg["ham"], spins_np[bs])
+    assert np.max(np.abs(eloc[bs] - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-4
+    # All single-flip ratios of a 512-configuration slice, 96 sampled flips against the oracle.
+    lo = int(rng.integers(0, B - 512))
+    cache = model.forward_cache(spins[lo:lo + 512].contiguous(), prec="fp32")
+    r = cache.single_flip_ratios().cpu().numpy()
+    assert cache.check() == dn.DN_OK
+    cache.destroy()
+    assert np.all(np.isfinite(r))
+    pick = rng.choice(512 * N, 96, replace=False)
+    sample = (pick // N).astype(np.int32)
+    sites = np.stack([pick % N, -np.ones_like(pick)], axis=1).astype(np.int32)
+    ref = oracle.dlogpsi(desc, params, spins_np[lo:lo + 512], sample, sites)
+    lp, _ = oracle.logpsi(desc, params, spins_np[lo + np.unique(sample)][:1])
+    den = np.maximum(np.abs(ref), 1e-3 * (1.0 + np.abs(lp[0])))
+    assert np.max(np.abs(r.reshape(-1)[pick] - ref) / den) <= 1e-4
+    model.close()
+
+
+def test_bench_workload_flip_list_matches_grouped(dn):
+    """The general flip-list kernel and the all-single-flips kernel agree on 64
+    configurations of the workload (same caches, different kernels)."""
+    cfg = synth.CONFIGS["c2"]
+    desc, params = cfg["desc"], synth.make_params(cfg)
+    spins_np = synth.make_spins(cfg, B=64)
+    model = dn.Model(desc, params)
+    cache = model.forward_cache(torch.from_numpy(spins_np).cuda(), prec="fp32")
+    grouped = cache.single_flip_ratios().cpu().numpy().reshape(-1)
+    sample, sites = synth.single_flips(64, cfg["N"])
+    listed = cache.flip_ratios(torch.from_numpy(sample).cuda(), torch.from_numpy(sites).cuda()).cpu().numpy()
+    cache.destroy()
+    model.close()
+    assert np.max(np.abs(grouped - listed) / np.maximum(1e-3, np.abs(listed))) <= 2e-5
