@@ -198,6 +198,7 @@ def main():
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
+    # Replicas: every rank runs the whole workload on its own GPU (no data-path collective).
     if world > 1:
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2603_11189_gb300 import build as B_
@@ -207,6 +208,7 @@ def main():
     if world > 1:
         tdist.barrier()
     from paper_2603_11189_gb300 import dysonnet as dn
+    from paper_2603_11189_gb300 import replicas
     import synth
 
     cfg = synth.CONFIGS["c2"]
@@ -247,12 +249,8 @@ def main():
     lib.dn_profile_enable(0)
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    ms_max = float(t.item())
     flips_step = Bs * N
-    value = world * flips_step / (ms_max / 1e3)
+    value, ms_max = replicas.throughput(flips_step, ms, device="cuda")
 
     prof = read_profile(lib)
     assert np.all(np.isfinite(eloc.cpu().numpy())), "non-finite local energies"
@@ -275,10 +273,7 @@ def main():
     ev1.record()
     barrier()
     e2e_ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    e2e_value = world * flips_step / (float(t.item()) / 1e3)
+    e2e_value, _ = replicas.throughput(flips_step, e2e_ms, device="cuda")
 
     # ABACUS kernel alone and the GPU full-forward recompute of every flipped configuration.
     ab_ms = sum(v[1] for k, v in prof.items() if "/abacus/" in "/" + k) / args.steps
@@ -323,7 +318,7 @@ def main():
         "cache_build_ms_per_step": build_ms,
         "recompute": recompute,
         "kernels": [{"name": k, "launches": n // args.steps, "ms_per_step": v / args.steps,
-                     "share": v / total_k} for k, n, v in kernels[:8]],
+                     "share": v / total_k} for k, n, v in kernels[:16]],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, params, spins_np, args.cpu_samples)
@@ -382,6 +377,22 @@ def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
                               "frac": ach / peak, "traffic": None, "launches": launches,
                               "ms_per_launch": tot_s * 1e3 / launches,
                               "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"}
+    tc = [(k, v) for k, v in prof.items() if k.endswith("links/k_tgemm_tc")]
+    if tc:
+        launches = sum(v[0] for _, v in tc)
+        tot_s = sum(v[1] for _, v in tc) / 1e3
+        flops = link_conv_flops(N, desc.L, desc.d, Bs) * steps
+        ach = flops / tot_s / 1e12
+        # Each FP32 product is carried by three BF16 tensor-core products
+        # (hi*hi + hi*lo + lo*hi), so the FP32-equivalent peak is a third of the
+        # BF16 dense rate; the kernel runs inside a long step, hence the
+        # sustained figure.
+        bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        peak = bf16 / 3.0
+        out["links_tgemm_tc"] = {"kernel": "k_tgemm_tc", "bound": "tensor", "achieved": ach, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches": launches,
+                                 "ms_per_launch": tot_s * 1e3 / launches,
+                                 "peak_source": f"{src} bf16_tflops_sustained / 3 (3-product BF16 split of FP32)"}
     return out
 
 
@@ -395,6 +406,8 @@ def roofline(prof, steps, desc, N, Bs, peaks, src, clocks):
         return fam["abacus"], fam
     if name.endswith("links/k_tgemm") and "links_tgemm" in fam:
         return fam["links_tgemm"], fam
+    if name.endswith("links/k_tgemm_tc") and "links_tgemm_tc" in fam:
+        return fam["links_tgemm_tc"], fam
     return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
             "traffic": None, "ms_per_launch": tot_ms / launches}, fam
 

@@ -759,25 +759,50 @@ __global__ void __launch_bounds__(256) k_ab_layer_tma(AbArgs<float> a, int l, fl
         if (q < W) pq[q * d + c] = acc[q];
     __syncwarp();
     const float yc = a.y[((b * L + lo) * N + i) * d + c];
+    // z[q] = y + V p[q] for all slots at once: one V element per lane serves every slot,
+    // and each slot vector is read as 16-byte broadcasts.
+    float z[kLayMaxW];
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) z[q] = yc;
+#pragma unroll 2
+    for (int c2 = 0; c2 < d; c2 += 4) {
+        const float v0 = VTs[(c2 + 0) * d + c], v1 = VTs[(c2 + 1) * d + c], v2 = VTs[(c2 + 2) * d + c],
+                    v3 = VTs[(c2 + 3) * d + c];
+#pragma unroll
+        for (int q = 0; q < kLayMaxW; ++q) {
+            if (q >= W) break;
+            const float4 pv = *reinterpret_cast<const float4 *>(pq + q * d + c2);
+            z[q] += v0 * pv.x + v1 * pv.y + v2 * pv.z + v3 * pv.w;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < kLayMaxW; ++q) {
         if (q >= W) break;
         const bool ok = (valid >> q) & 1u;
-        float z = yc;
-#pragma unroll 8
-        for (int c2 = 0; c2 < d; ++c2) z += VTs[c2 * d + c] * pq[q * d + c2];
         const float dx = ok ? DX[(lo * rows + ((long long)b * N + jq[q]) * W + q) * d + c] : 0.f;
-        gq[q * d + c] = dx * z;
+        gq[q * d + c] = dx * z[q];
     }
     __syncwarp();
+    float sv[kLayMaxW];
+#pragma unroll
+    for (int q = 0; q < kLayMaxW; ++q) sv[q] = 0.f;
+#pragma unroll 2
+    for (int c2 = 0; c2 < d; c2 += 4) {
+        const float u0 = UTs[(c2 + 0) * d + c], u1 = UTs[(c2 + 1) * d + c], u2 = UTs[(c2 + 2) * d + c],
+                    u3 = UTs[(c2 + 3) * d + c];
+#pragma unroll
+        for (int q = 0; q < kLayMaxW; ++q) {
+            if (q >= W) break;
+            const float4 gv = *reinterpret_cast<const float4 *>(gq + q * d + c2);
+            sv[q] += u0 * gv.x + u1 * gv.y + u2 * gv.z + u3 * gv.w;
+        }
+    }
     const float *rho = a.rho + ((b * L + lo) * dout) * (long long)N * d + (long long)i * d;
 #pragma unroll
     for (int q = 0; q < kLayMaxW; ++q) {
         if (q >= W) break;
         if (!((valid >> q) & 1u)) continue;
-        float s = 0.f;
-#pragma unroll 8
-        for (int c2 = 0; c2 < d; ++c2) s += UTs[c2 * d + c] * gq[q * d + c2];
+        const float s = sv[q];
         if (l < L) S[(lo * rows + ((long long)b * N + jq[q]) * W + q) * d + c] = s;
         for (int k = 0; k < dout; ++k) {
             double v = (double)rho[(long long)k * N * d + c] * (double)s;

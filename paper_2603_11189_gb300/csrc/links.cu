@@ -226,13 +226,13 @@ __global__ void __launch_bounds__(256) k_dhop(Geom g, int P, int cols, const T *
                                               const T *__restrict__ Yin, T *__restrict__ Xo) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d;
-    T *DsT = reinterpret_cast<T *>(smraw);      // [a][c] = D[c][a], rows padded to d+1
+    T *DsT = reinterpret_cast<T *>(smraw);      // [a][c] = D[c][a] (rows padded to d+1 off the fast path)
     T *Ys = DsT + ((d * (d + 1) + 3) / 4 * 4);  // [a][cols], 16-byte aligned
     const int p0 = blockIdx.x * cols;
     const int i = blockIdx.y;
     const long long bl = blockIdx.z;
     const T *D = Dm + bl * dm_ss + (long long)i * d * d;
-    const int dp = d + 1;                       // padded rows: conflict-free transpose
+    const int dp = FAST ? d : d + 1;            // fast path reads 8 consecutive rows as two 16-byte vectors
     for (int q = threadIdx.x; q < d * d; q += blockDim.x) {
         const int c = q / d, a = q % d;
         DsT[a * dp + c] = D[q];
@@ -263,12 +263,22 @@ __global__ void __launch_bounds__(256) k_dhop(Geom g, int P, int cols, const T *
         for (int r = 0; r < 8; ++r)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[r][j] = 0;
+#pragma unroll 4
         for (int a = 0; a < d; ++a) {
             T dv[8], yv[4];
+            if constexpr (sizeof(T) == 4) {
+                const float4 d0 = *reinterpret_cast<const float4 *>(DsT + a * dp + ty * 8);
+                const float4 d1 = *reinterpret_cast<const float4 *>(DsT + a * dp + ty * 8 + 4);
+                const float4 y0 = *reinterpret_cast<const float4 *>(Ys + a * cols + tx * 4);
+                dv[0] = d0.x; dv[1] = d0.y; dv[2] = d0.z; dv[3] = d0.w;
+                dv[4] = d1.x; dv[5] = d1.y; dv[6] = d1.z; dv[7] = d1.w;
+                yv[0] = y0.x; yv[1] = y0.y; yv[2] = y0.z; yv[3] = y0.w;
+            } else {
 #pragma unroll
-            for (int r = 0; r < 8; ++r) dv[r] = DsT[a * dp + ty * 8 + r];
+                for (int r = 0; r < 8; ++r) dv[r] = DsT[a * dp + ty * 8 + r];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) yv[j] = Ys[a * cols + tx * 4 + j];
+                for (int j = 0; j < 4; ++j) yv[j] = Ys[a * cols + tx * 4 + j];
+            }
 #pragma unroll
             for (int r = 0; r < 8; ++r)
 #pragma unroll
@@ -335,6 +345,7 @@ __global__ void __launch_bounds__(256) k_bandconv(Geom g, const T *__restrict__ 
         acc[q] = 0;
         win[q] = (q <= 2 * R) ? G(k - R + q) : (T)0;
     }
+#pragma unroll 4
     for (int n = 0; n < N; ++n) {
         const T xv = GEN ? gen_x<T>(gs, N, d, g.periodic, bl, a, n, p) : Xa[(long long)n * P];
 #pragma unroll

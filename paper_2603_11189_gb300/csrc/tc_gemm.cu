@@ -21,8 +21,8 @@ namespace dn {
 
 namespace {
 
-constexpr int kTcM = 128, kTcN = 256, kTcK = 64;     // K staged 64 sites (4 MMA slabs) at a time
-constexpr int kSlabA = kTcM * 16 * 2, kSlabB = kTcN * 16 * 2;   // bytes per 16-wide K slab
+constexpr int kTcM = 128, kTcK = 64;     // K staged 64 sites (4 MMA slabs) at a time
+constexpr int kSlabA = kTcM * 16 * 2;    // bytes per 16-wide K slab of A (B: TN * 32)
 constexpr long kTcSpin = 1L << 24;
 
 __device__ __forceinline__ uint32_t sm_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -79,20 +79,25 @@ __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity) {
 
 }  // namespace
 
-template <bool GEN>
+template <bool GEN, int TN>
 __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restrict__ taps, int P,
                                                   const float *__restrict__ X, const float *__restrict__ gtaps,
                                                   const float *__restrict__ gDm, long long dm_ss, float *__restrict__ Y,
                                                   float *__restrict__ band, long long bss, long long brs, long long bos,
                                                   int bR, int bns, long long b0, unsigned *__restrict__ flag) {
     extern __shared__ __align__(1024) unsigned char smtc[];
+    constexpr int kTcN = TN, kSlabB = TN * 16 * 2, kTpc = 256 / TN;   // threads per B column
     const int N = g.N, d = g.d;
     unsigned char *Ahi = smtc;                            // 4 slabs x kSlabA
     unsigned char *Alo = Ahi + 4 * kSlabA;
     unsigned char *Bhi = Alo + 4 * kSlabA;                // 4 slabs x kSlabB
     unsigned char *Blo = Bhi + 4 * kSlabB;
     float *gx = reinterpret_cast<float *>(Blo + 4 * kSlabB);   // taps of channel a: gx[r + N - 1]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(gx + ((2 * N + 1) & ~1));
+    float *Dms = gx + ((2 * N + 1) & ~1);                       // [32][d]   (generated operand only)
+    float *Tps = Dms + (GEN ? 32 * d : 0);                      // [32 + nk - 1][d]
+    const int nk = (kTcN + d - 1) / d + 1;                      // source sites a column tile touches
+    const bool gstage = GEN && (kTcN % d == 0) && d <= 64;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Tps + (GEN ? ((32 + nk - 1) * d + 1) / 2 * 2 : 0));
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int p0 = blockIdx.x * kTcN, i0 = blockIdx.y * kTcM;
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tslot)), "r"(256));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tslot)), "r"(TN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -113,15 +118,16 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
-    // This thread stages column p0 + pp of B (fixed) for every site of a chunk.
-    const int pp = tid;
+    // This thread stages column p0 + pp of B for its share (1 / kTpc) of the sites of a chunk.
+    const int pp = tid % TN, part = tid / TN;
     const int pcol = p0 + pp;
     const bool pok = pcol < P;
     int kq = 0, cq = 0;
-    if (GEN && pok) {
+    if (GEN) {
         kq = pcol / d;
         cq = pcol - kq * d;
     }
+    const int kfirst = p0 / d;                  // first source site of the tile
     const float *xcol = (!GEN) ? X + (bl * d + a) * (long long)N * P + pcol : nullptr;
     const float *dmcol = GEN ? gDm + bl * dm_ss + (long long)a * d + cq : nullptr;
     const long long dd = (long long)d * d;
@@ -146,21 +152,53 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
             }
             split_store8(Ahi, Alo, (uint32_t)(kc >> 1) * kSlabA + canon(r, (kc & 1) * 8), v);
         }
-        // B: this thread's column pcol, all 64 sites in 8 tasks of 8 (loads of a task in flight together).
-#pragma unroll 2
-        for (int kc = 0; kc < kTcK / 8; ++kc) {
-            float v[8];
+        if (GEN && gstage) {
+            // Generated operand: the vertex rows D0_n[a][:] and the tap rows g_{n-k} the tile needs
+            // are staged in shared memory (coalesced), 32 sites at a time.
+            for (int h = 0; h < kTcK; h += 32) {
+                __syncthreads();
+                for (int q = tid; q < 32 * d; q += blockDim.x) {
+                    const int nn = q / d, cc = q % d, n = n0 + h + nn;
+                    Dms[q] = n < N ? gDm[bl * dm_ss + ((long long)n * d + a) * d + cc] : 0.f;
+                }
+                const int rmin = n0 + h - (kfirst + nk - 1), nrow = 32 + nk - 1;
+                for (int q = tid; q < nrow * d; q += blockDim.x) {
+                    const int rr = q / d, cc = q % d, r = rmin + rr;
+                    Tps[q] = (r > -N && r < N) ? gtaps[(long long)tap_row_tc(r, N, g.periodic) * d + cc] : 0.f;
+                }
+                __syncthreads();
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int n = n0 + kc * 8 + u;
+                for (int kx = 0; kx < 4 / kTpc; ++kx) {
+                    const int kc = part * (4 / kTpc) + kx;
+                    float v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int nn = kc * 8 + u, n = n0 + h + nn;
+                        v[u] = (pok && n < N) ? Dms[nn * d + cq] * Tps[(n - kq - rmin) * d + cq] : 0.f;
+                    }
+                    const int kk = h + kc * 8;
+                    split_store8(Bhi, Blo, (uint32_t)(kk >> 4) * kSlabB + canon(pp, kk & 15), v);
+                }
+            }
+        } else {
+            // Column pcol of B for this thread's share of the 64 sites: every load issued before any is used.
+            constexpr int KS = kTcK / kTpc;
+            float v[KS];
+#pragma unroll
+            for (int kk = 0; kk < KS; ++kk) {
+                const int n = n0 + part * KS + kk;
                 float x = 0.f;
                 if (pok && n < N) {
                     if (GEN) x = dmcol[(long long)n * dd] * gtaps[(long long)tap_row_tc(n - kq, N, g.periodic) * d + cq];
                     else x = xcol[(long long)n * P];
                 }
-                v[u] = x;
+                v[kk] = x;
             }
-            split_store8(Bhi, Blo, (uint32_t)(kc >> 1) * kSlabB + canon(pp, (kc & 1) * 8), v);
+#pragma unroll
+            for (int kc = 0; kc < KS / 8; ++kc) {
+                const int kk = part * KS + kc * 8;
+                split_store8(Bhi, Blo, (uint32_t)(kk >> 4) * kSlabB + canon(pp, kk & 15), v + 8 * kc);
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -227,34 +265,46 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
 }
 
-size_t tgemm_tc_smem(int N) {
-    return (size_t)8 * kSlabA + 8 * kSlabB + (size_t)((2 * N + 1) & ~1) * sizeof(float) + 16;
+template <int TN>
+static size_t tgemm_tc_smem(int N, int d, bool gen) {
+    const int nk = (TN + d - 1) / d + 1;
+    const size_t stage = gen ? (size_t)32 * d + ((size_t)(32 + nk - 1) * d + 1) / 2 * 2 : 0;
+    return (size_t)8 * kSlabA + (size_t)8 * TN * 32 + ((size_t)((2 * N + 1) & ~1) + stage) * sizeof(float) + 16;
 }
 
+template <int TN>
+static cudaError_t launch_tgemm_tc_tn(const Geom &g, const float *taps, int P, const float *X, const float *gtaps,
+                                      const float *gDm, long long dm_ss, float *Y, float *band, long long bss,
+                                      long long brs, long long bos, int bR, int bns, long long b0, int nb,
+                                      unsigned *flag, cudaStream_t st) {
+    const size_t smem = tgemm_tc_smem<TN>(g.N, g.d, gtaps != nullptr);
+    if (smem > 220 * 1024) return cudaErrorNotSupported;
+    dim3 grid((P + TN - 1) / TN, (g.N + kTcM - 1) / kTcM, (unsigned)nb * g.d);
+    cudaError_t err;
+    if (gtaps) {
+        err = cudaFuncSetAttribute(k_tgemm_tc<true, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        ProfScope _ps("k_tgemm_tc", st);
+        k_tgemm_tc<true, TN><<<grid, 256, smem, st>>>(g, taps, P, nullptr, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR,
+                                                      bns, b0, flag);
+    } else {
+        err = cudaFuncSetAttribute(k_tgemm_tc<false, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        ProfScope _ps("k_tgemm_tc", st);
+        k_tgemm_tc<false, TN><<<grid, 256, smem, st>>>(g, taps, P, X, nullptr, nullptr, 0, Y, band, bss, brs, bos, bR,
+                                                       bns, b0, flag);
+    }
+    return cudaGetLastError();
+}
+
+// 128-column tiles (3 CTAs per SM: 64 KB of operands, 128 TMEM columns each).
 cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float *X, const float *gtaps,
                             const float *gDm, long long dm_ss, float *Y, float *band, long long bss, long long brs,
                             long long bos, int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st) {
-    const size_t smem = tgemm_tc_smem(g.N);
-    if (smem > 220 * 1024) return cudaErrorNotSupported;
-    dim3 grid((P + kTcN - 1) / kTcN, (g.N + kTcM - 1) / kTcM, (unsigned)nb * g.d);
-    cudaError_t err;
-    if (gtaps) {
-        err = cudaFuncSetAttribute(k_tgemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        ProfScope _ps("k_tgemm_tc", st);
-        k_tgemm_tc<true><<<grid, 256, smem, st>>>(g, taps, P, nullptr, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns,
-                                                  b0, flag);
-    } else {
-        err = cudaFuncSetAttribute(k_tgemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        ProfScope _ps("k_tgemm_tc", st);
-        k_tgemm_tc<false><<<grid, 256, smem, st>>>(g, taps, P, X, nullptr, nullptr, 0, Y, band, bss, brs, bos, bR, bns,
-                                                   b0, flag);
-    }
-    return cudaGetLastError();
+    return launch_tgemm_tc_tn<128>(g, taps, P, X, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
 }
 
 }  // namespace dn
