@@ -566,13 +566,6 @@ __global__ void __launch_bounds__(256) k_ab_layer(AbArgs<T> a, int l, T *__restr
     }
 }
 
-// Fast path of k_ab_layer for FP32 with d = 32: the link blocks of the warp's
-// site are streamed into a double-buffered shared-memory slot by the bulk-copy
-// engine (cp.async.bulk, completion on an mbarrier; every wait is bounded and a
-// timeout raises bit 4 of the cache flag).  Lane c reads 16-byte chunks of row
-// c of a block in the order (s + c) mod 8, so that the 8 lanes of a shared-memory
-// phase hit 8 different bank groups; the slice states are read in the same order.
-constexpr int kTmaWarps = 8;
 constexpr long kSpinLimit = 1L << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -597,218 +590,356 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
                  : "memory");
 }
 
-__global__ void __launch_bounds__(256) k_ab_layer_tma(AbArgs<float> a, int l, float *__restrict__ S,
-                                                      const float *__restrict__ DX, double *__restrict__ PART) {
+// Streaming fast path of k_ab_layer for FP32 with d = 32.  Warp w of a CTA owns a
+// run of R consecutive sites of one sample and walks them in order; for every
+// site it needs
+//  * the link blocks K^(l,m)_{i, i+dl} (m = 1..l-2, |dl| <= 2w), 4 KB each, which
+//    lie back to back in memory along the run; they are streamed through a ring
+//    of NS shared-memory slots by the bulk-copy engine, and the ring is kept full
+//    across site boundaries, so the copies of the next site are in flight while
+//    the current site's slice terms, matvecs and outputs are computed;
+//  * the states s^(m) (m = 1..l-1) of the W flips whose slice holds the site.
+//    Consecutive sites share W-1 of these flips, so they live in a window of
+//    W+1 flip slots per m (slot = flip mod (W+1)): moving one site on loads one
+//    new flip (W d contiguous values per m, one bulk copy), issued a site early
+//    into the slot that the previous site has released;
+//  * y, dchi, rho and the embedding links of the site, loaded into registers one
+//    site ahead.
+// Lane c owns output channel c.  A block row c is read in 16-byte chunks in the
+// order (s + c) mod 8, so the 8 lanes of a shared-memory phase hit 8 different
+// bank groups; slice states are broadcast reads.  Every wait is bounded; a
+// timeout raises bit 4 of the cache flag, lets the copies in flight land and
+// ends the warp.
+constexpr int kStWarps = 8;
+constexpr int kStMaxNS = 4;
+constexpr int kStMaxDout = 2;
+
+__device__ __forceinline__ void mbar_expect(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
+}
+
+// Bulk copy whose completion counts against a byte total announced by mbar_expect.
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ int floor_mod(int x, int m) {
+    const int r = x % m;
+    return r < 0 ? r + m : r;
+}
+
+// Sums NV <= 16 values over the warp; lane t with even t ends up holding the total
+// of value (t >> 1) & 15 (recursive halving: 16 + 15 shuffles instead of 5 NV).
+__device__ __forceinline__ double warp_sum16(double (&v)[16], int lane) {
+#pragma unroll
+    for (int h = 8, off = 16; h >= 1; h >>= 1, off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int u = 0; u < h; ++u) {
+            const double send = up ? v[u] : v[u + h];
+            const double keep = up ? v[u + h] : v[u];
+            v[u] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+template <int WW>
+__global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a, int l, int R, int NS,
+                                                                float *__restrict__ S, const float *__restrict__ DX,
+                                                                double *__restrict__ PART) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    constexpr int d = 32;
+    constexpr int d = 32, dd = d * d;
     const Geom &g = a.g;
-    const int N = g.N, L = g.L, wd = g.w, W = g.W, dout = g.dout;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int dd = d * d;
-    float *VTs = reinterpret_cast<float *>(smraw);                 // [d][d]
-    float *UTs = VTs + dd;                                         // [d][d]
-    float *Gs = UTs + dd;                                          // [4w+1][d] taps g^(l)_{-2w..2w}
-    const int per_warp = 2 * dd + W * W * d + 2 * W * d;
-    float *wb = Gs + (4 * wd + 1) * d + (size_t)warp * per_warp;
-    float *Kbuf = wb;                                              // [2][d][d]
-    float *Ss = Kbuf + 2 * dd;                                     // [W][W][d]
-    float *pq = Ss + W * W * d;                                    // [W][d]
-    float *gq = pq + W * d;                                        // [W][d]
-    uint64_t *mbars = reinterpret_cast<uint64_t *>(smraw + ((size_t)(2 * dd + (4 * wd + 1) * d + kTmaWarps * per_warp) *
-                                                                sizeof(float)));
-    uint64_t *mb = mbars + 2 * warp;
+    constexpr int W = WW, wd = (WW - 1) / 2, W1 = W + 1;
+    const int N = g.N, L = g.L, dout = g.dout;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c = lane;
+    const int nwin = l - 1, nlink = l > 2 ? l - 2 : 0, nper = 4 * wd + 1;
+    float *VTs = reinterpret_cast<float *>(smraw);                  // [d][d]
+    float *UTs = VTs + dd;                                          // [d][d]
+    float *Gs = UTs + dd;                                           // [4w+1][d] taps g^(l)_{-2w..2w}
+    float *Zs = Gs + nper * d;                                      // [d] zeros
+    const int per_warp = NS * dd + nwin * W1 * W * d + 2 * W * d;
+    float *wb = Zs + d + (size_t)warp * per_warp;
+    float *Kring = wb;                                              // [NS][d][d]
+    float *Win = Kring + NS * dd;                                   // [nwin][W+1][W][d]
+    float *pq = Win + nwin * W1 * W * d;                            // [W][d]
+    float *gq = pq + W * d;                                         // [W][d]
+    uint64_t *mb = reinterpret_cast<uint64_t *>(Zs + d + (size_t)kStWarps * per_warp) +
+                   (size_t)warp * (kStMaxNS + 2);                   // NS ring barriers, 2 window barriers
+    int8_t *sps = reinterpret_cast<int8_t *>(reinterpret_cast<uint64_t *>(Zs + d + (size_t)kStWarps * per_warp) +
+                                             (size_t)kStWarps * (kStMaxNS + 2));
     const long long lo = l - 1;
+    const long long b = blockIdx.y;
     for (int q = threadIdx.x; q < dd; q += blockDim.x) {
         VTs[q] = a.w.VT[lo * dd + q];
         UTs[q] = a.w.UT[lo * dd + q];
     }
-    for (int q = threadIdx.x; q < (4 * wd + 1) * d; q += blockDim.x) {
-        const int r = q / d - 2 * wd, c = q % d;
+    for (int q = threadIdx.x; q < nper * d; q += blockDim.x) {
+        const int r = q / d - 2 * wd, cc = q % d;
         const int row = g.periodic ? ((r % N) + N) % N : (r > -N && r < N ? r + N - 1 : -1);
-        Gs[q] = row >= 0 ? a.taps[((long long)lo * g.R + row) * d + c] : 0.f;
+        Gs[q] = row >= 0 ? a.taps[(lo * g.R + row) * d + cc] : 0.f;
     }
+    for (int q = threadIdx.x; q < N; q += blockDim.x) sps[q] = a.spins[b * N + q];
+    for (int q = threadIdx.x; q < d; q += blockDim.x) Zs[q] = 0.f;
     if (lane == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb)), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb + 1)), "r"(1));
+        for (int s = 0; s < kStMaxNS + 2; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mb + s)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     __syncthreads();
-    const long long b = blockIdx.y;
-    const int i = blockIdx.x * kTmaWarps + warp;
-    if (i >= N) return;
-    const int8_t *sp = a.spins + b * N;
+    const int i0 = (blockIdx.x * kStWarps + warp) * R;
+    const int nsite = N - i0 < R ? N - i0 : R;
+    if (nsite <= 0) return;
+    uint64_t *wmb = mb + kStMaxNS;
     const long long rows = (long long)a.B * N * W;
     const long long nRk = 2 * a.Rk + 1, nRl = 2 * a.Rl + 1;
-    int jq[kLayMaxW];
-    float dsq[kLayMaxW];
-    unsigned valid = 0;
-#pragma unroll
-    for (int q = 0; q < kLayMaxW; ++q) {
-        int j = i + wd - q;
-        bool ok = q < W;
-        if (g.periodic) j = ((j % N) + N) % N;
-        else ok = ok && j >= 0 && j < N;
-        jq[q] = ok ? j : 0;
-        dsq[q] = ok ? (float)(-2 * sp[j]) : 0.f;
-        if (ok) valid |= 1u << q;
-    }
+    auto wrap = [&](int x) -> int { return g.periodic ? floor_mod(x, N) : x; };
     auto site_ok = [&](int k) -> bool { return g.periodic || (k >= 0 && k < N); };
-    // Stage s^(m) of the warp's flips: Ss[q][t2][:].
-    auto stage = [&](int m) {
-        const float *src = S + (long long)(m - 1) * rows * d;
-#pragma unroll 5
-        for (int x = lane; x < W * W * (d / 4); x += 32) {
-            const int q = x / (W * (d / 4)), t2 = (x / (d / 4)) % W, c4 = x % (d / 4);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if ((valid >> q) & 1u) v = *reinterpret_cast<const float4 *>(src + (((long long)b * N + jq[q]) * W + t2) * d + 4 * c4);
-            *reinterpret_cast<float4 *>(Ss + (q * W + t2) * d + 4 * c4) = v;
-        }
-        __syncwarp();
+    // Window copies: flip jj (unwrapped) of every m into slot jj mod (W+1).
+    // One arrival per phase carries the byte count of all the phase's copies.
+    auto issue_flip = [&](int jj, uint64_t *bar) {
+        if (!site_ok(jj)) return;
+        const int j = wrap(jj), slot = floor_mod(jj, W1);
+        for (int m = 1; m <= nwin; ++m)
+            bulk_copy(Win + ((m - 1) * W1 + slot) * W * d, S + ((m - 1) * rows + (b * N + j) * W) * d,
+                      (uint32_t)(W * d * sizeof(float)), bar);
     };
-    float acc[kLayMaxW];
-#pragma unroll
-    for (int q = 0; q < kLayMaxW; ++q) acc[q] = 0.f;
-    const int c = lane;
-    // Slice Toeplitz and embedding terms.
-    if (l == 1) {
-#pragma unroll
-        for (int q = 0; q < kLayMaxW; ++q)
-            if ((valid >> q) & 1u) acc[q] = Gs[(q - wd + 2 * wd) * d + c] * a.w.e[c] * dsq[q];
-    } else {
-        stage(l - 1);
-        const float *el = a.ell + ((b * (L - 1) + (l - 2)) * N + i) * nRl * d;
-#pragma unroll
-        for (int q = 0; q < kLayMaxW; ++q) {
-            if (!((valid >> q) & 1u)) continue;
-            const int j = jq[q];
-            float v = dsq[q] * el[(wd - q + a.Rl) * d + c];
-            for (int t2 = 0; t2 < W; ++t2)
-                if (site_ok(j - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * Ss[(q * W + t2) * d + c];
-            acc[q] = v;
-        }
-        __syncwarp();
+    auto flip_bytes = [&](int jj) -> uint32_t { return site_ok(jj) ? (uint32_t)(nwin * W * d * sizeof(float)) : 0u; };
+    // Link blocks: stream index n -> (site r, pair m, offset dl), all contiguous per (r, m).
+    const long long nblk = (long long)nsite * nlink * nper;
+    auto blk_src = [&](long long n) -> const float * {
+        const int r = (int)(n / (nlink * nper)), rem = (int)(n % (nlink * nper));
+        const int m = rem / nper + 1, dl = rem % nper - 2 * wd;
+        return a.K + (((b * a.P + pair_index(l, m)) * N + (i0 + r)) * nRk + (dl + a.Rk)) * (long long)dd;
+    };
+    long long issued = 0, consumed = 0;
+    uint32_t wpend[2] = {0u, 0u}, wuse[2] = {0u, 0u};
+    if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (; issued < nblk && issued < NS; ++issued)
+            bulk_load(Kring + (issued % NS) * dd, blk_src(issued), dd * sizeof(float), mb + issued % NS);
     }
-    // Interlayer links: stream the site's blocks (m, dl) in order through two buffers.
-    const int nper = 4 * wd + 1;
-    const int nblk = (l - 2) > 0 ? (l - 2) * nper : 0;
+    issued = nblk < NS ? nblk : NS;
+    if (nwin > 0) {
+        uint32_t bytes = 0;
+        for (int jj = i0 - wd; jj <= i0 + wd; ++jj) bytes += flip_bytes(jj);
+        if (lane == 0 && bytes) {
+            mbar_expect(wmb, bytes);
+            for (int jj = i0 - wd; jj <= i0 + wd; ++jj) issue_flip(jj, wmb);
+        }
+        wpend[0] = bytes ? 1u : 0u;
+    }
     bool timed_out = false;
-    // Copy number n goes to slot n & 1; a slot is refilled only after it has been consumed.
-    uint32_t issued_s[2] = {0u, 0u}, consumed_s[2] = {0u, 0u};
-    int issue_bi = 0, issue_cnt = 0;
-    auto blk_ok = [&](int bi) -> bool { return site_ok(i + (bi % nper) - 2 * wd); };
-    auto issue_next = [&]() {
-        while (issue_bi < nblk && !blk_ok(issue_bi)) ++issue_bi;
-        if (issue_bi >= nblk) return;
-        const int slot = issue_cnt & 1;
-        if (lane == 0) {
-            const int m = issue_bi / nper + 1, dl = issue_bi % nper - 2 * wd;
-            const float *src = a.K + (((b * a.P + pair_index(l, m)) * N + i) * nRk + (dl + a.Rk)) * (long long)dd;
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bulk_load(Kbuf + slot * dd, src, dd * sizeof(float), mb + slot);
+    // Per-site vectors of site r (cur) and r + 1 (nxt).
+    float y_c, dx_c[W], rh_c[kStMaxDout], el_c[W];
+    auto load_site = [&](int i, float &yv, float (&dx)[W], float (&rh)[kStMaxDout], float (&el)[W]) {
+        yv = a.y[((b * L + lo) * N + i) * d + c];
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            dx[q] = 0.f;
+            el[q] = 0.f;
+            if (q >= W) continue;
+            const int jj = i + wd - q;
+            if (!site_ok(jj)) continue;
+            dx[q] = DX[(lo * rows + (b * N + wrap(jj)) * W + q) * d + c];
+            if (l >= 2) el[q] = a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
         }
-        issued_s[slot]++;
-        ++issue_bi;
-        ++issue_cnt;
+#pragma unroll
+        for (int k = 0; k < kStMaxDout; ++k) rh[k] = k < dout ? a.rho[((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d + c] : 0.f;
     };
-    issue_next();
-    issue_next();
-    int cnt = 0, cur_m = 0;
-    for (int bi = 0; bi < nblk && !timed_out; ++bi) {
-        if (!blk_ok(bi)) continue;
-        const int slot = cnt & 1;
-        ++cnt;
-        const int m = bi / nper + 1, dl = bi % nper - 2 * wd;
-        if (m != cur_m) {
-            stage(m);
-            cur_m = m;
-        }
-        if (!mbar_wait(mb + slot, consumed_s[slot] & 1u)) {
-            timed_out = true;
-            break;
-        }
-        consumed_s[slot]++;
-        const float *Kb = Kbuf + slot * dd + c * d;
-        const int qlo = dl < 0 ? -dl : 0, qhi = dl > 0 ? 2 * wd - dl : 2 * wd;
+    load_site(i0, y_c, dx_c, rh_c, el_c);
+    for (int r = 0; r < nsite && !timed_out; ++r) {
+        const int i = i0 + r;
+        int jq[W], wsl[W];
+        float dsq[W];
+        unsigned valid = 0;
 #pragma unroll
-        for (int s = 0; s < d / 4; ++s) {
-            const int ch = (s + lane) & (d / 4 - 1);
-            const float4 kv = *reinterpret_cast<const float4 *>(Kb + 4 * ch);
-#pragma unroll
-            for (int q = 0; q < kLayMaxW; ++q) {
-                if (q < qlo || q > qhi || !((valid >> q) & 1u)) continue;
-                const float4 sv = *reinterpret_cast<const float4 *>(Ss + (q * W + (dl + q)) * d + 4 * ch);
-                acc[q] += kv.x * sv.x + kv.y * sv.y + kv.z * sv.z + kv.w * sv.w;
+        for (int q = 0; q < W; ++q) {
+            const int jj = i + wd - q;
+            const bool ok = q < W && site_ok(jj);
+            jq[q] = ok ? wrap(jj) : 0;
+            wsl[q] = floor_mod(jj, W1);
+            dsq[q] = ok ? (float)(-2 * sps[jq[q]]) : 0.f;
+            if (ok) valid |= 1u << q;
+        }
+        // This site's window copies, then the next site's new flip into the released slot.
+        if (nwin > 0) {
+            const int pb = r & 1;
+            if (wpend[pb]) {
+                if (!mbar_wait(wmb + pb, wuse[pb] & 1u)) {
+                    timed_out = true;
+                    break;
+                }
+                wuse[pb]++;
+                wpend[pb] = 0;
+            }
+            if (r + 1 < nsite) {
+                const int jn = i + 1 + wd;
+                const uint32_t bytes = flip_bytes(jn);
+                if (lane == 0 && bytes) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect(wmb + (pb ^ 1), bytes);
+                    issue_flip(jn, wmb + (pb ^ 1));
+                }
+                wpend[pb ^ 1] = bytes ? 1u : 0u;
             }
         }
+        float y_n = 0.f, dx_n[W], rh_n[kStMaxDout], el_n[W];
+        if (r + 1 < nsite) load_site(i + 1, y_n, dx_n, rh_n, el_n);
+        float acc[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc[q] = 0.f;
+        if (l == 1) {
+#pragma unroll
+            for (int q = 0; q < W; ++q)
+                if ((valid >> q) & 1u) acc[q] = Gs[(q - wd + 2 * wd) * d + c] * a.w.e[c] * dsq[q];
+        } else {
+            const float *wl = Win + (size_t)(l - 2) * W1 * W * d;
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                if (!((valid >> q) & 1u)) continue;
+                float v = dsq[q] * el_c[q];
+                const float *ws = wl + wsl[q] * W * d;
+                for (int t2 = 0; t2 < W; ++t2)
+                    if (site_ok(jq[q] - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * ws[t2 * d + c];
+                acc[q] = v;
+            }
+        }
+        // Link blocks of this site.  Slot q of block dl multiplies the state of flip q at
+        // slice position q + dl; where that position is off the slice or the flip does not
+        // exist, the slot reads the zero row instead, so the inner loop has no branches.
+        // Even and odd 16-byte chunks go to separate accumulators (two FMA chains per slot).
+        float acc2[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc2[q] = 0.f;
+        for (int mi = 0; mi < nlink && !timed_out; ++mi) {
+            const float *wm = Win + (size_t)mi * W1 * W * d;
+            for (int bi = 0; bi < nper; ++bi) {
+                const int slot = (int)(consumed % NS);
+                if (!mbar_wait(mb + slot, (uint32_t)((consumed / NS) & 1))) {
+                    timed_out = true;
+                    break;
+                }
+                ++consumed;
+                const int dl = bi - 2 * wd;
+                if (site_ok(i + dl)) {
+                    const float *Kb = Kring + slot * dd + c * d;
+                    const float *sp[W];
+#pragma unroll
+                    for (int q = 0; q < W; ++q) {
+                        const int t2 = q + dl;
+                        sp[q] = (t2 >= 0 && t2 < W && ((valid >> q) & 1u)) ? wm + (wsl[q] * W + t2) * d : Zs;
+                    }
+#pragma unroll
+                    for (int s2 = 0; s2 < d / 4; s2 += 2) {
+                        const int ch0 = (s2 + lane) & (d / 4 - 1), ch1 = (s2 + 1 + lane) & (d / 4 - 1);
+                        const float4 k0 = *reinterpret_cast<const float4 *>(Kb + 4 * ch0);
+                        const float4 k1 = *reinterpret_cast<const float4 *>(Kb + 4 * ch1);
+#pragma unroll
+                        for (int q = 0; q < W; ++q) {
+                            const float4 s0 = *reinterpret_cast<const float4 *>(sp[q] + 4 * ch0);
+                            const float4 s1 = *reinterpret_cast<const float4 *>(sp[q] + 4 * ch1);
+                            acc[q] = fmaf(k0.x, s0.x, acc[q]);
+                            acc2[q] = fmaf(k1.x, s1.x, acc2[q]);
+                            acc[q] = fmaf(k0.y, s0.y, acc[q]);
+                            acc2[q] = fmaf(k1.y, s1.y, acc2[q]);
+                            acc[q] = fmaf(k0.z, s0.z, acc[q]);
+                            acc2[q] = fmaf(k1.z, s1.z, acc2[q]);
+                            acc[q] = fmaf(k0.w, s0.w, acc[q]);
+                            acc2[q] = fmaf(k1.w, s1.w, acc2[q]);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (issued < nblk) {
+                    if (lane == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        bulk_load(Kring + (issued % NS) * dd, blk_src(issued), dd * sizeof(float), mb + issued % NS);
+                    }
+                    ++issued;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc[q] += acc2[q];
+        if (timed_out) break;
+        // s^(l) = U (dchi * (y + V p)) and its contribution to dOmega.
+#pragma unroll
+        for (int q = 0; q < W; ++q)
+            if (q < W) pq[q * d + c] = acc[q];
         __syncwarp();
-        issue_next();
+        float z[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) z[q] = y_c;
+#pragma unroll 2
+        for (int c2 = 0; c2 < d; c2 += 4) {
+            const float v0 = VTs[(c2 + 0) * d + c], v1 = VTs[(c2 + 1) * d + c], v2 = VTs[(c2 + 2) * d + c],
+                        v3 = VTs[(c2 + 3) * d + c];
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                if (q >= W) break;
+                const float4 pv = *reinterpret_cast<const float4 *>(pq + q * d + c2);
+                z[q] += v0 * pv.x + v1 * pv.y + v2 * pv.z + v3 * pv.w;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q)
+            if (q < W) gq[q * d + c] = dx_c[q] * z[q];
+        __syncwarp();
+        float sv[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) sv[q] = 0.f;
+#pragma unroll 2
+        for (int c2 = 0; c2 < d; c2 += 4) {
+            const float u0 = UTs[(c2 + 0) * d + c], u1 = UTs[(c2 + 1) * d + c], u2 = UTs[(c2 + 2) * d + c],
+                        u3 = UTs[(c2 + 3) * d + c];
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                if (q >= W) break;
+                const float4 gv = *reinterpret_cast<const float4 *>(gq + q * d + c2);
+                sv[q] += u0 * gv.x + u1 * gv.y + u2 * gv.z + u3 * gv.w;
+            }
+        }
+        double part[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) part[u] = 0.0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (q >= W || !((valid >> q) & 1u)) continue;
+            if (l < L) S[(lo * rows + (b * N + jq[q]) * W + q) * d + c] = sv[q];
+#pragma unroll
+            for (int k = 0; k < kStMaxDout; ++k)
+                if (q * kStMaxDout + k < 16) part[q * kStMaxDout + k] = (double)rh_c[k] * (double)sv[q];
+        }
+        const double tot = warp_sum16(part, lane);
+        const int idx = (lane >> 1) & 15, qi = idx / kStMaxDout, ki = idx % kStMaxDout;
+        if (!(lane & 1) && qi < W && ki < dout && ((valid >> qi) & 1u)) {
+            double *dst = PART + ((b * N + wrap(i + wd - qi)) * W + qi) * dout + ki;
+            *dst += tot;
+        }
+        __syncwarp();
+        y_c = y_n;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            dx_c[q] = dx_n[q];
+            el_c[q] = el_n[q];
+        }
+#pragma unroll
+        for (int k = 0; k < kStMaxDout; ++k) rh_c[k] = rh_n[k];
     }
     if (timed_out) {
-        // Let copies still in flight land before the shared memory is released.
         if (lane == 0) atomicOr(a.flag, 4u);
-        for (int sl = 0; sl < 2; ++sl)
-            while (consumed_s[sl] < issued_s[sl]) {
-                mbar_wait(mb + sl, consumed_s[sl] & 1u);
-                consumed_s[sl]++;
-            }
-        return;
-    }
-    // s^(l) = U (dchi * (y + V p)) and its contribution to dOmega.
-#pragma unroll
-    for (int q = 0; q < kLayMaxW; ++q)
-        if (q < W) pq[q * d + c] = acc[q];
-    __syncwarp();
-    const float yc = a.y[((b * L + lo) * N + i) * d + c];
-    // z[q] = y + V p[q] for all slots at once: one V element per lane serves every slot,
-    // and each slot vector is read as 16-byte broadcasts.
-    float z[kLayMaxW];
-#pragma unroll
-    for (int q = 0; q < kLayMaxW; ++q) z[q] = yc;
-#pragma unroll 2
-    for (int c2 = 0; c2 < d; c2 += 4) {
-        const float v0 = VTs[(c2 + 0) * d + c], v1 = VTs[(c2 + 1) * d + c], v2 = VTs[(c2 + 2) * d + c],
-                    v3 = VTs[(c2 + 3) * d + c];
-#pragma unroll
-        for (int q = 0; q < kLayMaxW; ++q) {
-            if (q >= W) break;
-            const float4 pv = *reinterpret_cast<const float4 *>(pq + q * d + c2);
-            z[q] += v0 * pv.x + v1 * pv.y + v2 * pv.z + v3 * pv.w;
+        // Let the copies in flight land before the shared memory is released.
+        while (consumed < issued) {
+            mbar_wait(mb + consumed % NS, (uint32_t)((consumed / NS) & 1));
+            ++consumed;
         }
-    }
-#pragma unroll
-    for (int q = 0; q < kLayMaxW; ++q) {
-        if (q >= W) break;
-        const bool ok = (valid >> q) & 1u;
-        const float dx = ok ? DX[(lo * rows + ((long long)b * N + jq[q]) * W + q) * d + c] : 0.f;
-        gq[q * d + c] = dx * z[q];
-    }
-    __syncwarp();
-    float sv[kLayMaxW];
-#pragma unroll
-    for (int q = 0; q < kLayMaxW; ++q) sv[q] = 0.f;
-#pragma unroll 2
-    for (int c2 = 0; c2 < d; c2 += 4) {
-        const float u0 = UTs[(c2 + 0) * d + c], u1 = UTs[(c2 + 1) * d + c], u2 = UTs[(c2 + 2) * d + c],
-                    u3 = UTs[(c2 + 3) * d + c];
-#pragma unroll
-        for (int q = 0; q < kLayMaxW; ++q) {
-            if (q >= W) break;
-            const float4 gv = *reinterpret_cast<const float4 *>(gq + q * d + c2);
-            sv[q] += u0 * gv.x + u1 * gv.y + u2 * gv.z + u3 * gv.w;
-        }
-    }
-    const float *rho = a.rho + ((b * L + lo) * dout) * (long long)N * d + (long long)i * d;
-#pragma unroll
-    for (int q = 0; q < kLayMaxW; ++q) {
-        if (q >= W) break;
-        if (!((valid >> q) & 1u)) continue;
-        const float s = sv[q];
-        if (l < L) S[(lo * rows + ((long long)b * N + jq[q]) * W + q) * d + c] = s;
-        for (int k = 0; k < dout; ++k) {
-            double v = (double)rho[(long long)k * N * d + c] * (double)s;
-            v = warp_sum<double>(v);
-            if (lane == 0) PART[(((long long)b * N + jq[q]) * W + q) * dout + k] += v;
-        }
+        for (int pb = 0; pb < 2; ++pb)
+            if (wpend[pb]) mbar_wait(wmb + pb, wuse[pb] & 1u);
     }
 }
 
@@ -877,19 +1008,45 @@ static cudaError_t launch_ab_layer(const AbArgs<T> &a, int l, T *S, const T *DX,
     return cudaGetLastError();
 }
 
-static cudaError_t launch_ab_layer_tma(const AbArgs<float> &a, int l, float *S, const float *DX, double *PART,
-                                       cudaStream_t st) {
+// Shared memory of k_ab_stream with NS ring slots; 0 if it does not fit.
+static size_t ab_stream_smem(const Geom &g, int l, int NS) {
+    const size_t d = 32, W = g.W, nwin = l - 1;
+    const size_t per_warp = NS * d * d + nwin * (W + 1) * W * d + 2 * W * d;
+    const size_t floats = 2 * d * d + (size_t)(4 * g.w + 2) * d + kStWarps * per_warp;
+    const size_t bytes = floats * sizeof(float) + (size_t)kStWarps * (kStMaxNS + 2) * sizeof(uint64_t) +
+                         (((size_t)g.N + 15) & ~(size_t)15);
+    return bytes <= 227 * 1024 ? bytes : 0;
+}
+
+static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, const float *DX, double *PART,
+                                    cudaStream_t st) {
     const Geom &g = a.g;
-    const int d = 32, W = g.W;
-    const size_t per_warp = 2 * (size_t)d * d + (size_t)W * W * d + 2 * (size_t)W * d;
-    const size_t floats = 2 * (size_t)d * d + (size_t)(4 * g.w + 1) * d + kTmaWarps * per_warp;
-    const size_t smem = floats * sizeof(float) + 2 * kTmaWarps * sizeof(uint64_t);
-    cudaError_t err = cudaFuncSetAttribute(k_ab_layer_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    dim3 grid((g.N + kTmaWarps - 1) / kTmaWarps, a.B);
-    {
+    int NS = 0;
+    size_t smem = ab_stream_smem(g, l, 0);
+    if (l > 2) {
+        for (NS = kStMaxNS; NS >= 2; --NS)
+            if ((smem = ab_stream_smem(g, l, NS)) != 0) break;
+        if (NS < 2) return cudaErrorNotSupported;
+    }
+    if (smem == 0) return cudaErrorNotSupported;
+    // Runs of 8 sites per warp: long enough to keep the copy ring full across sites.
+    const int R = 8;
+    dim3 grid((unsigned)((g.N + kStWarps * R - 1) / (kStWarps * R)), (unsigned)a.B);
+    cudaError_t err;
+    if (g.W == 5) {
+        if ((err = cudaFuncSetAttribute(k_ab_stream<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return err;
         ProfScope _ps("k_ab_layer", st);
-        k_ab_layer_tma<<<grid, 32 * kTmaWarps, smem, st>>>(a, l, S, DX, PART);
+        k_ab_stream<5><<<grid, 32 * kStWarps, smem, st>>>(a, l, R, NS, S, DX, PART);
+    } else if (g.W == 3) {
+        if ((err = cudaFuncSetAttribute(k_ab_stream<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return err;
+        ProfScope _ps("k_ab_layer", st);
+        k_ab_stream<3><<<grid, 32 * kStWarps, smem, st>>>(a, l, R, NS, S, DX, PART);
+    } else {
+        return cudaErrorNotSupported;
     }
     return cudaGetLastError();
 }
@@ -918,11 +1075,18 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int hd = (g.d + 31) / 32;
+    // The streaming kernel takes FP32 caches with d = 32, W in {3, 5} and d_out <= 2; a
+    // layer whose shared memory would not fit falls back to k_ab_layer.
+    const bool stream_ok = sizeof(T) == 4 && g.d == 32 && (g.W == 3 || g.W == 5) && g.dout <= kStMaxDout;
     for (int l = 1; l <= g.L; ++l) {
-        if (sizeof(T) == 4 && g.d == 32) err = launch_ab_layer_tma(reinterpret_cast<const AbArgs<float> &>(a), l,
-                                                                  reinterpret_cast<float *>(S),
-                                                                  reinterpret_cast<const float *>(DX), PART, st);
-        else if (hd == 1) err = launch_ab_layer<T, 1>(a, l, S, DX, PART, st);
+        err = cudaErrorNotSupported;
+        if (stream_ok)
+            err = launch_ab_stream(reinterpret_cast<const AbArgs<float> &>(a), l, reinterpret_cast<float *>(S),
+                                   reinterpret_cast<const float *>(DX), PART, st);
+        if (err == cudaSuccess) continue;
+        if (err != cudaErrorNotSupported) return err;
+        cudaGetLastError();
+        if (hd == 1) err = launch_ab_layer<T, 1>(a, l, S, DX, PART, st);
         else if (hd == 2) err = launch_ab_layer<T, 2>(a, l, S, DX, PART, st);
         else err = launch_ab_layer<T, 4>(a, l, S, DX, PART, st);
         if (err != cudaSuccess) return err;

@@ -87,6 +87,10 @@ def test_c2_model_small_batch(dn, prec):
     (4, 6, 3, 2, 6, 3, 0, 40, 2, 2),       # cache wider than single flips need
     (2, 8, 4, 2, 8, 2, 0, 7, 2, 1),        # N below the flip group size
     (5, 3, 2, 3, 3, 1, 1, 17, 2, 1),       # w = 3 on a ring
+    # d = 32 shapes for the streaming FP32 kernel
+    (4, 32, 8, 2, 32, 2, 1, 77, 2, 1),     # ring, ragged run of sites
+    (3, 32, 8, 1, 16, 1, 0, 50, 2, 2),     # W = 3, d_out = 1, wider link rows
+    (6, 32, 8, 2, 32, 2, 0, 40, 2, 1),     # deepest layers fall back to the generic kernel
 ])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_all_single_flips_grouped(dn, case, prec):
