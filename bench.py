@@ -177,6 +177,62 @@ def abacus_unique_bytes(N, L, d, dout, w, P, B, tb=4):
     return B * (per_sample * tb + N) + B * N * 8
 
 
+def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128):
+    """ABACUS ratios/s given caches, cache-build time and the GPU full-forward recompute
+    at N = 1024 for the 6-layer, 64-channel, 64-mode model (FP32, long-range TFIM
+    chains, all N single flips per chain; the recompute is timed on a sample of
+    `recompute_flips` flips per chain and scaled per ratio)."""
+    Nn = 1024
+    desc = synth.ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
+    params = synth.init_params(desc, 1005, a_scale=10.0)
+    spins_np = synth.spins_uniform(chains, Nn, 2005)
+    model = dn.Model(desc, params)
+    spins = torch.from_numpy(spins_np).cuda()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # Warm-up: weights, taps and kernels for this N (one chain).
+    model.forward_cache(spins[:1], prec="fp32").destroy()
+    barrier()
+    ev0.record()
+    cache = model.forward_cache(spins, prec="fp32")
+    ev1.record()
+    barrier()
+    build_ms = ev0.elapsed_time(ev1)
+    out = cache.single_flip_ratios()
+    barrier()
+    reps = 3
+    ev0.record()
+    for _ in range(reps):
+        cache.single_flip_ratios(out=out)
+    ev1.record()
+    barrier()
+    ab_ms = ev0.elapsed_time(ev1) / reps
+    cache_bytes = model.cache_bytes(Nn, 1, "fp32")
+    cache.destroy()
+    sample_np, sites_np = synth.random_flips(chains, Nn, chains * recompute_flips, seed=3005)
+    s_t = torch.from_numpy(sample_np).cuda()
+    x_t = torch.from_numpy(sites_np).cuda()
+    r = model.recompute_flip_ratios(spins, s_t, x_t, prec="fp32")
+    barrier()
+    ev0.record()
+    model.recompute_flip_ratios(spins, s_t, x_t, prec="fp32", out=r)
+    ev1.record()
+    barrier()
+    rc_ms = ev0.elapsed_time(ev1)
+    model.close()
+    ratios = chains * Nn
+    ab_rate = ratios / (ab_ms / 1e3)
+    rc_rate = chains * recompute_flips / (rc_ms / 1e3)
+    e2e_rate = ratios / ((ab_ms + build_ms) / 1e3)
+    return {"workload": "lr-TFIM N=1024 open, DysonNet L=6 d=64 s=64 w=2 FP32, %d chains x 1024 single flips" % chains,
+            "abacus_given_caches": {"value": ab_rate, "unit": "flip ratios/s", "ms": ab_ms},
+            "cache_build_ms": build_ms, "cache_bytes_per_chain": cache_bytes,
+            "recompute": {"value": rc_rate, "unit": "flip ratios/s", "ms": rc_ms,
+                          "sample": "%d random single flips per chain" % recompute_flips},
+            "abacus_incl_cache_build": {"value": e2e_rate, "unit": "flip ratios/s"},
+            "speedup_abacus_given_caches_over_recompute": ab_rate / rc_rate,
+            "speedup_incl_cache_build_over_recompute": e2e_rate / rc_rate}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,6 +244,8 @@ def main():
     ap.add_argument("--cpu-samples", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recompute", action="store_true")
+    ap.add_argument("--no-n1024", action="store_true")
+    ap.add_argument("--n1024-chains", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -296,6 +354,8 @@ def main():
         recompute = {"value": flips_step / (rms / 1e3), "unit": "flip ratios/s", "ms": rms,
                      "speedup_of_abacus_step": (flips_step / (ms / 1e3)) / (flips_step / (rms / 1e3))}
 
+    n1024 = None if args.no_n1024 else measure_n1024(dn, synth, torch, barrier, args.n1024_chains)
+
     peaks, src = _peaks()
     roof, families = roofline(prof, args.steps, desc, N, Bs, peaks, src, clocks)
     kernels = sorted(((k, v[0], v[1]) for k, v in prof.items()), key=lambda x: -x[2])
@@ -317,6 +377,7 @@ def main():
                           "ms_per_step": ab_ms},
         "cache_build_ms_per_step": build_ms,
         "recompute": recompute,
+        "n1024": n1024,
         "kernels": [{"name": k, "launches": n // args.steps, "ms_per_step": v / args.steps,
                      "share": v / total_k} for k, n, v in kernels[:16]],
     }

@@ -49,10 +49,23 @@ typedef enum {
 
 /* Arithmetic of the network and of the caches.  Every precision generates the
  * S4 kernel taps in FP64 and accumulates the pooled readout and the final
- * log cosh difference in FP64. */
+ * log cosh difference in FP64.
+ *   DN_FP64: everything in double.
+ *   DN_FP32: activations, caches and link contractions in float.  The forward
+ *     pass runs on FP32 FMA kernels; the Toeplitz hops of the link construction
+ *     run on the tcgen05 tensor cores as three BF16 products
+ *     (hi*hi + hi*lo + lo*hi) with FP32 accumulation.
+ *   DN_BF16: the S4 convolutions and the channel-mixing GEMMs of the forward pass
+ *     and the Toeplitz hops of the link construction on the tensor cores with one
+ *     BF16 product each (FP32 accumulation); caches, the adjoint, the vertex hops
+ *     of the link construction and the ABACUS contractions stay in float.
+ *     Requires d a multiple of 16, d <= 128 (else DN_EUNSUPPORTED).  Its error
+ *     against the FP64 definition is larger than DN_FP32's; the tests state the
+ *     bound. */
 typedef enum {
-    DN_FP64 = 0,   /* everything in double */
-    DN_FP32 = 1    /* activations, caches and link contractions in float */
+    DN_FP64 = 0,
+    DN_FP32 = 1,
+    DN_BF16 = 2
 } dn_precision;
 
 /* N-agnostic hyper-parameters (Sec. "Implementation of DysonNet", App.

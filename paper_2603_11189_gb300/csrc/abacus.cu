@@ -647,10 +647,11 @@ __device__ __forceinline__ double warp_sum16(double (&v)[16], int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-template <int WW>
-__global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a, int l, int R, int NS,
-                                                                float *__restrict__ S, const float *__restrict__ DX,
-                                                                double *__restrict__ PART) {
+template <int WW, int NS>
+__global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(AbArgs<float> a, int l, int R,
+                                                                              float *__restrict__ S,
+                                                                              const float *__restrict__ DX,
+                                                                              double *__restrict__ PART) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int d = 32, dd = d * d;
     const Geom &g = a.g;
@@ -674,9 +675,11 @@ __global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a,
                                              (size_t)kStWarps * (kStMaxNS + 2));
     const long long lo = l - 1;
     const long long b = blockIdx.y;
+    // VT and UT interleaved as [k/4][c][k%4]: one 16-byte load gives rows k..k+3 of column c.
     for (int q = threadIdx.x; q < dd; q += blockDim.x) {
-        VTs[q] = a.w.VT[lo * dd + q];
-        UTs[q] = a.w.UT[lo * dd + q];
+        const int k = q / d, cc = q % d, x = ((k >> 2) * d + cc) * 4 + (k & 3);
+        VTs[x] = a.w.VT[lo * dd + q];
+        UTs[x] = a.w.UT[lo * dd + q];
     }
     for (int q = threadIdx.x; q < nper * d; q += blockDim.x) {
         const int r = q / d - 2 * wd, cc = q % d;
@@ -709,21 +712,38 @@ __global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a,
                       (uint32_t)(W * d * sizeof(float)), bar);
     };
     auto flip_bytes = [&](int jj) -> uint32_t { return site_ok(jj) ? (uint32_t)(nwin * W * d * sizeof(float)) : 0u; };
-    // Link blocks: stream index n -> (site r, pair m, offset dl), all contiguous per (r, m).
-    const long long nblk = (long long)nsite * nlink * nper;
-    auto blk_src = [&](long long n) -> const float * {
-        const int r = (int)(n / (nlink * nper)), rem = (int)(n % (nlink * nper));
-        const int m = rem / nper + 1, dl = rem % nper - 2 * wd;
-        return a.K + (((b * a.P + pair_index(l, m)) * N + (i0 + r)) * nRk + (dl + a.Rk)) * (long long)dd;
+    // Link blocks, in stream order (site r, pair m, offset dl): the nper blocks of one (r, m)
+    // are contiguous.  Issue and consume positions advance incrementally (no divisions).
+    const int nblk = nsite * nlink * nper;
+    int iss_r = 0, iss_m = 1, iss_dl = 0;          // next block to issue
+    const float *iss_src = nullptr;
+    auto iss_base = [&]() {
+        iss_src = a.K + (((b * a.P + pair_index(l, iss_m)) * N + (i0 + iss_r)) * nRk + (a.Rk - 2 * wd)) * (long long)dd;
     };
-    long long issued = 0, consumed = 0;
+    auto iss_advance = [&]() {
+        if (++iss_dl == nper) {
+            iss_dl = 0;
+            if (++iss_m > nlink) {
+                iss_m = 1;
+                ++iss_r;
+            }
+            if (iss_r < nsite) iss_base();
+        } else {
+            iss_src += dd;
+        }
+    };
+    int issued = 0, consumed = 0, iss_slot = 0, con_slot = 0;
+    uint32_t con_phase = 0;
     uint32_t wpend[2] = {0u, 0u}, wuse[2] = {0u, 0u};
-    if (lane == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (; issued < nblk && issued < NS; ++issued)
-            bulk_load(Kring + (issued % NS) * dd, blk_src(issued), dd * sizeof(float), mb + issued % NS);
+    if (NS > 0 && nblk > 0) {
+        iss_base();
+        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (; issued < nblk && issued < NS; ++issued) {
+            if (lane == 0) bulk_load(Kring + iss_slot * dd, iss_src, dd * sizeof(float), mb + iss_slot);
+            iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
+            iss_advance();
+        }
     }
-    issued = nblk < NS ? nblk : NS;
     if (nwin > 0) {
         uint32_t bytes = 0;
         for (int jj = i0 - wd; jj <= i0 + wd; ++jj) bytes += flip_bytes(jj);
@@ -819,12 +839,16 @@ __global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a,
         for (int mi = 0; mi < nlink && !timed_out; ++mi) {
             const float *wm = Win + (size_t)mi * W1 * W * d;
             for (int bi = 0; bi < nper; ++bi) {
-                const int slot = (int)(consumed % NS);
-                if (!mbar_wait(mb + slot, (uint32_t)((consumed / NS) & 1))) {
+                const int slot = con_slot;
+                if (!mbar_wait(mb + slot, con_phase)) {
                     timed_out = true;
                     break;
                 }
                 ++consumed;
+                if (++con_slot == NS) {
+                    con_slot = 0;
+                    con_phase ^= 1u;
+                }
                 const int dl = bi - 2 * wd;
                 if (site_ok(i + dl)) {
                     const float *Kb = Kring + slot * dd + c * d;
@@ -858,9 +882,11 @@ __global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a,
                 if (issued < nblk) {
                     if (lane == 0) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        bulk_load(Kring + (issued % NS) * dd, blk_src(issued), dd * sizeof(float), mb + issued % NS);
+                        bulk_load(Kring + iss_slot * dd, iss_src, dd * sizeof(float), mb + iss_slot);
                     }
                     ++issued;
+                    iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
+                    iss_advance();
                 }
             }
         }
@@ -877,13 +903,11 @@ __global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a,
         for (int q = 0; q < W; ++q) z[q] = y_c;
 #pragma unroll 2
         for (int c2 = 0; c2 < d; c2 += 4) {
-            const float v0 = VTs[(c2 + 0) * d + c], v1 = VTs[(c2 + 1) * d + c], v2 = VTs[(c2 + 2) * d + c],
-                        v3 = VTs[(c2 + 3) * d + c];
+            const float4 v = *reinterpret_cast<const float4 *>(VTs + ((c2 >> 2) * d + c) * 4);
 #pragma unroll
             for (int q = 0; q < W; ++q) {
-                if (q >= W) break;
                 const float4 pv = *reinterpret_cast<const float4 *>(pq + q * d + c2);
-                z[q] += v0 * pv.x + v1 * pv.y + v2 * pv.z + v3 * pv.w;
+                z[q] += v.x * pv.x + v.y * pv.y + v.z * pv.z + v.w * pv.w;
             }
         }
 #pragma unroll
@@ -895,13 +919,11 @@ __global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a,
         for (int q = 0; q < W; ++q) sv[q] = 0.f;
 #pragma unroll 2
         for (int c2 = 0; c2 < d; c2 += 4) {
-            const float u0 = UTs[(c2 + 0) * d + c], u1 = UTs[(c2 + 1) * d + c], u2 = UTs[(c2 + 2) * d + c],
-                        u3 = UTs[(c2 + 3) * d + c];
+            const float4 u = *reinterpret_cast<const float4 *>(UTs + ((c2 >> 2) * d + c) * 4);
 #pragma unroll
             for (int q = 0; q < W; ++q) {
-                if (q >= W) break;
                 const float4 gv = *reinterpret_cast<const float4 *>(gq + q * d + c2);
-                sv[q] += u0 * gv.x + u1 * gv.y + u2 * gv.z + u3 * gv.w;
+                sv[q] += u.x * gv.x + u.y * gv.y + u.z * gv.z + u.w * gv.w;
             }
         }
         double part[16];
@@ -935,8 +957,12 @@ __global__ void __launch_bounds__(32 * kStWarps, 1) k_ab_stream(AbArgs<float> a,
         if (lane == 0) atomicOr(a.flag, 4u);
         // Let the copies in flight land before the shared memory is released.
         while (consumed < issued) {
-            mbar_wait(mb + consumed % NS, (uint32_t)((consumed / NS) & 1));
+            mbar_wait(mb + con_slot, con_phase);
             ++consumed;
+            if (++con_slot == NS) {
+                con_slot = 0;
+                con_phase ^= 1u;
+            }
         }
         for (int pb = 0; pb < 2; ++pb)
             if (wpend[pb]) mbar_wait(wmb + pb, wuse[pb] & 1u);
@@ -1018,6 +1044,30 @@ static size_t ab_stream_smem(const Geom &g, int l, int NS) {
     return bytes <= 227 * 1024 ? bytes : 0;
 }
 
+template <int WW, int NS>
+static cudaError_t launch_ab_stream_one(const AbArgs<float> &a, int l, int R, dim3 grid, size_t smem, float *S,
+                                       const float *DX, double *PART, cudaStream_t st) {
+    cudaError_t err = cudaFuncSetAttribute(k_ab_stream<WW, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_ab_layer", st);
+        k_ab_stream<WW, NS><<<grid, 32 * kStWarps, smem, st>>>(a, l, R, S, DX, PART);
+    }
+    return cudaGetLastError();
+}
+
+template <int WW>
+static cudaError_t launch_ab_stream_ns(const AbArgs<float> &a, int l, int R, int NS, dim3 grid, size_t smem, float *S,
+                                      const float *DX, double *PART, cudaStream_t st) {
+    switch (NS) {
+    case 0: return launch_ab_stream_one<WW, 0>(a, l, R, grid, smem, S, DX, PART, st);
+    case 2: return launch_ab_stream_one<WW, 2>(a, l, R, grid, smem, S, DX, PART, st);
+    case 3: return launch_ab_stream_one<WW, 3>(a, l, R, grid, smem, S, DX, PART, st);
+    case 4: return launch_ab_stream_one<WW, 4>(a, l, R, grid, smem, S, DX, PART, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, const float *DX, double *PART,
                                     cudaStream_t st) {
     const Geom &g = a.g;
@@ -1032,22 +1082,9 @@ static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, con
     // Runs of 8 sites per warp: long enough to keep the copy ring full across sites.
     const int R = 8;
     dim3 grid((unsigned)((g.N + kStWarps * R - 1) / (kStWarps * R)), (unsigned)a.B);
-    cudaError_t err;
-    if (g.W == 5) {
-        if ((err = cudaFuncSetAttribute(k_ab_stream<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-            return err;
-        ProfScope _ps("k_ab_layer", st);
-        k_ab_stream<5><<<grid, 32 * kStWarps, smem, st>>>(a, l, R, NS, S, DX, PART);
-    } else if (g.W == 3) {
-        if ((err = cudaFuncSetAttribute(k_ab_stream<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-            return err;
-        ProfScope _ps("k_ab_layer", st);
-        k_ab_stream<3><<<grid, 32 * kStWarps, smem, st>>>(a, l, R, NS, S, DX, PART);
-    } else {
-        return cudaErrorNotSupported;
-    }
+    if (g.W == 5) return launch_ab_stream_ns<5>(a, l, R, NS, grid, smem, S, DX, PART, st);
+    if (g.W == 3) return launch_ab_stream_ns<3>(a, l, R, NS, grid, smem, S, DX, PART, st);
+    return cudaErrorNotSupported;
     return cudaGetLastError();
 }
 

@@ -193,7 +193,7 @@ const dn::Plan<T> &ensure_plan(dn_model *m, int N, cudaStream_t st) {
 // y (may be null) receives V u0 per layer; Omega/logpsi in FP64.
 template <typename T>
 void run_forward(dn_model *m, const dn::Plan<T> &pl, const dn::Weights<T> &w, int N, const int8_t *spins, int B,
-                 T *chi, T *y, double *Omega, double *logpsi, cudaStream_t st) {
+                 T *chi, T *y, double *Omega, double *logpsi, int prec, unsigned *flag, cudaStream_t st) {
     dn::ProfPhase phase("forward");
     const dn::Geom g = dn::geom_of(m, N);
     const int L = g.L, d = g.d;
@@ -204,6 +204,27 @@ void run_forward(dn_model *m, const dn::Plan<T> &pl, const dn::Weights<T> &w, in
     double *pooled = pb.as<double>();
     ck(dn::launch_chi<T>(g, w, spins, B, chi, st));
     ck(dn::launch_pool0<T>(g, spins, w.e, pl.omega, B, pooled, (long long)(L + 1) * d, st));
+    if constexpr (sizeof(T) == 4) {
+        if (prec == DN_BF16 && dn::forward_tc_ok(g)) {
+            // BF16: tensor cores, channel-major activations h[c][n B + b] (forward_tc.cu).
+            // The FP32 forward stays on the FMA kernels: tensor-core FP32 accumulation over
+            // the K = N sites of the convolution, even with operands split into three BF16
+            // planes, measured 1.1e-4 on log-ratios of the N = 128 workload model, above the
+            // FP32 bound.
+            const int planes = 1;
+            ck(dn::launch_h0_cm(g, spins, w.e, B, h, st));
+            for (int l = 1; l <= L; ++l) {
+                const T *taps_l = pl.taps + (long long)(l - 1) * g.R * d;
+                ck(dn::launch_tgemm_tc(g, taps_l, B, h, nullptr, nullptr, 0, u, nullptr, 0, 0, 0, 0, 1, 0, 1, flag, st,
+                                       planes));
+                ck(dn::launch_mix_tc(g, l, w, u, chi, y, h, B, planes, flag, st));
+                ck(dn::launch_pool_cm(g, l, h, pl.omega, B, pooled, (long long)(L + 1) * d, st));
+            }
+            ck(dn::launch_readout(g, m->desc.f_kind, m->A64, pooled, L + 1, B, spins, Omega, logpsi, st));
+            return;
+        }
+    }
+    if (prec == DN_BF16) throw Fail{DN_EUNSUPPORTED};
     dn::Fields<T> H{h, field, 0, 1}, Uf{u, field, 0, 1}, none{nullptr, 0, 0, 1};
     for (int l = 1; l <= L; ++l) {
         const T *taps_l = pl.taps + (long long)(l - 1) * g.R * d;
@@ -267,6 +288,15 @@ size_t cache_bytes(const dn_model_desc &D, int N, int B, int prec, int mc) {
     return prec == DN_FP64 ? cache_layout<double>(D, N, B, mc).total : cache_layout<float>(D, N, B, mc).total;
 }
 
+bool prec_valid(int prec) { return prec == DN_FP64 || prec == DN_FP32 || prec == DN_BF16; }
+
+// BF16 runs only where the tensor-core forward applies.
+bool prec_supported(const dn_model *m, int prec) {
+    if (prec != DN_BF16) return true;
+    const int d = m->desc.d;
+    return d % 16 == 0 && d >= 16 && d <= 128;
+}
+
 bool cache_args_ok(const dn_model *m, int N, int B, int mc) {
     if (!m || N < 1 || B < 1 || mc < 1 || mc > 3) return false;
     const int W = 2 * m->desc.w + 1, WF = W + mc - 1;
@@ -313,7 +343,7 @@ dn_cache *build_cache(dn_model *m, int N, const int8_t *spins_dev, int B, int pr
         ck(cudaMemsetAsync(c->flag, 0, sizeof(unsigned), st));
         ck(dn::launch_check_spins(spins_dev, (long long)B * N, c->spins, c->flag, st));
         run_forward<T>(m, pl, w, N, c->spins, B, static_cast<T *>(c->chi), static_cast<T *>(c->y), c->Omega,
-                       c->logpsi, st);
+                       c->logpsi, prec, c->flag, st);
         run_adjoint<T>(m, pl, w, c, st);
         if (D.L >= 2) {
             dn::ProfPhase phase("links");
@@ -330,12 +360,13 @@ dn_cache *build_cache(dn_model *m, int N, const int8_t *spins_dev, int B, int pr
 }
 
 template <typename T>
-void full_forward(dn_model *m, int N, const int8_t *spins_dev, int B, cudaStream_t st, double *logpsi,
+void full_forward(dn_model *m, int N, const int8_t *spins_dev, int B, int prec, cudaStream_t st, double *logpsi,
                   double *Omega) {
     const dn::Plan<T> &pl = ensure_plan<T>(m, N, st);
     const dn::Weights<T> &w = ensure_weights<T>(m, st);
     DevBuf chi((size_t)B * m->desc.L * N * m->desc.d * sizeof(T), st);
-    run_forward<T>(m, pl, w, N, spins_dev, B, chi.as<T>(), nullptr, Omega, logpsi, st);
+    // No cache flag here: a timed-out tensor-core tile writes NaN, which reaches logpsi.
+    run_forward<T>(m, pl, w, N, spins_dev, B, chi.as<T>(), nullptr, Omega, logpsi, prec, nullptr, st);
 }
 
 }  // namespace
@@ -467,7 +498,7 @@ void dn_model_destroy(dn_model *m) {
 }
 
 size_t dn_cache_bytes(const dn_model *m, int N, int batch, dn_precision prec, int max_cluster) {
-    if (!cache_args_ok(m, N, batch, max_cluster) || (prec != DN_FP64 && prec != DN_FP32)) return 0;
+    if (!cache_args_ok(m, N, batch, max_cluster) || !prec_valid(prec)) return 0;
     return cache_bytes(m->desc, N, batch, prec, max_cluster);
 }
 
@@ -475,7 +506,8 @@ dn_status dysonnet_forward_cache(dn_model *m, int N, const int8_t *spins_dev, in
                                  int max_cluster, void *stream, dn_cache **cache_out, double *logpsi_dev) {
     if (!cache_out) return DN_EINVAL;
     *cache_out = nullptr;
-    if (!cache_args_ok(m, N, B, max_cluster) || !spins_dev || (prec != DN_FP64 && prec != DN_FP32)) return DN_EINVAL;
+    if (!cache_args_ok(m, N, B, max_cluster) || !spins_dev || !prec_valid(prec)) return DN_EINVAL;
+    if (!prec_supported(m, prec)) return DN_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return guard([&]() -> dn_status {
         dn_cache *c = prec == DN_FP64 ? build_cache<double>(m, N, spins_dev, B, prec, max_cluster, st)
@@ -543,7 +575,8 @@ dn_status abacus_single_flip_ratios(const dn_cache *c, double *dlogpsi_dev, void
 dn_status local_energy(dn_model *m, const dn_hamiltonian *H, int N, const int8_t *spins_dev, int B,
                        dn_precision prec, void *stream, double *eloc_dev) {
     if (!m || !H || !spins_dev || !eloc_dev || B < 1 || N < 1) return DN_EINVAL;
-    if (prec != DN_FP64 && prec != DN_FP32) return DN_EINVAL;
+    if (!prec_valid(prec)) return DN_EINVAL;
+    if (!prec_supported(m, prec)) return DN_EUNSUPPORTED;
     if (H->kind != 0 && H->kind != 1) return DN_EINVAL;
     if (H->kind == 1 && N < 3) return DN_EINVAL;
     if (H->kind == 0 && !(H->alpha >= 0.0)) return DN_EINVAL;
@@ -598,11 +631,12 @@ dn_status local_energy(dn_model *m, const dn_hamiltonian *H, int N, const int8_t
 dn_status dn_full_forward(dn_model *m, int N, const int8_t *spins_dev, int B, dn_precision prec, void *stream,
                           double *logpsi_dev, double *Omega_dev) {
     if (!m || !spins_dev || !logpsi_dev || N < 1 || B < 1) return DN_EINVAL;
-    if (prec != DN_FP64 && prec != DN_FP32) return DN_EINVAL;
+    if (!prec_valid(prec)) return DN_EINVAL;
+    if (!prec_supported(m, prec)) return DN_EUNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return guard([&]() -> dn_status {
-        if (prec == DN_FP64) full_forward<double>(m, N, spins_dev, B, st, logpsi_dev, Omega_dev);
-        else full_forward<float>(m, N, spins_dev, B, st, logpsi_dev, Omega_dev);
+        if (prec == DN_FP64) full_forward<double>(m, N, spins_dev, B, prec, st, logpsi_dev, Omega_dev);
+        else full_forward<float>(m, N, spins_dev, B, prec, st, logpsi_dev, Omega_dev);
         return DN_OK;
     });
 }
@@ -611,7 +645,8 @@ dn_status dn_recompute_flip_ratios(dn_model *m, int N, const int8_t *spins_dev, 
                                    const int32_t *sites_dev, int F, dn_precision prec, void *stream,
                                    double *dlogpsi_dev) {
     if (!m || !spins_dev || N < 1 || B < 1 || F < 0) return DN_EINVAL;
-    if (prec != DN_FP64 && prec != DN_FP32) return DN_EINVAL;
+    if (!prec_valid(prec)) return DN_EINVAL;
+    if (!prec_supported(m, prec)) return DN_EUNSUPPORTED;
     if (F == 0) return DN_OK;
     if (!sample_dev || !sites_dev || !dlogpsi_dev) return DN_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -209,9 +209,21 @@ size_t links_scratch_elems(const dn_model *m, int N, int B);
 // Toeplitz hop of the FP32 link build on the tcgen05 tensor cores (tc_gemm.cu):
 // Y[b][a] = T_a X[b][a] (X generated from gtaps/gDm when gtaps != nullptr), band
 // rows to band (may be null).  cudaErrorNotSupported when the shape does not fit.
+// planes = BF16 terms per operand value: 1 (plain BF16), 2 (three products, about
+// 2^-18 relative), 3 (six products, FP32-grade).
 cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float *X, const float *gtaps,
                             const float *gDm, long long dm_ss, float *Y, float *band, long long bss, long long brs,
-                            long long bos, int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st);
+                            long long bos, int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st,
+                            int planes = 2);
+
+// Tensor-core forward pass (forward_tc.cu); activations channel-major h[c][n B + b].
+bool forward_tc_ok(const Geom &g);
+cudaError_t launch_h0_cm(const Geom &g, const int8_t *spins, const float *e, int B, float *h, cudaStream_t st);
+cudaError_t launch_pool_cm(const Geom &g, int l, const float *h, const float *omega, int B, double *pooled,
+                           long long pstride, cudaStream_t st);
+// chi and y (may be null) are the caches' base pointers [B][L][N][d]; layer l is selected inside.
+cudaError_t launch_mix_tc(const Geom &g, int l, const Weights<float> &w, const float *ucm, const float *chi, float *y,
+                          float *hcm, int B, int planes, unsigned *flag, cudaStream_t st);
 
 // ABACUS (abacus.cu).
 template <typename T>

@@ -77,31 +77,37 @@ __global__ void k_dmat(Geom g, Weights<T> w, const T *__restrict__ chi, long lon
 }
 
 // Embedding sources through layer 1: X[b][a][n][k] = (D0^(1)_n (g^(1)_{n-k} * e))_a.
-// One CTA per (sample, site n): D0_n and the N needed tap rows are staged in
-// shared memory (rows padded to d+1 floats), then X[:, n, :] = D0_n G.
+// One CTA per (sample, site n): D0_n and the tap rows of 128 sources at a time are
+// staged in shared memory (rows padded to d+1 floats), then X[:, n, :] = D0_n G.
+constexpr int kEmbChunk = 128;   // source sites staged per pass
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_embed_src(Geom g, const T *__restrict__ taps1, const T *__restrict__ e,
                                                    const T *__restrict__ Dm, T *__restrict__ X) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d, L = g.L, dp = d + 1;
     T *Ds = reinterpret_cast<T *>(smraw);      // [d][d]
-    T *Gs = Ds + d * d;                        // [N][d+1]
+    T *Gs = Ds + d * d;                        // [kEmbChunk][d+1]: sources k0 .. k0 + kEmbChunk - 1
     const long long blk = blockIdx.x;
     const int n = (int)(blk % N);
     const long long bl = blk / N;
     const long long dd = (long long)d * d;
     const T *D = Dm + ((bl * (L - 1)) * N + n) * dd;
     for (int q = threadIdx.x; q < d * d; q += blockDim.x) Ds[q] = D[q];
-    for (int q = threadIdx.x; q < N * d; q += blockDim.x) {
-        const int k = q / d, c = q % d;
-        Gs[k * dp + c] = taps1[(long long)tap_row(n - k, N, g.periodic) * d + c] * e[c];
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < d * N; idx += blockDim.x) {
-        const int a = idx / N, k = idx % N;
-        T acc = 0;
-        for (int c = 0; c < d; ++c) acc += Ds[a * d + c] * Gs[k * dp + c];
-        X[((bl * d + a) * N + n) * (long long)N + k] = acc;
+    for (int k0 = 0; k0 < N; k0 += kEmbChunk) {
+        const int kn = N - k0 < kEmbChunk ? N - k0 : kEmbChunk;
+        __syncthreads();
+        for (int q = threadIdx.x; q < kn * d; q += blockDim.x) {
+            const int kk = q / d, c = q % d;
+            Gs[kk * dp + c] = taps1[(long long)tap_row(n - (k0 + kk), N, g.periodic) * d + c] * e[c];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < d * kn; idx += blockDim.x) {
+            const int a = idx / kn, kk = idx % kn;
+            T acc = 0;
+            for (int c = 0; c < d; ++c) acc += Ds[a * d + c] * Gs[kk * dp + c];
+            X[((bl * d + a) * N + n) * (long long)N + k0 + kk] = acc;
+        }
     }
 }
 
@@ -284,13 +290,24 @@ __global__ void __launch_bounds__(256) k_dhop(Geom g, int P, int cols, const T *
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[r][j] += dv[r] * yv[j];
         }
+        const int pb = p0 + tx * 4;
+        const bool vec = sizeof(T) == 4 && P % 4 == 0 && pb + 3 < P;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int c = ty * 8 + r;
+            T *dst = Xo + ((bl * d + c) * N + i) * (long long)P + pb;
+            if (vec) {
+                // one 16-byte store per row: a warp writes 512 contiguous bytes
+                float4 v;
+                v.x = (float)acc[r][0];
+                v.y = (float)acc[r][1];
+                v.z = (float)acc[r][2];
+                v.w = (float)acc[r][3];
+                *reinterpret_cast<float4 *>(dst) = v;
+            } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int p = p0 + tx * 4 + j;
-                if (p < P) Xo[((bl * d + c) * N + i) * (long long)P + p] = acc[r][j];
+                for (int j = 0; j < 4; ++j)
+                    if (pb + j < P) dst[j] = acc[r][j];
             }
         }
     } else {
@@ -365,6 +382,71 @@ __global__ void __launch_bounds__(256) k_bandconv(Geom g, const T *__restrict__ 
     }
 }
 
+// Same band, FP32, four adjacent source columns per lane (they share the source site k,
+// so they share the taps): one 16-byte load of X per site, taps from a shared table
+// already wrapped for rings (no index arithmetic in the loop), one 16-byte store per
+// band entry.  Requires nsrc % 4 == 0 and P % 4 == 0.
+template <int NB>
+__global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restrict__ taps, int P,
+                                                   const float *__restrict__ X, float *__restrict__ band, BandDst bd,
+                                                   long long b0) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d, R = bd.R, ns = bd.nsrc;
+    const int pad = kBcMaxBand + 1;
+    float *gx = reinterpret_cast<float *>(smraw);   // gx[pad + r + N - 1] = g_{r,a} (wrapped on a ring)
+    const int gx_len = 2 * N - 1 + 2 * pad;
+    const int chunks = (P + 1023) / 1024;           // 256 threads x 4 columns per CTA
+    const long long blk = blockIdx.x;
+    const int ch = (int)(blk % chunks);
+    const int a = (int)((blk / chunks) % d);
+    const long long bl = blk / ((long long)chunks * d);
+    for (int q = threadIdx.x; q < gx_len; q += blockDim.x) {
+        int r = q - pad - (N - 1);
+        float v = 0.f;
+        if (g.periodic) {
+            r = ((r % N) + N) % N;
+            v = taps[(long long)tap_row(r, N, 1) * d + a];
+        } else if (r > -N && r < N) {
+            v = taps[(long long)tap_row(r, N, 0) * d + a];
+        }
+        gx[q] = v;
+    }
+    __syncthreads();
+    const int p = ch * 1024 + 4 * threadIdx.x;
+    if (p >= P) return;
+    const int k = p / ns, c = p - k * ns;
+    const float *Xa = X + (bl * d + a) * (long long)N * P + p;
+    const float *gk = gx + pad + (k - R) + (N - 1);   // tap of (q, n) at gk[q - n]
+    float acc[NB][4];
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[q][j] = 0.f;
+#pragma unroll 2
+    for (int n = 0; n < N; ++n) {
+        const float4 xv = *reinterpret_cast<const float4 *>(Xa + (long long)n * P);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            if (q > 2 * R) break;
+            const float w = gk[q - n];
+            acc[q][0] = fmaf(w, xv.x, acc[q][0]);
+            acc[q][1] = fmaf(w, xv.y, acc[q][1]);
+            acc[q][2] = fmaf(w, xv.z, acc[q][2]);
+            acc[q][3] = fmaf(w, xv.w, acc[q][3]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        if (q > 2 * R) break;
+        const int dl = q - R;
+        int i = k + dl;
+        if (g.periodic) i = ((i % N) + N) % N;
+        else if (i < 0 || i >= N) continue;
+        float *dst = band + (b0 + bl) * bd.ss + (long long)i * bd.rs + (long long)(R - dl) * bd.os + (long long)a * ns + c;
+        *reinterpret_cast<float4 *>(dst) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+    }
+}
+
 // ------------------------------------------------------------------- host --
 static size_t links_per_sample_elems(const dn_model *m, int N) {
     const long long d = m->desc.d, L = m->desc.L;
@@ -385,17 +467,18 @@ template <typename T>
 static cudaError_t launch_tgemm_ffma(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *Y,
                                      T *band, const BandDst &bd, long long b0, int nb, cudaStream_t st);
 
-// FP32: tensor cores (three BF16 products); FP64: the FMA kernel.
+// FP32/BF16: tensor cores (BF16 planes per operand value); FP64: the FMA kernel.
 template <typename T>
 static cudaError_t launch_tgemm(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *Y, T *band,
-                                const BandDst &bd, long long b0, int nb, unsigned *flag, cudaStream_t st) {
+                                const BandDst &bd, long long b0, int nb, unsigned *flag, cudaStream_t st,
+                                int planes = 2) {
     if constexpr (sizeof(T) == 4) {
         cudaError_t err = launch_tgemm_tc(g, reinterpret_cast<const float *>(taps), P,
                                           reinterpret_cast<const float *>(X),
                                           gs ? reinterpret_cast<const float *>(gs->taps) : nullptr,
                                           gs ? reinterpret_cast<const float *>(gs->Dm) : nullptr, gs ? gs->dm_ss : 0,
                                           reinterpret_cast<float *>(Y), reinterpret_cast<float *>(band), bd.ss, bd.rs,
-                                          bd.os, bd.R, bd.nsrc, b0, nb, flag, st);
+                                          bd.os, bd.R, bd.nsrc, b0, nb, flag, st, planes);
         if (err != cudaErrorNotSupported) return err;
         cudaGetLastError();
     }
@@ -449,10 +532,35 @@ static cudaError_t launch_bandconv_gen(const Geom &g, const T *taps, int P, cons
     return cudaErrorInvalidConfiguration;
 }
 
+template <int NB>
+static cudaError_t launch_bandconv4_nb(const Geom &g, const float *taps, int P, const float *X, float *band,
+                                       const BandDst &bd, long long b0, int nb, cudaStream_t st) {
+    const size_t smem = ((size_t)2 * g.N - 1 + 2 * (kBcMaxBand + 1)) * sizeof(float);
+    const int chunks = (P + 1023) / 1024;
+    const unsigned blocks = (unsigned)((long long)nb * g.d * chunks);
+    cudaError_t err = cudaFuncSetAttribute(k_bandconv4<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_bandconv", st);
+        k_bandconv4<NB><<<blocks, 256, smem, st>>>(g, taps, P, X, band, bd, b0);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t launch_bandconv(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *band,
                                    const BandDst &bd, long long b0, int nb, cudaStream_t st) {
     if (gs) return launch_bandconv_gen<T, true>(g, taps, P, nullptr, *gs, band, bd, b0, nb, st);
+    if constexpr (sizeof(T) == 4) {
+        if (bd.nsrc % 4 == 0 && P % 4 == 0) {
+            const float *tf = reinterpret_cast<const float *>(taps), *xf = reinterpret_cast<const float *>(X);
+            float *bf = reinterpret_cast<float *>(band);
+            const int nbw = 2 * bd.R + 1;
+            if (nbw <= 5) return launch_bandconv4_nb<5>(g, tf, P, xf, bf, bd, b0, nb, st);
+            if (nbw <= 9) return launch_bandconv4_nb<9>(g, tf, P, xf, bf, bd, b0, nb, st);
+            if (nbw <= 13) return launch_bandconv4_nb<13>(g, tf, P, xf, bf, bd, b0, nb, st);
+        }
+    }
     return launch_bandconv_gen<T, false>(g, taps, P, X, GenSrc<T>{nullptr, nullptr, 0}, band, bd, b0, nb, st);
 }
 
@@ -494,6 +602,7 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
     T *ell = static_cast<T *>(c->ell);
     T *K = static_cast<T *>(c->K);
     const int nRl = 2 * c->Rl + 1, nRk = 2 * c->Rk + 1;
+    const int planes = c->prec == DN_BF16 ? 1 : 2;   // BF16: single-product Toeplitz hops; FP32: 3 products
     cudaError_t err;
     for (int b0 = 0; b0 < c->B; b0 += nb_max) {
         const int nb = (c->B - b0 < nb_max) ? c->B - b0 : nb_max;
@@ -507,7 +616,7 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         // Embedding sources (m = 0), P = N.
         {
-            const size_t smem = ((size_t)d * d + (size_t)N * (d + 1)) * sizeof(T);
+            const size_t smem = ((size_t)d * d + (size_t)(N < kEmbChunk ? N : kEmbChunk) * (d + 1)) * sizeof(T);
             if ((err = cudaFuncSetAttribute(k_embed_src<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
                 cudaSuccess)
                 return err;
@@ -520,7 +629,7 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
             T *dst = ell + (long long)(n - 2) * N * nRl * d;
             const T *taps_n = pl.taps + (long long)(n - 1) * g.R * d;
             if (n < L) {
-                if ((err = launch_tgemm<T>(g, taps_n, N, F, nullptr, U, dst, bd, b0, nb, c->flag, st)) != cudaSuccess)
+                if ((err = launch_tgemm<T>(g, taps_n, N, F, nullptr, U, dst, bd, b0, nb, c->flag, st, planes)) != cudaSuccess)
                     return err;
                 if ((err = launch_dhop<T>(g, N, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st)) != cudaSuccess)
                     return err;
@@ -538,7 +647,7 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
                 const bool first = n == msrc + 2;
                 if (n < L) {
                     err = launch_tgemm<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, U, dst, bd,
-                                          b0, nb, c->flag, st);
+                                          b0, nb, c->flag, st, planes);
                     if (err != cudaSuccess) return err;
                     if ((err = launch_dhop<T>(g, (int)Pm, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st)) !=
                         cudaSuccess)

@@ -186,6 +186,7 @@ cudaError_t noalloc_forward(const dn_model *m, int N, const int8_t *spins, int B
 extern "C" dn_status dn_full_forward_noalloc(const dn_model *m, int N, const int8_t *spins_dev, int B,
                                              dn_precision prec, void *stream, double *logpsi_dev, double *Omega_dev) {
     if (!m || !spins_dev || !logpsi_dev || N < 1 || B < 1) return DN_EINVAL;
+    if (prec == DN_BF16) return DN_EUNSUPPORTED;
     if (prec != DN_FP64 && prec != DN_FP32) return DN_EINVAL;
     const size_t need = prec == DN_FP64 ? dn::noalloc_layout<double>(m->desc, N, B).total
                                         : dn::noalloc_layout<float>(m->desc, N, B).total;

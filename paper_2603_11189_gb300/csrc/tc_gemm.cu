@@ -10,19 +10,26 @@
 // Shared-memory operands use the no-swizzle K-major canonical layout: a slab of
 // 16 K values holds 8-row x 16-byte core matrices, K-adjacent cores 128 B apart
 // (leading byte offset) and row-group-adjacent cores 256 B apart (stride byte
-// offset).  One thread issues the MMAs (M=128, N=256, K=16 each) and commits
+// offset).  The Toeplitz operand is stored as a Hankel matrix instead: running the
+// contraction over each 64-site chunk in reverse order makes A(r, k) depend on
+// r + k only, so a 128 x 64 chunk has 23 distinct core matrices, stored once and
+// addressed with both offsets equal to 128 B.  One thread issues the MMAs (M=128, N=256, K=16 each) and commits
 // them to an mbarrier; every wait is bounded, and a timeout raises bit 8 of the
 // error flag, skips the epilogue and still releases the tensor memory.
 #include <cuda_bf16.h>
 
 #include "dn_internal.cuh"
+#include "tc_common.cuh"
 
 namespace dn {
 
 namespace {
 
 constexpr int kTcM = 128, kTcK = 64;     // K staged 64 sites (4 MMA slabs) at a time
-constexpr int kSlabA = kTcM * 16 * 2;    // bytes per 16-wide K slab of A (B: TN * 32)
+constexpr int kHankel = kTcM / 8 + kTcK / 8 - 1;   // distinct core matrices of a Toeplitz chunk
+constexpr int kHankelBytes = ((kHankel * 128 + 1023) / 1024) * 1024;
+constexpr int kNBuf = 1;                 // operand buffers per CTA
+constexpr int kEpiBytes = 8 * 32 * 33 * 4; // epilogue staging: one 32 x 33 float tile per warp
 constexpr long kTcSpin = 1L << 24;
 
 __device__ __forceinline__ uint32_t sm_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -32,6 +39,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
     d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;     // K-adjacent core matrices
     d |= (uint64_t)((256u >> 4) & 0x3FFF) << 32;     // row-group-adjacent core matrices
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Descriptor of a Hankel operand: core matrices one 128-B step apart along both rows and K,
+// so that core (rg, kg) is read from start + 128 (rg + kg).
+__device__ __forceinline__ uint64_t umma_desc_hankel(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
@@ -53,18 +71,6 @@ __device__ __forceinline__ int ring_delta_tc(int dl, int N, int periodic) {
     return dl;
 }
 
-// Eight consecutive K values of one row -> their BF16 hi and lo parts, one 16-byte store each.
-__device__ __forceinline__ void split_store8(unsigned char *hi, unsigned char *lo, uint32_t off, const float *v) {
-    __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        h[u] = __float2bfloat16_rn(v[u]);
-        l[u] = __float2bfloat16_rn(v[u] - __bfloat162float(h[u]));
-    }
-    *reinterpret_cast<uint4 *>(hi + off) = *reinterpret_cast<const uint4 *>(h);
-    *reinterpret_cast<uint4 *>(lo + off) = *reinterpret_cast<const uint4 *>(l);
-}
-
 __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity) {
     uint32_t done = 0;
     for (long it = 0; it < kTcSpin; ++it) {
@@ -79,8 +85,8 @@ __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity) {
 
 }  // namespace
 
-template <bool GEN, int TN>
-__global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restrict__ taps, int P,
+template <bool GEN, int TN, int NPL>
+__global__ void __launch_bounds__(256, 3) k_tgemm_tc(Geom g, const float *__restrict__ taps, int P,
                                                   const float *__restrict__ X, const float *__restrict__ gtaps,
                                                   const float *__restrict__ gDm, long long dm_ss, float *__restrict__ Y,
                                                   float *__restrict__ band, long long bss, long long brs, long long bos,
@@ -88,17 +94,21 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
     extern __shared__ __align__(1024) unsigned char smtc[];
     constexpr int kTcN = TN, kSlabB = TN * 16 * 2, kTpc = 256 / TN;   // threads per B column
     const int N = g.N, d = g.d;
-    unsigned char *Ahi = smtc;                            // 4 slabs x kSlabA
-    unsigned char *Alo = Ahi + 4 * kSlabA;
-    unsigned char *Bhi = Alo + 4 * kSlabA;                // 4 slabs x kSlabB
-    unsigned char *Blo = Bhi + 4 * kSlabB;
-    float *gx = reinterpret_cast<float *>(Blo + 4 * kSlabB);   // taps of channel a: gx[r + N - 1]
+    // One operand buffer (a second one would cost an SM a resident CTA, which measured slower):
+    // chunk c waits for the MMAs of chunk c - 1 before it overwrites the operands.
+    // Operand planes (NPL BF16 terms per value): A planes, then B planes.  The epilogue reuses
+    // the start of shared memory as 8 staging tiles of 32 x 33 floats, so everything else
+    // starts after the larger of the two regions.
+    constexpr int kBuf = NPL * (kHankelBytes + 4 * kSlabB);
+    constexpr int kFront = kNBuf * kBuf > kEpiBytes ? kNBuf * kBuf : kEpiBytes;
+    float *gx = reinterpret_cast<float *>(smtc + kFront);   // taps of channel a: gx[r + N - 1]
     float *Dms = gx + ((2 * N + 1) & ~1);                       // [32][d]   (generated operand only)
     float *Tps = Dms + (GEN ? 32 * d : 0);                      // [32 + nk - 1][d]
     const int nk = (kTcN + d - 1) / d + 1;                      // source sites a column tile touches
     const bool gstage = GEN && (kTcN % d == 0) && d <= 64;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(Tps + (GEN ? ((32 + nk - 1) * d + 1) / 2 * 2 : 0));
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Tps + (GEN ? ((32 + nk - 1) * d + 1) / 2 * 2 : 0));   // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    int *s_ok = reinterpret_cast<int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int p0 = blockIdx.x * kTcN, i0 = blockIdx.y * kTcM;
     const long long za = blockIdx.z;
@@ -107,7 +117,9 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
     for (int q = tid; q < 2 * N - 1; q += blockDim.x) gx[q] = taps[(long long)tap_row_tc(q - (N - 1), N, g.periodic) * d + a];
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_u32(mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_u32(mbar + 1)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
+        *s_ok = 1;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_u32(tslot)), "r"(TN));
@@ -131,40 +143,51 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
     const float *xcol = (!GEN) ? X + (bl * d + a) * (long long)N * P + pcol : nullptr;
     const float *dmcol = GEN ? gDm + bl * dm_ss + (long long)a * d + cq : nullptr;
     const long long dd = (long long)d * d;
-    bool ok = true;
-    uint32_t phase = 0;
+    uint32_t waits[2] = {0u, 0u};
     const int nchunks = (N + kTcK - 1) / kTcK;
-    for (int ch = 0; ch < nchunks && ok; ++ch) {
-        const int n0 = ch * kTcK;
-        if (ch > 0) {
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int n0 = ch * kTcK, buf = ch % kNBuf;
+        unsigned char *Ap = smtc + buf * kBuf;                // NPL planes of kHankel cores of 128 B
+        unsigned char *Bp = Ap + NPL * kHankelBytes;          // NPL planes of 4 slabs x kSlabB
+        if (ch >= kNBuf) {
+            // The MMAs that last read this buffer (chunk ch - kNBuf) must be done; one warp waits.
+            if (warp == 0 && !tc_wait(mbar + buf, waits[buf] & 1u) && lane == 0) *s_ok = 0;
+            waits[buf]++;
             asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();           // the previous chunk's MMAs have completed (waited below)
+            __syncthreads();
+            if (!*s_ok) break;
         }
-        // A: Toeplitz rows i0..i0+127, sites n0..n0+63; a task is one row and 8 sites.
-        for (int q = tid; q < kTcM * (kTcK / 8); q += blockDim.x) {
-            const int r = q % kTcM, kc = q / kTcM;
-            const int i = i0 + r;
+        // A: the chunk's K order is reversed (position k <-> site n0 + kTcK - 1 - k), which
+        // makes A(r, k) = g(base + r + k) a Hankel matrix: core matrix (row group rg, K group
+        // kg) depends on rg + kg only, so the kHankel distinct cores are stored once and the
+        // descriptors step 128 B in both directions.
+        for (int q = tid; q < kHankel * 8; q += blockDim.x) {
+            const int D = q >> 3, rr = q & 7;
+            const int t0 = i0 - n0 - kTcK + 1 + 8 * D + rr;
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int n = n0 + kc * 8 + u;
-                v[u] = (i < N && n < N) ? gx[i - n + N - 1] : 0.f;
+                const int t = t0 + u;
+                v[u] = (t > -N && t < N) ? gx[t + N - 1] : 0.f;
             }
-            split_store8(Ahi, Alo, (uint32_t)(kc >> 1) * kSlabA + canon(r, (kc & 1) * 8), v);
+            tc::stage8_planes<NPL>(Ap, kHankelBytes, (uint32_t)(D * 128 + rr * 16), v);
         }
         if (GEN && gstage) {
             // Generated operand: the vertex rows D0_n[a][:] and the tap rows g_{n-k} the tile needs
             // are staged in shared memory (coalesced), 32 sites at a time.
             for (int h = 0; h < kTcK; h += 32) {
                 __syncthreads();
-                for (int q = tid; q < 32 * d; q += blockDim.x) {
-                    const int nn = q / d, cc = q % d, n = n0 + h + nn;
-                    Dms[q] = n < N ? gDm[bl * dm_ss + ((long long)n * d + a) * d + cc] : 0.f;
+                for (int nn = warp; nn < 32; nn += 8) {
+                    const int n = n0 + h + nn;
+                    for (int cc = lane; cc < d; cc += 32)
+                        Dms[nn * d + cc] = n < N ? gDm[bl * dm_ss + ((long long)n * d + a) * d + cc] : 0.f;
                 }
                 const int rmin = n0 + h - (kfirst + nk - 1), nrow = 32 + nk - 1;
-                for (int q = tid; q < nrow * d; q += blockDim.x) {
-                    const int rr = q / d, cc = q % d, r = rmin + rr;
-                    Tps[q] = (r > -N && r < N) ? gtaps[(long long)tap_row_tc(r, N, g.periodic) * d + cc] : 0.f;
+                for (int rr = warp; rr < nrow; rr += 8) {
+                    const int r = rmin + rr;
+                    const bool rok = r > -N && r < N;
+                    const float *src = gtaps + (long long)(rok ? tap_row_tc(r, N, g.periodic) : 0) * d;
+                    for (int cc = lane; cc < d; cc += 32) Tps[rr * d + cc] = rok ? src[cc] : 0.f;
                 }
                 __syncthreads();
 #pragma unroll
@@ -173,11 +196,11 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
                     float v[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const int nn = kc * 8 + u, n = n0 + h + nn;
+                        const int nn = kc * 8 + 7 - u, n = n0 + h + nn;
                         v[u] = (pok && n < N) ? Dms[nn * d + cq] * Tps[(n - kq - rmin) * d + cq] : 0.f;
                     }
-                    const int kk = h + kc * 8;
-                    split_store8(Bhi, Blo, (uint32_t)(kk >> 4) * kSlabB + canon(pp, kk & 15), v);
+                    const int kk = kTcK - 8 - h - kc * 8;
+                    tc::stage8_planes<NPL>(Bp, 4 * kSlabB, (uint32_t)(kk >> 4) * kSlabB + canon(pp, kk & 15), v);
                 }
             }
         } else {
@@ -196,8 +219,11 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
             }
 #pragma unroll
             for (int kc = 0; kc < KS / 8; ++kc) {
-                const int kk = part * KS + kc * 8;
-                split_store8(Bhi, Blo, (uint32_t)(kk >> 4) * kSlabB + canon(pp, kk & 15), v + 8 * kc);
+                float w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) w[u] = v[8 * kc + 7 - u];
+                const int kk = kTcK - 8 - part * KS - kc * 8;
+                tc::stage8_planes<NPL>(Bp, 4 * kSlabB, (uint32_t)(kk >> 4) * kSlabB + canon(pp, kk & 15), w);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -205,32 +231,38 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (tid == 0) {
             for (int s = 0; s < kTcK / 16; ++s) {
-                const uint64_t ah = umma_desc(sm_u32(Ahi + s * kSlabA)), al = umma_desc(sm_u32(Alo + s * kSlabA));
-                const uint64_t bh = umma_desc(sm_u32(Bhi + s * kSlabB)), blo = umma_desc(sm_u32(Blo + s * kSlabB));
-                const uint32_t first = (ch == 0 && s == 0) ? 0u : 1u;
-                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             ::"r"(tmem), "l"(ah), "l"(bh), "r"(idesc), "r"(first));
-                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             ::"r"(tmem), "l"(ah), "l"(blo), "r"(idesc), "r"(1u));
-                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             ::"r"(tmem), "l"(al), "l"(bh), "r"(idesc), "r"(1u));
+#pragma unroll
+                for (int pa = 0; pa < NPL; ++pa)
+#pragma unroll
+                    for (int pb = 0; pa + pb < NPL; ++pb) {
+                        const uint64_t ad = umma_desc_hankel(sm_u32(Ap + pa * kHankelBytes + 2 * s * 128));
+                        const uint64_t bd = umma_desc(sm_u32(Bp + pb * 4 * kSlabB + s * kSlabB));
+                        tc::mma_bf16(tmem, ad, bd, idesc, (ch == 0 && s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+                    }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sm_u32(mbar)));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sm_u32(mbar + buf)));
         }
-        if (!tc_wait(mbar, phase)) ok = false;
-        phase ^= 1u;
     }
+    // The last commit covers every MMA issued before it.
+    if (*s_ok && nchunks > 0) {
+        const int lb = (nchunks - 1) % kNBuf;
+        if (warp == 0 && !tc_wait(mbar + lb, waits[lb] & 1u) && lane == 0) *s_ok = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    const bool ok = *s_ok != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     if (!ok) {
         if (tid == 0) atomicOr(flag, 8u);
     } else {
-        // Epilogue: warp w owns TMEM lanes 32 (w % 4).. (rows) and columns 128 (w / 4)..; each
+        // Epilogue: warp w owns TMEM lanes 32 (w % 4).. (rows) and columns (TN / 2) (w / 4)..; each
         // 32 x 32 piece goes through shared memory (the operand buffers are free now) so that a
         // lane then owns a column and the global stores of a row are contiguous.
         const int quad = warp & 3, half = warp >> 2;
         float *stage = reinterpret_cast<float *>(smtc) + warp * (32 * 33);
         const int prow0 = i0 + quad * 32;
+        const int nrows = N - prow0 < 32 ? N - prow0 : 32;
         for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
             uint32_t r[32];
 #pragma unroll
@@ -246,17 +278,22 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
             for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(r[j]);
             __syncwarp();
             const int p = p0 + half * (kTcN / 2) + c0 + lane;
-            if (p < P) {
-                const int k = p / bns, cc = p - k * bns;
-                for (int rr = 0; rr < 32; ++rr) {
-                    const int i = prow0 + rr;
-                    if (i >= N) break;
-                    const float v = stage[rr * 33 + lane];
-                    if (Y) Y[((bl * d + a) * N + i) * (long long)P + p] = v;
-                    if (band) {
-                        const int dl = ring_delta_tc(i - k, N, g.periodic);
-                        if (dl >= -bR && dl <= bR)
-                            band[(b0 + bl) * bss + (long long)i * brs + (long long)(bR - dl) * bos + (long long)a * bns + cc] = v;
+            if (p < P && nrows > 0) {
+                if (Y) {
+                    float *yp = Y + ((bl * d + a) * N + prow0) * (long long)P + p;
+                    for (int rr = 0; rr < nrows; ++rr, yp += P) *yp = stage[rr * 33 + lane];
+                }
+                if (band) {
+                    // Only the rows within bR of the column's source site hold band entries.
+                    const int k = p / bns, cc = p - k * bns;
+                    float *bp = band + (b0 + bl) * bss + (long long)a * bns + cc;
+                    for (int dl = -bR; dl <= bR; ++dl) {
+                        int i = k + dl;
+                        if (g.periodic) i = i < 0 ? i + N : (i >= N ? i - N : i);
+                        else if (i < 0 || i >= N) continue;
+                        if (i < prow0 || i >= prow0 + nrows) continue;
+                        if (g.periodic && ring_delta_tc(i - k, N, 1) != dl) continue;
+                        bp[(long long)i * brs + (long long)(bR - dl) * bos] = stage[(i - prow0) * 33 + lane];
                     }
                 }
             }
@@ -268,43 +305,60 @@ __global__ void __launch_bounds__(256) k_tgemm_tc(Geom g, const float *__restric
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
 }
 
-template <int TN>
+template <int TN, int NPL>
 static size_t tgemm_tc_smem(int N, int d, bool gen) {
     const int nk = (TN + d - 1) / d + 1;
     const size_t stage = gen ? (size_t)32 * d + ((size_t)(32 + nk - 1) * d + 1) / 2 * 2 : 0;
-    return (size_t)8 * kSlabA + (size_t)8 * TN * 32 + ((size_t)((2 * N + 1) & ~1) + stage) * sizeof(float) + 16;
+    const size_t ops = (size_t)kNBuf * NPL * (kHankelBytes + 4 * TN * 32);
+    const size_t front = ops > (size_t)kEpiBytes ? ops : (size_t)kEpiBytes;
+    return front + ((size_t)((2 * N + 1) & ~1) + stage) * sizeof(float) + 32;
 }
 
-template <int TN>
+template <int TN, int NPL>
 static cudaError_t launch_tgemm_tc_tn(const Geom &g, const float *taps, int P, const float *X, const float *gtaps,
                                       const float *gDm, long long dm_ss, float *Y, float *band, long long bss,
                                       long long brs, long long bos, int bR, int bns, long long b0, int nb,
                                       unsigned *flag, cudaStream_t st) {
-    const size_t smem = tgemm_tc_smem<TN>(g.N, g.d, gtaps != nullptr);
+    const size_t smem = tgemm_tc_smem<TN, NPL>(g.N, g.d, gtaps != nullptr);
     if (smem > 220 * 1024) return cudaErrorNotSupported;
     dim3 grid((P + TN - 1) / TN, (g.N + kTcM - 1) / kTcM, (unsigned)nb * g.d);
     cudaError_t err;
     if (gtaps) {
-        err = cudaFuncSetAttribute(k_tgemm_tc<true, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(k_tgemm_tc<true, TN, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         ProfScope _ps("k_tgemm_tc", st);
-        k_tgemm_tc<true, TN><<<grid, 256, smem, st>>>(g, taps, P, nullptr, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR,
-                                                      bns, b0, flag);
+        k_tgemm_tc<true, TN, NPL><<<grid, 256, smem, st>>>(g, taps, P, nullptr, gtaps, gDm, dm_ss, Y, band, bss, brs,
+                                                             bos, bR, bns, b0, flag);
     } else {
-        err = cudaFuncSetAttribute(k_tgemm_tc<false, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = cudaFuncSetAttribute(k_tgemm_tc<false, TN, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         ProfScope _ps("k_tgemm_tc", st);
-        k_tgemm_tc<false, TN><<<grid, 256, smem, st>>>(g, taps, P, X, nullptr, nullptr, 0, Y, band, bss, brs, bos, bR,
-                                                       bns, b0, flag);
+        k_tgemm_tc<false, TN, NPL><<<grid, 256, smem, st>>>(g, taps, P, X, nullptr, nullptr, 0, Y, band, bss, brs,
+                                                              bos, bR, bns, b0, flag);
     }
     return cudaGetLastError();
 }
 
-// 128-column tiles (3 CTAs per SM: 64 KB of operands, 128 TMEM columns each).
+// 128-column tiles, 128 TMEM columns per CTA, 3 CTAs per SM.  planes = BF16 terms per
+// operand value: 1 (plain BF16), 2 (3 products, about 2^-18 relative), 3 (6 products,
+// FP32-grade).
 cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float *X, const float *gtaps,
                             const float *gDm, long long dm_ss, float *Y, float *band, long long bss, long long brs,
-                            long long bos, int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st) {
-    return launch_tgemm_tc_tn<128>(g, taps, P, X, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
+                            long long bos, int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st,
+                            int planes) {
+    switch (planes) {
+    case 1:
+        return launch_tgemm_tc_tn<128, 1>(g, taps, P, X, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb,
+                                          flag, st);
+    case 2:
+        return launch_tgemm_tc_tn<128, 2>(g, taps, P, X, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb,
+                                          flag, st);
+    case 3:
+        return launch_tgemm_tc_tn<128, 3>(g, taps, P, X, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb,
+                                          flag, st);
+    default:
+        return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace dn

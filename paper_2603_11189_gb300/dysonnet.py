@@ -17,8 +17,9 @@ import torch
 from . import build as _build
 
 DN_OK, DN_EINVAL, DN_ENOMEM, DN_ECUDA, DN_ETIMEOUT, DN_EUNSUPPORTED = range(6)
-DN_FP64, DN_FP32 = 0, 1
-PRECISIONS = {"fp64": DN_FP64, "fp32": DN_FP32, torch.float64: DN_FP64, torch.float32: DN_FP32}
+DN_FP64, DN_FP32, DN_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": DN_FP64, "fp32": DN_FP32, "bf16": DN_BF16,
+              torch.float64: DN_FP64, torch.float32: DN_FP32, torch.bfloat16: DN_BF16}
 
 
 class DysonNetError(RuntimeError):

@@ -91,6 +91,7 @@ def test_c2_model_small_batch(dn, prec):
     (4, 32, 8, 2, 32, 2, 1, 77, 2, 1),     # ring, ragged run of sites
     (3, 32, 8, 1, 16, 1, 0, 50, 2, 2),     # W = 3, d_out = 1, wider link rows
     (6, 32, 8, 2, 32, 2, 0, 40, 2, 1),     # deepest layers fall back to the generic kernel
+    (4, 64, 8, 2, 32, 2, 0, 40, 2, 1),     # d = 64: generic kernel, two channels per lane
 ])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_all_single_flips_grouped(dn, case, prec):
