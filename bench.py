@@ -163,6 +163,30 @@ def link_conv_flops(N, L, d, B):
     return total
 
 
+def dhop_bytes(N, L, d, B):
+    """HBM bytes of the vertex hops of one step: every hop reads the probe field of
+    one layer and writes it back mixed (d N P values each way; P = N probes for the
+    embedding chain, N d for a source chain from layer m, which makes L - 2 - m hops)."""
+    per = (L - 2) * 2 * d * N * N * 4
+    per += sum((L - 2 - m) * 2 * d * N * (N * d) * 4 for m in range(1, L - 1))
+    return B * per
+
+
+def bandconv_bytes(N, L, d, w, B, WF=None):
+    """HBM bytes of the last-layer band convolutions of one step: the probe field
+    read once (the embedding chain and every source chain with a full hop; the
+    chain from layer L-2 generates its operand from D0 and the taps) plus the
+    band entries written."""
+    W = 2 * w + 1
+    WF = W if WF is None else WF
+    Rk, Rl = WF - 1, WF - 1 - w
+    per = d * N * N * 4 + N * (2 * Rl + 1) * d * 4
+    for m in range(1, L - 1):
+        src = d * N * (N * d) * 4 if m < L - 2 else N * d * d * 4
+        per += src + N * (2 * Rk + 1) * d * d * 4
+    return B * per
+
+
 def abacus_unique_bytes(N, L, d, dout, w, P, B, tb=4):
     """Algorithmic bytes of one ABACUS launch over all single flips of B samples:
     every cache value the flips read, counted once (per-sample caches are
@@ -197,6 +221,7 @@ def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128):
     ev1.record()
     barrier()
     build_ms = ev0.elapsed_time(ev1)
+    torch.cuda.empty_cache()          # hand the link-construction scratch back to the driver
     out = cache.single_flip_ratios()
     barrier()
     reps = 3
@@ -245,7 +270,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recompute", action="store_true")
     ap.add_argument("--no-n1024", action="store_true")
-    ap.add_argument("--n1024-chains", type=int, default=2)
+    ap.add_argument("--n1024-chains", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -410,10 +435,11 @@ def read_profile(lib):
 
 
 def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
-    """Rooflines of the two kernel families that carry the step:
-    the ABACUS layer kernels (HBM-bound: algorithmic bytes = every cache value
-    the flips need, once per configuration) and the Toeplitz GEMM of the link
-    build (FP32-FMA bound: 2 N^2 d flops per source column per full hop)."""
+    """Rooflines of the kernel families that carry the step: the ABACUS layer
+    kernels (HBM-bound: algorithmic bytes = every cache value the flips need, once
+    per configuration), the Toeplitz GEMM of the link build (2 N^2 d flops per
+    source column per full hop) and its vertex hops and band convolutions
+    (HBM-bound: probe fields read and written once)."""
     out = {}
     P = (desc.L - 1) * (desc.L - 2) // 2
     ab = [(k, v) for k, v in prof.items() if k.endswith("/k_ab_layer")]
@@ -438,6 +464,18 @@ def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
                               "frac": ach / peak, "traffic": None, "launches": launches,
                               "ms_per_launch": tot_s * 1e3 / launches,
                               "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"}
+    for fam_name, kname, byts in (("links_dhop", "k_dhop", dhop_bytes(N, desc.L, desc.d, Bs)),
+                                  ("links_bandconv", "k_bandconv", bandconv_bytes(N, desc.L, desc.d, desc.w, Bs))):
+        ks = [(k, v) for k, v in prof.items() if k.endswith("links/" + kname)]
+        if ks:
+            launches = sum(v[0] for _, v in ks)
+            tot_s = sum(v[1] for _, v in ks) / 1e3
+            ach = byts * steps / tot_s / 1e9
+            peak = peaks["hbm_gbs"]
+            out[fam_name] = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                             "frac": ach / peak, "traffic": None, "launches": launches,
+                             "ms_per_launch": tot_s * 1e3 / launches,
+                             "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"}
     tc = [(k, v) for k, v in prof.items() if k.endswith("links/k_tgemm_tc")]
     if tc:
         launches = sum(v[0] for _, v in tc)
@@ -467,6 +505,10 @@ def roofline(prof, steps, desc, N, Bs, peaks, src, clocks):
         return fam["abacus"], fam
     if name.endswith("links/k_tgemm") and "links_tgemm" in fam:
         return fam["links_tgemm"], fam
+    if name.endswith("links/k_dhop") and "links_dhop" in fam:
+        return fam["links_dhop"], fam
+    if name.endswith("links/k_bandconv") and "links_bandconv" in fam:
+        return fam["links_bandconv"], fam
     if name.endswith("links/k_tgemm_tc") and "links_tgemm_tc" in fam:
         return fam["links_tgemm_tc"], fam
     return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,

@@ -969,6 +969,311 @@ __global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(Ab
     }
 }
 
+// Cooperative streaming fast path of k_ab_layer for FP32 with d = 64 (the kernel is
+// written for d in {32, 64}): the 8 warps of a CTA work on the same site of a run of
+// consecutive sites.
+//  * Link blocks K^(l,m)_{i,i+dl} are cut into 4 KB chunks of 1024 / d rows; warp w
+//    owns row chunk j = w mod (d^2/1024) of every block whose index is congruent to
+//    w div (d^2/1024) modulo 8 / (d^2/1024), and streams its chunks through its own
+//    ring of NS shared-memory slots (cp.async.bulk, mbarrier completion).  The ring
+//    runs ahead across sites, so the copies of the next sites are in flight while the
+//    CTA finishes the current one.
+//  * A lane owns one row of a chunk and 32 of its d columns; slot q of block dl
+//    multiplies the state of flip q at slice position q + dl (the zero row where that
+//    position or flip does not exist).  Partial sums go through shared memory and are
+//    reduced per (slot, channel).
+//  * The states s^(m) of the W flips around the site live in a window of W+1 flip
+//    slots per m shared by the CTA (one bulk copy per m and site, issued a site early).
+//  * The per-site epilogue (slice Toeplitz and embedding terms, V and U matvecs,
+//    outputs, dOmega partials) is spread over the 256 threads.
+// Every wait is bounded; a timeout raises bit 4 of the cache flag and the CTA lets its
+// copies land before it ends.
+constexpr int kCoWarps = 8;
+
+template <int D, int WW, int NS>
+__global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbArgs<float> a, int l, int R,
+                                                                            float *__restrict__ S,
+                                                                            const float *__restrict__ DX,
+                                                                            double *__restrict__ PART) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int d = D, dd = D * D, W = WW, wd = (WW - 1) / 2, W1 = W + 1;
+    constexpr int RC = 1024 / D;          // rows per 4 KB chunk
+    constexpr int CPB = dd / 1024;        // chunks per block
+    constexpr int WPJ = kCoWarps / CPB;   // warps per chunk row class
+    constexpr int nper = 4 * wd + 1;
+    const Geom &g = a.g;
+    const int N = g.N, L = g.L, dout = g.dout;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nwin = l - 1, nlink = l > 2 ? l - 2 : 0;
+    float *VTs = reinterpret_cast<float *>(smraw);   // [c'][c] = V[c][c']
+    float *UTs = VTs + dd;
+    float *Gs = UTs + dd;                            // [4w+1][d] taps g^(l)_{-2w..2w}
+    float *Zs = Gs + nper * d;                       // [d] zeros
+    float *Win = Zs + d;                             // [nwin][W+1][W][d]
+    float *Pb = Win + nwin * W1 * W * d;             // [8][W][32] partial sums
+    float *pq = Pb + kCoWarps * W * 32;              // [W][d]
+    float *gq = pq + W * d;                          // [W][d]
+    float *Kring = gq + W * d;                       // [8][NS][1024]
+    uint64_t *mbw = reinterpret_cast<uint64_t *>(Kring + kCoWarps * NS * 1024);   // [8][NS] ring, then 2 window
+    uint64_t *wmb = mbw + kCoWarps * NS;
+    int8_t *sps = reinterpret_cast<int8_t *>(wmb + 2);
+    const long long lo = l - 1;
+    const long long b = blockIdx.y;
+    for (int q = tid; q < dd; q += blockDim.x) {
+        VTs[q] = a.w.VT[lo * dd + q];
+        UTs[q] = a.w.UT[lo * dd + q];
+    }
+    for (int q = tid; q < nper * d; q += blockDim.x) {
+        const int r = q / d - 2 * wd, cc = q % d;
+        const int row = g.periodic ? ((r % N) + N) % N : (r > -N && r < N ? r + N - 1 : -1);
+        Gs[q] = row >= 0 ? a.taps[(lo * g.R + row) * d + cc] : 0.f;
+    }
+    for (int q = tid; q < d; q += blockDim.x) Zs[q] = 0.f;
+    for (int q = tid; q < N; q += blockDim.x) sps[q] = a.spins[b * N + q];
+    if (tid == 0) {
+        for (int s = 0; s < kCoWarps * NS + 2; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbw + s)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    const int i0 = blockIdx.x * R;
+    const int nsite = N - i0 < R ? N - i0 : R;
+    if (nsite <= 0) return;
+    const long long rows = (long long)a.B * N * W;
+    const long long nRk = 2 * a.Rk + 1, nRl = 2 * a.Rl + 1;
+    auto wrap = [&](int x) -> int { return g.periodic ? floor_mod(x, N) : x; };
+    auto site_ok = [&](int k) -> bool { return g.periodic || (k >= 0 && k < N); };
+    // ---- window of flip states (thread 0 issues) ----
+    auto flip_bytes = [&](int jj) -> uint32_t { return site_ok(jj) ? (uint32_t)(nwin * W * d * sizeof(float)) : 0u; };
+    auto issue_flip = [&](int jj, uint64_t *bar) {
+        if (!site_ok(jj)) return;
+        const int j = wrap(jj), slot = floor_mod(jj, W1);
+        for (int m = 1; m <= nwin; ++m)
+            bulk_copy(Win + ((m - 1) * W1 + slot) * W * d, S + ((m - 1) * rows + (b * N + j) * W) * d,
+                      (uint32_t)(W * d * sizeof(float)), bar);
+    };
+    uint32_t wpend[2] = {0u, 0u}, wuse[2] = {0u, 0u};
+    if (nwin > 0) {
+        uint32_t bytes = 0;
+        for (int jj = i0 - wd; jj <= i0 + wd; ++jj) bytes += flip_bytes(jj);
+        if (tid == 0 && bytes) {
+            mbar_expect(wmb, bytes);
+            for (int jj = i0 - wd; jj <= i0 + wd; ++jj) issue_flip(jj, wmb);
+        }
+        wpend[0] = bytes ? 1u : 0u;
+    }
+    // ---- this warp's chunk stream ----
+    const int jrow = warp % CPB, bcls = warp / CPB;
+    const int nb_site = nlink * nper;
+    int my_per_site = 0;
+    for (int bb = bcls; bb < nb_site; bb += WPJ) ++my_per_site;
+    const int nchunk = nsite * my_per_site;
+    uint64_t *mb = mbw + warp * NS;
+    float *ring = Kring + warp * NS * 1024;
+    int iss_r = 0, iss_b = bcls, issued = 0, consumed = 0, iss_slot = 0, con_slot = 0;
+    uint32_t con_phase = 0;
+    auto iss_src = [&]() -> const float * {
+        const int m = iss_b / nper + 1, dl = iss_b % nper - 2 * wd;
+        return a.K + (((b * a.P + pair_index(l, m)) * N + (i0 + iss_r)) * nRk + (dl + a.Rk)) * (long long)dd +
+               jrow * 1024;
+    };
+    auto iss_advance = [&]() {
+        iss_b += WPJ;
+        if (iss_b >= nb_site) {
+            iss_b = bcls;
+            ++iss_r;
+        }
+    };
+    if (NS > 0 && nchunk > 0) {
+        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (; issued < nchunk && issued < NS; ++issued) {
+            if (lane == 0) bulk_load(ring + iss_slot * 1024, iss_src(), 4096u, mb + iss_slot);
+            iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
+            iss_advance();
+        }
+    }
+    __shared__ int s_fail;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    const int lrow = lane % RC, seg = lane / RC;      // chunk row, 32-column segment
+    bool failed = false;
+    for (int r = 0; r < nsite; ++r) {
+        const int i = i0 + r;
+        int jq[W], wsl[W];
+        unsigned valid = 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int jj = i + wd - q;
+            const bool ok = site_ok(jj);
+            jq[q] = ok ? wrap(jj) : 0;
+            wsl[q] = floor_mod(jj, W1);
+            if (ok) valid |= 1u << q;
+        }
+        // Window of this site; then the next site's new flip into the slot released by the last one.
+        if (nwin > 0) {
+            const int pb = r & 1;
+            if (wpend[pb]) {
+                if (tid == 0 && !mbar_wait(wmb + pb, wuse[pb] & 1u)) s_fail = 1;
+                wuse[pb]++;
+                wpend[pb] = 0;
+            }
+            __syncthreads();
+            if (s_fail) {
+                failed = true;
+                break;
+            }
+            if (r + 1 < nsite) {
+                const int jn = i + 1 + wd;
+                const uint32_t bytes = flip_bytes(jn);
+                if (tid == 0 && bytes) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect(wmb + (pb ^ 1), bytes);
+                    issue_flip(jn, wmb + (pb ^ 1));
+                }
+                wpend[pb ^ 1] = bytes ? 1u : 0u;
+            }
+        }
+        // Link chunks of this warp for site r.
+        float acc[W], acc2[W];
+#pragma unroll
+        for (int q = 0; q < W; ++q) acc[q] = acc2[q] = 0.f;
+        for (int bb = bcls; bb < nb_site && !failed; bb += WPJ) {
+            if (!mbar_wait(mb + con_slot, con_phase)) {
+                failed = true;
+                break;
+            }
+            const int slot = con_slot;
+            ++consumed;
+            if (++con_slot == NS) {
+                con_slot = 0;
+                con_phase ^= 1u;
+            }
+            const int mi = bb / nper, dl = bb % nper - 2 * wd;
+            if (site_ok(i + dl)) {
+                const float *wm = Win + (size_t)mi * W1 * W * d + seg * 32;
+                const float *Kc = ring + slot * 1024 + lrow * d + seg * 32;
+                const float *sp[W];
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    const int t2 = q + dl;
+                    sp[q] = (t2 >= 0 && t2 < W && ((valid >> q) & 1u)) ? wm + (wsl[q] * W + t2) * d : Zs;
+                }
+#pragma unroll
+                for (int s2 = 0; s2 < 8; s2 += 2) {
+                    const int ch0 = (s2 + lane) & 7, ch1 = (s2 + 1 + lane) & 7;
+                    const float4 k0 = *reinterpret_cast<const float4 *>(Kc + 4 * ch0);
+                    const float4 k1 = *reinterpret_cast<const float4 *>(Kc + 4 * ch1);
+#pragma unroll
+                    for (int q = 0; q < W; ++q) {
+                        const float4 s0 = *reinterpret_cast<const float4 *>(sp[q] + 4 * ch0);
+                        const float4 s1 = *reinterpret_cast<const float4 *>(sp[q] + 4 * ch1);
+                        acc[q] = fmaf(k0.x, s0.x, acc[q]);
+                        acc2[q] = fmaf(k1.x, s1.x, acc2[q]);
+                        acc[q] = fmaf(k0.y, s0.y, acc[q]);
+                        acc2[q] = fmaf(k1.y, s1.y, acc2[q]);
+                        acc[q] = fmaf(k0.z, s0.z, acc[q]);
+                        acc2[q] = fmaf(k1.z, s1.z, acc2[q]);
+                        acc[q] = fmaf(k0.w, s0.w, acc[q]);
+                        acc2[q] = fmaf(k1.w, s1.w, acc2[q]);
+                    }
+                }
+            }
+            __syncwarp();
+            if (issued < nchunk) {
+                if (lane == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bulk_load(ring + iss_slot * 1024, iss_src(), 4096u, mb + iss_slot);
+                }
+                ++issued;
+                iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
+                iss_advance();
+            }
+        }
+        if (failed) s_fail = 1;
+#pragma unroll
+        for (int q = 0; q < W; ++q) Pb[(warp * W + q) * 32 + lane] = acc[q] + acc2[q];
+        __syncthreads();
+        if (s_fail) {
+            failed = true;
+            break;
+        }
+        // Reduce the partials per (q, c), add the slice Toeplitz and embedding terms.
+        for (int it = tid; it < W * d; it += blockDim.x) {
+            const int q = it / d, c = it % d;
+            float v = 0.f;
+            if (nlink > 0) {
+                const int jj = c / RC, rr = c % RC;
+#pragma unroll
+                for (int bc = 0; bc < WPJ; ++bc)
+#pragma unroll
+                    for (int sg = 0; sg < 32 / RC; ++sg) v += Pb[((jj + bc * CPB) * W + q) * 32 + sg * RC + rr];
+            }
+            if ((valid >> q) & 1u) {
+                const float dsq = (float)(-2 * sps[jq[q]]);
+                if (l == 1) {
+                    v += Gs[(q - wd + 2 * wd) * d + c] * a.w.e[c] * dsq;
+                } else {
+                    v += dsq * a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
+                    const float *ws = Win + ((size_t)(l - 2) * W1 + wsl[q]) * W * d;
+                    for (int t2 = 0; t2 < W; ++t2)
+                        if (site_ok(jq[q] - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * ws[t2 * d + c];
+                }
+            }
+            pq[it] = v;
+        }
+        __syncthreads();
+        // z = y + V p, then the gate with dchi.
+        for (int it = tid; it < W * d; it += blockDim.x) {
+            const int q = it / d, c = it % d;
+            float z = a.y[((b * L + lo) * N + i) * d + c];
+            const float *pr = pq + q * d;
+#pragma unroll 8
+            for (int c2 = 0; c2 < d; ++c2) z = fmaf(VTs[c2 * d + c], pr[c2], z);
+            const float dx = ((valid >> q) & 1u) ? DX[(lo * rows + (b * N + jq[q]) * W + q) * d + c] : 0.f;
+            gq[it] = dx * z;
+        }
+        __syncthreads();
+        // s^(l) = U g; written to S (next layers) and kept in pq for the dOmega partials.
+        for (int it = tid; it < W * d; it += blockDim.x) {
+            const int q = it / d, c = it % d;
+            float s = 0.f;
+            const float *gr = gq + q * d;
+#pragma unroll 8
+            for (int c2 = 0; c2 < d; ++c2) s = fmaf(UTs[c2 * d + c], gr[c2], s);
+            pq[it] = s;
+            if (l < L && ((valid >> q) & 1u)) S[(lo * rows + (b * N + jq[q]) * W + q) * d + c] = s;
+        }
+        __syncthreads();
+        // dOmega_k partial of (flip q, layer l): rho^(l)_k(i) . s, in FP64; one warp per (q, k).
+        for (int pk = warp; pk < W * dout; pk += kCoWarps) {
+            const int q = pk / dout, k = pk % dout;
+            if (!((valid >> q) & 1u)) continue;
+            const float *rho = a.rho + ((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d;
+            double v = 0.0;
+            for (int c = lane; c < d; c += 32) v += (double)rho[c] * (double)pq[q * d + c];
+            v = warp_sum<double>(v);
+            if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] += v;
+        }
+        __syncthreads();
+    }
+    if (failed) {
+        if (tid == 0) atomicOr(a.flag, 4u);
+        // Let the copies in flight land before the shared memory is released.
+        while (consumed < issued) {
+            mbar_wait(mb + con_slot, con_phase);
+            ++consumed;
+            if (++con_slot == NS) {
+                con_slot = 0;
+                con_phase ^= 1u;
+            }
+        }
+        if (tid == 0)
+            for (int pb = 0; pb < 2; ++pb)
+                if (wpend[pb]) mbar_wait(wmb + pb, wuse[pb] & 1u);
+        __syncthreads();
+    }
+}
+
 __global__ void k_ab_final(Geom g, int B, int f_kind, const int8_t *__restrict__ spins, const double *__restrict__ Omega,
                            const double *__restrict__ PART, const void *__restrict__ tlink, int tsize,
                            double *__restrict__ out) {
@@ -1088,6 +1393,62 @@ static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, con
     return cudaGetLastError();
 }
 
+// Shared memory of k_ab_coop with NS ring slots per warp; 0 if it does not fit.
+static size_t ab_coop_smem(const Geom &g, int l, int NS) {
+    const size_t d = g.d, W = g.W, nwin = l - 1, nper = 4 * g.w + 1;
+    const size_t floats = 2 * d * d + nper * d + d + nwin * (W + 1) * W * d + (size_t)kCoWarps * W * 32 + 2 * W * d +
+                          (size_t)kCoWarps * NS * 1024;
+    const size_t bytes = floats * sizeof(float) + ((size_t)kCoWarps * NS + 2) * sizeof(uint64_t) +
+                         (((size_t)g.N + 15) & ~(size_t)15);
+    return bytes <= 226 * 1024 ? bytes : 0;   // the kernel adds a few bytes of static shared memory
+}
+
+template <int D, int WW, int NS>
+static cudaError_t launch_ab_coop_one(const AbArgs<float> &a, int l, int R, dim3 grid, size_t smem, float *S,
+                                      const float *DX, double *PART, cudaStream_t st) {
+    cudaError_t err = cudaFuncSetAttribute(k_ab_coop<D, WW, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_ab_layer", st);
+        k_ab_coop<D, WW, NS><<<grid, 32 * kCoWarps, smem, st>>>(a, l, R, S, DX, PART);
+    }
+    return cudaGetLastError();
+}
+
+template <int D, int WW>
+static cudaError_t launch_ab_coop_ns(const AbArgs<float> &a, int l, int R, int NS, dim3 grid, size_t smem, float *S,
+                                     const float *DX, double *PART, cudaStream_t st) {
+    switch (NS) {
+    case 0: return launch_ab_coop_one<D, WW, 0>(a, l, R, grid, smem, S, DX, PART, st);
+    case 2: return launch_ab_coop_one<D, WW, 2>(a, l, R, grid, smem, S, DX, PART, st);
+    case 4: return launch_ab_coop_one<D, WW, 4>(a, l, R, grid, smem, S, DX, PART, st);
+    case 6: return launch_ab_coop_one<D, WW, 6>(a, l, R, grid, smem, S, DX, PART, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+static cudaError_t launch_ab_coop(const AbArgs<float> &a, int l, float *S, const float *DX, double *PART,
+                                  cudaStream_t st) {
+    const Geom &g = a.g;
+    int NS = 0;
+    size_t smem = ab_coop_smem(g, l, 0);
+    if (l > 2) {
+        for (NS = 6; NS >= 2; NS -= 2)
+            if ((smem = ab_coop_smem(g, l, NS)) != 0) break;
+        if (NS < 2) return cudaErrorNotSupported;
+    }
+    if (smem == 0) return cudaErrorNotSupported;
+    // Runs of R sites per CTA: long runs amortise the ring and window fill, but at least
+    // two CTAs per SM's worth of runs.
+    long long R = (long long)g.N * a.B / (2 * 152);
+    R = R < 4 ? 4 : (R > 16 ? 16 : R);
+    dim3 grid((unsigned)((g.N + R - 1) / R), (unsigned)a.B);
+    const int Ri = (int)R;
+    if (g.d == 64 && g.W == 5) return launch_ab_coop_ns<64, 5>(a, l, Ri, NS, grid, smem, S, DX, PART, st);
+    if (g.d == 64 && g.W == 3) return launch_ab_coop_ns<64, 3>(a, l, Ri, NS, grid, smem, S, DX, PART, st);
+    return cudaErrorNotSupported;
+}
+
 template <typename T>
 cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
                                   void *scratch, double *out, cudaStream_t st) {
@@ -1115,11 +1476,19 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     // The streaming kernel takes FP32 caches with d = 32, W in {3, 5} and d_out <= 2; a
     // layer whose shared memory would not fit falls back to k_ab_layer.
     const bool stream_ok = sizeof(T) == 4 && g.d == 32 && (g.W == 3 || g.W == 5) && g.dout <= kStMaxDout;
+    // d = 64 takes the cooperative kernel; at d = 32 a site's link rows (72 KB at L = 4) are too
+    // little work to amortise its CTA-wide steps and the per-warp kernel is faster (measured).
+    const bool coop_ok = sizeof(T) == 4 && g.d == 64 && (g.W == 3 || g.W == 5);
     for (int l = 1; l <= g.L; ++l) {
         err = cudaErrorNotSupported;
-        if (stream_ok)
+        if (coop_ok)
+            err = launch_ab_coop(reinterpret_cast<const AbArgs<float> &>(a), l, reinterpret_cast<float *>(S),
+                                 reinterpret_cast<const float *>(DX), PART, st);
+        if (err == cudaErrorNotSupported && stream_ok) {
+            cudaGetLastError();
             err = launch_ab_stream(reinterpret_cast<const AbArgs<float> &>(a), l, reinterpret_cast<float *>(S),
                                    reinterpret_cast<const float *>(DX), PART, st);
+        }
         if (err == cudaSuccess) continue;
         if (err != cudaErrorNotSupported) return err;
         cudaGetLastError();

@@ -386,10 +386,10 @@ __global__ void __launch_bounds__(256) k_bandconv(Geom g, const T *__restrict__ 
 // so they share the taps): one 16-byte load of X per site, taps from a shared table
 // already wrapped for rings (no index arithmetic in the loop), one 16-byte store per
 // band entry.  Requires nsrc % 4 == 0 and P % 4 == 0.
-template <int NB>
+template <bool GEN, int NB>
 __global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restrict__ taps, int P,
-                                                   const float *__restrict__ X, float *__restrict__ band, BandDst bd,
-                                                   long long b0) {
+                                                   const float *__restrict__ X, GenSrc<float> gs,
+                                                   float *__restrict__ band, BandDst bd, long long b0) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d, R = bd.R, ns = bd.nsrc;
     const int pad = kBcMaxBand + 1;
@@ -415,7 +415,9 @@ __global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restri
     const int p = ch * 1024 + 4 * threadIdx.x;
     if (p >= P) return;
     const int k = p / ns, c = p - k * ns;
-    const float *Xa = X + (bl * d + a) * (long long)N * P + p;
+    const float *Xa = GEN ? nullptr : X + (bl * d + a) * (long long)N * P + p;
+    // Generated operand (first hop of a source chain): X[n][(k, c..c+3)] = D0_n[a][c..c+3] g_{n-k, c..c+3}.
+    const float *Dma = GEN ? gs.Dm + bl * gs.dm_ss + (long long)a * d + c : nullptr;
     const float *gk = gx + pad + (k - R) + (N - 1);   // tap of (q, n) at gk[q - n]
     float acc[NB][4];
 #pragma unroll
@@ -424,7 +426,14 @@ __global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restri
         for (int j = 0; j < 4; ++j) acc[q][j] = 0.f;
 #pragma unroll 2
     for (int n = 0; n < N; ++n) {
-        const float4 xv = *reinterpret_cast<const float4 *>(Xa + (long long)n * P);
+        float4 xv;
+        if (GEN) {
+            const float4 dm = *reinterpret_cast<const float4 *>(Dma + (long long)n * d * d);
+            const float4 tp = *reinterpret_cast<const float4 *>(gs.taps + (long long)tap_row(n - k, N, g.periodic) * d + c);
+            xv = make_float4(dm.x * tp.x, dm.y * tp.y, dm.z * tp.z, dm.w * tp.w);
+        } else {
+            xv = *reinterpret_cast<const float4 *>(Xa + (long long)n * P);
+        }
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
             if (q > 2 * R) break;
@@ -532,35 +541,51 @@ static cudaError_t launch_bandconv_gen(const Geom &g, const T *taps, int P, cons
     return cudaErrorInvalidConfiguration;
 }
 
-template <int NB>
-static cudaError_t launch_bandconv4_nb(const Geom &g, const float *taps, int P, const float *X, float *band,
-                                       const BandDst &bd, long long b0, int nb, cudaStream_t st) {
+template <bool GEN, int NB>
+static cudaError_t launch_bandconv4_nb(const Geom &g, const float *taps, int P, const float *X, const GenSrc<float> &gs,
+                                       float *band, const BandDst &bd, long long b0, int nb, cudaStream_t st) {
     const size_t smem = ((size_t)2 * g.N - 1 + 2 * (kBcMaxBand + 1)) * sizeof(float);
     const int chunks = (P + 1023) / 1024;
     const unsigned blocks = (unsigned)((long long)nb * g.d * chunks);
-    cudaError_t err = cudaFuncSetAttribute(k_bandconv4<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_bandconv4<GEN, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     {
         ProfScope _ps("k_bandconv", st);
-        k_bandconv4<NB><<<blocks, 256, smem, st>>>(g, taps, P, X, band, bd, b0);
+        k_bandconv4<GEN, NB><<<blocks, 256, smem, st>>>(g, taps, P, X, gs, band, bd, b0);
     }
     return cudaGetLastError();
+}
+
+template <bool GEN>
+static cudaError_t launch_bandconv4(const Geom &g, const float *taps, int P, const float *X, const GenSrc<float> &gs,
+                                    float *band, const BandDst &bd, long long b0, int nb, cudaStream_t st) {
+    const int nbw = 2 * bd.R + 1;
+    if (nbw <= 5) return launch_bandconv4_nb<GEN, 5>(g, taps, P, X, gs, band, bd, b0, nb, st);
+    if (nbw <= 9) return launch_bandconv4_nb<GEN, 9>(g, taps, P, X, gs, band, bd, b0, nb, st);
+    if (nbw <= 13) return launch_bandconv4_nb<GEN, 13>(g, taps, P, X, gs, band, bd, b0, nb, st);
+    return cudaErrorNotSupported;
 }
 
 template <typename T>
 static cudaError_t launch_bandconv(const Geom &g, const T *taps, int P, const T *X, const GenSrc<T> *gs, T *band,
                                    const BandDst &bd, long long b0, int nb, cudaStream_t st) {
-    if (gs) return launch_bandconv_gen<T, true>(g, taps, P, nullptr, *gs, band, bd, b0, nb, st);
     if constexpr (sizeof(T) == 4) {
-        if (bd.nsrc % 4 == 0 && P % 4 == 0) {
+        // Four source columns per lane (FP32, channel count a multiple of 4).
+        if (bd.nsrc % 4 == 0 && P % 4 == 0 && g.d % 4 == 0) {
             const float *tf = reinterpret_cast<const float *>(taps), *xf = reinterpret_cast<const float *>(X);
             float *bf = reinterpret_cast<float *>(band);
-            const int nbw = 2 * bd.R + 1;
-            if (nbw <= 5) return launch_bandconv4_nb<5>(g, tf, P, xf, bf, bd, b0, nb, st);
-            if (nbw <= 9) return launch_bandconv4_nb<9>(g, tf, P, xf, bf, bd, b0, nb, st);
-            if (nbw <= 13) return launch_bandconv4_nb<13>(g, tf, P, xf, bf, bd, b0, nb, st);
+            GenSrc<float> gf{nullptr, nullptr, 0};
+            if (gs)
+                gf = GenSrc<float>{reinterpret_cast<const float *>(gs->taps), reinterpret_cast<const float *>(gs->Dm),
+                                   gs->dm_ss};
+            cudaError_t err = gs ? launch_bandconv4<true>(g, tf, P, nullptr, gf, bf, bd, b0, nb, st)
+                                 : launch_bandconv4<false>(g, tf, P, xf, gf, bf, bd, b0, nb, st);
+            if (err != cudaErrorNotSupported) return err;
+            cudaGetLastError();
         }
     }
+    if (gs) return launch_bandconv_gen<T, true>(g, taps, P, nullptr, *gs, band, bd, b0, nb, st);
     return launch_bandconv_gen<T, false>(g, taps, P, X, GenSrc<T>{nullptr, nullptr, 0}, band, bd, b0, nb, st);
 }
 
