@@ -258,6 +258,68 @@ def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128):
             "speedup_incl_cache_build_over_recompute": e2e_rate / rc_rate}
 
 
+def measure_serving(dn, synth, n_req=160, rate=20.0, seed=4005):
+    """Serving workload: Markov chains with N in {64, 128, 256, 512, 1024} (two each) of
+    the 6-layer, 64-channel, 64-mode model (FP32), requests of 1-512 random single-flip
+    proposals for a random chain.  For the ABACUS server and the per-request
+    full-forward recompute server: throughput with every request queued at once, and
+    p50/p99 latency (submission to result in host memory) under Poisson arrivals at
+    `rate` requests/s."""
+    import numpy as np
+    import time
+    desc = synth.ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
+    params = synth.init_params(desc, 1005, a_scale=10.0)
+    Ns = [64, 128, 256, 512, 1024] * 2
+    chains = [synth.spins_uniform(1, N, 2005 + k)[0] for k, N in enumerate(Ns)]
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(n_req):
+        c = int(rng.integers(len(Ns)))
+        F = int(rng.integers(1, 513))
+        reqs.append((c, rng.integers(0, Ns[c], size=F).astype(np.int32)))
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    flips = sum(len(s_) for _, s_ in reqs)
+    model = dn.Model(desc, params)
+    res = {"workload": "chains N in {64,128,256,512,1024} x 2, DysonNet L=6 d=64 s=64 w=2 FP32, %d requests of "
+                       "1-512 random single flips (%d flips)" % (n_req, flips),
+           "rate_per_s": rate}
+    for mode in ("abacus", "recompute"):
+        srv = dn.Server(model, prec="fp32", mode=mode, hbm_budget_bytes=24 << 30, max_batch_flips=4096,
+                        max_batch_chains=16)
+        t0 = time.perf_counter()
+        for k, sp in enumerate(chains):
+            srv.set_chain(k, sp, build_now=True)
+        build_s = time.perf_counter() - t0
+        for t in [srv.submit(k, np.array([0], dtype=np.int32)) for k in range(len(Ns))]:
+            srv.wait(t)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(c, s_) for c, s_ in reqs]
+        for t in tickets:
+            srv.wait(t)
+        sat_s = time.perf_counter() - t0
+        lat = []
+        t_next = time.perf_counter()
+        tickets = []
+        for (c, s_), gap in zip(reqs, gaps):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                time.sleep(min(1e-4, max(0.0, t_next - time.perf_counter())))
+            tickets.append(srv.submit(c, s_))
+        for t in tickets:
+            lat.append(srv.wait(t)[1])
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat) * 1e3
+        res[mode] = {"saturation": {"value": flips / sat_s, "unit": "flip ratios/s", "requests_per_s": n_req / sat_s},
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_ms": float(lat.mean()), "batches": st["batches"],
+                     "cache_build_s": build_s if mode == "abacus" else None,
+                     "resident_cache_bytes": st["resident_bytes"]}
+    model.close()
+    res["speedup_saturation"] = res["abacus"]["saturation"]["value"] / res["recompute"]["saturation"]["value"]
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -270,6 +332,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recompute", action="store_true")
     ap.add_argument("--no-n1024", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--n1024-chains", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -380,6 +443,7 @@ def main():
                      "speedup_of_abacus_step": (flips_step / (ms / 1e3)) / (flips_step / (rms / 1e3))}
 
     n1024 = None if args.no_n1024 else measure_n1024(dn, synth, torch, barrier, args.n1024_chains)
+    serving = None if args.no_serving else measure_serving(dn, synth)
 
     peaks, src = _peaks()
     roof, families = roofline(prof, args.steps, desc, N, Bs, peaks, src, clocks)
@@ -403,6 +467,7 @@ def main():
         "cache_build_ms_per_step": build_ms,
         "recompute": recompute,
         "n1024": n1024,
+        "serving": serving,
         "kernels": [{"name": k, "launches": n // args.steps, "ms_per_step": v / args.steps,
                      "share": v / total_k} for k, n, v in kernels[:16]],
     }

@@ -240,6 +240,58 @@ dn_status dn_profile_get(int i, char *name, size_t name_len, long long *launches
 /* Release a cache (stream-ordered on the stream of the call that built it). */
 void dn_cache_destroy(dn_cache *cache);
 
+/* ------------------------------------------------------------- serving --
+ * Continuous-batching request loop over resident caches: the way ABACUS is
+ * used inside Markov-chain Monte Carlo, where each chain proposes flips and
+ * needs their log-amplitude ratios (Sec. "ABACUS"; the batching and masking of
+ * App. "Implementation" for many chains).  A server owns a library worker
+ * thread and two CUDA streams.  Chains (one configuration of N sites each, any
+ * N) are registered with dn_server_set_chain; a request carries F single-site
+ * proposals for one chain and receives F ratios log psi(s') - log psi(s) in
+ * FP64.  Requests that arrive while earlier batches run join the next batch;
+ * one kernel serves all requests of a batch, whatever their chains.  A chain
+ * without a resident cache gets one built when it is first admitted (or at
+ * dn_server_set_chain with build_now); when the caches would exceed the
+ * device-memory budget, the least recently used idle ones are dropped.
+ * DN_SERVE_RECOMPUTE serves the same requests by a full forward pass of every
+ * proposal (the baseline).  While a server exists, its model must not be used
+ * by other calls.  Results of a request do not depend on which other requests
+ * share its batch. */
+typedef struct dn_server dn_server;
+typedef enum { DN_SERVE_ABACUS = 0, DN_SERVE_RECOMPUTE = 1 } dn_serve_mode;
+typedef struct {
+    unsigned long long requests, flips, batches, cache_builds, evictions;
+    size_t resident_bytes; /* device bytes of the resident caches */
+} dn_server_stats;
+
+/* hbm_budget_bytes bounds the resident caches; a batch holds at most
+ * max_batch_flips proposals and max_batch_chains chains (a request larger than
+ * max_batch_flips is rejected by dn_server_submit).  DN_EINVAL, DN_ENOMEM. */
+dn_status dn_server_create(dn_model *model, dn_precision prec, int mode, size_t hbm_budget_bytes, int max_batch_flips,
+                           int max_batch_chains, dn_server **server_out);
+
+/* Register chain `chain` (>= 0) with configuration spins_host[N] (+1/-1, copied),
+ * replacing an earlier one (and its cache).  build_now != 0 builds its cache in
+ * this call (ABACUS mode).  DN_EINVAL while requests of the chain are pending or
+ * in flight, or for spins other than +1/-1. */
+dn_status dn_server_set_chain(dn_server *server, int chain, int N, const int8_t *spins_host, int build_now);
+
+/* Queue F proposals for `chain`: sites_host[F][2] (site, -1) is copied; the F
+ * ratios are written to out_host[F], which must stay valid until the request
+ * completes.  *ticket identifies the request.  Returns at once. */
+dn_status dn_server_submit(dn_server *server, int chain, const int32_t *sites_host, int F, double *out_host,
+                           unsigned long long *ticket);
+
+/* Wait until request `ticket` completes (timeout_s < 0: no limit) and release
+ * it; *latency_s (may be NULL) is the host time from submission to the result in
+ * out_host.  Returns the request's status (DN_ETIMEOUT leaves it pending). */
+dn_status dn_server_wait(dn_server *server, unsigned long long ticket, double timeout_s, double *latency_s);
+
+dn_status dn_server_get_stats(dn_server *server, dn_server_stats *out);
+
+/* Finish every queued request, stop the worker and release the caches. */
+void dn_server_destroy(dn_server *server);
+
 #ifdef __cplusplus
 }
 #endif

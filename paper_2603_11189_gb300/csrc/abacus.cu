@@ -13,6 +13,8 @@
 // contribution sum_j t_j dsigma_j.  Output: sum_k f(Omega_k + dOmega_k) - f(Omega_k).
 #include <math.h>
 
+#include <cstring>
+
 #include "dn_internal.cuh"
 
 namespace dn {
@@ -46,10 +48,10 @@ struct AbArgs {
 
 constexpr int kAbThreads = 256;
 
+// Body of the flip-list kernel: flip set f of the cache described by a, one CTA.
 template <typename T>
-__global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_t *__restrict__ sample,
-                                                       const int32_t *__restrict__ sites, int F,
-                                                       double *__restrict__ out) {
+__device__ __forceinline__ void abacus_flip_set(const AbArgs<T> &a, long long f, const int32_t *__restrict__ sample,
+                                                const int32_t *__restrict__ sites, double *__restrict__ out) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Geom &g = a.g;
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, WF = a.WF, dout = g.dout, wd = g.w;
@@ -62,7 +64,6 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_
     __shared__ int info[8];
     __shared__ int pos[16];
     const int tid = threadIdx.x;
-    const long long f = blockIdx.x;
     if (tid == 0) {
         int status = 0, b = sample[f], j0 = sites[2 * f], j1 = sites[2 * f + 1];
         int first = j0, sep = 0;
@@ -265,6 +266,28 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_
         }
         out[f] = res;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAbThreads) k_abacus(AbArgs<T> a, const int32_t *__restrict__ sample,
+                                                       const int32_t *__restrict__ sites, int F,
+                                                       double *__restrict__ out) {
+    abacus_flip_set<T>(a, blockIdx.x, sample, sites, out);
+}
+
+// Flip sets of several caches (of one model, same max_cluster) in one launch:
+// flip set f belongs to cache cache_of[f], described by descs[cache_of[f]].
+template <typename T>
+__global__ void __launch_bounds__(kAbThreads) k_abacus_multi(const AbArgs<T> *__restrict__ descs,
+                                                             const int32_t *__restrict__ cache_of,
+                                                             const int32_t *__restrict__ sample,
+                                                             const int32_t *__restrict__ sites, int F,
+                                                             double *__restrict__ out) {
+    __shared__ AbArgs<T> sa;
+    const long long f = blockIdx.x;
+    if (threadIdx.x == 0) sa = descs[cache_of[f]];
+    __syncthreads();
+    abacus_flip_set<T>(sa, f, sample, sites, out);
 }
 
 template <typename T>
@@ -1318,6 +1341,46 @@ static AbArgs<T> ab_args(const dn_model *m, const Plan<T> &pl, const Weights<T> 
     a.w = w;
     return a;
 }
+
+// Descriptor of a cache for k_abacus_multi (a plain struct, copied to the device by the caller).
+template <typename T>
+size_t abacus_desc_bytes() {
+    return sizeof(AbArgs<T>);
+}
+
+template <typename T>
+void abacus_desc(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c, void *dst) {
+    const AbArgs<T> a = ab_args<T>(m, pl, w, c);
+    memcpy(dst, &a, sizeof(a));
+}
+
+template <typename T>
+cudaError_t launch_abacus_multi(const dn_model *m, int WF, const void *descs, const int32_t *cache_of,
+                                const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    const dn_model_desc &D = m->desc;
+    const size_t tsz = ((size_t)(D.L + 3) * WF * D.d + 2 * (size_t)WF * D.d_h) * sizeof(T);
+    const size_t smem = ((tsz + 7) & ~(size_t)7) + (size_t)kMaxDout * kAbThreads * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_abacus_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_abacus_multi", st);
+        k_abacus_multi<T><<<F, kAbThreads, smem, st>>>(static_cast<const AbArgs<T> *>(descs), cache_of, sample, sites,
+                                                       F, out);
+    }
+    return cudaGetLastError();
+}
+
+template size_t abacus_desc_bytes<double>();
+template size_t abacus_desc_bytes<float>();
+template void abacus_desc<double>(const dn_model *, const Plan<double> &, const Weights<double> &, const dn_cache *,
+                                  void *);
+template void abacus_desc<float>(const dn_model *, const Plan<float> &, const Weights<float> &, const dn_cache *,
+                                 void *);
+template cudaError_t launch_abacus_multi<double>(const dn_model *, int, const void *, const int32_t *, const int32_t *,
+                                                 const int32_t *, int, double *, cudaStream_t);
+template cudaError_t launch_abacus_multi<float>(const dn_model *, int, const void *, const int32_t *, const int32_t *,
+                                                const int32_t *, int, double *, cudaStream_t);
 
 size_t singles_scratch_bytes(const dn_model *m, const dn_cache *c) {
     const size_t W = 2 * m->desc.w + 1, rows = (size_t)c->B * c->N * W;

@@ -229,6 +229,16 @@ cudaError_t launch_mix_tc(const Geom &g, int l, const Weights<float> &w, const f
 template <typename T>
 cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
                           const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st);
+// Flip sets of several caches of one model in one launch (serving): descs is a device
+// array of abacus_desc_bytes<T>() records filled by abacus_desc<T>(); flip f uses
+// cache cache_of[f]; all caches share max_cluster (slice width WF).
+template <typename T>
+size_t abacus_desc_bytes();
+template <typename T>
+void abacus_desc(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c, void *dst);
+template <typename T>
+cudaError_t launch_abacus_multi(const dn_model *m, int WF, const void *descs, const int32_t *cache_of,
+                                const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st);
 // All N single flips of every cached configuration, out[b N + j], layer by
 // layer; scratch of singles_scratch_bytes() bytes (cudaErrorNotSupported when
 // the shape does not fit the kernels).

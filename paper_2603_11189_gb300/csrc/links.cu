@@ -239,9 +239,11 @@ __global__ void __launch_bounds__(256) k_dhop(Geom g, int P, int cols, const T *
     const long long bl = blockIdx.z;
     const T *D = Dm + bl * dm_ss + (long long)i * d * d;
     const int dp = FAST ? d : d + 1;            // fast path reads 8 consecutive rows as two 16-byte vectors
+    // Transposed on the read side: consecutive threads write consecutive words of a DsT
+    // row (no bank conflicts); D (4 KB per site) is read from L1/L2.
     for (int q = threadIdx.x; q < d * d; q += blockDim.x) {
-        const int c = q / d, a = q % d;
-        DsT[a * dp + c] = D[q];
+        const int a = q / d, c = q % d;
+        DsT[a * dp + c] = D[(long long)c * d + a];
     }
     if (sizeof(T) == 4 && P % 4 == 0 && cols % 4 == 0 && p0 + cols <= P) {
         // 16-byte loads, several in flight per thread.
@@ -395,6 +397,10 @@ __global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restri
     const int pad = kBcMaxBand + 1;
     float *gx = reinterpret_cast<float *>(smraw);   // gx[pad + r + N - 1] = g_{r,a} (wrapped on a ring)
     const int gx_len = 2 * N - 1 + 2 * pad;
+    // Generated operand: D0_n[a][:] for every n and the source-layer taps g_r[:] for
+    // r in (-N, N), both staged in shared memory.
+    float *Dsm = gx + ((gx_len + 3) & ~3);          // [N][d]
+    float *Tsm = Dsm + (GEN ? N * d : 0);           // [2N-1][d], row r + N - 1
     const int chunks = (P + 1023) / 1024;           // 256 threads x 4 columns per CTA
     const long long blk = blockIdx.x;
     const int ch = (int)(blk % chunks);
@@ -411,28 +417,39 @@ __global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restri
         }
         gx[q] = v;
     }
+    if (GEN) {
+        for (int q = threadIdx.x; q < N * d; q += blockDim.x) {
+            const int n = q / d, cc = q - n * d;
+            Dsm[q] = gs.Dm[bl * gs.dm_ss + ((long long)n * d + a) * d + cc];
+        }
+        for (int q = threadIdx.x; q < (2 * N - 1) * d; q += blockDim.x) {
+            const int rr = q / d, cc = q - rr * d;
+            Tsm[q] = gs.taps[(long long)tap_row(rr - (N - 1), N, g.periodic) * d + cc];
+        }
+    }
     __syncthreads();
     const int p = ch * 1024 + 4 * threadIdx.x;
     if (p >= P) return;
     const int k = p / ns, c = p - k * ns;
     const float *Xa = GEN ? nullptr : X + (bl * d + a) * (long long)N * P + p;
     // Generated operand (first hop of a source chain): X[n][(k, c..c+3)] = D0_n[a][c..c+3] g_{n-k, c..c+3}.
-    const float *Dma = GEN ? gs.Dm + bl * gs.dm_ss + (long long)a * d + c : nullptr;
+    const float *Dma = GEN ? Dsm + c : nullptr;
+    const float *Tk = GEN ? Tsm + (long long)(N - 1 - k) * d + c : nullptr;   // row of g_{n-k} at Tk[n d]
     const float *gk = gx + pad + (k - R) + (N - 1);   // tap of (q, n) at gk[q - n]
     float acc[NB][4];
 #pragma unroll
     for (int q = 0; q < NB; ++q)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[q][j] = 0.f;
-#pragma unroll 2
+#pragma unroll 4
     for (int n = 0; n < N; ++n) {
         float4 xv;
         if (GEN) {
-            const float4 dm = *reinterpret_cast<const float4 *>(Dma + (long long)n * d * d);
-            const float4 tp = *reinterpret_cast<const float4 *>(gs.taps + (long long)tap_row(n - k, N, g.periodic) * d + c);
+            const float4 dm = *reinterpret_cast<const float4 *>(Dma + n * d);
+            const float4 tp = *reinterpret_cast<const float4 *>(Tk + n * d);
             xv = make_float4(dm.x * tp.x, dm.y * tp.y, dm.z * tp.z, dm.w * tp.w);
         } else {
-            xv = *reinterpret_cast<const float4 *>(Xa + (long long)n * P);
+            xv = __ldg(reinterpret_cast<const float4 *>(Xa + (long long)n * P));
         }
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
@@ -544,7 +561,9 @@ static cudaError_t launch_bandconv_gen(const Geom &g, const T *taps, int P, cons
 template <bool GEN, int NB>
 static cudaError_t launch_bandconv4_nb(const Geom &g, const float *taps, int P, const float *X, const GenSrc<float> &gs,
                                        float *band, const BandDst &bd, long long b0, int nb, cudaStream_t st) {
-    const size_t smem = ((size_t)2 * g.N - 1 + 2 * (kBcMaxBand + 1)) * sizeof(float);
+    const size_t gx_len = (((size_t)2 * g.N - 1 + 2 * (kBcMaxBand + 1)) + 3) & ~(size_t)3;
+    const size_t smem = (gx_len + (GEN ? (size_t)g.N * g.d + (size_t)(2 * g.N - 1) * g.d : 0)) * sizeof(float);
+    if (smem > 200 * 1024) return cudaErrorNotSupported;
     const int chunks = (P + 1023) / 1024;
     const unsigned blocks = (unsigned)((long long)nb * g.d * chunks);
     cudaError_t err =

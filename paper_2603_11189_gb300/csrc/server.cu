@@ -1,0 +1,467 @@
+// Serving: a continuous-batching request loop over resident activation caches.
+//
+// Markov chains of different lengths N register their current configuration; a
+// request carries single-flip proposals for one chain and receives their
+// log-amplitude ratios (Sec. "ABACUS": the ratios a Metropolis step or a local
+// energy needs, served from the chain's cache).  One worker thread per server
+//  * takes every pending request that fits the next batch (requests that arrive
+//    while earlier batches are on the GPU join the next one),
+//  * admits the chains of the batch against a device-memory budget: a chain
+//    without a resident cache gets one built (dysonnet_forward_cache), evicting
+//    the least recently used idle caches when the budget would be exceeded,
+//  * launches the whole batch as one kernel over several caches (k_abacus_multi,
+//    one CTA per flip) on one of two streams, so that batch k+1 is formed and
+//    launched while batch k is still running,
+//  * copies results to the callers' host buffers and timestamps completion.
+// The recompute mode serves the same requests by full forward passes of every
+// proposal (dn_recompute_flip_ratios), the baseline the caches replace.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "dn_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    unsigned long long ticket = 0;
+    int chain = 0, F = 0;
+    std::vector<int32_t> sites;   // [F][2]
+    double *out_host = nullptr;
+    Clock::time_point t_submit, t_done;
+    dn_status status = DN_OK;
+    bool done = false;
+};
+
+struct Chain {
+    int N = 0;
+    int8_t *spins_dev = nullptr;
+    dn_cache *cache = nullptr;
+    size_t bytes = 0;
+    unsigned long long last_use = 0;
+    int in_flight = 0;   // batches on the GPU that use this chain
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    int32_t *h_i = nullptr, *d_i = nullptr;   // [sites 2F | sample F | cache_of F]
+    double *h_out = nullptr, *d_out = nullptr;
+    unsigned char *h_desc = nullptr, *d_desc = nullptr;
+    size_t bytes_i = 0, bytes_out = 0, bytes_desc = 0;
+    std::vector<Request *> reqs;
+    std::vector<int> offs, chains;
+    bool busy = false;
+};
+
+double seconds(Clock::duration d) { return std::chrono::duration<double>(d).count(); }
+
+}  // namespace
+
+struct dn_server {
+    dn_model *m = nullptr;
+    int prec = DN_FP32, mode = DN_SERVE_ABACUS, device = 0, max_flips = 0, max_chains = 0;
+    size_t budget = 0, desc_bytes = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> pending;
+    std::unordered_map<unsigned long long, Request *> reqs;
+    std::unordered_map<int, Chain> chains;
+    size_t resident = 0;
+    unsigned long long next_ticket = 1, clock = 0;
+    bool stop = false;
+    std::thread worker;
+    Slot slots[2];
+    dn_server_stats stats{};
+    cudaStream_t setup = nullptr;
+};
+
+namespace {
+
+bool fp64(const dn_server *s) { return s->prec == DN_FP64; }
+
+// Drop the cache of chain c (its batches must be done).
+void drop_cache(dn_server *s, Chain &c) {
+    if (c.cache) {
+        dn_cache_destroy(c.cache);
+        c.cache = nullptr;
+        s->resident -= c.bytes;
+        c.bytes = 0;
+    }
+}
+
+// Make room for `need` bytes by evicting idle caches, least recently used first.
+// `keep` lists the chains of the batch being formed.  Called with s->mu held.
+bool make_room(dn_server *s, size_t need, const std::vector<int> &keep) {
+    while (s->resident + need > s->budget) {
+        Chain *victim = nullptr;
+        for (auto &kv : s->chains) {
+            Chain &c = kv.second;
+            if (!c.cache || c.in_flight > 0) continue;
+            if (std::find(keep.begin(), keep.end(), kv.first) != keep.end()) continue;
+            if (!victim || c.last_use < victim->last_use) victim = &c;
+        }
+        if (!victim) return false;
+        drop_cache(s, *victim);
+        s->stats.evictions++;
+    }
+    return true;
+}
+
+dn_status build_cache(dn_server *s, Chain &c, cudaStream_t st) {
+    dn_cache *cache = nullptr;
+    dn_status r = dysonnet_forward_cache(s->m, c.N, c.spins_dev, 1, (dn_precision)s->prec, 1, st, &cache, nullptr);
+    if (r != DN_OK) return r;
+    c.cache = cache;
+    c.bytes = dn_cache_bytes(s->m, c.N, 1, (dn_precision)s->prec, 1);
+    s->resident += c.bytes;
+    s->stats.cache_builds++;
+    return DN_OK;
+}
+
+void finish(dn_server *s, Slot &sl, dn_status status) {
+    const auto now = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (size_t k = 0; k < sl.reqs.size(); ++k) {
+        Request *r = sl.reqs[k];
+        if (status == DN_OK) memcpy(r->out_host, sl.h_out + sl.offs[k], (size_t)r->F * sizeof(double));
+        r->status = status;
+        r->t_done = now;
+        r->done = true;
+    }
+    for (int c : sl.chains) s->chains[c].in_flight--;
+    s->stats.batches++;
+    sl.reqs.clear();
+    sl.offs.clear();
+    sl.chains.clear();
+    sl.busy = false;
+    s->cv_done.notify_all();
+}
+
+// Form and launch one batch on slot sl: 0 when nothing could be admitted, 1 when a
+// batch is in flight on sl, 2 when it failed (its requests are already completed).
+int launch_batch(dn_server *s, Slot &sl) {
+    std::vector<Request *> batch;
+    std::vector<int> bchains;
+    int flips = 0;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        while (!s->pending.empty()) {
+            Request *r = s->pending.front();
+            if (flips + r->F > s->max_flips && !batch.empty()) break;
+            const bool new_chain = std::find(bchains.begin(), bchains.end(), r->chain) == bchains.end();
+            if (new_chain && (int)bchains.size() >= s->max_chains) break;
+            Chain &c = s->chains[r->chain];
+            if (new_chain && s->mode == DN_SERVE_ABACUS && !c.cache) {
+                const size_t need = dn_cache_bytes(s->m, c.N, 1, (dn_precision)s->prec, 1);
+                if (!make_room(s, need, bchains)) break;   // wait until in-flight batches release caches
+                dn_status b = build_cache(s, c, sl.st);
+                if (b != DN_OK) {
+                    s->pending.pop_front();
+                    r->status = b;
+                    r->t_done = Clock::now();
+                    r->done = true;
+                    s->cv_done.notify_all();
+                    continue;
+                }
+            }
+            s->pending.pop_front();
+            if (new_chain) {
+                bchains.push_back(r->chain);
+                c.in_flight++;
+            }
+            c.last_use = ++s->clock;
+            batch.push_back(r);
+            flips += r->F;
+        }
+    }
+    if (batch.empty()) return 0;
+    // Stage the batch: sites, sample 0 (every cache holds one configuration), cache index.
+    int32_t *h_sites = sl.h_i, *h_sample = sl.h_i + 2 * s->max_flips, *h_cof = h_sample + s->max_flips;
+    int off = 0;
+    for (Request *r : batch) {
+        const int ci = (int)(std::find(bchains.begin(), bchains.end(), r->chain) - bchains.begin());
+        memcpy(h_sites + 2 * off, r->sites.data(), (size_t)r->F * 2 * sizeof(int32_t));
+        for (int f = 0; f < r->F; ++f) {
+            h_sample[off + f] = 0;
+            h_cof[off + f] = ci;
+        }
+        sl.offs.push_back(off);
+        off += r->F;
+    }
+    sl.reqs = batch;
+    sl.chains = bchains;
+    sl.busy = true;
+    int32_t *d_sites = sl.d_i, *d_sample = sl.d_i + 2 * s->max_flips, *d_cof = d_sample + s->max_flips;
+    cudaError_t e = cudaMemcpyAsync(d_sites, h_sites, (size_t)off * 2 * sizeof(int32_t), cudaMemcpyHostToDevice, sl.st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_sample, h_sample, (size_t)off * sizeof(int32_t), cudaMemcpyHostToDevice, sl.st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_cof, h_cof, (size_t)off * sizeof(int32_t), cudaMemcpyHostToDevice, sl.st);
+    if (e == cudaSuccess && s->mode == DN_SERVE_ABACUS) {
+        for (size_t k = 0; k < bchains.size(); ++k) {
+            Chain &c = s->chains[bchains[k]];
+            if (fp64(s))
+                dn::abacus_desc<double>(s->m, s->m->plan64.at(c.N), s->m->w64, c.cache, sl.h_desc + k * s->desc_bytes);
+            else
+                dn::abacus_desc<float>(s->m, s->m->plan32.at(c.N), s->m->w32, c.cache, sl.h_desc + k * s->desc_bytes);
+        }
+        e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, bchains.size() * s->desc_bytes, cudaMemcpyHostToDevice, sl.st);
+        const int WF = 2 * s->m->desc.w + 1;
+        if (e == cudaSuccess)
+            e = fp64(s) ? dn::launch_abacus_multi<double>(s->m, WF, sl.d_desc, d_cof, d_sample, d_sites, off, sl.d_out,
+                                                          sl.st)
+                        : dn::launch_abacus_multi<float>(s->m, WF, sl.d_desc, d_cof, d_sample, d_sites, off, sl.d_out,
+                                                         sl.st);
+    } else if (e == cudaSuccess) {
+        // Recompute: every proposal of a request by full forward passes of its chain.
+        for (size_t k = 0; k < batch.size() && e == cudaSuccess; ++k) {
+            Request *r = batch[k];
+            Chain &c = s->chains[r->chain];
+            dn_status st = dn_recompute_flip_ratios(s->m, c.N, c.spins_dev, 1, d_sample + sl.offs[k],
+                                                    d_sites + 2 * sl.offs[k], r->F, (dn_precision)s->prec, sl.st,
+                                                    sl.d_out + sl.offs[k]);
+            if (st != DN_OK) e = cudaErrorUnknown;
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)off * sizeof(double), cudaMemcpyDeviceToHost, sl.st);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.st);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stats.flips += off;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(sl.st);
+        finish(s, sl, DN_ECUDA);
+        return 2;
+    }
+    return 1;
+}
+
+void worker_main(dn_server *s) {
+    cudaSetDevice(s->device);
+    std::deque<int> inflight;   // busy slots in launch order
+    for (;;) {
+        bool have_pending, stopping;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (inflight.empty()) s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
+            have_pending = !s->pending.empty();
+            stopping = s->stop;
+        }
+        if (stopping && !have_pending && inflight.empty()) break;
+        int launched = 0;
+        if (have_pending && inflight.size() < 2) {
+            const int k = s->slots[0].busy ? 1 : 0;
+            launched = launch_batch(s, s->slots[k]);
+            if (launched == 1) inflight.push_back(k);
+        }
+        if (!inflight.empty()) {
+            // Complete the oldest batch; block on it only when both slots are busy or there is
+            // nothing else to do.
+            Slot &o = s->slots[inflight.front()];
+            const bool block = inflight.size() == 2 || (!launched && !have_pending);
+            const cudaError_t q = block ? cudaEventSynchronize(o.ev) : cudaEventQuery(o.ev);
+            if (q != cudaErrorNotReady) {
+                if (q != cudaSuccess) cudaGetLastError();
+                finish(s, o, q == cudaSuccess ? DN_OK : DN_ECUDA);
+                inflight.pop_front();
+            } else if (!launched) {
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
+        } else if (have_pending && !launched) {
+            // Nothing admissible with nothing in flight: the budget cannot hold the next chain.
+            std::lock_guard<std::mutex> lk(s->mu);
+            Request *r = s->pending.front();
+            s->pending.pop_front();
+            r->status = DN_ENOMEM;
+            r->t_done = Clock::now();
+            r->done = true;
+            s->cv_done.notify_all();
+        }
+    }
+}
+
+void free_slot(Slot &sl) {
+    if (sl.st) cudaStreamSynchronize(sl.st);
+    if (sl.h_i) cudaFreeHost(sl.h_i);
+    if (sl.h_out) cudaFreeHost(sl.h_out);
+    if (sl.h_desc) cudaFreeHost(sl.h_desc);
+    if (sl.d_i) dn::dev_free(sl.d_i, sl.bytes_i, sl.st);
+    if (sl.d_out) dn::dev_free(sl.d_out, sl.bytes_out, sl.st);
+    if (sl.d_desc) dn::dev_free(sl.d_desc, sl.bytes_desc, sl.st);
+    if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.st) {
+        cudaStreamSynchronize(sl.st);
+        cudaStreamDestroy(sl.st);
+    }
+    sl = Slot{};
+}
+
+void destroy_server(dn_server *s) {
+    for (auto &sl : s->slots) free_slot(sl);
+    for (auto &kv : s->chains) {
+        drop_cache(s, kv.second);
+        if (kv.second.spins_dev) dn::dev_free(kv.second.spins_dev, (size_t)kv.second.N, s->setup);
+    }
+    for (auto &kv : s->reqs) delete kv.second;
+    if (s->setup) {
+        cudaStreamSynchronize(s->setup);
+        cudaStreamDestroy(s->setup);
+    }
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+dn_status dn_server_create(dn_model *m, dn_precision prec, int mode, size_t hbm_budget_bytes, int max_batch_flips,
+                           int max_batch_chains, dn_server **out) {
+    if (!out) return DN_EINVAL;
+    *out = nullptr;
+    if (!m || (prec != DN_FP64 && prec != DN_FP32 && prec != DN_BF16) ||
+        (mode != DN_SERVE_ABACUS && mode != DN_SERVE_RECOMPUTE) || max_batch_flips < 1 || max_batch_chains < 1)
+        return DN_EINVAL;
+    dn_server *s = new dn_server();
+    s->m = m;
+    s->prec = prec;
+    s->mode = mode;
+    s->budget = hbm_budget_bytes;
+    s->max_flips = max_batch_flips;
+    s->max_chains = max_batch_chains;
+    s->desc_bytes =
+        ((prec == DN_FP64 ? dn::abacus_desc_bytes<double>() : dn::abacus_desc_bytes<float>()) + 15) & ~(size_t)15;
+    cudaGetDevice(&s->device);
+    bool ok = cudaStreamCreateWithFlags(&s->setup, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &sl : s->slots) {
+        if (!ok) break;
+        sl.bytes_i = (size_t)4 * max_batch_flips * sizeof(int32_t);
+        sl.bytes_out = (size_t)max_batch_flips * sizeof(double);
+        sl.bytes_desc = (size_t)max_batch_chains * s->desc_bytes;
+        ok = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaMallocHost(&sl.h_i, sl.bytes_i) == cudaSuccess && cudaMallocHost(&sl.h_out, sl.bytes_out) == cudaSuccess &&
+             cudaMallocHost(&sl.h_desc, sl.bytes_desc) == cudaSuccess;
+        if (!ok) break;
+        sl.d_i = static_cast<int32_t *>(dn::dev_alloc(sl.bytes_i, sl.st));
+        sl.d_out = static_cast<double *>(dn::dev_alloc(sl.bytes_out, sl.st));
+        sl.d_desc = static_cast<unsigned char *>(dn::dev_alloc(sl.bytes_desc, sl.st));
+        ok = sl.d_i && sl.d_out && sl.d_desc;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        destroy_server(s);
+        return DN_ENOMEM;
+    }
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return DN_OK;
+}
+
+dn_status dn_server_set_chain(dn_server *s, int chain, int N, const int8_t *spins_host, int build_now) {
+    if (!s || chain < 0 || N < 1 || !spins_host) return DN_EINVAL;
+    for (int i = 0; i < N; ++i)
+        if (spins_host[i] != 1 && spins_host[i] != -1) return DN_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    Chain &c = s->chains[chain];
+    if (c.in_flight > 0) return DN_EINVAL;
+    for (Request *r : s->pending)
+        if (r->chain == chain) return DN_EINVAL;
+    drop_cache(s, c);
+    if (c.spins_dev && c.N != N) {
+        dn::dev_free(c.spins_dev, (size_t)c.N, s->setup);
+        c.spins_dev = nullptr;
+    }
+    c.N = N;
+    if (!c.spins_dev) c.spins_dev = static_cast<int8_t *>(dn::dev_alloc((size_t)N, s->setup));
+    if (!c.spins_dev) return DN_ENOMEM;
+    if (cudaMemcpyAsync(c.spins_dev, spins_host, (size_t)N, cudaMemcpyHostToDevice, s->setup) != cudaSuccess ||
+        cudaStreamSynchronize(s->setup) != cudaSuccess) {
+        cudaGetLastError();
+        return DN_ECUDA;
+    }
+    if (build_now && s->mode == DN_SERVE_ABACUS) {
+        if (!make_room(s, dn_cache_bytes(s->m, N, 1, (dn_precision)s->prec, 1), {chain})) return DN_ENOMEM;
+        dn_status r = build_cache(s, c, s->setup);
+        if (r != DN_OK) return r;
+        if (cudaStreamSynchronize(s->setup) != cudaSuccess) {
+            cudaGetLastError();
+            return DN_ECUDA;
+        }
+        c.last_use = ++s->clock;
+    }
+    return DN_OK;
+}
+
+dn_status dn_server_submit(dn_server *s, int chain, const int32_t *sites_host, int F, double *out_host,
+                           unsigned long long *ticket) {
+    if (!s || !sites_host || !out_host || !ticket || F < 1 || F > s->max_flips) return DN_EINVAL;
+    Request *r = new Request();
+    r->chain = chain;
+    r->F = F;
+    r->sites.assign(sites_host, sites_host + 2 * (size_t)F);
+    r->out_host = out_host;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->chains.find(chain);
+        if (it == s->chains.end() || !it->second.spins_dev) {
+            delete r;
+            return DN_EINVAL;
+        }
+        r->ticket = s->next_ticket++;
+        *ticket = r->ticket;
+        s->reqs[r->ticket] = r;
+        s->pending.push_back(r);
+        s->stats.requests++;
+    }
+    s->cv_work.notify_one();
+    return DN_OK;
+}
+
+dn_status dn_server_wait(dn_server *s, unsigned long long ticket, double timeout_s, double *latency_s) {
+    if (!s) return DN_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return DN_EINVAL;
+    Request *r = it->second;
+    const auto dl = std::chrono::duration<double>(timeout_s < 0 ? 1e9 : timeout_s);
+    if (!s->cv_done.wait_for(lk, dl, [&] { return r->done; })) return DN_ETIMEOUT;
+    if (latency_s) *latency_s = seconds(r->t_done - r->t_submit);
+    const dn_status st = r->status;
+    s->reqs.erase(it);
+    delete r;
+    return st;
+}
+
+dn_status dn_server_get_stats(dn_server *s, dn_server_stats *out) {
+    if (!s || !out) return DN_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    out->resident_bytes = s->resident;
+    return DN_OK;
+}
+
+void dn_server_destroy(dn_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    destroy_server(s);
+}
+
+}  // extern "C"

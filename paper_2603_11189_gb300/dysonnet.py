@@ -37,6 +37,14 @@ class Hamiltonian(ctypes.Structure):
                 ("J1", ctypes.c_double), ("J2", ctypes.c_double), ("periodic", ctypes.c_int), ("kac", ctypes.c_int)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_ulonglong), ("flips", ctypes.c_ulonglong), ("batches", ctypes.c_ulonglong),
+                ("cache_builds", ctypes.c_ulonglong), ("evictions", ctypes.c_ulonglong),
+                ("resident_bytes", ctypes.c_size_t)]
+
+
+DN_SERVE_ABACUS, DN_SERVE_RECOMPUTE = 0, 1
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -76,6 +84,12 @@ def _lib():
         "dn_cache_tensor": (i32, [vp, ctypes.c_char_p, ctypes.POINTER(vp), ctypes.POINTER(sz),
                                   ctypes.POINTER(i32)]),
         "dn_cache_destroy": (None, [vp]),
+        "dn_server_create": (i32, [vp, i32, i32, sz, i32, i32, ctypes.POINTER(vp)]),
+        "dn_server_set_chain": (i32, [vp, i32, i32, vp, i32]),
+        "dn_server_submit": (i32, [vp, i32, vp, i32, vp, ctypes.POINTER(ctypes.c_ulonglong)]),
+        "dn_server_wait": (i32, [vp, ctypes.c_ulonglong, dbl, ctypes.POINTER(dbl)]),
+        "dn_server_get_stats": (i32, [vp, ctypes.POINTER(ServerStats)]),
+        "dn_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -90,7 +104,9 @@ def exported_symbols():
     return ["dn_status_string", "dn_set_allocator", "dn_model_create", "dn_model_destroy", "dn_cache_bytes",
             "dysonnet_forward_cache", "abacus_flip_ratios", "local_energy", "dn_full_forward",
             "dn_recompute_flip_ratios", "dn_cache_check", "dn_cache_info", "dn_cache_tensor", "dn_cache_destroy",
-            "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable", "dn_profile_count", "dn_profile_get"]
+            "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable",
+            "dn_profile_count", "dn_profile_get", "dn_server_create", "dn_server_set_chain", "dn_server_submit",
+            "dn_server_wait", "dn_server_get_stats", "dn_server_destroy"]
 
 
 def _check(status: int, what: str):
@@ -281,3 +297,58 @@ def _device_view(ptr: int, count: int, typestr: str) -> torch.Tensor:
         __cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, True), "version": 3}
 
     return torch.as_tensor(_Arr(), device="cuda")
+
+
+class Server:
+    """Continuous-batching request loop of the library (dn_server_*): chains of any N
+    with resident caches, requests of single-site proposals served in batches by one
+    kernel; mode "abacus" or "recompute" (full forward pass of every proposal)."""
+
+    def __init__(self, model: "Model", prec="fp32", mode="abacus", hbm_budget_bytes: int = 16 << 30,
+                 max_batch_flips: int = 8192, max_batch_chains: int = 64):
+        self._model = model
+        self._h = ctypes.c_void_p()
+        m = DN_SERVE_ABACUS if mode == "abacus" else DN_SERVE_RECOMPUTE
+        _check(_lib().dn_server_create(model._h, PRECISIONS[prec], m, int(hbm_budget_bytes), int(max_batch_flips),
+                                       int(max_batch_chains), ctypes.byref(self._h)), "dn_server_create")
+        self._out = {}
+
+    def set_chain(self, chain: int, spins, build_now: bool = False):
+        import numpy as np
+        a = np.ascontiguousarray(spins, dtype=np.int8)
+        _check(_lib().dn_server_set_chain(self._h, int(chain), int(a.size), a.ctypes.data, int(bool(build_now))),
+               "dn_server_set_chain")
+
+    def submit(self, chain: int, sites) -> int:
+        """sites: int array [F] of single sites or [F, 2] (second entry -1)."""
+        import numpy as np
+        x = np.asarray(sites, dtype=np.int32)
+        if x.ndim == 1:
+            x = np.stack([x, -np.ones_like(x)], axis=1)
+        x = np.ascontiguousarray(x)
+        out = np.empty(x.shape[0], dtype=np.float64)
+        t = ctypes.c_ulonglong()
+        _check(_lib().dn_server_submit(self._h, int(chain), x.ctypes.data, int(x.shape[0]), out.ctypes.data,
+                                       ctypes.byref(t)), "dn_server_submit")
+        self._out[t.value] = (out, x)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        """(ratios, latency in seconds) of a submitted request."""
+        lat = ctypes.c_double()
+        st = _lib().dn_server_wait(self._h, ctypes.c_ulonglong(ticket), float(timeout_s), ctypes.byref(lat))
+        if st == DN_ETIMEOUT:
+            _check(st, "dn_server_wait")
+        out, _ = self._out.pop(ticket)
+        _check(st, "dn_server_wait")
+        return out, lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(_lib().dn_server_get_stats(self._h, ctypes.byref(s)), "dn_server_get_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _lib().dn_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
