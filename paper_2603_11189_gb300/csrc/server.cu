@@ -116,10 +116,17 @@ bool make_room(dn_server *s, size_t need, const std::vector<int> &keep) {
     return true;
 }
 
+// Build chain c's cache on stream st and wait for it: later batches may run on the
+// other stream, which nothing orders after this one.
 dn_status build_cache(dn_server *s, Chain &c, cudaStream_t st) {
     dn_cache *cache = nullptr;
     dn_status r = dysonnet_forward_cache(s->m, c.N, c.spins_dev, 1, (dn_precision)s->prec, 1, st, &cache, nullptr);
     if (r != DN_OK) return r;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        dn_cache_destroy(cache);
+        return DN_ECUDA;
+    }
     c.cache = cache;
     c.bytes = dn_cache_bytes(s->m, c.N, 1, (dn_precision)s->prec, 1);
     s->resident += c.bytes;

@@ -305,6 +305,209 @@ __global__ void __launch_bounds__(256, 3) k_tgemm_tc(Geom g, const float *__rest
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
 }
 
+// Persistent variant for the generated operand (first hop of a source chain) when the
+// whole chain fits in shared memory (N <= 256): one CTA per (sample, channel a, 128-row
+// site tile) loops over column tiles.  The source-layer vertex rows D0_n[a][:], the
+// source-layer taps g_r[:] for r in (-N, N) and the Hankel operand of every K chunk are
+// staged once per CTA, so a column tile costs its operand generation, MMAs and epilogue
+// only.  Chunks share one B buffer: chunk c waits for the MMAs of chunk c - 1.
+constexpr int kGpMaxChunks = 4;
+
+template <int NPL>
+__global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__restrict__ taps, int P,
+                                                       const float *__restrict__ gtaps, const float *__restrict__ gDm,
+                                                       long long dm_ss, float *__restrict__ Y, float *__restrict__ band,
+                                                       long long bss, long long brs, long long bos, int bR, int bns,
+                                                       long long b0, unsigned *__restrict__ flag) {
+    extern __shared__ __align__(1024) unsigned char smtc[];
+    constexpr int TN = 128, kSlabB = TN * 16 * 2;
+    constexpr int kBbytes = NPL * 4 * kSlabB;
+    constexpr int kFront = kBbytes > kEpiBytes ? kBbytes : kEpiBytes;
+    const int N = g.N, d = g.d;
+    const int nch = (N + kTcK - 1) / kTcK;
+    unsigned char *Bp = smtc;                                       // NPL planes x 4 slabs
+    unsigned char *Aall = smtc + kFront;                            // [nch][NPL][kHankelBytes]
+    float *gx = reinterpret_cast<float *>(Aall + (size_t)nch * NPL * kHankelBytes);   // gx[r + N - 1], channel a
+    float *Dfull = gx + ((2 * N + 1) & ~1);                         // [N][d]: D0_n[a][c']
+    float *Tfull = Dfull + (size_t)N * d;                           // [2N - 1][d]: g_r[c'], row r + N - 1
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Tfull + ((size_t)(2 * N - 1) * d + 1) / 2 * 2);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    int *s_ok = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.y * kTcM;
+    const long long za = blockIdx.z;
+    const int a = (int)(za % d);
+    const long long bl = za / d;
+    for (int q = tid; q < 2 * N - 1; q += blockDim.x) gx[q] = taps[(long long)tap_row_tc(q - (N - 1), N, g.periodic) * d + a];
+    for (int q = tid; q < N * d; q += blockDim.x) {
+        const int n = q / d, c = q - n * d;
+        Dfull[q] = gDm[bl * dm_ss + ((long long)n * d + a) * d + c];
+    }
+    for (int q = tid; q < (2 * N - 1) * d; q += blockDim.x) {
+        const int rr = q / d, c = q - rr * d;
+        Tfull[q] = gtaps[(long long)tap_row_tc(rr - (N - 1), N, g.periodic) * d + c];
+    }
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *s_ok = 1;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, TN);
+    __syncthreads();
+    // Hankel operand of every chunk (reversed K order, as in k_tgemm_tc).
+    for (int ch = 0; ch < nch; ++ch) {
+        const int n0 = ch * kTcK;
+        unsigned char *Ap = Aall + (size_t)ch * NPL * kHankelBytes;
+        for (int q = tid; q < kHankel * 8; q += blockDim.x) {
+            const int D = q >> 3, rr = q & 7;
+            const int t0 = i0 - n0 - kTcK + 1 + 8 * D + rr;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0 + u;
+                v[u] = (t > -N && t < N) ? gx[t + N - 1] : 0.f;
+            }
+            tc::stage8_planes<NPL>(Ap, kHankelBytes, (uint32_t)(D * 128 + rr * 16), v);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16(kTcM, TN);
+    const int pp = tid % TN, part = tid / TN;        // column of the tile, half of a chunk's sites
+    const int ntiles = (P + TN - 1) / TN;
+    uint32_t phase = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int p0 = t * TN, pcol = p0 + pp;
+        const bool pok = pcol < P;
+        const int kq = pcol / d, cq = pcol - kq * d;
+        bool ok = true;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int n0 = ch * kTcK;
+            if (ch > 0) {
+                // The MMAs of chunk ch - 1 read the B buffer this chunk overwrites.
+                if (warp == 0 && !tc::wait(mbar, phase) && lane == 0) *s_ok = 0;
+                phase ^= 1u;
+                __syncthreads();
+                if (!*s_ok) {
+                    ok = false;
+                    break;
+                }
+            }
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                const int base = part * 32 + kc * 8;
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int n = n0 + base + 7 - u;
+                    v[u] = (pok && n < N) ? Dfull[n * d + cq] * Tfull[(n - kq + N - 1) * d + cq] : 0.f;
+                }
+                const int kk = kTcK - 8 - base;
+                tc::stage8_planes<NPL>(Bp, 4 * kSlabB, (uint32_t)(kk >> 4) * kSlabB + tc::canon(pp, kk & 15), v);
+            }
+            tc::fence_async_smem();
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+            if (tid == 0) {
+                const unsigned char *Ap = Aall + (size_t)ch * NPL * kHankelBytes;
+                for (int s = 0; s < kTcK / 16; ++s)
+#pragma unroll
+                    for (int pa = 0; pa < NPL; ++pa)
+#pragma unroll
+                        for (int pb = 0; pa + pb < NPL; ++pb)
+                            tc::mma_bf16(tmem, umma_desc_hankel(sm_u32(Ap + pa * kHankelBytes + 2 * s * 128)),
+                                         umma_desc(sm_u32(Bp + pb * 4 * kSlabB + s * kSlabB)), idesc,
+                                         (ch == 0 && s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+                tc::commit(mbar);
+            }
+        }
+        if (ok) {
+            if (warp == 0 && !tc::wait(mbar, phase) && lane == 0) *s_ok = 0;
+            phase ^= 1u;
+        }
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (!*s_ok) break;
+        // Epilogue (as k_tgemm_tc): TMEM -> per-warp 32 x 33 staging tile -> rows of Y, band.
+        const int quad = warp & 3, half = warp >> 2;
+        float *stage = reinterpret_cast<float *>(smtc) + warp * (32 * 33);
+        const int prow0 = i0 + quad * 32;
+        const int nrows = N - prow0 < 32 ? N - prow0 : 32;
+        for (int c0 = 0; c0 < TN / 2; c0 += 32) {
+            float r[32];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                tc::tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * (TN / 2) + c0 + 8 * q), r + 8 * q);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = r[j];
+            __syncwarp();
+            const int p = p0 + half * (TN / 2) + c0 + lane;
+            if (p < P && nrows > 0) {
+                if (Y) {
+                    float *yp = Y + ((bl * d + a) * N + prow0) * (long long)P + p;
+                    for (int rr = 0; rr < nrows; ++rr, yp += P) *yp = stage[rr * 33 + lane];
+                }
+                if (band) {
+                    const int k = p / bns, cc = p - k * bns;
+                    float *bp = band + (b0 + bl) * bss + (long long)a * bns + cc;
+                    for (int dl = -bR; dl <= bR; ++dl) {
+                        int i = k + dl;
+                        if (g.periodic) i = i < 0 ? i + N : (i >= N ? i - N : i);
+                        else if (i < 0 || i >= N) continue;
+                        if (i < prow0 || i >= prow0 + nrows) continue;
+                        if (g.periodic && ring_delta_tc(i - k, N, 1) != dl) continue;
+                        bp[(long long)i * brs + (long long)(bR - dl) * bos] = stage[(i - prow0) * 33 + lane];
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        // The next tile overwrites the staging area (B buffer) and the accumulator.
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
+    if (!*s_ok && tid == 0) atomicOr(flag, 8u);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, TN);
+}
+
+static size_t tgemm_genp_smem(int N, int d, int npl) {
+    const int nch = (N + kTcK - 1) / kTcK;
+    const size_t B = (size_t)npl * 4 * 128 * 32;
+    const size_t front = B > (size_t)kEpiBytes ? B : (size_t)kEpiBytes;
+    return front + (size_t)nch * npl * kHankelBytes +
+           ((size_t)((2 * N + 1) & ~1) + (size_t)N * d + ((size_t)(2 * N - 1) * d + 1) / 2 * 2) * sizeof(float) + 32;
+}
+
+template <int NPL>
+static cudaError_t launch_tgemm_genp(const Geom &g, const float *taps, int P, const float *gtaps, const float *gDm,
+                                     long long dm_ss, float *Y, float *band, long long bss, long long brs,
+                                     long long bos, int bR, int bns, long long b0, int nb, unsigned *flag,
+                                     cudaStream_t st) {
+    const size_t smem = tgemm_genp_smem(g.N, g.d, NPL);
+    const int itiles = (g.N + kTcM - 1) / kTcM, ntiles = (P + 127) / 128;
+    const long long ctas = (long long)itiles * nb * g.d;
+    // Column tiles per CTA: all of them when there are enough CTAs to fill the GPU twice over.
+    long long cg = (2 * 2 * 152 + ctas - 1) / ctas;
+    if (cg < 1) cg = 1;
+    if (cg > ntiles) cg = ntiles;
+    dim3 grid((unsigned)cg, (unsigned)itiles, (unsigned)((long long)nb * g.d));
+    cudaError_t err = cudaFuncSetAttribute(k_tgemm_genp<NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_tgemm_tc", st);
+        k_tgemm_genp<NPL><<<grid, 256, smem, st>>>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0,
+                                                   flag);
+    }
+    return cudaGetLastError();
+}
+
 template <int TN, int NPL>
 static size_t tgemm_tc_smem(int N, int d, bool gen) {
     const int nk = (TN + d - 1) / d + 1;
@@ -346,6 +549,14 @@ cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float
                             const float *gDm, long long dm_ss, float *Y, float *band, long long bss, long long brs,
                             long long bos, int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st,
                             int planes) {
+    // Generated operand with the whole chain in shared memory: the persistent kernel.
+    if (gtaps && g.N <= kGpMaxChunks * kTcK && g.d <= 64 && 128 % g.d == 0 && (planes == 1 || planes == 2) &&
+        tgemm_genp_smem(g.N, g.d, planes) <= 110 * 1024) {
+        return planes == 1 ? launch_tgemm_genp<1>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0,
+                                                  nb, flag, st)
+                           : launch_tgemm_genp<2>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0,
+                                                  nb, flag, st);
+    }
     switch (planes) {
     case 1:
         return launch_tgemm_tc_tn<128, 1>(g, taps, P, X, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb,
