@@ -216,6 +216,11 @@ cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float
                             long long bos, int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st,
                             int planes = 2);
 
+// Vertex hop X[b][c][n][p] = sum_a D0_n[c][a] Y[b][a][n][p] on the tensor cores (tc_gemm.cu),
+// planes BF16 terms per value (3: FP32-grade, 1: BF16); cudaErrorNotSupported for other d.
+cudaError_t launch_dhop_tc(int d, int N, int P, const float *Dm, long long dm_ss, const float *Y, float *Xo, int nb,
+                           int planes, unsigned *flag, cudaStream_t st);
+
 // Tensor-core forward pass (forward_tc.cu); activations channel-major h[c][n B + b].
 bool forward_tc_ok(const Geom &g);
 cudaError_t launch_h0_cm(const Geom &g, const int8_t *spins, const float *e, int B, float *h, cudaStream_t st);

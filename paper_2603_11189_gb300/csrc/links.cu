@@ -610,7 +610,14 @@ static cudaError_t launch_bandconv(const Geom &g, const T *taps, int P, const T 
 
 template <typename T>
 static cudaError_t launch_dhop(const Geom &g, int P, const T *Dm, long long dm_ss, const T *Y, T *Xo, int nb,
-                               cudaStream_t st) {
+                               cudaStream_t st, int planes = 3, unsigned *flag = nullptr) {
+    if constexpr (sizeof(T) == 4) {
+        cudaError_t e = launch_dhop_tc(g.d, g.N, P, reinterpret_cast<const float *>(Dm), dm_ss,
+                                       reinterpret_cast<const float *>(Y), reinterpret_cast<float *>(Xo), nb, planes,
+                                       flag, st);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
+    }
     const bool fast = g.d % 8 == 0 && g.d <= 64;
     const int cols = fast ? (256 / (g.d / 8)) * 4 : 128;
     const size_t smem = (((size_t)g.d * (g.d + 1) + 3) / 4 * 4 + (size_t)g.d * cols) * sizeof(T);
@@ -647,6 +654,7 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
     T *K = static_cast<T *>(c->K);
     const int nRl = 2 * c->Rl + 1, nRk = 2 * c->Rk + 1;
     const int planes = c->prec == DN_BF16 ? 1 : 2;   // BF16: single-product Toeplitz hops; FP32: 3 products
+    const int dplanes = c->prec == DN_BF16 ? 1 : 3;  // vertex hops: K = d only, FP32-grade with 3 planes
     cudaError_t err;
     for (int b0 = 0; b0 < c->B; b0 += nb_max) {
         const int nb = (c->B - b0 < nb_max) ? c->B - b0 : nb_max;
@@ -675,7 +683,7 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
             if (n < L) {
                 if ((err = launch_tgemm<T>(g, taps_n, N, F, nullptr, U, dst, bd, b0, nb, c->flag, st, planes)) != cudaSuccess)
                     return err;
-                if ((err = launch_dhop<T>(g, N, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st)) != cudaSuccess)
+                if ((err = launch_dhop<T>(g, N, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st, dplanes, c->flag)) != cudaSuccess)
                     return err;
             } else {
                 if ((err = launch_bandconv<T>(g, taps_n, N, F, nullptr, dst, bd, b0, nb, st)) != cudaSuccess) return err;
@@ -693,7 +701,7 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
                     err = launch_tgemm<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, U, dst, bd,
                                           b0, nb, c->flag, st, planes);
                     if (err != cudaSuccess) return err;
-                    if ((err = launch_dhop<T>(g, (int)Pm, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st)) !=
+                    if ((err = launch_dhop<T>(g, (int)Pm, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st, dplanes, c->flag)) !=
                         cudaSuccess)
                         return err;
                 } else {

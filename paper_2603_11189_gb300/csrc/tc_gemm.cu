@@ -477,6 +477,131 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
     if (warp == 0) tc::tmem_free(tmem, TN);
 }
 
+// Vertex hop on the tensor cores: X[b][c][n][p] = sum_a D0_n[c][a] Y[b][a][n][p].  Per site n it is
+// a GEMM with the columns p as rows (M = 128 per tile), the output channels as N and the input
+// channels as K; D0_n is the B operand, staged once per CTA, which then loops over column tiles.
+// Each FP32 value is split into NPL BF16 planes (3 for FP32 accuracy, 1 for BF16).
+template <int D, int NPL>
+__global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__restrict__ Dm, long long dm_ss,
+                                                 const float *__restrict__ Yin, float *__restrict__ Xo,
+                                                 unsigned *__restrict__ flag) {
+    extern __shared__ __align__(1024) unsigned char smd[];
+    constexpr int ns = D / 16;
+    constexpr uint32_t aslab = 128 * 32, bslab = D * 32, aplane = ns * aslab, bplane = ns * bslab;
+    constexpr uint32_t cols = D < 32 ? 32 : D;
+    unsigned char *Ap = smd;                       // NPL planes: rows p, K a
+    unsigned char *Bp = Ap + NPL * aplane;         // NPL planes: rows c, K a
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Bp + NPL * bplane);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    int *s_ok = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n = blockIdx.y;
+    const long long bl = blockIdx.z;
+    const float *Dn = Dm + bl * dm_ss + (long long)n * D * D;
+    for (int q = tid; q < D * (D / 8); q += blockDim.x) {
+        const int c = q / (D / 8), k8 = (q % (D / 8)) * 8;
+        tc::stage8_planes<NPL>(Bp, bplane, (uint32_t)(k8 >> 4) * bslab + tc::canon(c, k8 & 15), Dn + (long long)c * D + k8);
+    }
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *s_ok = 1;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, cols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16(128, D);
+    const int ntiles = (P + 127) / 128;
+    uint32_t phase = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int p = t * 128 + tid;
+        const bool valid = p < P;
+        // A operand in groups of 16 input channels (16 loads in flight per thread); the group's
+        // base pointer advances with the loop so that no per-channel address is kept live.
+        const long long cs = (long long)N * P;        // channel stride of Y and X
+        const float *yg = Yin + (bl * D * N + n) * (long long)P + (valid ? p : 0);
+#pragma unroll 1
+        for (int a16 = 0; a16 < D; a16 += 16, yg += 16 * cs) {
+            float v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = valid ? yg[u * cs] : 0.f;
+            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 0), v);
+            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 8), v + 8);
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+            // Descriptors are formed per slab (not hoisted out of the tile loop: 2 * ns * NPL^2
+            // 64-bit values would take the registers the staging needs).
+#pragma unroll 1
+            for (int s = 0; s < ns; ++s)
+#pragma unroll
+                for (int pa = 0; pa < NPL; ++pa)
+#pragma unroll
+                    for (int pb = 0; pa + pb < NPL; ++pb)
+                        tc::mma_bf16(tmem, tc::desc(tc::smem_u32(Ap + pa * aplane + s * aslab)),
+                                     tc::desc(tc::smem_u32(Bp + pb * bplane + s * bslab)), idesc,
+                                     (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+            tc::commit(mbar);
+        }
+        if (warp == 0 && !tc::wait(mbar, phase) && lane == 0) *s_ok = 0;
+        phase ^= 1u;
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (!*s_ok) break;
+        float *xg = Xo + (bl * D * N + n) * (long long)P + (valid ? p : 0);
+#pragma unroll 1
+        for (int c8 = 0; c8 < D; c8 += 8, xg += 8 * cs) {
+            float f[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c8, f);
+            if (valid)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) xg[u * cs] = f[u];
+        }
+        // The next tile overwrites the A operand and the accumulator.
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
+    if (!*s_ok && tid == 0 && flag) atomicOr(flag, 8u);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, cols);
+}
+
+template <int D, int NPL>
+static cudaError_t launch_dhop_tc_dp(int N, int P, const float *Dm, long long dm_ss, const float *Y, float *Xo, int nb,
+                                     unsigned *flag, cudaStream_t st) {
+    constexpr int ns = D / 16;
+    const size_t smem = (size_t)NPL * ns * (128 * 32 + D * 32) + 32;
+    const int ntiles = (P + 127) / 128;
+    const int cg = ntiles < 4 ? ntiles : 4;      // column tiles split over at most 4 CTAs per site
+    dim3 grid((unsigned)cg, (unsigned)N, (unsigned)nb);
+    cudaError_t err = cudaFuncSetAttribute(k_dhop_tc<D, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_dhop", st);
+        k_dhop_tc<D, NPL><<<grid, 128, smem, st>>>(N, P, Dm, dm_ss, Y, Xo, flag);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dhop_tc(int d, int N, int P, const float *Dm, long long dm_ss, const float *Y, float *Xo, int nb,
+                           int planes, unsigned *flag, cudaStream_t st) {
+    if (d == 32 && planes == 3) return launch_dhop_tc_dp<32, 3>(N, P, Dm, dm_ss, Y, Xo, nb, flag, st);
+    if (d == 32 && planes == 1) return launch_dhop_tc_dp<32, 1>(N, P, Dm, dm_ss, Y, Xo, nb, flag, st);
+    if (d == 64 && planes == 3) return launch_dhop_tc_dp<64, 3>(N, P, Dm, dm_ss, Y, Xo, nb, flag, st);
+    if (d == 64 && planes == 1) return launch_dhop_tc_dp<64, 1>(N, P, Dm, dm_ss, Y, Xo, nb, flag, st);
+    if (d == 16 && planes == 3) return launch_dhop_tc_dp<16, 3>(N, P, Dm, dm_ss, Y, Xo, nb, flag, st);
+    if (d == 16 && planes == 1) return launch_dhop_tc_dp<16, 1>(N, P, Dm, dm_ss, Y, Xo, nb, flag, st);
+    return cudaErrorNotSupported;
+}
+
 static size_t tgemm_genp_smem(int N, int d, int npl) {
     const int nch = (N + kTcK - 1) / kTcK;
     const size_t B = (size_t)npl * 4 * 128 * 32;
