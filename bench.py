@@ -163,46 +163,27 @@ def link_conv_flops(N, L, d, B):
     return total
 
 
-def dhop_bytes(N, L, d, B, fused=False):
+def dhop_bytes(N, L, d, B):
     """HBM bytes of the vertex hops of one step: every hop reads the probe field of
     one layer and writes it back mixed (d N P values each way; P = N probes for the
-    embedding chain, N d for a source chain from layer m, which makes L - 2 - m hops).
-    With `fused`, the last hop of each chain runs in k_dhop_band and is not counted."""
-    last = 1 if fused else 0
-    per = max(0, L - 2 - last) * 2 * d * N * N * 4
-    per += sum(max(0, L - 2 - m - last) * 2 * d * N * (N * d) * 4 for m in range(1, L - 1))
+    embedding chain, N d for a source chain from layer m, which makes L - 2 - m hops)."""
+    per = (L - 2) * 2 * d * N * N * 4
+    per += sum((L - 2 - m) * 2 * d * N * (N * d) * 4 for m in range(1, L - 1))
     return B * per
 
 
-def bandconv_bytes(N, L, d, w, B, WF=None, fused=False):
+def bandconv_bytes(N, L, d, w, B, WF=None):
     """HBM bytes of the last-layer band convolutions of one step: the probe field
     read once (the embedding chain and every source chain with a full hop; the
     chain from layer L-2 generates its operand from D0 and the taps) plus the
-    band entries written.  With `fused`, only the chain from layer L-2 runs here."""
+    band entries written."""
     W = 2 * w + 1
     WF = W if WF is None else WF
     Rk, Rl = WF - 1, WF - 1 - w
-    per = 0 if fused else d * N * N * 4 + N * (2 * Rl + 1) * d * 4
+    per = d * N * N * 4 + N * (2 * Rl + 1) * d * 4
     for m in range(1, L - 1):
-        if fused and m < L - 2:
-            continue
         src = d * N * (N * d) * 4 if m < L - 2 else N * d * d * 4
         per += src + N * (2 * Rk + 1) * d * d * 4
-    return B * per
-
-
-def dhop_band_bytes(N, L, d, w, B, WF=None):
-    """HBM bytes of the fused last hops (k_dhop_band) of one step: the hop input of
-    every chain with at least one vertex hop read once (d N P values; the D0 matrices
-    and taps are L2-resident) plus its layer-L band written."""
-    W = 2 * w + 1
-    WF = W if WF is None else WF
-    Rk, Rl = WF - 1, WF - 1 - w
-    per = 0
-    if L >= 3:
-        per += d * N * N * 4 + N * (2 * Rl + 1) * d * 4
-    for m in range(1, L - 2):
-        per += d * N * (N * d) * 4 + N * (2 * Rk + 1) * d * d * 4
     return B * per
 
 
@@ -548,11 +529,8 @@ def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
                               "frac": ach / peak, "traffic": None, "launches": launches,
                               "ms_per_launch": tot_s * 1e3 / launches,
                               "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"}
-    fused = any(k.endswith("links/k_dhop_band") for k in prof)
-    for fam_name, kname, byts in (("links_dhop", "k_dhop", dhop_bytes(N, desc.L, desc.d, Bs, fused)),
-                                  ("links_bandconv", "k_bandconv",
-                                   bandconv_bytes(N, desc.L, desc.d, desc.w, Bs, fused=fused)),
-                                  ("links_dhop_band", "k_dhop_band", dhop_band_bytes(N, desc.L, desc.d, desc.w, Bs))):
+    for fam_name, kname, byts in (("links_dhop", "k_dhop", dhop_bytes(N, desc.L, desc.d, Bs)),
+                                  ("links_bandconv", "k_bandconv", bandconv_bytes(N, desc.L, desc.d, desc.w, Bs))):
         ks = [(k, v) for k, v in prof.items() if k.endswith("links/" + kname)]
         if ks:
             launches = sum(v[0] for _, v in ks)
@@ -596,8 +574,6 @@ def roofline(prof, steps, desc, N, Bs, peaks, src, clocks):
         return fam["links_dhop"], fam
     if name.endswith("links/k_bandconv") and "links_bandconv" in fam:
         return fam["links_bandconv"], fam
-    if name.endswith("links/k_dhop_band") and "links_dhop_band" in fam:
-        return fam["links_dhop_band"], fam
     if name.endswith("links/k_tgemm_tc") and "links_tgemm_tc" in fam:
         return fam["links_tgemm_tc"], fam
     return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,

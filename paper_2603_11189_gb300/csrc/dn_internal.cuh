@@ -221,14 +221,6 @@ cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float
 cudaError_t launch_dhop_tc(int d, int N, int P, const float *Dm, long long dm_ss, const float *Y, float *Xo, int nb,
                            int planes, unsigned *flag, cudaStream_t st);
 
-// Last hop of a link chain with the layer-L band convolution fused into its epilogue
-// (tc_gemm.cu): band[b][k+dl][R-dl][a][c'] = sum_n g_{k+dl-n,a} sum_c D_n[a][c] Y[b][c][n][p]
-// for p = k nsrc + c'; taps are the layer-L taps [R][d].  cudaErrorNotSupported when the
-// shape does not fit (d not 32 or 64, 2R+1 > 9, tap table too large for shared memory).
-cudaError_t launch_dhop_band_tc(int d, int N, int P, int periodic, const float *Dm, long long dm_ss, const float *Y,
-                                const float *taps, float *band, long long bss, long long brs, long long bos, int bR,
-                                int bns, long long b0, int nb, int planes, unsigned *flag, cudaStream_t st);
-
 // Tensor-core forward pass (forward_tc.cu); activations channel-major h[c][n B + b].
 bool forward_tc_ok(const Geom &g);
 cudaError_t launch_h0_cm(const Geom &g, const int8_t *spins, const float *e, int B, float *h, cudaStream_t st);

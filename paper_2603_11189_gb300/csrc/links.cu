@@ -608,21 +608,6 @@ static cudaError_t launch_bandconv(const Geom &g, const T *taps, int P, const T 
     return launch_bandconv_gen<T, false>(g, taps, P, X, GenSrc<T>{nullptr, nullptr, 0}, band, bd, b0, nb, st);
 }
 
-// Vertex hop of the last layer with the layer-L band convolution fused (FP32/BF16 tensor-core
-// kernel); cudaErrorNotSupported otherwise, and the caller runs the hop and the band separately.
-template <typename T>
-static cudaError_t launch_dhop_band(const Geom &g, int P, const T *Dm, long long dm_ss, const T *Y, const T *taps,
-                                    T *band, const BandDst &bd, long long b0, int nb, cudaStream_t st, int planes,
-                                    unsigned *flag) {
-    if constexpr (sizeof(T) == 4) {
-        return launch_dhop_band_tc(g.d, g.N, P, g.periodic, reinterpret_cast<const float *>(Dm), dm_ss,
-                                   reinterpret_cast<const float *>(Y), reinterpret_cast<const float *>(taps),
-                                   reinterpret_cast<float *>(band), bd.ss, bd.rs, bd.os, bd.R, bd.nsrc, b0, nb, planes,
-                                   flag, st);
-    }
-    return cudaErrorNotSupported;
-}
-
 template <typename T>
 static cudaError_t launch_dhop(const Geom &g, int P, const T *Dm, long long dm_ss, const T *Y, T *Xo, int nb,
                                cudaStream_t st, int planes = 3, unsigned *flag = nullptr) {
@@ -698,15 +683,6 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
             if (n < L) {
                 if ((err = launch_tgemm<T>(g, taps_n, N, F, nullptr, U, dst, bd, b0, nb, c->flag, st, planes)) != cudaSuccess)
                     return err;
-                if (n == L - 1) {
-                    // Last hop: the layer-L band straight from the vertex hop when the shape allows.
-                    BandDst bl_{bd.ss, bd.rs, bd.os, c->Rl, 1};
-                    err = launch_dhop_band<T>(g, N, Dm + (long long)(n - 1) * N * dd, dm_ss, U, pl.taps + (long long)(L - 1) * g.R * d,
-                                              ell + (long long)(L - 2) * N * nRl * d, bl_, b0, nb, st, dplanes, c->flag);
-                    if (err == cudaSuccess) break;
-                    if (err != cudaErrorNotSupported) return err;
-                    cudaGetLastError();
-                }
                 if ((err = launch_dhop<T>(g, N, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st, dplanes, c->flag)) != cudaSuccess)
                     return err;
             } else {
@@ -725,16 +701,6 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
                     err = launch_tgemm<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, U, dst, bd,
                                           b0, nb, c->flag, st, planes);
                     if (err != cudaSuccess) return err;
-                    if (n == L - 1) {
-                        BandDst bk{bd.ss, bd.rs, bd.os, c->Rk, d};
-                        err = launch_dhop_band<T>(g, (int)Pm, Dm + (long long)(n - 1) * N * dd, dm_ss, U,
-                                                  pl.taps + (long long)(L - 1) * g.R * d,
-                                                  K + (long long)pair_index(L, msrc) * N * nRk * dd, bk, b0, nb, st, dplanes,
-                                                  c->flag);
-                        if (err == cudaSuccess) break;
-                        if (err != cudaErrorNotSupported) return err;
-                        cudaGetLastError();
-                    }
                     if ((err = launch_dhop<T>(g, (int)Pm, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st, dplanes, c->flag)) !=
                         cudaSuccess)
                         return err;

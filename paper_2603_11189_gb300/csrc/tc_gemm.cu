@@ -602,266 +602,6 @@ cudaError_t launch_dhop_tc(int d, int N, int P, const float *Dm, long long dm_ss
     return cudaErrorNotSupported;
 }
 
-// Last hop of a link chain, fused: the vertex hop F[a][n][p] = sum_c D_n[a][c] Y[c][n][p] of
-// layer L-1 (tensor cores, as k_dhop_tc) feeds the layer-L band convolution
-// band[k+dl][R-dl][a][c'] = sum_n g^(L)_{k+dl-n,a} F[a][n][p], p = k nsrc + c', in the epilogue,
-// so F is never written.  One CTA per (sample, 128-column tile, 32 output channels) walks the
-// sites n in order:
-//  * Y rows of site n + S - 1 stream into a ring of S shared-memory slots by cp.async (each
-//    thread copies and later reads back its own column, so the ring needs no barrier);
-//  * the MMAs of site n (operands double-buffered in shared memory, accumulator
-//    double-buffered in TMEM) overlap the band update of site n - 1;
-//  * thread (h, p) keeps the 2R+1 band sums of column p for the 16 channels a0 + 16 h + j in
-//    registers; the taps of the 32 channels sit in a shared table (row stride 36 floats,
-//    only the rows the tile's source sites reach, wrapped for rings).
-// The sums run over n in increasing order with one FMA per term, as in the unfused band
-// convolution.
-constexpr int kDbG = 32;          // output channels per CTA
-constexpr int kDbTapStride = 36;  // floats per tap row
-
-__host__ __device__ inline int dhop_band_tap_rows(int N, int bR, int bns) { return 127 / bns + 2 + 2 * bR + N; }
-
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_u32(dst)), "l"(src), "r"(ok ? 4 : 0)
-                 : "memory");
-}
-
-template <int D, int NPL, int NB, int S>
-__global__ void __launch_bounds__(256, 1) k_dhop_band_tc(int N, int P, int periodic, const float *__restrict__ Dm,
-                                                         long long dm_ss, const float *__restrict__ Yin,
-                                                         const float *__restrict__ taps, float *__restrict__ band,
-                                                         long long bss, long long brs, long long bos, int bR, int bns,
-                                                         long long b0, unsigned *__restrict__ flag) {
-    extern __shared__ __align__(1024) unsigned char smb[];
-    constexpr int ns = D / 16, HC = D / 2;
-    constexpr uint32_t aslab = 128 * 32, aplane = ns * aslab, abuf = NPL * aplane;
-    constexpr uint32_t bslab = kDbG * 32, bplane = ns * bslab, bbuf = NPL * bplane;
-    unsigned char *Ab = smb;                                    // [2][NPL planes]: rows p, K c
-    unsigned char *Bb = Ab + 2 * abuf;                          // [2][NPL planes]: rows a - a0, K c
-    float *ring = reinterpret_cast<float *>(Bb + 2 * bbuf);     // [S][D][128]: Y rows of a site
-    float *gt = ring + S * D * 128;                             // [rows][36]
-    const int gt_rows = dhop_band_tap_rows(N, bR, bns);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(gt + (size_t)gt_rows * kDbTapStride);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
-    int *s_ok = reinterpret_cast<int *>(tslot + 1);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int pr = tid & 127, h = tid >> 7;          // column of the tile; channel half
-    constexpr int ngrp = D / kDbG;
-    const int tile = blockIdx.x / ngrp, a0 = (blockIdx.x - tile * ngrp) * kDbG;
-    const long long bl = blockIdx.z;
-    const int p = tile * 128 + pr;
-    const bool valid = p < P;
-    const int k_lo = tile * 128 / bns;
-    const int k = valid ? p / bns : k_lo, cq = valid ? p - k * bns : 0;
-    // Tap row t holds g_r for r = t + k_lo - R - (N - 1).
-    for (int q = tid; q < gt_rows * kDbG; q += blockDim.x) {
-        const int row = q / kDbG, j = q - row * kDbG;
-        int r = row + k_lo - bR - (N - 1);
-        float v = 0.f;
-        if (periodic) {
-            r = ((r % N) + N) % N;
-            v = taps[(long long)r * D + a0 + j];
-        } else if (r > -N && r < N) {
-            v = taps[(long long)(r + N - 1) * D + a0 + j];
-        }
-        gt[row * kDbTapStride + j] = v;
-    }
-    if (tid == 0) {
-        tc::mbar_init(mbar, 1);
-        tc::mbar_init(mbar + 1, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;");
-        *s_ok = 1;
-    }
-    if (warp == 0) tc::tmem_alloc(tslot, 2 * kDbG);
-    const long long cs = (long long)N * P;           // channel stride of Y
-    const float *ycol = Yin + (bl * D + h * HC) * cs + (valid ? p : 0);   // site 0, channel h HC
-    float *rcol = ring + h * HC * 128 + pr;                             // slot 0, channel h HC
-    auto fetch = [&](int m) {   // Y rows of site m into slot m % S (own column, own channels)
-        const float *src = ycol + (long long)m * P;
-        float *dst = rcol + (m % S) * (D * 128);
-#pragma unroll 4
-        for (int c = 0; c < HC; ++c, src += cs) cp_async4(dst + c * 128, src, valid);
-    };
-#pragma unroll
-    for (int m = 0; m < S - 1; ++m) {
-        if (m < N) fetch(m);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    const float *Db = Dm + bl * dm_ss + (long long)a0 * D;              // D_0 rows a0..
-    // B staging: thread tid < kDbG * D / 8 stages 8 K values of one row of D_n.
-    const bool bst = tid < kDbG * (D / 8);
-    const int brow = tid / (D / 8), bk8 = (tid - brow * (D / 8)) * 8;
-    float dv[8];
-    if (bst) {
-        const float4 x0 = __ldg(reinterpret_cast<const float4 *>(Db + brow * D + bk8));
-        const float4 x1 = __ldg(reinterpret_cast<const float4 *>(Db + brow * D + bk8 + 4));
-        dv[0] = x0.x; dv[1] = x0.y; dv[2] = x0.z; dv[3] = x0.w;
-        dv[4] = x1.x; dv[5] = x1.y; dv[6] = x1.z; dv[7] = x1.w;
-    }
-    float acc[NB][16];
-#pragma unroll
-    for (int q = 0; q < NB; ++q)
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[q][j] = 0.f;
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t idesc = tc::idesc_bf16(128, kDbG);
-    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 16);
-    const float *gk0 = gt + (size_t)(k - k_lo + N - 1) * kDbTapStride + h * 16;   // row of q = 0 at site 0
-    // Band update of site m from TMEM buffer m & 1 (its MMAs were committed to mbar[m & 1]).
-    auto band_step = [&](int m) {
-        const int b = m & 1;
-        if (!tc::wait(mbar + b, (uint32_t)(m >> 1) & 1u) && lane == 0) *s_ok = 0;
-        __syncwarp();
-        tc::fence_after();
-        float f[16];
-        tc::tmem_ld8(tl + (uint32_t)(b * kDbG), f);
-        tc::tmem_ld8(tl + (uint32_t)(b * kDbG + 8), f + 8);
-        const float *gk = gk0 - (size_t)m * kDbTapStride;
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            if (q > 2 * bR) break;
-            const float4 *w4 = reinterpret_cast<const float4 *>(gk + q * kDbTapStride);
-#pragma unroll
-            for (int j4 = 0; j4 < 4; ++j4) {
-                const float4 w = w4[j4];
-                acc[q][4 * j4 + 0] = fmaf(w.x, f[4 * j4 + 0], acc[q][4 * j4 + 0]);
-                acc[q][4 * j4 + 1] = fmaf(w.y, f[4 * j4 + 1], acc[q][4 * j4 + 1]);
-                acc[q][4 * j4 + 2] = fmaf(w.z, f[4 * j4 + 2], acc[q][4 * j4 + 2]);
-                acc[q][4 * j4 + 3] = fmaf(w.w, f[4 * j4 + 3], acc[q][4 * j4 + 3]);
-            }
-        }
-    };
-#pragma unroll 1
-    for (int n = 0; n < N; ++n) {
-        const int b = n & 1;
-        if (n + S - 1 < N) fetch(n + S - 1);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group %0;" ::"n"(S - 1) : "memory");
-        // Operands of site n into buffer b (the MMAs of site n - 2 that read it are complete:
-        // every warp waited for them in the band update of site n - 2).
-        unsigned char *Ap = Ab + b * abuf, *Bp = Bb + b * bbuf;
-        const float *rs = rcol + (n % S) * (D * 128);
-#pragma unroll
-        for (int c8 = 0; c8 < HC; c8 += 8) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = rs[(c8 + u) * 128];
-            const int c = h * HC + c8;
-            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(c >> 4) * aslab + tc::canon(pr, c & 15), v);
-        }
-        if (bst) {
-            tc::stage8_planes<NPL>(Bp, bplane, (uint32_t)(bk8 >> 4) * bslab + tc::canon(brow, bk8 & 15), dv);
-            if (n + 1 < N) {
-                const float *src = Db + (long long)(n + 1) * D * D + brow * D + bk8;
-                const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src));
-                const float4 x1 = __ldg(reinterpret_cast<const float4 *>(src + 4));
-                dv[0] = x0.x; dv[1] = x0.y; dv[2] = x0.z; dv[3] = x0.w;
-                dv[4] = x1.x; dv[5] = x1.y; dv[6] = x1.z; dv[7] = x1.w;
-            }
-        }
-        tc::fence_async_smem();
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-        if (!*s_ok) break;
-        if (tid == 0) {
-#pragma unroll 1
-            for (int s = 0; s < ns; ++s)
-#pragma unroll
-                for (int pa = 0; pa < NPL; ++pa)
-#pragma unroll
-                    for (int pb = 0; pa + pb < NPL; ++pb)
-                        tc::mma_bf16(tmem + (uint32_t)(b * kDbG), tc::desc(tc::smem_u32(Ap + pa * aplane + s * aslab)),
-                                     tc::desc(tc::smem_u32(Bp + pb * bplane + s * bslab)), idesc,
-                                     (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
-            tc::commit(mbar + b);
-        }
-        __syncwarp();
-        if (n > 0) band_step(n - 1);
-        tc::fence_before();
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (*s_ok) band_step(N - 1);
-    tc::fence_before();
-    __syncthreads();
-    const bool ok = *s_ok != 0;
-    if (valid) {
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            if (q > 2 * bR) break;
-            const int dl = q - bR;
-            int i = k + dl;
-            if (periodic) i = ((i % N) + N) % N;
-            else if (i < 0 || i >= N) continue;
-            float *dst = band + (b0 + bl) * bss + (long long)i * brs + (long long)(bR - dl) * bos +
-                         (long long)(a0 + h * 16) * bns + cq;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) dst[(long long)j * bns] = ok ? acc[q][j] : __int_as_float(0x7fc00000);
-        }
-    }
-    if (!ok && tid == 0 && flag) atomicOr(flag, 8u);
-    if (warp == 0) tc::tmem_free(tmem, 2 * kDbG);
-}
-
-static int dhop_band_stages(int D) { return D == 32 ? 3 : 2; }
-
-static size_t dhop_band_smem(int D, int NPL, int N, int bR, int bns) {
-    const size_t ab = 2 * (size_t)NPL * (D / 16) * (128 * 32 + kDbG * 32);
-    const size_t ring = (size_t)dhop_band_stages(D) * D * 128 * 4;
-    return ab + ring + (size_t)dhop_band_tap_rows(N, bR, bns) * kDbTapStride * 4 + 32;
-}
-
-template <int D, int NPL, int NB>
-static cudaError_t launch_dhop_band_p(int N, int P, int periodic, const float *Dm, long long dm_ss, const float *Y,
-                                      const float *taps, float *band, long long bss, long long brs, long long bos,
-                                      int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st) {
-    constexpr int S = D == 32 ? 3 : 2;
-    const size_t smem = dhop_band_smem(D, NPL, N, bR, bns);
-    if (smem > 227 * 1024) return cudaErrorNotSupported;
-    cudaError_t err =
-        cudaFuncSetAttribute(k_dhop_band_tc<D, NPL, NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    dim3 grid((unsigned)(((P + 127) / 128) * (D / kDbG)), 1, (unsigned)nb);
-    {
-        ProfScope _ps("k_dhop_band", st);
-        k_dhop_band_tc<D, NPL, NB, S><<<grid, 256, smem, st>>>(N, P, periodic, Dm, dm_ss, Y, taps, band, bss, brs,
-                                                                bos, bR, bns, b0, flag);
-    }
-    return cudaGetLastError();
-}
-
-template <int D, int NPL>
-static cudaError_t launch_dhop_band_dp(int N, int P, int periodic, const float *Dm, long long dm_ss, const float *Y,
-                                       const float *taps, float *band, long long bss, long long brs, long long bos,
-                                       int bR, int bns, long long b0, int nb, unsigned *flag, cudaStream_t st) {
-    const int nbw = 2 * bR + 1;
-    if (nbw <= 5)
-        return launch_dhop_band_p<D, NPL, 5>(N, P, periodic, Dm, dm_ss, Y, taps, band, bss, brs, bos, bR, bns, b0, nb,
-                                             flag, st);
-    if (nbw <= 9)
-        return launch_dhop_band_p<D, NPL, 9>(N, P, periodic, Dm, dm_ss, Y, taps, band, bss, brs, bos, bR, bns, b0, nb,
-                                             flag, st);
-    return cudaErrorNotSupported;
-}
-
-cudaError_t launch_dhop_band_tc(int d, int N, int P, int periodic, const float *Dm, long long dm_ss, const float *Y,
-                                const float *taps, float *band, long long bss, long long brs, long long bos, int bR,
-                                int bns, long long b0, int nb, int planes, unsigned *flag, cudaStream_t st) {
-    if (bR < 0 || bns < 1 || P % bns != 0 || N < 1 || P < 1) return cudaErrorNotSupported;
-    if (d == 32 && planes == 3)
-        return launch_dhop_band_dp<32, 3>(N, P, periodic, Dm, dm_ss, Y, taps, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
-    if (d == 32 && planes == 1)
-        return launch_dhop_band_dp<32, 1>(N, P, periodic, Dm, dm_ss, Y, taps, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
-    if (d == 64 && planes == 3)
-        return launch_dhop_band_dp<64, 3>(N, P, periodic, Dm, dm_ss, Y, taps, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
-    if (d == 64 && planes == 1)
-        return launch_dhop_band_dp<64, 1>(N, P, periodic, Dm, dm_ss, Y, taps, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
-    return cudaErrorNotSupported;
-}
-
 static size_t tgemm_genp_smem(int N, int d, int npl) {
     const int nch = (N + kTcK - 1) / kTcK;
     const size_t B = (size_t)npl * 4 * 128 * 32;
