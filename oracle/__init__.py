@@ -136,6 +136,18 @@ def logpsi(desc, params, spins: np.ndarray):
     return lp, om
 
 
+def grad_logpsi(desc, params, spins: np.ndarray):
+    """(log psi [B], d log psi / d theta [B][nparams]) by hand-written reverse mode."""
+    spins = np.ascontiguousarray(spins, dtype=np.int8)
+    B, N = spins.shape
+    lp = np.zeros(B)
+    g = np.zeros((B, nparams(desc)))
+    p = _p(params)
+    _load().or_grad_logpsi(ctypes.byref(_desc(desc)), _ptr(p), ctypes.c_int(N), _ptr(spins), ctypes.c_int(B),
+                           _ptr(lp), _ptr(g))
+    return lp, g
+
+
 def dlogpsi(desc, params, spins: np.ndarray, sample: np.ndarray, sites: np.ndarray) -> np.ndarray:
     """log psi(sigma') - log psi(sigma) for each flip set, by full recompute."""
     spins = np.ascontiguousarray(spins, dtype=np.int8)

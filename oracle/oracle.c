@@ -399,6 +399,311 @@ void or_dlogpsi(const or_desc *m, const double *p, int N, const int8_t *spins, i
     plan_free(&pl);
 }
 
+/* ------------------------------------------------ parameter derivatives -- */
+/* Per-configuration derivative of log psi with respect to every parameter (the
+ * log-derivatives O_k of the variational parameters used by the energy gradient and
+ * stochastic reconfiguration, Sec. "Variational Monte Carlo").  Plain reverse-mode
+ * differentiation of forward_one written out by hand, in the forward's order
+ * reversed; the result uses the parameter layout of the weights vector. */
+
+static double gelu_prime(double x) {
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * M_PI);
+}
+
+/* d J / d(S4 block) for J = sum_r dg[r][c] g[r][c] (taps layout of or_s4_taps).
+ * J is the real part of an analytic function F of each complex parameter z, so
+ * dJ/dRe z = Re F'(z) and dJ/dIm z = -Im F'(z). */
+static void s4_block_grad(const or_desc *m, const double *blk, int N, int periodic, const double *dg, double *gblk) {
+    int d = m->d, s = m->s;
+    double *glre = gblk, *glim = glre + d * s, *glogdt = glim + d * s;
+    double *gbre = glogdt + d, *gbim = gbre + d * s;
+    double *gcfre = gbim + d * s, *gcfim = gcfre + d * s;
+    double *gcbre = gcfim + d * s, *gcbim = gcbre + d * s;
+    const double *lre = blk, *lim = lre + d * s, *logdt = lim + d * s;
+    const double *bre = logdt + d, *bim = bre + d * s;
+    for (int c = 0; c < d; ++c) {
+        double dt = exp(logdt[c]);
+        double gdt = 0.0;
+        for (int n = 0; n < s; ++n) {
+            int k = c * s + n;
+            double complex lb, bb, cf, cb;
+            s4_mode(m, blk, c, n, &lb, &bb, &cf, &cb);
+            double complex lam = lre[k] + I * lim[k], Bc = bre[k] + I * bim[k];
+            double complex den = 1.0 - 0.5 * dt * lam;
+            double complex wf, wb, Q, E;   /* dF/dCf, dF/dCb, dF/dB_bar, dF/dlam_bar */
+            if (!periodic) {
+                double complex Gp = 0, Gm = 0, Hp = 0, Hm = 0;
+                for (int r = -(N - 1); r <= N - 1; ++r) {
+                    double x = dg[(size_t)(r + N - 1) * d + c];
+                    int q = r < 0 ? -r : r;
+                    double complex pw = cpow(lb, (double)q);
+                    double complex pw1 = q > 0 ? (double)q * cpow(lb, (double)(q - 1)) : 0.0;
+                    if (r >= 0) { Gp += x * pw; Hp += x * pw1; }
+                    else { Gm += x * pw; Hm += x * pw1; }
+                }
+                wf = bb * Gp;
+                wb = bb * Gm;
+                Q = cf * Gp + cb * Gm;
+                E = bb * (cf * Hp + cb * Hm);
+            } else {
+                double complex lN = cpow(lb, (double)N), inv = 1.0 / (1.0 - lN);
+                double complex Sf = 0, Sb = 0, Sf1 = 0, Sb1 = 0;
+                for (int r = 0; r < N; ++r) {
+                    double x = dg[(size_t)r * d + c];
+                    Sf += x * cpow(lb, (double)r);
+                    Sb += x * cpow(lb, (double)(N - r));
+                    if (r > 0) Sf1 += x * (double)r * cpow(lb, (double)(r - 1));
+                    Sb1 += x * (double)(N - r) * cpow(lb, (double)(N - r - 1));
+                }
+                double complex S = cf * Sf + cb * Sb, S1 = cf * Sf1 + cb * Sb1;
+                wf = bb * Sf * inv;
+                wb = bb * Sb * inv;
+                Q = S * inv;
+                E = bb * (S1 * inv + S * (double)N * cpow(lb, (double)(N - 1)) * inv * inv);
+            }
+            /* lam_bar = (1 + dt lam/2)/den, B_bar = dt B/den, den = 1 - dt lam/2 */
+            double complex den2 = den * den;
+            double complex dLam = E * dt / den2 + Q * dt * dt * Bc / (2.0 * den2);
+            double complex dB = Q * dt / den;
+            double complex dDt = E * lam / den2 + Q * Bc / den2;
+            glre[k] = creal(dLam);
+            glim[k] = -cimag(dLam);
+            gbre[k] = creal(dB);
+            gbim[k] = -cimag(dB);
+            gcfre[k] = creal(wf);
+            gcfim[k] = -cimag(wf);
+            gcbre[k] = creal(wb);
+            gcbim[k] = -cimag(wb);
+            gdt += creal(dDt);
+        }
+        glogdt[c] = gdt * dt;
+    }
+}
+
+typedef struct {
+    double *s4, *kappa, *beta, *W1, *b1, *W2, *b2, *U, *V;
+} layer_grad_view;
+
+static layer_grad_view view_layer_grad(const or_desc *m, double *p, int l) {
+    layer_view v = view_layer(m, p, l);
+    layer_grad_view g = {(double *)v.s4, (double *)v.kappa, (double *)v.beta, (double *)v.W1, (double *)v.b1,
+                         (double *)v.W2, (double *)v.b2, (double *)v.U, (double *)v.V};
+    return g;
+}
+
+/* log psi of one configuration and its derivative with respect to all parameters. */
+static double grad_one(const or_desc *m, const double *p, const or_plan *pl, const int8_t *sp, double *grad) {
+    int N = pl->N, d = m->d, dh = m->dh, L = m->L, w = m->w, R = pl->R;
+    size_t Nd = (size_t)N * d, Ndh = (size_t)N * dh;
+    double *h = (double *)calloc((size_t)(L + 1) * Nd, sizeof(double));   /* h^(0..L) */
+    double *u = (double *)calloc((size_t)L * Nd, sizeof(double));         /* u^(1..L) */
+    double *y = (double *)calloc((size_t)L * Nd, sizeof(double));
+    double *chi = (double *)calloc((size_t)L * Nd, sizeof(double));
+    double *phi = (double *)calloc((size_t)L * Ndh, sizeof(double));
+    double *z = (double *)calloc((size_t)L * Ndh, sizeof(double));        /* W1 phi + b1 */
+    double *dh_ = (double *)calloc(Nd, sizeof(double)), *du = (double *)calloc(Nd, sizeof(double));
+    double *dg = (double *)calloc((size_t)R * d, sizeof(double));
+    double *domega = (double *)calloc(Nd, sizeof(double));
+    double *tmp = (double *)calloc((size_t)3 * (d > dh ? d : dh), sizeof(double));
+    double *pool = (double *)malloc(sizeof(double) * (size_t)d), *acol = (double *)malloc(sizeof(double) * (size_t)d);
+    double fp[64];
+    const double *e = final_e(m, p), *A = final_A(m, p);
+    memset(grad, 0, sizeof(double) * (size_t)or_nparams(m));
+
+    /* forward, keeping every intermediate */
+    for (int i = 0; i < N; ++i)
+        for (int c = 0; c < d; ++c) h[(size_t)i * d + c] = e[c] * (double)sp[i];
+    for (int l = 1; l <= L; ++l) {
+        layer_view v = view_layer(m, p, l);
+        const double *g = pl->taps + (size_t)(l - 1) * R * d;
+        const double *hp = h + (size_t)(l - 1) * Nd;
+        double *ul = u + (size_t)(l - 1) * Nd, *yl = y + (size_t)(l - 1) * Nd, *cl = chi + (size_t)(l - 1) * Nd;
+        double *hl = h + (size_t)l * Nd, *pf = phi + (size_t)(l - 1) * Ndh, *zl = z + (size_t)(l - 1) * Ndh;
+        for (int i = 0; i < N; ++i)
+            for (int c = 0; c < d; ++c) {
+                double acc = 0;
+                for (int j = 0; j < N; ++j) {
+                    double gr = m->periodic ? g[(size_t)(((i - j) % N + N) % N) * d + c] : g[(size_t)(i - j + N - 1) * d + c];
+                    acc += gr * hp[(size_t)j * d + c];
+                }
+                ul[(size_t)i * d + c] = acc;
+            }
+        for (int i = 0; i < N; ++i) {
+            double *ph = pf + (size_t)i * dh, *zz = zl + (size_t)i * dh, *ch = cl + (size_t)i * d;
+            for (int f = 0; f < dh; ++f) {
+                double acc = v.beta[f];
+                for (int r = -w; r <= w; ++r) acc += v.kappa[(r + w) * dh + f] * spin_at(m, sp, N, i + r);
+                ph[f] = acc;
+            }
+            for (int f = 0; f < dh; ++f) {
+                double acc = v.b1[f];
+                for (int q = 0; q < dh; ++q) acc += v.W1[f * dh + q] * ph[q];
+                zz[f] = acc;
+            }
+            for (int c = 0; c < d; ++c) {
+                double acc = v.b2[c];
+                for (int f = 0; f < dh; ++f) acc += v.W2[c * dh + f] * gelu(zz[f]);
+                ch[c] = acc;
+            }
+            for (int a = 0; a < d; ++a) {
+                double acc = 0;
+                for (int b = 0; b < d; ++b) acc += v.V[a * d + b] * ul[(size_t)i * d + b];
+                yl[(size_t)i * d + a] = acc;
+            }
+            for (int a = 0; a < d; ++a) {
+                double acc = 0;
+                for (int b = 0; b < d; ++b) acc += v.U[a * d + b] * ch[b] * yl[(size_t)i * d + b];
+                hl[(size_t)i * d + a] = acc;
+            }
+        }
+    }
+    for (int c = 0; c < d; ++c) {
+        nsum acc = {0, 0};
+        for (int l = 0; l <= L; ++l)
+            for (int i = 0; i < N; ++i) nsum_add(&acc, pl->omega[(size_t)i * d + c] * h[(size_t)l * Nd + (size_t)i * d + c]);
+        pool[c] = acc.sum + acc.comp;
+    }
+    double logpsi = 0;
+    for (int k = 0; k < m->dout; ++k) {
+        double acc = 0;
+        for (int c = 0; c < d; ++c) acc += A[c * m->dout + k] * pool[c];
+        logpsi += (m->fkind == 0) ? log_cosh(acc) : acc;
+        fp[k] = (m->fkind == 0) ? tanh(acc) : 1.0;
+    }
+
+    /* readout: dA, the coefficient a_c of the pooled sum, d omega */
+    double *gA = grad + (final_A(m, p) - p);
+    for (int c = 0; c < d; ++c) {
+        double acc = 0;
+        for (int k = 0; k < m->dout; ++k) {
+            gA[c * m->dout + k] = pool[c] * fp[k];
+            acc += A[c * m->dout + k] * fp[k];
+        }
+        acol[c] = acc;
+    }
+    for (int i = 0; i < N; ++i)
+        for (int c = 0; c < d; ++c) {
+            double acc = 0;
+            for (int l = 0; l <= L; ++l) acc += h[(size_t)l * Nd + (size_t)i * d + c];
+            domega[(size_t)i * d + c] = acol[c] * acc;
+        }
+    /* layers in reverse */
+    for (int i = 0; i < N; ++i)
+        for (int c = 0; c < d; ++c) dh_[(size_t)i * d + c] = pl->omega[(size_t)i * d + c] * acol[c];
+    for (int l = L; l >= 1; --l) {
+        layer_view v = view_layer(m, p, l);
+        layer_grad_view gv = view_layer_grad(m, grad, l);
+        const double *g = pl->taps + (size_t)(l - 1) * R * d;
+        const double *hp = h + (size_t)(l - 1) * Nd;
+        const double *ul = u + (size_t)(l - 1) * Nd, *yl = y + (size_t)(l - 1) * Nd, *cl = chi + (size_t)(l - 1) * Nd;
+        const double *pf = phi + (size_t)(l - 1) * Ndh, *zl = z + (size_t)(l - 1) * Ndh;
+        double *dt_ = tmp, *dchi = tmp + d, *dy = tmp + 2 * d;
+        for (int i = 0; i < N; ++i) {
+            const double *dhi = dh_ + (size_t)i * d, *ch = cl + (size_t)i * d, *yi = yl + (size_t)i * d;
+            /* h_i = U (chi_i . y_i) */
+            for (int b = 0; b < d; ++b) {
+                double acc = 0;
+                for (int a = 0; a < d; ++a) {
+                    acc += v.U[a * d + b] * dhi[a];
+                    gv.U[a * d + b] += dhi[a] * ch[b] * yi[b];
+                }
+                dt_[b] = acc;
+            }
+            for (int b = 0; b < d; ++b) {
+                dchi[b] = dt_[b] * yi[b];
+                dy[b] = dt_[b] * ch[b];
+            }
+            /* y_i = V u_i */
+            for (int b = 0; b < d; ++b) {
+                double acc = 0;
+                for (int a = 0; a < d; ++a) {
+                    acc += v.V[a * d + b] * dy[a];
+                    gv.V[a * d + b] += dy[a] * ul[(size_t)i * d + b];
+                }
+                du[(size_t)i * d + b] = acc;
+            }
+            /* chi_i = W2 gelu(z_i) + b2, z_i = W1 phi_i + b1, phi_i = sum_r kappa_r sigma_{i+r} + beta */
+            const double *zz = zl + (size_t)i * dh, *ph = pf + (size_t)i * dh;
+            double *dz = (double *)malloc(sizeof(double) * (size_t)dh), *dphi = (double *)malloc(sizeof(double) * (size_t)dh);
+            for (int c = 0; c < d; ++c) gv.b2[c] += dchi[c];
+            for (int f = 0; f < dh; ++f) {
+                double acc = 0, gz = gelu(zz[f]);
+                for (int c = 0; c < d; ++c) {
+                    gv.W2[c * dh + f] += dchi[c] * gz;
+                    acc += v.W2[c * dh + f] * dchi[c];
+                }
+                dz[f] = acc * gelu_prime(zz[f]);
+            }
+            for (int f = 0; f < dh; ++f) {
+                gv.b1[f] += dz[f];
+                for (int q = 0; q < dh; ++q) gv.W1[f * dh + q] += dz[f] * ph[q];
+            }
+            for (int q = 0; q < dh; ++q) {
+                double acc = 0;
+                for (int f = 0; f < dh; ++f) acc += v.W1[f * dh + q] * dz[f];
+                dphi[q] = acc;
+            }
+            for (int q = 0; q < dh; ++q) {
+                gv.beta[q] += dphi[q];
+                for (int r = -w; r <= w; ++r) gv.kappa[(r + w) * dh + q] += dphi[q] * spin_at(m, sp, N, i + r);
+            }
+            free(dz);
+            free(dphi);
+        }
+        /* u = G h^(l-1): taps and the field below */
+        memset(dg, 0, sizeof(double) * (size_t)R * d);
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j)
+                for (int c = 0; c < d; ++c) {
+                    size_t row = m->periodic ? (size_t)(((i - j) % N + N) % N) : (size_t)(i - j + N - 1);
+                    dg[row * d + c] += du[(size_t)i * d + c] * hp[(size_t)j * d + c];
+                }
+        s4_block_grad(m, v.s4, N, m->periodic, dg, gv.s4);
+        for (int j = 0; j < N; ++j)
+            for (int c = 0; c < d; ++c) {
+                double acc = pl->omega[(size_t)j * d + c] * acol[c];
+                for (int i = 0; i < N; ++i) {
+                    double gr = m->periodic ? g[(size_t)(((i - j) % N + N) % N) * d + c] : g[(size_t)(i - j + N - 1) * d + c];
+                    acc += gr * du[(size_t)i * d + c];
+                }
+                dh_[(size_t)j * d + c] = acc;
+            }
+    }
+    /* h^(0) = e sigma */
+    double *ge = grad + (final_e(m, p) - p);
+    for (int c = 0; c < d; ++c) {
+        double acc = 0;
+        for (int i = 0; i < N; ++i) acc += dh_[(size_t)i * d + c] * (double)sp[i];
+        ge[c] = acc;
+    }
+    /* omega_{i,c} = (1/N) sum_k g^f_{k-i,c} */
+    memset(dg, 0, sizeof(double) * (size_t)R * d);
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < N; ++k)
+            for (int c = 0; c < d; ++c) {
+                size_t row = m->periodic ? (size_t)(((k - i) % N + N) % N) : (size_t)(k - i + N - 1);
+                dg[row * d + c] += domega[(size_t)i * d + c] / N;
+            }
+    s4_block_grad(m, final_s4(m, p), N, m->periodic, dg, grad + (final_s4(m, p) - p));
+    free(h); free(u); free(y); free(chi); free(phi); free(z); free(dh_); free(du); free(dg); free(domega); free(tmp);
+    free(pool); free(acol);
+    return logpsi;
+}
+
+/* log psi [B] and d log psi / d theta [B][nparams] (OpenMP over samples). */
+void or_grad_logpsi(const or_desc *m, const double *p, int N, const int8_t *spins, int B, double *logpsi,
+                    double *grad) {
+    or_plan pl;
+    plan_make(m, p, N, &pl);
+    size_t np = (size_t)or_nparams(m);
+#pragma omp parallel for schedule(dynamic)
+    for (int b = 0; b < B; ++b) {
+        double lp = grad_one(m, p, &pl, spins + (size_t)b * N, grad + (size_t)b * np);
+        if (logpsi) logpsi[b] = lp;
+    }
+    plan_free(&pl);
+}
+
 /* ---------------------------------------------------------- Hamiltonians -- */
 
 static double tfim_coupling(const or_ham *H, int N, int i, int j) {
