@@ -206,6 +206,41 @@ dn_status dn_recompute_flip_ratios(dn_model *model, int N, const int8_t *spins_d
 dn_status dn_full_forward_noalloc(const dn_model *model, int N, const int8_t *spins_dev, int B, dn_precision prec,
                                   void *stream, double *logpsi_dev, double *Omega_dev);
 
+/* Length of the parameter vector of a model (n_params of dn_model_create); 0 for NULL. */
+size_t dn_model_nparams(const dn_model *model);
+
+/* Per-configuration log-derivatives of the wave function with respect to every
+ * parameter, O[b][k] = d log psi(sigma_b) / d theta_k (the variational
+ * derivatives of the energy gradient and of stochastic reconfiguration, Sec.
+ * "Variational Monte Carlo"; Eq. wavefunc differentiated through every layer,
+ * the S4 kernels through their discretisation, App. "Details on the
+ * implementation of the DysonNet block"):
+ *   spins_dev [B][N] int8, each +1 or -1;
+ *   prec DN_FP64 or DN_FP32 (DN_BF16: DN_EUNSUPPORTED);
+ *   logpsi_dev [B] float64 (may be NULL);
+ *   O_dev [B][n_params] (may be NULL): float64 for DN_FP64, float32 for DN_FP32,
+ *     k in the layout of the parameter vector given to dn_model_create();
+ *   w_dev [B] float64 and vjp_dev [n_params] float64, both NULL or both set:
+ *     vjp = sum_b w_b O[b] (the vector-Jacobian product of a backward pass;
+ *     computed without O_dev when O_dev is NULL).
+ * At least one output must be given.  Samples are processed in chunks bounded
+ * by an internal memory budget.  The call synchronises `stream` at its end.
+ * Errors: DN_EINVAL (bad arguments, spins not +-1), DN_EUNSUPPORTED, DN_ENOMEM, DN_ECUDA. */
+dn_status dn_logpsi_grad(dn_model *model, int N, const int8_t *spins_dev, int B, dn_precision prec, void *stream,
+                         double *logpsi_dev, void *O_dev, const double *w_dev, double *vjp_dev);
+
+/* Stochastic-reconfiguration matrices (Sec. "Variational Monte Carlo") from the
+ * log-derivatives O_dev [B][n_params] of dn_logpsi_grad() (float64 for DN_FP64,
+ * float32 for DN_FP32), centred over the samples, Oc = O - mean_b O:
+ *   gram_dev [B][B] float64 (may be NULL): Oc Oc^T / B, the sample-space form whose
+ *     size does not grow with the parameter count;
+ *   s_dev [nk][nk] float64 (may be NULL): Oc[:, k0:k0+nk]^T Oc[:, k0:k0+nk] / B, the
+ *     parameter-space matrix of a contiguous block of parameters.
+ * Products accumulate in the precision of O and are folded into float64 every 512
+ * terms.  Errors: DN_EINVAL, DN_ENOMEM, DN_ECUDA. */
+dn_status dn_sr_matrices(const void *O_dev, int B, size_t n_params, dn_precision prec, void *stream, double *gram_dev,
+                         size_t k0, int nk, double *s_dev);
+
 /* Wait for `stream`, then report the cache's sticky device flag:
  * DN_OK, DN_EINVAL (invalid spins or flip sites were seen), DN_ECUDA. */
 dn_status dn_cache_check(const dn_cache *cache, void *stream);

@@ -148,6 +148,22 @@ def grad_logpsi(desc, params, spins: np.ndarray):
     return lp, g
 
 
+def sr_matrices(O: np.ndarray, block=None):
+    """Stochastic-reconfiguration matrices of log-derivatives O [B][P] (Sec. "Variational Monte
+    Carlo"), centred over the samples, Oc = O - mean_b O: (Oc Oc^T / B, and for block = (k0, nk)
+    Oc[:, k0:k0+nk]^T Oc[:, k0:k0+nk] / B or None).  Plain FP64 matrix products."""
+    O = np.asarray(O, dtype=np.float64)
+    B = O.shape[0]
+    Oc = O - O.mean(axis=0, keepdims=True)
+    G = Oc @ Oc.T / B
+    S = None
+    if block is not None:
+        k0, nk = block
+        Ob = Oc[:, k0:k0 + nk]
+        S = Ob.T @ Ob / B
+    return G, S
+
+
 def dlogpsi(desc, params, spins: np.ndarray, sample: np.ndarray, sites: np.ndarray) -> np.ndarray:
     """log psi(sigma') - log psi(sigma) for each flip set, by full recompute."""
     spins = np.ascontiguousarray(spins, dtype=np.int8)

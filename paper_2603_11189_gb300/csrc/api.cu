@@ -369,6 +369,108 @@ void full_forward(dn_model *m, int N, const int8_t *spins_dev, int B, int prec, 
     run_forward<T>(m, pl, w, N, spins_dev, B, chi.as<T>(), nullptr, Omega, logpsi, prec, nullptr, st);
 }
 
+// Upper bound on the activations kept by dn_logpsi_grad() per chunk of samples.
+constexpr size_t kGradBudget = size_t(6) << 30;
+
+// Per-configuration log-derivatives (grad.cu): forward keeping every activation, then the
+// reverse pass layer by layer.  O [B][P] in T (may be null when only vjp is wanted);
+// vjp [P] (may be null) += sum_b wts_b O_b.
+template <typename T>
+void run_grad(dn_model *m, int N, const int8_t *spins_dev, int B, cudaStream_t st, double *logpsi, T *O,
+              const double *wts, double *vjp) {
+    dn::ProfPhase phase("grad");
+    const dn::Plan<T> &pl = ensure_plan<T>(m, N, st);
+    const dn::Weights<T> &w = ensure_weights<T>(m, st);
+    const dn::Geom g = dn::geom_of(m, N);
+    const dn_model_desc &D = m->desc;
+    const int L = g.L, d = g.d, dh = g.dh, W = g.W, dout = g.dout, R = g.R;
+    const long long P = (long long)m->nparams, field = (long long)N * d, fh = (long long)N * dh;
+    const size_t per = sizeof(T) * ((size_t)(4 * L + 1) * field + 6 * field + 4 * fh + (size_t)N * W +
+                                    (size_t)R * d + (O ? 0 : (size_t)P)) +
+                       sizeof(double) * ((size_t)(L + 1) * d + d + dout + 1) + (size_t)N + 4096;
+    const int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, kGradBudget / per));
+    DevBuf flag(sizeof(unsigned), st);
+    DevBuf pw((size_t)(L + 1) * d * D.s * (N + 1) * 2 * sizeof(T), st);
+    ck(cudaMemsetAsync(flag.p, 0, sizeof(unsigned), st));
+    ck(dn::launch_s4_pow<T>(m, N, pw.as<T>(), st));
+    if (vjp) ck(cudaMemsetAsync(vjp, 0, (size_t)P * sizeof(double), st));
+    dn::Carve cv;
+    const size_t o_sp = cv.take<int8_t>((size_t)nb * N), o_chi = cv.take<T>((size_t)nb * L * field),
+                 o_h = cv.take<T>((size_t)(L + 1) * nb * field), o_u = cv.take<T>((size_t)L * nb * field),
+                 o_y = cv.take<T>((size_t)L * nb * field), o_dH = cv.take<T>((size_t)nb * field),
+                 o_dU = cv.take<T>((size_t)nb * field), o_dT = cv.take<T>((size_t)nb * field),
+                 o_tY = cv.take<T>((size_t)nb * field), o_dy = cv.take<T>((size_t)nb * field),
+                 o_dchi = cv.take<T>((size_t)nb * field), o_a1 = cv.take<T>((size_t)nb * fh),
+                 o_phi = cv.take<T>((size_t)nb * fh), o_dz = cv.take<T>((size_t)nb * fh),
+                 o_dphi = cv.take<T>((size_t)nb * fh), o_win = cv.take<T>((size_t)nb * N * W),
+                 o_dg = cv.take<T>((size_t)nb * R * d), o_pool = cv.take<double>((size_t)nb * (L + 1) * d),
+                 o_om = cv.take<double>((size_t)nb * dout), o_lp = cv.take<double>((size_t)nb),
+                 o_ac = cv.take<double>((size_t)nb * d), o_O = cv.take<T>(O ? 0 : (size_t)nb * P);
+    DevBuf work(cv.off, st);
+    int8_t *sp = work.as<int8_t>(o_sp);
+    T *chi = work.as<T>(o_chi), *h = work.as<T>(o_h), *u = work.as<T>(o_u), *y = work.as<T>(o_y);
+    T *dH = work.as<T>(o_dH), *dU = work.as<T>(o_dU), *dT = work.as<T>(o_dT), *dg = work.as<T>(o_dg);
+    dn::GradScratch<T> scr{work.as<T>(o_tY), work.as<T>(o_dy), work.as<T>(o_dchi), work.as<T>(o_a1),
+                           work.as<T>(o_phi), work.as<T>(o_dz), work.as<T>(o_dphi), work.as<T>(o_win)};
+    double *pooled = work.as<double>(o_pool), *Omega = work.as<double>(o_om), *acoef = work.as<double>(o_ac);
+    const long long pstride = (long long)(L + 1) * d;
+    const long long s4 = m->s4_size, ls = m->layer_size;
+    const long long offA = (long long)L * ls + s4, offE = offA + (long long)d * dout;
+    for (int b0 = 0; b0 < B; b0 += nb) {
+        const int n = std::min(nb, B - b0);
+        const long long nf = (long long)n * field;
+        T *Ob = O ? O + (long long)b0 * P : work.as<T>(o_O);
+        double *lp = logpsi ? logpsi + b0 : work.as<double>(o_lp);
+        auto F1 = [&](T *base) { return dn::Fields<T>{base, field, 0, 1}; };
+        // forward, every activation kept (layer-major h^(0..L), u, y)
+        ck(dn::launch_check_spins(spins_dev + (long long)b0 * N, (long long)n * N, sp, flag.as<unsigned>(), st));
+        ck(dn::launch_chi<T>(g, w, sp, n, chi, st));
+        ck(dn::launch_h0<T>(N, d, n, sp, w.e, h, st));
+        ck(dn::launch_pool0<T>(g, sp, w.e, pl.omega, n, pooled, pstride, st));
+        for (int l = 1; l <= L; ++l) {
+            const T *taps_l = pl.taps + (long long)(l - 1) * R * d;
+            ck(dn::launch_conv<T>(g, taps_l, F1(h + (l - 1) * nf), nullptr, w.e, F1(u + (l - 1) * nf), n, false,
+                                  nullptr, nullptr, st));
+            ck(dn::launch_mix<T>(g, l, w, chi, (long long)L * field, 1, 0, F1(u + (l - 1) * nf), F1(h + l * nf),
+                                 F1(y + (l - 1) * nf), pl.omega, pooled + (long long)l * d, pstride, n, false, st));
+        }
+        ck(dn::launch_readout(g, D.f_kind, m->A64, pooled, L + 1, n, sp, Omega, lp, st));
+        if (!O && !vjp) continue;
+        // reverse pass
+        ck(dn::launch_grad_readout<T>(g, D.f_kind, L + 1, n, m->A64, pooled, Omega, acoef, Ob, P, offA, st));
+        ck(dn::launch_add_omega<T>(g, n, pl.omega, acoef, dH, false, st));
+        for (int l = L; l >= 1; --l) {
+            const long long base = (long long)(l - 1) * ls;
+            const long long oK = base + s4, oBeta = oK + (long long)W * dh, oW1 = oBeta + dh, oB1 = oW1 + (long long)dh * dh,
+                            oW2 = oB1 + dh, oB2 = oW2 + (long long)d * dh, oU = oB2 + d, oV = oU + (long long)d * d;
+            ck(dn::launch_mix<T>(g, l, w, chi, (long long)L * field, 1, 0, F1(dH), F1(dU), F1(dT), nullptr, nullptr, 0,
+                                 n, true, st));
+            ck(dn::launch_mlp_back<T>(g, l, w, sp, n, chi, y + (l - 1) * nf, dT, scr, st));
+            ck(dn::launch_outer<T>(N, n, d, d, dH, scr.tY, Ob, P, oU, d, st));
+            ck(dn::launch_outer<T>(N, n, d, d, scr.dy, u + (l - 1) * nf, Ob, P, oV, d, st));
+            ck(dn::launch_outer<T>(N, n, d, dh, scr.dchi, scr.a1, Ob, P, oW2, dh, st));
+            ck(dn::launch_outer<T>(N, n, d, 1, scr.dchi, nullptr, Ob, P, oB2, 1, st));
+            ck(dn::launch_outer<T>(N, n, dh, dh, scr.dz, scr.phi, Ob, P, oW1, dh, st));
+            ck(dn::launch_outer<T>(N, n, dh, 1, scr.dz, nullptr, Ob, P, oB1, 1, st));
+            ck(dn::launch_outer<T>(N, n, W, dh, scr.win, scr.dphi, Ob, P, oK, dh, st));
+            ck(dn::launch_outer<T>(N, n, dh, 1, scr.dphi, nullptr, Ob, P, oBeta, 1, st));
+            ck(dn::launch_dtaps<T>(g, n, dU, h + (l - 1) * nf, dg, st));
+            ck(dn::launch_s4_grad<T>(m, l - 1, N, n, dg, pw.as<T>(), Ob, P, st));
+            ck(dn::launch_conv<T>(g, pl.taps + (long long)(l - 1) * R * d, F1(dU), nullptr, nullptr, F1(dH), n, true,
+                                  nullptr, nullptr, st));
+            ck(dn::launch_add_omega<T>(g, n, pl.omega, acoef, dH, true, st));
+        }
+        ck(dn::launch_grad_e<T>(g, n, dH, sp, Ob, P, offE, st));
+        ck(dn::launch_grad_gf<T>(g, n, h, nf, acoef, dg, st));
+        ck(dn::launch_s4_grad<T>(m, L, N, n, dg, pw.as<T>(), Ob, P, st));
+        if (vjp) ck(dn::launch_vjp<T>(Ob, wts + b0, n, P, vjp, st));
+    }
+    unsigned bad = 0;
+    ck(cudaMemcpyAsync(&bad, flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
+    if (bad) throw Fail{DN_EINVAL};
+}
+
 }  // namespace
 
 namespace dn {
@@ -637,6 +739,43 @@ dn_status dn_full_forward(dn_model *m, int N, const int8_t *spins_dev, int B, dn
     return guard([&]() -> dn_status {
         if (prec == DN_FP64) full_forward<double>(m, N, spins_dev, B, prec, st, logpsi_dev, Omega_dev);
         else full_forward<float>(m, N, spins_dev, B, prec, st, logpsi_dev, Omega_dev);
+        return DN_OK;
+    });
+}
+
+size_t dn_model_nparams(const dn_model *m) { return m ? m->nparams : 0; }
+
+dn_status dn_logpsi_grad(dn_model *m, int N, const int8_t *spins_dev, int B, dn_precision prec, void *stream,
+                         double *logpsi_dev, void *O_dev, const double *w_dev, double *vjp_dev) {
+    if (!m || !spins_dev || N < 1 || B < 1) return DN_EINVAL;
+    if ((w_dev == nullptr) != (vjp_dev == nullptr)) return DN_EINVAL;
+    if (!O_dev && !vjp_dev && !logpsi_dev) return DN_EINVAL;
+    if (!prec_valid(prec)) return DN_EINVAL;
+    if (prec == DN_BF16) return DN_EUNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return guard([&]() -> dn_status {
+        if (prec == DN_FP64) run_grad<double>(m, N, spins_dev, B, st, logpsi_dev, static_cast<double *>(O_dev), w_dev, vjp_dev);
+        else run_grad<float>(m, N, spins_dev, B, st, logpsi_dev, static_cast<float *>(O_dev), w_dev, vjp_dev);
+        return DN_OK;
+    });
+}
+
+dn_status dn_sr_matrices(const void *O_dev, int B, size_t n_params, dn_precision prec, void *stream, double *gram_dev,
+                         size_t k0, int nk, double *s_dev) {
+    if (!O_dev || B < 1 || n_params < 1) return DN_EINVAL;
+    if (prec != DN_FP64 && prec != DN_FP32) return DN_EINVAL;
+    if (!gram_dev && !s_dev) return DN_EINVAL;
+    if (s_dev && (nk < 1 || k0 + (size_t)nk > n_params)) return DN_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return guard([&]() -> dn_status {
+        dn::ProfPhase phase("sr");
+        DevBuf mean(n_params * sizeof(double), st);
+        if (prec == DN_FP64)
+            ck(dn::launch_sr_matrices<double>(static_cast<const double *>(O_dev), B, (long long)n_params, gram_dev,
+                                              (long long)k0, s_dev ? nk : 0, s_dev, mean.as<double>(), st));
+        else
+            ck(dn::launch_sr_matrices<float>(static_cast<const float *>(O_dev), B, (long long)n_params, gram_dev,
+                                             (long long)k0, s_dev ? nk : 0, s_dev, mean.as<double>(), st));
         return DN_OK;
     });
 }

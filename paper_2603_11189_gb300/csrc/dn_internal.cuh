@@ -221,6 +221,49 @@ cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float
 cudaError_t launch_dhop_tc(int d, int N, int P, const float *Dm, long long dm_ss, const float *Y, float *Xo, int nb,
                            int planes, unsigned *flag, cudaStream_t st);
 
+// Reverse pass for the parameter log-derivatives (grad.cu).  Operands of the per-sample
+// outer-product sums of one layer, [B][N][.] each.
+template <typename T>
+struct GradScratch {
+    T *tY, *dy, *dchi;          // chi . y, chi . dt, y . dt      [B][N][d]
+    T *a1, *phi, *dz, *dphi;    // GELU(z), phi, dz, W1^T dz      [B][N][dh]
+    T *win;                     // sigma_{i+r}, r = -w..w         [B][N][W]
+};
+template <typename T>
+cudaError_t launch_h0(int N, int d, int B, const int8_t *spins, const T *e, T *h, cudaStream_t st);
+template <typename T>
+cudaError_t launch_grad_readout(const Geom &g, int f_kind, int npool, int B, const double *A64, const double *pooled,
+                                const double *Omega, double *acoef, T *O, long long P, long long offA, cudaStream_t st);
+template <typename T>
+cudaError_t launch_add_omega(const Geom &g, int B, const T *omega, const double *acoef, T *dst, bool add,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_mlp_back(const Geom &g, int l, const Weights<T> &w, const int8_t *spins, int B, const T *chi,
+                            const T *y, const T *dtv, const GradScratch<T> &s, cudaStream_t st);
+template <typename T>
+cudaError_t launch_outer(int N, int B, int dx, int dyc, const T *X, const T *Y, T *O, long long P, long long off,
+                         int ldo, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dtaps(const Geom &g, int B, const T *du, const T *h, T *dg, cudaStream_t st);
+template <typename T>
+cudaError_t launch_grad_e(const Geom &g, int B, const T *dh0, const int8_t *spins, T *O, long long P, long long off,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_grad_gf(const Geom &g, int B, const T *h, long long lstride, const double *acoef, T *dgf,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launch_s4_pow(const dn_model *m, int N, T *pw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_vjp(const T *O, const double *wts, int B, long long P, double *vjp, cudaStream_t st);
+// Column means of O [B][P] into mean [P]; gram [B][B] = Oc Oc^T / B and Ssub [nk][nk] =
+// Oc[:, k0:k0+nk]^T Oc[:, k0:k0+nk] / B with Oc the centred O (either may be null).
+template <typename T>
+cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, long long k0, int nk, double *Ssub,
+                               double *mean, cudaStream_t st);
+template <typename T>
+cudaError_t launch_s4_grad(const dn_model *m, int blk, int N, int B, const T *dg, const T *pw, T *O, long long P,
+                           cudaStream_t st);
+
 // Tensor-core forward pass (forward_tc.cu); activations channel-major h[c][n B + b].
 bool forward_tc_ok(const Geom &g);
 cudaError_t launch_h0_cm(const Geom &g, const int8_t *spins, const float *e, int B, float *h, cudaStream_t st);

@@ -90,6 +90,9 @@ def _lib():
         "dn_server_wait": (i32, [vp, ctypes.c_ulonglong, dbl, ctypes.POINTER(dbl)]),
         "dn_server_get_stats": (i32, [vp, ctypes.POINTER(ServerStats)]),
         "dn_server_destroy": (None, [vp]),
+        "dn_model_nparams": (sz, [vp]),
+        "dn_logpsi_grad": (i32, [vp, i32, vp, i32, i32, vp, vp, vp, vp, vp]),
+        "dn_sr_matrices": (i32, [vp, i32, sz, i32, vp, vp, sz, i32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -106,7 +109,7 @@ def exported_symbols():
             "dn_recompute_flip_ratios", "dn_cache_check", "dn_cache_info", "dn_cache_tensor", "dn_cache_destroy",
             "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable",
             "dn_profile_count", "dn_profile_get", "dn_server_create", "dn_server_set_chain", "dn_server_submit",
-            "dn_server_wait", "dn_server_get_stats", "dn_server_destroy"]
+            "dn_server_wait", "dn_server_get_stats", "dn_server_destroy", "dn_model_nparams", "dn_logpsi_grad", "dn_sr_matrices"]
 
 
 def _check(status: int, what: str):
@@ -227,6 +230,26 @@ class Model:
         _check(_lib().dn_full_forward(self._h, N, _ptr(spins), B, PRECISIONS[prec], _stream(stream), _ptr(lp),
                                       _ptr(om)), "dn_full_forward")
         return (lp, om) if with_omega else lp
+
+    @property
+    def nparams(self) -> int:
+        return int(_lib().dn_model_nparams(self._h))
+
+    def logpsi_grad(self, spins: torch.Tensor, prec="fp32", stream=None, weights: torch.Tensor | None = None,
+                    with_O: bool = True):
+        """(log psi [B] f64, O [B][nparams] or None, vjp [nparams] f64 or None): the per-configuration
+        log-derivatives d log psi / d theta and, with `weights` [B] f64, sum_b w_b O_b."""
+        B, N = spins.shape
+        dev = spins.device
+        lp = torch.empty(B, dtype=torch.float64, device=dev)
+        O = None
+        if with_O:
+            O = torch.empty((B, self.nparams), dtype=torch.float64 if prec == "fp64" else torch.float32, device=dev)
+        vjp = torch.empty(self.nparams, dtype=torch.float64, device=dev) if weights is not None else None
+        w = weights.to(device=dev, dtype=torch.float64).contiguous() if weights is not None else None
+        _check(_lib().dn_logpsi_grad(self._h, N, _ptr(spins), B, PRECISIONS[prec], _stream(stream), _ptr(lp),
+                                     _ptr(O), _ptr(w), _ptr(vjp)), "dn_logpsi_grad")
+        return lp, O, vjp
 
     def recompute_flip_ratios(self, spins: torch.Tensor, sample: torch.Tensor, sites: torch.Tensor, prec="fp32",
                               stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
@@ -352,3 +375,43 @@ class Server:
         if self._h:
             _lib().dn_server_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+
+def sr_matrices(O: torch.Tensor, gram: bool = True, block: tuple[int, int] | None = None, stream=None):
+    """(Oc Oc^T / B or None, Oc[:, k0:k0+nk]^T Oc[:, k0:k0+nk] / B or None) for the log-derivatives
+    O [B][nparams] (float64 or float32), Oc = O - mean over the samples."""
+    B, P = O.shape
+    prec = "fp64" if O.dtype == torch.float64 else "fp32"
+    G = torch.empty((B, B), dtype=torch.float64, device=O.device) if gram else None
+    S, k0, nk = None, 0, 0
+    if block is not None:
+        k0, nk = block
+        S = torch.empty((nk, nk), dtype=torch.float64, device=O.device)
+    _check(_lib().dn_sr_matrices(_ptr(O), B, P, PRECISIONS[prec], _stream(stream), _ptr(G), k0, nk, _ptr(S)),
+           "dn_sr_matrices")
+    return G, S
+
+
+class LogPsi(torch.autograd.Function):
+    """log psi(sigma_b) [B] as a differentiable function of the parameter vector theta
+    (float64, the layout of dn_model_create).  The backward pass is the library's reverse
+    pass: grad_theta = sum_b grad_out_b d log psi(sigma_b) / d theta (dn_logpsi_grad).
+
+        lp = LogPsi.apply(theta, desc, spins, "fp64")
+    """
+
+    @staticmethod
+    def forward(ctx, theta, desc, spins, prec="fp64"):
+        model = Model(desc, theta.detach().cpu().numpy())
+        lp = model.full_forward(spins, prec=prec)
+        ctx.model, ctx.prec = model, prec
+        ctx.save_for_backward(spins)
+        ctx.theta_device = theta.device
+        return lp.to(theta.device)
+
+    @staticmethod
+    def backward(ctx, grad_lp):
+        (spins,) = ctx.saved_tensors
+        _, _, vjp = ctx.model.logpsi_grad(spins, prec=ctx.prec, weights=grad_lp.to(spins.device), with_O=False)
+        ctx.model.close()
+        return vjp.to(ctx.theta_device), None, None, None

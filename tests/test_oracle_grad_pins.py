@@ -81,3 +81,27 @@ def test_grad_homogeneity(periodic):
     rest = lp - (pool0 @ A).sum(axis=1)
     assert np.all(np.abs(euler(["l1.cf_re", "l1.cf_im", "l1.cb_re", "l1.cb_im"]) - rest) <= tol)
     assert np.all(np.abs(euler(["l1.b_re", "l1.b_im"]) - rest) <= tol)
+
+
+def test_sr_matrices_spectra_and_trace():
+    """The sample-space Gram Oc Oc^T / B and the parameter-space S = Oc^T Oc / B share their
+    non-zero eigenvalues (both are squares of the singular values of Oc / sqrt(B)); both are
+    symmetric positive semi-definite, the Gram annihilates the all-ones vector (centring), and
+    trace = sum_b |Oc_b|^2 / B."""
+    desc, p, sl = _desc_params(0, 0, L=2, seed=13)
+    spins = synth.spins_uniform(6, 8, 5)
+    _, O = oracle.grad_logpsi(desc, p, spins)
+    P = O.shape[1]
+    G, S = oracle.sr_matrices(O, block=(0, P))
+    B = O.shape[0]
+    assert np.allclose(G, G.T, atol=0) and np.allclose(S, S.T, rtol=1e-13, atol=1e-13 * np.abs(S).max())
+    eg = np.sort(np.linalg.eigvalsh(G))[::-1]
+    es = np.sort(np.linalg.eigvalsh(S))[::-1][:B]
+    assert eg.min() >= -1e-10 * eg.max()
+    assert np.allclose(eg[:B - 1], es[:B - 1], rtol=1e-9, atol=1e-10 * eg.max())
+    assert abs(eg[-1]) <= 1e-10 * eg.max()
+    assert np.abs(G @ np.ones(B)).max() <= 1e-10 * np.abs(G).max()
+    Oc = O - O.mean(axis=0)
+    assert np.isclose(np.trace(G), (Oc * Oc).sum() / B, rtol=1e-12)
+    _, Sb = oracle.sr_matrices(O, block=(5, 7))
+    assert np.allclose(Sb, S[5:12, 5:12], rtol=1e-12, atol=1e-14 * np.abs(S).max())
