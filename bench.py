@@ -258,6 +258,59 @@ def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128):
             "speedup_incl_cache_build_over_recompute": e2e_rate / rc_rate}
 
 
+def measure_grad(dn, synth, torch, barrier, lib, B=4096, reps=2):
+    """Forward + backward of the N = 256, 6-layer, 64-channel, 64-mode long-range TFIM
+    model (FP32, open chain): per-configuration log-derivatives O [B][P] of B configurations
+    (dn_logpsi_grad), then the sample-space SR matrix Oc Oc^T / B (dn_sr_matrices).
+    Per-kernel device times from the library's tracing."""
+    N = 256
+    desc = synth.ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
+    params = synth.init_params(desc, 1004, a_scale=10.0)
+    model = dn.Model(desc, params)
+    spins = torch.from_numpy(synth.spins_uniform(B, N, 2004)).cuda()
+    P = model.nparams
+    O = torch.empty((B, P), dtype=torch.float32, device="cuda")
+    G = torch.empty((B, B), dtype=torch.float64, device="cuda")
+    lp = torch.empty(B, dtype=torch.float64, device="cuda")
+    ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    st = torch.cuda.current_stream().cuda_stream
+
+    def step():
+        dn._check(lib.dn_logpsi_grad(model._h, N, dn._ptr(spins), B, dn.PRECISIONS["fp32"], st, dn._ptr(lp),
+                                     dn._ptr(O), None, None), "dn_logpsi_grad")
+        ev1.record()
+        dn._check(lib.dn_sr_matrices(dn._ptr(O), B, P, dn.PRECISIONS["fp32"], st, dn._ptr(G), 0, 0, None),
+                  "dn_sr_matrices")
+
+    step()
+    torch.cuda.synchronize()
+    barrier()
+    lib.dn_profile_enable(1)
+    grad_ms = gram_ms = 0.0
+    for _ in range(reps):
+        ev0.record()
+        step()
+        ev2.record()
+        torch.cuda.synchronize()
+        grad_ms += ev0.elapsed_time(ev1) / reps
+        gram_ms += ev1.elapsed_time(ev2) / reps
+    prof = read_profile(lib)
+    lib.dn_profile_enable(0)
+    barrier()
+    model.close()
+    tot = sum(v[1] for v in prof.values()) or 1.0
+    kern = sorted(({"name": k, "launches": v[0] // reps, "ms_per_step": v[1] / reps, "share": v[1] / tot}
+                   for k, v in prof.items()), key=lambda r: -r["ms_per_step"])
+    gram_flop = 2.0 * B * B * P / 2            # symmetric half
+    return {"workload": "lr-TFIM N=256 open, DysonNet L=6 d=64 s=64 w=2 FP32, %d configurations, %d parameters"
+                        % (B, P),
+            "grad": {"value": B / (grad_ms / 1e3), "unit": "configurations/s (forward + all %d log-derivatives)" % P,
+                     "ms": grad_ms},
+            "sr_gram": {"ms": gram_ms, "tflops": gram_flop / (gram_ms / 1e3) / 1e12,
+                        "note": "Oc Oc^T / B, FP32 products folded into FP64 every 512 terms, CUDA cores"},
+            "kernels": kern[:12]}
+
+
 def measure_serving(dn, synth, n_req=160, rate=20.0, seed=4005):
     """Serving workload: Markov chains with N in {64, 128, 256, 512, 1024} (two each) of
     the 6-layer, 64-channel, 64-mode model (FP32), requests of 1-512 random single-flip
@@ -333,6 +386,8 @@ def main():
     ap.add_argument("--no-recompute", action="store_true")
     ap.add_argument("--no-n1024", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--grad-samples", type=int, default=4096)
     ap.add_argument("--n1024-chains", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -444,6 +499,7 @@ def main():
 
     n1024 = None if args.no_n1024 else measure_n1024(dn, synth, torch, barrier, args.n1024_chains)
     serving = None if args.no_serving else measure_serving(dn, synth)
+    grad = None if args.no_grad else measure_grad(dn, synth, torch, barrier, lib, B=args.grad_samples)
 
     peaks, src = _peaks()
     roof, families = roofline(prof, args.steps, desc, N, Bs, peaks, src, clocks)
@@ -467,6 +523,7 @@ def main():
         "cache_build_ms_per_step": build_ms,
         "recompute": recompute,
         "n1024": n1024,
+        "grad": grad,
         "serving": serving,
         "kernels": [{"name": k, "launches": n // args.steps, "ms_per_step": v / args.steps,
                      "share": v / total_k} for k, n, v in kernels[:16]],
