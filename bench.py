@@ -307,7 +307,7 @@ def measure_grad(dn, synth, torch, barrier, lib, B=4096, reps=2):
             "grad": {"value": B / (grad_ms / 1e3), "unit": "configurations/s (forward + all %d log-derivatives)" % P,
                      "ms": grad_ms},
             "sr_gram": {"ms": gram_ms, "tflops": gram_flop / (gram_ms / 1e3) / 1e12,
-                        "note": "Oc Oc^T / B, FP32 products folded into FP64 every 512 terms, CUDA cores"},
+                        "note": "Oc Oc^T / B, FP32 FMA on CUDA cores, two-level FP32 sums (512-term partials)"},
             "kernels": kern[:12]}
 
 

@@ -236,8 +236,8 @@ dn_status dn_logpsi_grad(dn_model *model, int N, const int8_t *spins_dev, int B,
  *     size does not grow with the parameter count;
  *   s_dev [nk][nk] float64 (may be NULL): Oc[:, k0:k0+nk]^T Oc[:, k0:k0+nk] / B, the
  *     parameter-space matrix of a contiguous block of parameters.
- * Products accumulate in the precision of O and are folded into float64 every 512
- * terms.  Errors: DN_EINVAL, DN_ENOMEM, DN_ECUDA. */
+ * Products accumulate in the precision of O (float32: partial sums of 512 terms added
+ * into a second float32 sum).  Errors: DN_EINVAL, DN_ENOMEM, DN_ECUDA. */
 dn_status dn_sr_matrices(const void *O_dev, int B, size_t n_params, dn_precision prec, void *stream, double *gram_dev,
                          size_t k0, int nk, double *s_dev);
 

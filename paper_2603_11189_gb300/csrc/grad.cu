@@ -95,19 +95,27 @@ __global__ void k_add_omega(int N, int d, long long B, const T *__restrict__ ome
 //   out: tY = chi . y, dy = chi . dt, dchi = y . dt  [B][N][d];
 //        a1 = GELU(z), phi, dz = (W2^T dchi) . GELU'(z), dphi = W1^T dz  [B][N][dh];
 //        win[B][N][W] = sigma_{i+r}, r = -w..w.
-constexpr int kMbTile = 16;
+// One CTA per (sample, tile of kMbTile sites).  W1^T and W2^T of the layer are staged in
+// shared memory once per CTA; the site-major operands are kept transposed ([k][site]) so
+// that a thread (output e, group of 8 sites) reads its 8 sites with two 16-byte loads
+// (the same address for the whole warp) and its weight row without bank conflicts.
+constexpr int kMbTile = 32, kMbSub = 8;
 
 template <typename T>
-__global__ void k_mlp_back(Geom g, int l, Weights<T> w, const int8_t *__restrict__ spins, const T *__restrict__ chi,
-                           const T *__restrict__ y, const T *__restrict__ dtv, T *__restrict__ tY, T *__restrict__ dy,
-                           T *__restrict__ dchi, T *__restrict__ a1, T *__restrict__ phi, T *__restrict__ dz,
-                           T *__restrict__ dphi, T *__restrict__ win) {
+__global__ void __launch_bounds__(256) k_mlp_back(Geom g, int l, Weights<T> w, const int8_t *__restrict__ spins,
+                                                  const T *__restrict__ chi, const T *__restrict__ y,
+                                                  const T *__restrict__ dtv, T *__restrict__ tY, T *__restrict__ dy,
+                                                  T *__restrict__ dchi, T *__restrict__ a1, T *__restrict__ phi,
+                                                  T *__restrict__ dz, T *__restrict__ dphi, T *__restrict__ win) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
-    T *sphi = reinterpret_cast<T *>(smraw);   // [tile][dh]
-    T *sz = sphi + kMbTile * dh;              // [tile][dh]
-    T *sdchi = sz + kMbTile * dh;             // [tile][d]
-    T *sdz = sdchi + kMbTile * d;             // [tile][dh]
+    // Row strides dh+1 and d+1: a warp reading along either index of the weights hits
+    // distinct banks.
+    T *W1s = reinterpret_cast<T *>(smraw);     // [f][e] = W1[e][f], row stride dh + 1
+    T *W2s = W1s + dh * (dh + 1);              // [e][c] = W2[c][e], row stride d + 1
+    T *phT = W2s + dh * (d + 1);               // [f][tile]
+    T *zT = phT + dh * kMbTile;                // [e][tile]  z, then dz
+    T *dcT = zT + dh * kMbTile;                // [c][tile]  dchi
     const int ntile = (N + kMbTile - 1) / kMbTile;
     const long long b = blockIdx.x / ntile;
     const int i0 = (int)(blockIdx.x % ntile) * kMbTile;
@@ -115,58 +123,103 @@ __global__ void k_mlp_back(Geom g, int l, Weights<T> w, const int8_t *__restrict
     const int8_t *sp = spins + b * N;
     const T *kap = w.kappa + (long long)(l - 1) * W * dh;
     const T *beta = w.beta + (long long)(l - 1) * dh;
-    const T *W1T = w.W1T + (long long)(l - 1) * dh * dh;
     const T *b1 = w.b1 + (long long)(l - 1) * dh;
-    const T *W2T = w.W2T + (long long)(l - 1) * dh * d;
+    for (int q = threadIdx.x; q < dh * dh; q += blockDim.x)
+        W1s[(q / dh) * (dh + 1) + q % dh] = w.W1T[(long long)(l - 1) * dh * dh + q];
+    for (int q = threadIdx.x; q < dh * d; q += blockDim.x)
+        W2s[(q / d) * (d + 1) + q % d] = w.W2T[(long long)(l - 1) * dh * d + q];
     const long long fb = (b * N + i0);          // first row of the tile in [B][N][.] arrays
     const T *chib = chi + ((b * L + (l - 1)) * N + i0) * d;
     auto spin = [&](int j) -> T {
         if (g.periodic) return (T)sp[((j % N) + N) % N];
         return (j >= 0 && j < N) ? (T)sp[j] : (T)0;
     };
-    for (int idx = threadIdx.x; idx < ns * dh; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < kMbTile * dh; idx += blockDim.x) {
         const int t = idx / dh, e = idx % dh, i = i0 + t;
-        T acc = beta[e];
-        for (int r = -wd; r <= wd; ++r) acc += kap[(r + wd) * dh + e] * spin(i + r);
-        sphi[t * dh + e] = acc;
-        phi[(fb + t) * dh + e] = acc;
+        T acc = 0;
+        if (t < ns) {
+            acc = beta[e];
+            for (int r = -wd; r <= wd; ++r) acc += kap[(r + wd) * dh + e] * spin(i + r);
+            phi[(fb + t) * dh + e] = acc;
+        }
+        phT[e * kMbTile + t] = acc;
     }
     for (int idx = threadIdx.x; idx < ns * W; idx += blockDim.x) {
         const int t = idx / W, r = idx % W;
         win[(fb + t) * W + r] = spin(i0 + t + r - wd);
     }
-    for (int idx = threadIdx.x; idx < ns * d; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < kMbTile * d; idx += blockDim.x) {
         const int t = idx / d, c = idx % d;
-        const long long o = (fb + t) * d + c;
-        const T yv = y[o], dv = dtv[o], xv = chib[(long long)t * d + c];
-        tY[o] = xv * yv;
-        dy[o] = xv * dv;
-        dchi[o] = yv * dv;
-        sdchi[t * d + c] = yv * dv;
+        T v = 0;
+        if (t < ns) {
+            const long long o = (fb + t) * d + c;
+            const T yv = y[o], dv = dtv[o], xv = chib[(long long)t * d + c];
+            tY[o] = xv * yv;
+            dy[o] = xv * dv;
+            v = yv * dv;
+            dchi[o] = v;
+        }
+        dcT[c * kMbTile + t] = v;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < ns * dh; idx += blockDim.x) {
-        const int t = idx / dh, e = idx % dh;
-        T acc = b1[e];
-        for (int f = 0; f < dh; ++f) acc += W1T[f * dh + e] * sphi[t * dh + f];
-        sz[t * dh + e] = acc;
-        a1[(fb + t) * dh + e] = gelu_t<T>(acc);
+    constexpr int nsub = kMbTile / kMbSub;
+    // z = W1 phi + b1 (into zT), a1 = GELU(z)
+    for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
+        const int e = q % dh, t0 = (q / dh) * kMbSub;
+        T acc[kMbSub];
+#pragma unroll
+        for (int u = 0; u < kMbSub; ++u) acc[u] = b1[e];
+        for (int f = 0; f < dh; ++f) {
+            const T wv = W1s[f * (dh + 1) + e];
+            const T *pp = phT + f * kMbTile + t0;
+#pragma unroll
+            for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kMbSub; ++u) {
+            zT[e * kMbTile + t0 + u] = acc[u];
+            if (t0 + u < ns) a1[(fb + t0 + u) * dh + e] = gelu_t<T>(acc[u]);
+        }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < ns * dh; idx += blockDim.x) {
-        const int t = idx / dh, e = idx % dh;
-        T acc = 0;
-        for (int c = 0; c < d; ++c) acc += W2T[e * d + c] * sdchi[t * d + c];
-        const T v = acc * gelu_prime_t<T>(sz[t * dh + e]);
-        sdz[t * dh + e] = v;
-        dz[(fb + t) * dh + e] = v;
+    // dz = (W2^T dchi) . GELU'(z) (in place of z)
+    for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
+        const int e = q % dh, t0 = (q / dh) * kMbSub;
+        T acc[kMbSub];
+#pragma unroll
+        for (int u = 0; u < kMbSub; ++u) acc[u] = 0;
+        for (int c = 0; c < d; ++c) {
+            const T wv = W2s[e * (d + 1) + c];
+            const T *pp = dcT + c * kMbTile + t0;
+#pragma unroll
+            for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kMbSub; ++u) {
+            const T v = acc[u] * gelu_prime_t<T>(zT[e * kMbTile + t0 + u]);
+            acc[u] = v;
+            if (t0 + u < ns) dz[(fb + t0 + u) * dh + e] = v;
+        }
+        // (e, t0) belongs to this thread alone: overwrite z with dz in place.
+#pragma unroll
+        for (int u = 0; u < kMbSub; ++u) zT[e * kMbTile + t0 + u] = acc[u];
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < ns * dh; idx += blockDim.x) {
-        const int t = idx / dh, f = idx % dh;
-        T acc = 0;
-        for (int e = 0; e < dh; ++e) acc += W1T[f * dh + e] * sdz[t * dh + e];
-        dphi[(fb + t) * dh + f] = acc;
+    // dphi = W1^T dz
+    for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
+        const int f = q % dh, t0 = (q / dh) * kMbSub;
+        T acc[kMbSub];
+#pragma unroll
+        for (int u = 0; u < kMbSub; ++u) acc[u] = 0;
+        for (int e = 0; e < dh; ++e) {
+            const T wv = W1s[f * (dh + 1) + e];
+            const T *pp = zT + e * kMbTile + t0;
+#pragma unroll
+            for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kMbSub; ++u)
+            if (t0 + u < ns) dphi[(fb + t0 + u) * dh + f] = acc[u];
     }
 }
 
@@ -501,18 +554,22 @@ __global__ void k_colmean(const T *__restrict__ O, int B, long long P, double *_
 }
 
 // S[a][c] = scale sum_k (X[a][k] - m_a|k) (X[c][k] - m_a|k) for a, c < n, with X[a][k] at
-// X + a sa + k sk; the mean is m[k] (mean_by_k) or m[a].  One CTA per 64 x 64 tile with c0 >= a0
-// (the other half is mirrored); K streams through shared memory 32 at a time.  Each thread
-// keeps a 4 x 4 block in T and folds it into FP64 every kGrFold terms.
-constexpr int kGrT = 64, kGrK = 32, kGrFold = 512;
+// X + a sa + k sk; the mean is m[k] (mean_by_k) or m[a].  One CTA per 128 x 128 tile with
+// c0 >= a0 (the other half is mirrored); K streams through shared memory 16 at a time.
+// Each thread keeps an 8 x 8 block in registers; in FP32 the block is added every kGrFold
+// terms into a second FP32 sum held in shared memory (two-level summation: the error grows
+// with sqrt(kGrFold) + sqrt(K / kGrFold) instead of sqrt(K)).
+constexpr int kGrT = 128, kGrK = 16, kGrFold = 512, kGrPad = kGrT + 4;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const T *__restrict__ X, long long sa, long long sk, int n, long long K,
                                               const double *__restrict__ m, int mean_by_k, double scale,
                                               double *__restrict__ S) {
-    __shared__ T xa[kGrK][kGrT + 1], xc[kGrK][kGrT + 1];
+    __shared__ __align__(16) T xa[kGrK][kGrPad];
+    __shared__ __align__(16) T xc[kGrK][kGrPad];
+    extern __shared__ __align__(16) unsigned char smfold[];
+    T *fold = reinterpret_cast<T *>(smfold);     // [64][blockDim]: thread-private second-level sums
     const int nt = (n + kGrT - 1) / kGrT;
-    // tile index -> (ta, tc) with tc >= ta
     int t = blockIdx.x, ta = 0;
     while (t >= nt - ta) {
         t -= nt - ta;
@@ -521,20 +578,20 @@ __global__ void __launch_bounds__(256) k_gram(const T *__restrict__ X, long long
     const int tc = ta + t;
     const int a0 = ta * kGrT, c0 = tc * kGrT;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    T acc[4][4];
-    double dacc[4][4];
+    constexpr bool kFold = sizeof(T) == 4;
+    T acc[8][8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            acc[i][j] = 0;
-            dacc[i][j] = 0.0;
-        }
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0;
+    if constexpr (kFold) {
+        for (int q = 0; q < 64; ++q) fold[q * blockDim.x + threadIdx.x] = 0;
+    }
     int since = 0;
     for (long long k0 = 0; k0 < K; k0 += kGrK) {
         for (int q = threadIdx.x; q < kGrK * kGrT; q += blockDim.x) {
             int kk, r;
-            if (sk == 1) {           // rows along the tile, K fastest in memory
+            if (sk == 1) {           // K contiguous in memory
                 r = q / kGrK;
                 kk = q % kGrK;
             } else {
@@ -552,39 +609,43 @@ __global__ void __launch_bounds__(256) k_gram(const T *__restrict__ X, long long
             xc[kk][r] = vc;
         }
         __syncthreads();
-#pragma unroll 8
+#pragma unroll 2
         for (int kk = 0; kk < kGrK; ++kk) {
-            T av[4], cv[4];
+            T av[8], cv[8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                av[i] = xa[kk][ty * 4 + i];
-                cv[i] = xc[kk][tx * 4 + i];
+            for (int i = 0; i < 8; ++i) {
+                av[i] = xa[kk][ty * 8 + i];
+                cv[i] = xc[kk][tx * 8 + i];
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * cv[j];
+                for (int j = 0; j < 8; ++j) acc[i][j] += av[i] * cv[j];
         }
         __syncthreads();
-        since += kGrK;
-        if (since >= kGrFold) {
+        if constexpr (kFold) {
+            since += kGrK;
+            if (since >= kGrFold) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    dacc[i][j] += (double)acc[i][j];
-                    acc[i][j] = 0;
-                }
-            since = 0;
+                    for (int j = 0; j < 8; ++j) {
+                        fold[(i * 8 + j) * blockDim.x + threadIdx.x] += acc[i][j];
+                        acc[i][j] = 0;
+                    }
+                since = 0;
+            }
         }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int a = a0 + ty * 4 + i, c = c0 + tx * 4 + j;
+        for (int j = 0; j < 8; ++j) {
+            const int a = a0 + ty * 8 + i, c = c0 + tx * 8 + j;
             if (a < n && c < n) {
-                const double v = (dacc[i][j] + (double)acc[i][j]) * scale;
+                double v = (double)acc[i][j];
+                if constexpr (kFold) v += (double)fold[(i * 8 + j) * blockDim.x + threadIdx.x];
+                v *= scale;
                 S[(long long)a * n + c] = v;
                 S[(long long)c * n + a] = v;
             }
@@ -627,11 +688,13 @@ template <typename T>
 cudaError_t launch_mlp_back(const Geom &g, int l, const Weights<T> &w, const int8_t *spins, int B, const T *chi,
                             const T *y, const T *dtv, const GradScratch<T> &s, cudaStream_t st) {
     const int ntile = (g.N + kMbTile - 1) / kMbTile;
-    const size_t smem = (size_t)kMbTile * (3 * g.dh + g.d) * sizeof(T);
+    const size_t smem =
+        ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1) + (size_t)kMbTile * (2 * g.dh + g.d)) * sizeof(T);
+    if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
     cudaError_t err = cudaFuncSetAttribute(k_mlp_back<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     ProfScope _ps("k_mlp_back", st);
-    k_mlp_back<T><<<(unsigned)((long long)B * ntile), 128, smem, st>>>(g, l, w, spins, chi, y, dtv, s.tY, s.dy, s.dchi,
+    k_mlp_back<T><<<(unsigned)((long long)B * ntile), 256, smem, st>>>(g, l, w, spins, chi, y, dtv, s.tY, s.dy, s.dchi,
                                                                        s.a1, s.phi, s.dz, s.dphi, s.win);
     return cudaGetLastError();
 }
@@ -718,16 +781,19 @@ cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, lon
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    const size_t gfold = sizeof(T) == 4 ? 64 * 256 * sizeof(T) : 0;
+    if ((err = cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gfold)) != cudaSuccess)
+        return err;
     if (gram) {
         const long long nt = (B + kGrT - 1) / kGrT;
         ProfScope _ps("k_gram", st);
-        k_gram<T><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(O, P, 1, B, P, mean, 1, 1.0 / B, gram);
+        k_gram<T><<<(unsigned)(nt * (nt + 1) / 2), 256, gfold, st>>>(O, P, 1, B, P, mean, 1, 1.0 / B, gram);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (Ssub && nk > 0) {
         const long long nt = (nk + kGrT - 1) / kGrT;
         ProfScope _ps("k_gram", st);
-        k_gram<T><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(O + k0, 1, P, nk, B, mean + k0, 0, 1.0 / B, Ssub);
+        k_gram<T><<<(unsigned)(nt * (nt + 1) / 2), 256, gfold, st>>>(O + k0, 1, P, nk, B, mean + k0, 0, 1.0 / B, Ssub);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     return cudaSuccess;

@@ -16,7 +16,9 @@
 // addressed with both offsets equal to 128 B.  One thread issues the MMAs (M=128, N=256, K=16 each) and commits
 // them to an mbarrier; every wait is bounded, and a timeout raises bit 8 of the
 // error flag, skips the epilogue and still releases the tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <mutex>
 
 #include "dn_internal.cuh"
 #include "tc_common.cuh"
@@ -316,9 +318,10 @@ constexpr int kGpMaxChunks = 4;
 template <int NPL>
 __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__restrict__ taps, int P,
                                                        const float *__restrict__ gtaps, const float *__restrict__ gDm,
-                                                       long long dm_ss, float *__restrict__ Y, float *__restrict__ band,
-                                                       long long bss, long long brs, long long bos, int bR, int bns,
-                                                       long long b0, unsigned *__restrict__ flag) {
+                                                       long long dm_ss, const __grid_constant__ CUtensorMap tmY,
+                                                       float *__restrict__ band, long long bss, long long brs,
+                                                       long long bos, int bR, int bns, long long b0,
+                                                       unsigned *__restrict__ flag) {
     extern __shared__ __align__(1024) unsigned char smtc[];
     constexpr int TN = 128, kSlabB = TN * 16 * 2;
     constexpr int kBbytes = NPL * 4 * kSlabB;
@@ -432,45 +435,62 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
         __syncthreads();
         tc::fence_after();
         if (!*s_ok) break;
-        // Epilogue (as k_tgemm_tc): TMEM -> per-warp 32 x 33 staging tile -> rows of Y, band.
+        // Epilogue: thread = row i (TMEM lane), 32 columns per pass in registers.  Y leaves
+        // through a 32 x 32 staging tile per warp (128-byte rows, 16-byte chunks XOR-swizzled
+        // by row, the layout of the tensor map's 128B swizzle) and one TMA store; the band
+        // entries of the row are written straight from the registers (4 columns per store,
+        // which share a source site since the source count per site is a multiple of 4).
         const int quad = warp & 3, half = warp >> 2;
-        float *stage = reinterpret_cast<float *>(smtc) + warp * (32 * 33);
-        const int prow0 = i0 + quad * 32;
-        const int nrows = N - prow0 < 32 ? N - prow0 : 32;
+        unsigned char *stg = smtc + warp * 4096;
+        const uint32_t stg_s = sm_u32(stg);
+        const int prow0 = i0 + quad * 32, i = prow0 + lane;
+        const long long zc = bl * d + a;
         for (int c0 = 0; c0 < TN / 2; c0 += 32) {
             float r[32];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 tc::tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * (TN / 2) + c0 + 8 * q), r + 8 * q);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = r[j];
+            const int pb = p0 + half * (TN / 2) + c0;
+            if (pb >= P || prow0 >= N) continue;       // warp-uniform
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             __syncwarp();
-            const int p = p0 + half * (TN / 2) + c0 + lane;
-            if (p < P && nrows > 0) {
-                if (Y) {
-                    float *yp = Y + ((bl * d + a) * N + prow0) * (long long)P + p;
-                    for (int rr = 0; rr < nrows; ++rr, yp += P) *yp = stage[rr * 33 + lane];
-                }
-                if (band) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<float4 *>(stg + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                    make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                        reinterpret_cast<uint64_t>(&tmY)),
+                    "r"(pb), "r"(prow0), "r"((int)zc), "r"(stg_s)
+                    : "memory");
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+            if (band && i < N) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int p = pb + 4 * j;
+                    if (p >= P) break;
                     const int k = p / bns, cc = p - k * bns;
-                    float *bp = band + (b0 + bl) * bss + (long long)a * bns + cc;
-                    for (int dl = -bR; dl <= bR; ++dl) {
-                        int i = k + dl;
-                        if (g.periodic) i = i < 0 ? i + N : (i >= N ? i - N : i);
-                        else if (i < 0 || i >= N) continue;
-                        if (i < prow0 || i >= prow0 + nrows) continue;
-                        if (g.periodic && ring_delta_tc(i - k, N, 1) != dl) continue;
-                        bp[(long long)i * brs + (long long)(bR - dl) * bos] = stage[(i - prow0) * 33 + lane];
-                    }
+                    const int dl = g.periodic ? ring_delta_tc(i - k, N, 1) : i - k;
+                    if (dl < -bR || dl > bR) continue;
+                    float *bp = band + (b0 + bl) * bss + (long long)i * brs + (long long)(bR - dl) * bos +
+                                (long long)a * bns + cc;
+                    *reinterpret_cast<float4 *>(bp) = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
                 }
             }
-            __syncwarp();
         }
+        // The staging tiles are read before the next tile's operands overwrite them.
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        __syncwarp();
         // The next tile overwrites the staging area (B buffer) and the accumulator.
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
     }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (!*s_ok && tid == 0) atomicOr(flag, 8u);
     tc::fence_before();
     __syncthreads();
@@ -610,11 +630,46 @@ static size_t tgemm_genp_smem(int N, int d, int npl) {
            ((size_t)((2 * N + 1) & ~1) + (size_t)N * d + ((size_t)(2 * N - 1) * d + 1) / 2 * 2) * sizeof(float) + 32;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of a hop output Y [zs][N][P] (float), 32 x 32 boxes with the 128B swizzle.
+static bool hop_output_map(CUtensorMap *tm, float *Y, int N, int P, long long zs) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || P % 4 != 0 || (reinterpret_cast<uintptr_t>(Y) & 15) != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)N, (cuuint64_t)zs};
+    const cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)P * N * 4};
+    const cuuint32_t box[3] = {32, 32, 1}, estr[3] = {1, 1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int NPL>
 static cudaError_t launch_tgemm_genp(const Geom &g, const float *taps, int P, const float *gtaps, const float *gDm,
                                      long long dm_ss, float *Y, float *band, long long bss, long long brs,
                                      long long bos, int bR, int bns, long long b0, int nb, unsigned *flag,
                                      cudaStream_t st) {
+    alignas(64) CUtensorMap tmY;
+    if (!Y || bns % 4 != 0 || !hop_output_map(&tmY, Y, g.N, P, (long long)nb * g.d)) return cudaErrorNotSupported;
     const size_t smem = tgemm_genp_smem(g.N, g.d, NPL);
     const int itiles = (g.N + kTcM - 1) / kTcM, ntiles = (P + 127) / 128;
     const long long ctas = (long long)itiles * nb * g.d;
@@ -627,8 +682,8 @@ static cudaError_t launch_tgemm_genp(const Geom &g, const float *taps, int P, co
     if (err != cudaSuccess) return err;
     {
         ProfScope _ps("k_tgemm_tc", st);
-        k_tgemm_genp<NPL><<<grid, 256, smem, st>>>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0,
-                                                   flag);
+        k_tgemm_genp<NPL><<<grid, 256, smem, st>>>(g, taps, P, gtaps, gDm, dm_ss, tmY, band, bss, brs, bos, bR, bns,
+                                                   b0, flag);
     }
     return cudaGetLastError();
 }
@@ -677,10 +732,11 @@ cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float
     // Generated operand with the whole chain in shared memory: the persistent kernel.
     if (gtaps && g.N <= kGpMaxChunks * kTcK && g.d <= 64 && 128 % g.d == 0 && (planes == 1 || planes == 2) &&
         tgemm_genp_smem(g.N, g.d, planes) <= 110 * 1024) {
-        return planes == 1 ? launch_tgemm_genp<1>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0,
-                                                  nb, flag, st)
-                           : launch_tgemm_genp<2>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0,
-                                                  nb, flag, st);
+        const cudaError_t e = planes == 1 ? launch_tgemm_genp<1>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos,
+                                                                 bR, bns, b0, nb, flag, st)
+                                          : launch_tgemm_genp<2>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos,
+                                                                 bR, bns, b0, nb, flag, st);
+        if (e != cudaErrorNotSupported) return e;
     }
     switch (planes) {
     case 1:
