@@ -775,7 +775,7 @@ dn_status dn_sr_matrices(const void *O_dev, int B, size_t n_params, dn_precision
                                               (long long)k0, s_dev ? nk : 0, s_dev, mean.as<double>(), st));
         else
             ck(dn::launch_sr_matrices<float>(static_cast<const float *>(O_dev), B, (long long)n_params, gram_dev,
-                                             (long long)k0, s_dev ? nk : 0, s_dev, mean.as<double>(), st));
+                                             (long long)k0, s_dev ? nk : 0, s_dev, mean.as<float>(), st));
         return DN_OK;
     });
 }

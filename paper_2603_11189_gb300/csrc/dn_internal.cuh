@@ -259,7 +259,7 @@ cudaError_t launch_vjp(const T *O, const double *wts, int B, long long P, double
 // Oc[:, k0:k0+nk]^T Oc[:, k0:k0+nk] / B with Oc the centred O (either may be null).
 template <typename T>
 cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, long long k0, int nk, double *Ssub,
-                               double *mean, cudaStream_t st);
+                               T *mean, cudaStream_t st);
 template <typename T>
 cudaError_t launch_s4_grad(const dn_model *m, int blk, int N, int B, const T *dg, const T *pw, T *O, long long P,
                            cudaStream_t st);

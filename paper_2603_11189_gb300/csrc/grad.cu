@@ -545,25 +545,27 @@ __global__ void k_vjp(const T *__restrict__ O, const double *__restrict__ wts, i
 // Stochastic-reconfiguration matrices from the log-derivatives, centred over the samples.
 // Column means m[k] = (1/B) sum_b O[b][k] (FP64).
 template <typename T>
-__global__ void k_colmean(const T *__restrict__ O, int B, long long P, double *__restrict__ m) {
+__global__ void k_colmean(const T *__restrict__ O, int B, long long P, T *__restrict__ m) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < P; k += (long long)gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int b = 0; b < B; ++b) acc += (double)O[(long long)b * P + k];
-        m[k] = acc / B;
+        m[k] = (T)(acc / B);
     }
 }
 
 // S[a][c] = scale sum_k (X[a][k] - m_a|k) (X[c][k] - m_a|k) for a, c < n, with X[a][k] at
-// X + a sa + k sk; the mean is m[k] (mean_by_k) or m[a].  One CTA per 128 x 128 tile with
-// c0 >= a0 (the other half is mirrored); K streams through shared memory 16 at a time.
+// X + a sa + k sk; the mean (in the precision of X) is m[k] (mean_by_k) or m[a].  One CTA per
+// 128 x 128 tile with c0 >= a0 (the other half is mirrored); K streams through shared
+// memory 16 at a time, the next slice's loads in flight while the current one is used.
 // Each thread keeps an 8 x 8 block in registers; in FP32 the block is added every kGrFold
 // terms into a second FP32 sum held in shared memory (two-level summation: the error grows
 // with sqrt(kGrFold) + sqrt(K / kGrFold) instead of sqrt(K)).
 constexpr int kGrT = 128, kGrK = 16, kGrFold = 512, kGrPad = kGrT + 4;
+constexpr int kGrLd = kGrK * kGrT / 256;   // elements of each operand a thread stages per slice
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const T *__restrict__ X, long long sa, long long sk, int n, long long K,
-                                              const double *__restrict__ m, int mean_by_k, double scale,
+                                              const T *__restrict__ m, int mean_by_k, double scale,
                                               double *__restrict__ S) {
     __shared__ __align__(16) T xa[kGrK][kGrPad];
     __shared__ __align__(16) T xc[kGrK][kGrPad];
@@ -579,6 +581,34 @@ __global__ void __launch_bounds__(256) k_gram(const T *__restrict__ X, long long
     const int a0 = ta * kGrT, c0 = tc * kGrT;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     constexpr bool kFold = sizeof(T) == 4;
+    // This thread's staging slots: (kk, r) for q = threadIdx.x + 256 u.
+    int skk[kGrLd], sr[kGrLd];
+#pragma unroll
+    for (int u = 0; u < kGrLd; ++u) {
+        const int q = threadIdx.x + 256 * u;
+        if (sk == 1) {           // K contiguous in memory: 16 threads read one row's slice
+            sr[u] = q / kGrK;
+            skk[u] = q % kGrK;
+        } else {
+            skk[u] = q / kGrT;
+            sr[u] = q % kGrT;
+        }
+    }
+    T pa[kGrLd], pc[kGrLd];
+    auto fetch = [&](long long k0) {
+#pragma unroll
+        for (int u = 0; u < kGrLd; ++u) {
+            const long long k = k0 + skk[u];
+            const int a = a0 + sr[u], c = c0 + sr[u];
+            T va = 0, vc = 0;
+            if (k < K) {
+                if (a < n) va = X[a * sa + k * sk] - (mean_by_k ? m[k] : m[a]);
+                if (c < n) vc = X[c * sa + k * sk] - (mean_by_k ? m[k] : m[c]);
+            }
+            pa[u] = va;
+            pc[u] = vc;
+        }
+    };
     T acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -588,27 +618,15 @@ __global__ void __launch_bounds__(256) k_gram(const T *__restrict__ X, long long
         for (int q = 0; q < 64; ++q) fold[q * blockDim.x + threadIdx.x] = 0;
     }
     int since = 0;
+    fetch(0);
     for (long long k0 = 0; k0 < K; k0 += kGrK) {
-        for (int q = threadIdx.x; q < kGrK * kGrT; q += blockDim.x) {
-            int kk, r;
-            if (sk == 1) {           // K contiguous in memory
-                r = q / kGrK;
-                kk = q % kGrK;
-            } else {
-                kk = q / kGrT;
-                r = q % kGrT;
-            }
-            const long long k = k0 + kk;
-            const int a = a0 + r, c = c0 + r;
-            T va = 0, vc = 0;
-            if (k < K) {
-                if (a < n) va = (T)((double)X[a * sa + k * sk] - (mean_by_k ? m[k] : m[a]));
-                if (c < n) vc = (T)((double)X[c * sa + k * sk] - (mean_by_k ? m[k] : m[c]));
-            }
-            xa[kk][r] = va;
-            xc[kk][r] = vc;
+#pragma unroll
+        for (int u = 0; u < kGrLd; ++u) {
+            xa[skk[u]][sr[u]] = pa[u];
+            xc[skk[u]][sr[u]] = pc[u];
         }
         __syncthreads();
+        if (k0 + kGrK < K) fetch(k0 + kGrK);
 #pragma unroll 2
         for (int kk = 0; kk < kGrK; ++kk) {
             T av[8], cv[8];
@@ -774,7 +792,7 @@ cudaError_t launch_vjp(const T *O, const double *wts, int B, long long P, double
 
 template <typename T>
 cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, long long k0, int nk, double *Ssub,
-                               double *mean, cudaStream_t st) {
+                               T *mean, cudaStream_t st) {
     {
         ProfScope _ps("k_colmean", st);
         k_colmean<T><<<grid_of(P), 256, 0, st>>>(O, B, P, mean);
@@ -815,8 +833,8 @@ cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, lon
                                            cudaStream_t);                                                            \
     template cudaError_t launch_s4_pow<T>(const dn_model *, int, T *, cudaStream_t);                                  \
     template cudaError_t launch_vjp<T>(const T *, const double *, int, long long, double *, cudaStream_t);            \
-    template cudaError_t launch_sr_matrices<T>(const T *, int, long long, double *, long long, int, double *,          \
-                                               double *, cudaStream_t);                                               \
+    template cudaError_t launch_sr_matrices<T>(const T *, int, long long, double *, long long, int, double *, T *,     \
+                                               cudaStream_t);                                                          \
     template cudaError_t launch_s4_grad<T>(const dn_model *, int, int, int, const T *, const T *, T *, long long,     \
                                            cudaStream_t);
 

@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(256) k_dhop(Geom g, int P, int cols, const T *
 // lane = column; it streams its column of X over n and keeps the 2R+1 taps
 // g_{k+dl-n} it needs in a register window that slides by one tap per site.
 constexpr int kBcMaxBand = 31;
+constexpr int kBcU = 8;   // sites per tap window in k_bandconv4
 
 template <typename T, bool GEN, int NB>
 __global__ void __launch_bounds__(256) k_bandconv(Geom g, const T *__restrict__ taps, int P, const T *__restrict__ X,
@@ -441,8 +442,10 @@ __global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restri
     for (int q = 0; q < NB; ++q)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[q][j] = 0.f;
-#pragma unroll 4
-    for (int n = 0; n < N; ++n) {
+    // Sites in blocks of kBcU: the taps of a block are a window of NB + kBcU - 1 values,
+    // win[m] = gk[m - (n0 + kBcU - 1)], loaded once, so that (q, n0 + u) reads
+    // win[q - u + kBcU - 1] at a compile-time index.  Taps for q > 2R are never used.
+    auto site = [&](int n, const float *win, int u) {
         float4 xv;
         if (GEN) {
             const float4 dm = *reinterpret_cast<const float4 *>(Dma + n * d);
@@ -453,13 +456,26 @@ __global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restri
         }
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            if (q > 2 * R) break;
-            const float w = gk[q - n];
+            const float w = win[q - u + kBcU - 1];
             acc[q][0] = fmaf(w, xv.x, acc[q][0]);
             acc[q][1] = fmaf(w, xv.y, acc[q][1]);
             acc[q][2] = fmaf(w, xv.z, acc[q][2]);
             acc[q][3] = fmaf(w, xv.w, acc[q][3]);
         }
+    };
+    int n0 = 0;
+    for (; n0 + kBcU <= N; n0 += kBcU) {
+        float win[NB + kBcU - 1];
+#pragma unroll
+        for (int m = 0; m < NB + kBcU - 1; ++m) win[m] = gk[m - (n0 + kBcU - 1)];
+#pragma unroll
+        for (int u = 0; u < kBcU; ++u) site(n0 + u, win, u);
+    }
+    for (; n0 < N; ++n0) {
+        float win[NB + kBcU - 1];
+#pragma unroll
+        for (int m = 0; m < NB + kBcU - 1; ++m) win[m] = gk[m - (n0 + kBcU - 1)];
+        site(n0, win, 0);
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) {

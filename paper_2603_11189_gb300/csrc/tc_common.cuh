@@ -57,19 +57,24 @@ __device__ __forceinline__ void stage8(unsigned char *hi, unsigned char *lo, uin
 // pa + pb <= NPL - 1 reproduce the FP32 product to about 2^-(9 NPL) relative.
 template <int NPL>
 __device__ __forceinline__ void stage8_planes(unsigned char *base, uint32_t pstride, uint32_t off, const float *v) {
-    __align__(16) __nv_bfloat16 h[NPL][8];
+    float r[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        float r = v[u];
+    for (int u = 0; u < 8; ++u) r[u] = v[u];
 #pragma unroll
-        for (int p = 0; p < NPL; ++p) {
-            h[p][u] = __float2bfloat16_rn(r);
-            r -= __bfloat162float(h[p][u]);
+    for (int p = 0; p < NPL; ++p) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            // one conversion rounds a pair (element 2i in the low half, as in memory)
+            const __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t *>(&h);
+            if (p + 1 < NPL) {
+                r[2 * i] -= __low2float(h);
+                r[2 * i + 1] -= __high2float(h);
+            }
         }
+        *reinterpret_cast<uint4 *>(base + p * pstride + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-#pragma unroll
-    for (int p = 0; p < NPL; ++p)
-        *reinterpret_cast<uint4 *>(base + p * pstride + off) = *reinterpret_cast<const uint4 *>(h[p]);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {

@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256, 3) k_tgemm_tc(Geom g, const float *__rest
 // only.  Chunks share one B buffer: chunk c waits for the MMAs of chunk c - 1.
 constexpr int kGpMaxChunks = 4;
 
-template <int NPL>
+template <int NPL, int DD>
 __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__restrict__ taps, int P,
                                                        const float *__restrict__ gtaps, const float *__restrict__ gDm,
                                                        long long dm_ss, const __grid_constant__ CUtensorMap tmY,
@@ -326,7 +326,8 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
     constexpr int TN = 128, kSlabB = TN * 16 * 2;
     constexpr int kBbytes = NPL * 4 * kSlabB;
     constexpr int kFront = kBbytes > kEpiBytes ? kBbytes : kEpiBytes;
-    const int N = g.N, d = g.d;
+    const int N = g.N;
+    constexpr int d = DD;   // channels: compile-time, so site strides fold into immediates
     const int nch = (N + kTcK - 1) / kTcK;
     unsigned char *Bp = smtc;                                       // NPL planes x 4 slabs
     unsigned char *Aall = smtc + kFront;                            // [nch][NPL][kHankelBytes]
@@ -469,16 +470,23 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
             if (band && i < N) {
+                // (k, cc) of column pb, then stepped by 4 columns without dividing again
+                int k = pb / bns, cc = pb - k * bns;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int p = pb + 4 * j;
-                    if (p >= P) break;
-                    const int k = p / bns, cc = p - k * bns;
+                    if (pb + 4 * j >= P) break;
                     const int dl = g.periodic ? ring_delta_tc(i - k, N, 1) : i - k;
-                    if (dl < -bR || dl > bR) continue;
-                    float *bp = band + (b0 + bl) * bss + (long long)i * brs + (long long)(bR - dl) * bos +
-                                (long long)a * bns + cc;
-                    *reinterpret_cast<float4 *>(bp) = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+                    if (dl >= -bR && dl <= bR) {
+                        float *bp = band + (b0 + bl) * bss + (long long)i * brs + (long long)(bR - dl) * bos +
+                                    (long long)a * bns + cc;
+                        *reinterpret_cast<float4 *>(bp) =
+                            make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+                    }
+                    cc += 4;
+                    if (cc == bns) {
+                        cc = 0;
+                        ++k;
+                    }
                 }
             }
         }
@@ -663,11 +671,11 @@ static bool hop_output_map(CUtensorMap *tm, float *Y, int N, int P, long long zs
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NPL>
-static cudaError_t launch_tgemm_genp(const Geom &g, const float *taps, int P, const float *gtaps, const float *gDm,
-                                     long long dm_ss, float *Y, float *band, long long bss, long long brs,
-                                     long long bos, int bR, int bns, long long b0, int nb, unsigned *flag,
-                                     cudaStream_t st) {
+template <int NPL, int DD>
+static cudaError_t launch_tgemm_genp_d(const Geom &g, const float *taps, int P, const float *gtaps, const float *gDm,
+                                       long long dm_ss, float *Y, float *band, long long bss, long long brs,
+                                       long long bos, int bR, int bns, long long b0, int nb, unsigned *flag,
+                                       cudaStream_t st) {
     alignas(64) CUtensorMap tmY;
     if (!Y || bns % 4 != 0 || !hop_output_map(&tmY, Y, g.N, P, (long long)nb * g.d)) return cudaErrorNotSupported;
     const size_t smem = tgemm_genp_smem(g.N, g.d, NPL);
@@ -678,14 +686,28 @@ static cudaError_t launch_tgemm_genp(const Geom &g, const float *taps, int P, co
     if (cg < 1) cg = 1;
     if (cg > ntiles) cg = ntiles;
     dim3 grid((unsigned)cg, (unsigned)itiles, (unsigned)((long long)nb * g.d));
-    cudaError_t err = cudaFuncSetAttribute(k_tgemm_genp<NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_tgemm_genp<NPL, DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     {
         ProfScope _ps("k_tgemm_tc", st);
-        k_tgemm_genp<NPL><<<grid, 256, smem, st>>>(g, taps, P, gtaps, gDm, dm_ss, tmY, band, bss, brs, bos, bR, bns,
-                                                   b0, flag);
+        k_tgemm_genp<NPL, DD><<<grid, 256, smem, st>>>(g, taps, P, gtaps, gDm, dm_ss, tmY, band, bss, brs, bos, bR,
+                                                       bns, b0, flag);
     }
     return cudaGetLastError();
+}
+
+template <int NPL>
+static cudaError_t launch_tgemm_genp(const Geom &g, const float *taps, int P, const float *gtaps, const float *gDm,
+                                     long long dm_ss, float *Y, float *band, long long bss, long long brs,
+                                     long long bos, int bR, int bns, long long b0, int nb, unsigned *flag,
+                                     cudaStream_t st) {
+    switch (g.d) {
+    case 16: return launch_tgemm_genp_d<NPL, 16>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
+    case 32: return launch_tgemm_genp_d<NPL, 32>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
+    case 64: return launch_tgemm_genp_d<NPL, 64>(g, taps, P, gtaps, gDm, dm_ss, Y, band, bss, brs, bos, bR, bns, b0, nb, flag, st);
+    default: return cudaErrorNotSupported;
+    }
 }
 
 template <int TN, int NPL>
