@@ -770,12 +770,18 @@ dn_status dn_sr_matrices(const void *O_dev, int B, size_t n_params, dn_precision
     return guard([&]() -> dn_status {
         dn::ProfPhase phase("sr");
         DevBuf mean(n_params * sizeof(double), st);
-        if (prec == DN_FP64)
+        if (prec == DN_FP64) {
             ck(dn::launch_sr_matrices<double>(static_cast<const double *>(O_dev), B, (long long)n_params, gram_dev,
-                                              (long long)k0, s_dev ? nk : 0, s_dev, mean.as<double>(), st));
-        else
+                                              (long long)k0, s_dev ? nk : 0, s_dev, mean.as<double>(), nullptr, 0,
+                                              st));
+        } else {
+            int nsplit = 1;
+            const size_t pe = gram_dev ? dn::gram_tc_partial_elems(B, (long long)n_params, &nsplit) : 0;
+            DevBuf part(std::max<size_t>(pe, 1) * sizeof(float), st);
             ck(dn::launch_sr_matrices<float>(static_cast<const float *>(O_dev), B, (long long)n_params, gram_dev,
-                                             (long long)k0, s_dev ? nk : 0, s_dev, mean.as<float>(), st));
+                                             (long long)k0, s_dev ? nk : 0, s_dev, mean.as<float>(),
+                                             gram_dev ? part.as<float>() : nullptr, nsplit, st));
+        }
         return DN_OK;
     });
 }

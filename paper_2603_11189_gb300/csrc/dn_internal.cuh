@@ -257,12 +257,19 @@ template <typename T>
 cudaError_t launch_vjp(const T *O, const double *wts, int B, long long P, double *vjp, cudaStream_t st);
 // Column means of O [B][P] into mean [P]; gram [B][B] = Oc Oc^T / B and Ssub [nk][nk] =
 // Oc[:, k0:k0+nk]^T Oc[:, k0:k0+nk] / B with Oc the centred O (either may be null).
+// part (may be null: CUDA-core kernel) holds the tensor-core Gram's K-split partials.
 template <typename T>
 cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, long long k0, int nk, double *Ssub,
-                               T *mean, cudaStream_t st);
+                               T *mean, float *part, int nsplit, cudaStream_t st);
 template <typename T>
 cudaError_t launch_s4_grad(const dn_model *m, int blk, int N, int B, const T *dg, const T *pw, T *O, long long P,
                            cudaStream_t st);
+
+// Sample-space Gram on the tensor cores (tc_gemm.cu): S [n][n] = scale Xc Xc^T, Xc = X - m,
+// X [n][K] float row-major; partial buffer of gram_tc_partial_elems() floats.
+size_t gram_tc_partial_elems(int n, long long K, int *nsplit);
+cudaError_t launch_gram_tc(const float *X, int n, long long K, const float *m, double scale, double *S, float *part,
+                           int nsplit, unsigned *flag, cudaStream_t st);
 
 // Tensor-core forward pass (forward_tc.cu); activations channel-major h[c][n B + b].
 bool forward_tc_ok(const Geom &g);

@@ -792,7 +792,7 @@ cudaError_t launch_vjp(const T *O, const double *wts, int B, long long P, double
 
 template <typename T>
 cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, long long k0, int nk, double *Ssub,
-                               T *mean, cudaStream_t st) {
+                               T *mean, float *part, int nsplit, cudaStream_t st) {
     {
         ProfScope _ps("k_colmean", st);
         k_colmean<T><<<grid_of(P), 256, 0, st>>>(O, B, P, mean);
@@ -802,7 +802,12 @@ cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, lon
     const size_t gfold = sizeof(T) == 4 ? 64 * 256 * sizeof(T) : 0;
     if ((err = cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gfold)) != cudaSuccess)
         return err;
-    if (gram) {
+    if (gram && part) {
+        // FP32: tensor cores (BF16 planes, FP32-grade products), K split, splits summed in FP64
+        if ((err = launch_gram_tc(reinterpret_cast<const float *>(O), B, P, reinterpret_cast<const float *>(mean),
+                                  1.0 / B, gram, part, nsplit, nullptr, st)) != cudaSuccess)
+            return err;
+    } else if (gram) {
         const long long nt = (B + kGrT - 1) / kGrT;
         ProfScope _ps("k_gram", st);
         k_gram<T><<<(unsigned)(nt * (nt + 1) / 2), 256, gfold, st>>>(O, P, 1, B, P, mean, 1, 1.0 / B, gram);
@@ -834,7 +839,7 @@ cudaError_t launch_sr_matrices(const T *O, int B, long long P, double *gram, lon
     template cudaError_t launch_s4_pow<T>(const dn_model *, int, T *, cudaStream_t);                                  \
     template cudaError_t launch_vjp<T>(const T *, const double *, int, long long, double *, cudaStream_t);            \
     template cudaError_t launch_sr_matrices<T>(const T *, int, long long, double *, long long, int, double *, T *,     \
-                                               cudaStream_t);                                                          \
+                                               float *, int, cudaStream_t);                                            \
     template cudaError_t launch_s4_grad<T>(const dn_model *, int, int, int, const T *, const T *, T *, long long,     \
                                            cudaStream_t);
 

@@ -630,6 +630,188 @@ cudaError_t launch_dhop_tc(int d, int N, int P, const float *Dm, long long dm_ss
     return cudaErrorNotSupported;
 }
 
+// Sample-space SR Gram on the tensor cores: partial[split][tile] = Xc[a0:a0+128] Xc[c0:c0+128]^T over
+// one K range, Xc = X - m (centred in FP32), X [n][K] row-major.  One CTA per (upper-triangle
+// 128 x 128 tile, K split); K streams in chunks of 64 through two operand stages (the next
+// chunk is converted into BF16 planes while the MMAs of the current one run); the FP32
+// accumulator stays in TMEM for the whole K range and is written as an FP32 tile.  Diagonal
+// tiles stage one operand and use it on both sides.  With NPL planes per value the products
+// of planes pa + pb < NPL are accumulated (NPL = 3: FP32-grade products).
+constexpr int kGcK = 64;
+
+template <int NPL>
+__global__ void __launch_bounds__(256, 1) k_gram_tc(const float *__restrict__ X, int n, long long K,
+                                                    const float *__restrict__ m, long long kspan, float *__restrict__ part,
+                                                    unsigned *__restrict__ flag) {
+    extern __shared__ __align__(1024) unsigned char smg[];
+    constexpr uint32_t slab = 128 * 32, plane = 4 * slab, opnd = NPL * plane, stage_b = 2 * opnd;
+    unsigned char *st0 = smg;                                       // [2 stages][A | B][NPL planes][4 slabs]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smg + 2 * stage_b);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    int *s_ok = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nt = (n + 127) / 128;
+    int t = blockIdx.x, ta = 0;
+    while (t >= nt - ta) {
+        t -= nt - ta;
+        ++ta;
+    }
+    const int tc_ = ta + t;
+    const bool diag = tc_ == ta;
+    const int a0 = ta * 128, c0 = tc_ * 128;
+    const long long kb = (long long)blockIdx.y * kspan;
+    const long long ke = kb + kspan < K ? kb + kspan : K;
+    const int nch = (int)((ke - kb + kGcK - 1) / kGcK);
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        tc::mbar_init(mbar + 1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *s_ok = 1;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 128);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16(128, 128);
+    const int r = tid & 127, kh = tid >> 7;          // row of the tile, half of the chunk's K
+    const bool ra = a0 + r < n, rc = c0 + r < n;
+    const float *xa = X + (long long)(ra ? a0 + r : 0) * K;
+    const float *xc = X + (long long)(rc ? c0 + r : 0) * K;
+    const bool vec = (K & 3) == 0;   // rows 16-byte aligned: two 16-byte loads per 8 values
+    auto stage = [&](unsigned char *dst, const float *row, bool ok, long long k0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int kk = kh * 32 + 8 * j;
+            const long long k = k0 + kk;
+            float v[8];
+            if (ok && vec && k + 8 <= ke) {
+                const float4 x0 = __ldg(reinterpret_cast<const float4 *>(row + k));
+                const float4 x1 = __ldg(reinterpret_cast<const float4 *>(row + k + 4));
+                const float4 m0 = __ldg(reinterpret_cast<const float4 *>(m + k));
+                const float4 m1 = __ldg(reinterpret_cast<const float4 *>(m + k + 4));
+                v[0] = x0.x - m0.x; v[1] = x0.y - m0.y; v[2] = x0.z - m0.z; v[3] = x0.w - m0.w;
+                v[4] = x1.x - m1.x; v[5] = x1.y - m1.y; v[6] = x1.z - m1.z; v[7] = x1.w - m1.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = (ok && k + u < ke) ? row[k + u] - m[k + u] : 0.f;
+            }
+            tc::stage8_planes<NPL>(dst, plane, (uint32_t)(kk >> 4) * slab + tc::canon(r, kk & 15), v);
+        }
+    };
+    for (int c = 0; c < nch; ++c) {
+        const int sidx = c & 1;
+        unsigned char *A = st0 + sidx * stage_b, *Bm = A + opnd;
+        if (c >= 2) {
+            // the MMAs of chunk c - 2 read this stage
+            if (!tc::wait(mbar + sidx, (uint32_t)((c >> 1) + 1) & 1u) && lane == 0) *s_ok = 0;
+            __syncwarp();
+        }
+        const long long k0 = kb + (long long)c * kGcK;
+        stage(A, xa, ra, k0);
+        if (!diag) stage(Bm, xc, rc, k0);
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (!*s_ok) break;
+        if (tid == 0) {
+            const unsigned char *Bu = diag ? A : Bm;
+#pragma unroll 1
+            for (int sl = 0; sl < 4; ++sl)
+#pragma unroll
+                for (int pa = 0; pa < NPL; ++pa)
+#pragma unroll
+                    for (int pb = 0; pa + pb < NPL; ++pb)
+                        tc::mma_bf16(tmem, tc::desc(tc::smem_u32(A + pa * plane + sl * slab)),
+                                     tc::desc(tc::smem_u32(Bu + pb * plane + sl * slab)), idesc,
+                                     (c == 0 && sl == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+            tc::commit(mbar + sidx);
+        }
+    }
+    // the last commit covers every earlier MMA
+    if (nch > 0 && *s_ok) {
+        const int cl = nch - 1;
+        if (!tc::wait(mbar + (cl & 1), (uint32_t)(cl >> 1) & 1u) && lane == 0) *s_ok = 0;
+        __syncwarp();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const bool ok = *s_ok != 0;
+    // epilogue: warp (quad, half) -> rows quad*32 + lane, columns half*64 .. +63
+    const int quad = warp & 3, half = warp >> 2;
+    float *pt = part + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 128 * 128 + (long long)(quad * 32 + lane) * 128 +
+                half * 64;
+#pragma unroll 1
+    for (int c8 = 0; c8 < 64; c8 += 8) {
+        float v[8];
+        if (nch > 0) tc::tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64 + c8), v);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) pt[c8 + u] = (ok && nch > 0) ? v[u] : (nch > 0 ? __int_as_float(0x7fc00000) : 0.f);
+    }
+    if (!ok && tid == 0 && flag) atomicOr(flag, 8u);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, 128);
+}
+
+// S[a][c] = scale sum over the K splits of the tile partials (FP64), both triangles.
+__global__ void k_gram_reduce(const float *__restrict__ part, int n, int nsplit, int ntri, double scale,
+                              double *__restrict__ S) {
+    const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (x >= (long long)n * n) return;
+    const int a = (int)(x / n), c = (int)(x % n);
+    const int lo = a < c ? a : c, hi = a < c ? c : a;
+    const int ta = lo / 128, tc_ = hi / 128, nt = (n + 127) / 128;
+    const int tile = ta * nt - ta * (ta - 1) / 2 + (tc_ - ta);     // row-major upper triangle
+    // inside the tile: the row index comes from the tile's first block, the column from its second
+    const bool a_row = a / 128 == ta;
+    const int ri = a_row ? a % 128 : c % 128, ci = a_row ? c % 128 : a % 128;
+    double acc = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) acc += (double)part[((long long)sp * ntri + tile) * 128 * 128 + ri * 128 + ci];
+    S[x] = acc * scale;
+}
+
+template <int NPL>
+static cudaError_t launch_gram_tc_p(const float *X, int n, long long K, const float *m, double scale, double *S,
+                                    float *part, int nsplit, unsigned *flag, cudaStream_t st) {
+    constexpr size_t smem = 2 * 2 * (size_t)NPL * 4 * 128 * 32 + 64;
+    cudaError_t err = cudaFuncSetAttribute(k_gram_tc<NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int nt = (n + 127) / 128, ntri = nt * (nt + 1) / 2;
+    const long long kspan = ((K + nsplit - 1) / nsplit + kGcK - 1) / kGcK * kGcK;
+    {
+        ProfScope _ps("k_gram_tc", st);
+        k_gram_tc<NPL><<<dim3((unsigned)ntri, (unsigned)nsplit), 256, smem, st>>>(X, n, K, m, kspan, part, flag);
+    }
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_gram_reduce", st);
+        k_gram_reduce<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, st>>>(part, n, nsplit, ntri, scale, S);
+    }
+    return cudaGetLastError();
+}
+
+size_t gram_tc_partial_elems(int n, long long K, int *nsplit) {
+    const int nt = (n + 127) / 128, ntri = nt * (nt + 1) / 2;
+    // at most 16384 terms per split (each split accumulates in FP32 in TMEM; the splits are
+    // summed in FP64), and enough CTAs for four waves
+    int ns = (int)((K + 16383) / 16384);
+    const int waves = (4 * 152 + ntri - 1) / ntri;
+    if (ns < waves) ns = waves;
+    const long long maxs = (K + kGcK - 1) / kGcK;
+    if (ns > maxs) ns = (int)maxs;
+    if (ns < 1) ns = 1;
+    *nsplit = ns;
+    return (size_t)ns * ntri * 128 * 128;
+}
+
+cudaError_t launch_gram_tc(const float *X, int n, long long K, const float *m, double scale, double *S, float *part,
+                           int nsplit, unsigned *flag, cudaStream_t st) {
+    return launch_gram_tc_p<3>(X, n, K, m, scale, S, part, nsplit, flag, st);
+}
+
 static size_t tgemm_genp_smem(int N, int d, int npl) {
     const int nch = (N + kTcK - 1) / kTcK;
     const size_t B = (size_t)npl * 4 * 128 * 32;
