@@ -307,7 +307,7 @@ def measure_grad(dn, synth, torch, barrier, lib, B=4096, reps=2):
             "grad": {"value": B / (grad_ms / 1e3), "unit": "configurations/s (forward + all %d log-derivatives)" % P,
                      "ms": grad_ms},
             "sr_gram": {"ms": gram_ms, "tflops": gram_flop / (gram_ms / 1e3) / 1e12,
-                        "note": "Oc Oc^T / B, FP32 FMA on CUDA cores, two-level FP32 sums (512-term partials)"},
+                        "note": "Oc Oc^T / B on tcgen05, FP32 values as 3 BF16 planes (6 products), FP32 accumulation per K split of <= 16384 terms, splits summed in FP64; flops counted once per FP32 product"},
             "kernels": kern[:12]}
 
 

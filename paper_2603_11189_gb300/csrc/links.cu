@@ -56,9 +56,59 @@ __device__ __forceinline__ T gen_x(const GenSrc<T> &gs, int N, int d, int period
 }
 
 // ------------------------------------------------------------ site vertices --
-// Dm[b][l-1][n] = U diag(chi_n) V (row-major d x d) for layers 1..L-1.
+// Dm[b][l-1][n] = U diag(chi_n) V (row-major d x d) for layers 1..L-1.  One CTA per
+// (sample, layer, tile of kDmTile sites): U, V and the tile's chi (transposed, [e][site])
+// are staged in shared memory; a thread owns output entries (a, c) and forms
+// U[a][e] V[e][c] once per e for all sites of the tile.
+constexpr int kDmTile = 16;
+
 template <typename T>
-__global__ void k_dmat(Geom g, Weights<T> w, const T *__restrict__ chi, long long b0, T *__restrict__ Dm) {
+__global__ void __launch_bounds__(256) k_dmat(Geom g, Weights<T> w, const T *__restrict__ chi, long long b0,
+                                              T *__restrict__ Dm) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d, L = g.L;
+    const long long dd = (long long)d * d;
+    T *Us = reinterpret_cast<T *>(smraw);     // [a][e]
+    T *Vs = Us + dd;                          // [e][c]
+    T *xs = Vs + dd;                          // [e][kDmTile]
+    const int ntile = (N + kDmTile - 1) / kDmTile;
+    const long long blk = blockIdx.x;
+    const int n0 = (int)(blk % ntile) * kDmTile;
+    const int l = (int)((blk / ntile) % (L - 1)) + 1;
+    const long long bl = blk / ((long long)ntile * (L - 1));
+    const int ns = N - n0 < kDmTile ? N - n0 : kDmTile;
+    for (int q = threadIdx.x; q < dd; q += blockDim.x) {
+        Us[q] = w.U[(l - 1) * dd + q];
+        Vs[q] = w.V[(l - 1) * dd + q];
+    }
+    const T *x = chi + (((b0 + bl) * L + (l - 1)) * N + n0) * d;
+    for (int q = threadIdx.x; q < kDmTile * d; q += blockDim.x) {
+        const int s = q / d, e = q % d;
+        xs[e * kDmTile + s] = s < ns ? x[(long long)s * d + e] : (T)0;
+    }
+    __syncthreads();
+    T *dst = Dm + ((bl * (L - 1) + (l - 1)) * N + n0) * dd;
+    for (int q = threadIdx.x; q < dd; q += blockDim.x) {
+        const int a = q / d, c = q % d;
+        T acc[kDmTile];
+#pragma unroll
+        for (int s = 0; s < kDmTile; ++s) acc[s] = 0;
+        for (int e = 0; e < d; ++e) {
+            const T wv = Us[a * d + e] * Vs[e * d + c];
+            const T *xe = xs + e * kDmTile;
+#pragma unroll
+            for (int s = 0; s < kDmTile; ++s) acc[s] += wv * xe[s];
+        }
+#pragma unroll
+        for (int s = 0; s < kDmTile; ++s)
+            if (s < ns) dst[s * dd + q] = acc[s];
+    }
+}
+
+// Same entries, one CTA per (sample, layer, site), weights read through L1 (channel
+// counts whose staged weights exceed shared memory).
+template <typename T>
+__global__ void k_dmat_site(Geom g, Weights<T> w, const T *__restrict__ chi, long long b0, T *__restrict__ Dm) {
     const int N = g.N, d = g.d, L = g.L;
     const long long blk = blockIdx.x;
     const int n = (int)(blk % N);
@@ -77,8 +127,10 @@ __global__ void k_dmat(Geom g, Weights<T> w, const T *__restrict__ chi, long lon
 }
 
 // Embedding sources through layer 1: X[b][a][n][k] = (D0^(1)_n (g^(1)_{n-k} * e))_a.
-// One CTA per (sample, site n): D0_n and the tap rows of 128 sources at a time are
-// staged in shared memory (rows padded to d+1 floats), then X[:, n, :] = D0_n G.
+// One CTA per (sample, site n): D0_n (transposed, [c][a]) and the tap rows of 128 sources
+// at a time are staged in shared memory (rows padded to d+1 floats); thread (half, kk)
+// forms 16 outputs a at a time for source kk, reading 16 D0 entries per channel as four
+// 16-byte broadcasts.
 constexpr int kEmbChunk = 128;   // source sites staged per pass
 
 template <typename T>
@@ -86,27 +138,48 @@ __global__ void __launch_bounds__(256) k_embed_src(Geom g, const T *__restrict__
                                                    const T *__restrict__ Dm, T *__restrict__ X) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d, L = g.L, dp = d + 1;
-    T *Ds = reinterpret_cast<T *>(smraw);      // [d][d]
+    T *Ds = reinterpret_cast<T *>(smraw);      // [c][a]
     T *Gs = Ds + d * d;                        // [kEmbChunk][d+1]: sources k0 .. k0 + kEmbChunk - 1
     const long long blk = blockIdx.x;
     const int n = (int)(blk % N);
     const long long bl = blk / N;
     const long long dd = (long long)d * d;
     const T *D = Dm + ((bl * (L - 1)) * N + n) * dd;
-    for (int q = threadIdx.x; q < d * d; q += blockDim.x) Ds[q] = D[q];
+    for (int q = threadIdx.x; q < d * d; q += blockDim.x) Ds[(q % d) * d + q / d] = D[q];
+    const int kk = threadIdx.x % kEmbChunk, half = threadIdx.x / kEmbChunk;
+    const int ah = (d + 1) / 2;                // output channels per half
     for (int k0 = 0; k0 < N; k0 += kEmbChunk) {
         const int kn = N - k0 < kEmbChunk ? N - k0 : kEmbChunk;
         __syncthreads();
         for (int q = threadIdx.x; q < kn * d; q += blockDim.x) {
-            const int kk = q / d, c = q % d;
-            Gs[kk * dp + c] = taps1[(long long)tap_row(n - (k0 + kk), N, g.periodic) * d + c] * e[c];
+            const int k = q / d, c = q % d;
+            Gs[k * dp + c] = taps1[(long long)tap_row(n - (k0 + k), N, g.periodic) * d + c] * e[c];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < d * kn; idx += blockDim.x) {
-            const int a = idx / kn, kk = idx % kn;
-            T acc = 0;
-            for (int c = 0; c < d; ++c) acc += Ds[a * d + c] * Gs[kk * dp + c];
-            X[((bl * d + a) * N + n) * (long long)N + k0 + kk] = acc;
+        if (kk >= kn) continue;
+        const T *gk = Gs + kk * dp;
+        for (int a0 = half * ah; a0 < (half + 1) * ah && a0 < d; a0 += 16) {
+            T acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
+            if (a0 + 16 <= d) {
+                for (int c = 0; c < d; ++c) {
+                    const T gv = gk[c];
+                    const T *dc = Ds + c * d + a0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[j] += dc[j] * gv;
+                }
+            } else {
+                for (int c = 0; c < d; ++c) {
+                    const T gv = gk[c];
+                    const T *dc = Ds + c * d + a0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[j] += (a0 + j < d ? dc[j] : (T)0) * gv;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (a0 + j < d && a0 + j < (half + 1) * ah) X[((bl * d + a0 + j) * N + n) * (long long)N + k0 + kk] = acc[j];
         }
     }
 }
@@ -678,8 +751,17 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
         T *F = U + (size_t)nb * d * N * Pm;
         T *Dm = F + (size_t)nb * d * N * Pm;
         {
+            const size_t smem = ((size_t)2 * dd + (size_t)kDmTile * d) * sizeof(T);
             ProfScope _ps("k_dmat", st);
-            k_dmat<T><<<(unsigned)((long long)nb * (L - 1) * N), 128, 0, st>>>(g, w, chi, b0, Dm);
+            if (smem <= 200 * 1024) {
+                if ((err = cudaFuncSetAttribute(k_dmat<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                    cudaSuccess)
+                    return err;
+                const long long ntile = (N + kDmTile - 1) / kDmTile;
+                k_dmat<T><<<(unsigned)((long long)nb * (L - 1) * ntile), 256, smem, st>>>(g, w, chi, b0, Dm);
+            } else {
+                k_dmat_site<T><<<(unsigned)((long long)nb * (L - 1) * N), 128, 0, st>>>(g, w, chi, b0, Dm);
+            }
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         // Embedding sources (m = 0), P = N.
