@@ -311,6 +311,73 @@ def measure_grad(dn, synth, torch, barrier, lib, B=4096, reps=2):
             "kernels": kern[:12]}
 
 
+def measure_sampler(dn, synth, torch, barrier, C=4096, s=8, eps=0.01, sweeps=2):
+    """Screened typewriter sampler (Alg. 2) on C chains of the N = 128 benchmark model (FP32):
+    full sweeps (even then odd blocks of width s, one proposal per block), ambiguous window
+    eps; against sequential exact Metropolis on the GPU (every proposal by a full forward
+    pass of the flipped configurations, dn_recompute_flip_ratios), both on the same
+    proposals and uniforms."""
+    N = 128
+    desc = synth.ModelDesc(L=4, d=32, s=32, w=2, dh=32, dout=2, periodic=0)
+    params = synth.init_params(desc, 1002, a_scale=8.0)
+    model = dn.Model(desc, params)
+    spins0 = synth.spins_uniform(C, N, 2002)
+    batches = []
+    for sw in range(sweeps + 1):
+        for parity in (0, 1):
+            sites = synth.typewriter_sites(C, N, s, parity, 3000 + 2 * sw + parity)
+            u = synth.uniforms(C, sites.shape[1], 5000 + 2 * sw + parity)
+            batches.append((torch.from_numpy(sites).cuda(), torch.from_numpy(u).cuda()))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # screened sampler: warm-up sweep, then timed sweeps
+    sp = torch.from_numpy(spins0).cuda()
+    for sites, u in batches[:2]:
+        model.sampler_batch(sp, sites, u, eps, prec="fp32")
+    barrier()
+    tot = {"proposals": 0, "accepted": 0, "refreshes": 0}
+    ev0.record()
+    for sites, u in batches[2:]:
+        _, st = model.sampler_batch(sp, sites, u, eps, prec="fp32")
+        for k in tot:
+            tot[k] += st[k]
+    ev1.record()
+    barrier()
+    scr_ms = ev0.elapsed_time(ev1)
+    # exact sequential Metropolis, one proposal index at a time over all chains
+    sp2 = torch.from_numpy(spins0).cuda()
+    sample = torch.arange(C, dtype=torch.int32, device="cuda")
+    fl = torch.full((C, 2), -1, dtype=torch.int32, device="cuda")
+    out = torch.empty(C, dtype=torch.float64, device="cuda")
+
+    def exact(batch):
+        sites, u = batch
+        for k in range(sites.shape[1]):
+            fl[:, 0] = sites[:, k]
+            model.recompute_flip_ratios(sp2, sample, fl, prec="fp32", out=out)
+            take = u[:, k] < torch.clamp(torch.exp(2.0 * out), max=1.0)
+            rows = torch.nonzero(take).flatten()
+            cols = sites[rows, k].long()
+            sp2[rows, cols] = -sp2[rows, cols]
+
+    for b in batches[:2]:
+        exact(b)
+    barrier()
+    ev0.record()
+    for b in batches[2:]:
+        exact(b)
+    ev1.record()
+    barrier()
+    ex_ms = ev0.elapsed_time(ev1)
+    model.close()
+    props = tot["proposals"]
+    return {"workload": "lr-TFIM N=128 open, DysonNet L=4 d=32 s=32 w=2 FP32, %d chains, typewriter blocks of "
+                        "%d sites, eps=%g, %d sweeps" % (C, s, eps, sweeps),
+            "screened": {"value": props / (scr_ms / 1e3), "unit": "proposals/s", "ms_per_sweep": scr_ms / sweeps,
+                         "accepted": tot["accepted"], "refreshes": tot["refreshes"], "proposals": props},
+            "exact_recompute": {"value": props / (ex_ms / 1e3), "unit": "proposals/s", "ms_per_sweep": ex_ms / sweeps},
+            "speedup": ex_ms / scr_ms}
+
+
 def measure_serving(dn, synth, n_req=160, rate=20.0, seed=4005):
     """Serving workload: Markov chains with N in {64, 128, 256, 512, 1024} (two each) of
     the 6-layer, 64-channel, 64-mode model (FP32), requests of 1-512 random single-flip
@@ -387,6 +454,7 @@ def main():
     ap.add_argument("--no-n1024", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-sampler", action="store_true")
     ap.add_argument("--grad-samples", type=int, default=4096)
     ap.add_argument("--n1024-chains", type=int, default=4)
     args = ap.parse_args()
@@ -500,6 +568,7 @@ def main():
     n1024 = None if args.no_n1024 else measure_n1024(dn, synth, torch, barrier, args.n1024_chains)
     serving = None if args.no_serving else measure_serving(dn, synth)
     grad = None if args.no_grad else measure_grad(dn, synth, torch, barrier, lib, B=args.grad_samples)
+    sampler = None if args.no_sampler else measure_sampler(dn, synth, torch, barrier)
 
     peaks, src = _peaks()
     roof, families = roofline(prof, args.steps, desc, N, Bs, peaks, src, clocks)
@@ -524,6 +593,7 @@ def main():
         "recompute": recompute,
         "n1024": n1024,
         "grad": grad,
+        "sampler": sampler,
         "serving": serving,
         "kernels": [{"name": k, "launches": n // args.steps, "ms_per_step": v / args.steps,
                      "share": v / total_k} for k, n, v in kernels[:16]],

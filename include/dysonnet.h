@@ -241,6 +241,37 @@ dn_status dn_logpsi_grad(dn_model *model, int N, const int8_t *spins_dev, int B,
 dn_status dn_sr_matrices(const void *O_dev, int B, size_t n_params, dn_precision prec, void *stream, double *gram_dev,
                          size_t k0, int nk, double *s_dev);
 
+/* Counters of dn_sampler_batch(): proposals decided, proposals accepted, and proposals
+ * that fell into the ambiguous window (each decided exactly and followed by a cache
+ * refresh of its chain). */
+typedef struct {
+    unsigned long long proposals, accepted, refreshes;
+} dn_sampler_stats;
+
+/* One batch of the screened typewriter sampler (Alg. 2, Sec. "Screened typewriter
+ * sampler"; screened acceptance, App. "Screened Metropolis sampler is exact") on C
+ * Markov chains:
+ *   spins_dev [C][N] int8 (+-1), updated in place;
+ *   sites_dev [C][K] int32: single-site proposals of each chain, decided in order
+ *     (-1 = no proposal).  The proposals of a batch are evaluated against the caches of
+ *     the configuration the batch starts from (independent scattering approximation), so
+ *     they should be spaced by at least the window (the typewriter schedule: one site in
+ *     every other block of width s >= w);
+ *   u_dev [C][K] float64: the uniforms of the Metropolis tests;
+ *   eps >= 0: half-width of the ambiguous window.  A proposal with |u - min(1, R~)| <= eps
+ *     (R~ the ratio from the scattering approximation) is decided with the exact ratio
+ *     from two full forward passes, and its chain's caches are rebuilt from the new
+ *     configuration before the chain continues.  Decisions equal exact Metropolis
+ *     decisions whenever |min(1, R~) - min(1, R)| <= eps for every proposal;
+ *   accepted_dev [C][K] int8 (may be NULL): 1 where the proposal was accepted;
+ *   stats (may be NULL): counters of the call.
+ * prec DN_FP64 or DN_FP32.  The call synchronises `stream`.
+ * Errors: DN_EINVAL (bad arguments, spins not +-1), DN_EUNSUPPORTED (DN_BF16), DN_ENOMEM,
+ * DN_ECUDA. */
+dn_status dn_sampler_batch(dn_model *model, int N, int8_t *spins_dev, int C, const int32_t *sites_dev,
+                           const double *u_dev, int K, double eps, dn_precision prec, void *stream,
+                           int8_t *accepted_dev, dn_sampler_stats *stats);
+
 /* Wait for `stream`, then report the cache's sticky device flag:
  * DN_OK, DN_EINVAL (invalid spins or flip sites were seen), DN_ECUDA. */
 dn_status dn_cache_check(const dn_cache *cache, void *stream);

@@ -164,6 +164,86 @@ def sr_matrices(O: np.ndarray, block=None):
     return G, S
 
 
+def _flipped(sigma: np.ndarray, site: int) -> np.ndarray:
+    s = sigma.copy()
+    s[site] = -s[site]
+    return s
+
+
+def _f(desc, om):
+    """log of the amplitude function of the readout: sum_k log cosh(Omega_k) (or the identity)."""
+    om = np.asarray(om, dtype=np.float64)
+    if desc.fkind == 0:
+        a = np.abs(om)
+        return np.sum(a + np.log1p(np.exp(-2.0 * a)) - np.log(2.0), axis=-1)
+    return np.sum(om, axis=-1)
+
+
+def metropolis_exact(desc, params, spins: np.ndarray, sites: np.ndarray, u: np.ndarray):
+    """Sequential Metropolis with exact amplitudes: for each chain and each proposal in order,
+    accept iff u < min(1, |psi(sigma')|^2 / |psi(sigma)|^2).  Returns (spins, accepted)."""
+    spins = np.array(spins, dtype=np.int8)
+    C, K = sites.shape
+    acc = np.zeros((C, K), dtype=np.int8)
+    for c in range(C):
+        sigma = spins[c].copy()
+        for k in range(K):
+            site = int(sites[c, k])
+            if site < 0:
+                continue
+            s2 = _flipped(sigma, site)
+            lp, _ = logpsi(desc, params, np.stack([sigma, s2]))
+            if u[c, k] < min(1.0, np.exp(2.0 * (lp[1] - lp[0]))):
+                sigma = s2
+                acc[c, k] = 1
+        spins[c] = sigma
+    return spins, acc
+
+
+def sampler_batch(desc, params, spins: np.ndarray, sites: np.ndarray, u: np.ndarray, eps: float):
+    """One batch of the screened typewriter sampler (Alg. 2) in the algorithm's order.  The
+    update vector of a proposal is Omega(sigma0 with the flip) - Omega(sigma0) by two full
+    forward passes (what ABACUS computes exactly, Theorem 1).  Returns (spins, accepted,
+    refreshes, max_err) with max_err the largest |min(1, R~) - min(1, R)| over the proposals
+    decided from the scattering approximation."""
+    spins = np.array(spins, dtype=np.int8)
+    C, K = sites.shape
+    acc = np.zeros((C, K), dtype=np.int8)
+    refreshes, max_err = 0, 0.0
+
+    def updates(ref, c):
+        cfgs = [ref] + [(_flipped(ref, int(sites[c, k])) if sites[c, k] >= 0 else ref) for k in range(K)]
+        _, om = logpsi(desc, params, np.stack(cfgs))
+        return om[0], om[1:] - om[0]
+
+    for c in range(C):
+        sigma = spins[c].copy()
+        Om, dOm = updates(sigma, c)
+        for k in range(K):
+            site = int(sites[c, k])
+            if site < 0:
+                continue
+            p = min(1.0, float(np.exp(2.0 * (_f(desc, Om + dOm[k]) - _f(desc, Om)))))
+            s2 = _flipped(sigma, site)
+            lp, _ = logpsi(desc, params, np.stack([sigma, s2]))
+            p_exact = min(1.0, float(np.exp(2.0 * (lp[1] - lp[0]))))
+            if abs(u[c, k] - p) <= eps:
+                take = u[c, k] < p_exact
+                if take:
+                    sigma = s2
+                refreshes += 1
+                Om, dOm = updates(sigma, c)
+            else:
+                max_err = max(max_err, abs(p - p_exact))
+                take = u[c, k] < p
+                if take:
+                    sigma = s2
+                    Om = Om + dOm[k]
+            acc[c, k] = 1 if take else 0
+        spins[c] = sigma
+    return spins, acc, refreshes, max_err
+
+
 def dlogpsi(desc, params, spins: np.ndarray, sample: np.ndarray, sites: np.ndarray) -> np.ndarray:
     """log psi(sigma') - log psi(sigma) for each flip set, by full recompute."""
     spins = np.ascontiguousarray(spins, dtype=np.int8)

@@ -44,6 +44,7 @@ struct AbArgs {
     const double *Omega;
     unsigned *flag;
     Weights<T> w;
+    double *dOmega;             // optional [F][dout]: the update vector of each flip set (Alg. 2), or null
 };
 
 constexpr int kAbThreads = 256;
@@ -263,8 +264,9 @@ __device__ __forceinline__ void abacus_flip_set(const AbArgs<T> &a, long long f,
             const double om = a.Omega[b * dout + k];
             const double dk = red[k * blockDim.x];
             res += a.f_kind == 0 ? (log_cosh_ab(om + dk) - log_cosh_ab(om)) : dk;
+            if (a.dOmega) a.dOmega[f * dout + k] = dk;
         }
-        out[f] = res;
+        if (out) out[f] = res;
     }
 }
 
@@ -292,9 +294,11 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus_multi(const AbArgs<T> *__
 
 template <typename T>
 cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
-                          const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st) {
+                          const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st,
+                          double *dOmega) {
     if (F <= 0) return cudaSuccess;
     AbArgs<T> a;
+    a.dOmega = dOmega;
     a.g = geom_of(m, c->N);
     a.B = c->B;
     a.WF = c->WF;
@@ -1339,6 +1343,7 @@ static AbArgs<T> ab_args(const dn_model *m, const Plan<T> &pl, const Weights<T> 
     a.Omega = c->Omega;
     a.flag = c->flag;
     a.w = w;
+    a.dOmega = nullptr;
     return a;
 }
 
@@ -1575,10 +1580,10 @@ template cudaError_t launch_abacus_singles<float>(const dn_model *, const Plan<f
 
 template cudaError_t launch_abacus<double>(const dn_model *, const Plan<double> &, const Weights<double> &,
                                            const dn_cache *, const int32_t *, const int32_t *, int, double *,
-                                           cudaStream_t);
+                                           cudaStream_t, double *);
 template cudaError_t launch_abacus<float>(const dn_model *, const Plan<float> &, const Weights<float> &,
                                           const dn_cache *, const int32_t *, const int32_t *, int, double *,
-                                          cudaStream_t);
+                                          cudaStream_t, double *);
 
 // ------------------------------------------------------ local estimator ----
 // Connected flip sets.  kind 0 (TFIM): every single site, f = b N + i.

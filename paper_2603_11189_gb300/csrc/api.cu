@@ -786,6 +786,109 @@ dn_status dn_sr_matrices(const void *O_dev, int B, size_t n_params, dn_precision
     });
 }
 
+dn_status dn_sampler_batch(dn_model *m, int N, int8_t *spins_dev, int C, const int32_t *sites_dev, const double *u_dev,
+                           int K, double eps, dn_precision prec, void *stream, int8_t *accepted_dev,
+                           dn_sampler_stats *stats) {
+    if (!m || !spins_dev || !sites_dev || !u_dev || N < 1 || C < 1 || K < 1 || !(eps >= 0.0)) return DN_EINVAL;
+    if (!prec_valid(prec)) return DN_EINVAL;
+    if (prec == DN_BF16) return DN_EUNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return guard([&]() -> dn_status {
+        dn::ProfPhase phase("sampler");
+        const int dout = m->desc.d_out;
+        const long long F = (long long)C * K;
+        DevBuf dom((size_t)F * dout * sizeof(double), st), om((size_t)C * dout * sizeof(double), st),
+            kpos((size_t)C * sizeof(int32_t), st), amb((size_t)C * sizeof(int32_t), st),
+            list((size_t)C * sizeof(int32_t), st), smp((size_t)F * sizeof(int32_t), st),
+            sts((size_t)F * 2 * sizeof(int32_t), st), cnt(3 * sizeof(unsigned long long), st);
+        ck(cudaMemsetAsync(cnt.p, 0, 3 * sizeof(unsigned long long), st));
+        ck(cudaMemsetAsync(kpos.p, 0, (size_t)C * sizeof(int32_t), st));
+        if (accepted_dev) ck(cudaMemsetAsync(accepted_dev, 0, (size_t)F, st));
+        auto abacus_updates = [&](dn_cache *c, long long nf, double *dst) {
+            if (c->prec == DN_FP64)
+                ck(dn::launch_abacus<double>(m, m->plan64.at(N), m->w64, c, smp.as<int32_t>(), sts.as<int32_t>(),
+                                             (int)nf, nullptr, st, dst));
+            else
+                ck(dn::launch_abacus<float>(m, m->plan32.at(N), m->w32, c, smp.as<int32_t>(), sts.as<int32_t>(),
+                                            (int)nf, nullptr, st, dst));
+        };
+        auto check_cache = [&](dn_cache *c) {
+            const dn_status s = dn_cache_check(c, stream);
+            if (s != DN_OK) {
+                dn_cache_destroy(c);
+                throw Fail{s};
+            }
+        };
+        // caches of the starting configurations and the update vector of every proposal
+        {
+            dn_cache *c = nullptr;
+            dn_status s = dysonnet_forward_cache(m, N, spins_dev, C, prec, 1, stream, &c, nullptr);
+            if (s != DN_OK) return s;
+            check_cache(c);
+            try {
+                ck(dn::launch_flip_list(C, K, sites_dev, nullptr, nullptr, smp.as<int32_t>(), sts.as<int32_t>(), st));
+                abacus_updates(c, F, dom.as<double>());
+                ck(cudaMemcpyAsync(om.p, c->Omega, (size_t)C * dout * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                check_cache(c);
+            } catch (...) {
+                dn_cache_destroy(c);
+                throw;
+            }
+            dn_cache_destroy(c);
+        }
+        std::vector<int32_t> ambh((size_t)C);
+        for (;;) {
+            ck(dn::launch_screened_sweep(N, C, K, dout, m->desc.f_kind, eps, sites_dev, u_dev, dom.as<double>(),
+                                         om.as<double>(), kpos.as<int32_t>(), spins_dev, accepted_dev,
+                                         amb.as<int32_t>(), cnt.as<unsigned long long>(), st));
+            ck(cudaMemcpyAsync(ambh.data(), amb.p, (size_t)C * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            ck(cudaStreamSynchronize(st));
+            std::vector<int32_t> lst;
+            for (int c = 0; c < C; ++c)
+                if (ambh[c] >= 0) lst.push_back(c);
+            if (lst.empty()) break;
+            const int n = (int)lst.size();
+            ck(cudaMemcpyAsync(list.p, lst.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            // exact decisions: log psi of the current configuration and of the proposal
+            DevBuf cfg((size_t)2 * n * N, st), lp((size_t)2 * n * sizeof(double), st), rows((size_t)n * N, st);
+            ck(dn::launch_pair_configs(N, K, n, list.as<int32_t>(), amb.as<int32_t>(), sites_dev, spins_dev,
+                                       cfg.as<int8_t>(), st));
+            dn_status s = dn_full_forward(m, N, cfg.as<int8_t>(), 2 * n, prec, stream, lp.as<double>(), nullptr);
+            if (s != DN_OK) return s;
+            ck(dn::launch_exact_decide(N, K, n, list.as<int32_t>(), amb.as<int32_t>(), sites_dev, u_dev,
+                                       lp.as<double>(), spins_dev, accepted_dev, kpos.as<int32_t>(),
+                                       cnt.as<unsigned long long>(), st));
+            // refresh: caches of the new configurations, update vectors of the remaining proposals
+            ck(dn::launch_gather_rows(N, n, list.as<int32_t>(), spins_dev, rows.as<int8_t>(), st));
+            dn_cache *c = nullptr;
+            s = dysonnet_forward_cache(m, N, rows.as<int8_t>(), n, prec, 1, stream, &c, nullptr);
+            if (s != DN_OK) return s;
+            try {
+                DevBuf domn((size_t)n * K * dout * sizeof(double), st);
+                ck(dn::launch_flip_list(n, K, sites_dev, list.as<int32_t>(), kpos.as<int32_t>(), smp.as<int32_t>(),
+                                        sts.as<int32_t>(), st));
+                abacus_updates(c, (long long)n * K, domn.as<double>());
+                ck(dn::launch_scatter_refresh(K, dout, n, list.as<int32_t>(), kpos.as<int32_t>(), c->Omega,
+                                              domn.as<double>(), om.as<double>(), dom.as<double>(), st));
+                check_cache(c);
+            } catch (...) {
+                dn_cache_destroy(c);
+                throw;
+            }
+            dn_cache_destroy(c);
+        }
+        if (stats) {
+            unsigned long long h[3];
+            ck(cudaMemcpyAsync(h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+            ck(cudaStreamSynchronize(st));
+            stats->proposals = h[0];
+            stats->accepted = h[1];
+            stats->refreshes = h[2];
+        }
+        return DN_OK;
+    });
+}
+
 dn_status dn_recompute_flip_ratios(dn_model *m, int N, const int8_t *spins_dev, int B, const int32_t *sample_dev,
                                    const int32_t *sites_dev, int F, dn_precision prec, void *stream,
                                    double *dlogpsi_dev) {

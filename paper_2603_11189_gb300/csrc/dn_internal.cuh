@@ -271,6 +271,22 @@ size_t gram_tc_partial_elems(int n, long long K, int *nsplit);
 cudaError_t launch_gram_tc(const float *X, int n, long long K, const float *m, double scale, double *S, float *part,
                            int nsplit, unsigned *flag, cudaStream_t st);
 
+// Screened typewriter sampler (sampler.cu).
+cudaError_t launch_flip_list(int C, int K, const int32_t *sites, const int32_t *row, const int32_t *kfrom,
+                             int32_t *sample, int32_t *fsites, cudaStream_t st);
+cudaError_t launch_screened_sweep(int N, int C, int K, int dout, int f_kind, double eps, const int32_t *sites,
+                                  const double *u, const double *dOm, double *Om, int32_t *kpos, int8_t *spins,
+                                  int8_t *acc, int32_t *amb, unsigned long long *counters, cudaStream_t st);
+cudaError_t launch_pair_configs(int N, int K, int n, const int32_t *list, const int32_t *amb, const int32_t *sites,
+                                const int8_t *spins, int8_t *cfg, cudaStream_t st);
+cudaError_t launch_exact_decide(int N, int K, int n, const int32_t *list, const int32_t *amb, const int32_t *sites,
+                                const double *u, const double *lp, int8_t *spins, int8_t *acc, int32_t *kpos,
+                                unsigned long long *counters, cudaStream_t st);
+cudaError_t launch_gather_rows(int N, int n, const int32_t *list, const int8_t *spins, int8_t *dst, cudaStream_t st);
+cudaError_t launch_scatter_refresh(int K, int dout, int n, const int32_t *list, const int32_t *kpos,
+                                   const double *Om_new, const double *dOm_new, double *Om, double *dOm,
+                                   cudaStream_t st);
+
 // Tensor-core forward pass (forward_tc.cu); activations channel-major h[c][n B + b].
 bool forward_tc_ok(const Geom &g);
 cudaError_t launch_h0_cm(const Geom &g, const int8_t *spins, const float *e, int B, float *h, cudaStream_t st);
@@ -281,9 +297,11 @@ cudaError_t launch_mix_tc(const Geom &g, int l, const Weights<float> &w, const f
                           float *hcm, int B, int planes, unsigned *flag, cudaStream_t st);
 
 // ABACUS (abacus.cu).
+// out [F] (may be null) log-amplitude ratios; dOmega [F][dout] (may be null) update vectors.
 template <typename T>
 cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
-                          const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st);
+                          const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st,
+                          double *dOmega = nullptr);
 // Flip sets of several caches of one model in one launch (serving): descs is a device
 // array of abacus_desc_bytes<T>() records filled by abacus_desc<T>(); flip f uses
 // cache cache_of[f]; all caches share max_cluster (slice width WF).

@@ -37,6 +37,10 @@ class Hamiltonian(ctypes.Structure):
                 ("J1", ctypes.c_double), ("J2", ctypes.c_double), ("periodic", ctypes.c_int), ("kac", ctypes.c_int)]
 
 
+class SamplerStats(ctypes.Structure):
+    _fields_ = [("proposals", ctypes.c_ulonglong), ("accepted", ctypes.c_ulonglong), ("refreshes", ctypes.c_ulonglong)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_ulonglong), ("flips", ctypes.c_ulonglong), ("batches", ctypes.c_ulonglong),
                 ("cache_builds", ctypes.c_ulonglong), ("evictions", ctypes.c_ulonglong),
@@ -93,6 +97,7 @@ def _lib():
         "dn_model_nparams": (sz, [vp]),
         "dn_logpsi_grad": (i32, [vp, i32, vp, i32, i32, vp, vp, vp, vp, vp]),
         "dn_sr_matrices": (i32, [vp, i32, sz, i32, vp, vp, sz, i32, vp]),
+        "dn_sampler_batch": (i32, [vp, i32, vp, i32, vp, vp, i32, dbl, i32, vp, vp, ctypes.POINTER(SamplerStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -109,7 +114,7 @@ def exported_symbols():
             "dn_recompute_flip_ratios", "dn_cache_check", "dn_cache_info", "dn_cache_tensor", "dn_cache_destroy",
             "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable",
             "dn_profile_count", "dn_profile_get", "dn_server_create", "dn_server_set_chain", "dn_server_submit",
-            "dn_server_wait", "dn_server_get_stats", "dn_server_destroy", "dn_model_nparams", "dn_logpsi_grad", "dn_sr_matrices"]
+            "dn_server_wait", "dn_server_get_stats", "dn_server_destroy", "dn_model_nparams", "dn_logpsi_grad", "dn_sr_matrices", "dn_sampler_batch"]
 
 
 def _check(status: int, what: str):
@@ -250,6 +255,20 @@ class Model:
         _check(_lib().dn_logpsi_grad(self._h, N, _ptr(spins), B, PRECISIONS[prec], _stream(stream), _ptr(lp),
                                      _ptr(O), _ptr(w), _ptr(vjp)), "dn_logpsi_grad")
         return lp, O, vjp
+
+    def sampler_batch(self, spins: torch.Tensor, sites: torch.Tensor, u: torch.Tensor, eps: float, prec="fp32",
+                      stream=None):
+        """One batch of the screened typewriter sampler on C chains (spins [C][N] int8 updated in
+        place; sites [C][K] int32 proposals, -1 = none; u [C][K] float64).  Returns
+        (accepted [C][K] int8, {"proposals", "accepted", "refreshes"})."""
+        C, N = spins.shape
+        K = sites.shape[1]
+        acc = torch.empty((C, K), dtype=torch.int8, device=spins.device)
+        st = SamplerStats()
+        _check(_lib().dn_sampler_batch(self._h, N, _ptr(spins), C, _ptr(sites), _ptr(u), K, float(eps),
+                                       PRECISIONS[prec], _stream(stream), _ptr(acc), ctypes.byref(st)),
+               "dn_sampler_batch")
+        return acc, {"proposals": st.proposals, "accepted": st.accepted, "refreshes": st.refreshes}
 
     def recompute_flip_ratios(self, spins: torch.Tensor, sample: torch.Tensor, sites: torch.Tensor, prec="fp32",
                               stream=None, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -251,3 +251,21 @@ def make_spins(cfg: dict, B: int | None = None) -> np.ndarray:
     if cfg["spins"] == "uniform":
         return spins_uniform(B, cfg["N"], cfg["spins_seed"])
     return spins_zero_magnetisation(B, cfg["N"], cfg["spins_seed"])
+
+
+def typewriter_sites(C: int, N: int, s: int, parity: int, seed: int) -> np.ndarray:
+    """Proposal sites of one typewriter half-sweep for C chains: the chain is cut into blocks
+    of width s; every block of the given parity (0: even, 1: odd) gets one uniformly drawn
+    site.  int32 [C][K], K = number of such blocks."""
+    blocks = [b for b in range((N + s - 1) // s) if b % 2 == parity]
+    u = SplitMix64(seed).uniform(C * len(blocks)).reshape(C, len(blocks))
+    out = np.empty((C, len(blocks)), dtype=np.int32)
+    for j, b in enumerate(blocks):
+        width = min(s, N - b * s)
+        out[:, j] = b * s + np.minimum((u[:, j] * width).astype(np.int64), width - 1)
+    return out
+
+
+def uniforms(C: int, K: int, seed: int) -> np.ndarray:
+    """Uniform [0, 1) float64 [C][K] (the Metropolis test draws)."""
+    return SplitMix64(seed).uniform(C * K).reshape(C, K)
