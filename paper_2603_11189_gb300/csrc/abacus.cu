@@ -94,14 +94,14 @@ __device__ __forceinline__ void abacus_flip_set(const AbArgs<T> &a, long long f,
     }
     __syncthreads();
     const int status = info[0];
-    if (status == 1) {
-        if (tid == 0) out[f] = 0.0;
-        return;
-    }
-    if (status == 2) {
+    if (status == 1 || status == 2) {
+        // empty entry: zero; invalid entry: NaN and the sticky flag (each output is optional)
         if (tid == 0) {
-            out[f] = nan("");
-            atomicOr(a.flag, 2u);
+            const double v = status == 1 ? 0.0 : nan("");
+            if (out) out[f] = v;
+            if (a.dOmega)
+                for (int k = 0; k < dout; ++k) a.dOmega[f * dout + k] = v;
+            if (status == 2) atomicOr(a.flag, 2u);
         }
         return;
     }
