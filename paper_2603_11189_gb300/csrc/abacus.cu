@@ -35,8 +35,10 @@ __device__ __forceinline__ double log_cosh_ab(double x) {
     return a + log1p(exp(-2.0 * a)) - 0.69314718055994530942;
 }
 
+// 16-byte aligned, so that an array of these (the serving kernel's descriptor table, filled
+// by the host with abacus_desc_bytes() per record) has the same stride on both sides.
 template <typename T>
-struct AbArgs {
+struct alignas(16) AbArgs {
     Geom g;
     int B, WF, Rk, Rl, P, max_cluster, f_kind;
     const int8_t *spins;
@@ -1350,6 +1352,7 @@ static AbArgs<T> ab_args(const dn_model *m, const Plan<T> &pl, const Weights<T> 
 // Descriptor of a cache for k_abacus_multi (a plain struct, copied to the device by the caller).
 template <typename T>
 size_t abacus_desc_bytes() {
+    static_assert(sizeof(AbArgs<T>) % 16 == 0, "descriptor records are read as an array on the device");
     return sizeof(AbArgs<T>);
 }
 
