@@ -378,6 +378,42 @@ def measure_sampler(dn, synth, torch, barrier, C=4096, s=8, eps=0.01, sweeps=2):
             "speedup": ex_ms / scr_ms}
 
 
+def measure_bf16_forward(dn, synth, torch, barrier, lib, B=2048, reps=3):
+    """Full forward passes (log psi) of the N = 256, 6-layer, 64-channel, 64-mode model in BF16
+    on the tensor cores (S4 convolutions as Toeplitz GEMMs with the configurations as columns,
+    channel mixing and gate as two chained MMAs) and in FP32 on the FMA kernels, B configurations
+    each; the BF16 result's largest deviation from FP32 is reported beside the timings."""
+    N = 256
+    desc = synth.ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=1)
+    params = synth.init_params(desc, 1003, a_scale=10.0)
+    model = dn.Model(desc, params)
+    spins = torch.from_numpy(synth.spins_uniform(B, N, 2003)).cuda()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    lps = {}
+    for prec in ("bf16", "fp32"):
+        lps[prec] = model.full_forward(spins, prec=prec)
+        barrier()
+        lib.dn_profile_enable(1)
+        ev0.record()
+        for _ in range(reps):
+            model.full_forward(spins, prec=prec)
+        ev1.record()
+        barrier()
+        prof = read_profile(lib)
+        lib.dn_profile_enable(0)
+        ms = ev0.elapsed_time(ev1) / reps
+        out[prec] = {"value": B / (ms / 1e3), "unit": "configurations/s", "ms": ms,
+                     "kernels": {k: round(v[1] / reps, 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]}}
+    # tensor-core work of the BF16 forward: convolution 2 N^2 d and mixing 2 x 2 N d^2 flops per layer
+    flops = 6 * B * (2.0 * N * N * 64 + 4.0 * N * 64 * 64)
+    out["bf16"]["tflops"] = flops / (out["bf16"]["ms"] / 1e3) / 1e12
+    dev = (lps["bf16"] - lps["fp32"]).abs() / lps["fp32"].abs().clamp(min=1.0)
+    out["bf16_vs_fp32_max_rel"] = float(dev.max())
+    model.close()
+    return {"workload": "J1-J2 ring N=256, DysonNet L=6 d=64 s=64 w=2, %d configurations, full forward" % B, **out}
+
+
 def measure_serving(dn, synth, n_req=160, rate=20.0, seed=4005):
     """Serving workload: Markov chains with N in {64, 128, 256, 512, 1024} (two each) of
     the 6-layer, 64-channel, 64-mode model (FP32), requests of 1-512 random single-flip
@@ -455,6 +491,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-sampler", action="store_true")
+    ap.add_argument("--no-bf16-forward", action="store_true")
+    ap.add_argument("--bf16-samples", type=int, default=2048)
     ap.add_argument("--grad-samples", type=int, default=4096)
     ap.add_argument("--n1024-chains", type=int, default=4)
     args = ap.parse_args()
@@ -569,6 +607,8 @@ def main():
     serving = None if args.no_serving else measure_serving(dn, synth)
     grad = None if args.no_grad else measure_grad(dn, synth, torch, barrier, lib, B=args.grad_samples)
     sampler = None if args.no_sampler else measure_sampler(dn, synth, torch, barrier)
+    bf16_forward = None if args.no_bf16_forward else measure_bf16_forward(dn, synth, torch, barrier, lib,
+                                                                           B=args.bf16_samples)
 
     peaks, src = _peaks()
     roof, families = roofline(prof, args.steps, desc, N, Bs, peaks, src, clocks)
@@ -594,6 +634,7 @@ def main():
         "n1024": n1024,
         "grad": grad,
         "sampler": sampler,
+        "bf16_forward": bf16_forward,
         "serving": serving,
         "kernels": [{"name": k, "launches": n // args.steps, "ms_per_step": v / args.steps,
                      "share": v / total_k} for k, n, v in kernels[:16]],
