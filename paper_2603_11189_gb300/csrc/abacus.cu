@@ -349,24 +349,28 @@ cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T>
 // Every link byte of a configuration is read once per call.
 constexpr int kLayMaxW = 9;
 
+// One CTA per (64 (flip, slot) rows, layer).  The MLP weights are staged once; the
+// activations are kept transposed ([feature][row]) so that a thread (output feature, group
+// of 8 rows) reads its 8 rows as two 16-byte broadcasts and its weight row without bank
+// conflicts (row stride dh + 1 / d + 1).
 template <typename T>
 __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__ DX) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Geom &g = a.g;
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
-    constexpr int RT = 64;                                  // rows per CTA
-    T *W1s = reinterpret_cast<T *>(smraw);                  // [dh][dh]  (in, out)
-    T *W2s = W1s + dh * dh;                                 // [dh][d]
-    T *ph = W2s + dh * d;                                   // [RT][dh]
-    T *ac = ph + RT * dh;                                   // [RT][dh]
+    constexpr int RT = 64, RG = 8;                          // rows per CTA, rows per thread
+    T *phT = reinterpret_cast<T *>(smraw);                  // [dh][RT]  phi, then GELU(z)
+    T *acT = phT + dh * RT;                                 // [dh][RT]
+    T *W1s = acT + dh * RT;                                 // [f][e] = W1[e][f], row stride dh + 1
+    T *W2s = W1s + dh * (dh + 1);                           // [e][c] = W2[c][e], row stride d + 1
     const int l = blockIdx.y;
     const long long rows = (long long)a.B * N * W;
     const long long r0 = (long long)blockIdx.x * RT;
     const T *W1T = a.w.W1T + (long long)l * dh * dh, *W2T = a.w.W2T + (long long)l * dh * d;
     const T *b1 = a.w.b1 + (long long)l * dh, *b2 = a.w.b2 + (long long)l * d;
     const T *kap = a.w.kappa + (long long)l * W * dh, *beta = a.w.beta + (long long)l * dh;
-    for (int q = threadIdx.x; q < dh * dh; q += blockDim.x) W1s[q] = W1T[q];
-    for (int q = threadIdx.x; q < dh * d; q += blockDim.x) W2s[q] = W2T[q];
+    for (int q = threadIdx.x; q < dh * dh; q += blockDim.x) W1s[(q / dh) * (dh + 1) + q % dh] = W1T[q];
+    for (int q = threadIdx.x; q < dh * d; q += blockDim.x) W2s[(q / d) * (d + 1) + q % d] = W2T[q];
     for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
         const int rr = q / dh, e = q % dh;
         const long long r = r0 + rr;
@@ -393,31 +397,49 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
                 }
             }
         }
-        ph[q] = acc;
+        phT[e * RT + rr] = acc;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
-        const int rr = q / dh, e = q % dh;
-        T acc = b1[e];
-        for (int f = 0; f < dh; ++f) acc += W1s[f * dh + e] * ph[rr * dh + f];
-        ac[q] = gelu_ab<T>(acc);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < RT * d; q += blockDim.x) {
-        const int rr = q / d, c = q % d;
-        const long long r = r0 + rr;
-        if (r >= rows) continue;
-        const int t = (int)(r % W), j = (int)((r / W) % N);
-        const long long b = r / ((long long)W * N);
-        int i = j - wd + t;
-        T v = 0;
-        if (g.periodic || (i >= 0 && i < N)) {
-            if (g.periodic) i = ((i % N) + N) % N;
-            T chin = b2[c];
-            for (int e = 0; e < dh; ++e) chin += W2s[e * d + c] * ac[rr * dh + e];
-            v = chin - a.chi[((b * L + l) * N + i) * d + c];
+    for (int q = threadIdx.x; q < dh * (RT / RG); q += blockDim.x) {
+        const int e = q % dh, t0 = (q / dh) * RG;
+        T acc[RG];
+#pragma unroll
+        for (int u = 0; u < RG; ++u) acc[u] = b1[e];
+        for (int f = 0; f < dh; ++f) {
+            const T wv = W1s[f * (dh + 1) + e];
+            const T *pp = phT + f * RT + t0;
+#pragma unroll
+            for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
         }
-        DX[((long long)l * rows + r) * d + c] = v;
+#pragma unroll
+        for (int u = 0; u < RG; ++u) acT[e * RT + t0 + u] = gelu_ab<T>(acc[u]);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < d * (RT / RG); q += blockDim.x) {
+        const int c = q % d, t0 = (q / d) * RG;
+        T acc[RG];
+#pragma unroll
+        for (int u = 0; u < RG; ++u) acc[u] = b2[c];
+        for (int e = 0; e < dh; ++e) {
+            const T wv = W2s[e * (d + 1) + c];
+            const T *pp = acT + e * RT + t0;
+#pragma unroll
+            for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
+        }
+#pragma unroll
+        for (int u = 0; u < RG; ++u) {
+            const long long r = r0 + t0 + u;
+            if (r >= rows) continue;
+            const int t = (int)(r % W), j = (int)((r / W) % N);
+            const long long b = r / ((long long)W * N);
+            int i = j - wd + t;
+            T v = 0;
+            if (g.periodic || (i >= 0 && i < N)) {
+                if (g.periodic) i = ((i % N) + N) % N;
+                v = acc[u] - a.chi[((b * L + l) * N + i) * d + c];
+            }
+            DX[((long long)l * rows + r) * d + c] = v;
+        }
     }
 }
 
@@ -1455,8 +1477,10 @@ static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, con
         if (NS < 2) return cudaErrorNotSupported;
     }
     if (smem == 0) return cudaErrorNotSupported;
-    // Runs of 8 sites per warp: long enough to keep the copy ring full across sites.
-    const int R = 8;
+    // Runs of 8 sites per warp: long enough to keep the copy ring full across sites.  Layers
+    // without link blocks (no ring) use runs of 2 sites: four times the warps for the same
+    // work, which is latency-bound there.
+    const int R = NS == 0 ? 2 : 8;
     dim3 grid((unsigned)((g.N + kStWarps * R - 1) / (kStWarps * R)), (unsigned)a.B);
     if (g.W == 5) return launch_ab_stream_ns<5>(a, l, R, NS, grid, smem, S, DX, PART, st);
     if (g.W == 3) return launch_ab_stream_ns<3>(a, l, R, NS, grid, smem, S, DX, PART, st);
@@ -1526,7 +1550,7 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     const Geom g = geom_of(m, c->N);
     if (g.W > kLayMaxW || g.d > 128) return cudaErrorNotSupported;
     const size_t lsm = (2 * (size_t)g.d * g.d + 8 * ((size_t)g.W * g.W * g.d + 2 * (size_t)g.W * g.d)) * sizeof(T);
-    const size_t tsm = ((size_t)g.dh * g.dh + (size_t)g.dh * g.d + 2 * 64 * (size_t)g.dh) * sizeof(T);
+    const size_t tsm = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1) + 2 * 64 * (size_t)g.dh) * sizeof(T);
     if (lsm > 220 * 1024 || tsm > 220 * 1024) return cudaErrorNotSupported;
     const AbArgs<T> a = ab_args<T>(m, pl, w, c);
     const long long rows = (long long)c->B * c->N * g.W;

@@ -144,14 +144,21 @@ cudaError_t launch_check_spins(const int8_t *spins, long long n, int8_t *copy, u
 }
 
 // ------------------------------------------------------------------- chi --
-constexpr int kChiTile = 16;
+// One CTA per (sample, layer, tile of kChiTile sites).  W1 and W2 of the layer are staged
+// once (row strides dh + 1 and d + 1, so a warp reading along either index hits distinct
+// banks); phi and GELU(z) are kept transposed ([feature][site]) so that a thread (output
+// feature, group of 8 sites) reads its 8 sites as two 16-byte broadcasts.
+constexpr int kChiTile = 64, kChiRG = 8;
 
 template <typename T>
-__global__ void k_chi(Geom g, Weights<T> w, const int8_t *__restrict__ spins, int B, T *__restrict__ chi) {
+__global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t *__restrict__ spins, int B,
+                                             T *__restrict__ chi, int stage) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
-    T *phi = reinterpret_cast<T *>(smraw);
-    T *act = phi + kChiTile * dh;
+    T *phT = reinterpret_cast<T *>(smraw);      // [dh][tile]
+    T *acT = phT + dh * kChiTile;               // [dh][tile]
+    T *W1s = acT + dh * kChiTile;               // [f][e] = W1[e][f]
+    T *W2s = W1s + dh * (dh + 1);               // [e][c] = W2[c][e]
     const int ntile = (N + kChiTile - 1) / kChiTile;
     const long long blk = blockIdx.x;
     const int tile = (int)(blk % ntile);
@@ -163,40 +170,68 @@ __global__ void k_chi(Geom g, Weights<T> w, const int8_t *__restrict__ spins, in
     const int8_t *sp = spins + b * N;
     const T *kap = w.kappa + (long long)l * W * dh;
     const T *beta = w.beta + (long long)l * dh;
-    const T *W1T = w.W1T + (long long)l * dh * dh;
     const T *b1 = w.b1 + (long long)l * dh;
-    const T *W2T = w.W2T + (long long)l * dh * d;
     const T *b2 = w.b2 + (long long)l * d;
-    for (int idx = threadIdx.x; idx < ns * dh; idx += blockDim.x) {
+    // Weights from shared memory, or (when they do not fit) straight from global memory.
+    const T *W1p = stage ? W1s : w.W1T + (long long)l * dh * dh;
+    const T *W2p = stage ? W2s : w.W2T + (long long)l * dh * d;
+    const int s1 = stage ? dh + 1 : dh, s2 = stage ? d + 1 : d;
+    if (stage) {
+        for (int q = threadIdx.x; q < dh * dh; q += blockDim.x)
+            W1s[(q / dh) * (dh + 1) + q % dh] = w.W1T[(long long)l * dh * dh + q];
+        for (int q = threadIdx.x; q < dh * d; q += blockDim.x)
+            W2s[(q / d) * (d + 1) + q % d] = w.W2T[(long long)l * dh * d + q];
+    }
+    for (int idx = threadIdx.x; idx < kChiTile * dh; idx += blockDim.x) {
         const int t = idx / dh, e = idx % dh, i = i0 + t;
-        T acc = beta[e];
-        for (int r = -wd; r <= wd; ++r) {
-            int j = i + r;
-            T sv;
-            if (g.periodic) {
-                j = ((j % N) + N) % N;
-                sv = (T)sp[j];
-            } else {
-                sv = (j >= 0 && j < N) ? (T)sp[j] : (T)0;
+        T acc = 0;
+        if (t < ns) {
+            acc = beta[e];
+            for (int r = -wd; r <= wd; ++r) {
+                int j = i + r;
+                T sv;
+                if (g.periodic) {
+                    j = ((j % N) + N) % N;
+                    sv = (T)sp[j];
+                } else {
+                    sv = (j >= 0 && j < N) ? (T)sp[j] : (T)0;
+                }
+                acc += kap[(r + wd) * dh + e] * sv;
             }
-            acc += kap[(r + wd) * dh + e] * sv;
         }
-        phi[t * dh + e] = acc;
+        phT[e * kChiTile + t] = acc;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < ns * dh; idx += blockDim.x) {
-        const int t = idx / dh, e = idx % dh;
-        T acc = b1[e];
-        for (int f = 0; f < dh; ++f) acc += W1T[f * dh + e] * phi[t * dh + f];
-        act[t * dh + e] = gelu<T>(acc);
+    for (int q = threadIdx.x; q < dh * (kChiTile / kChiRG); q += blockDim.x) {
+        const int e = q % dh, t0 = (q / dh) * kChiRG;
+        T acc[kChiRG];
+#pragma unroll
+        for (int u = 0; u < kChiRG; ++u) acc[u] = b1[e];
+        for (int f = 0; f < dh; ++f) {
+            const T wv = W1p[f * s1 + e];
+            const T *pp = phT + f * kChiTile + t0;
+#pragma unroll
+            for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pp[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kChiRG; ++u) acT[e * kChiTile + t0 + u] = gelu<T>(acc[u]);
     }
     __syncthreads();
     T *dst = chi + ((b * L + l) * N + i0) * d;
-    for (int idx = threadIdx.x; idx < ns * d; idx += blockDim.x) {
-        const int t = idx / d, c = idx % d;
-        T acc = b2[c];
-        for (int e = 0; e < dh; ++e) acc += W2T[e * d + c] * act[t * dh + e];
-        dst[(long long)t * d + c] = acc;
+    for (int q = threadIdx.x; q < d * (kChiTile / kChiRG); q += blockDim.x) {
+        const int c = q % d, t0 = (q / d) * kChiRG;
+        T acc[kChiRG];
+#pragma unroll
+        for (int u = 0; u < kChiRG; ++u) acc[u] = b2[c];
+        for (int e = 0; e < dh; ++e) {
+            const T wv = W2p[e * s2 + c];
+            const T *pp = acT + e * kChiTile + t0;
+#pragma unroll
+            for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pp[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kChiRG; ++u)
+            if (t0 + u < ns) dst[(long long)(t0 + u) * d + c] = acc[u];
     }
 }
 
@@ -204,10 +239,15 @@ template <typename T>
 cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, int B, T *chi, cudaStream_t st) {
     const int ntile = (g.N + kChiTile - 1) / kChiTile;
     const long long blocks = (long long)B * g.L * ntile;
-    const size_t smem = 2 * kChiTile * g.dh * sizeof(T);
+    const size_t act = (size_t)2 * kChiTile * g.dh * sizeof(T);
+    const size_t wts = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1)) * sizeof(T);
+    const int stage = act + wts <= 200 * 1024 ? 1 : 0;
+    const size_t smem = act + (stage ? wts : 0);
+    cudaError_t err = cudaFuncSetAttribute(k_chi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
     {
         ProfScope _ps("k_chi", st);
-        k_chi<T><<<(unsigned)blocks, 128, smem, st>>>(g, w, spins, B, chi);
+        k_chi<T><<<(unsigned)blocks, 256, smem, st>>>(g, w, spins, B, chi, stage);
     }
     return cudaGetLastError();
 }

@@ -679,26 +679,37 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(const float *__restrict__ X,
     const float *xa = X + (long long)(ra ? a0 + r : 0) * K;
     const float *xc = X + (long long)(rc ? c0 + r : 0) * K;
     const bool vec = (K & 3) == 0;   // rows 16-byte aligned: two 16-byte loads per 8 values
-    auto stage = [&](unsigned char *dst, const float *row, bool ok, long long k0) {
+    // The 32 values of this thread's half row of chunk k0 (centred), into registers.
+    auto load = [&](float (&v)[32], const float *row, bool ok, long long k0) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int kk = kh * 32 + 8 * j;
-            const long long k = k0 + kk;
-            float v[8];
+            const long long k = k0 + kh * 32 + 8 * j;
             if (ok && vec && k + 8 <= ke) {
                 const float4 x0 = __ldg(reinterpret_cast<const float4 *>(row + k));
                 const float4 x1 = __ldg(reinterpret_cast<const float4 *>(row + k + 4));
                 const float4 m0 = __ldg(reinterpret_cast<const float4 *>(m + k));
                 const float4 m1 = __ldg(reinterpret_cast<const float4 *>(m + k + 4));
-                v[0] = x0.x - m0.x; v[1] = x0.y - m0.y; v[2] = x0.z - m0.z; v[3] = x0.w - m0.w;
-                v[4] = x1.x - m1.x; v[5] = x1.y - m1.y; v[6] = x1.z - m1.z; v[7] = x1.w - m1.w;
+                v[8 * j + 0] = x0.x - m0.x; v[8 * j + 1] = x0.y - m0.y; v[8 * j + 2] = x0.z - m0.z;
+                v[8 * j + 3] = x0.w - m0.w; v[8 * j + 4] = x1.x - m1.x; v[8 * j + 5] = x1.y - m1.y;
+                v[8 * j + 6] = x1.z - m1.z; v[8 * j + 7] = x1.w - m1.w;
             } else {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = (ok && k + u < ke) ? row[k + u] - m[k + u] : 0.f;
+                for (int u = 0; u < 8; ++u) v[8 * j + u] = (ok && k + u < ke) ? row[k + u] - m[k + u] : 0.f;
             }
-            tc::stage8_planes<NPL>(dst, plane, (uint32_t)(kk >> 4) * slab + tc::canon(r, kk & 15), v);
         }
     };
+    auto store = [&](unsigned char *dst, const float (&v)[32]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int kk = kh * 32 + 8 * j;
+            tc::stage8_planes<NPL>(dst, plane, (uint32_t)(kk >> 4) * slab + tc::canon(r, kk & 15), v + 8 * j);
+        }
+    };
+    float va[32], vc[32];
+    if (nch > 0) {
+        load(va, xa, ra, kb);
+        if (!diag) load(vc, xc, rc, kb);
+    }
     for (int c = 0; c < nch; ++c) {
         const int sidx = c & 1;
         unsigned char *A = st0 + sidx * stage_b, *Bm = A + opnd;
@@ -707,9 +718,14 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(const float *__restrict__ X,
             if (!tc::wait(mbar + sidx, (uint32_t)((c >> 1) + 1) & 1u) && lane == 0) *s_ok = 0;
             __syncwarp();
         }
-        const long long k0 = kb + (long long)c * kGcK;
-        stage(A, xa, ra, k0);
-        if (!diag) stage(Bm, xc, rc, k0);
+        store(A, va);
+        if (!diag) store(Bm, vc);
+        // the next chunk's loads are in flight during the barrier and the MMAs
+        if (c + 1 < nch) {
+            const long long k1 = kb + (long long)(c + 1) * kGcK;
+            load(va, xa, ra, k1);
+            if (!diag) load(vc, xc, rc, k1);
+        }
         tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
