@@ -348,6 +348,7 @@ cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T>
 //  k_ab_final    dOmega_j = sum_t partial + t_j dsigma_j, and the log cosh difference.
 // Every link byte of a configuration is read once per call.
 constexpr int kLayMaxW = 9;
+constexpr int kDxTPB = 8;   // row tiles per CTA of k_dchi_table
 
 // One CTA per (64 (flip, slot) rows, layer).  The MLP weights are staged once; the
 // activations are kept transposed ([feature][row]) so that a thread (output feature, group
@@ -365,80 +366,84 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
     T *W2s = W1s + dh * (dh + 1);                           // [e][c] = W2[c][e], row stride d + 1
     const int l = blockIdx.y;
     const long long rows = (long long)a.B * N * W;
-    const long long r0 = (long long)blockIdx.x * RT;
     const T *W1T = a.w.W1T + (long long)l * dh * dh, *W2T = a.w.W2T + (long long)l * dh * d;
     const T *b1 = a.w.b1 + (long long)l * dh, *b2 = a.w.b2 + (long long)l * d;
     const T *kap = a.w.kappa + (long long)l * W * dh, *beta = a.w.beta + (long long)l * dh;
     for (int q = threadIdx.x; q < dh * dh; q += blockDim.x) W1s[(q / dh) * (dh + 1) + q % dh] = W1T[q];
     for (int q = threadIdx.x; q < dh * d; q += blockDim.x) W2s[(q / d) * (d + 1) + q % d] = W2T[q];
-    for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
-        const int rr = q / dh, e = q % dh;
-        const long long r = r0 + rr;
-        T acc = 0;
-        if (r < rows) {
-            const int t = (int)(r % W), j = (int)((r / W) % N);
-            const long long b = r / ((long long)W * N);
-            const int8_t *sp = a.spins + b * N;
-            const int iu = j - wd + t;
-            const bool ok = g.periodic || (iu >= 0 && iu < N);
-            if (ok) {
-                acc = beta[e];
-                for (int o = -wd; o <= wd; ++o) {
-                    int jn = iu + o;
-                    T v;
-                    if (g.periodic) {
-                        jn = ((jn % N) + N) % N;
-                        v = (T)sp[jn];
-                    } else {
-                        v = (jn >= 0 && jn < N) ? (T)sp[jn] : (T)0;
+    for (int it = 0; it < kDxTPB; ++it) {
+        const long long r0 = ((long long)blockIdx.x * kDxTPB + it) * RT;
+        if (r0 >= rows) break;
+        __syncthreads();   // the previous tile's reads of phT / acT (and the weight staging) are done
+        for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
+            const int rr = q / dh, e = q % dh;
+            const long long r = r0 + rr;
+            T acc = 0;
+            if (r < rows) {
+                const int t = (int)(r % W), j = (int)((r / W) % N);
+                const long long b = r / ((long long)W * N);
+                const int8_t *sp = a.spins + b * N;
+                const int iu = j - wd + t;
+                const bool ok = g.periodic || (iu >= 0 && iu < N);
+                if (ok) {
+                    acc = beta[e];
+                    for (int o = -wd; o <= wd; ++o) {
+                        int jn = iu + o;
+                        T v;
+                        if (g.periodic) {
+                            jn = ((jn % N) + N) % N;
+                            v = (T)sp[jn];
+                        } else {
+                            v = (jn >= 0 && jn < N) ? (T)sp[jn] : (T)0;
+                        }
+                        if (jn == j) v = -v;
+                        acc += kap[(o + wd) * dh + e] * v;
                     }
-                    if (jn == j) v = -v;
-                    acc += kap[(o + wd) * dh + e] * v;
                 }
             }
+            phT[e * RT + rr] = acc;
         }
-        phT[e * RT + rr] = acc;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < dh * (RT / RG); q += blockDim.x) {
-        const int e = q % dh, t0 = (q / dh) * RG;
-        T acc[RG];
-#pragma unroll
-        for (int u = 0; u < RG; ++u) acc[u] = b1[e];
-        for (int f = 0; f < dh; ++f) {
-            const T wv = W1s[f * (dh + 1) + e];
-            const T *pp = phT + f * RT + t0;
-#pragma unroll
-            for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
-        }
-#pragma unroll
-        for (int u = 0; u < RG; ++u) acT[e * RT + t0 + u] = gelu_ab<T>(acc[u]);
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < d * (RT / RG); q += blockDim.x) {
-        const int c = q % d, t0 = (q / d) * RG;
-        T acc[RG];
-#pragma unroll
-        for (int u = 0; u < RG; ++u) acc[u] = b2[c];
-        for (int e = 0; e < dh; ++e) {
-            const T wv = W2s[e * (d + 1) + c];
-            const T *pp = acT + e * RT + t0;
-#pragma unroll
-            for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
-        }
-#pragma unroll
-        for (int u = 0; u < RG; ++u) {
-            const long long r = r0 + t0 + u;
-            if (r >= rows) continue;
-            const int t = (int)(r % W), j = (int)((r / W) % N);
-            const long long b = r / ((long long)W * N);
-            int i = j - wd + t;
-            T v = 0;
-            if (g.periodic || (i >= 0 && i < N)) {
-                if (g.periodic) i = ((i % N) + N) % N;
-                v = acc[u] - a.chi[((b * L + l) * N + i) * d + c];
+        __syncthreads();
+        for (int q = threadIdx.x; q < dh * (RT / RG); q += blockDim.x) {
+            const int e = q % dh, t0 = (q / dh) * RG;
+            T acc[RG];
+    #pragma unroll
+            for (int u = 0; u < RG; ++u) acc[u] = b1[e];
+            for (int f = 0; f < dh; ++f) {
+                const T wv = W1s[f * (dh + 1) + e];
+                const T *pp = phT + f * RT + t0;
+    #pragma unroll
+                for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
             }
-            DX[((long long)l * rows + r) * d + c] = v;
+    #pragma unroll
+            for (int u = 0; u < RG; ++u) acT[e * RT + t0 + u] = gelu_ab<T>(acc[u]);
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < d * (RT / RG); q += blockDim.x) {
+            const int c = q % d, t0 = (q / d) * RG;
+            T acc[RG];
+    #pragma unroll
+            for (int u = 0; u < RG; ++u) acc[u] = b2[c];
+            for (int e = 0; e < dh; ++e) {
+                const T wv = W2s[e * (d + 1) + c];
+                const T *pp = acT + e * RT + t0;
+    #pragma unroll
+                for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
+            }
+    #pragma unroll
+            for (int u = 0; u < RG; ++u) {
+                const long long r = r0 + t0 + u;
+                if (r >= rows) continue;
+                const int t = (int)(r % W), j = (int)((r / W) % N);
+                const long long b = r / ((long long)W * N);
+                int i = j - wd + t;
+                T v = 0;
+                if (g.periodic || (i >= 0 && i < N)) {
+                    if (g.periodic) i = ((i % N) + N) % N;
+                    v = acc[u] - a.chi[((b * L + l) * N + i) * d + c];
+                }
+                DX[((long long)l * rows + r) * d + c] = v;
+            }
         }
     }
 }
@@ -1477,10 +1482,8 @@ static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, con
         if (NS < 2) return cudaErrorNotSupported;
     }
     if (smem == 0) return cudaErrorNotSupported;
-    // Runs of 8 sites per warp: long enough to keep the copy ring full across sites.  Layers
-    // without link blocks (no ring) use runs of 2 sites: four times the warps for the same
-    // work, which is latency-bound there.
-    const int R = NS == 0 ? 2 : 8;
+    // Runs of 8 sites per warp: long enough to keep the copy ring full across sites.
+    const int R = 8;
     dim3 grid((unsigned)((g.N + kStWarps * R - 1) / (kStWarps * R)), (unsigned)a.B);
     if (g.W == 5) return launch_ab_stream_ns<5>(a, l, R, NS, grid, smem, S, DX, PART, st);
     if (g.W == 3) return launch_ab_stream_ns<3>(a, l, R, NS, grid, smem, S, DX, PART, st);
@@ -1564,7 +1567,7 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
         return err;
     {
         ProfScope _ps("k_dchi_table", st);
-        k_dchi_table<T><<<dim3((unsigned)((rows + 63) / 64), g.L), 256, tsm, st>>>(a, DX);
+        k_dchi_table<T><<<dim3((unsigned)((rows + 64 * kDxTPB - 1) / (64 * kDxTPB)), g.L), 256, tsm, st>>>(a, DX);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int hd = (g.d + 31) / 32;

@@ -148,7 +148,7 @@ cudaError_t launch_check_spins(const int8_t *spins, long long n, int8_t *copy, u
 // once (row strides dh + 1 and d + 1, so a warp reading along either index hits distinct
 // banks); phi and GELU(z) are kept transposed ([feature][site]) so that a thread (output
 // feature, group of 8 sites) reads its 8 sites as two 16-byte broadcasts.
-constexpr int kChiTile = 64, kChiRG = 8;
+constexpr int kChiTile = 64, kChiRG = 8, kChiTPB = 8;   // sites per tile, per thread group, tiles per CTA
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t *__restrict__ spins, int B,
@@ -160,19 +160,13 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
     T *W1s = acT + dh * kChiTile;               // [f][e] = W1[e][f]
     T *W2s = W1s + dh * (dh + 1);               // [e][c] = W2[c][e]
     const int ntile = (N + kChiTile - 1) / kChiTile;
-    const long long blk = blockIdx.x;
-    const int tile = (int)(blk % ntile);
-    const long long rest = blk / ntile;
-    const int l = (int)(rest % L);
-    const long long b = rest / L;
-    const int i0 = tile * kChiTile;
-    const int ns = min(kChiTile, N - i0);
-    const int8_t *sp = spins + b * N;
+    const int l = blockIdx.y;
     const T *kap = w.kappa + (long long)l * W * dh;
     const T *beta = w.beta + (long long)l * dh;
     const T *b1 = w.b1 + (long long)l * dh;
     const T *b2 = w.b2 + (long long)l * d;
-    // Weights from shared memory, or (when they do not fit) straight from global memory.
+    // Weights from shared memory (staged once for the CTA's tiles), or from global memory
+    // when they do not fit.
     const T *W1p = stage ? W1s : w.W1T + (long long)l * dh * dh;
     const T *W2p = stage ? W2s : w.W2T + (long long)l * dh * d;
     const int s1 = stage ? dh + 1 : dh, s2 = stage ? d + 1 : d;
@@ -182,63 +176,73 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
         for (int q = threadIdx.x; q < dh * d; q += blockDim.x)
             W2s[(q / d) * (d + 1) + q % d] = w.W2T[(long long)l * dh * d + q];
     }
-    for (int idx = threadIdx.x; idx < kChiTile * dh; idx += blockDim.x) {
-        const int t = idx / dh, e = idx % dh, i = i0 + t;
-        T acc = 0;
-        if (t < ns) {
-            acc = beta[e];
-            for (int r = -wd; r <= wd; ++r) {
-                int j = i + r;
-                T sv;
-                if (g.periodic) {
-                    j = ((j % N) + N) % N;
-                    sv = (T)sp[j];
-                } else {
-                    sv = (j >= 0 && j < N) ? (T)sp[j] : (T)0;
+    const long long items = (long long)B * ntile;
+    for (int it = 0; it < kChiTPB; ++it) {
+        const long long item = (long long)blockIdx.x * kChiTPB + it;
+        if (item >= items) break;
+        const long long b = item / ntile;
+        const int i0 = (int)(item % ntile) * kChiTile;
+        const int ns = min(kChiTile, N - i0);
+        const int8_t *sp = spins + b * N;
+        __syncthreads();   // previous tile's reads of phT / acT (and the weight staging) are done
+        for (int idx = threadIdx.x; idx < kChiTile * dh; idx += blockDim.x) {
+            const int t = idx / dh, e = idx % dh, i = i0 + t;
+            T acc = 0;
+            if (t < ns) {
+                acc = beta[e];
+                for (int r = -wd; r <= wd; ++r) {
+                    int j = i + r;
+                    T sv;
+                    if (g.periodic) {
+                        j = ((j % N) + N) % N;
+                        sv = (T)sp[j];
+                    } else {
+                        sv = (j >= 0 && j < N) ? (T)sp[j] : (T)0;
+                    }
+                    acc += kap[(r + wd) * dh + e] * sv;
                 }
-                acc += kap[(r + wd) * dh + e] * sv;
             }
+            phT[e * kChiTile + t] = acc;
         }
-        phT[e * kChiTile + t] = acc;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < dh * (kChiTile / kChiRG); q += blockDim.x) {
-        const int e = q % dh, t0 = (q / dh) * kChiRG;
-        T acc[kChiRG];
+        __syncthreads();
+        for (int q = threadIdx.x; q < dh * (kChiTile / kChiRG); q += blockDim.x) {
+            const int e = q % dh, t0 = (q / dh) * kChiRG;
+            T acc[kChiRG];
 #pragma unroll
-        for (int u = 0; u < kChiRG; ++u) acc[u] = b1[e];
-        for (int f = 0; f < dh; ++f) {
-            const T wv = W1p[f * s1 + e];
-            const T *pp = phT + f * kChiTile + t0;
+            for (int u = 0; u < kChiRG; ++u) acc[u] = b1[e];
+            for (int f = 0; f < dh; ++f) {
+                const T wv = W1p[f * s1 + e];
+                const T *pp = phT + f * kChiTile + t0;
 #pragma unroll
-            for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pp[u];
+                for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pp[u];
+            }
+#pragma unroll
+            for (int u = 0; u < kChiRG; ++u) acT[e * kChiTile + t0 + u] = gelu<T>(acc[u]);
         }
+        __syncthreads();
+        T *dst = chi + ((b * L + l) * N + i0) * d;
+        for (int q = threadIdx.x; q < d * (kChiTile / kChiRG); q += blockDim.x) {
+            const int c = q % d, t0 = (q / d) * kChiRG;
+            T acc[kChiRG];
 #pragma unroll
-        for (int u = 0; u < kChiRG; ++u) acT[e * kChiTile + t0 + u] = gelu<T>(acc[u]);
-    }
-    __syncthreads();
-    T *dst = chi + ((b * L + l) * N + i0) * d;
-    for (int q = threadIdx.x; q < d * (kChiTile / kChiRG); q += blockDim.x) {
-        const int c = q % d, t0 = (q / d) * kChiRG;
-        T acc[kChiRG];
+            for (int u = 0; u < kChiRG; ++u) acc[u] = b2[c];
+            for (int e = 0; e < dh; ++e) {
+                const T wv = W2p[e * s2 + c];
+                const T *pp = acT + e * kChiTile + t0;
 #pragma unroll
-        for (int u = 0; u < kChiRG; ++u) acc[u] = b2[c];
-        for (int e = 0; e < dh; ++e) {
-            const T wv = W2p[e * s2 + c];
-            const T *pp = acT + e * kChiTile + t0;
+                for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pp[u];
+            }
 #pragma unroll
-            for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pp[u];
+            for (int u = 0; u < kChiRG; ++u)
+                if (t0 + u < ns) dst[(long long)(t0 + u) * d + c] = acc[u];
         }
-#pragma unroll
-        for (int u = 0; u < kChiRG; ++u)
-            if (t0 + u < ns) dst[(long long)(t0 + u) * d + c] = acc[u];
     }
 }
 
 template <typename T>
 cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, int B, T *chi, cudaStream_t st) {
     const int ntile = (g.N + kChiTile - 1) / kChiTile;
-    const long long blocks = (long long)B * g.L * ntile;
+    const long long groups = ((long long)B * ntile + kChiTPB - 1) / kChiTPB;
     const size_t act = (size_t)2 * kChiTile * g.dh * sizeof(T);
     const size_t wts = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1)) * sizeof(T);
     const int stage = act + wts <= 200 * 1024 ? 1 : 0;
@@ -247,7 +251,7 @@ cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, 
     if (err != cudaSuccess) return err;
     {
         ProfScope _ps("k_chi", st);
-        k_chi<T><<<(unsigned)blocks, 256, smem, st>>>(g, w, spins, B, chi, stage);
+        k_chi<T><<<dim3((unsigned)groups, (unsigned)g.L), 256, smem, st>>>(g, w, spins, B, chi, stage);
     }
     return cudaGetLastError();
 }

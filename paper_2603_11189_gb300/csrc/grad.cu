@@ -99,14 +99,15 @@ __global__ void k_add_omega(int N, int d, long long B, const T *__restrict__ ome
 // shared memory once per CTA; the site-major operands are kept transposed ([k][site]) so
 // that a thread (output e, group of 8 sites) reads its 8 sites with two 16-byte loads
 // (the same address for the whole warp) and its weight row without bank conflicts.
-constexpr int kMbTile = 32, kMbSub = 8;
+constexpr int kMbTile = 32, kMbSub = 8, kMbTPB = 4;   // sites per tile, per thread group, tiles per CTA
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_mlp_back(Geom g, int l, Weights<T> w, const int8_t *__restrict__ spins,
                                                   const T *__restrict__ chi, const T *__restrict__ y,
                                                   const T *__restrict__ dtv, T *__restrict__ tY, T *__restrict__ dy,
                                                   T *__restrict__ dchi, T *__restrict__ a1, T *__restrict__ phi,
-                                                  T *__restrict__ dz, T *__restrict__ dphi, T *__restrict__ win) {
+                                                  T *__restrict__ dz, T *__restrict__ dphi, T *__restrict__ win,
+                                                  int nb) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
     // Row strides dh+1 and d+1: a warp reading along either index of the weights hits
@@ -117,10 +118,6 @@ __global__ void __launch_bounds__(256) k_mlp_back(Geom g, int l, Weights<T> w, c
     T *zT = phT + dh * kMbTile;                // [e][tile]  z, then dz
     T *dcT = zT + dh * kMbTile;                // [c][tile]  dchi
     const int ntile = (N + kMbTile - 1) / kMbTile;
-    const long long b = blockIdx.x / ntile;
-    const int i0 = (int)(blockIdx.x % ntile) * kMbTile;
-    const int ns = min(kMbTile, N - i0);
-    const int8_t *sp = spins + b * N;
     const T *kap = w.kappa + (long long)(l - 1) * W * dh;
     const T *beta = w.beta + (long long)(l - 1) * dh;
     const T *b1 = w.b1 + (long long)(l - 1) * dh;
@@ -128,98 +125,107 @@ __global__ void __launch_bounds__(256) k_mlp_back(Geom g, int l, Weights<T> w, c
         W1s[(q / dh) * (dh + 1) + q % dh] = w.W1T[(long long)(l - 1) * dh * dh + q];
     for (int q = threadIdx.x; q < dh * d; q += blockDim.x)
         W2s[(q / d) * (d + 1) + q % d] = w.W2T[(long long)(l - 1) * dh * d + q];
-    const long long fb = (b * N + i0);          // first row of the tile in [B][N][.] arrays
-    const T *chib = chi + ((b * L + (l - 1)) * N + i0) * d;
-    auto spin = [&](int j) -> T {
-        if (g.periodic) return (T)sp[((j % N) + N) % N];
-        return (j >= 0 && j < N) ? (T)sp[j] : (T)0;
-    };
-    for (int idx = threadIdx.x; idx < kMbTile * dh; idx += blockDim.x) {
-        const int t = idx / dh, e = idx % dh, i = i0 + t;
-        T acc = 0;
-        if (t < ns) {
-            acc = beta[e];
-            for (int r = -wd; r <= wd; ++r) acc += kap[(r + wd) * dh + e] * spin(i + r);
-            phi[(fb + t) * dh + e] = acc;
+    for (int it = 0; it < kMbTPB; ++it) {
+        const long long item = (long long)blockIdx.x * kMbTPB + it;
+        if (item >= (long long)nb * ntile) break;
+        __syncthreads();   // the previous tile's reads of the staged activations (and the weight staging) are done
+        const long long b = item / ntile;
+        const int i0 = (int)(item % ntile) * kMbTile;
+        const int ns = min(kMbTile, N - i0);
+        const int8_t *sp = spins + b * N;
+        const long long fb = (b * N + i0);          // first row of the tile in [B][N][.] arrays
+        const T *chib = chi + ((b * L + (l - 1)) * N + i0) * d;
+        auto spin = [&](int j) -> T {
+            if (g.periodic) return (T)sp[((j % N) + N) % N];
+            return (j >= 0 && j < N) ? (T)sp[j] : (T)0;
+        };
+        for (int idx = threadIdx.x; idx < kMbTile * dh; idx += blockDim.x) {
+            const int t = idx / dh, e = idx % dh, i = i0 + t;
+            T acc = 0;
+            if (t < ns) {
+                acc = beta[e];
+                for (int r = -wd; r <= wd; ++r) acc += kap[(r + wd) * dh + e] * spin(i + r);
+                phi[(fb + t) * dh + e] = acc;
+            }
+            phT[e * kMbTile + t] = acc;
         }
-        phT[e * kMbTile + t] = acc;
-    }
-    for (int idx = threadIdx.x; idx < ns * W; idx += blockDim.x) {
-        const int t = idx / W, r = idx % W;
-        win[(fb + t) * W + r] = spin(i0 + t + r - wd);
-    }
-    for (int idx = threadIdx.x; idx < kMbTile * d; idx += blockDim.x) {
-        const int t = idx / d, c = idx % d;
-        T v = 0;
-        if (t < ns) {
-            const long long o = (fb + t) * d + c;
-            const T yv = y[o], dv = dtv[o], xv = chib[(long long)t * d + c];
-            tY[o] = xv * yv;
-            dy[o] = xv * dv;
-            v = yv * dv;
-            dchi[o] = v;
+        for (int idx = threadIdx.x; idx < ns * W; idx += blockDim.x) {
+            const int t = idx / W, r = idx % W;
+            win[(fb + t) * W + r] = spin(i0 + t + r - wd);
         }
-        dcT[c * kMbTile + t] = v;
-    }
-    __syncthreads();
-    constexpr int nsub = kMbTile / kMbSub;
-    // z = W1 phi + b1 (into zT), a1 = GELU(z)
-    for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
-        const int e = q % dh, t0 = (q / dh) * kMbSub;
-        T acc[kMbSub];
-#pragma unroll
-        for (int u = 0; u < kMbSub; ++u) acc[u] = b1[e];
-        for (int f = 0; f < dh; ++f) {
-            const T wv = W1s[f * (dh + 1) + e];
-            const T *pp = phT + f * kMbTile + t0;
-#pragma unroll
-            for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
+        for (int idx = threadIdx.x; idx < kMbTile * d; idx += blockDim.x) {
+            const int t = idx / d, c = idx % d;
+            T v = 0;
+            if (t < ns) {
+                const long long o = (fb + t) * d + c;
+                const T yv = y[o], dv = dtv[o], xv = chib[(long long)t * d + c];
+                tY[o] = xv * yv;
+                dy[o] = xv * dv;
+                v = yv * dv;
+                dchi[o] = v;
+            }
+            dcT[c * kMbTile + t] = v;
         }
-#pragma unroll
-        for (int u = 0; u < kMbSub; ++u) {
-            zT[e * kMbTile + t0 + u] = acc[u];
-            if (t0 + u < ns) a1[(fb + t0 + u) * dh + e] = gelu_t<T>(acc[u]);
+        __syncthreads();
+        constexpr int nsub = kMbTile / kMbSub;
+        // z = W1 phi + b1 (into zT), a1 = GELU(z)
+        for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
+            const int e = q % dh, t0 = (q / dh) * kMbSub;
+            T acc[kMbSub];
+    #pragma unroll
+            for (int u = 0; u < kMbSub; ++u) acc[u] = b1[e];
+            for (int f = 0; f < dh; ++f) {
+                const T wv = W1s[f * (dh + 1) + e];
+                const T *pp = phT + f * kMbTile + t0;
+    #pragma unroll
+                for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
+            }
+    #pragma unroll
+            for (int u = 0; u < kMbSub; ++u) {
+                zT[e * kMbTile + t0 + u] = acc[u];
+                if (t0 + u < ns) a1[(fb + t0 + u) * dh + e] = gelu_t<T>(acc[u]);
+            }
         }
-    }
-    __syncthreads();
-    // dz = (W2^T dchi) . GELU'(z) (in place of z)
-    for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
-        const int e = q % dh, t0 = (q / dh) * kMbSub;
-        T acc[kMbSub];
-#pragma unroll
-        for (int u = 0; u < kMbSub; ++u) acc[u] = 0;
-        for (int c = 0; c < d; ++c) {
-            const T wv = W2s[e * (d + 1) + c];
-            const T *pp = dcT + c * kMbTile + t0;
-#pragma unroll
-            for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
+        __syncthreads();
+        // dz = (W2^T dchi) . GELU'(z) (in place of z)
+        for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
+            const int e = q % dh, t0 = (q / dh) * kMbSub;
+            T acc[kMbSub];
+    #pragma unroll
+            for (int u = 0; u < kMbSub; ++u) acc[u] = 0;
+            for (int c = 0; c < d; ++c) {
+                const T wv = W2s[e * (d + 1) + c];
+                const T *pp = dcT + c * kMbTile + t0;
+    #pragma unroll
+                for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
+            }
+    #pragma unroll
+            for (int u = 0; u < kMbSub; ++u) {
+                const T v = acc[u] * gelu_prime_t<T>(zT[e * kMbTile + t0 + u]);
+                acc[u] = v;
+                if (t0 + u < ns) dz[(fb + t0 + u) * dh + e] = v;
+            }
+            // (e, t0) belongs to this thread alone: overwrite z with dz in place.
+    #pragma unroll
+            for (int u = 0; u < kMbSub; ++u) zT[e * kMbTile + t0 + u] = acc[u];
         }
-#pragma unroll
-        for (int u = 0; u < kMbSub; ++u) {
-            const T v = acc[u] * gelu_prime_t<T>(zT[e * kMbTile + t0 + u]);
-            acc[u] = v;
-            if (t0 + u < ns) dz[(fb + t0 + u) * dh + e] = v;
+        __syncthreads();
+        // dphi = W1^T dz
+        for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
+            const int f = q % dh, t0 = (q / dh) * kMbSub;
+            T acc[kMbSub];
+    #pragma unroll
+            for (int u = 0; u < kMbSub; ++u) acc[u] = 0;
+            for (int e = 0; e < dh; ++e) {
+                const T wv = W1s[f * (dh + 1) + e];
+                const T *pp = zT + e * kMbTile + t0;
+    #pragma unroll
+                for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
+            }
+    #pragma unroll
+            for (int u = 0; u < kMbSub; ++u)
+                if (t0 + u < ns) dphi[(fb + t0 + u) * dh + f] = acc[u];
         }
-        // (e, t0) belongs to this thread alone: overwrite z with dz in place.
-#pragma unroll
-        for (int u = 0; u < kMbSub; ++u) zT[e * kMbTile + t0 + u] = acc[u];
-    }
-    __syncthreads();
-    // dphi = W1^T dz
-    for (int q = threadIdx.x; q < dh * nsub; q += blockDim.x) {
-        const int f = q % dh, t0 = (q / dh) * kMbSub;
-        T acc[kMbSub];
-#pragma unroll
-        for (int u = 0; u < kMbSub; ++u) acc[u] = 0;
-        for (int e = 0; e < dh; ++e) {
-            const T wv = W1s[f * (dh + 1) + e];
-            const T *pp = zT + e * kMbTile + t0;
-#pragma unroll
-            for (int u = 0; u < kMbSub; ++u) acc[u] += wv * pp[u];
-        }
-#pragma unroll
-        for (int u = 0; u < kMbSub; ++u)
-            if (t0 + u < ns) dphi[(fb + t0 + u) * dh + f] = acc[u];
     }
 }
 
@@ -712,8 +718,9 @@ cudaError_t launch_mlp_back(const Geom &g, int l, const Weights<T> &w, const int
     cudaError_t err = cudaFuncSetAttribute(k_mlp_back<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     ProfScope _ps("k_mlp_back", st);
-    k_mlp_back<T><<<(unsigned)((long long)B * ntile), 256, smem, st>>>(g, l, w, spins, chi, y, dtv, s.tY, s.dy, s.dchi,
-                                                                       s.a1, s.phi, s.dz, s.dphi, s.win);
+    const long long groups = ((long long)B * ntile + kMbTPB - 1) / kMbTPB;
+    k_mlp_back<T><<<(unsigned)groups, 256, smem, st>>>(g, l, w, spins, chi, y, dtv, s.tY, s.dy, s.dchi, s.a1, s.phi,
+                                                       s.dz, s.dphi, s.win, B);
     return cudaGetLastError();
 }
 
