@@ -148,6 +148,22 @@ cudaError_t launch_check_spins(const int8_t *spins, long long n, int8_t *copy, u
 // once (row strides dh + 1 and d + 1, so a warp reading along either index hits distinct
 // banks); phi and GELU(z) are kept transposed ([feature][site]) so that a thread (output
 // feature, group of 8 sites) reads its 8 sites as two 16-byte broadcasts.
+// Eight consecutive values from shared memory at a 16-byte-aligned address.
+template <typename T>
+__device__ __forceinline__ void lds8(const T *p, T (&v)[8]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            const double2 a = *reinterpret_cast<const double2 *>(p + u);
+            v[u] = a.x;
+            v[u + 1] = a.y;
+        }
+    }
+}
+
 constexpr int kChiTile = 64, kChiRG = 8, kChiTPB = 8;   // sites per tile, per thread group, tiles per CTA
 
 template <typename T>
@@ -157,7 +173,8 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
     T *phT = reinterpret_cast<T *>(smraw);      // [dh][tile]
     T *acT = phT + dh * kChiTile;               // [dh][tile]
-    T *W1s = acT + dh * kChiTile;               // [f][e] = W1[e][f]
+    T *sw = acT + dh * kChiTile;                // [tile + 2w] spins of the tile's windows
+    T *W1s = sw + ((kChiTile + 2 * wd + 1) & ~1);   // [f][e] = W1[e][f]
     T *W2s = W1s + dh * (dh + 1);               // [e][c] = W2[c][e]
     const int ntile = (N + kChiTile - 1) / kChiTile;
     const int l = blockIdx.y;
@@ -184,23 +201,25 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
         const int i0 = (int)(item % ntile) * kChiTile;
         const int ns = min(kChiTile, N - i0);
         const int8_t *sp = spins + b * N;
-        __syncthreads();   // previous tile's reads of phT / acT (and the weight staging) are done
+        __syncthreads();   // previous tile's reads of phT / acT / sw (and the weight staging) are done
+        for (int q = threadIdx.x; q < kChiTile + 2 * wd; q += blockDim.x) {
+            int j = i0 + q - wd;
+            T sv;
+            if (g.periodic) {
+                j = ((j % N) + N) % N;
+                sv = (T)sp[j];
+            } else {
+                sv = (j >= 0 && j < N) ? (T)sp[j] : (T)0;
+            }
+            sw[q] = sv;
+        }
+        __syncthreads();
         for (int idx = threadIdx.x; idx < kChiTile * dh; idx += blockDim.x) {
-            const int t = idx / dh, e = idx % dh, i = i0 + t;
+            const int t = idx / dh, e = idx % dh;
             T acc = 0;
             if (t < ns) {
                 acc = beta[e];
-                for (int r = -wd; r <= wd; ++r) {
-                    int j = i + r;
-                    T sv;
-                    if (g.periodic) {
-                        j = ((j % N) + N) % N;
-                        sv = (T)sp[j];
-                    } else {
-                        sv = (j >= 0 && j < N) ? (T)sp[j] : (T)0;
-                    }
-                    acc += kap[(r + wd) * dh + e] * sv;
-                }
+                for (int r = 0; r < W; ++r) acc += kap[r * dh + e] * sw[t + r];
             }
             phT[e * kChiTile + t] = acc;
         }
@@ -212,9 +231,10 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
             for (int u = 0; u < kChiRG; ++u) acc[u] = b1[e];
             for (int f = 0; f < dh; ++f) {
                 const T wv = W1p[f * s1 + e];
-                const T *pp = phT + f * kChiTile + t0;
+                T pv[8];
+                lds8<T>(phT + f * kChiTile + t0, pv);
 #pragma unroll
-                for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pp[u];
+                for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pv[u];
             }
 #pragma unroll
             for (int u = 0; u < kChiRG; ++u) acT[e * kChiTile + t0 + u] = gelu<T>(acc[u]);
@@ -228,9 +248,10 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
             for (int u = 0; u < kChiRG; ++u) acc[u] = b2[c];
             for (int e = 0; e < dh; ++e) {
                 const T wv = W2p[e * s2 + c];
-                const T *pp = acT + e * kChiTile + t0;
+                T pv[8];
+                lds8<T>(acT + e * kChiTile + t0, pv);
 #pragma unroll
-                for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pp[u];
+                for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pv[u];
             }
 #pragma unroll
             for (int u = 0; u < kChiRG; ++u)
@@ -243,7 +264,7 @@ template <typename T>
 cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, int B, T *chi, cudaStream_t st) {
     const int ntile = (g.N + kChiTile - 1) / kChiTile;
     const long long groups = ((long long)B * ntile + kChiTPB - 1) / kChiTPB;
-    const size_t act = (size_t)2 * kChiTile * g.dh * sizeof(T);
+    const size_t act = ((size_t)2 * kChiTile * g.dh + (size_t)((kChiTile + 2 * g.w + 1) & ~1)) * sizeof(T);
     const size_t wts = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1)) * sizeof(T);
     const int stage = act + wts <= 200 * 1024 ? 1 : 0;
     const size_t smem = act + (stage ? wts : 0);
