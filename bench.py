@@ -172,18 +172,29 @@ def dhop_bytes(N, L, d, B):
     return B * per
 
 
+def bandconv_gen_flops(N, L, d, w, B, WF=None):
+    """FLOPs of the band convolutions whose operand is generated in-kernel (the chain from
+    layer L-2, one hop): (2R+1) band sums over N sites for each of the N d sources and d
+    channels, 2 flops each."""
+    if L < 3:
+        return 0
+    W = 2 * w + 1
+    WF = W if WF is None else WF
+    Rk = WF - 1
+    return B * 2 * (2 * Rk + 1) * N * (N * d) * d
+
+
 def bandconv_bytes(N, L, d, w, B, WF=None):
-    """HBM bytes of the last-layer band convolutions of one step: the probe field
-    read once (the embedding chain and every source chain with a full hop; the
-    chain from layer L-2 generates its operand from D0 and the taps) plus the
-    band entries written."""
+    """HBM bytes of the last-layer band convolutions that read their operand (k_bandconv) in
+    one step: the probe field read once (the embedding chain and every source chain with
+    a full hop) plus the band entries written.  The chain from layer L-2 generates its
+    operand from D0 and the taps (k_bandconv_gen, counted in flops)."""
     W = 2 * w + 1
     WF = W if WF is None else WF
     Rk, Rl = WF - 1, WF - 1 - w
     per = d * N * N * 4 + N * (2 * Rl + 1) * d * 4
-    for m in range(1, L - 1):
-        src = d * N * (N * d) * 4 if m < L - 2 else N * d * d * 4
-        per += src + N * (2 * Rk + 1) * d * d * 4
+    for m in range(1, L - 2):
+        per += d * N * (N * d) * 4 + N * (2 * Rk + 1) * d * d * 4
     return B * per
 
 
@@ -709,6 +720,17 @@ def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
                              "frac": ach / peak, "traffic": None, "launches": launches,
                              "ms_per_launch": tot_s * 1e3 / launches,
                              "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"}
+    gen = [(k, v) for k, v in prof.items() if k.endswith("links/k_bandconv_gen")]
+    if gen:
+        launches = sum(v[0] for _, v in gen)
+        tot_s = sum(v[1] for _, v in gen) / 1e3
+        ach = bandconv_gen_flops(N, desc.L, desc.d, desc.w, Bs) * steps / tot_s / 1e12
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+        out["links_bandconv_gen"] = {"kernel": "k_bandconv_gen", "bound": "alu", "achieved": ach, "peak": peak,
+                                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches": launches,
+                                     "ms_per_launch": tot_s * 1e3 / launches,
+                                     "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"}
     tc = [(k, v) for k, v in prof.items() if k.endswith("links/k_tgemm_tc")]
     if tc:
         launches = sum(v[0] for _, v in tc)
@@ -742,6 +764,8 @@ def roofline(prof, steps, desc, N, Bs, peaks, src, clocks):
         return fam["links_dhop"], fam
     if name.endswith("links/k_bandconv") and "links_bandconv" in fam:
         return fam["links_bandconv"], fam
+    if name.endswith("links/k_bandconv_gen") and "links_bandconv_gen" in fam:
+        return fam["links_bandconv_gen"], fam
     if name.endswith("links/k_tgemm_tc") and "links_tgemm_tc" in fam:
         return fam["links_tgemm_tc"], fam
     return {"kernel": name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,

@@ -280,14 +280,15 @@ cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, 
 // ------------------------------------------------------------------ conv --
 // One CTA per (field, channel tile).  Shared memory holds the taps of the
 // channel tile extended to offsets r in (-N, N) and the field's channels.
+constexpr int kCvOut = 8;   // consecutive outputs per thread
 template <typename T>
 __global__ void k_conv(Geom g, const T *__restrict__ taps_l, Fields<T> in, const int8_t *__restrict__ spins,
                        const T *__restrict__ e, Fields<T> out, int CT, int transpose, const T *__restrict__ A,
                        const T *__restrict__ omega) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d;
-    T *gx = reinterpret_cast<T *>(smraw);     // [2N-1][CT]
-    T *x = gx + (2 * N - 1) * CT;             // [N][CT]
+    T *gx = reinterpret_cast<T *>(smraw);     // [2N-1+kCvOut][CT]
+    T *x = gx + (2 * N - 1 + kCvOut) * CT;    // [N][CT]
     const int nct = d / CT;
     const long long f = blockIdx.x / nct;
     const int c0 = (int)(blockIdx.x % nct) * CT;
@@ -311,16 +312,46 @@ __global__ void k_conv(Geom g, const T *__restrict__ taps_l, Fields<T> in, const
             x[idx] = src[(long long)j * d + c0 + c];
         }
     }
+    // rows 2N-1 .. 2N-1+kCvOut: zero taps read by the last output group past the chain end
+    for (int idx = threadIdx.x; idx < kCvOut * CT; idx += blockDim.x) gx[(2 * N - 1) * CT + idx] = 0;
     __syncthreads();
     T *dst = out.at(f);
     const int kk = A ? (int)(f % g.dout) : 0;
-    for (int idx = threadIdx.x; idx < N * CT; idx += blockDim.x) {
-        const int i = idx / CT, c = idx % CT;
-        const T *gp = gx + (i + N - 1) * CT + c;     // gx[(i - j) + N - 1] = gp[-j * CT]
-        T acc = 0;
-        for (int j = 0; j < N; ++j) acc += gp[-j * CT] * x[j * CT + c];
-        if (A) acc += A[(c0 + c) * g.dout + kk] * omega[(long long)i * d + c0 + c];
-        dst[(long long)i * d + c0 + c] = acc;
+    // Thread (group of kCvOut consecutive outputs i0.., channel c): for input site j the taps
+    // are g_{i0+u-j}; over a block of 4 sites j..j+3 they form a window of kCvOut + 3 taps,
+    // loaded once, so a block costs 4 + kCvOut + 3 loads for 4 kCvOut FMAs.
+    const int ngrp = (N + kCvOut - 1) / kCvOut;
+    for (int idx = threadIdx.x; idx < ngrp * CT; idx += blockDim.x) {
+        const int i0 = (idx / CT) * kCvOut, c = idx % CT;
+        const T *gp = gx + (i0 + N - 1) * CT + c;     // g_{i0+u-j} = gp[(u - j) * CT]
+        T acc[kCvOut];
+#pragma unroll
+        for (int u = 0; u < kCvOut; ++u) acc[u] = 0;
+        int j = 0;
+        for (; j + 4 <= N; j += 4) {
+            T xv[4], win[kCvOut + 3];                 // win[m] = g_{i0 + m - 3 - j}
+#pragma unroll
+            for (int t = 0; t < 4; ++t) xv[t] = x[(j + t) * CT + c];
+#pragma unroll
+            for (int m = 0; m < kCvOut + 3; ++m) win[m] = gp[(m - 3 - j) * CT];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int u = 0; u < kCvOut; ++u) acc[u] += win[u - t + 3] * xv[t];
+        }
+        for (; j < N; ++j) {
+            const T xv = x[j * CT + c];
+#pragma unroll
+            for (int u = 0; u < kCvOut; ++u) acc[u] += gp[(u - j) * CT] * xv;
+        }
+#pragma unroll
+        for (int u = 0; u < kCvOut; ++u) {
+            const int i = i0 + u;
+            if (i >= N) break;
+            T v = acc[u];
+            if (A) v += A[(c0 + c) * g.dout + kk] * omega[(long long)i * d + c0 + c];
+            dst[(long long)i * d + c0 + c] = v;
+        }
     }
 }
 
@@ -330,10 +361,10 @@ static int conv_tile(const Geom &g, size_t *smem) {
     int best = 1;
     for (int ct = 1; ct <= 32 && ct <= g.d; ++ct) {
         if (g.d % ct) continue;
-        size_t bytes = (size_t)(3 * g.N - 1) * ct * sizeof(T);
+        size_t bytes = (size_t)(3 * g.N - 1 + kCvOut) * ct * sizeof(T);
         if (bytes <= 200 * 1024) best = ct;
     }
-    *smem = (size_t)(3 * g.N - 1) * best * sizeof(T);
+    *smem = (size_t)(3 * g.N - 1 + kCvOut) * best * sizeof(T);
     return best;
 }
 

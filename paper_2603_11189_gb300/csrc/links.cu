@@ -630,7 +630,8 @@ static cudaError_t launch_bandconv_nb(const Geom &g, const T *taps, int P, const
     cudaError_t err = cudaFuncSetAttribute(k_bandconv<T, GEN, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     {
-        ProfScope _ps("k_bandconv", st);
+        // traced apart: the generated-operand variant is FMA-bound, the other reads its operand
+        ProfScope _ps(GEN ? "k_bandconv_gen" : "k_bandconv", st);
         k_bandconv<T, GEN, NB><<<blocks, 256, smem, st>>>(g, taps, P, X, gs, band, bd, b0);
     }
     return cudaGetLastError();
@@ -659,7 +660,7 @@ static cudaError_t launch_bandconv4_nb(const Geom &g, const float *taps, int P, 
         cudaFuncSetAttribute(k_bandconv4<GEN, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     {
-        ProfScope _ps("k_bandconv", st);
+        ProfScope _ps(GEN ? "k_bandconv_gen" : "k_bandconv", st);
         k_bandconv4<GEN, NB><<<blocks, 256, smem, st>>>(g, taps, P, X, gs, band, bd, b0);
     }
     return cudaGetLastError();
