@@ -1482,8 +1482,17 @@ static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, con
         if (NS < 2) return cudaErrorNotSupported;
     }
     if (smem == 0) return cudaErrorNotSupported;
-    // Runs of 8 sites per warp: long enough to keep the copy ring full across sites.
-    const int R = 8;
+    // Runs of R sites per warp (8 warps per CTA, one CTA per SM): 8 keeps the copy ring
+    // full across sites; shorter runs where 8 leaves the last wave of CTAs mostly empty.
+    int R = 8;
+    {
+        auto tail = [&](int r) {
+            const long long ctas = (long long)((g.N + kStWarps * r - 1) / (kStWarps * r)) * a.B;
+            const long long w = (ctas + 151) / 152;
+            return (double)(w * 152 - ctas) / (double)(w * 152);
+        };
+        if (tail(8) > 0.25 && tail(4) < tail(8)) R = 4;
+    }
     dim3 grid((unsigned)((g.N + kStWarps * R - 1) / (kStWarps * R)), (unsigned)a.B);
     if (g.W == 5) return launch_ab_stream_ns<5>(a, l, R, NS, grid, smem, S, DX, PART, st);
     if (g.W == 3) return launch_ab_stream_ns<3>(a, l, R, NS, grid, smem, S, DX, PART, st);
@@ -1536,10 +1545,13 @@ static cudaError_t launch_ab_coop(const AbArgs<float> &a, int l, float *S, const
         if (NS < 2) return cudaErrorNotSupported;
     }
     if (smem == 0) return cudaErrorNotSupported;
-    // Runs of R sites per CTA: long runs amortise the ring and window fill, but at least
-    // two CTAs per SM's worth of runs.
-    long long R = (long long)g.N * a.B / (2 * 152);
-    R = R < 4 ? 4 : (R > 16 ? 16 : R);
+    // Runs of R sites per CTA (one CTA per SM fits): R is chosen so that the runs make
+    // whole waves of 152 CTAs, with runs of at most 32 sites - a grid of 2.07 waves spent a
+    // third round on its last 11 CTAs.
+    const long long sites = (long long)g.N * a.B;
+    const long long waves = (sites + 152LL * 32 - 1) / (152LL * 32);
+    long long R = (sites + 152 * waves - 1) / (152 * waves);
+    R = R < 2 ? 2 : (R > 32 ? 32 : R);
     dim3 grid((unsigned)((g.N + R - 1) / R), (unsigned)a.B);
     const int Ri = (int)R;
     if (g.d == 64 && g.W == 5) return launch_ab_coop_ns<64, 5>(a, l, Ri, NS, grid, smem, S, DX, PART, st);
