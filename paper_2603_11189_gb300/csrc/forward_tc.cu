@@ -40,7 +40,7 @@ __global__ void k_h0_cm(int d, int N, int B, const int8_t *__restrict__ spins, c
     }
 }
 
-// pooled[b][l][c] = sum_n omega_{n,c} h[c][n B + b], in FP64 (readout sums of layer l).
+// pooled[b][l][c] = sum_n omega_{n,c} h[c][n B + b] (readout sums of layer l, FP64 result).
 __global__ void k_pool_cm(int d, int N, int B, int l, const float *__restrict__ h, const float *__restrict__ omega,
                           double *__restrict__ pooled, long long pstride) {
     const long long R = (long long)N * B;
@@ -48,8 +48,15 @@ __global__ void k_pool_cm(int d, int N, int B, int l, const float *__restrict__ 
     if (x >= (long long)d * B) return;
     const int c = (int)(x / B), b = (int)(x - (long long)c * B);
     const float *hc = h + (long long)c * R + b;
+    // products and partial sums of 16 sites in FP32, the partials added in FP64 (FP64
+    // arithmetic is slow on this part; 16-term partials are far inside the BF16 error)
     double s = 0.0;
-    for (int n = 0; n < N; ++n) s += (double)omega[(long long)n * d + c] * (double)hc[(long long)n * B];
+    for (int n0 = 0; n0 < N; n0 += 16) {
+        float p = 0.f;
+        const int n1 = n0 + 16 < N ? n0 + 16 : N;
+        for (int n = n0; n < n1; ++n) p = fmaf(omega[(long long)n * d + c], hc[(long long)n * B], p);
+        s += (double)p;
+    }
     pooled[(long long)b * pstride + (long long)l * d + c] = s;
 }
 
