@@ -359,10 +359,10 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
     extern __shared__ __align__(16) unsigned char smraw[];
     const Geom &g = a.g;
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
-    constexpr int RT = 64, RG = 8;                          // rows per CTA, rows per thread
-    T *phT = reinterpret_cast<T *>(smraw);                  // [dh][RT]  phi, then GELU(z)
-    T *acT = phT + dh * RT;                                 // [dh][RT]
-    T *W1s = acT + dh * RT;                                 // [f][e] = W1[e][f], row stride dh + 1
+    constexpr int RT = 64, RG = 8, TS = RT + 4;             // rows per tile, rows per thread, row stride
+    T *phT = reinterpret_cast<T *>(smraw);                  // [dh][TS]  phi
+    T *acT = phT + dh * TS;                                 // [dh][TS]  GELU(z)
+    T *W1s = acT + dh * TS;                                 // [f][e] = W1[e][f], row stride dh + 1
     T *W2s = W1s + dh * (dh + 1);                           // [e][c] = W2[c][e], row stride d + 1
     const int l = blockIdx.y;
     const long long rows = (long long)a.B * N * W;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
         if (r0 >= rows) break;
         __syncthreads();   // the previous tile's reads of phT / acT (and the weight staging) are done
         for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
-            const int rr = q / dh, e = q % dh;
+            const int e = q / RT, rr = q % RT;   // lanes along rows: conflict-free stores
             const long long r = r0 + rr;
             T acc = 0;
             if (r < rows) {
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
                     }
                 }
             }
-            phT[e * RT + rr] = acc;
+            phT[e * TS + rr] = acc;
         }
         __syncthreads();
         for (int q = threadIdx.x; q < dh * (RT / RG); q += blockDim.x) {
@@ -411,12 +411,12 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
             for (int u = 0; u < RG; ++u) acc[u] = b1[e];
             for (int f = 0; f < dh; ++f) {
                 const T wv = W1s[f * (dh + 1) + e];
-                const T *pp = phT + f * RT + t0;
+                const T *pp = phT + f * TS + t0;
     #pragma unroll
                 for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
             }
     #pragma unroll
-            for (int u = 0; u < RG; ++u) acT[e * RT + t0 + u] = gelu_ab<T>(acc[u]);
+            for (int u = 0; u < RG; ++u) acT[e * TS + t0 + u] = gelu_ab<T>(acc[u]);
         }
         __syncthreads();
         for (int q = threadIdx.x; q < d * (RT / RG); q += blockDim.x) {
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
             for (int u = 0; u < RG; ++u) acc[u] = b2[c];
             for (int e = 0; e < dh; ++e) {
                 const T wv = W2s[e * (d + 1) + c];
-                const T *pp = acT + e * RT + t0;
+                const T *pp = acT + e * TS + t0;
     #pragma unroll
                 for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
             }
@@ -1565,7 +1565,7 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     const Geom g = geom_of(m, c->N);
     if (g.W > kLayMaxW || g.d > 128) return cudaErrorNotSupported;
     const size_t lsm = (2 * (size_t)g.d * g.d + 8 * ((size_t)g.W * g.W * g.d + 2 * (size_t)g.W * g.d)) * sizeof(T);
-    const size_t tsm = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1) + 2 * 64 * (size_t)g.dh) * sizeof(T);
+    const size_t tsm = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1) + 2 * 68 * (size_t)g.dh) * sizeof(T);
     if (lsm > 220 * 1024 || tsm > 220 * 1024) return cudaErrorNotSupported;
     const AbArgs<T> a = ab_args<T>(m, pl, w, c);
     const long long rows = (long long)c->B * c->N * g.W;

@@ -165,15 +165,16 @@ __device__ __forceinline__ void lds8(const T *p, T (&v)[8]) {
 }
 
 constexpr int kChiTile = 64, kChiRG = 8, kChiTPB = 8;   // sites per tile, per thread group, tiles per CTA
+constexpr int kChiTS = kChiTile + 4;   // row stride of the transposed tiles: 16-byte rows that start 4 banks apart
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t *__restrict__ spins, int B,
                                              T *__restrict__ chi, int stage) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
-    T *phT = reinterpret_cast<T *>(smraw);      // [dh][tile]
-    T *acT = phT + dh * kChiTile;               // [dh][tile]
-    T *sw = acT + dh * kChiTile;                // [tile + 2w] spins of the tile's windows
+    T *phT = reinterpret_cast<T *>(smraw);      // [dh][kChiTS]
+    T *acT = phT + dh * kChiTS;                 // [dh][kChiTS]
+    T *sw = acT + dh * kChiTS;                  // [tile + 2w] spins of the tile's windows
     T *W1s = sw + ((kChiTile + 2 * wd + 1) & ~1);   // [f][e] = W1[e][f]
     T *W2s = W1s + dh * (dh + 1);               // [e][c] = W2[c][e]
     const int ntile = (N + kChiTile - 1) / kChiTile;
@@ -215,13 +216,13 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < kChiTile * dh; idx += blockDim.x) {
-            const int t = idx / dh, e = idx % dh;
+            const int e = idx / kChiTile, t = idx % kChiTile;   // lanes along sites: conflict-free stores
             T acc = 0;
             if (t < ns) {
                 acc = beta[e];
                 for (int r = 0; r < W; ++r) acc += kap[r * dh + e] * sw[t + r];
             }
-            phT[e * kChiTile + t] = acc;
+            phT[e * kChiTS + t] = acc;
         }
         __syncthreads();
         for (int q = threadIdx.x; q < dh * (kChiTile / kChiRG); q += blockDim.x) {
@@ -232,12 +233,12 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
             for (int f = 0; f < dh; ++f) {
                 const T wv = W1p[f * s1 + e];
                 T pv[8];
-                lds8<T>(phT + f * kChiTile + t0, pv);
+                lds8<T>(phT + f * kChiTS + t0, pv);
 #pragma unroll
                 for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pv[u];
             }
 #pragma unroll
-            for (int u = 0; u < kChiRG; ++u) acT[e * kChiTile + t0 + u] = gelu<T>(acc[u]);
+            for (int u = 0; u < kChiRG; ++u) acT[e * kChiTS + t0 + u] = gelu<T>(acc[u]);
         }
         __syncthreads();
         T *dst = chi + ((b * L + l) * N + i0) * d;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
             for (int e = 0; e < dh; ++e) {
                 const T wv = W2p[e * s2 + c];
                 T pv[8];
-                lds8<T>(acT + e * kChiTile + t0, pv);
+                lds8<T>(acT + e * kChiTS + t0, pv);
 #pragma unroll
                 for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pv[u];
             }
@@ -264,7 +265,7 @@ template <typename T>
 cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, int B, T *chi, cudaStream_t st) {
     const int ntile = (g.N + kChiTile - 1) / kChiTile;
     const long long groups = ((long long)B * ntile + kChiTPB - 1) / kChiTPB;
-    const size_t act = ((size_t)2 * kChiTile * g.dh + (size_t)((kChiTile + 2 * g.w + 1) & ~1)) * sizeof(T);
+    const size_t act = ((size_t)2 * kChiTS * g.dh + (size_t)((kChiTile + 2 * g.w + 1) & ~1)) * sizeof(T);
     const size_t wts = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1)) * sizeof(T);
     const int stage = act + wts <= 200 * 1024 ? 1 : 0;
     const size_t smem = act + (stage ? wts : 0);
