@@ -353,17 +353,21 @@ constexpr int kDxTPB = 8;   // row tiles per CTA of k_dchi_table
 // One CTA per (64 (flip, slot) rows, layer).  The MLP weights are staged once; the
 // activations are kept transposed ([feature][row]) so that a thread (output feature, group
 // of 8 rows) reads its 8 rows as two 16-byte broadcasts and its weight row without bank
-// conflicts (row stride dh + 1 / d + 1).
+// conflicts (row stride dh + 1 / d + 1).  Each tile first resolves its rows once: the
+// flipped spin window of the row (W values) and the offset of the row's chi entry (-1
+// where slot site j - w + t lies off an open chain).
 template <typename T>
 __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__ DX) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Geom &g = a.g;
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
     constexpr int RT = 64, RG = 8, TS = RT + 4;             // rows per tile, rows per thread, row stride
-    T *phT = reinterpret_cast<T *>(smraw);                  // [dh][TS]  phi
+    long long *roff = reinterpret_cast<long long *>(smraw);   // [RT] chi offset of the row's site, or -1
+    T *phT = reinterpret_cast<T *>(roff + RT);              // [dh][TS]  phi
     T *acT = phT + dh * TS;                                 // [dh][TS]  GELU(z)
     T *W1s = acT + dh * TS;                                 // [f][e] = W1[e][f], row stride dh + 1
     T *W2s = W1s + dh * (dh + 1);                           // [e][c] = W2[c][e], row stride d + 1
+    T *win = W2s + dh * (d + 1);                            // [RT][W] flipped spin window of the row
     const int l = blockIdx.y;
     const long long rows = (long long)a.B * N * W;
     const T *W1T = a.w.W1T + (long long)l * dh * dh, *W2T = a.w.W2T + (long long)l * dh * d;
@@ -374,19 +378,17 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
     for (int it = 0; it < kDxTPB; ++it) {
         const long long r0 = ((long long)blockIdx.x * kDxTPB + it) * RT;
         if (r0 >= rows) break;
-        __syncthreads();   // the previous tile's reads of phT / acT (and the weight staging) are done
-        for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
-            const int e = q / RT, rr = q % RT;   // lanes along rows: conflict-free stores
+        __syncthreads();   // the previous tile's reads of phT / acT / roff (and the weight staging) are done
+        for (int rr = threadIdx.x; rr < RT; rr += blockDim.x) {
             const long long r = r0 + rr;
-            T acc = 0;
+            long long off = -1;
             if (r < rows) {
                 const int t = (int)(r % W), j = (int)((r / W) % N);
                 const long long b = r / ((long long)W * N);
                 const int8_t *sp = a.spins + b * N;
                 const int iu = j - wd + t;
-                const bool ok = g.periodic || (iu >= 0 && iu < N);
-                if (ok) {
-                    acc = beta[e];
+                if (g.periodic || (iu >= 0 && iu < N)) {
+                    off = ((b * L + l) * N + (g.periodic ? ((iu % N) + N) % N : iu)) * d;
                     for (int o = -wd; o <= wd; ++o) {
                         int jn = iu + o;
                         T v;
@@ -397,9 +399,19 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
                             v = (jn >= 0 && jn < N) ? (T)sp[jn] : (T)0;
                         }
                         if (jn == j) v = -v;
-                        acc += kap[(o + wd) * dh + e] * v;
+                        win[rr * W + o + wd] = v;
                     }
                 }
+            }
+            roff[rr] = off;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < RT * dh; q += blockDim.x) {
+            const int e = q / RT, rr = q % RT;   // lanes along rows: conflict-free stores
+            T acc = 0;
+            if (roff[rr] >= 0) {
+                acc = beta[e];
+                for (int o = 0; o < W; ++o) acc += kap[o * dh + e] * win[rr * W + o];
             }
             phT[e * TS + rr] = acc;
         }
@@ -411,9 +423,10 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
             for (int u = 0; u < RG; ++u) acc[u] = b1[e];
             for (int f = 0; f < dh; ++f) {
                 const T wv = W1s[f * (dh + 1) + e];
-                const T *pp = phT + f * TS + t0;
+                T pv[RG];
+                lds8<T>(phT + f * TS + t0, pv);
     #pragma unroll
-                for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
+                for (int u = 0; u < RG; ++u) acc[u] += wv * pv[u];
             }
     #pragma unroll
             for (int u = 0; u < RG; ++u) acT[e * TS + t0 + u] = gelu_ab<T>(acc[u]);
@@ -426,23 +439,17 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
             for (int u = 0; u < RG; ++u) acc[u] = b2[c];
             for (int e = 0; e < dh; ++e) {
                 const T wv = W2s[e * (d + 1) + c];
-                const T *pp = acT + e * TS + t0;
+                T pv[RG];
+                lds8<T>(acT + e * TS + t0, pv);
     #pragma unroll
-                for (int u = 0; u < RG; ++u) acc[u] += wv * pp[u];
+                for (int u = 0; u < RG; ++u) acc[u] += wv * pv[u];
             }
     #pragma unroll
             for (int u = 0; u < RG; ++u) {
                 const long long r = r0 + t0 + u;
                 if (r >= rows) continue;
-                const int t = (int)(r % W), j = (int)((r / W) % N);
-                const long long b = r / ((long long)W * N);
-                int i = j - wd + t;
-                T v = 0;
-                if (g.periodic || (i >= 0 && i < N)) {
-                    if (g.periodic) i = ((i % N) + N) % N;
-                    v = acc[u] - a.chi[((b * L + l) * N + i) * d + c];
-                }
-                DX[((long long)l * rows + r) * d + c] = v;
+                const long long off = roff[t0 + u];
+                DX[((long long)l * rows + r) * d + c] = off >= 0 ? acc[u] - a.chi[off + c] : (T)0;
             }
         }
     }
@@ -1565,7 +1572,9 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     const Geom g = geom_of(m, c->N);
     if (g.W > kLayMaxW || g.d > 128) return cudaErrorNotSupported;
     const size_t lsm = (2 * (size_t)g.d * g.d + 8 * ((size_t)g.W * g.W * g.d + 2 * (size_t)g.W * g.d)) * sizeof(T);
-    const size_t tsm = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1) + 2 * 68 * (size_t)g.dh) * sizeof(T);
+    const size_t tsm = 64 * sizeof(long long) +
+                       ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1) + 2 * 68 * (size_t)g.dh + 64 * (size_t)g.W) *
+                           sizeof(T);
     if (lsm > 220 * 1024 || tsm > 220 * 1024) return cudaErrorNotSupported;
     const AbArgs<T> a = ab_args<T>(m, pl, w, c);
     const long long rows = (long long)c->B * c->N * g.W;

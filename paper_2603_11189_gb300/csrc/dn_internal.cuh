@@ -94,6 +94,22 @@ struct dn_cache {
 
 namespace dn {
 
+// Eight consecutive values from shared memory at a 16-byte-aligned address.
+template <typename T>
+__device__ __forceinline__ void lds8(const T *p, T (&v)[8]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            const double2 a = *reinterpret_cast<const double2 *>(p + u);
+            v[u] = a.x;
+            v[u + 1] = a.y;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ memory --
 void *dev_alloc(size_t bytes, cudaStream_t stream);
 void dev_free(void *p, size_t bytes, cudaStream_t stream);

@@ -148,22 +148,6 @@ cudaError_t launch_check_spins(const int8_t *spins, long long n, int8_t *copy, u
 // once (row strides dh + 1 and d + 1, so a warp reading along either index hits distinct
 // banks); phi and GELU(z) are kept transposed ([feature][site]) so that a thread (output
 // feature, group of 8 sites) reads its 8 sites as two 16-byte broadcasts.
-// Eight consecutive values from shared memory at a 16-byte-aligned address.
-template <typename T>
-__device__ __forceinline__ void lds8(const T *p, T (&v)[8]) {
-    if constexpr (sizeof(T) == 4) {
-        const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else {
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-            const double2 a = *reinterpret_cast<const double2 *>(p + u);
-            v[u] = a.x;
-            v[u + 1] = a.y;
-        }
-    }
-}
-
 constexpr int kChiTile = 64, kChiRG = 8, kChiTPB = 8;   // sites per tile, per thread group, tiles per CTA
 constexpr int kChiTS = kChiTile + 4;   // row stride of the transposed tiles: 16-byte rows that start 4 banks apart
 
