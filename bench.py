@@ -678,6 +678,23 @@ def read_profile(lib):
     return out
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic unit of each
+# family (byte for the HBM-bound ones, flop for the others), from one ncu capture of every
+# launch of those kernels over four steps of this workload at 64 configurations.  The
+# launches have the same per-launch shapes at 64 and 4096 configurations (link sub-batches
+# of at most 47 configurations; ABACUS traffic proportional to the configurations), so a
+# full-size launch's traffic is the ratio times its algorithmic units.  Valid for the
+# kernels as captured: a family whose kernel changes is reported with traffic null until
+# it is captured again.
+DRAM_PER_UNIT = {"abacus": 1.076, "links_dhop": 0.9826, "links_bandconv": 0.9919,
+                 "links_bandconv_gen": 0.01053, "links_tgemm_tc": 0.01665}
+
+
+def traffic_per_launch(fam, units_per_launch):
+    r = DRAM_PER_UNIT.get(fam)
+    return None if r is None else r * units_per_launch
+
+
 def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
     """Rooflines of the kernel families that carry the step: the ABACUS layer
     kernels (HBM-bound: algorithmic bytes = every cache value the flips need, once
@@ -694,7 +711,8 @@ def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
         ach = byts / tot_s / 1e9
         peak = peaks["hbm_gbs"]
         out["abacus"] = {"kernel": "k_ab_layer", "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak, "traffic": None, "launches": launches,
+                         "frac": ach / peak, "traffic": traffic_per_launch("abacus", byts / launches),
+                         "launches": launches,
                          "ms_per_launch": tot_s * 1e3 / launches, "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"}
     tg = [(k, v) for k, v in prof.items() if k.endswith("links/k_tgemm")]
     if tg:
@@ -717,18 +735,22 @@ def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
             ach = byts * steps / tot_s / 1e9
             peak = peaks["hbm_gbs"]
             out[fam_name] = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                             "frac": ach / peak, "traffic": None, "launches": launches,
+                             "frac": ach / peak, "traffic": traffic_per_launch(fam_name, byts * steps / launches),
+                             "launches": launches,
                              "ms_per_launch": tot_s * 1e3 / launches,
                              "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"}
     gen = [(k, v) for k, v in prof.items() if k.endswith("links/k_bandconv_gen")]
     if gen:
         launches = sum(v[0] for _, v in gen)
         tot_s = sum(v[1] for _, v in gen) / 1e3
-        ach = bandconv_gen_flops(N, desc.L, desc.d, desc.w, Bs) * steps / tot_s / 1e12
+        gflops = bandconv_gen_flops(N, desc.L, desc.d, desc.w, Bs) * steps
+        ach = gflops / tot_s / 1e12
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
         out["links_bandconv_gen"] = {"kernel": "k_bandconv_gen", "bound": "alu", "achieved": ach, "peak": peak,
-                                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches": launches,
+                                     "unit": "TFLOP/s", "frac": ach / peak,
+                                     "traffic": traffic_per_launch("links_bandconv_gen", gflops / launches),
+                                     "launches": launches,
                                      "ms_per_launch": tot_s * 1e3 / launches,
                                      "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"}
     tc = [(k, v) for k, v in prof.items() if k.endswith("links/k_tgemm_tc")]
@@ -744,7 +766,9 @@ def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
         bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         peak = bf16 / 3.0
         out["links_tgemm_tc"] = {"kernel": "k_tgemm_tc", "bound": "tensor", "achieved": ach, "peak": peak,
-                                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches": launches,
+                                 "unit": "TFLOP/s", "frac": ach / peak,
+                                 "traffic": traffic_per_launch("links_tgemm_tc", flops / launches),
+                                 "launches": launches,
                                  "ms_per_launch": tot_s * 1e3 / launches,
                                  "peak_source": f"{src} bf16_tflops_sustained / 3 (3-product BF16 split of FP32)"}
     return out

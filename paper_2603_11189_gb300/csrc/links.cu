@@ -184,6 +184,78 @@ __global__ void __launch_bounds__(256) k_embed_src(Geom g, const T *__restrict__
     }
 }
 
+// Same sources, several sites per CTA: the scaled tap rows g^(1)_r * e for every offset
+// r in (-N, N) are staged once per CTA ([2N-1][d+1]); site n's rows are then the
+// window starting at row n - k.  D0_n is staged transposed ([c][a], row stride d + 4 so
+// that its 16-byte reads stay aligned), double-buffered across the CTA's sites.
+constexpr int kEmbSites = 8;   // sites per CTA of k_embed_src_multi
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_embed_src_multi(Geom g, const T *__restrict__ taps1, const T *__restrict__ e,
+                                                         const T *__restrict__ Dm, T *__restrict__ X) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d, L = g.L, dp = d + 1, ds = d + 4;
+    T *Ds = reinterpret_cast<T *>(smraw);      // [2][d][d + 4]
+    T *Ga = Ds + 2 * d * ds;                   // [2N - 1][d + 1]: row r + N - 1 = g^(1)_r * e
+    const int groups = (N + kEmbSites - 1) / kEmbSites;
+    const long long blk = blockIdx.x;
+    const int n0 = (int)(blk % groups) * kEmbSites;
+    const long long bl = blk / groups;
+    const long long dd = (long long)d * d;
+    const int nn = N - n0 < kEmbSites ? N - n0 : kEmbSites;
+    for (int q = threadIdx.x; q < (2 * N - 1) * d; q += blockDim.x) {
+        const int r = q / d, c = q % d;
+        Ga[r * dp + c] = taps1[(long long)tap_row(r - (N - 1), N, g.periodic) * d + c] * e[c];
+    }
+    auto stage = [&](int j) {
+        const T *D = Dm + ((bl * (L - 1)) * N + n0 + j) * dd;
+        T *dst = Ds + (j & 1) * d * ds;
+        for (int q = threadIdx.x; q < d * d; q += blockDim.x) dst[(q % d) * ds + q / d] = D[q];
+    };
+    stage(0);
+    const int kk = threadIdx.x % kEmbChunk, half = threadIdx.x / kEmbChunk;
+    const int ah = (d + 1) / 2;                // output channels per half
+    for (int j = 0; j < nn; ++j) {
+        __syncthreads();                       // site j's D0 (and the tap rows) staged; site j - 1 done
+        if (j + 1 < nn) stage(j + 1);          // into the other buffer, read by nobody now
+        const int n = n0 + j;
+        const T *Dj = Ds + (j & 1) * d * ds;
+        for (int k0 = 0; k0 < N; k0 += kEmbChunk) {
+            const int k = k0 + kk;
+            if (k >= N) break;
+            const T *gk = Ga + (long long)(n - k + N - 1) * dp;
+            for (int a0 = half * ah; a0 < (half + 1) * ah && a0 < d; a0 += 16) {
+                T acc[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) acc[u] = 0;
+                if (a0 + 16 <= d) {
+                    for (int c = 0; c < d; ++c) {
+                        const T gv = gk[c];
+                        T dv[8], dw[8];
+                        lds8<T>(Dj + c * ds + a0, dv);
+                        lds8<T>(Dj + c * ds + a0 + 8, dw);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            acc[u] += dv[u] * gv;
+                            acc[u + 8] += dw[u] * gv;
+                        }
+                    }
+                } else {
+                    for (int c = 0; c < d; ++c) {
+                        const T gv = gk[c];
+                        const T *dc = Dj + c * ds + a0;
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) acc[u] += (a0 + u < d ? dc[u] : (T)0) * gv;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    if (a0 + u < d && a0 + u < (half + 1) * ah) X[((bl * d + a0 + u) * N + n) * (long long)N + k] = acc[u];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ Toeplitz hop --
 // Y[b][a][i][p] = sum_n g_{i-n,a} X[b][a][n][p] on a 128 x 128 (i, p) tile per
 // CTA; 256 threads, each an 8 x 8 register tile (rows ty*8.., columns tx*4..
@@ -767,12 +839,21 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         // Embedding sources (m = 0), P = N.
         {
-            const size_t smem = ((size_t)d * d + (size_t)(N < kEmbChunk ? N : kEmbChunk) * (d + 1)) * sizeof(T);
-            if ((err = cudaFuncSetAttribute(k_embed_src<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-                cudaSuccess)
-                return err;
+            const size_t msm = ((size_t)2 * d * (d + 4) + (size_t)(2 * N - 1) * (d + 1)) * sizeof(T);
             ProfScope _ps("k_embed_src", st);
-            k_embed_src<T><<<(unsigned)((long long)nb * N), 256, smem, st>>>(g, pl.taps, w.e, Dm, F);
+            if (d % 8 == 0 && msm <= 160 * 1024) {
+                if ((err = cudaFuncSetAttribute(k_embed_src_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)msm)) != cudaSuccess)
+                    return err;
+                const long long groups = (N + kEmbSites - 1) / kEmbSites;
+                k_embed_src_multi<T><<<(unsigned)((long long)nb * groups), 256, msm, st>>>(g, pl.taps, w.e, Dm, F);
+            } else {
+                const size_t smem = ((size_t)d * d + (size_t)(N < kEmbChunk ? N : kEmbChunk) * (d + 1)) * sizeof(T);
+                if ((err = cudaFuncSetAttribute(k_embed_src<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem)) != cudaSuccess)
+                    return err;
+                k_embed_src<T><<<(unsigned)((long long)nb * N), 256, smem, st>>>(g, pl.taps, w.e, Dm, F);
+            }
         }
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
         for (int n = 2; n <= L; ++n) {
