@@ -658,7 +658,7 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // site it needs
 //  * the link blocks K^(l,m)_{i, i+dl} (m = 1..l-2, |dl| <= 2w), 4 KB each, which
 //    lie back to back in memory along the run; they are streamed through a ring
-//    of NS shared-memory slots by the bulk-copy engine, and the ring is kept full
+//    of NS shared-memory slots by TMA tensor copies, and the ring is kept full
 //    across site boundaries, so the copies of the next site are in flight while
 //    the current site's slice terms, matvecs and outputs are computed;
 //  * the states s^(m) (m = 1..l-1) of the W flips whose slice holds the site.
@@ -668,9 +668,10 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 //    into the slot that the previous site has released;
 //  * y, dchi, rho and the embedding links of the site, loaded into registers one
 //    site ahead.
-// Lane c owns output channel c.  A block row c is read in 16-byte chunks in the
-// order (s + c) mod 8, so the 8 lanes of a shared-memory phase hit 8 different
-// bank groups; slice states are broadcast reads.  Every wait is bounded; a
+// Lane c owns output channel c.  Link blocks are copied by TMA with the 128-byte
+// swizzle (chunk j of row r lands at chunk j ^ (r mod 8)), so when every lane reads
+// chunk s of its own row the 8 lanes of a shared-memory phase hit 8 different bank
+// groups, and the matching chunk s of a slice state is one broadcast to all lanes.  Every wait is bounded; a
 // timeout raises bit 4 of the cache flag, lets the copies in flight land and
 // ends the warp.
 constexpr int kStWarps = 8;
@@ -687,6 +688,17 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
                      smem_addr(dst)),
                  "l"(src), "r"(bytes), "r"(smem_addr(mbar))
                  : "memory");
+}
+
+// One 4 KB link block (32 rows of 32 floats starting at row `row` of the tensor map) into a
+// 1024-byte-aligned slot, 128B-swizzled: chunk j of row r lands at chunk j ^ (r mod 8).
+__device__ __forceinline__ void tma_block(void *dst, const CUtensorMap *tm, int row, uint64_t *mbar) {
+    mbar_expect(mbar, 4096u);
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(row), "r"(smem_addr(mbar))
+        : "memory");
 }
 
 __device__ __forceinline__ int floor_mod(int x, int m) {
@@ -714,22 +726,27 @@ template <int WW, int NS>
 __global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(AbArgs<float> a, int l, int R,
                                                                               float *__restrict__ S,
                                                                               const float *__restrict__ DX,
-                                                                              double *__restrict__ PART) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+                                                                              double *__restrict__ PART,
+                                                                              const __grid_constant__ CUtensorMap tmK) {
+    extern __shared__ __align__(1024) unsigned char smst[];
+    unsigned char *smraw = smst;
     constexpr int d = 32, dd = d * d;
     const Geom &g = a.g;
+    if ((smem_addr(smraw) & 1023u) != 0u) {   // the swizzled ring needs 1024-byte-aligned slots
+        if (threadIdx.x == 0) atomicOr(a.flag, 8u);
+        return;
+    }
     constexpr int W = WW, wd = (WW - 1) / 2, W1 = W + 1;
     const int N = g.N, L = g.L, dout = g.dout;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, c = lane;
     const int nwin = l - 1, nlink = l > 2 ? l - 2 : 0, nper = 4 * wd + 1;
-    float *VTs = reinterpret_cast<float *>(smraw);                  // [d][d]
+    float *Kring = reinterpret_cast<float *>(smraw) + (size_t)warp * NS * dd;   // [NS][d][d], 4 KB-aligned slots
+    float *VTs = reinterpret_cast<float *>(smraw) + (size_t)kStWarps * NS * dd;  // [d][d]
     float *UTs = VTs + dd;                                          // [d][d]
     float *Gs = UTs + dd;                                           // [4w+1][d] taps g^(l)_{-2w..2w}
     float *Zs = Gs + nper * d;                                      // [d] zeros
-    const int per_warp = NS * dd + nwin * W1 * W * d + 2 * W * d;
-    float *wb = Zs + d + (size_t)warp * per_warp;
-    float *Kring = wb;                                              // [NS][d][d]
-    float *Win = Kring + NS * dd;                                   // [nwin][W+1][W][d]
+    const int per_warp = nwin * W1 * W * d + 2 * W * d;
+    float *Win = Zs + d + (size_t)warp * per_warp;                  // [nwin][W+1][W][d]
     float *pq = Win + nwin * W1 * W * d;                            // [W][d]
     float *gq = pq + W * d;                                         // [W][d]
     uint64_t *mb = reinterpret_cast<uint64_t *>(Zs + d + (size_t)kStWarps * per_warp) +
@@ -802,7 +819,7 @@ __global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(Ab
         iss_base();
         if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (; issued < nblk && issued < NS; ++issued) {
-            if (lane == 0) bulk_load(Kring + iss_slot * dd, iss_src, dd * sizeof(float), mb + iss_slot);
+            if (lane == 0) tma_block(Kring + iss_slot * dd, &tmK, (int)((iss_src - a.K) >> 5), mb + iss_slot);
             iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
             iss_advance();
         }
@@ -914,7 +931,8 @@ __global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(Ab
                 }
                 const int dl = bi - 2 * wd;
                 if (site_ok(i + dl)) {
-                    const float *Kb = Kring + slot * dd + c * d;
+                    const float *Kb = Kring + slot * dd + c * d;   // row c, 16-byte chunks swizzled by c mod 8
+                    const int sw = c & 7;
                     const float *sp[W];
 #pragma unroll
                     for (int q = 0; q < W; ++q) {
@@ -923,9 +941,9 @@ __global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(Ab
                     }
 #pragma unroll
                     for (int s2 = 0; s2 < d / 4; s2 += 2) {
-                        const int ch0 = (s2 + lane) & (d / 4 - 1), ch1 = (s2 + 1 + lane) & (d / 4 - 1);
-                        const float4 k0 = *reinterpret_cast<const float4 *>(Kb + 4 * ch0);
-                        const float4 k1 = *reinterpret_cast<const float4 *>(Kb + 4 * ch1);
+                        const int ch0 = s2, ch1 = s2 + 1;
+                        const float4 k0 = *reinterpret_cast<const float4 *>(Kb + 4 * (ch0 ^ sw));
+                        const float4 k1 = *reinterpret_cast<const float4 *>(Kb + 4 * (ch1 ^ sw));
 #pragma unroll
                         for (int q = 0; q < W; ++q) {
                             const float4 s0 = *reinterpret_cast<const float4 *>(sp[q] + 4 * ch0);
@@ -945,7 +963,7 @@ __global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(Ab
                 if (issued < nblk) {
                     if (lane == 0) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        bulk_load(Kring + iss_slot * dd, iss_src, dd * sizeof(float), mb + iss_slot);
+                        tma_block(Kring + iss_slot * dd, &tmK, (int)((iss_src - a.K) >> 5), mb + iss_slot);
                     }
                     ++issued;
                     iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
@@ -1447,7 +1465,7 @@ static cudaError_t launch_ab_layer(const AbArgs<T> &a, int l, T *S, const T *DX,
 // Shared memory of k_ab_stream with NS ring slots; 0 if it does not fit.
 static size_t ab_stream_smem(const Geom &g, int l, int NS) {
     const size_t d = 32, W = g.W, nwin = l - 1;
-    const size_t per_warp = NS * d * d + nwin * (W + 1) * W * d + 2 * W * d;
+    const size_t per_warp = NS * d * d + nwin * (W + 1) * W * d + 2 * W * d;   // ring slots first, then the rest
     const size_t floats = 2 * d * d + (size_t)(4 * g.w + 2) * d + kStWarps * per_warp;
     const size_t bytes = floats * sizeof(float) + (size_t)kStWarps * (kStMaxNS + 2) * sizeof(uint64_t) +
                          (((size_t)g.N + 15) & ~(size_t)15);
@@ -1456,24 +1474,24 @@ static size_t ab_stream_smem(const Geom &g, int l, int NS) {
 
 template <int WW, int NS>
 static cudaError_t launch_ab_stream_one(const AbArgs<float> &a, int l, int R, dim3 grid, size_t smem, float *S,
-                                       const float *DX, double *PART, cudaStream_t st) {
+                                       const float *DX, double *PART, const CUtensorMap &tmK, cudaStream_t st) {
     cudaError_t err = cudaFuncSetAttribute(k_ab_stream<WW, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     {
         ProfScope _ps("k_ab_layer", st);
-        k_ab_stream<WW, NS><<<grid, 32 * kStWarps, smem, st>>>(a, l, R, S, DX, PART);
+        k_ab_stream<WW, NS><<<grid, 32 * kStWarps, smem, st>>>(a, l, R, S, DX, PART, tmK);
     }
     return cudaGetLastError();
 }
 
 template <int WW>
 static cudaError_t launch_ab_stream_ns(const AbArgs<float> &a, int l, int R, int NS, dim3 grid, size_t smem, float *S,
-                                      const float *DX, double *PART, cudaStream_t st) {
+                                      const float *DX, double *PART, const CUtensorMap &tmK, cudaStream_t st) {
     switch (NS) {
-    case 0: return launch_ab_stream_one<WW, 0>(a, l, R, grid, smem, S, DX, PART, st);
-    case 2: return launch_ab_stream_one<WW, 2>(a, l, R, grid, smem, S, DX, PART, st);
-    case 3: return launch_ab_stream_one<WW, 3>(a, l, R, grid, smem, S, DX, PART, st);
-    case 4: return launch_ab_stream_one<WW, 4>(a, l, R, grid, smem, S, DX, PART, st);
+    case 0: return launch_ab_stream_one<WW, 0>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    case 2: return launch_ab_stream_one<WW, 2>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    case 3: return launch_ab_stream_one<WW, 3>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    case 4: return launch_ab_stream_one<WW, 4>(a, l, R, grid, smem, S, DX, PART, tmK, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -1501,10 +1519,18 @@ static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, con
         if (tail(8) > 0.25 && tail(4) < tail(8)) R = 4;
     }
     dim3 grid((unsigned)((g.N + kStWarps * R - 1) / (kStWarps * R)), (unsigned)a.B);
-    if (g.W == 5) return launch_ab_stream_ns<5>(a, l, R, NS, grid, smem, S, DX, PART, st);
-    if (g.W == 3) return launch_ab_stream_ns<3>(a, l, R, NS, grid, smem, S, DX, PART, st);
+    // Link blocks through a tensor map over the cache's K array viewed as rows of 32 floats
+    // (unused by the link-free layers l <= 2).
+    alignas(64) CUtensorMap tmK;
+    std::memset(&tmK, 0, sizeof(tmK));
+    if (l > 2) {
+        const unsigned long long rows =
+            (unsigned long long)a.B * a.P * g.N * (2ull * a.Rk + 1) * 32ull;
+        if (!a.K || !link_rows_map(&tmK, a.K, rows)) return cudaErrorNotSupported;
+    }
+    if (g.W == 5) return launch_ab_stream_ns<5>(a, l, R, NS, grid, smem, S, DX, PART, tmK, st);
+    if (g.W == 3) return launch_ab_stream_ns<3>(a, l, R, NS, grid, smem, S, DX, PART, tmK, st);
     return cudaErrorNotSupported;
-    return cudaGetLastError();
 }
 
 // Shared memory of k_ab_coop with NS ring slots per warp; 0 if it does not fit.

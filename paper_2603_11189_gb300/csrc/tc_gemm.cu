@@ -869,6 +869,19 @@ static bool hop_output_map(CUtensorMap *tm, float *Y, int N, int P, long long zs
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of an array of rows of 32 floats (a d = 32 cache's 4 KB link blocks are 32
+// such rows each): 32 x 32 boxes with the 128B swizzle.  Row indices must fit in int.
+bool link_rows_map(CUtensorMap *tm, const float *base, unsigned long long rows) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || rows == 0 || rows > 0x7fffffffull || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t dims[2] = {32, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {32, 32}, estr[2] = {1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int NPL, int DD>
 static cudaError_t launch_tgemm_genp_d(const Geom &g, const float *taps, int P, const float *gtaps, const float *gDm,
                                        long long dm_ss, float *Y, float *band, long long bss, long long brs,
