@@ -701,6 +701,19 @@ __device__ __forceinline__ void tma_block(void *dst, const CUtensorMap *tm, int 
         : "memory");
 }
 
+// One 4 KB chunk of 16 rows of 64 floats (starting at row `row` of the tensor map) as two
+// 32-column boxes: columns 0-31 to dst, columns 32-63 to dst + 2 KB, both 128B-swizzled.
+__device__ __forceinline__ void tma_chunk64(float *dst, const CUtensorMap *tm, int row, uint64_t *mbar) {
+    mbar_expect(mbar, 4096u);
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                smem_addr(dst + sg * 512)),
+            "l"(reinterpret_cast<uint64_t>(tm)), "r"(32 * sg), "r"(row), "r"(smem_addr(mbar))
+            : "memory");
+}
+
 __device__ __forceinline__ int floor_mod(int x, int m) {
     const int r = x % m;
     return r < 0 ? r + m : r;
@@ -1075,8 +1088,10 @@ template <int D, int WW, int NS>
 __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbArgs<float> a, int l, int R,
                                                                             float *__restrict__ S,
                                                                             const float *__restrict__ DX,
-                                                                            double *__restrict__ PART) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+                                                                            double *__restrict__ PART,
+                                                                            const __grid_constant__ CUtensorMap tmK) {
+    extern __shared__ __align__(1024) unsigned char smco[];
+    unsigned char *smraw = smco;
     constexpr int d = D, dd = D * D, W = WW, wd = (WW - 1) / 2, W1 = W + 1;
     constexpr int RC = 1024 / D;          // rows per 4 KB chunk
     constexpr int CPB = dd / 1024;        // chunks per block
@@ -1086,7 +1101,14 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
     const int N = g.N, L = g.L, dout = g.dout;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nwin = l - 1, nlink = l > 2 ? l - 2 : 0;
-    float *VTs = reinterpret_cast<float *>(smraw);   // [c'][c] = V[c][c']
+    if ((smem_addr(smraw) & 1023u) != 0u) {   // the swizzled ring needs 1024-byte-aligned slots
+        if (tid == 0) atomicOr(a.flag, 8u);
+        return;
+    }
+    // Ring slots hold a chunk as [32-column segment][row][32], 128B-swizzled: chunk j of
+    // line r (= segment * RC + row) sits at chunk j ^ (r mod 8).
+    float *Kring = reinterpret_cast<float *>(smraw);   // [8][NS][1024], 4 KB-aligned slots
+    float *VTs = Kring + kCoWarps * NS * 1024;         // [c'][c] = V[c][c']
     float *UTs = VTs + dd;
     float *Gs = UTs + dd;                            // [4w+1][d] taps g^(l)_{-2w..2w}
     float *Zs = Gs + nper * d;                       // [d] zeros
@@ -1094,10 +1116,10 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
     float *Pb = Win + nwin * W1 * W * d;             // [8][W][32] partial sums
     float *pq = Pb + kCoWarps * W * 32;              // [W][d]
     float *gq = pq + W * d;                          // [W][d]
-    float *Kring = gq + W * d;                       // [8][NS][1024]
-    uint64_t *mbw = reinterpret_cast<uint64_t *>(Kring + kCoWarps * NS * 1024);   // [8][NS] ring, then 2 window
+    uint64_t *mbw = reinterpret_cast<uint64_t *>(gq + W * d);   // [8][NS] ring, then 2 window
     uint64_t *wmb = mbw + kCoWarps * NS;
-    int8_t *sps = reinterpret_cast<int8_t *>(wmb + 2);
+    int *s_fail_p = reinterpret_cast<int *>(wmb + 2);
+    int8_t *sps = reinterpret_cast<int8_t *>(s_fail_p + 2);
     const long long lo = l - 1;
     const long long b = blockIdx.y;
     for (int q = tid; q < dd; q += blockDim.x) {
@@ -1168,12 +1190,12 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
     if (NS > 0 && nchunk > 0) {
         if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         for (; issued < nchunk && issued < NS; ++issued) {
-            if (lane == 0) bulk_load(ring + iss_slot * 1024, iss_src(), 4096u, mb + iss_slot);
+            if (lane == 0) tma_chunk64(ring + iss_slot * 1024, &tmK, (int)((iss_src() - a.K) / d), mb + iss_slot);
             iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
             iss_advance();
         }
     }
-    __shared__ int s_fail;
+    int &s_fail = *s_fail_p;
     if (tid == 0) s_fail = 0;
     __syncthreads();
     const int lrow = lane % RC, seg = lane / RC;      // chunk row, 32-column segment
@@ -1232,7 +1254,8 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
             const int mi = bb / nper, dl = bb % nper - 2 * wd;
             if (site_ok(i + dl)) {
                 const float *wm = Win + (size_t)mi * W1 * W * d + seg * 32;
-                const float *Kc = ring + slot * 1024 + lrow * d + seg * 32;
+                const float *Kc = ring + slot * 1024 + (seg * RC + lrow) * 32;   // line seg * RC + lrow
+                const int sw = lrow & 7;
                 const float *sp[W];
 #pragma unroll
                 for (int q = 0; q < W; ++q) {
@@ -1241,9 +1264,9 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
                 }
 #pragma unroll
                 for (int s2 = 0; s2 < 8; s2 += 2) {
-                    const int ch0 = (s2 + lane) & 7, ch1 = (s2 + 1 + lane) & 7;
-                    const float4 k0 = *reinterpret_cast<const float4 *>(Kc + 4 * ch0);
-                    const float4 k1 = *reinterpret_cast<const float4 *>(Kc + 4 * ch1);
+                    const int ch0 = s2, ch1 = s2 + 1;
+                    const float4 k0 = *reinterpret_cast<const float4 *>(Kc + 4 * (ch0 ^ sw));
+                    const float4 k1 = *reinterpret_cast<const float4 *>(Kc + 4 * (ch1 ^ sw));
 #pragma unroll
                     for (int q = 0; q < W; ++q) {
                         const float4 s0 = *reinterpret_cast<const float4 *>(sp[q] + 4 * ch0);
@@ -1263,7 +1286,7 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
             if (issued < nchunk) {
                 if (lane == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bulk_load(ring + iss_slot * 1024, iss_src(), 4096u, mb + iss_slot);
+                    tma_chunk64(ring + iss_slot * 1024, &tmK, (int)((iss_src() - a.K) / d), mb + iss_slot);
                 }
                 ++issued;
                 iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
@@ -1526,7 +1549,7 @@ static cudaError_t launch_ab_stream(const AbArgs<float> &a, int l, float *S, con
     if (l > 2) {
         const unsigned long long rows =
             (unsigned long long)a.B * a.P * g.N * (2ull * a.Rk + 1) * 32ull;
-        if (!a.K || !link_rows_map(&tmK, a.K, rows)) return cudaErrorNotSupported;
+        if (!a.K || !link_rows_map(&tmK, a.K, rows, 32, 32)) return cudaErrorNotSupported;
     }
     if (g.W == 5) return launch_ab_stream_ns<5>(a, l, R, NS, grid, smem, S, DX, PART, tmK, st);
     if (g.W == 3) return launch_ab_stream_ns<3>(a, l, R, NS, grid, smem, S, DX, PART, tmK, st);
@@ -1538,31 +1561,31 @@ static size_t ab_coop_smem(const Geom &g, int l, int NS) {
     const size_t d = g.d, W = g.W, nwin = l - 1, nper = 4 * g.w + 1;
     const size_t floats = 2 * d * d + nper * d + d + nwin * (W + 1) * W * d + (size_t)kCoWarps * W * 32 + 2 * W * d +
                           (size_t)kCoWarps * NS * 1024;
-    const size_t bytes = floats * sizeof(float) + ((size_t)kCoWarps * NS + 2) * sizeof(uint64_t) +
+    const size_t bytes = floats * sizeof(float) + ((size_t)kCoWarps * NS + 2) * sizeof(uint64_t) + 2 * sizeof(int) +
                          (((size_t)g.N + 15) & ~(size_t)15);
-    return bytes <= 226 * 1024 ? bytes : 0;   // the kernel adds a few bytes of static shared memory
+    return bytes <= 227 * 1024 ? bytes : 0;
 }
 
 template <int D, int WW, int NS>
 static cudaError_t launch_ab_coop_one(const AbArgs<float> &a, int l, int R, dim3 grid, size_t smem, float *S,
-                                      const float *DX, double *PART, cudaStream_t st) {
+                                      const float *DX, double *PART, const CUtensorMap &tmK, cudaStream_t st) {
     cudaError_t err = cudaFuncSetAttribute(k_ab_coop<D, WW, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     {
         ProfScope _ps("k_ab_layer", st);
-        k_ab_coop<D, WW, NS><<<grid, 32 * kCoWarps, smem, st>>>(a, l, R, S, DX, PART);
+        k_ab_coop<D, WW, NS><<<grid, 32 * kCoWarps, smem, st>>>(a, l, R, S, DX, PART, tmK);
     }
     return cudaGetLastError();
 }
 
 template <int D, int WW>
 static cudaError_t launch_ab_coop_ns(const AbArgs<float> &a, int l, int R, int NS, dim3 grid, size_t smem, float *S,
-                                     const float *DX, double *PART, cudaStream_t st) {
+                                     const float *DX, double *PART, const CUtensorMap &tmK, cudaStream_t st) {
     switch (NS) {
-    case 0: return launch_ab_coop_one<D, WW, 0>(a, l, R, grid, smem, S, DX, PART, st);
-    case 2: return launch_ab_coop_one<D, WW, 2>(a, l, R, grid, smem, S, DX, PART, st);
-    case 4: return launch_ab_coop_one<D, WW, 4>(a, l, R, grid, smem, S, DX, PART, st);
-    case 6: return launch_ab_coop_one<D, WW, 6>(a, l, R, grid, smem, S, DX, PART, st);
+    case 0: return launch_ab_coop_one<D, WW, 0>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    case 2: return launch_ab_coop_one<D, WW, 2>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    case 4: return launch_ab_coop_one<D, WW, 4>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    case 6: return launch_ab_coop_one<D, WW, 6>(a, l, R, grid, smem, S, DX, PART, tmK, st);
     default: return cudaErrorNotSupported;
     }
 }
@@ -1587,8 +1610,16 @@ static cudaError_t launch_ab_coop(const AbArgs<float> &a, int l, float *S, const
     R = R < 2 ? 2 : (R > 32 ? 32 : R);
     dim3 grid((unsigned)((g.N + R - 1) / R), (unsigned)a.B);
     const int Ri = (int)R;
-    if (g.d == 64 && g.W == 5) return launch_ab_coop_ns<64, 5>(a, l, Ri, NS, grid, smem, S, DX, PART, st);
-    if (g.d == 64 && g.W == 3) return launch_ab_coop_ns<64, 3>(a, l, Ri, NS, grid, smem, S, DX, PART, st);
+    // Link chunks through a tensor map over the cache's K array viewed as rows of 64 floats
+    // (unused by the link-free layers l <= 2).
+    alignas(64) CUtensorMap tmK;
+    std::memset(&tmK, 0, sizeof(tmK));
+    if (l > 2) {
+        const unsigned long long rows = (unsigned long long)a.B * a.P * g.N * (2ull * a.Rk + 1) * 64ull;
+        if (g.d != 64 || !a.K || !link_rows_map(&tmK, a.K, rows, 64, 16)) return cudaErrorNotSupported;
+    }
+    if (g.d == 64 && g.W == 5) return launch_ab_coop_ns<64, 5>(a, l, Ri, NS, grid, smem, S, DX, PART, tmK, st);
+    if (g.d == 64 && g.W == 3) return launch_ab_coop_ns<64, 3>(a, l, Ri, NS, grid, smem, S, DX, PART, tmK, st);
     return cudaErrorNotSupported;
 }
 

@@ -285,7 +285,7 @@ cudaError_t launch_s4_grad(const dn_model *m, int blk, int N, int B, const T *dg
 // Sample-space Gram on the tensor cores (tc_gemm.cu): S [n][n] = scale Xc Xc^T, Xc = X - m,
 // X [n][K] float row-major; partial buffer of gram_tc_partial_elems() floats.
 size_t gram_tc_partial_elems(int n, long long K, int *nsplit);
-bool link_rows_map(CUtensorMap *tm, const float *base, unsigned long long rows);
+bool link_rows_map(CUtensorMap *tm, const float *base, unsigned long long rows, int d, int box_rows);
 cudaError_t launch_gram_tc(const float *X, int n, long long K, const float *m, double scale, double *S, float *part,
                            int nsplit, unsigned *flag, cudaStream_t st);
 

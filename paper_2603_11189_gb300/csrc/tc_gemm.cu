@@ -869,14 +869,16 @@ static bool hop_output_map(CUtensorMap *tm, float *Y, int N, int P, long long zs
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Tensor map of an array of rows of 32 floats (a d = 32 cache's 4 KB link blocks are 32
-// such rows each): 32 x 32 boxes with the 128B swizzle.  Row indices must fit in int.
-bool link_rows_map(CUtensorMap *tm, const float *base, unsigned long long rows) {
+// Tensor map of a cache's link array viewed as rows of d floats (d = 32 or 64): boxes of
+// 32 columns x box_rows rows with the 128B swizzle.  Row indices must fit in int.
+bool link_rows_map(CUtensorMap *tm, const float *base, unsigned long long rows, int d, int box_rows) {
     EncodeTiledFn enc = encode_tiled();
-    if (!enc || rows == 0 || rows > 0x7fffffffull || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
-    const cuuint64_t dims[2] = {32, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {128};
-    const cuuint32_t box[2] = {32, 32}, estr[2] = {1, 1};
+    if (!enc || rows == 0 || rows > 0x7fffffffull || (d != 32 && d != 64) || box_rows < 1 || box_rows > 256 ||
+        (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)d * 4};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows}, estr[2] = {1, 1};
     return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;

@@ -109,3 +109,32 @@ def test_j1j2_local_energy_workload_architecture(dn):
     model.close()
     ref = oracle.eloc(desc, params, cfg["ham"], spins_np)
     assert np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-4
+
+
+def test_n1024_cooperative_kernel_sampled_against_oracle(dn):
+    """The bench's long-chain line: N = 1024, 6 x 64 x 64 FP32 model, 4 chains with all
+    1024 single flips each through the grouped call (cooperative d = 64 layer kernel with
+    swizzled link chunks); 6 sampled flips checked one by one against the oracle's full
+    recompute (about 4 s of host time per flip), all outputs finite."""
+    N = 1024
+    desc = synth.ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
+    params = synth.init_params(desc, 1005, a_scale=10.0)
+    spins_np = synth.spins_uniform(4, N, 2005)
+    model = dn.Model(desc, params)
+    cache = model.forward_cache(torch.from_numpy(spins_np).cuda(), prec="fp32")
+    r = cache.single_flip_ratios().cpu().numpy().reshape(-1)
+    assert cache.check() == dn.DN_OK
+    cache.destroy()
+    model.close()
+    assert r.shape == (4 * N,) and np.all(np.isfinite(r))
+    rng = np.random.default_rng(11)
+    # sites near both ends and in the bulk of the chain
+    pick = np.concatenate([rng.choice(4 * N, 3, replace=False), [0, 2 * N + 1, 4 * N - 2]])
+    sample = (pick // N).astype(np.int32)
+    sites = np.stack([pick % N, -np.ones_like(pick)], axis=1).astype(np.int32)
+    ref = oracle.dlogpsi(desc, params, spins_np, sample, sites)
+    lp, _ = oracle.logpsi(desc, params, spins_np)
+    den = np.maximum(np.abs(ref), 1e-3 * (1.0 + np.abs(lp[sample])))
+    err = np.max(np.abs(r[pick] - ref) / den)
+    print(f"N=1024 coop sampled rel err {err:.3e}")
+    assert err <= 1e-4
