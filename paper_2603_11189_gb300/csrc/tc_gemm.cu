@@ -542,22 +542,29 @@ __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__re
     const uint32_t tmem = *tslot;
     const uint32_t idesc = tc::idesc_bf16(128, D);
     const int ntiles = (P + 127) / 128;
+    const long long cs = (long long)N * P;            // channel stride of Y and X
+    const float *ybase = Yin + (bl * D * N + n) * (long long)P;
+    // The column of the next tile (all D input channels) is loaded into registers while the
+    // current tile's MMAs and stores run, so the HBM reads of consecutive tiles overlap.
+    float v[D];
+    auto load_col = [&](int tt) {
+        const int pp = tt * 128 + tid;
+        const bool ok = pp < P;
+        const float *yg = ybase + (ok ? pp : 0);
+#pragma unroll
+        for (int u = 0; u < D; ++u) v[u] = ok ? yg[u * cs] : 0.f;
+    };
+    if ((int)blockIdx.x < ntiles) load_col(blockIdx.x);
     uint32_t phase = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int p = t * 128 + tid;
         const bool valid = p < P;
-        // A operand in groups of 16 input channels (16 loads in flight per thread); the group's
-        // base pointer advances with the loop so that no per-channel address is kept live.
-        const long long cs = (long long)N * P;        // channel stride of Y and X
-        const float *yg = Yin + (bl * D * N + n) * (long long)P + (valid ? p : 0);
-#pragma unroll 1
-        for (int a16 = 0; a16 < D; a16 += 16, yg += 16 * cs) {
-            float v[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) v[u] = valid ? yg[u * cs] : 0.f;
-            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 0), v);
-            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 8), v + 8);
+        for (int a16 = 0; a16 < D; a16 += 16) {
+            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 0), v + a16);
+            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 8), v + a16 + 8);
         }
+        if (t + (int)gridDim.x < ntiles) load_col(t + gridDim.x);
         tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
