@@ -687,7 +687,7 @@ def read_profile(lib):
 # kernels as captured: a family whose kernel changes is reported with traffic null until
 # it is captured again.
 DRAM_PER_UNIT = {"abacus": None, "links_dhop": None, "links_bandconv": 0.9919,
-                 "links_bandconv_gen": 0.01053, "links_tgemm_tc": 0.01665}
+                 "links_bandconv_gen": None, "links_tgemm_tc": 0.01665}
 
 
 def traffic_per_launch(fam, units_per_launch):

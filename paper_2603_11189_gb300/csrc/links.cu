@@ -634,6 +634,111 @@ __global__ void __launch_bounds__(256) k_bandconv4(Geom g, const float *__restri
     }
 }
 
+// Generated-operand band (first hop of a source chain), two adjacent source sites k and
+// k + 1 per lane with the same four source channels: they share the D0 row loads, and the
+// tap window of k + 1 is that of k shifted by one, so the shared-memory loads per FMA are
+// about halved.  Every band sum is formed in the same order as in k_bandconv4<true, NB>.
+// Requires nsrc % 4 == 0 and 1024 % nsrc == 0.
+template <int NB>
+__global__ void __launch_bounds__(256) k_bandconv4g(Geom g, const float *__restrict__ taps, GenSrc<float> gs,
+                                                    float *__restrict__ band, BandDst bd, long long b0) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d, R = bd.R, ns = bd.nsrc;
+    const int pad = kBcMaxBand + 1;
+    float *gx = reinterpret_cast<float *>(smraw);   // gx[pad + r + N - 1] = g_{r,a} (wrapped on a ring)
+    const int gx_len = 2 * N - 1 + 2 * pad;
+    float *Dsm = gx + ((gx_len + 3) & ~3);          // [N][d]: D0_n[a][:]
+    float *Tsm = Dsm + N * d;                       // [2N-1][d], row r + N - 1: source-layer taps g_r[:]
+    const int kpc = 2 * (1024 / ns);                // source sites per CTA
+    const int chunks = (N + kpc - 1) / kpc;
+    const long long blk = blockIdx.x;
+    const int ch = (int)(blk % chunks);
+    const int a = (int)((blk / chunks) % d);
+    const long long bl = blk / ((long long)chunks * d);
+    for (int q = threadIdx.x; q < gx_len; q += blockDim.x) {
+        int r = q - pad - (N - 1);
+        float v = 0.f;
+        if (g.periodic) {
+            r = ((r % N) + N) % N;
+            v = taps[(long long)tap_row(r, N, 1) * d + a];
+        } else if (r > -N && r < N) {
+            v = taps[(long long)tap_row(r, N, 0) * d + a];
+        }
+        gx[q] = v;
+    }
+    for (int q = threadIdx.x; q < N * d; q += blockDim.x) {
+        const int n = q / d, cc = q - n * d;
+        Dsm[q] = gs.Dm[bl * gs.dm_ss + ((long long)n * d + a) * d + cc];
+    }
+    for (int q = threadIdx.x; q < (2 * N - 1) * d; q += blockDim.x) {
+        const int rr = q / d, cc = q - rr * d;
+        Tsm[q] = gs.taps[(long long)tap_row(rr - (N - 1), N, g.periodic) * d + cc];
+    }
+    __syncthreads();
+    const int k = ch * kpc + 2 * (int)(threadIdx.x / (ns / 4)), c = 4 * (int)(threadIdx.x % (ns / 4));
+    if (k >= N) return;
+    const bool has1 = k + 1 < N;
+    const float *Dma = Dsm + c;
+    const float *Tk0 = Tsm + (long long)(N - 1 - k) * d + c;   // row of g_{n-k} at Tk0[n d]
+    const float *Tk1 = has1 ? Tk0 - d : Tk0;                    // g_{n-k-1} (a copy of k's when k + 1 = N)
+    const float *gk = gx + pad + (k - R) + (N - 1);             // tap of (q, n) at gk[q - n]; k + 1: gk[q - n + 1]
+    float acc0[NB][4], acc1[NB][4];
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc0[q][j] = acc1[q][j] = 0.f;
+    // win[m] = gk[m - (n0 + kBcU - 1)]: (q, n0 + u) of k reads win[q - u + kBcU - 1], of k + 1
+    // win[q - u + kBcU].
+    auto site = [&](int n, const float *win, int u) {
+        const float4 dm = *reinterpret_cast<const float4 *>(Dma + n * d);
+        const float4 t0 = *reinterpret_cast<const float4 *>(Tk0 + n * d);
+        const float4 t1 = *reinterpret_cast<const float4 *>(Tk1 + n * d);
+        const float4 x0 = make_float4(dm.x * t0.x, dm.y * t0.y, dm.z * t0.z, dm.w * t0.w);
+        const float4 x1 = make_float4(dm.x * t1.x, dm.y * t1.y, dm.z * t1.z, dm.w * t1.w);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const float w0 = win[q - u + kBcU - 1], w1 = win[q - u + kBcU];
+            acc0[q][0] = fmaf(w0, x0.x, acc0[q][0]);
+            acc1[q][0] = fmaf(w1, x1.x, acc1[q][0]);
+            acc0[q][1] = fmaf(w0, x0.y, acc0[q][1]);
+            acc1[q][1] = fmaf(w1, x1.y, acc1[q][1]);
+            acc0[q][2] = fmaf(w0, x0.z, acc0[q][2]);
+            acc1[q][2] = fmaf(w1, x1.z, acc1[q][2]);
+            acc0[q][3] = fmaf(w0, x0.w, acc0[q][3]);
+            acc1[q][3] = fmaf(w1, x1.w, acc1[q][3]);
+        }
+    };
+    int n0 = 0;
+    for (; n0 + kBcU <= N; n0 += kBcU) {
+        float win[NB + kBcU];
+#pragma unroll
+        for (int m = 0; m < NB + kBcU; ++m) win[m] = gk[m - (n0 + kBcU - 1)];
+#pragma unroll
+        for (int u = 0; u < kBcU; ++u) site(n0 + u, win, u);
+    }
+    for (; n0 < N; ++n0) {
+        float win[NB + kBcU];
+#pragma unroll
+        for (int m = 0; m < NB + kBcU; ++m) win[m] = gk[m - (n0 + kBcU - 1)];
+        site(n0, win, 0);
+    }
+    auto store = [&](int kk, const float (&acc)[NB][4]) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            if (q > 2 * R) break;
+            const int dl = q - R;
+            int i = kk + dl;
+            if (g.periodic) i = ((i % N) + N) % N;
+            else if (i < 0 || i >= N) continue;
+            float *dst = band + (b0 + bl) * bd.ss + (long long)i * bd.rs + (long long)(R - dl) * bd.os +
+                         (long long)a * ns + c;
+            *reinterpret_cast<float4 *>(dst) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+        }
+    };
+    store(k, acc0);
+    if (has1) store(k + 1, acc1);
+}
+
 // ------------------------------------------------------------------- host --
 static size_t links_per_sample_elems(const dn_model *m, int N) {
     const long long d = m->desc.d, L = m->desc.L;
@@ -726,6 +831,15 @@ static cudaError_t launch_bandconv4_nb(const Geom &g, const float *taps, int P, 
     const size_t gx_len = (((size_t)2 * g.N - 1 + 2 * (kBcMaxBand + 1)) + 3) & ~(size_t)3;
     const size_t smem = (gx_len + (GEN ? (size_t)g.N * g.d + (size_t)(2 * g.N - 1) * g.d : 0)) * sizeof(float);
     if (smem > 200 * 1024) return cudaErrorNotSupported;
+    if (GEN && bd.nsrc % 4 == 0 && 1024 % bd.nsrc == 0 && P == g.N * bd.nsrc) {
+        const int kpc = 2 * (1024 / bd.nsrc);
+        const unsigned blocks = (unsigned)((long long)nb * g.d * ((g.N + kpc - 1) / kpc));
+        cudaError_t err = cudaFuncSetAttribute(k_bandconv4g<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        ProfScope _ps("k_bandconv_gen", st);
+        k_bandconv4g<NB><<<blocks, 256, smem, st>>>(g, taps, gs, band, bd, b0);
+        return cudaGetLastError();
+    }
     const int chunks = (P + 1023) / 1024;
     const unsigned blocks = (unsigned)((long long)nb * g.d * chunks);
     cudaError_t err =
