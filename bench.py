@@ -495,7 +495,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--samples", type=int, default=4096)
     ap.add_argument("--ref-samples", type=int, default=8)
-    ap.add_argument("--cpu-samples", type=int, default=64)
+    ap.add_argument("--cpu-samples", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recompute", action="store_true")
     ap.add_argument("--no-n1024", action="store_true")
