@@ -123,7 +123,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import synth
-    cfg = synth.CONFIGS["c2"]
+    cfg = synth.CONFIGS["lrtfim_n128"]
     params = synth.make_params(cfg)
     spins_np = synth.make_spins(cfg, B=max(args.ref_samples, 1))
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
@@ -529,7 +529,7 @@ def main():
     from paper_2603_11189_gb300 import replicas
     import synth
 
-    cfg = synth.CONFIGS["c2"]
+    cfg = synth.CONFIGS["lrtfim_n128"]
     desc = cfg["desc"]
     N, Bs = cfg["N"], args.samples
     params = synth.make_params(cfg)

@@ -544,7 +544,7 @@ const char *dn_status_string(dn_status s) {
         case DN_ENOMEM: return "DN_ENOMEM: device allocation refused";
         case DN_ECUDA: return "DN_ECUDA: CUDA runtime or launch error";
         case DN_ETIMEOUT: return "DN_ETIMEOUT: bounded device wait gave up";
-        case DN_EUNSUPPORTED: return "DN_EUNSUPPORTED: not implemented in this build";
+        case DN_EUNSUPPORTED: return "DN_EUNSUPPORTED: not implemented by this library";
     }
     return "unknown dn_status";
 }

@@ -228,15 +228,16 @@ def random_flips(B: int, N: int, F: int, seed: int, pair_frac: float = 0.0,
     return sample, sites
 
 
-# Workloads of the benchmark configurations (sizes, seeds and spin recipe).
+# Named workloads (sizes, seeds and spin recipe): long-range TFIM chains of 16 and 128
+# sites, the J1-J2 ring of 256 sites.
 CONFIGS = {
-    "c1": dict(desc=ModelDesc(L=2, d=8, s=8, w=2, dh=8, dout=2, periodic=0), N=16, B=64,
+    "lrtfim_n16": dict(desc=ModelDesc(L=2, d=8, s=8, w=2, dh=8, dout=2, periodic=0), N=16, B=64,
                weights_seed=1001, spins_seed=2001, spins="uniform", a_scale=10.0,
                ham=dict(kind=0, J=1.0, alpha=3.0, h=1.0, periodic=0, kac=0)),
-    "c2": dict(desc=ModelDesc(L=4, d=32, s=32, w=2, dh=32, dout=2, periodic=0), N=128, B=4096,
+    "lrtfim_n128": dict(desc=ModelDesc(L=4, d=32, s=32, w=2, dh=32, dout=2, periodic=0), N=128, B=4096,
                weights_seed=1002, spins_seed=2002, spins="uniform", a_scale=10.0,
                ham=dict(kind=0, J=1.0, alpha=3.0, h=1.0, periodic=0, kac=0)),
-    "c3": dict(desc=ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=1), N=256, B=8192,
+    "j1j2_n256": dict(desc=ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=1), N=256, B=8192,
                weights_seed=1003, spins_seed=2003, spins="zero_mag", a_scale=10.0,
                ham=dict(kind=1, J1=1.0, J2=0.5, periodic=1)),
 }

@@ -21,7 +21,7 @@ def dn():
 
 
 def test_bench_workload_sampled_against_oracle(dn):
-    cfg = synth.CONFIGS["c2"]
+    cfg = synth.CONFIGS["lrtfim_n128"]
     desc, params = cfg["desc"], synth.make_params(cfg)
     B, N = cfg["B"], cfg["N"]
     spins_np = synth.make_spins(cfg)
@@ -54,7 +54,7 @@ def test_bench_workload_sampled_against_oracle(dn):
 def test_bench_workload_flip_list_matches_grouped(dn):
     """The general flip-list kernel and the all-single-flips kernel agree on 64
     configurations of the workload (same caches, different kernels)."""
-    cfg = synth.CONFIGS["c2"]
+    cfg = synth.CONFIGS["lrtfim_n128"]
     desc, params = cfg["desc"], synth.make_params(cfg)
     spins_np = synth.make_spins(cfg, B=64)
     model = dn.Model(desc, params)
@@ -71,7 +71,7 @@ def test_bench_workload_flip_list_matches_grouped(dn):
 
 
 def _c3_model(N):
-    cfg = synth.CONFIGS["c3"]
+    cfg = synth.CONFIGS["j1j2_n256"]
     return cfg, cfg["desc"], synth.make_params(cfg)
 
 

@@ -108,7 +108,7 @@ def test_grad_rejects_bad_input(dn):
     model.close()
 
 
-def test_grad_workload_c4_sampled(dn):
+def test_grad_lrtfim_n256_workload_sampled(dn):
     """Forward + backward of 4096 configurations of the N = 256, 6 x 64 x 64 long-range
     TFIM model in FP32; two configurations checked against the oracle."""
     desc = ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
@@ -121,7 +121,7 @@ def test_grad_workload_c4_sampled(dn):
     pick = [0, 4095]
     lp_ref, O_ref = oracle.grad_logpsi(desc, p, spins[pick])
     e = _err(O[pick].double().cpu().numpy(), O_ref)
-    print(f"C4 sampled O rel err {e:.3e}")
+    print(f"N=256 workload sampled O rel err {e:.3e}")
     assert e <= 1e-4
     model.close()
 

@@ -60,9 +60,9 @@ def check_case(dn, desc, params, spins_np, sample_np, sites_np, prec, max_cluste
 # ------------------------------------------------------------ workloads --
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_c1_workload_all_flips(dn, prec):
+def test_lrtfim_n16_workload_all_flips(dn, prec):
     """N=16, 2 layers x 8 channels, 64 samples x all 16 single flips."""
-    cfg = synth.CONFIGS["c1"]
+    cfg = synth.CONFIGS["lrtfim_n16"]
     desc, params = cfg["desc"], synth.make_params(cfg)
     spins = synth.make_spins(cfg)
     sample, sites = synth.single_flips(cfg["B"], cfg["N"])
@@ -70,10 +70,10 @@ def test_c1_workload_all_flips(dn, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_c2_model_small_batch(dn, prec):
+def test_lrtfim_n128_model_small_batch(dn, prec):
     """The N=128, 4 x 32 x 32 model on 3 samples x all 128 flips (spans many
     tiles; exercises all three interlayer links)."""
-    cfg = synth.CONFIGS["c2"]
+    cfg = synth.CONFIGS["lrtfim_n128"]
     desc, params = cfg["desc"], synth.make_params(cfg)
     spins = synth.make_spins(cfg, B=3)
     sample, sites = synth.single_flips(3, cfg["N"])
@@ -210,8 +210,8 @@ def test_zero_flips_and_bad_arguments(dn):
 def test_allocation_failure_is_reported(dn):
     """A budget allocator that refuses large requests makes the cache build
     return DN_ENOMEM and leaves the library usable."""
-    desc = synth.CONFIGS["c2"]["desc"]
-    params = synth.make_params(synth.CONFIGS["c2"])
+    desc = synth.CONFIGS["lrtfim_n128"]["desc"]
+    params = synth.make_params(synth.CONFIGS["lrtfim_n128"])
     model = dn.Model(desc, params)
     spins = cuda(synth.spins_uniform(4, 128, 2))
     keep = {}
@@ -244,7 +244,7 @@ def test_allocation_failure_is_reported(dn):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_local_energy_tfim(dn, prec):
-    cfg = synth.CONFIGS["c1"]
+    cfg = synth.CONFIGS["lrtfim_n16"]
     desc, params = cfg["desc"], synth.make_params(cfg)
     spins = synth.make_spins(cfg, B=16)
     model = dn.Model(desc, params)

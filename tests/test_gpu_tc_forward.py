@@ -4,7 +4,7 @@ the same tensor-core shapes (d a multiple of 16: link hops on tcgen05).
 FP32 keeps the FP32 bars of the other parity tests (1e-4 on log psi and on log-amplitude
 ratios).  BF16 rounds every operand of the S4 convolutions, the channel mixing and the link
 Toeplitz hops to 8 mantissa bits (relative 2^-9 per operand) with FP32 accumulation.
-Its bounds below are the stated BF16 bounds of this build, about twice the largest
+Its bounds below are the library's stated BF16 bounds, about twice the largest
 errors measured on these workloads on a GB300 (log psi 1.3e-3; log-amplitude ratios
 3.0e-3 for single flips at d = 16 and 0.20 for the pair flips of the d = 32 ring, whose
 ratios are O(0.1) while log psi is O(10): absolute errors of 1e-2).
@@ -91,7 +91,7 @@ def test_bf16_forward_and_ratios(dn, case):
 
 def test_bf16_workload_model_local_energy(dn):
     """BF16 local energy of the N=128, 4 x 32 workload model on 6 configurations."""
-    cfg = synth.CONFIGS["c2"]
+    cfg = synth.CONFIGS["lrtfim_n128"]
     desc, N = cfg["desc"], cfg["N"]
     params = synth.make_params(cfg)
     spins = synth.make_spins(cfg, 6)

@@ -89,7 +89,7 @@ def test_parameter_count_matches_generator(lib):
     """The library's layout check agrees with the generator for several shapes
     (DN_EINVAL is returned before any device work only when the count differs)."""
     import numpy as np
-    for desc in (synth.CONFIGS["c1"]["desc"], synth.CONFIGS["c2"]["desc"], synth.CONFIGS["c3"]["desc"]):
+    for desc in (synth.CONFIGS["lrtfim_n16"]["desc"], synth.CONFIGS["lrtfim_n128"]["desc"], synth.CONFIGS["j1j2_n256"]["desc"]):
         n = synth.n_params(desc)
         d = Desc(desc.L, desc.d, desc.s, desc.w, desc.dh, desc.dout, desc.periodic, desc.fkind)
         p = np.zeros(n + 1)

@@ -377,9 +377,9 @@ def test_exact_enumeration_rayleigh_quotient(case):
 
 
 @pytest.mark.slow
-def test_exact_enumeration_c1_workload():
+def test_exact_enumeration_lrtfim_n16_workload():
     """The N=16 workload: all 2^16 amplitudes, E_var = Rayleigh quotient >= E_0."""
-    cfg = synth.CONFIGS["c1"]
+    cfg = synth.CONFIGS["lrtfim_n16"]
     _enumeration_check(cfg["desc"], synth.make_params(cfg), cfg["ham"], cfg["N"])
 
 

@@ -43,7 +43,7 @@ def _noalloc(dn, model, spins, prec):
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
 def test_noalloc_matches_full_forward_on_consecutive_calls(dn, prec, tol):
-    cfg = synth.CONFIGS["c2"]
+    cfg = synth.CONFIGS["lrtfim_n128"]
     model = dn.Model(cfg["desc"], synth.make_params(cfg))
     calls = {"alloc": 0}
 
@@ -89,7 +89,7 @@ def test_noalloc_other_shapes_and_capacity(dn):
     np.testing.assert_allclose(lp.cpu().numpy(), lp_ref.cpu().numpy(), rtol=1e-10, atol=1e-12)
     # A batch that does not fit the fixed scratch is refused without touching the outputs.
     big = torch.ones((4096, 128), dtype=torch.int8, device="cuda")
-    cfg = synth.CONFIGS["c2"]
+    cfg = synth.CONFIGS["lrtfim_n128"]
     model2 = dn.Model(cfg["desc"], synth.make_params(cfg))
     st, _, _ = _noalloc(dn, model2, big, "fp32")
     assert st == dn.DN_EINVAL
