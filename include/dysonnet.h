@@ -44,7 +44,7 @@ typedef enum {
     DN_ENOMEM = 2,        /* the allocator refused a request */
     DN_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
     DN_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
-    DN_EUNSUPPORTED = 5   /* valid request this build does not implement */
+    DN_EUNSUPPORTED = 5   /* valid request the library does not implement */
 } dn_status;
 
 /* Arithmetic of the network and of the caches.  Every precision generates the
