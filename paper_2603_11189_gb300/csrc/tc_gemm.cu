@@ -544,27 +544,29 @@ __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__re
     const int ntiles = (P + 127) / 128;
     const long long cs = (long long)N * P;            // channel stride of Y and X
     const float *ybase = Yin + (bl * D * N + n) * (long long)P;
-    // The column of the next tile (all D input channels) is loaded into registers while the
-    // current tile's MMAs and stores run, so the HBM reads of consecutive tiles overlap.
-    float v[D];
-    auto load_col = [&](int tt) {
+    // Input columns (all D channels of one column per thread) are loaded into registers
+    // ahead of use - two tiles ahead for D <= 32, one for D = 64 - so the HBM reads of later
+    // tiles are in flight while the current tile's MMAs and stores run.
+    auto load_col = [&](float (&buf)[D], int tt) {
         const int pp = tt * 128 + tid;
         const bool ok = pp < P;
         const float *yg = ybase + (ok ? pp : 0);
 #pragma unroll
-        for (int u = 0; u < D; ++u) v[u] = ok ? yg[u * cs] : 0.f;
+        for (int u = 0; u < D; ++u) buf[u] = ok ? yg[u * cs] : 0.f;
     };
-    if ((int)blockIdx.x < ntiles) load_col(blockIdx.x);
+    constexpr int depth = D <= 32 ? 2 : 1;
     uint32_t phase = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // One tile: stage its inputs from buf, refill buf with the tile `depth` steps later,
+    // then MMAs and the stores of X.  Returns false when the MMA wait gave up.
+    auto tile = [&](int t, float (&buf)[D]) -> bool {
         const int p = t * 128 + tid;
         const bool valid = p < P;
 #pragma unroll
         for (int a16 = 0; a16 < D; a16 += 16) {
-            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 0), v + a16);
-            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 8), v + a16 + 8);
+            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 0), buf + a16);
+            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 8), buf + a16 + 8);
         }
-        if (t + (int)gridDim.x < ntiles) load_col(t + gridDim.x);
+        if (t + depth * (int)gridDim.x < ntiles) load_col(buf, t + depth * gridDim.x);
         tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
@@ -588,7 +590,7 @@ __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__re
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
-        if (!*s_ok) break;
+        if (!*s_ok) return false;
         float *xg = Xo + (bl * D * N + n) * (long long)P + (valid ? p : 0);
 #pragma unroll 1
         for (int c8 = 0; c8 < D; c8 += 8, xg += 8 * cs) {
@@ -602,6 +604,23 @@ __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__re
         tc::fence_before();
         __syncthreads();
         tc::fence_after();
+        return true;
+    };
+    const int g0 = (int)gridDim.x;
+    if constexpr (depth == 2) {
+        float va[D], vb[D];
+        if ((int)blockIdx.x < ntiles) load_col(va, blockIdx.x);
+        if ((int)blockIdx.x + g0 < ntiles) load_col(vb, blockIdx.x + g0);
+        for (int t = blockIdx.x; t < ntiles; t += 2 * g0) {
+            if (!tile(t, va)) break;
+            if (t + g0 >= ntiles) break;
+            if (!tile(t + g0, vb)) break;
+        }
+    } else {
+        float va[D];
+        if ((int)blockIdx.x < ntiles) load_col(va, blockIdx.x);
+        for (int t = blockIdx.x; t < ntiles; t += g0)
+            if (!tile(t, va)) break;
     }
     if (!*s_ok && tid == 0 && flag) atomicOr(flag, 8u);
     tc::fence_before();
