@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "dn_internal.cuh"
 
@@ -1649,13 +1650,12 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     const bool coop_ok = sizeof(T) == 4 && g.d == 64 && (g.W == 3 || g.W == 5);
     for (int l = 1; l <= g.L; ++l) {
         err = cudaErrorNotSupported;
-        if (coop_ok)
-            err = launch_ab_coop(reinterpret_cast<const AbArgs<float> &>(a), l, reinterpret_cast<float *>(S),
-                                 reinterpret_cast<const float *>(DX), PART, st);
-        if (err == cudaErrorNotSupported && stream_ok) {
-            cudaGetLastError();
-            err = launch_ab_stream(reinterpret_cast<const AbArgs<float> &>(a), l, reinterpret_cast<float *>(S),
-                                   reinterpret_cast<const float *>(DX), PART, st);
+        if constexpr (std::is_same_v<T, float>) {
+            if (coop_ok) err = launch_ab_coop(a, l, S, DX, PART, st);
+            if (err == cudaErrorNotSupported && stream_ok) {
+                cudaGetLastError();
+                err = launch_ab_stream(a, l, S, DX, PART, st);
+            }
         }
         if (err == cudaSuccess) continue;
         if (err != cudaErrorNotSupported) return err;
