@@ -201,8 +201,11 @@ dn_status dn_recompute_flip_ratios(dn_model *model, int N, const int8_t *spins_d
  * (t = 8 for DN_FP64, 4 for DN_FP32); a request that does not fit returns
  * DN_EINVAL and does nothing.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the array and nothing in it needs clearing,
- * but calls that overlap on the GPU (other streams or threads) race on it. */
+ * stream capture.  The address is kept for the life of the process and does not
+ * survive cudaDeviceReset() or another reset of the device's primary context: do
+ * not call this entry point on a device after such a reset.  All calls share the
+ * array and nothing in it needs clearing, but calls that overlap on the GPU (other
+ * streams or threads) race on it. */
 dn_status dn_full_forward_noalloc(const dn_model *model, int N, const int8_t *spins_dev, int B, dn_precision prec,
                                   void *stream, double *logpsi_dev, double *Omega_dev);
 
@@ -236,8 +239,12 @@ dn_status dn_logpsi_grad(dn_model *model, int N, const int8_t *spins_dev, int B,
  *     size does not grow with the parameter count;
  *   s_dev [nk][nk] float64 (may be NULL): Oc[:, k0:k0+nk]^T Oc[:, k0:k0+nk] / B, the
  *     parameter-space matrix of a contiguous block of parameters.
- * Products accumulate in the precision of O (float32: partial sums of 512 terms added
- * into a second float32 sum).  Errors: DN_EINVAL, DN_ENOMEM, DN_ECUDA. */
+ * float64 O: FMA products accumulated in float64.  float32 O: the Gram matrix runs on
+ * the tensor cores with every value split into three BF16 terms (6 products, about
+ * float32 accuracy), accumulated in float32 over K splits of at most 16384 parameters,
+ * the splits summed in float64; the parameter block s_dev accumulates FMA products in
+ * float32 in partial sums of 512 terms added into a second float32 sum.
+ * Errors: DN_EINVAL, DN_ENOMEM, DN_ECUDA. */
 dn_status dn_sr_matrices(const void *O_dev, int B, size_t n_params, dn_precision prec, void *stream, double *gram_dev,
                          size_t k0, int nk, double *s_dev);
 

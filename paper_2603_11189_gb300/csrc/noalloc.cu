@@ -13,7 +13,10 @@
 // loads the library until the process exits.  Its device address is looked up
 // once per device (cudaGetSymbolAddress, on the first call made with that
 // device current); that first call should therefore happen before any stream
-// capture.  All calls share the array and it keeps the contents of the last
+// capture.  The looked-up address is kept for the life of the process: a
+// cudaDeviceReset() (or any reset of the primary context by the host program)
+// reloads the module and invalidates it, so this entry point must not be used
+// on a device after such a reset.  All calls share the array and it keeps the contents of the last
 // call: every value a call reads is written earlier in the same call, so
 // nothing needs clearing, but two calls that overlap on the GPU (different
 // streams, or different host threads) race on it.

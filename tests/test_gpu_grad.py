@@ -2,7 +2,11 @@
 (dn_logpsi_grad through the C ABI) against the oracle's reverse pass, which the CPU tests
 pin to central differences and to the network's homogeneity.
 
-Bars: FP64 1e-10 and FP32 1e-4, relative to max(1, max_k |O_ref[b, k]|) per sample.
+Bars: FP64 1e-10 and FP32 1e-4 on every element, relative to
+max(|O_ref[b, k]|, 1e-2 max(1, max_k |O_ref[b, k]|)): entries down to one percent of their
+sample's largest log-derivative are held to the bar relative to themselves; smaller ones,
+whose FP32 value is set by cancellation between much larger terms, to the bar relative to
+that floor.
 """
 import numpy as np
 import pytest
@@ -41,9 +45,13 @@ def _params(desc, seed):
     return p
 
 
-def _err(got, ref):
-    scale = np.maximum(1.0, np.abs(ref).max(axis=1, keepdims=True))
-    return np.max(np.abs(got - ref) / scale)
+FLOOR = 1e-2
+
+
+def _err(got, ref, floor=FLOOR):
+    """Largest element-wise error relative to max(|ref|, floor * max(1, row maximum))."""
+    row = np.maximum(1.0, np.abs(ref).max(axis=1, keepdims=True))
+    return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), floor * row))
 
 
 CASES = [
@@ -68,7 +76,8 @@ def test_grad_matches_oracle(dn, case, prec):
     got = O.double().cpu().numpy()
     bar = 1e-10 if prec == "fp64" else 1e-4
     e = _err(got, O_ref)
-    print(f"{prec} {case}: O rel err {e:.3e}")
+    print(f"{prec} {case}: O element-wise rel err {e:.3e} (floor 1e-2); "
+          f"floor 1e-4: {_err(got, O_ref, 1e-4):.3e}; row-max normalised: {_err(got, O_ref, 1.0):.3e}")
     assert e <= bar
     assert np.max(np.abs(lp.cpu().numpy() - lp_ref) / np.maximum(1.0, np.abs(lp_ref))) <= bar
     model.close()
@@ -120,8 +129,10 @@ def test_grad_lrtfim_n256_workload_sampled(dn):
     assert torch.isfinite(O).all()
     pick = [0, 4095]
     lp_ref, O_ref = oracle.grad_logpsi(desc, p, spins[pick])
-    e = _err(O[pick].double().cpu().numpy(), O_ref)
-    print(f"N=256 workload sampled O rel err {e:.3e}")
+    got = O[pick].double().cpu().numpy()
+    e = _err(got, O_ref)
+    print(f"N=256 workload sampled O element-wise rel err {e:.3e} (floor 1e-2); "
+          f"floor 1e-4: {_err(got, O_ref, 1e-4):.3e}")
     assert e <= 1e-4
     model.close()
 
@@ -141,3 +152,19 @@ def test_sr_matrices(dn, prec):
     assert np.max(np.abs(G.cpu().numpy() - G_ref)) <= bar * np.abs(G_ref).max()
     assert np.max(np.abs(S.cpu().numpy() - S_ref)) <= bar * np.abs(S_ref).max()
     assert P > 100
+
+
+def test_sr_gram_many_k_splits(dn):
+    """FP32 Gram over 700,000 parameters: the tensor-core Gram accumulates at most 16384
+    terms per split in FP32 and sums the 43 splits in FP64; checked against an FP64
+    product of the same (FP32) values, with ragged 128-sample tiles."""
+    B, P = 600, 700_000
+    rng = np.random.default_rng(11)
+    O = (rng.standard_normal((B, P)) * rng.uniform(0.1, 3.0, size=P)).astype(np.float32)
+    O[:, :5000] += 0.7                      # columns with a mean, removed by the centring
+    G, _ = dn.sr_matrices(cuda(O), gram=True)
+    Oc = O.astype(np.float64) - O.astype(np.float64).mean(axis=0)
+    G_ref = Oc @ Oc.T / B
+    err = np.max(np.abs(G.cpu().numpy() - G_ref)) / np.abs(G_ref).max()
+    print(f"SR Gram B={B} P={P}: max error / max |G| = {err:.3e}")
+    assert err <= 1e-5

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 from synth import ModelDesc
 
@@ -75,6 +76,10 @@ def test_noalloc_matches_full_forward_on_consecutive_calls(dn, prec, tol):
         a, b = om.cpu().numpy(), om_ref.cpu().numpy()
         assert np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b))) <= tol
     assert torch.cuda.memory_allocated() - before < (1 << 20)   # only the result tensors
+    # The same amplitudes against the CPU FP64 oracle.
+    for (st, lp, _), s in zip(outs, batches):
+        lp_or, _ = oracle.logpsi(cfg["desc"], synth.make_params(cfg), s.cpu().numpy())
+        assert np.max(np.abs(lp.cpu().numpy() - lp_or) / np.maximum(1.0, np.abs(lp_or))) <= tol
     model.close()
 
 
