@@ -310,6 +310,14 @@ dn_status dn_profile_enable(int on);
 int dn_profile_count(void);
 dn_status dn_profile_get(int i, char *name, size_t name_len, long long *launches, double *total_ms);
 
+/* Choice between two exact implementations of the end of a link-propagation chain
+ * (App. "Exact algorithm to construct link tensors", Eqs. X_def, L_def): on (1, the
+ * default) the last vertex hop D0^(L-1) and the band of G^(L) run as one fused kernel
+ * where it supports the shape (FP32 caches, d = 32, band half-width Rk <= 4); off (0)
+ * they run as two kernels with the hop output in device memory.  Both give the same
+ * link tensors.  Process-wide; affects caches built after the call.  Always DN_OK. */
+dn_status dn_set_fused_links(int on);
+
 /* Release a cache (stream-ordered on the stream of the call that built it). */
 void dn_cache_destroy(dn_cache *cache);
 

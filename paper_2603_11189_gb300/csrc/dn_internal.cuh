@@ -238,6 +238,16 @@ cudaError_t launch_tgemm_tc(const Geom &g, const float *taps, int P, const float
 cudaError_t launch_dhop_tc(int d, int N, int P, const float *Dm, long long dm_ss, const float *Y, float *Xo, int nb,
                            int planes, unsigned *flag, cudaStream_t st);
 
+// Last vertex hop of a chain fused with the last layer's band convolution (dband_tc.cu):
+// band of G^(L) D0^(L-1) Y for interlayer sources (nsrc = d), FP32 with 3 BF16 planes.
+// dband_tc_ok() tells whether launch_dband_tc() takes the shape (else cudaErrorNotSupported).
+bool dband_tc_ok(int d, int N, int periodic, int P, int nsrc, int R);
+cudaError_t launch_dband_tc(int d, int N, int periodic, int P, int nsrc, int R, const float *taps, const float *Dm,
+                            long long dm_ss, const float *Y, float *band, long long bss, long long brs, long long bos,
+                            long long b0, int nb, unsigned *flag, cudaStream_t st);
+// Process-wide choice between the fused and the two-kernel chain ends (both exact; on by default).
+extern int g_fused_links;
+
 // Reverse pass for the parameter log-derivatives (grad.cu).  Operands of the per-sample
 // outer-product sums of one layer, [B][N][.] each.
 template <typename T>

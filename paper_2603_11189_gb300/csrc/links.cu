@@ -986,6 +986,10 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
         // Interlayer sources (m >= 1), P = N d.
         for (int msrc = 1; msrc <= L - 2; ++msrc) {
             GenSrc<T> gs{pl.taps + (long long)msrc * g.R * d, Dm + (long long)msrc * N * dd, dm_ss};
+            // The chain's last vertex hop and the band of G^(L) run as one kernel where it applies
+            // (FP32, d = 32): the hop output Y = G^(L-1) ... then never round-trips HBM.
+            const bool fuse_end = sizeof(T) == 4 && dplanes == 3 && g_fused_links && msrc + 2 < L &&
+                                  dband_tc_ok(d, N, g.periodic, (int)Pm, d, c->Rk);
             for (int n = msrc + 2; n <= L; ++n) {
                 BandDst bd{(long long)c->P * N * nRk * dd, (long long)nRk * dd, dd, c->Rk, d};
                 T *dst = K + (long long)pair_index(n, msrc) * N * nRk * dd;
@@ -995,9 +999,18 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
                     err = launch_tgemm<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, U, dst, bd,
                                           b0, nb, c->flag, st, planes);
                     if (err != cudaSuccess) return err;
+                    if (fuse_end && n == L - 1) continue;
                     if ((err = launch_dhop<T>(g, (int)Pm, Dm + (long long)(n - 1) * N * dd, dm_ss, U, F, nb, st, dplanes, c->flag)) !=
                         cudaSuccess)
                         return err;
+                } else if (fuse_end) {
+                    if constexpr (sizeof(T) == 4) {
+                        err = launch_dband_tc(d, N, g.periodic, (int)Pm, d, c->Rk, reinterpret_cast<const float *>(taps_n),
+                                              reinterpret_cast<const float *>(Dm + (long long)(L - 2) * N * dd), dm_ss,
+                                              reinterpret_cast<const float *>(U), reinterpret_cast<float *>(dst), bd.ss,
+                                              bd.rs, bd.os, b0, nb, c->flag, st);
+                        if (err != cudaSuccess) return err;
+                    }
                 } else {
                     err = launch_bandconv<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, dst, bd,
                                              b0, nb, st);

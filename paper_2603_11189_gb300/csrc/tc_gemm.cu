@@ -664,6 +664,10 @@ cudaError_t launch_dhop_tc(int d, int N, int P, const float *Dm, long long dm_ss
 // tiles stage one operand and use it on both sides.  With NPL planes per value the products
 // of planes pa + pb < NPL are accumulated (NPL = 3: FP32-grade products).
 constexpr int kGcK = 64;
+// Chunks per tensor-memory partial: the accumulator's FP32 additions carry a small one-sided
+// rounding bias (measured: 1e-4 relative after 16384 terms), so every kGcFold chunks (1024
+// terms) the partial is added into per-thread FP32 totals (round to nearest) and restarted.
+constexpr int kGcFold = 16;
 
 template <int NPL>
 __global__ void __launch_bounds__(256, 1) k_gram_tc(const float *__restrict__ X, int n, long long K,
@@ -736,6 +740,21 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(const float *__restrict__ X,
         load(va, xa, ra, kb);
         if (!diag) load(vc, xc, rc, kb);
     }
+    // Running totals of this thread's 64 cells (rows quad*32 + lane, columns half*64 .. +63).
+    const int quad = warp & 3, half = warp >> 2;
+    const uint32_t tcell = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64);
+    float tot[64];
+#pragma unroll
+    for (int u = 0; u < 64; ++u) tot[u] = 0.f;
+    auto fold = [&]() {
+#pragma unroll
+        for (int c8 = 0; c8 < 64; c8 += 8) {
+            float v[8];
+            tc::tmem_ld8(tcell + (uint32_t)c8, v);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) tot[c8 + u] += v[u];
+        }
+    };
     for (int c = 0; c < nch; ++c) {
         const int sidx = c & 1;
         unsigned char *A = st0 + sidx * stage_b, *Bm = A + opnd;
@@ -743,6 +762,18 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(const float *__restrict__ X,
             // the MMAs of chunk c - 2 read this stage
             if (!tc::wait(mbar + sidx, (uint32_t)((c >> 1) + 1) & 1u) && lane == 0) *s_ok = 0;
             __syncwarp();
+        }
+        if (c % kGcFold == 0 && c > 0) {
+            // the partial of chunks c - kGcFold .. c - 1 is complete once chunk c - 1's MMAs are
+            uint32_t done = 1u;
+            if (lane == 0) done = tc::wait(mbar + ((c - 1) & 1), (uint32_t)(((c - 1) >> 1) & 1)) ? 1u : 0u;
+            done = __shfl_sync(0xffffffffu, done, 0);
+            if (!done) {
+                if (lane == 0) *s_ok = 0;
+            } else {
+                tc::fence_after();
+                fold();
+            }
         }
         store(A, va);
         if (!diag) store(Bm, vc);
@@ -767,7 +798,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(const float *__restrict__ X,
                     for (int pb = 0; pa + pb < NPL; ++pb)
                         tc::mma_bf16(tmem, tc::desc(tc::smem_u32(A + pa * plane + sl * slab)),
                                      tc::desc(tc::smem_u32(Bu + pb * plane + sl * slab)), idesc,
-                                     (c == 0 && sl == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+                                     (c % kGcFold == 0 && sl == 0 && pa == 0 && pb == 0) ? 0u : 1u);
             tc::commit(mbar + sidx);
         }
     }
@@ -782,16 +813,11 @@ __global__ void __launch_bounds__(256, 1) k_gram_tc(const float *__restrict__ X,
     tc::fence_after();
     const bool ok = *s_ok != 0;
     // epilogue: warp (quad, half) -> rows quad*32 + lane, columns half*64 .. +63
-    const int quad = warp & 3, half = warp >> 2;
+    if (ok && nch > 0) fold();
     float *pt = part + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 128 * 128 + (long long)(quad * 32 + lane) * 128 +
                 half * 64;
-#pragma unroll 1
-    for (int c8 = 0; c8 < 64; c8 += 8) {
-        float v[8];
-        if (nch > 0) tc::tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 64 + c8), v);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) pt[c8 + u] = (ok && nch > 0) ? v[u] : (nch > 0 ? __int_as_float(0x7fc00000) : 0.f);
-    }
+    for (int u = 0; u < 64; ++u) pt[u] = (ok && nch > 0) ? tot[u] : (nch > 0 ? __int_as_float(0x7fc00000) : 0.f);
     if (!ok && tid == 0 && flag) atomicOr(flag, 8u);
     tc::fence_before();
     __syncthreads();
