@@ -340,10 +340,11 @@ class Cache:
 
 
 def _device_view(ptr: int, count: int, typestr: str) -> torch.Tensor:
-    """Non-owning torch view of library-owned device memory."""
+    """Non-owning torch view of library-owned device memory (callers copy it at once; torch
+    accepts only views flagged writable)."""
 
     class _Arr:
-        __cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, True), "version": 3}
+        __cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, False), "version": 3}
 
     return torch.as_tensor(_Arr(), device="cuda")
 
