@@ -17,9 +17,11 @@
 //     thread issues the six plane products with pa + pb <= 2 (M = 128 columns,
 //     N = 32 output channels, K = 32 input channels, FP32 accumulation in tensor
 //     memory), the same products and order as the separate vertex-hop kernel;
+//   - each warp announces its staged planes on an mbarrier; only the MMA-issuing thread
+//     waits for all sixteen, the others go on to the band sums;
 //   - while the MMAs of site n run, every thread adds site n-1 into its band sums:
 //     warp w owns TMEM lanes 32 (w & 3) .. + 31 (one source site, lane = source channel
-//     c') and output channels 16 (w >> 2) .. + 15, with the 2R+1 band offsets held in
+//     c') and output channels 8 (w >> 2) .. + 7, with the 2R+1 band offsets held in
 //     registers (taps from a shared table, already wrapped for rings).  The band sums
 //     are formed in the same order (site n ascending, fmaf(tap, z, acc)) as the separate
 //     band kernel, so the fused result equals the two-kernel one.
@@ -35,7 +37,7 @@ namespace {
 constexpr int kDbD = 32;                             // channels
 constexpr int kDbCols = 128;                         // source columns per CTA
 constexpr int kDbStages = 4;                         // depth of the input ring
-constexpr int kDbThreads = 256;
+constexpr int kDbThreads = 512;
 constexpr uint32_t kDbUBytes = kDbD * kDbCols * 4;   // Y[:, n, tile]: 16 KB
 constexpr uint32_t kDbDBytes = kDbD * kDbD * 4;      // D0_n: 4 KB
 constexpr uint32_t kDbStage = kDbUBytes + kDbDBytes;
@@ -69,8 +71,9 @@ __global__ void __launch_bounds__(kDbThreads, 1)
     unsigned char *ring = Bbuf + 2 * kDbBBuf;                    // [stages][Y slice | D0_n]
     float *tap_s = reinterpret_cast<float *>(ring + kDbStages * kDbStage);   // [N + 3 + 2R][32]
     const int ntap = N + 3 + 2 * R;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(tap_s + (size_t)ntap * kDbD);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 2);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(tap_s + (size_t)ntap * kDbD);   // [2] MMAs of site n done
+    uint64_t *staged = mbar + 2;                                                   // [2] operands of site n staged
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(staged + 2);
     int *s_ok = reinterpret_cast<int *>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -96,22 +99,24 @@ __global__ void __launch_bounds__(kDbThreads, 1)
         }
         tap_s[q] = v;
     }
-    // Site n's inputs into ring stage st: 1024 + 256 chunks of 16 bytes, five per thread.
+    // Site n's inputs into ring stage st: 1024 + 256 chunks of 16 bytes.
     auto issue = [&](int n, int st) {
         unsigned char *dst = ring + st * kDbStage;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
             const int j = tid + u * kDbThreads;
             const int a = j >> 5, c16 = j & 31;
             const int p = p0 + c16 * 4;
             const bool ok = p < P;
             cp_async16(dst + a * (kDbCols * 4) + c16 * 16, ok ? Yb + ((long long)a * N + n) * P + p : Yb, ok ? 16u : 0u);
         }
-        cp_async16(dst + kDbUBytes + tid * 16, Db + (long long)n * (kDbD * kDbD) + tid * 4, 16u);
+        if (tid < 256) cp_async16(dst + kDbUBytes + tid * 16, Db + (long long)n * (kDbD * kDbD) + tid * 4, 16u);
     };
     if (tid == 0) {
         tc::mbar_init(&mbar[0], 1);
         tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init(&staged[0], kDbThreads / 32);
+        tc::mbar_init(&staged[1], kDbThreads / 32);
         asm volatile("fence.mbarrier_init.release.cluster;");
         *s_ok = 1;
     }
@@ -126,14 +131,14 @@ __global__ void __launch_bounds__(kDbThreads, 1)
     tc::fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t idesc = tc::idesc_bf16(128, kDbD);
-    const int q4 = warp & 3, ch = warp >> 2;                      // lane quadrant, output-channel half
+    const int q4 = warp & 3, cg = warp >> 2;                      // lane quadrant, group of 8 output channels
     const uint32_t tlane = (uint32_t)(32 * q4) << 16;
 
-    float acc[NB][16];
+    float acc[NB][8];
 #pragma unroll
     for (int dl = 0; dl < NB; ++dl)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc[dl][c] = 0.f;
+        for (int c = 0; c < 8; ++c) acc[dl][c] = 0.f;
 
     bool good = true;
     for (int n = 0; n <= N; ++n) {
@@ -153,14 +158,13 @@ __global__ void __launch_bounds__(kDbThreads, 1)
             unsigned char *A = Abuf + (n & 1) * kDbABuf;
             unsigned char *Bp = Bbuf + (n & 1) * kDbBBuf;
             {
-                // A operand: rows = the tile's columns p, K = input channel a (this thread: 16 of them).
-                const int pl = tid & 127, ah = tid >> 7;
-                const float *us = reinterpret_cast<const float *>(st) + (ah * 16) * kDbCols + pl;
-                float v[16];
+                // A operand: rows = the tile's columns p, K = input channel a (this thread: 8 of them).
+                const int pl = tid & 127, a8 = (tid >> 7) * 8;
+                const float *us = reinterpret_cast<const float *>(st) + a8 * kDbCols + pl;
+                float v[8];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) v[u] = us[u * kDbCols];
-                tc::stage8_planes<3>(A, kDbAPlane, (uint32_t)ah * kDbASlab + tc::canon(pl, 0), v);
-                tc::stage8_planes<3>(A, kDbAPlane, (uint32_t)ah * kDbASlab + tc::canon(pl, 8), v + 8);
+                for (int u = 0; u < 8; ++u) v[u] = us[u * kDbCols];
+                tc::stage8_planes<3>(A, kDbAPlane, (uint32_t)(a8 >> 4) * kDbASlab + tc::canon(pl, a8 & 15), v);
             }
             if (tid < 128) {
                 // B operand: rows = output channel c, K = input channel a.
@@ -171,29 +175,34 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 for (int u = 0; u < 8; ++u) v[u] = ds[u];
                 tc::stage8_planes<3>(Bp, kDbBPlane, (uint32_t)(k8 >> 4) * kDbBSlab + tc::canon(c, k8 & 15), v);
             }
+            // Every thread's plane stores become visible to the tensor cores, then one arrival per warp.
             tc::fence_async_smem();
-            tc::fence_before();
-            __syncthreads();
-            tc::fence_after();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&staged[n & 1])) : "memory");
             if (tid == 0) {
+                if (!tc::wait(&staged[n & 1], (uint32_t)((n >> 1) & 1))) {
+                    *s_ok = 0;
+                } else {
+                    tc::fence_after();
 #pragma unroll 1
-                for (int s = 0; s < 2; ++s)
+                    for (int s = 0; s < 2; ++s)
 #pragma unroll
-                    for (int pa = 0; pa < 3; ++pa)
+                        for (int pa = 0; pa < 3; ++pa)
 #pragma unroll
-                        for (int pb = 0; pa + pb < 3; ++pb)
-                            tc::mma_bf16(tmem + (uint32_t)((n & 1) * kDbD),
-                                         tc::desc(tc::smem_u32(A + pa * kDbAPlane + s * kDbASlab)),
-                                         tc::desc(tc::smem_u32(Bp + pb * kDbBPlane + s * kDbBSlab)), idesc,
-                                         (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
-                tc::commit(&mbar[n & 1]);
+                            for (int pb = 0; pa + pb < 3; ++pb)
+                                tc::mma_bf16(tmem + (uint32_t)((n & 1) * kDbD),
+                                             tc::desc(tc::smem_u32(A + pa * kDbAPlane + s * kDbASlab)),
+                                             tc::desc(tc::smem_u32(Bp + pb * kDbBPlane + s * kDbBSlab)), idesc,
+                                             (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+                    tc::commit(&mbar[n & 1]);
+                }
             }
         }
         if (n >= 1) {
             // Band sums of site m = n - 1 (its MMAs were issued one iteration ago).
             const int m = n - 1;
             // One waiter per warp; the shuffle keeps the warp converged for the
-            // warp-wide tensor-memory loads that follow.
+            // warp-wide tensor-memory load that follows.
             uint32_t done = 1u;
             if (lane == 0) done = tc::wait(&mbar[m & 1], (uint32_t)((m >> 1) & 1)) ? 1u : 0u;
             done = __shfl_sync(0xffffffffu, done, 0);
@@ -204,16 +213,14 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 continue;
             }
             tc::fence_after();
-            float z[16];
-            const uint32_t zc = tmem + tlane + (uint32_t)((m & 1) * kDbD + 16 * ch);
-            tc::tmem_ld8(zc, z);
-            tc::tmem_ld8(zc + 8, z + 8);
-            const float *trow = tap_s + (size_t)(q4 + N - 1 - m) * kDbD + 16 * ch;
+            float z[8];
+            tc::tmem_ld8(tmem + tlane + (uint32_t)((m & 1) * kDbD + 8 * cg), z);
+            const float *trow = tap_s + (size_t)(q4 + N - 1 - m) * kDbD + 8 * cg;
 #pragma unroll
             for (int dl = 0; dl < NB; ++dl) {
                 const float4 *t4 = reinterpret_cast<const float4 *>(trow + dl * kDbD);
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
+                for (int c4 = 0; c4 < 2; ++c4) {
                     const float4 t = t4[c4];
                     acc[dl][4 * c4 + 0] = fmaf(t.x, z[4 * c4 + 0], acc[dl][4 * c4 + 0]);
                     acc[dl][4 * c4 + 1] = fmaf(t.y, z[4 * c4 + 1], acc[dl][4 * c4 + 1]);
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
     if (good) {
         const int k = k0 + q4;
         if (k < N && p0 + 32 * q4 < P) {
-            float *colb = band + (b0 + bl) * bss + (long long)(16 * ch) * kDbD + lane;
+            float *colb = band + (b0 + bl) * bss + (long long)(8 * cg) * kDbD + lane;
 #pragma unroll
             for (int dl = 0; dl < NB; ++dl) {
                 int i = k + dl - R;
@@ -239,7 +246,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 else if (i < 0 || i >= N) continue;
                 float *dst = colb + (long long)i * brs + (long long)(2 * R - dl) * bos;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) dst[c * kDbD] = acc[dl][c];
+                for (int c = 0; c < 8; ++c) dst[c * kDbD] = acc[dl][c];
             }
         }
     } else if (tid == 0 && flag) {
@@ -271,7 +278,7 @@ bool dband_tc_ok(int d, int N, int periodic, int P, int nsrc, int R) {
     if (d != kDbD || nsrc != kDbD || P != N * kDbD || N < 1) return false;
     if (periodic && N < 2 * R + 1) return false;
     if (R != 2 && R != 3 && R != 4) return false;
-    return kDbFixed + (size_t)(N + 3 + 2 * R) * kDbD * 4 + 64 <= 225 * 1024;
+    return kDbFixed + (size_t)(N + 3 + 2 * R) * kDbD * 4 + 64 <= 225 * 1024;   // mbarriers and slots: 40 B
 }
 
 cudaError_t launch_dband_tc(int d, int N, int periodic, int P, int nsrc, int R, const float *taps, const float *Dm,
