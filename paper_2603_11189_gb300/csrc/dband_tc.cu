@@ -10,23 +10,26 @@
 // written to HBM and read back; here it never leaves the chip.
 //
 // One CTA per (configuration, tile of 128 source columns = 4 source sites), looping
-// over all N sites n:
-//   - Y[:, n, tile] (32 x 128 floats) and D0_n (32 x 32) arrive by cp.async in a
-//     four-stage ring, so that the HBM reads of later sites are in flight;
-//   - both are split into three BF16 planes (v = p0 + p1 + p2 + rest) and one elected
-//     thread issues the six plane products with pa + pb <= 2 (M = 128 columns,
-//     N = 32 output channels, K = 32 input channels, FP32 accumulation in tensor
-//     memory), the same products and order as the separate vertex-hop kernel;
-//   - each warp announces its staged planes on an mbarrier; only the MMA-issuing thread
-//     waits for all sixteen, the others go on to the band sums;
-//   - while the MMAs of site n run, every thread adds site n-1 into its band sums:
-//     warp w owns TMEM lanes 32 (w & 3) .. + 31 (one source site, lane = source channel
-//     c') and output channels 8 (w >> 2) .. + 7, with the 2R+1 band offsets held in
-//     registers (taps from a shared table, already wrapped for rings).  The band sums
-//     are formed in the same order (site n ascending, fmaf(tap, z, acc)) as the separate
-//     band kernel, so the fused result equals the two-kernel one.
+// over all N sites n, with specialised warps connected by mbarriers:
+//   - warpgroup 0 (warps 0-3) stages operands: Y[:, n, tile] (32 x 128 floats) and D0_n
+//     (32 x 32) arrive in a five-stage ring by bulk asynchronous copies (one thread
+//     issues them as stages free up); every value is split into three BF16 planes
+//     (v = p0 + p1 + p2 + rest) in one of two operand buffers, and one thread issues the
+//     six plane products with pa + pb <= 2 (M = 128 columns, N = 32 output channels,
+//     K = 32 input channels, FP32 accumulation into one of two tensor-memory buffers):
+//     the same products and order as the separate vertex-hop kernel;
+//   - warpgroups 1-2 (warps 4-11) only add each site into the band sums: warp w owns
+//     TMEM lanes 32 (w & 3) .. + 31 (one source site, lane = source channel c') and
+//     output channels 16 ((w - 4) >> 2) .. + 15, with the 2R+1 band offsets in registers
+//     (taps from a shared table, already wrapped for rings); they release each
+//     accumulator buffer as soon as they have read it.  The band sums are formed in the
+//     same order (site n ascending, fmaf(tap, z, acc)) as the separate band kernel, so
+//     the fused result equals the two-kernel one.
+//   Registers move from the staging warpgroup to the band warpgroups (setmaxnreg):
+//   384 threads x 168 at launch = 128 x 72 + 256 x 216.
 // Every mbarrier wait is bounded; a wait that gives up raises bit 8 of the cache flag,
-// the CTA drains its own copies, frees its tensor memory and writes nothing.
+// every role stops, the copies already issued are waited for (bounded), the tensor
+// memory is freed and nothing is written.
 #include "dn_internal.cuh"
 #include "tc_common.cuh"
 
@@ -36,8 +39,9 @@ namespace {
 
 constexpr int kDbD = 32;                             // channels
 constexpr int kDbCols = 128;                         // source columns per CTA
-constexpr int kDbStages = 4;                         // depth of the input ring
-constexpr int kDbThreads = 512;
+constexpr int kDbStages = 5;                         // depth of the input ring
+constexpr int kDbThreads = 384;                      // warpgroup 0: staging; 1-2: band sums
+constexpr int kDbStageRegs = 72, kDbBandRegs = 216;  // 128 x 72 + 256 x 216 = 384 x 168
 constexpr uint32_t kDbUBytes = kDbD * kDbCols * 4;   // Y[:, n, tile]: 16 KB
 constexpr uint32_t kDbDBytes = kDbD * kDbD * 4;      // D0_n: 4 KB
 constexpr uint32_t kDbStage = kDbUBytes + kDbDBytes;
@@ -48,14 +52,22 @@ constexpr uint32_t kDbBPlane = 2 * kDbBSlab;
 constexpr uint32_t kDbABuf = 3 * kDbAPlane;          // three planes
 constexpr uint32_t kDbBBuf = 3 * kDbBPlane;
 constexpr uint32_t kDbFixed = 2 * kDbABuf + 2 * kDbBBuf + kDbStages * kDbStage;
+constexpr uint32_t kDbTail = (2 * kDbStages + 6) * 8 + 16;   // mbarriers, TMEM slot, status
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)), "l"(src), "r"(bytes)
+__device__ __forceinline__ void arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void arrive_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)),
+                 "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+                 : "memory");
+}
 
 }  // namespace
 
@@ -71,9 +83,12 @@ __global__ void __launch_bounds__(kDbThreads, 1)
     unsigned char *ring = Bbuf + 2 * kDbBBuf;                    // [stages][Y slice | D0_n]
     float *tap_s = reinterpret_cast<float *>(ring + kDbStages * kDbStage);   // [N + 3 + 2R][32]
     const int ntap = N + 3 + 2 * R;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(tap_s + (size_t)ntap * kDbD);   // [2] MMAs of site n done
-    uint64_t *staged = mbar + 2;                                                   // [2] operands of site n staged
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(staged + 2);
+    uint64_t *full = reinterpret_cast<uint64_t *>(tap_s + (size_t)ntap * kDbD);   // [S] stage loaded
+    uint64_t *empty = full + kDbStages;                                            // [S] stage read
+    uint64_t *staged = empty + kDbStages;                                          // [2] planes of site n
+    uint64_t *mmad = staged + 2;                                                   // [2] MMAs of site n done
+    uint64_t *zfree = mmad + 2;                                                    // [2] accumulator read
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(zfree + 2);
     int *s_ok = reinterpret_cast<int *>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -82,7 +97,9 @@ __global__ void __launch_bounds__(kDbThreads, 1)
     const int p0 = (int)(blk % tiles) * kDbCols;
     const long long bl = blk / tiles;
     const int k0 = p0 / kDbD;
-    const float *Yb = Y + bl * (long long)kDbD * N * P;          // [a][n][p] of this configuration
+    const int ncol = P - p0 < kDbCols ? P - p0 : kDbCols;           // a multiple of 32
+    const uint32_t rowbytes = (uint32_t)ncol * 4, sitebytes = kDbD * rowbytes + kDbDBytes;
+    const float *Yb = Y + bl * (long long)kDbD * N * P + p0;     // [a][n][p] of this configuration, tile start
     const float *Db = Dm + bl * dm_ss;                           // [n][c][a]
 
     // tap_s[j][c] = g_{r,c}, r = k0 - R - (N - 1) + j (circulant index on a ring, zero outside (-N, N)
@@ -99,90 +116,86 @@ __global__ void __launch_bounds__(kDbThreads, 1)
         }
         tap_s[q] = v;
     }
-    // Site n's inputs into ring stage st: 1024 + 256 chunks of 16 bytes.
-    auto issue = [&](int n, int st) {
-        unsigned char *dst = ring + st * kDbStage;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int j = tid + u * kDbThreads;
-            const int a = j >> 5, c16 = j & 31;
-            const int p = p0 + c16 * 4;
-            const bool ok = p < P;
-            cp_async16(dst + a * (kDbCols * 4) + c16 * 16, ok ? Yb + ((long long)a * N + n) * P + p : Yb, ok ? 16u : 0u);
-        }
-        if (tid < 256) cp_async16(dst + kDbUBytes + tid * 16, Db + (long long)n * (kDbD * kDbD) + tid * 4, 16u);
-    };
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
-        tc::mbar_init(&staged[0], kDbThreads / 32);
-        tc::mbar_init(&staged[1], kDbThreads / 32);
+        for (int st = 0; st < kDbStages; ++st) {
+            tc::mbar_init(&full[st], 1);
+            tc::mbar_init(&empty[st], 4);
+        }
+        for (int j = 0; j < 2; ++j) {
+            tc::mbar_init(&staged[j], 4);
+            tc::mbar_init(&mmad[j], 1);
+            tc::mbar_init(&zfree[j], 8);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         *s_ok = 1;
     }
     if (warp == 0) tc::tmem_alloc(tslot, 64);
-#pragma unroll
-    for (int s = 0; s < kDbStages - 1; ++s) {
-        if (s < N) issue(s, s);
-        cp_async_commit();
-    }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = tc::idesc_bf16(128, kDbD);
-    const int q4 = warp & 3, cg = warp >> 2;                      // lane quadrant, group of 8 output channels
-    const uint32_t tlane = (uint32_t)(32 * q4) << 16;
 
-    float acc[NB][8];
-#pragma unroll
-    for (int dl = 0; dl < NB; ++dl)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[dl][c] = 0.f;
-
-    bool good = true;
-    for (int n = 0; n <= N; ++n) {
-        if (n < N) {
-            cp_async_wait<kDbStages - 2>();
-            __syncthreads();
-            if (!*s_ok) {
-                good = false;
+    if (warp < 4) {
+        // ------------------------------------------------ warpgroup 0: loads, planes, MMAs --
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kDbStageRegs));
+        auto load = [&](int n, int st) {   // one thread: site n's inputs into ring stage st
+            unsigned char *dst = ring + st * kDbStage;
+            arrive_tx(&full[st], sitebytes);
+            for (int a = 0; a < kDbD; ++a)
+                bulk_g2s(dst + a * (kDbCols * 4), Yb + ((long long)a * N + n) * P, rowbytes, &full[st]);
+            bulk_g2s(dst + kDbUBytes, Db + (long long)n * (kDbD * kDbD), kDbDBytes, &full[st]);
+        };
+        int issued = 0;                    // sites whose copies thread 0 has issued
+        if (tid == 0)
+            for (; issued < kDbStages && issued < N; ++issued) load(issued, issued);
+        const uint32_t idesc = tc::idesc_bf16(128, kDbD);
+        for (int n = 0; n < N; ++n) {
+            const int st = n % kDbStages, j = n & 1;
+            bool ok = *((volatile int *)s_ok) != 0;
+            // the planes of buffer j were read by the MMAs of site n - 2; the stage holds site n
+            if (ok && n >= 2) ok = tc::wait(&mmad[j], (uint32_t)(((n - 2) >> 1) & 1));
+            if (ok) ok = tc::wait(&full[st], (uint32_t)((n / kDbStages) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) *s_ok = 0;
                 break;
             }
+            const unsigned char *src = ring + st * kDbStage;
+            unsigned char *A = Abuf + j * kDbABuf;
+            unsigned char *Bp = Bbuf + j * kDbBBuf;
             {
-                const int nn = n + kDbStages - 1;
-                if (nn < N) issue(nn, nn % kDbStages);
-                cp_async_commit();
-            }
-            const unsigned char *st = ring + (n % kDbStages) * kDbStage;
-            unsigned char *A = Abuf + (n & 1) * kDbABuf;
-            unsigned char *Bp = Bbuf + (n & 1) * kDbBBuf;
-            {
-                // A operand: rows = the tile's columns p, K = input channel a (this thread: 8 of them).
-                const int pl = tid & 127, a8 = (tid >> 7) * 8;
-                const float *us = reinterpret_cast<const float *>(st) + a8 * kDbCols + pl;
-                float v[8];
+                // A operand: row = column p = tid of the tile, K = input channel a (all 32).
+                const float *us = reinterpret_cast<const float *>(src) + tid;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = us[u * kDbCols];
-                tc::stage8_planes<3>(A, kDbAPlane, (uint32_t)(a8 >> 4) * kDbASlab + tc::canon(pl, a8 & 15), v);
-            }
-            if (tid < 128) {
-                // B operand: rows = output channel c, K = input channel a.
+                for (int a8 = 0; a8 < kDbD; a8 += 8) {
+                    float v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = us[(a8 + u) * kDbCols];
+                    tc::stage8_planes<3>(A, kDbAPlane, (uint32_t)(a8 >> 4) * kDbASlab + tc::canon(tid, a8 & 15), v);
+                }
+                // B operand: row = output channel c, K = input channel a.
                 const int c = tid >> 2, k8 = (tid & 3) * 8;
-                const float *ds = reinterpret_cast<const float *>(st + kDbUBytes) + c * kDbD + k8;
+                const float *ds = reinterpret_cast<const float *>(src + kDbUBytes) + c * kDbD + k8;
                 float v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = ds[u];
                 tc::stage8_planes<3>(Bp, kDbBPlane, (uint32_t)(k8 >> 4) * kDbBSlab + tc::canon(c, k8 & 15), v);
             }
-            // Every thread's plane stores become visible to the tensor cores, then one arrival per warp.
             tc::fence_async_smem();
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&staged[n & 1])) : "memory");
-            if (tid == 0) {
-                if (!tc::wait(&staged[n & 1], (uint32_t)((n >> 1) & 1))) {
-                    *s_ok = 0;
-                } else {
+            if (lane == 0) {
+                arrive(&staged[j]);
+                arrive(&empty[st]);
+            }
+            if (tid == 0 && issued < N) {
+                // refill this stage with site n + S once all four warps have read it
+                if (tc::wait(&empty[st], (uint32_t)((n / kDbStages) & 1))) load(issued++, st);
+                else *s_ok = 0;
+            }
+            if (tid == 96) {
+                bool go = tc::wait(&staged[j], (uint32_t)((n >> 1) & 1));
+                if (go && n >= 2) go = tc::wait(&zfree[j], (uint32_t)(((n - 2) >> 1) & 1));
+                if (go) {
                     tc::fence_after();
 #pragma unroll 1
                     for (int s = 0; s < 2; ++s)
@@ -190,37 +203,57 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                         for (int pa = 0; pa < 3; ++pa)
 #pragma unroll
                             for (int pb = 0; pa + pb < 3; ++pb)
-                                tc::mma_bf16(tmem + (uint32_t)((n & 1) * kDbD),
+                                tc::mma_bf16(tmem + (uint32_t)(j * kDbD),
                                              tc::desc(tc::smem_u32(A + pa * kDbAPlane + s * kDbASlab)),
                                              tc::desc(tc::smem_u32(Bp + pb * kDbBPlane + s * kDbBSlab)), idesc,
                                              (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
-                    tc::commit(&mbar[n & 1]);
+                    tc::commit(&mmad[j]);
+                } else {
+                    *s_ok = 0;
                 }
             }
+            __syncwarp();
         }
-        if (n >= 1) {
-            // Band sums of site m = n - 1 (its MMAs were issued one iteration ago).
-            const int m = n - 1;
-            // One waiter per warp; the shuffle keeps the warp converged for the
-            // warp-wide tensor-memory load that follows.
-            uint32_t done = 1u;
-            if (lane == 0) done = tc::wait(&mbar[m & 1], (uint32_t)((m >> 1) & 1)) ? 1u : 0u;
-            done = __shfl_sync(0xffffffffu, done, 0);
-            if (!done) {
+        if (tid == 0) {
+            // copies still in flight (only after a failure) land before the CTA exits
+            for (int n = issued - kDbStages > 0 ? issued - kDbStages : 0; n < issued; ++n)
+                (void)tc::wait(&full[n % kDbStages], (uint32_t)((n / kDbStages) & 1));
+        }
+    } else {
+        // ---------------------------------------------------- warpgroups 1-2: band sums --
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kDbBandRegs));
+        const int q4 = warp & 3, ch = (warp - 4) >> 2;
+        const uint32_t tlane = (uint32_t)(32 * q4) << 16;
+        float acc[NB][16];
+#pragma unroll
+        for (int dl = 0; dl < NB; ++dl)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[dl][c] = 0.f;
+        bool good = true;
+        for (int m = 0; m < N; ++m) {
+            const int j = m & 1;
+            bool ok = *((volatile int *)s_ok) != 0;
+            if (ok) ok = tc::wait(&mmad[j], (uint32_t)((m >> 1) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
                 if (lane == 0) *s_ok = 0;
                 good = false;
-                if (n == N) break;
-                continue;
+                break;
             }
             tc::fence_after();
-            float z[8];
-            tc::tmem_ld8(tmem + tlane + (uint32_t)((m & 1) * kDbD + 8 * cg), z);
-            const float *trow = tap_s + (size_t)(q4 + N - 1 - m) * kDbD + 8 * cg;
+            float z[16];
+            const uint32_t zc = tmem + tlane + (uint32_t)(j * kDbD + 16 * ch);
+            tc::tmem_ld8(zc, z);
+            tc::tmem_ld8(zc + 8, z + 8);
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) arrive(&zfree[j]);
+            const float *trow = tap_s + (size_t)(q4 + N - 1 - m) * kDbD + 16 * ch;
 #pragma unroll
             for (int dl = 0; dl < NB; ++dl) {
                 const float4 *t4 = reinterpret_cast<const float4 *>(trow + dl * kDbD);
 #pragma unroll
-                for (int c4 = 0; c4 < 2; ++c4) {
+                for (int c4 = 0; c4 < 4; ++c4) {
                     const float4 t = t4[c4];
                     acc[dl][4 * c4 + 0] = fmaf(t.x, z[4 * c4 + 0], acc[dl][4 * c4 + 0]);
                     acc[dl][4 * c4 + 1] = fmaf(t.y, z[4 * c4 + 1], acc[dl][4 * c4 + 1]);
@@ -228,17 +261,10 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                     acc[dl][4 * c4 + 3] = fmaf(t.w, z[4 * c4 + 3], acc[dl][4 * c4 + 3]);
                 }
             }
-            tc::fence_before();
         }
-    }
-    cp_async_wait<0>();
-    tc::fence_before();
-    __syncthreads();
-    if (!*s_ok) good = false;
-    if (good) {
         const int k = k0 + q4;
-        if (k < N && p0 + 32 * q4 < P) {
-            float *colb = band + (b0 + bl) * bss + (long long)(8 * cg) * kDbD + lane;
+        if (good && *((volatile int *)s_ok) && k < N && 32 * q4 < ncol) {
+            float *colb = band + (b0 + bl) * bss + (long long)(16 * ch) * kDbD + lane;
 #pragma unroll
             for (int dl = 0; dl < NB; ++dl) {
                 int i = k + dl - R;
@@ -246,12 +272,13 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 else if (i < 0 || i >= N) continue;
                 float *dst = colb + (long long)i * brs + (long long)(2 * R - dl) * bos;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) dst[c * kDbD] = acc[dl][c];
+                for (int c = 0; c < 16; ++c) dst[c * kDbD] = acc[dl][c];
             }
         }
-    } else if (tid == 0 && flag) {
-        atomicOr(flag, 8u);
     }
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0 && !*s_ok && flag) atomicOr(flag, 8u);
     tc::fence_after();
     if (warp == 0) tc::tmem_free(tmem, 64);
 }
@@ -261,7 +288,7 @@ static cudaError_t launch_dband_nb(int N, int periodic, int P, const float *taps
                                    const float *Y, float *band, long long bss, long long brs, long long bos,
                                    long long b0, int nb, unsigned *flag, cudaStream_t st) {
     constexpr int R = (NB - 1) / 2;
-    const size_t smem = kDbFixed + (size_t)(N + 3 + 2 * R) * kDbD * 4 + 64;
+    const size_t smem = kDbFixed + (size_t)(N + 3 + 2 * R) * kDbD * 4 + kDbTail;
     if (smem > 225 * 1024) return cudaErrorNotSupported;
     cudaError_t err = cudaFuncSetAttribute(k_dband_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -274,11 +301,30 @@ static cudaError_t launch_dband_nb(int N, int periodic, int P, const float *taps
 
 int g_fused_links = 1;
 
+// The register split of k_dband_tc (setmaxnreg) assumes the launch allocation of
+// kDbThreads x 168 registers; a build that allocates another count is never launched
+// (the chain ends then run as two kernels).
+template <int NB>
+static bool dband_regs_ok() {
+    static int regs = -1;
+    if (regs < 0) {
+        cudaFuncAttributes fa;
+        regs = cudaFuncGetAttributes(&fa, k_dband_tc<NB>) == cudaSuccess ? fa.numRegs : 0;
+        cudaGetLastError();
+    }
+    return regs * kDbThreads == 128 * kDbStageRegs + 256 * kDbBandRegs;
+}
+
 bool dband_tc_ok(int d, int N, int periodic, int P, int nsrc, int R) {
     if (d != kDbD || nsrc != kDbD || P != N * kDbD || N < 1) return false;
     if (periodic && N < 2 * R + 1) return false;
-    if (R != 2 && R != 3 && R != 4) return false;
-    return kDbFixed + (size_t)(N + 3 + 2 * R) * kDbD * 4 + 64 <= 225 * 1024;   // mbarriers and slots: 40 B
+    if (kDbFixed + (size_t)(N + 3 + 2 * R) * kDbD * 4 + kDbTail > 225 * 1024) return false;
+    switch (R) {
+        case 2: return dband_regs_ok<5>();
+        case 3: return dband_regs_ok<7>();
+        case 4: return dband_regs_ok<9>();
+        default: return false;
+    }
 }
 
 cudaError_t launch_dband_tc(int d, int N, int periodic, int P, int nsrc, int R, const float *taps, const float *Dm,
