@@ -11,9 +11,9 @@
 //
 // One CTA per (configuration, tile of 128 source columns = 4 source sites), looping
 // over all N sites n, with specialised warps connected by mbarriers:
-//   - warpgroup 0 (warps 0-3) stages operands: Y[:, n, tile] (32 x 128 floats) and D0_n
-//     (32 x 32) arrive in a five-stage ring by bulk asynchronous copies (one thread
-//     issues them as stages free up); every value is split into three BF16 planes
+//   - warpgroup 0 (warps 0-3) stages operands: Y[:, n, tile] (32 x 128 floats, one TMA
+//     tensor copy) and D0_n (32 x 32, one bulk copy) arrive in a five-stage ring (one
+//     thread issues them as stages free up); every value is split into three BF16 planes
 //     (v = p0 + p1 + p2 + rest) in one of two operand buffers, and one thread issues the
 //     six plane products with pa + pb <= 2 (M = 128 columns, N = 32 output channels,
 //     K = 32 input channels, FP32 accumulation into one of two tensor-memory buffers):
@@ -62,6 +62,13 @@ __device__ __forceinline__ void arrive_tx(uint64_t *bar, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void tma_slice(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(tc::smem_u32(bar))
+        : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      tc::smem_u32(dst)),
@@ -75,7 +82,7 @@ template <int NB>
 __global__ void __launch_bounds__(kDbThreads, 1)
     k_dband_tc(int N, int periodic, int P, const float *__restrict__ taps, const float *__restrict__ Dm,
                long long dm_ss, const float *__restrict__ Y, float *__restrict__ band, long long bss, long long brs,
-               long long bos, long long b0, unsigned *__restrict__ flag) {
+               long long bos, long long b0, unsigned *__restrict__ flag, const __grid_constant__ CUtensorMap ymap) {
     constexpr int R = (NB - 1) / 2;
     extern __shared__ __align__(1024) unsigned char smb[];
     unsigned char *Abuf = smb;                                   // [2][3 planes][2 slabs]
@@ -98,8 +105,6 @@ __global__ void __launch_bounds__(kDbThreads, 1)
     const long long bl = blk / tiles;
     const int k0 = p0 / kDbD;
     const int ncol = P - p0 < kDbCols ? P - p0 : kDbCols;           // a multiple of 32
-    const uint32_t rowbytes = (uint32_t)ncol * 4, sitebytes = kDbD * rowbytes + kDbDBytes;
-    const float *Yb = Y + bl * (long long)kDbD * N * P + p0;     // [a][n][p] of this configuration, tile start
     const float *Db = Dm + bl * dm_ss;                           // [n][c][a]
 
     // tap_s[j][c] = g_{r,c}, r = k0 - R - (N - 1) + j (circulant index on a ring, zero outside (-N, N)
@@ -140,9 +145,8 @@ __global__ void __launch_bounds__(kDbThreads, 1)
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kDbStageRegs));
         auto load = [&](int n, int st) {   // one thread: site n's inputs into ring stage st
             unsigned char *dst = ring + st * kDbStage;
-            arrive_tx(&full[st], sitebytes);
-            for (int a = 0; a < kDbD; ++a)
-                bulk_g2s(dst + a * (kDbCols * 4), Yb + ((long long)a * N + n) * P, rowbytes, &full[st]);
+            arrive_tx(&full[st], kDbStage);   // the whole box counts, zero-filled past P
+            tma_slice(dst, &ymap, p0, n, (int)bl * kDbD, &full[st]);
             bulk_g2s(dst + kDbUBytes, Db + (long long)n * (kDbD * kDbD), kDbDBytes, &full[st]);
         };
         int issued = 0;                    // sites whose copies thread 0 has issued
@@ -293,9 +297,11 @@ static cudaError_t launch_dband_nb(int N, int periodic, int P, const float *taps
     cudaError_t err = cudaFuncSetAttribute(k_dband_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     const long long blocks = (long long)nb * ((P + kDbCols - 1) / kDbCols);
+    alignas(64) CUtensorMap ymap;
+    if (!dband_input_map(&ymap, Y, N, P, (long long)nb * kDbD)) return cudaErrorNotSupported;
     ProfScope _ps("k_dband", st);
     k_dband_tc<NB><<<(unsigned)blocks, kDbThreads, smem, st>>>(N, periodic, P, taps, Dm, dm_ss, Y, band, bss, brs,
-                                                                bos, b0, flag);
+                                                                bos, b0, flag, ymap);
     return cudaGetLastError();
 }
 

@@ -296,6 +296,8 @@ cudaError_t launch_s4_grad(const dn_model *m, int blk, int N, int B, const T *dg
 // X [n][K] float row-major; partial buffer of gram_tc_partial_elems() floats.
 size_t gram_tc_partial_elems(int n, long long K, int *nsplit);
 bool link_rows_map(CUtensorMap *tm, const float *base, unsigned long long rows, int d, int box_rows);
+// Tensor map of a hop output Y [zs][N][P] (float) in boxes of 128 columns x 1 site x 32 z (tc_gemm.cu).
+bool dband_input_map(CUtensorMap *tm, const float *Y, int N, int P, long long zs);
 cudaError_t launch_gram_tc(const float *X, int n, long long K, const float *m, double scale, double *S, float *part,
                            int nsplit, unsigned *flag, cudaStream_t st);
 

@@ -1009,6 +1009,14 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
                                               reinterpret_cast<const float *>(Dm + (long long)(L - 2) * N * dd), dm_ss,
                                               reinterpret_cast<const float *>(U), reinterpret_cast<float *>(dst), bd.ss,
                                               bd.rs, bd.os, b0, nb, c->flag, st);
+                        if (err == cudaErrorNotSupported) {
+                            // the two-kernel end of the chain: vertex hop of layer L - 1, then the band
+                            cudaGetLastError();
+                            err = launch_dhop<T>(g, (int)Pm, Dm + (long long)(L - 2) * N * dd, dm_ss, U, F, nb, st,
+                                                 dplanes, c->flag);
+                            if (err == cudaSuccess)
+                                err = launch_bandconv<T>(g, taps_n, (int)Pm, F, nullptr, dst, bd, b0, nb, st);
+                        }
                         if (err != cudaSuccess) return err;
                     }
                 } else {

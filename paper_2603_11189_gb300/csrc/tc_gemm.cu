@@ -921,6 +921,19 @@ static bool hop_output_map(CUtensorMap *tm, float *Y, int N, int P, long long zs
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of a hop output Y [z][N][P] (float, z = configuration x channel) for the fused
+// chain end: boxes of 128 columns x 1 site x 32 channels, no swizzle, zero fill past P.
+bool dband_input_map(CUtensorMap *tm, const float *Y, int N, int P, long long zs) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || P % 4 != 0 || zs < 1 || (reinterpret_cast<uintptr_t>(Y) & 15) != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)N, (cuuint64_t)zs};
+    const cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)P * N * 4};
+    const cuuint32_t box[3] = {128, 1, 32}, estr[3] = {1, 1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(Y), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tensor map of a cache's link array viewed as rows of d floats (d = 32 or 64): boxes of
 // 32 columns x box_rows rows with the 128B swizzle.  Row indices must fit in int.
 bool link_rows_map(CUtensorMap *tm, const float *base, unsigned long long rows, int d, int box_rows) {
