@@ -11,13 +11,14 @@
 //
 // One CTA per (configuration, tile of 128 source columns = 4 source sites), looping
 // over all N sites n, with specialised warps connected by mbarriers:
-//   - warpgroup 0 (warps 0-3) stages operands: Y[:, n, tile] (32 x 128 floats, one TMA
-//     tensor copy) and D0_n (32 x 32, one bulk copy) arrive in a five-stage ring (one
-//     thread issues them as stages free up); every value is split into three BF16 planes
-//     (v = p0 + p1 + p2 + rest) in one of two operand buffers, and one thread issues the
-//     six plane products with pa + pb <= 2 (M = 128 columns, N = 32 output channels,
-//     K = 32 input channels, FP32 accumulation into one of two tensor-memory buffers):
-//     the same products and order as the separate vertex-hop kernel;
+//   - warpgroup 3: one thread brings Y[:, n, tile] (32 x 128 floats, one TMA tensor copy)
+//     and D0_n (32 x 32, one bulk copy) into a four-stage ring as stages free up; another
+//     issues, per site, the six BF16 plane products with pa + pb <= 2 (M = 128 columns,
+//     N = 32 output channels, K = 32 input channels, FP32 accumulation into one of three
+//     tensor-memory buffers): the same products and order as the separate vertex-hop
+//     kernel;
+//   - warpgroup 0 splits every value into three BF16 planes (v = p0 + p1 + p2 + rest) in
+//     one of three operand buffers;
 //   - warpgroups 1-2 (warps 4-11) only add each site into the band sums: warp w owns
 //     TMEM lanes 32 (w & 3) .. + 31 (one source site, lane = source channel c') and
 //     output channels 16 ((w - 4) >> 2) .. + 15, with the 2R+1 band offsets in registers
@@ -25,8 +26,8 @@
 //     accumulator buffer as soon as they have read it.  The band sums are formed in the
 //     same order (site n ascending, fmaf(tap, z, acc)) as the separate band kernel, so
 //     the fused result equals the two-kernel one.
-//   Registers move from the staging warpgroup to the band warpgroups (setmaxnreg):
-//   384 threads x 168 at launch = 128 x 72 + 256 x 216.
+//   Registers move from the staging and control warpgroups to the band warpgroups
+//   (setmaxnreg): 512 threads x 128 at launch = 128 x 72 + 256 x 200 + 128 x 40.
 // Every mbarrier wait is bounded; a wait that gives up raises bit 8 of the cache flag,
 // every role stops, the copies already issued are waited for (bounded), the tensor
 // memory is freed and nothing is written.
@@ -39,9 +40,10 @@ namespace {
 
 constexpr int kDbD = 32;                             // channels
 constexpr int kDbCols = 128;                         // source columns per CTA
-constexpr int kDbStages = 5;                         // depth of the input ring
-constexpr int kDbThreads = 384;                      // warpgroup 0: staging; 1-2: band sums
-constexpr int kDbStageRegs = 72, kDbBandRegs = 216;  // 128 x 72 + 256 x 216 = 384 x 168
+constexpr int kDbStages = 4;                         // depth of the input ring
+constexpr int kDbBufs = 3;                           // operand buffers and accumulators in flight
+constexpr int kDbThreads = 512;                      // warpgroups: 0 staging, 1-2 band sums, 3 loads + MMAs
+constexpr int kDbStageRegs = 72, kDbBandRegs = 200, kDbCtlRegs = 40;   // x 128, 256, 128 threads = 512 x 128
 constexpr uint32_t kDbUBytes = kDbD * kDbCols * 4;   // Y[:, n, tile]: 16 KB
 constexpr uint32_t kDbDBytes = kDbD * kDbD * 4;      // D0_n: 4 KB
 constexpr uint32_t kDbStage = kDbUBytes + kDbDBytes;
@@ -51,8 +53,8 @@ constexpr uint32_t kDbBSlab = kDbD * 32;
 constexpr uint32_t kDbBPlane = 2 * kDbBSlab;
 constexpr uint32_t kDbABuf = 3 * kDbAPlane;          // three planes
 constexpr uint32_t kDbBBuf = 3 * kDbBPlane;
-constexpr uint32_t kDbFixed = 2 * kDbABuf + 2 * kDbBBuf + kDbStages * kDbStage;
-constexpr uint32_t kDbTail = (2 * kDbStages + 6) * 8 + 16;   // mbarriers, TMEM slot, status
+constexpr uint32_t kDbFixed = kDbBufs * (kDbABuf + kDbBBuf) + kDbStages * kDbStage;
+constexpr uint32_t kDbTail = (2 * kDbStages + 3 * kDbBufs) * 8 + 16;   // mbarriers, TMEM slot, status
 
 __device__ __forceinline__ void arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
@@ -85,17 +87,17 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                long long bos, long long b0, unsigned *__restrict__ flag, const __grid_constant__ CUtensorMap ymap) {
     constexpr int R = (NB - 1) / 2;
     extern __shared__ __align__(1024) unsigned char smb[];
-    unsigned char *Abuf = smb;                                   // [2][3 planes][2 slabs]
-    unsigned char *Bbuf = Abuf + 2 * kDbABuf;                    // [2][3 planes][2 slabs]
-    unsigned char *ring = Bbuf + 2 * kDbBBuf;                    // [stages][Y slice | D0_n]
+    unsigned char *Abuf = smb;                                   // [bufs][3 planes][2 slabs]
+    unsigned char *Bbuf = Abuf + kDbBufs * kDbABuf;              // [bufs][3 planes][2 slabs]
+    unsigned char *ring = Bbuf + kDbBufs * kDbBBuf;              // [stages][Y slice | D0_n]
     float *tap_s = reinterpret_cast<float *>(ring + kDbStages * kDbStage);   // [N + 3 + 2R][32]
     const int ntap = N + 3 + 2 * R;
     uint64_t *full = reinterpret_cast<uint64_t *>(tap_s + (size_t)ntap * kDbD);   // [S] stage loaded
     uint64_t *empty = full + kDbStages;                                            // [S] stage read
-    uint64_t *staged = empty + kDbStages;                                          // [2] planes of site n
-    uint64_t *mmad = staged + 2;                                                   // [2] MMAs of site n done
-    uint64_t *zfree = mmad + 2;                                                    // [2] accumulator read
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(zfree + 2);
+    uint64_t *staged = empty + kDbStages;                                          // [bufs] planes of a site
+    uint64_t *mmad = staged + kDbBufs;                                             // [bufs] its MMAs done
+    uint64_t *zfree = mmad + kDbBufs;                                              // [bufs] accumulator read
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(zfree + kDbBufs);
     int *s_ok = reinterpret_cast<int *>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
             tc::mbar_init(&full[st], 1);
             tc::mbar_init(&empty[st], 4);
         }
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < kDbBufs; ++j) {
             tc::mbar_init(&staged[j], 4);
             tc::mbar_init(&mmad[j], 1);
             tc::mbar_init(&zfree[j], 8);
@@ -134,30 +136,21 @@ __global__ void __launch_bounds__(kDbThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;");
         *s_ok = 1;
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 64);
+    if (warp == 0) tc::tmem_alloc(tslot, 128);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *tslot;
+    auto alive = [&]() { return *((volatile int *)s_ok) != 0; };
 
     if (warp < 4) {
-        // ------------------------------------------------ warpgroup 0: loads, planes, MMAs --
+        // --------------------------------------------------------- warpgroup 0: planes --
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kDbStageRegs));
-        auto load = [&](int n, int st) {   // one thread: site n's inputs into ring stage st
-            unsigned char *dst = ring + st * kDbStage;
-            arrive_tx(&full[st], kDbStage);   // the whole box counts, zero-filled past P
-            tma_slice(dst, &ymap, p0, n, (int)bl * kDbD, &full[st]);
-            bulk_g2s(dst + kDbUBytes, Db + (long long)n * (kDbD * kDbD), kDbDBytes, &full[st]);
-        };
-        int issued = 0;                    // sites whose copies thread 0 has issued
-        if (tid == 0)
-            for (; issued < kDbStages && issued < N; ++issued) load(issued, issued);
-        const uint32_t idesc = tc::idesc_bf16(128, kDbD);
         for (int n = 0; n < N; ++n) {
-            const int st = n % kDbStages, j = n & 1;
-            bool ok = *((volatile int *)s_ok) != 0;
-            // the planes of buffer j were read by the MMAs of site n - 2; the stage holds site n
-            if (ok && n >= 2) ok = tc::wait(&mmad[j], (uint32_t)(((n - 2) >> 1) & 1));
+            const int st = n % kDbStages, j = n % kDbBufs;
+            bool ok = alive();
+            // buffer j was read by the MMAs of site n - bufs; the stage holds site n
+            if (ok && n >= kDbBufs) ok = tc::wait(&mmad[j], (uint32_t)((n / kDbBufs - 1) & 1));
             if (ok) ok = tc::wait(&full[st], (uint32_t)((n / kDbStages) & 1));
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
@@ -167,17 +160,17 @@ __global__ void __launch_bounds__(kDbThreads, 1)
             const unsigned char *src = ring + st * kDbStage;
             unsigned char *A = Abuf + j * kDbABuf;
             unsigned char *Bp = Bbuf + j * kDbBBuf;
+            // A operand: row = column p = tid of the tile, K = input channel a (all 32).
+            const float *us = reinterpret_cast<const float *>(src) + tid;
+#pragma unroll
+            for (int a8 = 0; a8 < kDbD; a8 += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = us[(a8 + u) * kDbCols];
+                tc::stage8_planes<3>(A, kDbAPlane, (uint32_t)(a8 >> 4) * kDbASlab + tc::canon(tid, a8 & 15), v);
+            }
+            // B operand: row = output channel c, K = input channel a.
             {
-                // A operand: row = column p = tid of the tile, K = input channel a (all 32).
-                const float *us = reinterpret_cast<const float *>(src) + tid;
-#pragma unroll
-                for (int a8 = 0; a8 < kDbD; a8 += 8) {
-                    float v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = us[(a8 + u) * kDbCols];
-                    tc::stage8_planes<3>(A, kDbAPlane, (uint32_t)(a8 >> 4) * kDbASlab + tc::canon(tid, a8 & 15), v);
-                }
-                // B operand: row = output channel c, K = input channel a.
                 const int c = tid >> 2, k8 = (tid & 3) * 8;
                 const float *ds = reinterpret_cast<const float *>(src + kDbUBytes) + c * kDbD + k8;
                 float v[8];
@@ -191,39 +184,8 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 arrive(&staged[j]);
                 arrive(&empty[st]);
             }
-            if (tid == 0 && issued < N) {
-                // refill this stage with site n + S once all four warps have read it
-                if (tc::wait(&empty[st], (uint32_t)((n / kDbStages) & 1))) load(issued++, st);
-                else *s_ok = 0;
-            }
-            if (tid == 96) {
-                bool go = tc::wait(&staged[j], (uint32_t)((n >> 1) & 1));
-                if (go && n >= 2) go = tc::wait(&zfree[j], (uint32_t)(((n - 2) >> 1) & 1));
-                if (go) {
-                    tc::fence_after();
-#pragma unroll 1
-                    for (int s = 0; s < 2; ++s)
-#pragma unroll
-                        for (int pa = 0; pa < 3; ++pa)
-#pragma unroll
-                            for (int pb = 0; pa + pb < 3; ++pb)
-                                tc::mma_bf16(tmem + (uint32_t)(j * kDbD),
-                                             tc::desc(tc::smem_u32(A + pa * kDbAPlane + s * kDbASlab)),
-                                             tc::desc(tc::smem_u32(Bp + pb * kDbBPlane + s * kDbBSlab)), idesc,
-                                             (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
-                    tc::commit(&mmad[j]);
-                } else {
-                    *s_ok = 0;
-                }
-            }
-            __syncwarp();
         }
-        if (tid == 0) {
-            // copies still in flight (only after a failure) land before the CTA exits
-            for (int n = issued - kDbStages > 0 ? issued - kDbStages : 0; n < issued; ++n)
-                (void)tc::wait(&full[n % kDbStages], (uint32_t)((n / kDbStages) & 1));
-        }
-    } else {
+    } else if (warp < 12) {
         // ---------------------------------------------------- warpgroups 1-2: band sums --
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kDbBandRegs));
         const int q4 = warp & 3, ch = (warp - 4) >> 2;
@@ -235,9 +197,9 @@ __global__ void __launch_bounds__(kDbThreads, 1)
             for (int c = 0; c < 16; ++c) acc[dl][c] = 0.f;
         bool good = true;
         for (int m = 0; m < N; ++m) {
-            const int j = m & 1;
-            bool ok = *((volatile int *)s_ok) != 0;
-            if (ok) ok = tc::wait(&mmad[j], (uint32_t)((m >> 1) & 1));
+            const int j = m % kDbBufs;
+            bool ok = alive();
+            if (ok) ok = tc::wait(&mmad[j], (uint32_t)((m / kDbBufs) & 1));
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) *s_ok = 0;
@@ -267,7 +229,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
             }
         }
         const int k = k0 + q4;
-        if (good && *((volatile int *)s_ok) && k < N && 32 * q4 < ncol) {
+        if (good && alive() && k < N && 32 * q4 < ncol) {
             float *colb = band + (b0 + bl) * bss + (long long)(16 * ch) * kDbD + lane;
 #pragma unroll
             for (int dl = 0; dl < NB; ++dl) {
@@ -279,12 +241,61 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 for (int c = 0; c < 16; ++c) dst[c * kDbD] = acc[dl][c];
             }
         }
+    } else {
+        // ------------------------------------------------ warpgroup 3: loads and MMAs --
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kDbCtlRegs));
+        if (warp == 12 && lane == 0) {
+            // loader: site n into stage n % S once the staging warps have read site n - S
+            int n = 0;
+            for (; n < N; ++n) {
+                const int st = n % kDbStages;
+                if (!alive()) break;
+                if (n >= kDbStages && !tc::wait(&empty[st], (uint32_t)((n / kDbStages - 1) & 1))) {
+                    *s_ok = 0;
+                    break;
+                }
+                unsigned char *dst = ring + st * kDbStage;
+                arrive_tx(&full[st], kDbStage);   // the whole box counts, zero-filled past P
+                tma_slice(dst, &ymap, p0, n, (int)bl * kDbD, &full[st]);
+                bulk_g2s(dst + kDbUBytes, Db + (long long)n * (kDbD * kDbD), kDbDBytes, &full[st]);
+            }
+            // copies still in flight (only after a failure) land before the CTA exits
+            for (int q = n - kDbStages > 0 ? n - kDbStages : 0; q < n; ++q)
+                (void)tc::wait(&full[q % kDbStages], (uint32_t)((q / kDbStages) & 1));
+        } else if (warp == 13 && lane == 0) {
+            // MMA issue: site n's planes into accumulator n % bufs once it has been read
+            const uint32_t idesc = tc::idesc_bf16(128, kDbD);
+            for (int n = 0; n < N; ++n) {
+                const int j = n % kDbBufs;
+                bool go = alive() && tc::wait(&staged[j], (uint32_t)((n / kDbBufs) & 1));
+                if (go && n >= kDbBufs) go = tc::wait(&zfree[j], (uint32_t)((n / kDbBufs - 1) & 1));
+                if (!go) {
+                    *s_ok = 0;
+                    break;
+                }
+                tc::fence_after();
+                const unsigned char *A = Abuf + j * kDbABuf;
+                const unsigned char *Bp = Bbuf + j * kDbBBuf;
+#pragma unroll 1
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int pa = 0; pa < 3; ++pa)
+#pragma unroll
+                        for (int pb = 0; pa + pb < 3; ++pb)
+                            tc::mma_bf16(tmem + (uint32_t)(j * kDbD),
+                                         tc::desc(tc::smem_u32(A + pa * kDbAPlane + s * kDbASlab)),
+                                         tc::desc(tc::smem_u32(Bp + pb * kDbBPlane + s * kDbBSlab)), idesc,
+                                         (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+                tc::commit(&mmad[j]);
+            }
+        }
+        __syncwarp();
     }
     tc::fence_before();
     __syncthreads();
     if (tid == 0 && !*s_ok && flag) atomicOr(flag, 8u);
     tc::fence_after();
-    if (warp == 0) tc::tmem_free(tmem, 64);
+    if (warp == 0) tc::tmem_free(tmem, 128);
 }
 
 template <int NB>
@@ -318,7 +329,7 @@ static bool dband_regs_ok() {
         regs = cudaFuncGetAttributes(&fa, k_dband_tc<NB>) == cudaSuccess ? fa.numRegs : 0;
         cudaGetLastError();
     }
-    return regs * kDbThreads == 128 * kDbStageRegs + 256 * kDbBandRegs;
+    return regs * kDbThreads == 128 * kDbStageRegs + 256 * kDbBandRegs + 128 * kDbCtlRegs;
 }
 
 bool dband_tc_ok(int d, int N, int periodic, int P, int nsrc, int R) {
