@@ -17,13 +17,17 @@
 //     N = 32 output channels, K = 32 input channels, FP32 accumulation into one of three
 //     tensor-memory buffers): the same products and order as the separate vertex-hop
 //     kernel;
-//   - warpgroup 0 splits every value into three BF16 planes (v = p0 + p1 + p2 + rest) in
-//     one of three operand buffers;
+//   - warpgroup 0 splits every value into three BF16 planes (v = p0 + p1 + p2 + rest): the
+//     A operand (the hop output slice, row = column p) into one of three tensor-memory
+//     buffers, the B operand (D0_n) into one of three shared-memory buffers; the MMAs read
+//     A from tensor memory, which keeps the six plane products' operand reads off the
+//     shared-memory port;
 //   - warpgroups 1-2 (warps 4-11) only add each site into the band sums: warp w owns
 //     TMEM lanes 32 (w & 3) .. + 31 (one source site, lane = source channel c') and
 //     output channels 16 ((w - 4) >> 2) .. + 15, with the 2R+1 band offsets in registers
-//     (taps from a shared table, already wrapped for rings); they release each
-//     accumulator buffer as soon as they have read it.  The band sums are formed in the
+//     (taps from a shared table, already wrapped for rings), two sites per step so that
+//     each tap row is loaded once for both; they release each accumulator buffer as soon
+//     as they have read it.  The band sums are formed in the
 //     same order (site n ascending, fmaf(tap, z, acc)) as the separate band kernel, so
 //     the fused result equals the two-kernel one.
 //   Registers move from the staging and control warpgroups to the band warpgroups
@@ -47,13 +51,14 @@ constexpr int kDbStageRegs = 72, kDbBandRegs = 200, kDbCtlRegs = 40;   // x 128,
 constexpr uint32_t kDbUBytes = kDbD * kDbCols * 4;   // Y[:, n, tile]: 16 KB
 constexpr uint32_t kDbDBytes = kDbD * kDbD * 4;      // D0_n: 4 KB
 constexpr uint32_t kDbStage = kDbUBytes + kDbDBytes;
-constexpr uint32_t kDbASlab = kDbCols * 32;          // one 16-wide K slab of 128 BF16 rows
-constexpr uint32_t kDbAPlane = 2 * kDbASlab;         // K = 32
 constexpr uint32_t kDbBSlab = kDbD * 32;
 constexpr uint32_t kDbBPlane = 2 * kDbBSlab;
-constexpr uint32_t kDbABuf = 3 * kDbAPlane;          // three planes
 constexpr uint32_t kDbBBuf = 3 * kDbBPlane;
-constexpr uint32_t kDbFixed = kDbBufs * (kDbABuf + kDbBBuf) + kDbStages * kDbStage;
+constexpr uint32_t kDbFixed = kDbBufs * kDbBBuf + kDbStages * kDbStage;
+// Tensor-memory columns: A operands (3 planes x K = 32 BF16, two per column) and accumulators.
+constexpr uint32_t kDbACols = 3 * 16;
+constexpr uint32_t kDbZCol0 = kDbBufs * kDbACols;                  // accumulators after the A operands
+constexpr uint32_t kDbTmemCols = 256;                               // >= kDbZCol0 + kDbBufs * 32
 constexpr uint32_t kDbTail = (2 * kDbStages + 3 * kDbBufs) * 8 + 16;   // mbarriers, TMEM slot, status
 
 __device__ __forceinline__ void arrive(uint64_t *bar) {
@@ -64,6 +69,19 @@ __device__ __forceinline__ void arrive_tx(uint64_t *bar, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
+// Eight 32-bit columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+// MMA with the A operand in tensor memory (BF16, row i in lane i, two K values per column).
+__device__ __forceinline__ void mma_bf16_ta(uint32_t dt, uint32_t at, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dt),
+                 "r"(at), "l"(b), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void tma_slice(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
@@ -87,14 +105,13 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                long long bos, long long b0, unsigned *__restrict__ flag, const __grid_constant__ CUtensorMap ymap) {
     constexpr int R = (NB - 1) / 2;
     extern __shared__ __align__(1024) unsigned char smb[];
-    unsigned char *Abuf = smb;                                   // [bufs][3 planes][2 slabs]
-    unsigned char *Bbuf = Abuf + kDbBufs * kDbABuf;              // [bufs][3 planes][2 slabs]
-    unsigned char *ring = Bbuf + kDbBufs * kDbBBuf;              // [stages][Y slice | D0_n]
-    float *tap_s = reinterpret_cast<float *>(ring + kDbStages * kDbStage);   // [N + 3 + 2R][32]
+    unsigned char *ring = smb;                                   // [stages][Y slice | D0_n]
+    unsigned char *Bbuf = ring + kDbStages * kDbStage;           // [bufs][3 planes][2 slabs]
+    float *tap_s = reinterpret_cast<float *>(Bbuf + kDbBufs * kDbBBuf);   // [N + 3 + 2R][32]
     const int ntap = N + 3 + 2 * R;
     uint64_t *full = reinterpret_cast<uint64_t *>(tap_s + (size_t)ntap * kDbD);   // [S] stage loaded
     uint64_t *empty = full + kDbStages;                                            // [S] stage read
-    uint64_t *staged = empty + kDbStages;                                          // [bufs] planes of a site
+    uint64_t *staged = empty + kDbStages;                                          // [bufs] operands of a site
     uint64_t *mmad = staged + kDbBufs;                                             // [bufs] its MMAs done
     uint64_t *zfree = mmad + kDbBufs;                                              // [bufs] accumulator read
     uint32_t *tslot = reinterpret_cast<uint32_t *>(zfree + kDbBufs);
@@ -136,7 +153,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;");
         *s_ok = 1;
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 128);
+    if (warp == 0) tc::tmem_alloc(tslot, kDbTmemCols);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -144,8 +161,9 @@ __global__ void __launch_bounds__(kDbThreads, 1)
     auto alive = [&]() { return *((volatile int *)s_ok) != 0; };
 
     if (warp < 4) {
-        // --------------------------------------------------------- warpgroup 0: planes --
+        // ---------------------------------------------------- warpgroup 0: operand planes --
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kDbStageRegs));
+        const uint32_t trow = (uint32_t)(32 * warp) << 16;            // this thread's lane = row p = tid
         for (int n = 0; n < N; ++n) {
             const int st = n % kDbStages, j = n % kDbBufs;
             bool ok = alive();
@@ -157,20 +175,35 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 if (lane == 0) *s_ok = 0;
                 break;
             }
+            tc::fence_after();
             const unsigned char *src = ring + st * kDbStage;
-            unsigned char *A = Abuf + j * kDbABuf;
-            unsigned char *Bp = Bbuf + j * kDbBBuf;
-            // A operand: row = column p = tid of the tile, K = input channel a (all 32).
+            // A operand (tensor memory): row p = tid of the tile, K = input channel a; each
+            // 16-wide K slab as three BF16 planes of 8 columns (element 2c in the low half).
             const float *us = reinterpret_cast<const float *>(src) + tid;
+            const uint32_t abase = tmem + trow + (uint32_t)(j * kDbACols);
 #pragma unroll
-            for (int a8 = 0; a8 < kDbD; a8 += 8) {
-                float v[8];
+            for (int a16 = 0; a16 < kDbD; a16 += 16) {
+                float r[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = us[(a8 + u) * kDbCols];
-                tc::stage8_planes<3>(A, kDbAPlane, (uint32_t)(a8 >> 4) * kDbASlab + tc::canon(tid, a8 & 15), v);
+                for (int u = 0; u < 16; ++u) r[u] = us[(a16 + u) * kDbCols];
+#pragma unroll
+                for (int pl = 0; pl < 3; ++pl) {
+                    uint32_t w[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
+                        w[i] = *reinterpret_cast<const uint32_t *>(&h);
+                        if (pl < 2) {
+                            r[2 * i] -= __low2float(h);
+                            r[2 * i + 1] -= __high2float(h);
+                        }
+                    }
+                    tmem_st8(abase + (uint32_t)(pl * 16 + (a16 >> 1)), w);
+                }
             }
-            // B operand: row = output channel c, K = input channel a.
+            // B operand (shared memory): row = output channel c, K = input channel a.
             {
+                unsigned char *Bp = Bbuf + j * kDbBBuf;
                 const int c = tid >> 2, k8 = (tid & 3) * 8;
                 const float *ds = reinterpret_cast<const float *>(src + kDbUBytes) + c * kDbD + k8;
                 float v[8];
@@ -178,7 +211,9 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 for (int u = 0; u < 8; ++u) v[u] = ds[u];
                 tc::stage8_planes<3>(Bp, kDbBPlane, (uint32_t)(k8 >> 4) * kDbBSlab + tc::canon(c, k8 & 15), v);
             }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc::fence_async_smem();
+            tc::fence_before();
             __syncwarp();
             if (lane == 0) {
                 arrive(&staged[j]);
@@ -196,10 +231,15 @@ __global__ void __launch_bounds__(kDbThreads, 1)
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[dl][c] = 0.f;
         bool good = true;
-        for (int m = 0; m < N; ++m) {
-            const int j = m % kDbBufs;
+        // Sites in pairs (m, m + 1): their tap rows overlap (row q4 + N - 1 - m + dl for site m,
+        // one lower for site m + 1), so each row is loaded once for both.  Rows go in descending
+        // order, so every accumulator still receives site m before site m + 1.
+        for (int m = 0; m < N; m += 2) {
+            const bool two = m + 1 < N;
+            const int j0 = m % kDbBufs, j1 = (m + 1) % kDbBufs;
             bool ok = alive();
-            if (ok) ok = tc::wait(&mmad[j], (uint32_t)((m / kDbBufs) & 1));
+            if (ok) ok = tc::wait(&mmad[j0], (uint32_t)((m / kDbBufs) & 1));
+            if (ok && two) ok = tc::wait(&mmad[j1], (uint32_t)(((m + 1) / kDbBufs) & 1));
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) *s_ok = 0;
@@ -207,24 +247,41 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 break;
             }
             tc::fence_after();
-            float z[16];
-            const uint32_t zc = tmem + tlane + (uint32_t)(j * kDbD + 16 * ch);
-            tc::tmem_ld8(zc, z);
-            tc::tmem_ld8(zc + 8, z + 8);
+            float z0[16], z1[16];
+            const uint32_t zc0 = tmem + tlane + kDbZCol0 + (uint32_t)(j0 * kDbD + 16 * ch);
+            tc::tmem_ld8(zc0, z0);
+            tc::tmem_ld8(zc0 + 8, z0 + 8);
+            if (two) {
+                const uint32_t zc1 = tmem + tlane + kDbZCol0 + (uint32_t)(j1 * kDbD + 16 * ch);
+                tc::tmem_ld8(zc1, z1);
+                tc::tmem_ld8(zc1 + 8, z1 + 8);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) z1[c] = 0.f;
+            }
             tc::fence_before();
             __syncwarp();
-            if (lane == 0) arrive(&zfree[j]);
-            const float *trow = tap_s + (size_t)(q4 + N - 1 - m) * kDbD + 16 * ch;
+            if (lane == 0) {
+                arrive(&zfree[j0]);
+                if (two) arrive(&zfree[j1]);
+            }
+            // row t of the pair: tap_s row q4 + N - 2 - m + t; site m uses it for dl = t - 1,
+            // site m + 1 for dl = t.
+            const float *tr = tap_s + (size_t)(q4 + N - 2 - m) * kDbD + 16 * ch;
 #pragma unroll
-            for (int dl = 0; dl < NB; ++dl) {
-                const float4 *t4 = reinterpret_cast<const float4 *>(trow + dl * kDbD);
+            for (int t = NB; t >= 0; --t) {
+                if (t == 0 && !two) break;
+                const float4 *t4 = reinterpret_cast<const float4 *>(tr + t * kDbD);
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
-                    const float4 t = t4[c4];
-                    acc[dl][4 * c4 + 0] = fmaf(t.x, z[4 * c4 + 0], acc[dl][4 * c4 + 0]);
-                    acc[dl][4 * c4 + 1] = fmaf(t.y, z[4 * c4 + 1], acc[dl][4 * c4 + 1]);
-                    acc[dl][4 * c4 + 2] = fmaf(t.z, z[4 * c4 + 2], acc[dl][4 * c4 + 2]);
-                    acc[dl][4 * c4 + 3] = fmaf(t.w, z[4 * c4 + 3], acc[dl][4 * c4 + 3]);
+                    const float4 g = t4[c4];
+                    const float gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 4 * c4 + u;
+                        if (t >= 1) acc[t - 1][c] = fmaf(gv[u], z0[c], acc[t - 1][c]);
+                        if (t <= NB - 1 && two) acc[t][c] = fmaf(gv[u], z1[c], acc[t][c]);
+                    }
                 }
             }
         }
@@ -263,7 +320,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
             for (int q = n - kDbStages > 0 ? n - kDbStages : 0; q < n; ++q)
                 (void)tc::wait(&full[q % kDbStages], (uint32_t)((q / kDbStages) & 1));
         } else if (warp == 13 && lane == 0) {
-            // MMA issue: site n's planes into accumulator n % bufs once it has been read
+            // MMA issue: site n's operands into accumulator n % bufs once it has been read
             const uint32_t idesc = tc::idesc_bf16(128, kDbD);
             for (int n = 0; n < N; ++n) {
                 const int j = n % kDbBufs;
@@ -274,7 +331,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                     break;
                 }
                 tc::fence_after();
-                const unsigned char *A = Abuf + j * kDbABuf;
+                const uint32_t at = tmem + (uint32_t)(j * kDbACols);
                 const unsigned char *Bp = Bbuf + j * kDbBBuf;
 #pragma unroll 1
                 for (int s = 0; s < 2; ++s)
@@ -282,10 +339,9 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                     for (int pa = 0; pa < 3; ++pa)
 #pragma unroll
                         for (int pb = 0; pa + pb < 3; ++pb)
-                            tc::mma_bf16(tmem + (uint32_t)(j * kDbD),
-                                         tc::desc(tc::smem_u32(A + pa * kDbAPlane + s * kDbASlab)),
-                                         tc::desc(tc::smem_u32(Bp + pb * kDbBPlane + s * kDbBSlab)), idesc,
-                                         (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+                            mma_bf16_ta(tmem + kDbZCol0 + (uint32_t)(j * kDbD), at + (uint32_t)(pa * 16 + s * 8),
+                                        tc::desc(tc::smem_u32(Bp + pb * kDbBPlane + s * kDbBSlab)), idesc,
+                                        (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
                 tc::commit(&mmad[j]);
             }
         }
@@ -295,7 +351,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
     __syncthreads();
     if (tid == 0 && !*s_ok && flag) atomicOr(flag, 8u);
     tc::fence_after();
-    if (warp == 0) tc::tmem_free(tmem, 128);
+    if (warp == 0) tc::tmem_free(tmem, kDbTmemCols);
 }
 
 template <int NB>
