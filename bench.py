@@ -163,13 +163,26 @@ def link_conv_flops(N, L, d, B):
     return total
 
 
-def dhop_bytes(N, L, d, B):
+def dhop_bytes(N, L, d, B, fused=False):
     """HBM bytes of the vertex hops of one step: every hop reads the probe field of
     one layer and writes it back mixed (d N P values each way; P = N probes for the
-    embedding chain, N d for a source chain from layer m, which makes L - 2 - m hops)."""
+    embedding chain, N d for a source chain from layer m, which makes L - 2 - m hops).
+    With the fused chain ends the last hop of every source chain with a full hop
+    (m <= L - 3) runs inside k_dband instead."""
     per = (L - 2) * 2 * d * N * N * 4
-    per += sum((L - 2 - m) * 2 * d * N * (N * d) * 4 for m in range(1, L - 1))
+    per += sum((L - 2 - m - (1 if fused and m <= L - 3 else 0)) * 2 * d * N * (N * d) * 4 for m in range(1, L - 1))
     return B * per
+
+
+def dband_bytes(N, L, d, w, B, WF=None):
+    """HBM bytes of the fused chain ends (k_dband) of one step: for every source chain
+    with a full hop (m = 1 .. L - 3) the hop output read once, the vertex matrices of
+    layer L - 1 and the band of G^(L) written."""
+    W = 2 * w + 1
+    WF = W if WF is None else WF
+    Rk = WF - 1
+    chains = max(0, L - 3)
+    return B * chains * (d * N * (N * d) * 4 + N * d * d * 4 + N * (2 * Rk + 1) * d * d * 4)
 
 
 def bandconv_gen_flops(N, L, d, w, B, WF=None):
@@ -184,17 +197,19 @@ def bandconv_gen_flops(N, L, d, w, B, WF=None):
     return B * 2 * (2 * Rk + 1) * N * (N * d) * d
 
 
-def bandconv_bytes(N, L, d, w, B, WF=None):
+def bandconv_bytes(N, L, d, w, B, WF=None, fused=False):
     """HBM bytes of the last-layer band convolutions that read their operand (k_bandconv) in
     one step: the probe field read once (the embedding chain and every source chain with
-    a full hop) plus the band entries written.  The chain from layer L-2 generates its
-    operand from D0 and the taps (k_bandconv_gen, counted in flops)."""
+    a full hop, unless its end is fused into k_dband) plus the band entries written.  The
+    chain from layer L-2 generates its operand from D0 and the taps (k_bandconv_gen,
+    counted in flops)."""
     W = 2 * w + 1
     WF = W if WF is None else WF
     Rk, Rl = WF - 1, WF - 1 - w
     per = d * N * N * 4 + N * (2 * Rl + 1) * d * 4
-    for m in range(1, L - 2):
-        per += d * N * (N * d) * 4 + N * (2 * Rk + 1) * d * d * 4
+    if not fused:
+        for m in range(1, L - 2):
+            per += d * N * (N * d) * 4 + N * (2 * Rk + 1) * d * d * 4
     return B * per
 
 
@@ -321,7 +336,7 @@ def measure_grad(dn, synth, torch, barrier, lib, B=4096, reps=2):
             "grad": {"value": B / (grad_ms / 1e3), "unit": "configurations/s (forward + all %d log-derivatives)" % P,
                      "ms": grad_ms},
             "sr_gram": {"ms": gram_ms, "tflops": gram_flop / (gram_ms / 1e3) / 1e12,
-                        "note": "Oc Oc^T / B on tcgen05, FP32 values as 3 BF16 planes (6 products), FP32 accumulation per K split of <= 16384 terms, splits summed in FP64; flops counted once per FP32 product"},
+                        "note": "Oc Oc^T / B on tcgen05, FP32 values as 3 BF16 planes (6 products), FP32 accumulation in tensor memory folded into FP32 totals every 1024 terms, K splits of <= 16384 terms summed in FP64; flops counted once per FP32 product"},
             "kernels": kern[:12]}
 
 
@@ -701,7 +716,7 @@ def read_profile(lib):
 # full-size launch's traffic is the ratio times its algorithmic units.  Valid for the
 # kernels as captured: a family whose kernel changes is reported with traffic null until
 # it is captured again.
-DRAM_PER_UNIT = {"abacus": 1.076, "links_dhop": None, "links_bandconv": 0.9919,
+DRAM_PER_UNIT = {"abacus": 1.076, "links_dhop": None, "links_bandconv": None, "links_dband": None,
                  "links_bandconv_gen": 0.0105, "links_tgemm_tc": 0.01665}
 
 
@@ -741,8 +756,11 @@ def kernel_rooflines(prof, steps, desc, N, Bs, peaks, src):
                               "frac": ach / peak, "traffic": None, "launches": launches,
                               "ms_per_launch": tot_s * 1e3 / launches,
                               "peak_source": f"FP32 FMA issue rate: 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"}
-    for fam_name, kname, byts in (("links_dhop", "k_dhop", dhop_bytes(N, desc.L, desc.d, Bs)),
-                                  ("links_bandconv", "k_bandconv", bandconv_bytes(N, desc.L, desc.d, desc.w, Bs))):
+    fused = any(k.endswith("links/k_dband") for k in prof)
+    for fam_name, kname, byts in (("links_dhop", "k_dhop", dhop_bytes(N, desc.L, desc.d, Bs, fused)),
+                                  ("links_bandconv", "k_bandconv",
+                                   bandconv_bytes(N, desc.L, desc.d, desc.w, Bs, fused=fused)),
+                                  ("links_dband", "k_dband", dband_bytes(N, desc.L, desc.d, desc.w, Bs))):
         ks = [(k, v) for k, v in prof.items() if k.endswith("links/" + kname)]
         if ks:
             launches = sum(v[0] for _, v in ks)
@@ -803,6 +821,8 @@ def roofline(prof, steps, desc, N, Bs, peaks, src, clocks):
         return fam["links_dhop"], fam
     if name.endswith("links/k_bandconv") and "links_bandconv" in fam:
         return fam["links_bandconv"], fam
+    if name.endswith("links/k_dband") and "links_dband" in fam:
+        return fam["links_dband"], fam
     if name.endswith("links/k_bandconv_gen") and "links_bandconv_gen" in fam:
         return fam["links_bandconv_gen"], fam
     if name.endswith("links/k_tgemm_tc") and "links_tgemm_tc" in fam:
