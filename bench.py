@@ -227,13 +227,13 @@ def abacus_unique_bytes(N, L, d, dout, w, P, B, tb=4):
     return B * (per_sample * tb + N) + B * N * 8
 
 
-def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128):
+def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128, L=6):
     """ABACUS ratios/s given caches, cache-build time and the GPU full-forward recompute
-    at N = 1024 for the 6-layer, 64-channel, 64-mode model (FP32, long-range TFIM
+    at N = 1024 for the L-layer, 64-channel, 64-mode model (FP32, long-range TFIM
     chains, all N single flips per chain; the recompute is timed on a sample of
     `recompute_flips` flips per chain and scaled per ratio)."""
     Nn = 1024
-    desc = synth.ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
+    desc = synth.ModelDesc(L=L, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
     params = synth.init_params(desc, 1005, a_scale=10.0)
     spins_np = synth.spins_uniform(chains, Nn, 2005)
     model = dn.Model(desc, params)
@@ -274,7 +274,8 @@ def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128):
     ab_rate = ratios / (ab_ms / 1e3)
     rc_rate = chains * recompute_flips / (rc_ms / 1e3)
     e2e_rate = ratios / ((ab_ms + build_ms) / 1e3)
-    return {"workload": "lr-TFIM N=1024 open, DysonNet L=6 d=64 s=64 w=2 FP32, %d chains x 1024 single flips" % chains,
+    return {"workload": "lr-TFIM N=1024 open, DysonNet L=%d d=64 s=64 w=2 FP32, %d chains x 1024 single flips"
+                        % (L, chains),
             "abacus_given_caches": {"value": ab_rate, "unit": "flip ratios/s", "ms": ab_ms},
             "cache_build_ms": build_ms, "cache_bytes_per_chain": cache_bytes,
             "recompute": {"value": rc_rate, "unit": "flip ratios/s", "ms": rc_ms,
@@ -443,6 +444,58 @@ def measure_bf16_forward(dn, synth, torch, barrier, lib, B=2048, reps=3):
     out["bf16_vs_fp32_max_rel"] = float(dev.max())
     model.close()
     return {"workload": "J1-J2 ring N=256, DysonNet L=6 d=64 s=64 w=2, %d configurations, full forward" % B, **out}
+
+
+def measure_bf16_j1j2(dn, synth, torch, barrier, lib, B=64):
+    """Local energies of the J1-J2 ring workload model (N = 256, L = 6, d = 64, s = 64,
+    zero-magnetisation configurations, connected configurations from antialigned NN and
+    NNN pairs) in BF16 (tensor-core forward; links, adjoint and ABACUS at FP32 accuracy)
+    and in FP32, on B configurations: pair ratios/s including the cache build, the split
+    into forward, link construction and ABACUS, the BF16 deviation from FP32, and the GPU
+    full-forward recompute of the same pairs.  The error against the FP64 oracle is
+    measured by the GPU tests (tests/test_gpu_tc_forward.py)."""
+    import numpy as np
+    cfg = synth.CONFIGS["j1j2_n256"]
+    desc, N = cfg["desc"], cfg["N"]
+    model = dn.Model(desc, synth.make_params(cfg))
+    spins_np = synth.make_spins(cfg, B)
+    spins = torch.from_numpy(spins_np).cuda()
+    pairs = [(b, i, (i + sep) % N) for b in range(B) for sep in (1, 2) for i in range(N)
+             if spins_np[b, i] != spins_np[b, (i + sep) % N]]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out, el = {}, {}
+    for prec in ("bf16", "fp32"):
+        el[prec] = torch.empty(B, dtype=torch.float64, device="cuda")
+        model.local_energy(cfg["ham"], spins, prec=prec, out=el[prec])
+        barrier()
+        ev0.record()
+        model.local_energy(cfg["ham"], spins, prec=prec, out=el[prec])
+        ev1.record()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        lib.dn_profile_enable(1)   # split from a separate traced pass
+        model.local_energy(cfg["ham"], spins, prec=prec, out=el[prec])
+        prof = read_profile(lib)
+        lib.dn_profile_enable(0)
+        part = lambda key: sum(v[1] for k, v in prof.items() if ("/" + key + "/") in ("/" + k))
+        out[prec] = {"value": len(pairs) / (ms / 1e3), "unit": "pair ratios/s (local energy incl. cache build)",
+                     "ms": ms, "forward_ms": part("forward"), "adjoint_ms": part("adjoint"),
+                     "links_ms": part("links"), "abacus_ms": part("abacus")}
+    e16, e32 = el["bf16"].cpu().numpy(), el["fp32"].cpu().numpy()
+    out["bf16_vs_fp32_eloc_max_rel"] = float(np.max(np.abs(e16 - e32) / np.maximum(1.0, np.abs(e32))))
+    sample = torch.tensor([p[0] for p in pairs], dtype=torch.int32, device="cuda")
+    sites = torch.tensor([[p[1], p[2]] for p in pairs], dtype=torch.int32, device="cuda")
+    r = model.recompute_flip_ratios(spins, sample, sites, prec="fp32")
+    barrier()
+    ev0.record()
+    model.recompute_flip_ratios(spins, sample, sites, prec="fp32", out=r)
+    ev1.record()
+    barrier()
+    rc_ms = ev0.elapsed_time(ev1)
+    out["recompute"] = {"value": len(pairs) / (rc_ms / 1e3), "unit": "pair ratios/s", "ms": rc_ms}
+    model.close()
+    return {"workload": "J1-J2 ring N=256 (J2/J1 = 0.5), DysonNet L=6 d=64 s=64 w=2, %d zero-magnetisation "
+                        "configurations, %d antialigned NN/NNN pairs" % (B, len(pairs)), **out}
 
 
 def measure_serving(dn, synth, n_req=160, rate=20.0, seed=4005):
@@ -644,11 +697,16 @@ def main():
                      "speedup_of_abacus_step": (flips_step / (ms / 1e3)) / (flips_step / (rms / 1e3))}
 
     n1024 = None if args.no_n1024 else measure_n1024(dn, synth, torch, barrier, args.n1024_chains)
+    # The same at depths whose exact links need no full N x N hop beyond the embedding chain
+    # (L = 2: the paper's own depth; L = 3: one interlayer pair, built directly).
+    n1024_shallow = None if args.no_n1024 else {
+        "L%d" % Ls: measure_n1024(dn, synth, torch, barrier, 16, L=Ls) for Ls in (3, 2)}
     serving = None if args.no_serving else measure_serving(dn, synth)
     grad = None if args.no_grad else measure_grad(dn, synth, torch, barrier, lib, B=args.grad_samples)
     sampler = None if args.no_sampler else measure_sampler(dn, synth, torch, barrier)
     bf16_forward = None if args.no_bf16_forward else measure_bf16_forward(dn, synth, torch, barrier, lib,
                                                                            B=args.bf16_samples)
+    bf16_j1j2 = None if args.no_bf16_forward else measure_bf16_j1j2(dn, synth, torch, barrier, lib)
 
     peaks, src = _peaks()
     roof, families = roofline(prof, args.steps, desc, N, Bs, peaks, src, clocks)
@@ -673,9 +731,11 @@ def main():
         "cache_build_ms_per_step": build_ms,
         "recompute": recompute,
         "n1024": n1024,
+        "n1024_shallow": n1024_shallow,
         "grad": grad,
         "sampler": sampler,
         "bf16_forward": bf16_forward,
+        "bf16_j1j2_local_energy": bf16_j1j2,
         "serving": serving,
         "kernels": [{"name": k, "launches": n // args.steps, "ms_per_step": v / args.steps,
                      "share": v / total_k} for k, n, v in kernels[:16]],
@@ -716,7 +776,7 @@ def read_profile(lib):
 # full-size launch's traffic is the ratio times its algorithmic units.  Valid for the
 # kernels as captured: a family whose kernel changes is reported with traffic null until
 # it is captured again.
-DRAM_PER_UNIT = {"abacus": 1.076, "links_dhop": None, "links_bandconv": None, "links_dband": None,
+DRAM_PER_UNIT = {"abacus": 1.076, "links_dhop": 0.908, "links_bandconv": 0.964, "links_dband": 0.994,
                  "links_bandconv_gen": 0.0105, "links_tgemm_tc": 0.01665}
 
 

@@ -929,8 +929,11 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
     T *ell = static_cast<T *>(c->ell);
     T *K = static_cast<T *>(c->K);
     const int nRl = 2 * c->Rl + 1, nRk = 2 * c->Rk + 1;
-    const int planes = c->prec == DN_BF16 ? 1 : 2;   // BF16: single-product Toeplitz hops; FP32: 3 products
-    const int dplanes = c->prec == DN_BF16 ? 1 : 3;  // vertex hops: K = d only, FP32-grade with 3 planes
+    // The link tensors are built at FP32 accuracy for FP32 and BF16 caches alike (BF16 is
+    // confined to the forward pass's convolutions and channel mixing): Toeplitz hops as
+    // hi*hi + hi*lo + lo*hi of two BF16 planes, vertex hops (K = d) with three planes.
+    const int planes = 2;
+    const int dplanes = 3;
     cudaError_t err;
     for (int b0 = 0; b0 < c->B; b0 += nb_max) {
         const int nb = (c->B - b0 < nb_max) ? c->B - b0 : nb_max;
