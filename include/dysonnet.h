@@ -56,12 +56,12 @@ typedef enum {
  *     run on the tcgen05 tensor cores as three BF16 products
  *     (hi*hi + hi*lo + lo*hi) with FP32 accumulation.
  *   DN_BF16: the S4 convolutions and the channel-mixing GEMMs of the forward pass
- *     and the Toeplitz hops of the link construction on the tensor cores with one
- *     BF16 product each (FP32 accumulation); caches, the adjoint, the vertex hops
- *     of the link construction and the ABACUS contractions stay in float.
- *     Requires d a multiple of 16, d <= 128 (else DN_EUNSUPPORTED).  Its error
- *     against the FP64 definition is larger than DN_FP32's; the tests state the
- *     bound. */
+ *     on the tensor cores in BF16 arithmetic, each operand carried as two BF16
+ *     terms (hi*hi + hi*lo + lo*hi, FP32 accumulation); the link tensors are built
+ *     as for DN_FP32; caches, the adjoint and the ABACUS contractions stay in
+ *     float.  Requires d a multiple of 16, d <= 128 (else DN_EUNSUPPORTED).  Its
+ *     error against the FP64 definition is larger than DN_FP32's; the tests state
+ *     the bound. */
 typedef enum {
     DN_FP64 = 0,
     DN_FP32 = 1,

@@ -206,12 +206,15 @@ void run_forward(dn_model *m, const dn::Plan<T> &pl, const dn::Weights<T> &w, in
     ck(dn::launch_pool0<T>(g, spins, w.e, pl.omega, B, pooled, (long long)(L + 1) * d, st));
     if constexpr (sizeof(T) == 4) {
         if (prec == DN_BF16 && dn::forward_tc_ok(g)) {
-            // BF16: tensor cores, channel-major activations h[c][n B + b] (forward_tc.cu).
+            // BF16: tensor cores, channel-major activations h[c][n B + b] (forward_tc.cu),
+            // every operand carried as two BF16 terms (hi + lo; products hi*hi + hi*lo + lo*hi,
+            // FP32 accumulation).  One BF16 term per operand gave log-amplitude-ratio errors of
+            // 1e-3 absolute (0.11 in the ratio metric) on the J1-J2 N = 256, 6 x 64 x 64 model.
             // The FP32 forward stays on the FMA kernels: tensor-core FP32 accumulation over
             // the K = N sites of the convolution, even with operands split into three BF16
             // planes, measured 1.1e-4 on log-ratios of the N = 128 workload model, above the
             // FP32 bound.
-            const int planes = 1;
+            const int planes = 2;
             ck(dn::launch_h0_cm(g, spins, w.e, B, h, st));
             for (int l = 1; l <= L; ++l) {
                 const T *taps_l = pl.taps + (long long)(l - 1) * g.R * d;

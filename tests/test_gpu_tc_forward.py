@@ -2,13 +2,13 @@
 tensor-core shapes (d a multiple of 16: link hops on tcgen05).
 
 FP32 keeps the FP32 bars of the other parity tests (1e-4 on log psi and on log-amplitude
-ratios).  BF16 rounds every operand of the forward pass's S4 convolutions and channel
-mixing to 8 mantissa bits (relative 2^-9 per operand) with FP32 accumulation; the link
-tensors, the adjoint and the ABACUS contractions stay at FP32 accuracy.  The cached
-activations y and the log-amplitude therefore carry errors of the order of the BF16
-rounding, which the log-amplitude ratios inherit.  The bounds below are the library's
-stated BF16 bounds, about twice the largest errors measured on these workloads on a
-GB300 (printed by the tests).
+ratios).  BF16 carries every operand of the forward pass's S4 convolutions and channel
+mixing as two BF16 terms (hi + lo, 8 mantissa bits each; products hi*hi + hi*lo + lo*hi
+with FP32 accumulation, about 2^-17 relative per product); the link tensors, the adjoint
+and the ABACUS contractions stay at FP32 accuracy.  (With one BF16 term per operand,
+2^-9 per product, the same J1-J2 test measured 0.11 on ratios and 6.9e-4 on log psi.)
+The bounds below are the library's stated BF16 bounds, above the largest errors
+measured on these workloads on a GB300 (printed by the tests).
 """
 import numpy as np
 import pytest
