@@ -297,7 +297,7 @@ def test_full_forward_and_recompute_baseline(dn, prec):
     ref = oracle.dlogpsi(desc, params, spins, sample, sites)
     e = rel_err(got, ref, lp_ref[sample]).max()
     print(f"recompute {prec}: ratio rel err {e:.3e}")
-    assert e <= (1e-10 if prec == "fp64" else 1e-3)
+    assert e <= (1e-10 if prec == "fp64" else 1e-4)
     model.close()
 
 
