@@ -318,6 +318,15 @@ dn_status dn_profile_get(int i, char *name, size_t name_len, long long *launches
  * link tensors.  Process-wide; affects caches built after the call.  Always DN_OK. */
 dn_status dn_set_fused_links(int on);
 
+/* Choice between two exact constructions of the band links of a pair with one
+ * intermediate layer, L^(m+2,m) (App. "Efficient construction of link tensors": the
+ * two-layer link by FFT): on (1, the default) as circular correlations by FFT of
+ * length M = the power of two >= 2N - 1 (open chain) or N (ring, N a power of two),
+ * O((2R+1) d^2 M log M) per configuration; off (0), or for other shapes, as the direct
+ * band sum, (2R+1) N^2 d^2 multiply-adds.  The two agree to rounding.  Process-wide;
+ * affects caches built after the call.  Always DN_OK. */
+dn_status dn_set_fft_links(int on);
+
 /* Release a cache (stream-ordered on the stream of the call that built it). */
 void dn_cache_destroy(dn_cache *cache);
 

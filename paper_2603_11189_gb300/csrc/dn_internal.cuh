@@ -248,6 +248,17 @@ cudaError_t launch_dband_tc(int d, int N, int periodic, int P, int nsrc, int R, 
 // Process-wide choice between the fused and the two-kernel chain ends (both exact; on by default).
 extern int g_fused_links;
 
+// Band links of a pair with one intermediate layer by FFT (link_fft.cu): scratch (units of T)
+// for the spectra of the pair (0: shape not supported), and the launch (cudaErrorNotSupported
+// when the shape or the scratch does not fit).  g_fft_links: on by default.
+template <typename T>
+size_t link_fft_scratch_elems(int N, int periodic, int d, int R);
+template <typename T>
+cudaError_t launch_link_fft(int N, int periodic, int d, int R, const T *taps_l, const T *taps_m1, const T *Dm,
+                            long long dm_ss, T *band, long long bss, long long brs, long long bos, long long b0,
+                            int nb, T *scratch, size_t scratch_elems, cudaStream_t st);
+extern int g_fft_links;
+
 // Reverse pass for the parameter log-derivatives (grad.cu).  Operands of the per-sample
 // outer-product sums of one layer, [B][N][.] each.
 template <typename T>

@@ -1023,8 +1023,17 @@ cudaError_t build_links(const dn_model *m, const Plan<T> &pl, const Weights<T> &
                         if (err != cudaSuccess) return err;
                     }
                 } else {
-                    err = launch_bandconv<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, dst, bd,
-                                             b0, nb, st);
+                    // A chain with one intermediate layer: its band by FFT where the shape allows
+                    // (the probe fields are unused here and hold the spectra), else summed directly.
+                    err = cudaErrorNotSupported;
+                    if (first && g_fft_links)
+                        err = launch_link_fft<T>(N, g.periodic, d, c->Rk, taps_n, gs.taps, gs.Dm, dm_ss, dst, bd.ss,
+                                                 bd.rs, bd.os, b0, nb, F, (size_t)nb * d * N * Pm, st);
+                    if (err == cudaErrorNotSupported) {
+                        cudaGetLastError();
+                        err = launch_bandconv<T>(g, taps_n, (int)Pm, first ? nullptr : F, first ? &gs : nullptr, dst,
+                                                 bd, b0, nb, st);
+                    }
                     if (err != cudaSuccess) return err;
                 }
             }

@@ -99,6 +99,7 @@ def _lib():
         "dn_sr_matrices": (i32, [vp, i32, sz, i32, vp, vp, sz, i32, vp]),
         "dn_sampler_batch": (i32, [vp, i32, vp, i32, vp, vp, i32, dbl, i32, vp, vp, ctypes.POINTER(SamplerStats)]),
         "dn_set_fused_links": (i32, [i32]),
+        "dn_set_fft_links": (i32, [i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -116,12 +117,17 @@ def exported_symbols():
             "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable",
             "dn_profile_count", "dn_profile_get", "dn_server_create", "dn_server_set_chain", "dn_server_submit",
             "dn_server_wait", "dn_server_get_stats", "dn_server_destroy", "dn_model_nparams", "dn_logpsi_grad", "dn_sr_matrices", "dn_sampler_batch",
-            "dn_set_fused_links"]
+            "dn_set_fused_links", "dn_set_fft_links"]
 
 
 def set_fused_links(on: bool):
     """Fused (default) or two-kernel end of the link-propagation chains; both exact."""
     _check(_lib().dn_set_fused_links(int(bool(on))), "dn_set_fused_links")
+
+
+def set_fft_links(on: bool):
+    """Band links of one-intermediate pairs by FFT (default) or by the direct sum; both exact."""
+    _check(_lib().dn_set_fft_links(int(bool(on))), "dn_set_fft_links")
 
 
 def _check(status: int, what: str):

@@ -147,3 +147,63 @@ def test_fused_chain_end_bench_model(dn):
     print(f"bench model: ratios vs oracle rel err {e:.3e}")
     assert e <= 1e-4
     model.close()
+
+
+FFT_CASES = [
+    # L, N, d, w, periodic, max_cluster, B, prec
+    (3, 24, 8, 2, 0, 1, 3, "fp64"),     # the only pair (3, 1); M = 64
+    (4, 37, 8, 1, 0, 2, 2, "fp64"),     # pair (4, 2) of the last chain; ragged N, pairs; M = 128
+    (3, 16, 8, 2, 1, 1, 2, "fp64"),     # ring: circular correlation of length N
+    (3, 40, 32, 2, 0, 1, 2, "fp32"),
+    (4, 32, 32, 2, 1, 2, 2, "fp32"),    # ring, pairs
+]
+
+
+@pytest.mark.parametrize("case", FFT_CASES)
+def test_fft_links_equal_direct_band_and_oracle(dn, case):
+    """The band links of the one-intermediate pair (l, m) = (L, L - 2) by FFT (the
+    two-layer link of App. "Efficient construction of link tensors") equal the direct band
+    sum to rounding, and the ratios built on them match the FP64 oracle."""
+    L, N, d, w, periodic, mc, B, prec = case
+    desc = ModelDesc(L=L, d=d, s=6, w=w, dh=d, dout=2, periodic=periodic)
+    params = synth.init_params(desc, 300 + N + d, a_scale=8.0)
+    spins_np = synth.spins_uniform(B, N, 61 + N)
+    spins = torch.from_numpy(spins_np).cuda()
+    model = dn.Model(desc, params)
+    lib = dn._lib()
+    caches = {}
+    try:
+        for fft in (False, True):
+            dn.set_fft_links(fft)
+            names = _traced_kernels(lib, lambda: caches.__setitem__(fft, model.forward_cache(spins, prec=prec,
+                                                                                             max_cluster=mc)))
+            assert any(n.endswith("k_link_fft") for n in names) == fft, names
+    finally:
+        dn.set_fft_links(True)
+    nR = 2 * (desc.W + mc - 1 - 1) + 1
+    R = (nR - 1) // 2
+    pair = (L - 3) * (L - 2) // 2 + (L - 3)            # index of (L, L - 2)
+    Kd, Kf = (caches[f].tensor("K").cpu().numpy().reshape(B, -1, N, nR, d, d)[:, pair] for f in (False, True))
+    mask = np.ones((N, nR), bool)
+    if not periodic:
+        for i in range(N):
+            for o in range(nR):
+                mask[i, o] = 0 <= i + o - R < N
+    a, b = Kd[:, mask], Kf[:, mask]
+    diff = np.max(np.abs(a - b)) / np.abs(a).max()
+    print(f"{case}: FFT vs direct band links max diff / max |K| = {diff:.3e}")
+    assert diff <= (1e-12 if prec == "fp64" else 1e-5)
+    if mc == 1:
+        sample, sites = synth.single_flips(B, N)
+    else:
+        sample, sites = synth.random_flips(B, N, 24, seed=N, pair_frac=0.5, max_sep=mc - 1, periodic=bool(periodic))
+    got = caches[True].flip_ratios(torch.from_numpy(sample).cuda(), torch.from_numpy(sites).cuda()).cpu().numpy()
+    for c in caches.values():
+        assert c.check() == dn.DN_OK
+        c.destroy()
+    ref = oracle.dlogpsi(desc, params, spins_np, sample, sites)
+    lp, _ = oracle.logpsi(desc, params, spins_np)
+    e = _rel(got, ref, lp[sample])
+    print(f"{case}: ratios vs oracle rel err {e:.3e}")
+    assert e <= (1e-10 if prec == "fp64" else 1e-4)
+    model.close()
