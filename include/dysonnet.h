@@ -320,12 +320,13 @@ dn_status dn_set_fused_links(int on);
 
 /* Choice between two exact constructions of the band links of a pair with one
  * intermediate layer, L^(m+2,m) (App. "Efficient construction of link tensors": the
- * two-layer link by FFT): on (1, the default) as circular correlations by FFT of
- * length M = the power of two >= 2N - 1 (open chain) or N (ring, N a power of two),
- * O((2R+1) d^2 M log M) per configuration; off (0), or for other shapes, as the direct
- * band sum, (2R+1) N^2 d^2 multiply-adds.  The two agree to rounding.  Process-wide;
- * affects caches built after the call.  Always DN_OK. */
-dn_status dn_set_fft_links(int on);
+ * two-layer link by FFT): as circular correlations by FFT of length M = the power of
+ * two >= 2N - 1 (open chain) or N (ring, N a power of two), O((2R+1) d^2 M log M) per
+ * configuration, or as the direct band sum, (2R+1) N^2 d^2 multiply-adds.  mode 1 (the
+ * default): FFT where the direct sum has no fast kernel or N >= 512; 2: FFT wherever
+ * the shape allows; 0: never.  The two agree to rounding.  Process-wide; affects caches
+ * built after the call.  DN_EINVAL for another mode. */
+dn_status dn_set_fft_links(int mode);
 
 /* Release a cache (stream-ordered on the stream of the call that built it). */
 void dn_cache_destroy(dn_cache *cache);

@@ -276,7 +276,8 @@ int g_fft_links = 1;
 
 }  // namespace dn
 
-extern "C" dn_status dn_set_fft_links(int on) {
-    dn::g_fft_links = on ? 1 : 0;
+extern "C" dn_status dn_set_fft_links(int mode) {
+    if (mode < 0 || mode > 2) return DN_EINVAL;
+    dn::g_fft_links = mode;
     return DN_OK;
 }

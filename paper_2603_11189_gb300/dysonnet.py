@@ -125,9 +125,10 @@ def set_fused_links(on: bool):
     _check(_lib().dn_set_fused_links(int(bool(on))), "dn_set_fused_links")
 
 
-def set_fft_links(on: bool):
-    """Band links of one-intermediate pairs by FFT (default) or by the direct sum; both exact."""
-    _check(_lib().dn_set_fft_links(int(bool(on))), "dn_set_fft_links")
+def set_fft_links(mode: int):
+    """Band links of one-intermediate pairs: 0 direct sum, 1 FFT where it is the faster one
+    (default), 2 FFT wherever the shape allows; all exact."""
+    _check(_lib().dn_set_fft_links(int(mode)), "dn_set_fft_links")
 
 
 def _check(status: int, what: str):

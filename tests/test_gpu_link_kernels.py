@@ -174,12 +174,12 @@ def test_fft_links_equal_direct_band_and_oracle(dn, case):
     caches = {}
     try:
         for fft in (False, True):
-            dn.set_fft_links(fft)
+            dn.set_fft_links(2 if fft else 0)
             names = _traced_kernels(lib, lambda: caches.__setitem__(fft, model.forward_cache(spins, prec=prec,
                                                                                              max_cluster=mc)))
             assert any(n.endswith("k_link_fft") for n in names) == fft, names
     finally:
-        dn.set_fft_links(True)
+        dn.set_fft_links(1)
     nR = 2 * (desc.W + mc - 1 - 1) + 1
     R = (nR - 1) // 2
     pair = (L - 3) * (L - 2) // 2 + (L - 3)            # index of (L, L - 2)
