@@ -345,11 +345,19 @@ void dn_cache_destroy(dn_cache *cache);
  * dn_server_set_chain with build_now); when the caches would exceed the
  * device-memory budget, the least recently used idle ones are dropped.
  * DN_SERVE_RECOMPUTE serves the same requests by a full forward pass of every
- * proposal (the baseline).  While a server exists, its model must not be used
- * by other calls.  Results of a request do not depend on which other requests
- * share its batch. */
+ * proposal (the baseline).  DN_SERVE_PERSISTENT serves them with one resident
+ * kernel (one or two CTAs per SM) instead of a launch per batch: admitted
+ * proposals are appended to a work queue in host-mapped memory and published by
+ * a counter; the kernel's CTAs claim them as they appear and return each ratio
+ * through mapped memory, so requests that arrive while others run are served
+ * with no launch in between.  The kernel waits for work at most an idle limit
+ * (dn_server_set_idle_limit, default 0.2 s) and then leaves with DN_ETIMEOUT
+ * (dn_server_kernel_status); the worker launches it again when work arrives and
+ * stops it while a new chain's cache is built.  While a server exists, its model
+ * must not be used by other calls.  Results of a request do not depend on which
+ * other requests share its batch. */
 typedef struct dn_server dn_server;
-typedef enum { DN_SERVE_ABACUS = 0, DN_SERVE_RECOMPUTE = 1 } dn_serve_mode;
+typedef enum { DN_SERVE_ABACUS = 0, DN_SERVE_RECOMPUTE = 1, DN_SERVE_PERSISTENT = 2 } dn_serve_mode;
 typedef struct {
     unsigned long long requests, flips, batches, cache_builds, evictions;
     size_t resident_bytes; /* device bytes of the resident caches */
@@ -379,6 +387,16 @@ dn_status dn_server_submit(dn_server *server, int chain, const int32_t *sites_ho
 dn_status dn_server_wait(dn_server *server, unsigned long long ticket, double timeout_s, double *latency_s);
 
 dn_status dn_server_get_stats(dn_server *server, dn_server_stats *out);
+
+/* DN_SERVE_PERSISTENT: how long (seconds, > 0) the kernel waits for work before it
+ * leaves; applies to launches after the call.  DN_EINVAL for other modes. */
+dn_status dn_server_set_idle_limit(dn_server *server, double seconds);
+
+/* DN_SERVE_PERSISTENT: wait up to wait_s seconds for the resident kernel to have
+ * left; *running (may be NULL) = 1 if it is still running.  Returns DN_OK while it
+ * runs or after the worker stopped it, DN_ETIMEOUT when its last exit was the idle
+ * limit running out with the queue unfed.  DN_EINVAL for other modes. */
+dn_status dn_server_kernel_status(dn_server *server, double wait_s, int *running);
 
 /* Finish every queued request, stop the worker and release the caches. */
 void dn_server_destroy(dn_server *server);

@@ -295,6 +295,74 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus_multi(const AbArgs<T> *__
     abacus_flip_set<T>(sa, f, sample, sites, out);
 }
 
+// Persistent serving loop: every CTA claims the next published item (compare-and-swap on
+// head against the host's tail, so that an item is never claimed by a CTA that then
+// leaves), runs the flip-list body on it and hands the ratio back through host-mapped
+// memory.  Waiting for work is bounded by idle_ns of %globaltimer time.
+__device__ __forceinline__ unsigned long long load_acquire_sys(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAbThreads) k_abacus_serve(const AbArgs<T> *__restrict__ descs, ServeQueue *q,
+                                                             ServeItems it, unsigned long long *head, long long idle_ns) {
+    __shared__ AbArgs<T> sa;
+    __shared__ int32_t s_sample[1], s_sites[2];
+    __shared__ double s_out[1];
+    __shared__ long long s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long item = -1;
+            const unsigned long long t0 = global_ns();
+            for (;;) {
+                const unsigned long long h = atomicAdd(head, 0ull);
+                const unsigned long long tail = load_acquire_sys(&q->tail);
+                if (h < tail) {
+                    if (atomicCAS(head, h, h + 1) == h) {
+                        item = (long long)h;
+                        break;
+                    }
+                    continue;
+                }
+                if (*((volatile unsigned int *)&q->stop)) break;
+                if ((long long)(global_ns() - t0) > idle_ns) {
+                    *((volatile int *)&q->status) = (int)DN_ETIMEOUT;   // every leaving CTA writes the same value
+                    __threadfence_system();
+                    break;
+                }
+                __nanosleep(2000);
+            }
+            s_item = item;
+            if (item >= 0) {
+                const int slot = (int)(item % it.cap);
+                sa = descs[((volatile int32_t *)it.cache)[slot]];
+                s_sample[0] = 0;
+                s_sites[0] = ((volatile int32_t *)it.sites)[2 * slot];
+                s_sites[1] = ((volatile int32_t *)it.sites)[2 * slot + 1];
+            }
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item < 0) break;
+        abacus_flip_set<T>(sa, 0, s_sample, s_sites, s_out);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int slot = (int)(item % it.cap);
+            ((volatile double *)it.out)[slot] = s_out[0];
+            __threadfence_system();
+            ((volatile unsigned long long *)it.done)[slot] = (unsigned long long)item + 1;
+        }
+    }
+}
+
 template <typename T>
 cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
                           const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st,
@@ -1447,12 +1515,31 @@ cudaError_t launch_abacus_multi(const dn_model *m, int WF, const void *descs, co
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_abacus_serve(const dn_model *m, int WF, const void *descs, ServeQueue *q, ServeItems it,
+                                unsigned long long *head, long long idle_ns, int ctas, cudaStream_t st) {
+    const dn_model_desc &D = m->desc;
+    const size_t tsz = ((size_t)(D.L + 3) * WF * D.d + 2 * (size_t)WF * D.d_h) * sizeof(T);
+    const size_t smem = ((tsz + 7) & ~(size_t)7) + (size_t)kMaxDout * kAbThreads * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_abacus_serve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_abacus_serve", st);
+        k_abacus_serve<T><<<ctas, kAbThreads, smem, st>>>(static_cast<const AbArgs<T> *>(descs), q, it, head, idle_ns);
+    }
+    return cudaGetLastError();
+}
+
 template size_t abacus_desc_bytes<double>();
 template size_t abacus_desc_bytes<float>();
 template void abacus_desc<double>(const dn_model *, const Plan<double> &, const Weights<double> &, const dn_cache *,
                                   void *);
 template void abacus_desc<float>(const dn_model *, const Plan<float> &, const Weights<float> &, const dn_cache *,
                                  void *);
+template cudaError_t launch_abacus_serve<double>(const dn_model *, int, const void *, ServeQueue *, ServeItems,
+                                                 unsigned long long *, long long, int, cudaStream_t);
+template cudaError_t launch_abacus_serve<float>(const dn_model *, int, const void *, ServeQueue *, ServeItems,
+                                                unsigned long long *, long long, int, cudaStream_t);
 template cudaError_t launch_abacus_multi<double>(const dn_model *, int, const void *, const int32_t *, const int32_t *,
                                                  const int32_t *, int, double *, cudaStream_t);
 template cudaError_t launch_abacus_multi<float>(const dn_model *, int, const void *, const int32_t *, const int32_t *,

@@ -353,6 +353,28 @@ void abacus_desc(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, cons
 template <typename T>
 cudaError_t launch_abacus_multi(const dn_model *m, int WF, const void *descs, const int32_t *cache_of,
                                 const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st);
+
+// Persistent serving kernel (abacus.cu): work items in host-mapped memory, claimed one
+// per CTA once the host has published them (item i is available when i < q->tail).
+// Item slot s = i mod cap holds cache[s] (descriptor index), sites[2 s .. 2 s + 1]; the
+// kernel writes out[s] and then done[s] = i + 1.  A CTA that finds no item for idle_ns
+// nanoseconds (or sees q->stop) leaves; the first CTA that leaves on the idle limit sets
+// q->status = DN_ETIMEOUT.  head (device memory) counts claimed items across launches.
+struct ServeQueue {
+    unsigned long long tail;   // items published (host)
+    unsigned int stop;         // host: leave as soon as no item is available
+    int status;                // kernel: DN_OK, or DN_ETIMEOUT after the idle limit
+};
+struct ServeItems {
+    int32_t *cache;            // [cap]
+    int32_t *sites;            // [cap][2]
+    double *out;               // [cap]
+    unsigned long long *done;  // [cap]
+    int cap;
+};
+template <typename T>
+cudaError_t launch_abacus_serve(const dn_model *m, int WF, const void *descs, ServeQueue *q, ServeItems it,
+                                unsigned long long *head, long long idle_ns, int ctas, cudaStream_t st);
 // All N single flips of every cached configuration, out[b N + j], layer by
 // layer; scratch of singles_scratch_bytes() bytes (cudaErrorNotSupported when
 // the shape does not fit the kernels).

@@ -15,7 +15,18 @@
 //  * copies results to the callers' host buffers and timestamps completion.
 // The recompute mode serves the same requests by full forward passes of every
 // proposal (dn_recompute_flip_ratios), the baseline the caches replace.
+//
+// The persistent mode keeps one kernel resident instead of launching one per batch: the
+// worker appends each admitted request's proposals to a work queue in host-mapped memory
+// and publishes them by advancing a counter; the CTAs of k_abacus_serve claim items as
+// they appear, run the flip-list body on the item's cache and hand the ratio back through
+// the same mapped memory.  Requests arriving while others are on the GPU are appended
+// behind them with no launch in between.  The kernel waits for work only up to an idle
+// limit, then leaves with DN_ETIMEOUT in its status word (dn_server_kernel_status); the
+// worker launches it again when work arrives, and stops it before a new chain's cache is
+// built so that the build's kernels get the SMs.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -32,7 +43,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct Request {
-    unsigned long long ticket = 0;
+    unsigned long long ticket = 0, item0 = 0;
     int chain = 0, F = 0;
     std::vector<int32_t> sites;   // [F][2]
     double *out_host = nullptr;
@@ -48,6 +59,7 @@ struct Chain {
     size_t bytes = 0;
     unsigned long long last_use = 0;
     int in_flight = 0;   // batches on the GPU that use this chain
+    int slot = -1;       // persistent mode: row of the device descriptor table
 };
 
 struct Slot {
@@ -82,9 +94,25 @@ struct dn_server {
     Slot slots[2];
     dn_server_stats stats{};
     cudaStream_t setup = nullptr;
+    // persistent mode
+    bool persistent = false;
+    dn::ServeQueue *q = nullptr, *q_dev = nullptr;         // host-mapped
+    dn::ServeItems items{}, items_dev{};                   // host-mapped ring of cap items
+    unsigned long long *head_dev = nullptr;                 // claimed items (device)
+    unsigned char *desc_tab = nullptr;                      // [kDescSlots] descriptors (device)
+    std::vector<int> free_slots;
+    unsigned long long next_item = 0, done_upto = 0;
+    cudaStream_t kst = nullptr;
+    cudaEvent_t kev = nullptr;
+    bool k_launched = false;
+    long long idle_ns = 200000000;                          // 0.2 s
+    int ctas = 0;
+    std::mutex kmu;                                         // kernel launch and status
 };
 
 namespace {
+
+constexpr int kDescSlots = 1024;   // resident caches addressable by the persistent kernel
 
 bool fp64(const dn_server *s) { return s->prec == DN_FP64; }
 
@@ -96,6 +124,54 @@ void drop_cache(dn_server *s, Chain &c) {
         s->resident -= c.bytes;
         c.bytes = 0;
     }
+    if (c.slot >= 0) {
+        s->free_slots.push_back(c.slot);
+        c.slot = -1;
+    }
+}
+
+// Persistent kernel: is it running (launched and not finished)?  Called with kmu held.
+bool kernel_running(dn_server *s) {
+    if (!s->k_launched) return false;
+    const cudaError_t e = cudaEventQuery(s->kev);
+    if (e == cudaErrorNotReady) return true;
+    if (e != cudaSuccess) cudaGetLastError();
+    return false;
+}
+
+// Ask the persistent kernel to leave and wait for it (it finishes the items already
+// published first); the wait on the host is bounded by 30 s.
+void stop_kernel(dn_server *s) {
+    std::lock_guard<std::mutex> lk(s->kmu);
+    if (!s->k_launched) return;
+    *((volatile unsigned int *)&s->q->stop) = 1u;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    const auto t0 = Clock::now();
+    while (kernel_running(s) && seconds(Clock::now() - t0) < 30.0) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    if (!kernel_running(s)) s->k_launched = false;
+    *((volatile unsigned int *)&s->q->stop) = 0u;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+}
+
+// Launch the persistent kernel if items are outstanding and it is not running.
+dn_status ensure_kernel(dn_server *s) {
+    std::lock_guard<std::mutex> lk(s->kmu);
+    if (kernel_running(s)) return DN_OK;
+    s->k_launched = false;
+    *((volatile int *)&s->q->status) = DN_OK;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    const int WF = 2 * s->m->desc.w + 1;
+    cudaError_t e = fp64(s) ? dn::launch_abacus_serve<double>(s->m, WF, s->desc_tab, s->q_dev, s->items_dev,
+                                                               s->head_dev, s->idle_ns, s->ctas, s->kst)
+                            : dn::launch_abacus_serve<float>(s->m, WF, s->desc_tab, s->q_dev, s->items_dev,
+                                                              s->head_dev, s->idle_ns, s->ctas, s->kst);
+    if (e == cudaSuccess) e = cudaEventRecord(s->kev, s->kst);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DN_ECUDA;
+    }
+    s->k_launched = true;
+    return DN_OK;
 }
 
 // Make room for `need` bytes by evicting idle caches, least recently used first.
@@ -299,6 +375,139 @@ void worker_main(dn_server *s) {
     }
 }
 
+// Persistent mode: give chain c a row of the descriptor table holding its cache's
+// descriptor (written and synchronised before any item refers to it).
+dn_status bind_slot(dn_server *s, Chain &c) {
+    if (c.slot >= 0) return DN_OK;
+    if (s->free_slots.empty()) return DN_ENOMEM;
+    const int slot = s->free_slots.back();
+    std::vector<unsigned char> d(s->desc_bytes);
+    if (fp64(s)) dn::abacus_desc<double>(s->m, s->m->plan64.at(c.N), s->m->w64, c.cache, d.data());
+    else dn::abacus_desc<float>(s->m, s->m->plan32.at(c.N), s->m->w32, c.cache, d.data());
+    if (cudaMemcpyAsync(s->desc_tab + (size_t)slot * s->desc_bytes, d.data(), s->desc_bytes, cudaMemcpyHostToDevice,
+                        s->setup) != cudaSuccess ||
+        cudaStreamSynchronize(s->setup) != cudaSuccess) {
+        cudaGetLastError();
+        return DN_ECUDA;
+    }
+    s->free_slots.pop_back();
+    c.slot = slot;
+    return DN_OK;
+}
+
+void fail_request(dn_server *s, Request *r, dn_status st) {
+    r->status = st;
+    r->t_done = Clock::now();
+    r->done = true;
+    s->cv_done.notify_all();
+}
+
+void worker_persistent(dn_server *s) {
+    cudaSetDevice(s->device);
+    std::deque<Request *> inflight;   // requests whose items are published, in publication order
+    const unsigned long long cap = (unsigned long long)s->items.cap;
+    for (;;) {
+        bool stopping;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (inflight.empty())
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(5), [&] { return s->stop || !s->pending.empty(); });
+            stopping = s->stop && s->pending.empty() && inflight.empty();
+        }
+        if (stopping) break;
+        bool progress = false;
+        // Publish every pending request whose proposals fit in the ring, admitting its chain.
+        for (;;) {
+            Request *r = nullptr;
+            Chain *c = nullptr;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                if (s->pending.empty()) break;
+                r = s->pending.front();
+                if (s->next_item + (unsigned long long)r->F - s->done_upto > cap) break;   // ring full: wait
+                c = &s->chains[r->chain];
+                if (!c->cache) {
+                    const size_t need = dn_cache_bytes(s->m, c->N, 1, (dn_precision)s->prec, 1);
+                    if (!make_room(s, need, {r->chain})) {
+                        if (!inflight.empty()) break;   // wait until in-flight requests release caches
+                        s->pending.pop_front();
+                        fail_request(s, r, DN_ENOMEM);
+                        continue;
+                    }
+                    stop_kernel(s);                     // the build's kernels need the SMs
+                    const dn_status b = build_cache(s, *c, s->setup);
+                    if (b != DN_OK) {
+                        s->pending.pop_front();
+                        fail_request(s, r, b);
+                        continue;
+                    }
+                }
+                const dn_status bs = bind_slot(s, *c);
+                if (bs != DN_OK) {
+                    s->pending.pop_front();
+                    fail_request(s, r, bs);
+                    continue;
+                }
+                s->pending.pop_front();
+                c->in_flight++;
+                c->last_use = ++s->clock;
+                s->stats.flips += r->F;
+                s->stats.batches++;
+            }
+            // The ring slots of items next_item .. next_item + F - 1 are free (done_upto).
+            for (int f = 0; f < r->F; ++f) {
+                const unsigned long long i = s->next_item + f;
+                const int slot = (int)(i % cap);
+                s->items.cache[slot] = c->slot;
+                s->items.sites[2 * slot] = r->sites[2 * f];
+                s->items.sites[2 * slot + 1] = r->sites[2 * f + 1];
+                s->items.done[slot] = 0ull;
+            }
+            r->item0 = s->next_item;
+            s->next_item += (unsigned long long)r->F;
+            std::atomic_thread_fence(std::memory_order_release);
+            *((volatile unsigned long long *)&s->q->tail) = s->next_item;
+            std::atomic_thread_fence(std::memory_order_seq_cst);
+            inflight.push_back(r);
+            progress = true;
+        }
+        if (!inflight.empty() && ensure_kernel(s) != DN_OK) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (Request *r : inflight) {
+                s->chains[r->chain].in_flight--;
+                fail_request(s, r, DN_ECUDA);
+            }
+            inflight.clear();
+            s->done_upto = s->next_item;
+        }
+        // Complete requests in publication order (ring slots are released in that order).
+        while (!inflight.empty()) {
+            Request *r = inflight.front();
+            bool all = true;
+            for (int f = 0; f < r->F && all; ++f) {
+                const unsigned long long i = r->item0 + f;
+                all = *((volatile unsigned long long *)&s->items.done[i % cap]) == i + 1;
+            }
+            if (!all) break;
+            std::atomic_thread_fence(std::memory_order_acquire);
+            for (int f = 0; f < r->F; ++f) r->out_host[f] = ((volatile double *)s->items.out)[(r->item0 + f) % cap];
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->chains[r->chain].in_flight--;
+                r->status = DN_OK;
+                r->t_done = Clock::now();
+                r->done = true;
+                s->cv_done.notify_all();
+            }
+            s->done_upto = r->item0 + (unsigned long long)r->F;
+            inflight.pop_front();
+            progress = true;
+        }
+        if (!progress && !inflight.empty()) std::this_thread::sleep_for(std::chrono::microseconds(5));
+    }
+    stop_kernel(s);
+}
+
 void free_slot(Slot &sl) {
     if (sl.st) cudaStreamSynchronize(sl.st);
     if (sl.h_i) cudaFreeHost(sl.h_i);
@@ -317,6 +526,18 @@ void free_slot(Slot &sl) {
 
 void destroy_server(dn_server *s) {
     for (auto &sl : s->slots) free_slot(sl);
+    if (s->kst) {
+        cudaStreamSynchronize(s->kst);
+        cudaStreamDestroy(s->kst);
+    }
+    if (s->kev) cudaEventDestroy(s->kev);
+    if (s->q) cudaFreeHost(s->q);
+    if (s->items.cache) cudaFreeHost(s->items.cache);
+    if (s->items.sites) cudaFreeHost(s->items.sites);
+    if (s->items.out) cudaFreeHost(s->items.out);
+    if (s->items.done) cudaFreeHost(s->items.done);
+    if (s->head_dev) cudaFree(s->head_dev);
+    if (s->desc_tab) cudaFree(s->desc_tab);
     for (auto &kv : s->chains) {
         drop_cache(s, kv.second);
         if (kv.second.spins_dev) dn::dev_free(kv.second.spins_dev, (size_t)kv.second.N, s->setup);
@@ -338,7 +559,8 @@ dn_status dn_server_create(dn_model *m, dn_precision prec, int mode, size_t hbm_
     if (!out) return DN_EINVAL;
     *out = nullptr;
     if (!m || (prec != DN_FP64 && prec != DN_FP32 && prec != DN_BF16) ||
-        (mode != DN_SERVE_ABACUS && mode != DN_SERVE_RECOMPUTE) || max_batch_flips < 1 || max_batch_chains < 1)
+        (mode != DN_SERVE_ABACUS && mode != DN_SERVE_RECOMPUTE && mode != DN_SERVE_PERSISTENT) ||
+        max_batch_flips < 1 || max_batch_chains < 1)
         return DN_EINVAL;
     dn_server *s = new dn_server();
     s->m = m;
@@ -366,12 +588,48 @@ dn_status dn_server_create(dn_model *m, dn_precision prec, int mode, size_t hbm_
         sl.d_desc = static_cast<unsigned char *>(dn::dev_alloc(sl.bytes_desc, sl.st));
         ok = sl.d_i && sl.d_out && sl.d_desc;
     }
+    if (ok && mode == DN_SERVE_PERSISTENT) {
+        // Work queue and ring in host-mapped memory (read by the kernel while it runs), the
+        // claim counter and the descriptor table in device memory.
+        s->persistent = true;
+        const int cap = 4 * max_batch_flips;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+        s->ctas = 2 * (sms > 0 ? sms : 1);
+        void *hq = nullptr, *hc = nullptr, *hs = nullptr, *ho = nullptr, *hd = nullptr;
+        ok = cudaHostAlloc(&hq, sizeof(dn::ServeQueue), cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostAlloc(&hc, (size_t)cap * sizeof(int32_t), cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostAlloc(&hs, (size_t)cap * 2 * sizeof(int32_t), cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostAlloc(&ho, (size_t)cap * sizeof(double), cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostAlloc(&hd, (size_t)cap * sizeof(unsigned long long), cudaHostAllocMapped) == cudaSuccess;
+        s->q = static_cast<dn::ServeQueue *>(hq);
+        s->items = dn::ServeItems{static_cast<int32_t *>(hc), static_cast<int32_t *>(hs), static_cast<double *>(ho),
+                                  static_cast<unsigned long long *>(hd), cap};
+        if (ok) {
+            memset(hq, 0, sizeof(dn::ServeQueue));
+            memset(hd, 0, (size_t)cap * sizeof(unsigned long long));
+            void *dq = nullptr, *dc = nullptr, *ds = nullptr, *dout = nullptr, *dd = nullptr;
+            ok = cudaHostGetDevicePointer(&dq, hq, 0) == cudaSuccess && cudaHostGetDevicePointer(&dc, hc, 0) == cudaSuccess &&
+                 cudaHostGetDevicePointer(&ds, hs, 0) == cudaSuccess && cudaHostGetDevicePointer(&dout, ho, 0) == cudaSuccess &&
+                 cudaHostGetDevicePointer(&dd, hd, 0) == cudaSuccess;
+            s->q_dev = static_cast<dn::ServeQueue *>(dq);
+            s->items_dev = dn::ServeItems{static_cast<int32_t *>(dc), static_cast<int32_t *>(ds),
+                                          static_cast<double *>(dout), static_cast<unsigned long long *>(dd), cap};
+        }
+        ok = ok && cudaMalloc(&s->head_dev, sizeof(unsigned long long)) == cudaSuccess &&
+             cudaMemset(s->head_dev, 0, sizeof(unsigned long long)) == cudaSuccess &&
+             cudaMalloc(&s->desc_tab, (size_t)kDescSlots * s->desc_bytes) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&s->kst, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&s->kev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaDeviceSynchronize() == cudaSuccess;
+        for (int k = kDescSlots - 1; k >= 0; --k) s->free_slots.push_back(k);
+    }
     if (!ok) {
         cudaGetLastError();
         destroy_server(s);
         return DN_ENOMEM;
     }
-    s->worker = std::thread(worker_main, s);
+    s->worker = std::thread(s->persistent ? worker_persistent : worker_main, s);
     *out = s;
     return DN_OK;
 }
@@ -450,6 +708,31 @@ dn_status dn_server_wait(dn_server *s, unsigned long long ticket, double timeout
     s->reqs.erase(it);
     delete r;
     return st;
+}
+
+dn_status dn_server_set_idle_limit(dn_server *s, double seconds_) {
+    if (!s || !s->persistent || !(seconds_ > 0.0) || seconds_ > 3600.0) return DN_EINVAL;
+    std::lock_guard<std::mutex> lk(s->kmu);
+    s->idle_ns = (long long)(seconds_ * 1e9);
+    return DN_OK;
+}
+
+dn_status dn_server_kernel_status(dn_server *s, double wait_s, int *running) {
+    if (!s || !s->persistent) return DN_EINVAL;
+    const auto t0 = Clock::now();
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(s->kmu);
+            const bool run = kernel_running(s);
+            if (!run || seconds(Clock::now() - t0) >= wait_s) {
+                if (running) *running = run ? 1 : 0;
+                if (run) return DN_OK;
+                std::atomic_thread_fence(std::memory_order_acquire);
+                return (dn_status) * ((volatile int *)&s->q->status);
+            }
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
 }
 
 dn_status dn_server_get_stats(dn_server *s, dn_server_stats *out) {

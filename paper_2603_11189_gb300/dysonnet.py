@@ -47,7 +47,7 @@ class ServerStats(ctypes.Structure):
                 ("resident_bytes", ctypes.c_size_t)]
 
 
-DN_SERVE_ABACUS, DN_SERVE_RECOMPUTE = 0, 1
+DN_SERVE_ABACUS, DN_SERVE_RECOMPUTE, DN_SERVE_PERSISTENT = 0, 1, 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -100,6 +100,8 @@ def _lib():
         "dn_sampler_batch": (i32, [vp, i32, vp, i32, vp, vp, i32, dbl, i32, vp, vp, ctypes.POINTER(SamplerStats)]),
         "dn_set_fused_links": (i32, [i32]),
         "dn_set_fft_links": (i32, [i32]),
+        "dn_server_set_idle_limit": (i32, [vp, dbl]),
+        "dn_server_kernel_status": (i32, [vp, dbl, ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -117,7 +119,7 @@ def exported_symbols():
             "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable",
             "dn_profile_count", "dn_profile_get", "dn_server_create", "dn_server_set_chain", "dn_server_submit",
             "dn_server_wait", "dn_server_get_stats", "dn_server_destroy", "dn_model_nparams", "dn_logpsi_grad", "dn_sr_matrices", "dn_sampler_batch",
-            "dn_set_fused_links", "dn_set_fft_links"]
+            "dn_set_fused_links", "dn_set_fft_links", "dn_server_set_idle_limit", "dn_server_kernel_status"]
 
 
 def set_fused_links(on: bool):
@@ -359,16 +361,26 @@ def _device_view(ptr: int, count: int, typestr: str) -> torch.Tensor:
 class Server:
     """Continuous-batching request loop of the library (dn_server_*): chains of any N
     with resident caches, requests of single-site proposals served in batches by one
-    kernel; mode "abacus" or "recompute" (full forward pass of every proposal)."""
+    kernel; mode "abacus", "persistent" (one resident kernel fed by a work queue) or
+    "recompute" (full forward pass of every proposal)."""
 
     def __init__(self, model: "Model", prec="fp32", mode="abacus", hbm_budget_bytes: int = 16 << 30,
                  max_batch_flips: int = 8192, max_batch_chains: int = 64):
         self._model = model
         self._h = ctypes.c_void_p()
-        m = DN_SERVE_ABACUS if mode == "abacus" else DN_SERVE_RECOMPUTE
+        m = {"abacus": DN_SERVE_ABACUS, "recompute": DN_SERVE_RECOMPUTE, "persistent": DN_SERVE_PERSISTENT}[mode]
         _check(_lib().dn_server_create(model._h, PRECISIONS[prec], m, int(hbm_budget_bytes), int(max_batch_flips),
                                        int(max_batch_chains), ctypes.byref(self._h)), "dn_server_create")
         self._out = {}
+
+    def set_idle_limit(self, seconds: float):
+        _check(_lib().dn_server_set_idle_limit(self._h, float(seconds)), "dn_server_set_idle_limit")
+
+    def kernel_status(self, wait_s: float = 0.0):
+        """(status, running) of the resident kernel of a persistent server."""
+        run = ctypes.c_int()
+        st = _lib().dn_server_kernel_status(self._h, float(wait_s), ctypes.byref(run))
+        return st, bool(run.value)
 
     def set_chain(self, chain: int, spins, build_now: bool = False):
         import numpy as np

@@ -74,14 +74,15 @@ def setup_model(desc, seed, chain_N):
     return params, chains
 
 
-def test_serving_mixed_equals_alone_and_oracle_fp64(dn):
+@pytest.mark.parametrize("mode", ["abacus", "persistent"])
+def test_serving_mixed_equals_alone_and_oracle_fp64(dn, mode):
     desc = ModelDesc(L=3, d=8, s=4, w=1, dh=8, dout=2, periodic=0)
     chain_N = [12, 17, 24, 31]
     params, chains = setup_model(desc, 301, chain_N)
     reqs = make_requests(chain_N, 24, 10, seed=1)
     model = dn.Model(desc, params)
-    mixed, st = serve(dn, model, "fp64", "abacus", chains, reqs)
-    alone, st1 = serve(dn, model, "fp64", "abacus", chains, reqs, alone=True)
+    mixed, st = serve(dn, model, "fp64", mode, chains, reqs)
+    alone, st1 = serve(dn, model, "fp64", mode, chains, reqs, alone=True)
     model.close()
     assert st["requests"] == len(reqs) and st["flips"] == sum(len(s) for _, s in reqs)
     assert st["batches"] >= 1 and st1["batches"] == len(reqs)
@@ -90,14 +91,15 @@ def test_serving_mixed_equals_alone_and_oracle_fp64(dn):
     check_oracle(desc, params, chains, reqs, mixed, TOL["fp64"])
 
 
-def test_serving_budget_evicts_and_stays_exact(dn):
+@pytest.mark.parametrize("mode", ["abacus", "persistent"])
+def test_serving_budget_evicts_and_stays_exact(dn, mode):
     desc = ModelDesc(L=3, d=8, s=4, w=1, dh=8, dout=2, periodic=1)
     chain_N = [15, 22, 30]
     params, chains = setup_model(desc, 302, chain_N)
     model = dn.Model(desc, params)
     one = max(model.cache_bytes(N, 1, "fp64") for N in chain_N)
     reqs = make_requests(chain_N, 18, 6, seed=2)
-    out, st = serve(dn, model, "fp64", "abacus", chains, reqs, budget=int(1.5 * one))
+    out, st = serve(dn, model, "fp64", mode, chains, reqs, budget=int(1.5 * one))
     model.close()
     assert st["evictions"] > 0
     assert st["resident_bytes"] <= int(1.5 * one)
@@ -124,9 +126,10 @@ def test_serving_fp32_d64_chains(dn):
     model = dn.Model(desc, params)
     mixed, _ = serve(dn, model, "fp32", "abacus", chains, reqs)
     alone, _ = serve(dn, model, "fp32", "abacus", chains, reqs, alone=True)
+    resident, _ = serve(dn, model, "fp32", "persistent", chains, reqs)
     model.close()
-    for a, b in zip(mixed, alone):
-        assert np.array_equal(a, b)
+    for a, b, c in zip(mixed, alone, resident):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
     check_oracle(desc, params, chains, reqs, mixed, TOL["fp32"])
 
 
@@ -145,5 +148,47 @@ def test_serving_rejects_bad_requests(dn):
     t = srv.submit(0, np.array([0, 4], dtype=np.int32))
     r, lat = srv.wait(t, timeout_s=60.0)
     assert r.shape == (2,) and np.all(np.isfinite(r)) and lat >= 0.0
+    srv.close()
+    model.close()
+
+
+def test_persistent_kernel_waits_are_bounded(dn):
+    """The resident kernel of a persistent server waits for work only up to its idle
+    limit: with the queue left unfed it leaves and reports DN_ETIMEOUT, and the next
+    request launches it again and is served exactly."""
+    desc = ModelDesc(L=3, d=8, s=4, w=1, dh=8, dout=2, periodic=0)
+    chain_N = [13, 21]
+    params, chains = setup_model(desc, 305, chain_N)
+    model = dn.Model(desc, params)
+    srv = dn.Server(model, prec="fp64", mode="persistent", max_batch_flips=64)
+    st, running = srv.kernel_status()
+    assert st == dn.DN_OK and not running               # nothing launched yet
+    srv.set_idle_limit(0.05)
+    for c, sp in enumerate(chains):
+        srv.set_chain(c, sp, build_now=True)
+    reqs = make_requests(chain_N, 6, 8, seed=5)
+    out = [srv.wait(srv.submit(c, sites), timeout_s=60.0)[0] for c, sites in reqs]
+    st, running = srv.kernel_status(wait_s=5.0)         # no more work: the idle limit runs out
+    assert st == dn.DN_ETIMEOUT and not running
+    more = make_requests(chain_N, 4, 8, seed=6)
+    out += [srv.wait(srv.submit(c, sites), timeout_s=60.0)[0] for c, sites in more]
+    st, running = srv.kernel_status(wait_s=5.0)
+    assert st == dn.DN_ETIMEOUT and not running
+    srv.close()
+    model.close()
+    check_oracle(desc, params, chains, reqs + more, out, TOL["fp64"])
+
+
+def test_persistent_mode_rejected_options(dn):
+    desc = ModelDesc(L=2, d=4, s=3, w=1, dh=4, dout=2, periodic=0)
+    model = dn.Model(desc, synth.init_params(desc, 6, a_scale=2.0))
+    srv = dn.Server(model, prec="fp64", mode="abacus", max_batch_flips=16)
+    with pytest.raises(dn.DysonNetError):
+        srv.set_idle_limit(0.1)                          # only persistent servers have a resident kernel
+    assert srv.kernel_status()[0] == dn.DN_EINVAL
+    srv.close()
+    srv = dn.Server(model, prec="fp64", mode="persistent", max_batch_flips=16)
+    with pytest.raises(dn.DysonNetError):
+        srv.set_idle_limit(0.0)
     srv.close()
     model.close()
