@@ -501,10 +501,11 @@ def measure_bf16_j1j2(dn, synth, torch, barrier, lib, B=64):
 def measure_serving(dn, synth, n_req=160, rate=20.0, seed=4005):
     """Serving workload: Markov chains with N in {64, 128, 256, 512, 1024} (two each) of
     the 6-layer, 64-channel, 64-mode model (FP32), requests of 1-512 random single-flip
-    proposals for a random chain.  For the ABACUS server and the per-request
-    full-forward recompute server: throughput with every request queued at once, and
-    p50/p99 latency (submission to result in host memory) under Poisson arrivals at
-    `rate` requests/s."""
+    proposals for a random chain.  For the ABACUS server (one launch per batch), the
+    persistent ABACUS server (one resident kernel fed through a work queue) and the
+    per-request full-forward recompute server: throughput with every request queued at
+    once, and p50/p99 latency (submission to result in host memory) under Poisson
+    arrivals at `rate` requests/s."""
     import numpy as np
     import time
     desc = synth.ModelDesc(L=6, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
@@ -523,7 +524,7 @@ def measure_serving(dn, synth, n_req=160, rate=20.0, seed=4005):
     res = {"workload": "chains N in {64,128,256,512,1024} x 2, DysonNet L=6 d=64 s=64 w=2 FP32, %d requests of "
                        "1-512 random single flips (%d flips)" % (n_req, flips),
            "rate_per_s": rate}
-    for mode in ("abacus", "recompute"):
+    for mode in ("abacus", "persistent", "recompute"):
         srv = dn.Server(model, prec="fp32", mode=mode, hbm_budget_bytes=24 << 30, max_batch_flips=4096,
                         max_batch_chains=16)
         t0 = time.perf_counter()
@@ -553,10 +554,12 @@ def measure_serving(dn, synth, n_req=160, rate=20.0, seed=4005):
         res[mode] = {"saturation": {"value": flips / sat_s, "unit": "flip ratios/s", "requests_per_s": n_req / sat_s},
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "mean_ms": float(lat.mean()), "batches": st["batches"],
-                     "cache_build_s": build_s if mode == "abacus" else None,
+                     "cache_build_s": build_s if mode != "recompute" else None,
                      "resident_cache_bytes": st["resident_bytes"]}
     model.close()
     res["speedup_saturation"] = res["abacus"]["saturation"]["value"] / res["recompute"]["saturation"]["value"]
+    res["speedup_saturation_persistent"] = (res["persistent"]["saturation"]["value"] /
+                                            res["recompute"]["saturation"]["value"])
     return res
 
 
