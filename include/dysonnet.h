@@ -348,12 +348,13 @@ void dn_cache_destroy(dn_cache *cache);
  * proposal (the baseline).  DN_SERVE_PERSISTENT serves them with one resident
  * kernel (one or two CTAs per SM) instead of a launch per batch: admitted
  * proposals are appended to a work queue in host-mapped memory and published by
- * a counter; the kernel's CTAs claim them as they appear and return each ratio
- * through mapped memory, so requests that arrive while others run are served
- * with no launch in between.  The kernel waits for work at most an idle limit
- * (dn_server_set_idle_limit, default 0.2 s) and then leaves with DN_ETIMEOUT
- * (dn_server_kernel_status); the worker launches it again when work arrives and
- * stops it while a new chain's cache is built.  While a server exists, its model
+ * a counter; the items are dealt to the kernel's CTAs in turn, each serves its
+ * items as they appear and returns each ratio through mapped memory, so requests
+ * that arrive while others run are served with no launch in between.  When the
+ * counter has not moved for an idle limit (dn_server_set_idle_limit, default
+ * 0.2 s) the kernel leaves with DN_ETIMEOUT (dn_server_kernel_status); the worker
+ * launches it again when work arrives and stops it while a new chain's cache is
+ * built.  While a server exists, its model
  * must not be used by other calls.  Results of a request do not depend on which
  * other requests share its batch. */
 typedef struct dn_server dn_server;
@@ -371,7 +372,7 @@ dn_status dn_server_create(dn_model *model, dn_precision prec, int mode, size_t 
 
 /* Register chain `chain` (>= 0) with configuration spins_host[N] (+1/-1, copied),
  * replacing an earlier one (and its cache).  build_now != 0 builds its cache in
- * this call (ABACUS mode).  DN_EINVAL while requests of the chain are pending or
+ * this call (ABACUS and persistent modes).  DN_EINVAL while requests of the chain are pending or
  * in flight, or for spins other than +1/-1. */
 dn_status dn_server_set_chain(dn_server *server, int chain, int N, const int8_t *spins_host, int build_now);
 

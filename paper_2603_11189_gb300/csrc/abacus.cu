@@ -295,10 +295,19 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus_multi(const AbArgs<T> *__
     abacus_flip_set<T>(sa, f, sample, sites, out);
 }
 
-// Persistent serving loop: every CTA claims the next published item (compare-and-swap on
-// head against the host's tail, so that an item is never claimed by a CTA that then
-// leaves), runs the flip-list body on it and hands the ratio back through host-mapped
-// memory.  Waiting for work is bounded by idle_ns of %globaltimer time.
+// Persistent serving loop.  A CTA takes a ticket (the next item number, from a counter
+// that starts at `base`), waits until the host's tail passes it, runs the flip-list body
+// on the item and hands the ratio back through host-mapped memory.  One atomic per item
+// and no retry loop: claiming items by compare-and-swap against the tail served at most
+// one claim per round trip.  The state word of ring slot i % cap is 2i + 1 once the host
+// has published item i and 2i + 2 once a CTA has served it; a ticket whose slot says
+// anything but 2i + 1 was served by an earlier launch and is dropped.
+//
+// Leaving: when the host asks to stop, or when the tail has not moved for idle_ns of
+// %globaltimer time (the CTA then records DN_ETIMEOUT and raises the closing word), a CTA
+// leaves as soon as its ticket is not published.  Tickets held by leaving CTAs are
+// served by the next launch, which the host makes, from the first item not yet served,
+// once every CTA is gone.
 __device__ __forceinline__ unsigned long long load_acquire_sys(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -312,33 +321,45 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 template <typename T>
 __global__ void __launch_bounds__(kAbThreads) k_abacus_serve(const AbArgs<T> *__restrict__ descs, ServeQueue *q,
-                                                             ServeItems it, unsigned long long *head, long long idle_ns) {
+                                                             ServeItems it, unsigned long long *ctl,
+                                                             unsigned long long base, long long idle_ns) {
     __shared__ AbArgs<T> sa;
     __shared__ int32_t s_sample[1], s_sites[2];
     __shared__ double s_out[1];
     __shared__ long long s_item;
+    unsigned long long tail_seen = 0ull, t_change = global_ns();   // thread 0's view of the tail
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
             long long item = -1;
-            const unsigned long long t0 = global_ns();
+            unsigned long long h = base + atomicAdd(ctl, 1ull);
+            unsigned int nap = 256;
             for (;;) {
-                const unsigned long long h = atomicAdd(head, 0ull);
                 const unsigned long long tail = load_acquire_sys(&q->tail);
+                const unsigned long long now = global_ns();
+                if (tail != tail_seen) {
+                    tail_seen = tail;
+                    t_change = now;
+                }
                 if (h < tail) {
-                    if (atomicCAS(head, h, h + 1) == h) {
+                    const int slot = (int)(h % (unsigned long long)it.cap);
+                    if (load_acquire_sys(it.done + slot) == 2 * h + 1) {
                         item = (long long)h;
                         break;
                     }
+                    h = base + atomicAdd(ctl, 1ull);   // served by an earlier launch
+                    nap = 256;
                     continue;
                 }
-                if (*((volatile unsigned int *)&q->stop)) break;
-                if ((long long)(global_ns() - t0) > idle_ns) {
+                if (*((volatile unsigned int *)&q->stop) || *((volatile unsigned long long *)(ctl + 1))) break;
+                if ((long long)(now - t_change) > idle_ns) {
+                    *((volatile unsigned long long *)(ctl + 1)) = 1ull;
                     *((volatile int *)&q->status) = (int)DN_ETIMEOUT;   // every leaving CTA writes the same value
                     __threadfence_system();
                     break;
                 }
-                __nanosleep(2000);
+                __nanosleep(nap);
+                if (nap < 8192) nap *= 2;
             }
             s_item = item;
             if (item >= 0) {
@@ -358,7 +379,7 @@ __global__ void __launch_bounds__(kAbThreads) k_abacus_serve(const AbArgs<T> *__
             const int slot = (int)(item % it.cap);
             ((volatile double *)it.out)[slot] = s_out[0];
             __threadfence_system();
-            ((volatile unsigned long long *)it.done)[slot] = (unsigned long long)item + 1;
+            ((volatile unsigned long long *)it.done)[slot] = 2 * (unsigned long long)item + 2;
         }
     }
 }
@@ -1517,7 +1538,8 @@ cudaError_t launch_abacus_multi(const dn_model *m, int WF, const void *descs, co
 
 template <typename T>
 cudaError_t launch_abacus_serve(const dn_model *m, int WF, const void *descs, ServeQueue *q, ServeItems it,
-                                unsigned long long *head, long long idle_ns, int ctas, cudaStream_t st) {
+                                unsigned long long *ctl, unsigned long long base, long long idle_ns, int ctas,
+                                cudaStream_t st) {
     const dn_model_desc &D = m->desc;
     const size_t tsz = ((size_t)(D.L + 3) * WF * D.d + 2 * (size_t)WF * D.d_h) * sizeof(T);
     const size_t smem = ((tsz + 7) & ~(size_t)7) + (size_t)kMaxDout * kAbThreads * sizeof(double);
@@ -1525,7 +1547,8 @@ cudaError_t launch_abacus_serve(const dn_model *m, int WF, const void *descs, Se
     if (err != cudaSuccess) return err;
     {
         ProfScope _ps("k_abacus_serve", st);
-        k_abacus_serve<T><<<ctas, kAbThreads, smem, st>>>(static_cast<const AbArgs<T> *>(descs), q, it, head, idle_ns);
+        k_abacus_serve<T><<<ctas, kAbThreads, smem, st>>>(static_cast<const AbArgs<T> *>(descs), q, it, ctl, base,
+                                                          idle_ns);
     }
     return cudaGetLastError();
 }
@@ -1537,9 +1560,9 @@ template void abacus_desc<double>(const dn_model *, const Plan<double> &, const 
 template void abacus_desc<float>(const dn_model *, const Plan<float> &, const Weights<float> &, const dn_cache *,
                                  void *);
 template cudaError_t launch_abacus_serve<double>(const dn_model *, int, const void *, ServeQueue *, ServeItems,
-                                                 unsigned long long *, long long, int, cudaStream_t);
+                                                 unsigned long long *, unsigned long long, long long, int, cudaStream_t);
 template cudaError_t launch_abacus_serve<float>(const dn_model *, int, const void *, ServeQueue *, ServeItems,
-                                                unsigned long long *, long long, int, cudaStream_t);
+                                                unsigned long long *, unsigned long long, long long, int, cudaStream_t);
 template cudaError_t launch_abacus_multi<double>(const dn_model *, int, const void *, const int32_t *, const int32_t *,
                                                  const int32_t *, int, double *, cudaStream_t);
 template cudaError_t launch_abacus_multi<float>(const dn_model *, int, const void *, const int32_t *, const int32_t *,

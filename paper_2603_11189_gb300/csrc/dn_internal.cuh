@@ -354,12 +354,14 @@ template <typename T>
 cudaError_t launch_abacus_multi(const dn_model *m, int WF, const void *descs, const int32_t *cache_of,
                                 const int32_t *sample, const int32_t *sites, int F, double *out, cudaStream_t st);
 
-// Persistent serving kernel (abacus.cu): work items in host-mapped memory, claimed one
-// per CTA once the host has published them (item i is available when i < q->tail).
-// Item slot s = i mod cap holds cache[s] (descriptor index), sites[2 s .. 2 s + 1]; the
-// kernel writes out[s] and then done[s] = i + 1.  A CTA that finds no item for idle_ns
-// nanoseconds (or sees q->stop) leaves; the first CTA that leaves on the idle limit sets
-// q->status = DN_ETIMEOUT.  head (device memory) counts claimed items across launches.
+// Persistent serving kernel (abacus.cu): work items in host-mapped memory, taken by
+// ticket (item base + ctl[0]++) and served once the host has published them (item i is
+// available when i < q->tail).  Item slot s = i mod cap holds cache[s] (descriptor
+// index), sites[2 s .. 2 s + 1] and the state word done[s] (2i + 1 after publication);
+// the kernel writes out[s] and then done[s] = 2i + 2.  When the tail has not moved for
+// idle_ns nanoseconds a CTA sets q->status = DN_ETIMEOUT and ctl[1] = 1; on ctl[1] or
+// q->stop every CTA leaves once its ticket is not published.  ctl (device memory, two
+// words) is zeroed before each launch.
 struct ServeQueue {
     unsigned long long tail;   // items published (host)
     unsigned int stop;         // host: leave as soon as no item is available
@@ -369,12 +371,13 @@ struct ServeItems {
     int32_t *cache;            // [cap]
     int32_t *sites;            // [cap][2]
     double *out;               // [cap]
-    unsigned long long *done;  // [cap]
+    unsigned long long *done;  // [cap] state of slot i % cap: 2i + 1 published, 2i + 2 served
     int cap;
 };
 template <typename T>
 cudaError_t launch_abacus_serve(const dn_model *m, int WF, const void *descs, ServeQueue *q, ServeItems it,
-                                unsigned long long *head, long long idle_ns, int ctas, cudaStream_t st);
+                                unsigned long long *ctl, unsigned long long base, long long idle_ns, int ctas,
+                                cudaStream_t st);
 // All N single flips of every cached configuration, out[b N + j], layer by
 // layer; scratch of singles_scratch_bytes() bytes (cudaErrorNotSupported when
 // the shape does not fit the kernels).

@@ -98,7 +98,7 @@ struct dn_server {
     bool persistent = false;
     dn::ServeQueue *q = nullptr, *q_dev = nullptr;         // host-mapped
     dn::ServeItems items{}, items_dev{};                   // host-mapped ring of cap items
-    unsigned long long *head_dev = nullptr;                 // claimed items (device)
+    unsigned long long *ctl_dev = nullptr;                  // ticket counter, closing word (device)
     unsigned char *desc_tab = nullptr;                      // [kDescSlots] descriptors (device)
     std::vector<int> free_slots;
     unsigned long long next_item = 0, done_upto = 0;
@@ -153,18 +153,26 @@ void stop_kernel(dn_server *s) {
     std::atomic_thread_fence(std::memory_order_seq_cst);
 }
 
-// Launch the persistent kernel if items are outstanding and it is not running.
+// Launch the persistent kernel if items are outstanding and it is not running.  Called
+// by the worker only (it alone publishes items).  The new launch's tickets start at the
+// first item not yet served; the kernel drops those after it that the previous launch
+// served (their state words say so).
 dn_status ensure_kernel(dn_server *s) {
     std::lock_guard<std::mutex> lk(s->kmu);
     if (kernel_running(s)) return DN_OK;
     s->k_launched = false;
     *((volatile int *)&s->q->status) = DN_OK;
     std::atomic_thread_fence(std::memory_order_seq_cst);
+    const unsigned long long cap = (unsigned long long)s->items.cap;
+    unsigned long long base = s->done_upto;
+    while (base < s->next_item && *((volatile unsigned long long *)&s->items.done[base % cap]) == 2 * base + 2) ++base;
     const int WF = 2 * s->m->desc.w + 1;
-    cudaError_t e = fp64(s) ? dn::launch_abacus_serve<double>(s->m, WF, s->desc_tab, s->q_dev, s->items_dev,
-                                                               s->head_dev, s->idle_ns, s->ctas, s->kst)
-                            : dn::launch_abacus_serve<float>(s->m, WF, s->desc_tab, s->q_dev, s->items_dev,
-                                                              s->head_dev, s->idle_ns, s->ctas, s->kst);
+    cudaError_t e = cudaMemsetAsync(s->ctl_dev, 0, 2 * sizeof(unsigned long long), s->kst);
+    if (e == cudaSuccess)
+        e = fp64(s) ? dn::launch_abacus_serve<double>(s->m, WF, s->desc_tab, s->q_dev, s->items_dev, s->ctl_dev, base,
+                                                      s->idle_ns, s->ctas, s->kst)
+                    : dn::launch_abacus_serve<float>(s->m, WF, s->desc_tab, s->q_dev, s->items_dev, s->ctl_dev, base,
+                                                     s->idle_ns, s->ctas, s->kst);
     if (e == cudaSuccess) e = cudaEventRecord(s->kev, s->kst);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -461,7 +469,7 @@ void worker_persistent(dn_server *s) {
                 s->items.cache[slot] = c->slot;
                 s->items.sites[2 * slot] = r->sites[2 * f];
                 s->items.sites[2 * slot + 1] = r->sites[2 * f + 1];
-                s->items.done[slot] = 0ull;
+                s->items.done[slot] = 2 * i + 1;   // published
             }
             r->item0 = s->next_item;
             s->next_item += (unsigned long long)r->F;
@@ -486,7 +494,7 @@ void worker_persistent(dn_server *s) {
             bool all = true;
             for (int f = 0; f < r->F && all; ++f) {
                 const unsigned long long i = r->item0 + f;
-                all = *((volatile unsigned long long *)&s->items.done[i % cap]) == i + 1;
+                all = *((volatile unsigned long long *)&s->items.done[i % cap]) == 2 * i + 2;
             }
             if (!all) break;
             std::atomic_thread_fence(std::memory_order_acquire);
@@ -536,7 +544,7 @@ void destroy_server(dn_server *s) {
     if (s->items.sites) cudaFreeHost(s->items.sites);
     if (s->items.out) cudaFreeHost(s->items.out);
     if (s->items.done) cudaFreeHost(s->items.done);
-    if (s->head_dev) cudaFree(s->head_dev);
+    if (s->ctl_dev) cudaFree(s->ctl_dev);
     if (s->desc_tab) cudaFree(s->desc_tab);
     for (auto &kv : s->chains) {
         drop_cache(s, kv.second);
@@ -590,7 +598,7 @@ dn_status dn_server_create(dn_model *m, dn_precision prec, int mode, size_t hbm_
     }
     if (ok && mode == DN_SERVE_PERSISTENT) {
         // Work queue and ring in host-mapped memory (read by the kernel while it runs), the
-        // claim counter and the descriptor table in device memory.
+        // ticket counter, the closing word and the descriptor table in device memory.
         s->persistent = true;
         const int cap = 4 * max_batch_flips;
         int sms = 0;
@@ -616,8 +624,8 @@ dn_status dn_server_create(dn_model *m, dn_precision prec, int mode, size_t hbm_
             s->items_dev = dn::ServeItems{static_cast<int32_t *>(dc), static_cast<int32_t *>(ds),
                                           static_cast<double *>(dout), static_cast<unsigned long long *>(dd), cap};
         }
-        ok = ok && cudaMalloc(&s->head_dev, sizeof(unsigned long long)) == cudaSuccess &&
-             cudaMemset(s->head_dev, 0, sizeof(unsigned long long)) == cudaSuccess &&
+        ok = ok && cudaMalloc(&s->ctl_dev, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+             cudaMemset(s->ctl_dev, 0, 2 * sizeof(unsigned long long)) == cudaSuccess &&
              cudaMalloc(&s->desc_tab, (size_t)kDescSlots * s->desc_bytes) == cudaSuccess &&
              cudaStreamCreateWithFlags(&s->kst, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&s->kev, cudaEventDisableTiming) == cudaSuccess &&
@@ -656,8 +664,9 @@ dn_status dn_server_set_chain(dn_server *s, int chain, int N, const int8_t *spin
         cudaGetLastError();
         return DN_ECUDA;
     }
-    if (build_now && s->mode == DN_SERVE_ABACUS) {
+    if (build_now && s->mode != DN_SERVE_RECOMPUTE) {
         if (!make_room(s, dn_cache_bytes(s->m, N, 1, (dn_precision)s->prec, 1), {chain})) return DN_ENOMEM;
+        if (s->persistent) stop_kernel(s);   // the build's kernels need the SMs
         dn_status r = build_cache(s, c, s->setup);
         if (r != DN_OK) return r;
         if (cudaStreamSynchronize(s->setup) != cudaSuccess) {

@@ -179,6 +179,38 @@ def test_persistent_kernel_waits_are_bounded(dn):
     check_oracle(desc, params, chains, reqs + more, out, TOL["fp64"])
 
 
+def test_persistent_relaunch_while_requests_arrive(dn):
+    """A persistent server whose idle limit (2 ms) is about as long as the gaps between
+    requests: the kernel leaves and is launched again while requests are in flight, so
+    items published after some CTAs left are served by the next launch and items the
+    previous launch served are dropped by their state words.  Every request completes
+    exactly once with the oracle's ratios and the batch server's values."""
+    import time
+    desc = ModelDesc(L=3, d=8, s=4, w=1, dh=8, dout=2, periodic=0)
+    chain_N = [12, 19, 26]
+    params, chains = setup_model(desc, 307, chain_N)
+    reqs = make_requests(chain_N, 48, 40, seed=7)
+    gaps = np.random.default_rng(8).uniform(0.0, 0.006, size=len(reqs))
+    model = dn.Model(desc, params)
+    srv = dn.Server(model, prec="fp64", mode="persistent", max_batch_flips=64)
+    srv.set_idle_limit(0.002)
+    for c, sp in enumerate(chains):
+        srv.set_chain(c, sp, build_now=True)
+    tickets = []
+    for (c, sites), gap in zip(reqs, gaps):
+        tickets.append(srv.submit(c, sites))
+        time.sleep(gap)
+    out = [srv.wait(t, timeout_s=60.0)[0] for t in tickets]
+    st, running = srv.kernel_status(wait_s=5.0)
+    assert st == dn.DN_ETIMEOUT and not running
+    srv.close()
+    ref, _ = serve(dn, model, "fp64", "abacus", chains, reqs)
+    model.close()
+    for a, b in zip(out, ref):
+        assert np.array_equal(a, b)
+    check_oracle(desc, params, chains, reqs, out, TOL["fp64"])
+
+
 def test_persistent_mode_rejected_options(dn):
     desc = ModelDesc(L=2, d=4, s=3, w=1, dh=4, dout=2, periodic=0)
     model = dn.Model(desc, synth.init_params(desc, 6, a_scale=2.0))
