@@ -227,11 +227,13 @@ def abacus_unique_bytes(N, L, d, dout, w, P, B, tb=4):
     return B * (per_sample * tb + N) + B * N * 8
 
 
-def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128, L=6):
+def measure_n1024(dn, synth, torch, barrier, lib, chains, recompute_flips=128, L=6):
     """ABACUS ratios/s given caches, cache-build time and the GPU full-forward recompute
     at N = 1024 for the L-layer, 64-channel, 64-mode model (FP32, long-range TFIM
     chains, all N single flips per chain; the recompute is timed on a sample of
-    `recompute_flips` flips per chain and scaled per ratio)."""
+    `recompute_flips` flips per chain and scaled per ratio).  The ABACUS roofline: the
+    cache bytes the flips need, once, over the layer kernels' device time (a separate
+    traced pass) and over the whole ABACUS call."""
     Nn = 1024
     desc = synth.ModelDesc(L=L, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
     params = synth.init_params(desc, 1005, a_scale=10.0)
@@ -257,8 +259,26 @@ def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128, L=6):
     ev1.record()
     barrier()
     ab_ms = ev0.elapsed_time(ev1) / reps
+    lib.dn_profile_enable(1)
+    for _ in range(reps):
+        cache.single_flip_ratios(out=out)
+    barrier()
+    prof = read_profile(lib)
+    lib.dn_profile_enable(0)
     cache_bytes = model.cache_bytes(Nn, 1, "fp32")
     cache.destroy()
+    P = (L - 1) * (L - 2) // 2
+    ab_bytes = abacus_unique_bytes(Nn, L, 64, 2, 2, P, chains)
+    peaks, src = _peaks()
+    lay = [v for k, v in prof.items() if k.endswith("k_ab_layer")]
+    lay_ms = sum(v[1] for v in lay) / reps
+    split = {k.split("/")[-1]: round(v[1] / reps, 4) for k, v in prof.items()}
+    roof = {"kernel": "k_ab_layer", "bound": "hbm", "achieved": ab_bytes / (lay_ms / 1e3) / 1e9,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ab_bytes / (lay_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "launches": sum(v[0] for v in lay) // reps, "ms": lay_ms,
+            "whole_call_frac": ab_bytes / (ab_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "algorithmic_bytes": ab_bytes, "kernels_ms": split,
+            "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"} if lay_ms > 0 else None
     sample_np, sites_np = synth.random_flips(chains, Nn, chains * recompute_flips, seed=3005)
     s_t = torch.from_numpy(sample_np).cuda()
     x_t = torch.from_numpy(sites_np).cuda()
@@ -277,6 +297,7 @@ def measure_n1024(dn, synth, torch, barrier, chains, recompute_flips=128, L=6):
     return {"workload": "lr-TFIM N=1024 open, DysonNet L=%d d=64 s=64 w=2 FP32, %d chains x 1024 single flips"
                         % (L, chains),
             "abacus_given_caches": {"value": ab_rate, "unit": "flip ratios/s", "ms": ab_ms},
+            "abacus_roofline": roof,
             "cache_build_ms": build_ms, "cache_bytes_per_chain": cache_bytes,
             "recompute": {"value": rc_rate, "unit": "flip ratios/s", "ms": rc_ms,
                           "sample": "%d random single flips per chain" % recompute_flips},
@@ -699,11 +720,11 @@ def main():
         recompute = {"value": flips_step / (rms / 1e3), "unit": "flip ratios/s", "ms": rms,
                      "speedup_of_abacus_step": (flips_step / (ms / 1e3)) / (flips_step / (rms / 1e3))}
 
-    n1024 = None if args.no_n1024 else measure_n1024(dn, synth, torch, barrier, args.n1024_chains)
+    n1024 = None if args.no_n1024 else measure_n1024(dn, synth, torch, barrier, lib, args.n1024_chains)
     # The same at depths whose exact links need no full N x N hop beyond the embedding chain
     # (L = 2: the paper's own depth; L = 3: one interlayer pair, built directly).
     n1024_shallow = None if args.no_n1024 else {
-        "L%d" % Ls: measure_n1024(dn, synth, torch, barrier, 16, L=Ls) for Ls in (3, 2)}
+        "L%d" % Ls: measure_n1024(dn, synth, torch, barrier, lib, 16, L=Ls) for Ls in (3, 2)}
     serving = None if args.no_serving else measure_serving(dn, synth)
     grad = None if args.no_grad else measure_grad(dn, synth, torch, barrier, lib, B=args.grad_samples)
     sampler = None if args.no_sampler else measure_sampler(dn, synth, torch, barrier)

@@ -1165,6 +1165,7 @@ __global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(Ab
 // Every wait is bounded; a timeout raises bit 4 of the cache flag and the CTA lets its
 // copies land before it ends.
 constexpr int kCoWarps = 8;
+constexpr int kCoPk = 2;   // (flip, output) pairs per warp whose inputs are loaded a contraction early
 
 template <int D, int WW, int NS>
 __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbArgs<float> a, int l, int R,
@@ -1179,6 +1180,7 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
     constexpr int CPB = dd / 1024;        // chunks per block
     constexpr int WPJ = kCoWarps / CPB;   // warps per chunk row class
     constexpr int nper = 4 * wd + 1;
+    constexpr int kCoIt = (W * D + 32 * kCoWarps - 1) / (32 * kCoWarps);   // (flip, channel) items per thread
     const Geom &g = a.g;
     const int N = g.N, L = g.L, dout = g.dout;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1294,6 +1296,38 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
             wsl[q] = floor_mod(jj, W1);
             if (ok) valid |= 1u << q;
         }
+        // The epilogue's inputs from global memory (y, dchi, the embedding links, rho and
+        // the dOmega partials of the earlier layers), loaded now so that their latency
+        // hides behind the link contraction: thread tid owns items tid + 256 u of the
+        // (flip, channel) loops, warp w the (flip, output) pairs w + 8 u.
+        float pre_y[kCoIt], pre_dx[kCoIt], pre_el[kCoIt], pre_rho[kCoPk][D / 32];
+        double pre_part[kCoPk];
+#pragma unroll
+        for (int u = 0; u < kCoIt; ++u) {
+            const int it = tid + u * 32 * kCoWarps;
+            pre_y[u] = pre_dx[u] = pre_el[u] = 0.f;
+            if (it < W * d) {
+                const int q = it / d, c = it % d;
+                pre_y[u] = a.y[((b * L + lo) * N + i) * d + c];
+                if ((valid >> q) & 1u) {
+                    pre_dx[u] = DX[(lo * rows + (b * N + jq[q]) * W + q) * d + c];
+                    if (l > 1) pre_el[u] = a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kCoPk; ++u) {
+            const int pk = warp + u * kCoWarps, q = pk / dout, k = pk % dout;
+            pre_part[u] = 0.0;
+#pragma unroll
+            for (int h = 0; h < D / 32; ++h) pre_rho[u][h] = 0.f;
+            if (pk < W * dout && ((valid >> q) & 1u)) {
+                const float *rho = a.rho + ((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d;
+#pragma unroll
+                for (int h = 0; h < D / 32; ++h) pre_rho[u][h] = rho[lane + 32 * h];
+                if (lane == 0) pre_part[u] = PART[((b * N + jq[q]) * W + q) * dout + k];
+            }
+        }
         // Window of this site; then the next site's new flip into the slot released by the last one.
         if (nwin > 0) {
             const int pb = r & 1;
@@ -1384,7 +1418,10 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
             break;
         }
         // Reduce the partials per (q, c), add the slice Toeplitz and embedding terms.
-        for (int it = tid; it < W * d; it += blockDim.x) {
+#pragma unroll
+        for (int u = 0; u < kCoIt; ++u) {
+            const int it = tid + u * 32 * kCoWarps;
+            if (it >= W * d) break;
             const int q = it / d, c = it % d;
             float v = 0.f;
             if (nlink > 0) {
@@ -1399,7 +1436,7 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
                 if (l == 1) {
                     v += Gs[(q - wd + 2 * wd) * d + c] * a.w.e[c] * dsq;
                 } else {
-                    v += dsq * a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
+                    v += dsq * pre_el[u];
                     const float *ws = Win + ((size_t)(l - 2) * W1 + wsl[q]) * W * d;
                     for (int t2 = 0; t2 < W; ++t2)
                         if (site_ok(jq[q] - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * ws[t2 * d + c];
@@ -1409,14 +1446,16 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
         }
         __syncthreads();
         // z = y + V p, then the gate with dchi.
-        for (int it = tid; it < W * d; it += blockDim.x) {
+#pragma unroll
+        for (int u = 0; u < kCoIt; ++u) {
+            const int it = tid + u * 32 * kCoWarps;
+            if (it >= W * d) break;
             const int q = it / d, c = it % d;
-            float z = a.y[((b * L + lo) * N + i) * d + c];
+            float z = pre_y[u];
             const float *pr = pq + q * d;
 #pragma unroll 8
             for (int c2 = 0; c2 < d; ++c2) z = fmaf(VTs[c2 * d + c], pr[c2], z);
-            const float dx = ((valid >> q) & 1u) ? DX[(lo * rows + (b * N + jq[q]) * W + q) * d + c] : 0.f;
-            gq[it] = dx * z;
+            gq[it] = pre_dx[u] * z;
         }
         __syncthreads();
         // s^(l) = U g; written to S (next layers) and kept in pq for the dOmega partials.
@@ -1431,7 +1470,17 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
         }
         __syncthreads();
         // dOmega_k partial of (flip q, layer l): rho^(l)_k(i) . s, in FP64; one warp per (q, k).
-        for (int pk = warp; pk < W * dout; pk += kCoWarps) {
+#pragma unroll
+        for (int u = 0; u < kCoPk; ++u) {
+            const int pk = warp + u * kCoWarps, q = pk / dout, k = pk % dout;
+            if (pk >= W * dout || !((valid >> q) & 1u)) continue;
+            double v = 0.0;
+#pragma unroll
+            for (int h = 0; h < D / 32; ++h) v += (double)pre_rho[u][h] * (double)pq[q * d + lane + 32 * h];
+            v = warp_sum<double>(v);
+            if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] = pre_part[u] + v;
+        }
+        for (int pk = warp + kCoPk * kCoWarps; pk < W * dout; pk += kCoWarps) {
             const int q = pk / dout, k = pk % dout;
             if (!((valid >> q) & 1u)) continue;
             const float *rho = a.rho + ((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d;

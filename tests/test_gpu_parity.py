@@ -91,7 +91,9 @@ def test_lrtfim_n128_model_small_batch(dn, prec):
     (4, 32, 8, 2, 32, 2, 1, 77, 2, 1),     # ring, ragged run of sites
     (3, 32, 8, 1, 16, 1, 0, 50, 2, 2),     # W = 3, d_out = 1, wider link rows
     (6, 32, 8, 2, 32, 2, 0, 40, 2, 1),     # deepest layers fall back to the generic kernel
-    (4, 64, 8, 2, 32, 2, 0, 40, 2, 1),     # d = 64: generic kernel, two channels per lane
+    (4, 64, 8, 2, 32, 2, 0, 40, 2, 1),     # d = 64: cooperative FP32 kernel (FP64: generic kernel)
+    (6, 64, 8, 2, 32, 4, 1, 45, 3, 1),     # d = 64 ring, six layers, d_out = 4 (more (flip, output) pairs than prefetched)
+    (5, 64, 8, 1, 32, 1, 0, 29, 2, 1),     # d = 64, W = 3, d_out = 1
 ])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_all_single_flips_grouped(dn, case, prec):
