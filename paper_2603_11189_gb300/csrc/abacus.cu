@@ -1451,20 +1451,34 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
             const int it = tid + u * 32 * kCoWarps;
             if (it >= W * d) break;
             const int q = it / d, c = it % d;
-            float z = pre_y[u];
+            // four partial sums: the chain of dependent FMAs is a quarter as long
+            float z0 = pre_y[u], z1 = 0.f, z2 = 0.f, z3 = 0.f;
             const float *pr = pq + q * d;
-#pragma unroll 8
-            for (int c2 = 0; c2 < d; ++c2) z = fmaf(VTs[c2 * d + c], pr[c2], z);
-            gq[it] = pre_dx[u] * z;
+#pragma unroll 4
+            for (int c2 = 0; c2 < d; c2 += 4) {
+                const float4 pv = *reinterpret_cast<const float4 *>(pr + c2);
+                z0 = fmaf(VTs[c2 * d + c], pv.x, z0);
+                z1 = fmaf(VTs[(c2 + 1) * d + c], pv.y, z1);
+                z2 = fmaf(VTs[(c2 + 2) * d + c], pv.z, z2);
+                z3 = fmaf(VTs[(c2 + 3) * d + c], pv.w, z3);
+            }
+            gq[it] = pre_dx[u] * ((z0 + z1) + (z2 + z3));
         }
         __syncthreads();
         // s^(l) = U g; written to S (next layers) and kept in pq for the dOmega partials.
         for (int it = tid; it < W * d; it += blockDim.x) {
             const int q = it / d, c = it % d;
-            float s = 0.f;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             const float *gr = gq + q * d;
-#pragma unroll 8
-            for (int c2 = 0; c2 < d; ++c2) s = fmaf(UTs[c2 * d + c], gr[c2], s);
+#pragma unroll 4
+            for (int c2 = 0; c2 < d; c2 += 4) {
+                const float4 gv = *reinterpret_cast<const float4 *>(gr + c2);
+                s0 = fmaf(UTs[c2 * d + c], gv.x, s0);
+                s1 = fmaf(UTs[(c2 + 1) * d + c], gv.y, s1);
+                s2 = fmaf(UTs[(c2 + 2) * d + c], gv.z, s2);
+                s3 = fmaf(UTs[(c2 + 3) * d + c], gv.w, s3);
+            }
+            const float s = (s0 + s1) + (s2 + s3);
             pq[it] = s;
             if (l < L && ((valid >> q) & 1u)) S[(lo * rows + (b * N + jq[q]) * W + q) * d + c] = s;
         }
@@ -1753,12 +1767,13 @@ static cudaError_t launch_ab_coop(const AbArgs<float> &a, int l, float *S, const
         if (NS < 2) return cudaErrorNotSupported;
     }
     if (smem == 0) return cudaErrorNotSupported;
-    // Runs of R sites per CTA (one CTA per SM fits): R is chosen so that the runs make
-    // whole waves of 152 CTAs, with runs of at most 32 sites - a grid of 2.07 waves spent a
-    // third round on its last 11 CTAs.
+    // Runs of R sites per CTA (one CTA per SM fits with a link ring, two without): R is chosen
+    // so that the runs make whole waves of 152 (304) CTAs, with runs of at most 32 sites - a
+    // grid of 2.07 waves spent a third round on its last 11 CTAs.
     const long long sites = (long long)g.N * a.B;
-    const long long waves = (sites + 152LL * 32 - 1) / (152LL * 32);
-    long long R = (sites + 152 * waves - 1) / (152 * waves);
+    const long long slots = NS == 0 ? 2 * 152 : 152;   // link-free layers: two CTAs per SM fit
+    const long long waves = (sites + slots * 32 - 1) / (slots * 32);
+    long long R = (sites + slots * waves - 1) / (slots * waves);
     R = R < 2 ? 2 : (R > 32 ? 32 : R);
     dim3 grid((unsigned)((g.N + R - 1) / R), (unsigned)a.B);
     const int Ri = (int)R;
