@@ -803,14 +803,14 @@ __device__ __forceinline__ int floor_mod(int x, int m) {
 
 // Sums NV <= 16 values over the warp; lane t with even t ends up holding the total
 // of value (t >> 1) & 15 (recursive halving: 16 + 15 shuffles instead of 5 NV).
-__device__ __forceinline__ double warp_sum16(double (&v)[16], int lane) {
+__device__ __forceinline__ float warp_sum16(float (&v)[16], int lane) {
 #pragma unroll
     for (int h = 8, off = 16; h >= 1; h >>= 1, off >>= 1) {
         const bool up = (lane & off) != 0;
 #pragma unroll
         for (int u = 0; u < h; ++u) {
-            const double send = up ? v[u] : v[u + h];
-            const double keep = up ? v[u + h] : v[u];
+            const float send = up ? v[u] : v[u + h];
+            const float keep = up ? v[u + h] : v[u];
             v[u] = keep + __shfl_xor_sync(0xffffffffu, send, off);
         }
     }
@@ -1102,22 +1102,22 @@ __global__ void __launch_bounds__(32 * kStWarps, NS == 0 ? 2 : 1) k_ab_stream(Ab
                 sv[q] += u.x * gv.x + u.y * gv.y + u.z * gv.z + u.w * gv.w;
             }
         }
-        double part[16];
+        float part[16];   // FP32 dot over the 32 channels; summed over layers in FP64
 #pragma unroll
-        for (int u = 0; u < 16; ++u) part[u] = 0.0;
+        for (int u = 0; u < 16; ++u) part[u] = 0.f;
 #pragma unroll
         for (int q = 0; q < W; ++q) {
             if (q >= W || !((valid >> q) & 1u)) continue;
             if (l < L) S[(lo * rows + (b * N + jq[q]) * W + q) * d + c] = sv[q];
 #pragma unroll
             for (int k = 0; k < kStMaxDout; ++k)
-                if (q * kStMaxDout + k < 16) part[q * kStMaxDout + k] = (double)rh_c[k] * (double)sv[q];
+                if (q * kStMaxDout + k < 16) part[q * kStMaxDout + k] = rh_c[k] * sv[q];
         }
-        const double tot = warp_sum16(part, lane);
+        const float tot = warp_sum16(part, lane);
         const int idx = (lane >> 1) & 15, qi = idx / kStMaxDout, ki = idx % kStMaxDout;
         if (!(lane & 1) && qi < W && ki < dout && ((valid >> qi) & 1u)) {
             double *dst = PART + ((b * N + wrap(i + wd - qi)) * W + qi) * dout + ki;
-            *dst += tot;
+            *dst += (double)tot;
         }
         __syncwarp();
         y_c = y_n;
@@ -1488,20 +1488,22 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
         for (int u = 0; u < kCoPk; ++u) {
             const int pk = warp + u * kCoWarps, q = pk / dout, k = pk % dout;
             if (pk >= W * dout || !((valid >> q) & 1u)) continue;
-            double v = 0.0;
+            // FP32 dot over the channels (FP64 arithmetic is scarce on this part); the
+            // partials of the layers are summed in FP64
+            float v = 0.f;
 #pragma unroll
-            for (int h = 0; h < D / 32; ++h) v += (double)pre_rho[u][h] * (double)pq[q * d + lane + 32 * h];
-            v = warp_sum<double>(v);
-            if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] = pre_part[u] + v;
+            for (int h = 0; h < D / 32; ++h) v = fmaf(pre_rho[u][h], pq[q * d + lane + 32 * h], v);
+            v = warp_sum<float>(v);
+            if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] = pre_part[u] + (double)v;
         }
         for (int pk = warp + kCoPk * kCoWarps; pk < W * dout; pk += kCoWarps) {
             const int q = pk / dout, k = pk % dout;
             if (!((valid >> q) & 1u)) continue;
             const float *rho = a.rho + ((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d;
-            double v = 0.0;
-            for (int c = lane; c < d; c += 32) v += (double)rho[c] * (double)pq[q * d + c];
-            v = warp_sum<double>(v);
-            if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] += v;
+            float v = 0.f;
+            for (int c = lane; c < d; c += 32) v = fmaf(rho[c], pq[q * d + c], v);
+            v = warp_sum<float>(v);
+            if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] += (double)v;
         }
         __syncthreads();
     }
@@ -1520,6 +1522,416 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
             for (int pb = 0; pb < 2; ++pb)
                 if (wpend[pb]) mbar_wait(wmb + pb, wuse[pb] & 1u);
         __syncthreads();
+    }
+}
+
+// Warp-specialised form of k_ab_coop for the layers with link blocks (l > 2), FP32,
+// d = 64.  The link contraction of a site and its epilogue no longer alternate on the
+// same warps: the contraction of site r + 1 streams link chunks while the epilogue of
+// site r runs, so the CTA-wide steps of the epilogue no longer stall the HBM stream.
+//  * warps 0-7 (contraction): as in k_ab_coop, warp w streams row chunk w mod 4 of the
+//    link blocks of class w div 4 through its own ring of NS slots, and multiplies them
+//    with the slice states of the window; its per-flip partials go to one of two
+//    partial buffers.  Warp 0 also copies the next site's new flip into the window.
+//  * warps 8-11 (epilogue): reduce the partials, add the slice Toeplitz and embedding
+//    terms, the V and U matvecs with the gate, the states s^(l) (to S) and the dOmega
+//    partials; their global inputs are loaded before they wait for the partials.
+// Hand-offs are mbarriers: full[b] (all contraction threads arrive after writing partial
+// buffer b), empty[b] (the epilogue arrives once it has read buffer b and the window
+// slots of that site), and four window barriers by site (r mod 4).  The window has
+// W + 2 flip slots, so that the copy for site r + 1 only overwrites a flip that site r - 2
+// used last.  Every wait is bounded; a wait that gives up raises bit 4 of the cache flag
+// and sets the CTA's stop word, every role leaves its loop, and the copies in flight are
+// waited for (bounded) before the CTA ends.
+constexpr int kCoEpiWarps = 4;
+
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+// Barrier 1 over the epilogue warps, returning whether `ok` holds on every thread.
+__device__ __forceinline__ bool epi_all(bool ok) {
+    uint32_t r;
+    asm volatile("{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(r)
+                 : "r"((uint32_t)ok), "n"(32 * kCoEpiWarps)
+                 : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kCoEpiWarps) : "memory"); }
+
+template <int D, int WW, int NS>
+__global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
+    k_ab_coop_ws(AbArgs<float> a, int l, int R, float *__restrict__ S, const float *__restrict__ DX,
+                 double *__restrict__ PART, const __grid_constant__ CUtensorMap tmK) {
+    extern __shared__ __align__(1024) unsigned char smws[];
+    unsigned char *smraw = smws;
+    constexpr int d = D, dd = D * D, W = WW, wd = (WW - 1) / 2, W2 = W + 2;
+    constexpr int RC = 1024 / D;          // rows per 4 KB chunk
+    constexpr int CPB = dd / 1024;        // chunks per block
+    constexpr int WPJ = kCoWarps / CPB;   // warps per chunk row class
+    constexpr int nper = 4 * wd + 1;
+    constexpr int kET = 32 * kCoEpiWarps;                 // epilogue threads
+    constexpr int kEIt = (W * D + kET - 1) / kET;         // (flip, channel) items per epilogue thread
+    constexpr int kEPk = 3;                              // (flip, output) pairs per warp loaded early
+    const Geom &g = a.g;
+    const int N = g.N, L = g.L, dout = g.dout;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nwin = l - 1, nlink = l - 2;
+    if ((smem_addr(smraw) & 1023u) != 0u) {   // the swizzled ring needs 1024-byte-aligned slots
+        if (tid == 0) atomicOr(a.flag, 8u);
+        return;
+    }
+    float *Kring = reinterpret_cast<float *>(smraw);   // [8][NS][1024], 4 KB-aligned slots
+    float *VTs = Kring + kCoWarps * NS * 1024;         // [c'][c] = V[c][c']
+    float *UTs = VTs + dd;
+    float *Gs = UTs + dd;                              // [4w+1][d] taps g^(l)_{-2w..2w}
+    float *Zs = Gs + nper * d;                         // [d] zeros
+    float *Win = Zs + d;                               // [nwin][W + 2][W][d]
+    float *Pb = Win + nwin * W2 * W * d;               // [2][8][W][32] partial sums
+    float *pq = Pb + 2 * kCoWarps * W * 32;            // [W][d]
+    float *gq = pq + W * d;                            // [W][d]
+    uint64_t *mbw = reinterpret_cast<uint64_t *>(gq + W * d);   // [8][NS] ring
+    uint64_t *wmb = mbw + kCoWarps * NS;                         // [4] window, by site mod 4
+    uint64_t *full = wmb + 4;                                    // [2]
+    uint64_t *empty = full + 2;                                  // [2]
+    int *s_stop = reinterpret_cast<int *>(empty + 2);
+    int8_t *sps = reinterpret_cast<int8_t *>(s_stop + 2);
+    const long long lo = l - 1;
+    const long long b = blockIdx.y;
+    for (int q = tid; q < dd; q += blockDim.x) {
+        VTs[q] = a.w.VT[lo * dd + q];
+        UTs[q] = a.w.UT[lo * dd + q];
+    }
+    for (int q = tid; q < nper * d; q += blockDim.x) {
+        const int r = q / d - 2 * wd, cc = q % d;
+        const int row = g.periodic ? ((r % N) + N) % N : (r > -N && r < N ? r + N - 1 : -1);
+        Gs[q] = row >= 0 ? a.taps[(lo * g.R + row) * d + cc] : 0.f;
+    }
+    for (int q = tid; q < d; q += blockDim.x) Zs[q] = 0.f;
+    for (int q = tid; q < N; q += blockDim.x) sps[q] = a.spins[b * N + q];
+    if (tid == 0) {
+        for (int s = 0; s < kCoWarps * NS + 4; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbw + s)), "r"(1));
+        for (int s = 0; s < 2; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(full + s)), "r"(32 * kCoWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(empty + s)), "r"(1));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *s_stop = 0;
+    }
+    __syncthreads();
+    const int i0 = blockIdx.x * R;
+    const int nsite = N - i0 < R ? N - i0 : R;
+    if (nsite <= 0) return;
+    const long long rows = (long long)a.B * N * W;
+    const long long nRk = 2 * a.Rk + 1, nRl = 2 * a.Rl + 1;
+    auto wrap = [&](int x) -> int { return g.periodic ? floor_mod(x, N) : x; };
+    auto site_ok = [&](int k) -> bool { return g.periodic || (k >= 0 && k < N); };
+    auto stopped = [&]() -> bool { return *((volatile int *)s_stop) != 0; };
+    // flips of site i: slot q holds flip i + wd - q
+    auto flips_of = [&](int i, int (&jq)[W], int (&wsl)[W]) -> unsigned {
+        unsigned valid = 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int jj = i + wd - q;
+            const bool ok = site_ok(jj);
+            jq[q] = ok ? wrap(jj) : 0;
+            wsl[q] = floor_mod(jj, W2);
+            if (ok) valid |= 1u << q;
+        }
+        return valid;
+    };
+    if (warp < kCoWarps) {
+        // ------------------------------------------------------------ contraction --
+        auto flip_bytes = [&](int jj) -> uint32_t {
+            return site_ok(jj) ? (uint32_t)(nwin * W * d * sizeof(float)) : 0u;
+        };
+        auto issue_flip = [&](int jj, uint64_t *bar) {
+            if (!site_ok(jj)) return;
+            const int j = wrap(jj), slot = floor_mod(jj, W2);
+            for (int m = 1; m <= nwin; ++m)
+                bulk_copy(Win + ((m - 1) * W2 + slot) * W * d, S + ((m - 1) * rows + (b * N + j) * W) * d,
+                          (uint32_t)(W * d * sizeof(float)), bar);
+        };
+        const bool leader = warp == 0 && lane == 0;
+        int wissued = 0, wdone = 0;   // window phases armed / observed by this warp (leader's bookkeeping)
+        if (leader) {
+            uint32_t bytes = 0;
+            for (int jj = i0 - wd; jj <= i0 + wd; ++jj) bytes += flip_bytes(jj);
+            mbar_expect(wmb, bytes);
+            for (int jj = i0 - wd; jj <= i0 + wd; ++jj) issue_flip(jj, wmb);
+        }
+        wissued = 1;
+        // this warp's chunk stream
+        const int jrow = warp % CPB, bcls = warp / CPB;
+        const int nb_site = nlink * nper;
+        int my_per_site = 0;
+        for (int bb = bcls; bb < nb_site; bb += WPJ) ++my_per_site;
+        const int nchunk = nsite * my_per_site;
+        uint64_t *mb = mbw + warp * NS;
+        float *ring = Kring + warp * NS * 1024;
+        int iss_r = 0, iss_b = bcls, issued = 0, consumed = 0, iss_slot = 0, con_slot = 0;
+        uint32_t con_phase = 0;
+        auto iss_row = [&]() -> int {
+            const int m = iss_b / nper + 1, dl = iss_b % nper - 2 * wd;
+            const float *src = a.K + (((b * a.P + pair_index(l, m)) * N + (i0 + iss_r)) * nRk + (dl + a.Rk)) *
+                                         (long long)dd + jrow * 1024;
+            return (int)((src - a.K) / d);
+        };
+        auto iss_advance = [&]() {
+            iss_b += WPJ;
+            if (iss_b >= nb_site) {
+                iss_b = bcls;
+                ++iss_r;
+            }
+        };
+        if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (; issued < nchunk && issued < NS; ++issued) {
+            if (lane == 0) tma_chunk64(ring + iss_slot * 1024, &tmK, iss_row(), mb + iss_slot);
+            iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
+            iss_advance();
+        }
+        const int lrow = lane % RC, seg = lane / RC;      // chunk row, 32-column segment
+        bool failed = false;
+        for (int r = 0; r < nsite && !failed; ++r) {
+            const int i = i0 + r, buf = r & 1;
+            int jq[W], wsl[W];
+            const unsigned valid = flips_of(i, jq, wsl);
+            // partial buffer `buf` and the window slot of flip i - wd - 2 were released by the
+            // epilogue of site r - 2
+            bool ok = !stopped();
+            if (ok && r >= 2) ok = mbar_wait(empty + buf, ((r - 2) >> 1) & 1);
+            if (!__all_sync(0xffffffffu, ok)) {
+                failed = true;
+                break;
+            }
+            if (leader && r + 1 < nsite) {
+                const int jn = i + 1 + wd;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect(wmb + ((r + 1) & 3), flip_bytes(jn));   // 0 bytes: a plain arrive
+                issue_flip(jn, wmb + ((r + 1) & 3));
+            }
+            if (r + 1 < nsite) wissued = r + 2;
+            ok = mbar_wait(wmb + (r & 3), (r >> 2) & 1);
+            if (!__all_sync(0xffffffffu, ok)) {
+                failed = true;
+                break;
+            }
+            wdone = r + 1;
+            float acc[W], acc2[W];
+#pragma unroll
+            for (int q = 0; q < W; ++q) acc[q] = acc2[q] = 0.f;
+            for (int bb = bcls; bb < nb_site; bb += WPJ) {
+                ok = mbar_wait(mb + con_slot, con_phase);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    failed = true;
+                    break;
+                }
+                const int slot = con_slot;
+                ++consumed;
+                if (++con_slot == NS) {
+                    con_slot = 0;
+                    con_phase ^= 1u;
+                }
+                const int mi = bb / nper, dl = bb % nper - 2 * wd;
+                if (site_ok(i + dl)) {
+                    const float *wm = Win + (size_t)mi * W2 * W * d + seg * 32;
+                    const float *Kc = ring + slot * 1024 + (seg * RC + lrow) * 32;   // line seg * RC + lrow
+                    const int sw = lrow & 7;
+                    const float *sp[W];
+#pragma unroll
+                    for (int q = 0; q < W; ++q) {
+                        const int t2 = q + dl;
+                        sp[q] = (t2 >= 0 && t2 < W && ((valid >> q) & 1u)) ? wm + (wsl[q] * W + t2) * d : Zs;
+                    }
+#pragma unroll
+                    for (int s2 = 0; s2 < 8; s2 += 2) {
+                        const int ch0 = s2, ch1 = s2 + 1;
+                        const float4 k0 = *reinterpret_cast<const float4 *>(Kc + 4 * (ch0 ^ sw));
+                        const float4 k1 = *reinterpret_cast<const float4 *>(Kc + 4 * (ch1 ^ sw));
+#pragma unroll
+                        for (int q = 0; q < W; ++q) {
+                            const float4 s0 = *reinterpret_cast<const float4 *>(sp[q] + 4 * ch0);
+                            const float4 s1 = *reinterpret_cast<const float4 *>(sp[q] + 4 * ch1);
+                            acc[q] = fmaf(k0.x, s0.x, acc[q]);
+                            acc2[q] = fmaf(k1.x, s1.x, acc2[q]);
+                            acc[q] = fmaf(k0.y, s0.y, acc[q]);
+                            acc2[q] = fmaf(k1.y, s1.y, acc2[q]);
+                            acc[q] = fmaf(k0.z, s0.z, acc[q]);
+                            acc2[q] = fmaf(k1.z, s1.z, acc2[q]);
+                            acc[q] = fmaf(k0.w, s0.w, acc[q]);
+                            acc2[q] = fmaf(k1.w, s1.w, acc2[q]);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (issued < nchunk) {
+                    if (lane == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        tma_chunk64(ring + iss_slot * 1024, &tmK, iss_row(), mb + iss_slot);
+                    }
+                    ++issued;
+                    iss_slot = iss_slot + 1 == NS ? 0 : iss_slot + 1;
+                    iss_advance();
+                }
+            }
+            if (failed) break;
+            float *pb = Pb + ((size_t)buf * kCoWarps + warp) * W * 32;
+#pragma unroll
+            for (int q = 0; q < W; ++q) pb[q * 32 + lane] = acc[q] + acc2[q];
+            mbar_arrive_cta(full + buf);
+        }
+        if (failed) {
+            if (lane == 0) {
+                *((volatile int *)s_stop) = 1;
+                atomicOr(a.flag, 4u);
+            }
+            // Let the copies in flight land before the shared memory is released.
+            while (consumed < issued) {
+                mbar_wait(mb + con_slot, con_phase);
+                ++consumed;
+                if (++con_slot == NS) {
+                    con_slot = 0;
+                    con_phase ^= 1u;
+                }
+            }
+            if (leader)
+                for (int s = wdone; s < wissued; ++s) mbar_wait(wmb + (s & 3), (s >> 2) & 1);
+        }
+    } else {
+        // --------------------------------------------------------------- epilogue --
+        const int et = tid - 32 * kCoWarps, ew = warp - kCoWarps;
+        bool good = true;
+        for (int r = 0; r < nsite; ++r) {
+            const int i = i0 + r, buf = r & 1;
+            int jq[W], wsl[W];
+            const unsigned valid = flips_of(i, jq, wsl);
+            // Global inputs of this site, loaded before the wait for its partials: thread et
+            // owns items et + 128 u of the (flip, channel) loops, warp ew the (flip, output)
+            // pairs ew + 4 u.
+            float pre_y[kEIt], pre_dx[kEIt], pre_el[kEIt], pre_rho[kEPk][D / 32];
+            double pre_part[kEPk];
+#pragma unroll
+            for (int u = 0; u < kEIt; ++u) {
+                const int it = et + u * kET;
+                pre_y[u] = pre_dx[u] = pre_el[u] = 0.f;
+                if (it < W * d) {
+                    const int q = it / d, c = it % d;
+                    pre_y[u] = a.y[((b * L + lo) * N + i) * d + c];
+                    if ((valid >> q) & 1u) {
+                        pre_dx[u] = DX[(lo * rows + (b * N + jq[q]) * W + q) * d + c];
+                        pre_el[u] = a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kEPk; ++u) {
+                const int pk = ew + u * kCoEpiWarps, q = pk / dout, k = pk % dout;
+                pre_part[u] = 0.0;
+#pragma unroll
+                for (int h = 0; h < D / 32; ++h) pre_rho[u][h] = 0.f;
+                if (pk < W * dout && ((valid >> q) & 1u)) {
+                    const float *rho = a.rho + ((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d;
+#pragma unroll
+                    for (int h = 0; h < D / 32; ++h) pre_rho[u][h] = rho[lane + 32 * h];
+                    if (lane == 0) pre_part[u] = PART[((b * N + jq[q]) * W + q) * dout + k];
+                }
+            }
+            const bool ok = !stopped() && mbar_wait(full + buf, (r >> 1) & 1);
+            if (!epi_all(ok)) {
+                good = false;
+                break;
+            }
+            // Reduce the partials per (q, c), add the slice Toeplitz and embedding terms.
+            const float *pbuf = Pb + (size_t)buf * kCoWarps * W * 32;
+#pragma unroll
+            for (int u = 0; u < kEIt; ++u) {
+                const int it = et + u * kET;
+                if (it >= W * d) break;
+                const int q = it / d, c = it % d;
+                float v = 0.f;
+                const int jj = c / RC, rr = c % RC;
+#pragma unroll
+                for (int bc = 0; bc < WPJ; ++bc)
+#pragma unroll
+                    for (int sg = 0; sg < 32 / RC; ++sg) v += pbuf[((jj + bc * CPB) * W + q) * 32 + sg * RC + rr];
+                if ((valid >> q) & 1u) {
+                    const float dsq = (float)(-2 * sps[jq[q]]);
+                    v += dsq * pre_el[u];
+                    const float *ws = Win + ((size_t)(l - 2) * W2 + wsl[q]) * W * d;
+                    for (int t2 = 0; t2 < W; ++t2)
+                        if (site_ok(jq[q] - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * ws[t2 * d + c];
+                }
+                pq[it] = v;
+            }
+            epi_sync();
+            if (et == 0) mbar_arrive_cta(empty + buf);   // partials and window slots of site r read
+            // z = y + V p, then the gate with dchi.
+#pragma unroll
+            for (int u = 0; u < kEIt; ++u) {
+                const int it = et + u * kET;
+                if (it >= W * d) break;
+                const int q = it / d, c = it % d;
+                float z0 = pre_y[u], z1 = 0.f, z2 = 0.f, z3 = 0.f;
+                const float *pr = pq + q * d;
+#pragma unroll 4
+                for (int c2 = 0; c2 < d; c2 += 4) {
+                    const float4 pv = *reinterpret_cast<const float4 *>(pr + c2);
+                    z0 = fmaf(VTs[c2 * d + c], pv.x, z0);
+                    z1 = fmaf(VTs[(c2 + 1) * d + c], pv.y, z1);
+                    z2 = fmaf(VTs[(c2 + 2) * d + c], pv.z, z2);
+                    z3 = fmaf(VTs[(c2 + 3) * d + c], pv.w, z3);
+                }
+                gq[it] = pre_dx[u] * ((z0 + z1) + (z2 + z3));
+            }
+            epi_sync();
+            // s^(l) = U g; written to S (next layers) and kept in pq for the dOmega partials.
+#pragma unroll
+            for (int u = 0; u < kEIt; ++u) {
+                const int it = et + u * kET;
+                if (it >= W * d) break;
+                const int q = it / d, c = it % d;
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                const float *gr = gq + q * d;
+#pragma unroll 4
+                for (int c2 = 0; c2 < d; c2 += 4) {
+                    const float4 gv = *reinterpret_cast<const float4 *>(gr + c2);
+                    s0 = fmaf(UTs[c2 * d + c], gv.x, s0);
+                    s1 = fmaf(UTs[(c2 + 1) * d + c], gv.y, s1);
+                    s2 = fmaf(UTs[(c2 + 2) * d + c], gv.z, s2);
+                    s3 = fmaf(UTs[(c2 + 3) * d + c], gv.w, s3);
+                }
+                const float s = (s0 + s1) + (s2 + s3);
+                pq[it] = s;
+                if (l < L && ((valid >> q) & 1u)) S[(lo * rows + (b * N + jq[q]) * W + q) * d + c] = s;
+            }
+            epi_sync();
+            // dOmega_k partial of (flip q, layer l): rho^(l)_k(i) . s (FP32 dot, FP64 sum over layers).
+#pragma unroll
+            for (int u = 0; u < kEPk; ++u) {
+                const int pk = ew + u * kCoEpiWarps, q = pk / dout, k = pk % dout;
+                if (pk >= W * dout || !((valid >> q) & 1u)) continue;
+                float v = 0.f;
+#pragma unroll
+                for (int h = 0; h < D / 32; ++h) v = fmaf(pre_rho[u][h], pq[q * d + lane + 32 * h], v);
+                v = warp_sum<float>(v);
+                if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] = pre_part[u] + (double)v;
+            }
+            for (int pk = ew + kEPk * kCoEpiWarps; pk < W * dout; pk += kCoEpiWarps) {
+                const int q = pk / dout, k = pk % dout;
+                if (!((valid >> q) & 1u)) continue;
+                const float *rho = a.rho + ((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d;
+                float v = 0.f;
+                for (int c = lane; c < d; c += 32) v = fmaf(rho[c], pq[q * d + c], v);
+                v = warp_sum<float>(v);
+                if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] += (double)v;
+            }
+            epi_sync();   // pq and gq are rewritten by the next site
+        }
+        if (!good && et == 0) {
+            *((volatile int *)s_stop) = 1;
+            atomicOr(a.flag, 4u);
+        }
     }
 }
 
@@ -1756,6 +2168,41 @@ static cudaError_t launch_ab_coop_ns(const AbArgs<float> &a, int l, int R, int N
     }
 }
 
+// Shared memory of k_ab_coop_ws with NS ring slots per contraction warp; 0 if it does not fit.
+static size_t ab_coop_ws_smem(const Geom &g, int l, int NS) {
+    const size_t d = g.d, W = g.W, nwin = l - 1, nper = 4 * g.w + 1;
+    const size_t floats = 2 * d * d + nper * d + d + nwin * (W + 2) * W * d + 2 * (size_t)kCoWarps * W * 32 +
+                          2 * W * d + (size_t)kCoWarps * NS * 1024;
+    const size_t bytes = floats * sizeof(float) + ((size_t)kCoWarps * NS + 8) * sizeof(uint64_t) + 2 * sizeof(int) +
+                         (((size_t)g.N + 15) & ~(size_t)15);
+    return bytes <= 227 * 1024 ? bytes : 0;
+}
+
+template <int D, int WW, int NS>
+static cudaError_t launch_ab_coop_ws_one(const AbArgs<float> &a, int l, int R, dim3 grid, size_t smem, float *S,
+                                         const float *DX, double *PART, const CUtensorMap &tmK, cudaStream_t st) {
+    cudaError_t err =
+        cudaFuncSetAttribute(k_ab_coop_ws<D, WW, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    {
+        ProfScope _ps("k_ab_layer", st);
+        k_ab_coop_ws<D, WW, NS><<<grid, 32 * (kCoWarps + kCoEpiWarps), smem, st>>>(a, l, R, S, DX, PART, tmK);
+    }
+    return cudaGetLastError();
+}
+
+template <int D, int WW>
+static cudaError_t launch_ab_coop_ws_ns(const AbArgs<float> &a, int l, int R, int NS, dim3 grid, size_t smem,
+                                        float *S, const float *DX, double *PART, const CUtensorMap &tmK,
+                                        cudaStream_t st) {
+    switch (NS) {
+    case 2: return launch_ab_coop_ws_one<D, WW, 2>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    case 4: return launch_ab_coop_ws_one<D, WW, 4>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    case 6: return launch_ab_coop_ws_one<D, WW, 6>(a, l, R, grid, smem, S, DX, PART, tmK, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 static cudaError_t launch_ab_coop(const AbArgs<float> &a, int l, float *S, const float *DX, double *PART,
                                   cudaStream_t st) {
     const Geom &g = a.g;
@@ -1784,6 +2231,18 @@ static cudaError_t launch_ab_coop(const AbArgs<float> &a, int l, float *S, const
     if (l > 2) {
         const unsigned long long rows = (unsigned long long)a.B * a.P * g.N * (2ull * a.Rk + 1) * 64ull;
         if (g.d != 64 || !a.K || !link_rows_map(&tmK, a.K, rows, 64, 16)) return cudaErrorNotSupported;
+    }
+    if (l > 2) {
+        // Layers with link blocks: the warp-specialised kernel (contraction and epilogue
+        // overlapped), with the deepest ring that fits.
+        int NSw = 6;
+        size_t smw = 0;
+        for (; NSw >= 2; NSw -= 2)
+            if ((smw = ab_coop_ws_smem(g, l, NSw)) != 0) break;
+        if (NSw >= 2) {
+            if (g.W == 5) return launch_ab_coop_ws_ns<64, 5>(a, l, Ri, NSw, grid, smw, S, DX, PART, tmK, st);
+            if (g.W == 3) return launch_ab_coop_ws_ns<64, 3>(a, l, Ri, NSw, grid, smw, S, DX, PART, tmK, st);
+        }
     }
     if (g.d == 64 && g.W == 5) return launch_ab_coop_ns<64, 5>(a, l, Ri, NS, grid, smem, S, DX, PART, tmK, st);
     if (g.d == 64 && g.W == 3) return launch_ab_coop_ns<64, 3>(a, l, Ri, NS, grid, smem, S, DX, PART, tmK, st);

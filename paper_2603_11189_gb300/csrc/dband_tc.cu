@@ -247,17 +247,20 @@ __global__ void __launch_bounds__(kDbThreads, 1)
                 break;
             }
             tc::fence_after();
-            float z0[16], z1[16];
+            // both sites' accumulator columns in four loads, then one wait
+            uint32_t zr[32];
             const uint32_t zc0 = tmem + tlane + kDbZCol0 + (uint32_t)(j0 * kDbD + 16 * ch);
-            tc::tmem_ld8(zc0, z0);
-            tc::tmem_ld8(zc0 + 8, z0 + 8);
-            if (two) {
-                const uint32_t zc1 = tmem + tlane + kDbZCol0 + (uint32_t)(j1 * kDbD + 16 * ch);
-                tc::tmem_ld8(zc1, z1);
-                tc::tmem_ld8(zc1 + 8, z1 + 8);
-            } else {
+            const uint32_t zc1 = tmem + tlane + kDbZCol0 + (uint32_t)((two ? j1 : j0) * kDbD + 16 * ch);
+            tc::tmem_ld8_async(zc0, zr);
+            tc::tmem_ld8_async(zc0 + 8, zr + 8);
+            tc::tmem_ld8_async(zc1, zr + 16);
+            tc::tmem_ld8_async(zc1 + 8, zr + 24);
+            tc::tmem_wait_ld(zr, 32);
+            float z0[16], z1[16];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) z1[c] = 0.f;
+            for (int c = 0; c < 16; ++c) {
+                z0[c] = __uint_as_float(zr[c]);
+                z1[c] = two ? __uint_as_float(zr[16 + c]) : 0.f;
             }
             tc::fence_before();
             __syncwarp();

@@ -123,6 +123,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Issue a load of 8 columns into raw registers without waiting; tmem_wait_ld() waits for
+// every load issued before it, after which the registers may be read.
+__device__ __forceinline__ void tmem_ld8_async(uint32_t taddr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t *r, int n) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // the registers are live across the wait: a no-op that ties them to it
+    for (int j = 0; j < n; ++j) asm volatile("" : "+r"(r[j]));
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
