@@ -1802,41 +1802,51 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
         // --------------------------------------------------------------- epilogue --
         const int et = tid - 32 * kCoWarps, ew = warp - kCoWarps;
         bool good = true;
-        for (int r = 0; r < nsite; ++r) {
-            const int i = i0 + r, buf = r & 1;
+        // Global inputs of a site: thread et owns items et + 128 u of the (flip, channel) loops,
+        // warp ew the (flip, output) pairs ew + 4 u.  They are loaded a site ahead, so that their
+        // latency hides behind the previous site's epilogue.
+        struct EIn {
+            float y[kEIt], dx[kEIt], el[kEIt], rho[kEPk][D / 32];
+            double part[kEPk];
+        };
+        auto load_in = [&](int i, EIn &v) {
             int jq[W], wsl[W];
             const unsigned valid = flips_of(i, jq, wsl);
-            // Global inputs of this site, loaded before the wait for its partials: thread et
-            // owns items et + 128 u of the (flip, channel) loops, warp ew the (flip, output)
-            // pairs ew + 4 u.
-            float pre_y[kEIt], pre_dx[kEIt], pre_el[kEIt], pre_rho[kEPk][D / 32];
-            double pre_part[kEPk];
 #pragma unroll
             for (int u = 0; u < kEIt; ++u) {
                 const int it = et + u * kET;
-                pre_y[u] = pre_dx[u] = pre_el[u] = 0.f;
+                v.y[u] = v.dx[u] = v.el[u] = 0.f;
                 if (it < W * d) {
                     const int q = it / d, c = it % d;
-                    pre_y[u] = a.y[((b * L + lo) * N + i) * d + c];
+                    v.y[u] = a.y[((b * L + lo) * N + i) * d + c];
                     if ((valid >> q) & 1u) {
-                        pre_dx[u] = DX[(lo * rows + (b * N + jq[q]) * W + q) * d + c];
-                        pre_el[u] = a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
+                        v.dx[u] = DX[(lo * rows + (b * N + jq[q]) * W + q) * d + c];
+                        v.el[u] = a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < kEPk; ++u) {
                 const int pk = ew + u * kCoEpiWarps, q = pk / dout, k = pk % dout;
-                pre_part[u] = 0.0;
+                v.part[u] = 0.0;
 #pragma unroll
-                for (int h = 0; h < D / 32; ++h) pre_rho[u][h] = 0.f;
+                for (int h = 0; h < D / 32; ++h) v.rho[u][h] = 0.f;
                 if (pk < W * dout && ((valid >> q) & 1u)) {
                     const float *rho = a.rho + ((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d;
 #pragma unroll
-                    for (int h = 0; h < D / 32; ++h) pre_rho[u][h] = rho[lane + 32 * h];
-                    if (lane == 0) pre_part[u] = PART[((b * N + jq[q]) * W + q) * dout + k];
+                    for (int h = 0; h < D / 32; ++h) v.rho[u][h] = rho[lane + 32 * h];
+                    if (lane == 0) v.part[u] = PART[((b * N + jq[q]) * W + q) * dout + k];
                 }
             }
+        };
+        EIn cur, nxt;
+        load_in(i0, cur);
+        nxt = cur;
+        for (int r = 0; r < nsite; ++r) {
+            const int i = i0 + r, buf = r & 1;
+            int jq[W], wsl[W];
+            const unsigned valid = flips_of(i, jq, wsl);
+            if (r + 1 < nsite) load_in(i + 1, nxt);
             const bool ok = !stopped() && mbar_wait(full + buf, (r >> 1) & 1);
             if (!epi_all(ok)) {
                 good = false;
@@ -1857,7 +1867,7 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                     for (int sg = 0; sg < 32 / RC; ++sg) v += pbuf[((jj + bc * CPB) * W + q) * 32 + sg * RC + rr];
                 if ((valid >> q) & 1u) {
                     const float dsq = (float)(-2 * sps[jq[q]]);
-                    v += dsq * pre_el[u];
+                    v += dsq * cur.el[u];
                     const float *ws = Win + ((size_t)(l - 2) * W2 + wsl[q]) * W * d;
                     for (int t2 = 0; t2 < W; ++t2)
                         if (site_ok(jq[q] - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * ws[t2 * d + c];
@@ -1872,7 +1882,7 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                 const int it = et + u * kET;
                 if (it >= W * d) break;
                 const int q = it / d, c = it % d;
-                float z0 = pre_y[u], z1 = 0.f, z2 = 0.f, z3 = 0.f;
+                float z0 = cur.y[u], z1 = 0.f, z2 = 0.f, z3 = 0.f;
                 const float *pr = pq + q * d;
 #pragma unroll 4
                 for (int c2 = 0; c2 < d; c2 += 4) {
@@ -1882,7 +1892,7 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                     z2 = fmaf(VTs[(c2 + 2) * d + c], pv.z, z2);
                     z3 = fmaf(VTs[(c2 + 3) * d + c], pv.w, z3);
                 }
-                gq[it] = pre_dx[u] * ((z0 + z1) + (z2 + z3));
+                gq[it] = cur.dx[u] * ((z0 + z1) + (z2 + z3));
             }
             epi_sync();
             // s^(l) = U g; written to S (next layers) and kept in pq for the dOmega partials.
@@ -1913,9 +1923,9 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                 if (pk >= W * dout || !((valid >> q) & 1u)) continue;
                 float v = 0.f;
 #pragma unroll
-                for (int h = 0; h < D / 32; ++h) v = fmaf(pre_rho[u][h], pq[q * d + lane + 32 * h], v);
+                for (int h = 0; h < D / 32; ++h) v = fmaf(cur.rho[u][h], pq[q * d + lane + 32 * h], v);
                 v = warp_sum<float>(v);
-                if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] = pre_part[u] + (double)v;
+                if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] = cur.part[u] + (double)v;
             }
             for (int pk = ew + kEPk * kCoEpiWarps; pk < W * dout; pk += kCoEpiWarps) {
                 const int q = pk / dout, k = pk % dout;
@@ -1927,11 +1937,234 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                 if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] += (double)v;
             }
             epi_sync();   // pq and gq are rewritten by the next site
+            cur = nxt;
         }
         if (!good && et == 0) {
             *((volatile int *)s_stop) = 1;
             atomicOr(a.flag, 4u);
         }
+    }
+}
+
+// The link-free layers (l <= 2: no interlayer link block, at most one window of slice
+// states) of an FP32 cache with d = 64 and d_out <= 2.  Their work per site is small
+// (two 64 x 64 matvecs on W flips) and bounded by latency, so every warp walks its own
+// run of R sites with no CTA-wide step, 16 warps per CTA: lane t owns channels t and
+// t + 32.  The per-warp window of layer-1 slice states (l = 2) is kept as in
+// k_ab_stream: W + 1 flip slots, one bulk copy per new flip, issued a site early.  Every
+// wait is bounded; a timeout raises bit 4 of the cache flag and the warp lets its copies
+// land before it ends.
+constexpr int kLfWarps = 16;
+
+template <int WW>
+__global__ void __launch_bounds__(32 * kLfWarps, 1) k_ab_lf64(AbArgs<float> a, int l, int R, float *__restrict__ S,
+                                                              const float *__restrict__ DX,
+                                                              double *__restrict__ PART) {
+    extern __shared__ __align__(16) unsigned char smlf[];
+    constexpr int d = 64, dd = d * d, W = WW, wd = (WW - 1) / 2, W1 = W + 1, nper = 4 * wd + 1;
+    const Geom &g = a.g;
+    const int N = g.N, L = g.L, dout = g.dout;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwin = l - 1;
+    float *VTs = reinterpret_cast<float *>(smlf);   // [k/4][c][k%4]: one 16-byte load = rows k..k+3 of column c
+    float *UTs = VTs + dd;
+    float *Gs = UTs + dd;                           // [4w+1][d] taps g^(l)_{-2w..2w}
+    const int per_warp = nwin * W1 * W * d + 2 * W * d;
+    float *Win = Gs + nper * d + (size_t)warp * per_warp;   // [nwin][W+1][W][d]
+    float *pq = Win + nwin * W1 * W * d;                    // [W][d]
+    float *gq = pq + W * d;                                 // [W][d]
+    uint64_t *wmb = reinterpret_cast<uint64_t *>(Gs + nper * d + (size_t)kLfWarps * per_warp) + 2 * warp;
+    int8_t *sps = reinterpret_cast<int8_t *>(reinterpret_cast<uint64_t *>(Gs + nper * d + (size_t)kLfWarps * per_warp) +
+                                             2 * kLfWarps);
+    const long long lo = l - 1;
+    const long long b = blockIdx.y;
+    for (int q = threadIdx.x; q < dd; q += blockDim.x) {
+        const int k = q / d, cc = q % d, x = ((k >> 2) * d + cc) * 4 + (k & 3);
+        VTs[x] = a.w.VT[lo * dd + q];
+        UTs[x] = a.w.UT[lo * dd + q];
+    }
+    for (int q = threadIdx.x; q < nper * d; q += blockDim.x) {
+        const int r = q / d - 2 * wd, cc = q % d;
+        const int row = g.periodic ? ((r % N) + N) % N : (r > -N && r < N ? r + N - 1 : -1);
+        Gs[q] = row >= 0 ? a.taps[(lo * g.R + row) * d + cc] : 0.f;
+    }
+    for (int q = threadIdx.x; q < N; q += blockDim.x) sps[q] = a.spins[b * N + q];
+    if (lane == 0) {
+        for (int s = 0; s < 2; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(wmb + s)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    const int i0 = (blockIdx.x * kLfWarps + warp) * R;
+    const int nsite = N - i0 < R ? N - i0 : R;
+    if (nsite <= 0) return;
+    const long long rows = (long long)a.B * N * W;
+    const long long nRl = 2 * a.Rl + 1;
+    auto wrap = [&](int x) -> int { return g.periodic ? floor_mod(x, N) : x; };
+    auto site_ok = [&](int k) -> bool { return g.periodic || (k >= 0 && k < N); };
+    // Window copies (l = 2): flip jj (unwrapped) of layer 1 into slot jj mod (W+1).
+    auto issue_flip = [&](int jj, uint64_t *bar) {
+        if (!site_ok(jj)) return;
+        bulk_copy(Win + floor_mod(jj, W1) * W * d, S + (b * N + wrap(jj)) * W * d, (uint32_t)(W * d * sizeof(float)),
+                  bar);
+    };
+    auto flip_bytes = [&](int jj) -> uint32_t { return site_ok(jj) ? (uint32_t)(W * d * sizeof(float)) : 0u; };
+    uint32_t wpend[2] = {0u, 0u}, wuse[2] = {0u, 0u};
+    if (nwin > 0) {
+        uint32_t bytes = 0;
+        for (int jj = i0 - wd; jj <= i0 + wd; ++jj) bytes += flip_bytes(jj);
+        if (lane == 0 && bytes) {
+            mbar_expect(wmb, bytes);
+            for (int jj = i0 - wd; jj <= i0 + wd; ++jj) issue_flip(jj, wmb);
+        }
+        wpend[0] = bytes ? 1u : 0u;
+    }
+    float e_h[2] = {0.f, 0.f};
+    if (l == 1) {
+        e_h[0] = a.w.e[lane];
+        e_h[1] = a.w.e[lane + 32];
+    }
+    // Per-site inputs of site r (cur) and r + 1 (nxt), channels lane and lane + 32.
+    struct In {
+        float y[2], dx[W][2], el[W][2], rh[kStMaxDout][2];
+    };
+    auto load_site = [&](int i, In &v) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            v.y[h] = a.y[((b * L + lo) * N + i) * d + c];
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                v.dx[q][h] = 0.f;
+                v.el[q][h] = 0.f;
+                const int jj = i + wd - q;
+                if (!site_ok(jj)) continue;
+                v.dx[q][h] = DX[(lo * rows + (b * N + wrap(jj)) * W + q) * d + c];
+                if (l >= 2) v.el[q][h] = a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
+            }
+#pragma unroll
+            for (int k = 0; k < kStMaxDout; ++k)
+                v.rh[k][h] = k < dout ? a.rho[((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d + c] : 0.f;
+        }
+    };
+    In cur, nxt;
+    load_site(i0, cur);
+    nxt = cur;
+    bool timed_out = false;
+    for (int r = 0; r < nsite; ++r) {
+        const int i = i0 + r;
+        int jq[W], wsl[W];
+        float dsq[W];
+        unsigned valid = 0;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int jj = i + wd - q;
+            const bool ok = site_ok(jj);
+            jq[q] = ok ? wrap(jj) : 0;
+            wsl[q] = floor_mod(jj, W1);
+            dsq[q] = ok ? (float)(-2 * sps[jq[q]]) : 0.f;
+            if (ok) valid |= 1u << q;
+        }
+        if (nwin > 0) {
+            const int pb = r & 1;
+            if (wpend[pb]) {
+                if (!mbar_wait(wmb + pb, wuse[pb] & 1u)) {
+                    timed_out = true;
+                    break;
+                }
+                wuse[pb]++;
+                wpend[pb] = 0;
+            }
+            if (r + 1 < nsite) {
+                const int jn = i + 1 + wd;
+                const uint32_t bytes = flip_bytes(jn);
+                if (lane == 0 && bytes) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect(wmb + (pb ^ 1), bytes);
+                    issue_flip(jn, wmb + (pb ^ 1));
+                }
+                wpend[pb ^ 1] = bytes ? 1u : 0u;
+            }
+        }
+        if (r + 1 < nsite) load_site(i + 1, nxt);
+        // p: slice Toeplitz and embedding terms (l = 2) or the embedding column (l = 1).
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                float v = 0.f;
+                if ((valid >> q) & 1u) {
+                    if (l == 1) {
+                        v = Gs[(q - wd + 2 * wd) * d + c] * e_h[h] * dsq[q];
+                    } else {
+                        v = dsq[q] * cur.el[q][h];
+                        const float *ws = Win + wsl[q] * W * d;
+                        for (int t2 = 0; t2 < W; ++t2)
+                            if (site_ok(jq[q] - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * ws[t2 * d + c];
+                    }
+                }
+                pq[q * d + c] = v;
+            }
+        }
+        __syncwarp();
+        // z = y + V p, gate with dchi
+        float z[W][2];
+#pragma unroll
+        for (int q = 0; q < W; ++q) z[q][0] = z[q][1] = 0.f;
+#pragma unroll 2
+        for (int c2 = 0; c2 < d; c2 += 4) {
+            const float4 v0 = *reinterpret_cast<const float4 *>(VTs + ((c2 >> 2) * d + lane) * 4);
+            const float4 v1 = *reinterpret_cast<const float4 *>(VTs + ((c2 >> 2) * d + lane + 32) * 4);
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                const float4 pv = *reinterpret_cast<const float4 *>(pq + q * d + c2);
+                z[q][0] += v0.x * pv.x + v0.y * pv.y + v0.z * pv.z + v0.w * pv.w;
+                z[q][1] += v1.x * pv.x + v1.y * pv.y + v1.z * pv.z + v1.w * pv.w;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < W; ++q)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) gq[q * d + lane + 32 * h] = cur.dx[q][h] * (cur.y[h] + z[q][h]);
+        __syncwarp();
+        // s = U g
+#pragma unroll
+        for (int q = 0; q < W; ++q) z[q][0] = z[q][1] = 0.f;
+#pragma unroll 2
+        for (int c2 = 0; c2 < d; c2 += 4) {
+            const float4 u0 = *reinterpret_cast<const float4 *>(UTs + ((c2 >> 2) * d + lane) * 4);
+            const float4 u1 = *reinterpret_cast<const float4 *>(UTs + ((c2 >> 2) * d + lane + 32) * 4);
+#pragma unroll
+            for (int q = 0; q < W; ++q) {
+                const float4 gv = *reinterpret_cast<const float4 *>(gq + q * d + c2);
+                z[q][0] += u0.x * gv.x + u0.y * gv.y + u0.z * gv.z + u0.w * gv.w;
+                z[q][1] += u1.x * gv.x + u1.y * gv.y + u1.z * gv.z + u1.w * gv.w;
+            }
+        }
+        float part[16];   // FP32 dot over the channels; summed over layers in FP64
+#pragma unroll
+        for (int u = 0; u < 16; ++u) part[u] = 0.f;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            if (!((valid >> q) & 1u)) continue;
+            if (l < L)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) S[(lo * rows + (b * N + jq[q]) * W + q) * d + lane + 32 * h] = z[q][h];
+#pragma unroll
+            for (int k = 0; k < kStMaxDout; ++k)
+                if (q * kStMaxDout + k < 16) part[q * kStMaxDout + k] = cur.rh[k][0] * z[q][0] + cur.rh[k][1] * z[q][1];
+        }
+        const float tot = warp_sum16(part, lane);
+        const int idx = (lane >> 1) & 15, qi = idx / kStMaxDout, ki = idx % kStMaxDout;
+        if (!(lane & 1) && qi < W && ki < dout && ((valid >> qi) & 1u))
+            PART[((b * N + wrap(i + wd - qi)) * W + qi) * dout + ki] += (double)tot;
+        __syncwarp();   // pq and gq are rewritten by the next site
+        cur = nxt;
+    }
+    if (timed_out) {
+        if (lane == 0) atomicOr(a.flag, 4u);
+        for (int pb = 0; pb < 2; ++pb)
+            if (wpend[pb]) mbar_wait(wmb + pb, wuse[pb] & 1u);
     }
 }
 
@@ -2203,9 +2436,41 @@ static cudaError_t launch_ab_coop_ws_ns(const AbArgs<float> &a, int l, int R, in
     }
 }
 
+// Shared memory of k_ab_lf64; 0 if it does not fit.
+static size_t ab_lf64_smem(const Geom &g, int l) {
+    const size_t d = 64, W = g.W, nwin = l - 1, nper = 4 * g.w + 1;
+    const size_t per_warp = nwin * (W + 1) * W * d + 2 * W * d;
+    const size_t floats = 2 * d * d + nper * d + (size_t)kLfWarps * per_warp;
+    const size_t bytes = floats * sizeof(float) + 2 * (size_t)kLfWarps * sizeof(uint64_t) + (((size_t)g.N + 15) & ~(size_t)15);
+    return bytes <= 227 * 1024 ? bytes : 0;
+}
+
+template <int WW>
+static cudaError_t launch_ab_lf64(const AbArgs<float> &a, int l, float *S, const float *DX, double *PART,
+                                  size_t smem, cudaStream_t st) {
+    const Geom &g = a.g;
+    cudaError_t err = cudaFuncSetAttribute(k_ab_lf64<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    // Runs of R sites per warp, R chosen so that the warps of one CTA per SM cover the sites.
+    const long long sites = (long long)g.N * a.B, slots = 152LL * kLfWarps;
+    long long R = (sites + slots - 1) / slots;
+    R = R < 1 ? 1 : (R > 32 ? 32 : R);
+    dim3 grid((unsigned)((g.N + kLfWarps * R - 1) / (kLfWarps * R)), (unsigned)a.B);
+    {
+        ProfScope _ps("k_ab_layer", st);
+        k_ab_lf64<WW><<<grid, 32 * kLfWarps, smem, st>>>(a, l, (int)R, S, DX, PART);
+    }
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_ab_coop(const AbArgs<float> &a, int l, float *S, const float *DX, double *PART,
                                   cudaStream_t st) {
     const Geom &g = a.g;
+    if (l <= 2 && g.d == 64 && g.dout <= kStMaxDout) {
+        const size_t sml = ab_lf64_smem(g, l);
+        if (sml && g.W == 5) return launch_ab_lf64<5>(a, l, S, DX, PART, sml, st);
+        if (sml && g.W == 3) return launch_ab_lf64<3>(a, l, S, DX, PART, sml, st);
+    }
     int NS = 0;
     size_t smem = ab_coop_smem(g, l, 0);
     if (l > 2) {
