@@ -438,7 +438,7 @@ cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T>
 //  k_ab_final    dOmega_j = sum_t partial + t_j dsigma_j, and the log cosh difference.
 // Every link byte of a configuration is read once per call.
 constexpr int kLayMaxW = 9;
-constexpr int kDxTPB = 8;   // row tiles per CTA of k_dchi_table
+constexpr int kDxTPB = 8;   // most row tiles per CTA of k_dchi_table (fewer when the grid would not fill the GPU)
 
 // One CTA per (64 (flip, slot) rows, layer).  The MLP weights are staged once; the
 // activations are kept transposed ([feature][row]) so that a thread (output feature, group
@@ -447,7 +447,7 @@ constexpr int kDxTPB = 8;   // row tiles per CTA of k_dchi_table
 // flipped spin window of the row (W values) and the offset of the row's chi entry (-1
 // where slot site j - w + t lies off an open chain).
 template <typename T>
-__global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__ DX) {
+__global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__ DX, int tpb) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Geom &g = a.g;
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
@@ -465,8 +465,8 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
     const T *kap = a.w.kappa + (long long)l * W * dh, *beta = a.w.beta + (long long)l * dh;
     for (int q = threadIdx.x; q < dh * dh; q += blockDim.x) W1s[(q / dh) * (dh + 1) + q % dh] = W1T[q];
     for (int q = threadIdx.x; q < dh * d; q += blockDim.x) W2s[(q / d) * (d + 1) + q % d] = W2T[q];
-    for (int it = 0; it < kDxTPB; ++it) {
-        const long long r0 = ((long long)blockIdx.x * kDxTPB + it) * RT;
+    for (int it = 0; it < tpb; ++it) {
+        const long long r0 = ((long long)blockIdx.x * tpb + it) * RT;
         if (r0 >= rows) break;
         __syncthreads();   // the previous tile's reads of phT / acT / roff (and the weight staging) are done
         for (int rr = threadIdx.x; rr < RT; rr += blockDim.x) {
@@ -1802,51 +1802,41 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
         // --------------------------------------------------------------- epilogue --
         const int et = tid - 32 * kCoWarps, ew = warp - kCoWarps;
         bool good = true;
-        // Global inputs of a site: thread et owns items et + 128 u of the (flip, channel) loops,
-        // warp ew the (flip, output) pairs ew + 4 u.  They are loaded a site ahead, so that their
-        // latency hides behind the previous site's epilogue.
-        struct EIn {
-            float y[kEIt], dx[kEIt], el[kEIt], rho[kEPk][D / 32];
-            double part[kEPk];
-        };
-        auto load_in = [&](int i, EIn &v) {
+        for (int r = 0; r < nsite; ++r) {
+            const int i = i0 + r, buf = r & 1;
             int jq[W], wsl[W];
             const unsigned valid = flips_of(i, jq, wsl);
+            // Global inputs of this site, loaded before the wait for its partials: thread et
+            // owns items et + 128 u of the (flip, channel) loops, warp ew the (flip, output)
+            // pairs ew + 4 u.
+            float pre_y[kEIt], pre_dx[kEIt], pre_el[kEIt], pre_rho[kEPk][D / 32];
+            double pre_part[kEPk];
 #pragma unroll
             for (int u = 0; u < kEIt; ++u) {
                 const int it = et + u * kET;
-                v.y[u] = v.dx[u] = v.el[u] = 0.f;
+                pre_y[u] = pre_dx[u] = pre_el[u] = 0.f;
                 if (it < W * d) {
                     const int q = it / d, c = it % d;
-                    v.y[u] = a.y[((b * L + lo) * N + i) * d + c];
+                    pre_y[u] = a.y[((b * L + lo) * N + i) * d + c];
                     if ((valid >> q) & 1u) {
-                        v.dx[u] = DX[(lo * rows + (b * N + jq[q]) * W + q) * d + c];
-                        v.el[u] = a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
+                        pre_dx[u] = DX[(lo * rows + (b * N + jq[q]) * W + q) * d + c];
+                        pre_el[u] = a.ell[((b * (L - 1) + (l - 2)) * N + i) * nRl * d + (wd - q + a.Rl) * d + c];
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < kEPk; ++u) {
                 const int pk = ew + u * kCoEpiWarps, q = pk / dout, k = pk % dout;
-                v.part[u] = 0.0;
+                pre_part[u] = 0.0;
 #pragma unroll
-                for (int h = 0; h < D / 32; ++h) v.rho[u][h] = 0.f;
+                for (int h = 0; h < D / 32; ++h) pre_rho[u][h] = 0.f;
                 if (pk < W * dout && ((valid >> q) & 1u)) {
                     const float *rho = a.rho + ((b * L + lo) * dout + k) * (long long)N * d + (long long)i * d;
 #pragma unroll
-                    for (int h = 0; h < D / 32; ++h) v.rho[u][h] = rho[lane + 32 * h];
-                    if (lane == 0) v.part[u] = PART[((b * N + jq[q]) * W + q) * dout + k];
+                    for (int h = 0; h < D / 32; ++h) pre_rho[u][h] = rho[lane + 32 * h];
+                    if (lane == 0) pre_part[u] = PART[((b * N + jq[q]) * W + q) * dout + k];
                 }
             }
-        };
-        EIn cur, nxt;
-        load_in(i0, cur);
-        nxt = cur;
-        for (int r = 0; r < nsite; ++r) {
-            const int i = i0 + r, buf = r & 1;
-            int jq[W], wsl[W];
-            const unsigned valid = flips_of(i, jq, wsl);
-            if (r + 1 < nsite) load_in(i + 1, nxt);
             const bool ok = !stopped() && mbar_wait(full + buf, (r >> 1) & 1);
             if (!epi_all(ok)) {
                 good = false;
@@ -1867,7 +1857,7 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                     for (int sg = 0; sg < 32 / RC; ++sg) v += pbuf[((jj + bc * CPB) * W + q) * 32 + sg * RC + rr];
                 if ((valid >> q) & 1u) {
                     const float dsq = (float)(-2 * sps[jq[q]]);
-                    v += dsq * cur.el[u];
+                    v += dsq * pre_el[u];
                     const float *ws = Win + ((size_t)(l - 2) * W2 + wsl[q]) * W * d;
                     for (int t2 = 0; t2 < W; ++t2)
                         if (site_ok(jq[q] - wd + t2)) v += Gs[(q - t2 + 2 * wd) * d + c] * ws[t2 * d + c];
@@ -1882,7 +1872,7 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                 const int it = et + u * kET;
                 if (it >= W * d) break;
                 const int q = it / d, c = it % d;
-                float z0 = cur.y[u], z1 = 0.f, z2 = 0.f, z3 = 0.f;
+                float z0 = pre_y[u], z1 = 0.f, z2 = 0.f, z3 = 0.f;
                 const float *pr = pq + q * d;
 #pragma unroll 4
                 for (int c2 = 0; c2 < d; c2 += 4) {
@@ -1892,7 +1882,7 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                     z2 = fmaf(VTs[(c2 + 2) * d + c], pv.z, z2);
                     z3 = fmaf(VTs[(c2 + 3) * d + c], pv.w, z3);
                 }
-                gq[it] = cur.dx[u] * ((z0 + z1) + (z2 + z3));
+                gq[it] = pre_dx[u] * ((z0 + z1) + (z2 + z3));
             }
             epi_sync();
             // s^(l) = U g; written to S (next layers) and kept in pq for the dOmega partials.
@@ -1923,9 +1913,9 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                 if (pk >= W * dout || !((valid >> q) & 1u)) continue;
                 float v = 0.f;
 #pragma unroll
-                for (int h = 0; h < D / 32; ++h) v = fmaf(cur.rho[u][h], pq[q * d + lane + 32 * h], v);
+                for (int h = 0; h < D / 32; ++h) v = fmaf(pre_rho[u][h], pq[q * d + lane + 32 * h], v);
                 v = warp_sum<float>(v);
-                if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] = cur.part[u] + (double)v;
+                if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] = pre_part[u] + (double)v;
             }
             for (int pk = ew + kEPk * kCoEpiWarps; pk < W * dout; pk += kCoEpiWarps) {
                 const int q = pk / dout, k = pk % dout;
@@ -1937,7 +1927,6 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
                 if (lane == 0) PART[((b * N + jq[q]) * W + q) * dout + k] += (double)v;
             }
             epi_sync();   // pq and gq are rewritten by the next site
-            cur = nxt;
         }
         if (!good && et == 0) {
             *((volatile int *)s_stop) = 1;
@@ -2536,7 +2525,12 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
         return err;
     {
         ProfScope _ps("k_dchi_table", st);
-        k_dchi_table<T><<<dim3((unsigned)((rows + 64 * kDxTPB - 1) / (64 * kDxTPB)), g.L), 256, tsm, st>>>(a, DX);
+        // Tiles of 64 rows, up to kDxTPB per CTA (the weights are staged once per CTA), but
+        // enough CTAs for four per SM.
+        const long long tiles = (rows + 63) / 64;
+        long long tpb = (tiles * g.L + 4 * 152 - 1) / (4 * 152);
+        tpb = tpb < 1 ? 1 : (tpb > kDxTPB ? kDxTPB : tpb);
+        k_dchi_table<T><<<dim3((unsigned)((tiles + tpb - 1) / tpb), g.L), 256, tsm, st>>>(a, DX, (int)tpb);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int hd = (g.d + 31) / 32;
