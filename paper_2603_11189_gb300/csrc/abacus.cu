@@ -1533,7 +1533,7 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
 //    link blocks of class w div 4 through its own ring of NS slots, and multiplies them
 //    with the slice states of the window; its per-flip partials go to one of two
 //    partial buffers.  Warp 0 also copies the next site's new flip into the window.
-//  * warps 8-11 (epilogue): reduce the partials, add the slice Toeplitz and embedding
+//  * warps 8-15 (epilogue): reduce the partials, add the slice Toeplitz and embedding
 //    terms, the V and U matvecs with the gate, the states s^(l) (to S) and the dOmega
 //    partials; their global inputs are loaded before they wait for the partials.
 // Hand-offs are mbarriers: full[b] (all contraction threads arrive after writing partial
@@ -1543,7 +1543,7 @@ __global__ void __launch_bounds__(32 * kCoWarps, NS == 0 ? 2 : 1) k_ab_coop(AbAr
 // used last.  Every wait is bounded; a wait that gives up raises bit 4 of the cache flag
 // and sets the CTA's stop word, every role leaves its loop, and the copies in flight are
 // waited for (bounded) before the CTA ends.
-constexpr int kCoEpiWarps = 4;
+constexpr int kCoEpiWarps = 8;
 
 __device__ __forceinline__ void mbar_arrive_cta(uint64_t *mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
@@ -1807,8 +1807,8 @@ __global__ void __launch_bounds__(32 * (kCoWarps + kCoEpiWarps), 1)
             int jq[W], wsl[W];
             const unsigned valid = flips_of(i, jq, wsl);
             // Global inputs of this site, loaded before the wait for its partials: thread et
-            // owns items et + 128 u of the (flip, channel) loops, warp ew the (flip, output)
-            // pairs ew + 4 u.
+            // owns items et + 256 u of the (flip, channel) loops, warp ew the (flip, output)
+            // pairs ew + 8 u.
             float pre_y[kEIt], pre_dx[kEIt], pre_el[kEIt], pre_rho[kEPk][D / 32];
             double pre_part[kEPk];
 #pragma unroll
