@@ -505,6 +505,258 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
     if (warp == 0) tc::tmem_free(tmem, TN);
 }
 
+// Warp-specialised form of k_tgemm_genp (used when its shared memory fits): the operand
+// generation of the next chunk, the MMAs of the current one and the epilogue of the
+// previous column tile run at the same time instead of one after the other.
+//  * warps 0-3 generate the B operand (column pp = thread, 64 sites per chunk, NPL BF16
+//    planes) into one of two buffers;
+//  * warp 8 (one thread) issues the MMAs of a chunk once its buffer is full, into one of
+//    two 128-column accumulators in tensor memory, and commits them to the buffer's empty
+//    barrier and, after the last chunk of a tile, to the accumulator's full barrier;
+//  * warps 4-7 drain an accumulator (TMEM lanes 32 (w - 4) ..): hop output through
+//    per-warp double-buffered 128B-swizzled staging tiles and TMA tensor stores, band
+//    rows from registers, and release the accumulator after their last tensor-memory
+//    load.
+// The products, their order and the epilogue's values are those of k_tgemm_genp.  Every
+// wait is bounded; a wait that gives up raises bit 8 of the flag, every role leaves its
+// loop, the MMAs issued are waited for and the tensor memory is released.
+constexpr int kGwThreads = 288;
+
+template <int NPL>
+static size_t tgemm_genp_ws_smem(int N, int d) {
+    const int nch = (N + kTcK - 1) / kTcK;
+    const size_t B = 2 * (size_t)NPL * 4 * 128 * 32, stg = 4 * 2 * 4096;
+    return B + stg + (size_t)nch * NPL * kHankelBytes +
+           ((size_t)((2 * N + 1) & ~1) + (size_t)N * d + ((size_t)(2 * N - 1) * d + 1) / 2 * 2) * sizeof(float) +
+           8 * sizeof(uint64_t) + 16;
+}
+
+template <int NPL, int DD>
+__global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const float *__restrict__ taps, int P,
+                                                                 const float *__restrict__ gtaps,
+                                                                 const float *__restrict__ gDm, long long dm_ss,
+                                                                 const __grid_constant__ CUtensorMap tmY,
+                                                                 float *__restrict__ band, long long bss,
+                                                                 long long brs, long long bos, int bR, int bns,
+                                                                 long long b0, unsigned *__restrict__ flag) {
+    extern __shared__ __align__(1024) unsigned char smgw[];
+    constexpr int TN = 128, kSlabB = TN * 16 * 2;
+    constexpr int kBbytes = NPL * 4 * kSlabB;
+    const int N = g.N;
+    constexpr int d = DD;
+    const int nch = (N + kTcK - 1) / kTcK;
+    unsigned char *Bbuf = smgw;                                   // [2][kBbytes]
+    unsigned char *Stg = smgw + 2 * kBbytes;                      // [4 warps][2][4096]
+    unsigned char *Aall = Stg + 4 * 2 * 4096;                     // [nch][NPL][kHankelBytes]
+    float *gx = reinterpret_cast<float *>(Aall + (size_t)nch * NPL * kHankelBytes);   // gx[r + N - 1], channel a
+    float *Dfull = gx + ((2 * N + 1) & ~1);                       // [N][d]: D0_n[a][c']
+    float *Tfull = Dfull + (size_t)N * d;                         // [2N - 1][d]: g_r[c'], row r + N - 1
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Tfull + ((size_t)(2 * N - 1) * d + 1) / 2 * 2);
+    uint64_t *bfull = bar, *bempty = bar + 2, *afull = bar + 4, *aempty = bar + 6;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 8);
+    int *s_ok = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.y * kTcM;
+    const long long za = blockIdx.z;
+    const int a = (int)(za % d);
+    const long long bl = za / d;
+    for (int q = tid; q < 2 * N - 1; q += blockDim.x) gx[q] = taps[(long long)tap_row_tc(q - (N - 1), N, g.periodic) * d + a];
+    for (int q = tid; q < N * d; q += blockDim.x) {
+        const int n = q / d, c = q - n * d;
+        Dfull[q] = gDm[bl * dm_ss + ((long long)n * d + a) * d + c];
+    }
+    for (int q = tid; q < (2 * N - 1) * d; q += blockDim.x) {
+        const int rr = q / d, c = q - rr * d;
+        Tfull[q] = gtaps[(long long)tap_row_tc(rr - (N - 1), N, g.periodic) * d + c];
+    }
+    if (tid == 0) {
+        for (int j = 0; j < 2; ++j) {
+            tc::mbar_init(bfull + j, 128);
+            tc::mbar_init(bempty + j, 1);
+            tc::mbar_init(afull + j, 1);
+            tc::mbar_init(aempty + j, 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *s_ok = 1;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 2 * TN);
+    __syncthreads();
+    // Hankel operand of every chunk (reversed K order, as in k_tgemm_tc).
+    for (int ch = 0; ch < nch; ++ch) {
+        const int n0 = ch * kTcK;
+        unsigned char *Ap = Aall + (size_t)ch * NPL * kHankelBytes;
+        for (int q = tid; q < kHankel * 8; q += blockDim.x) {
+            const int D = q >> 3, rr = q & 7;
+            const int t0 = i0 - n0 - kTcK + 1 + 8 * D + rr;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0 + u;
+                v[u] = (t > -N && t < N) ? gx[t + N - 1] : 0.f;
+            }
+            tc::stage8_planes<NPL>(Ap, kHankelBytes, (uint32_t)(D * 128 + rr * 16), v);
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const int ntiles = (P + TN - 1) / TN;
+    const int nt = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto alive = [&]() { return *((volatile int *)s_ok) != 0; };
+    if (warp < 4) {
+        // ------------------------------------------------------------- B operand --
+        const int pp = tid;
+        int use = 0;
+        bool ok = true;
+        for (int k = 0; k < nt && ok; ++k) {
+            const int p0 = ((int)blockIdx.x + k * (int)gridDim.x) * TN, pcol = p0 + pp;
+            const bool pok = pcol < P;
+            const int kq = pcol / d, cq = pcol - kq * d;
+            for (int ch = 0; ch < nch; ++ch, ++use) {
+                const int bb = use & 1, n0 = ch * kTcK;
+                ok = alive();
+                if (ok && use >= 2) ok = tc::wait(bempty + bb, (uint32_t)(((use - 2) >> 1) & 1));
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    if (lane == 0) *s_ok = 0;
+                    break;
+                }
+                unsigned char *Bp = Bbuf + bb * kBbytes;
+#pragma unroll
+                for (int part = 0; part < 2; ++part)
+#pragma unroll
+                    for (int kc = 0; kc < 4; ++kc) {
+                        const int base = part * 32 + kc * 8;
+                        float v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int n = n0 + base + 7 - u;
+                            v[u] = (pok && n < N) ? Dfull[n * d + cq] * Tfull[(n - kq + N - 1) * d + cq] : 0.f;
+                        }
+                        const int kk = kTcK - 8 - base;
+                        tc::stage8_planes<NPL>(Bp, 4 * kSlabB, (uint32_t)(kk >> 4) * kSlabB + tc::canon(pp, kk & 15), v);
+                    }
+                tc::fence_async_smem();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(bfull + bb)) : "memory");
+            }
+        }
+    } else if (warp < 8) {
+        // --------------------------------------------------------------- epilogue --
+        const int quad = warp - 4;
+        const int prow0 = i0 + quad * 32, i = prow0 + lane;
+        const long long zc = bl * d + a;
+        int nst = 0;   // stores committed by this warp: staging tile nst & 1 is next
+        for (int k = 0; k < nt; ++k) {
+            const int ab = k & 1;
+            bool ok = alive() && tc::wait(afull + ab, (uint32_t)((k >> 1) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) *s_ok = 0;
+                break;
+            }
+            tc::fence_after();
+            const int p0 = ((int)blockIdx.x + k * (int)gridDim.x) * TN;
+            for (int c0 = 0; c0 < TN; c0 += 32) {
+                uint32_t rr[32];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    tc::tmem_ld8_async(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * TN + c0 + 8 * q), rr + 8 * q);
+                tc::tmem_wait_ld(rr, 32);
+                if (c0 + 32 == TN) {
+                    tc::fence_before();
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(aempty + ab)) : "memory");
+                }
+                float r[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) r[j] = __uint_as_float(rr[j]);
+                const int pb = p0 + c0;
+                if (pb >= P || prow0 >= N) continue;       // warp-uniform
+                unsigned char *stg = Stg + (quad * 2 + (nst & 1)) * 4096;
+                // the store before last, which used this staging tile, has read it
+                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    *reinterpret_cast<float4 *>(stg + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                        make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                            reinterpret_cast<uint64_t>(&tmY)),
+                        "r"(pb), "r"(prow0), "r"((int)zc), "r"(sm_u32(stg))
+                        : "memory");
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+                ++nst;
+                if (band && i < N) {
+                    // (k, cc) of column pb, then stepped by 4 columns without dividing again
+                    int ks = pb / bns, cc = pb - ks * bns;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (pb + 4 * j >= P) break;
+                        const int dl = g.periodic ? ring_delta_tc(i - ks, N, 1) : i - ks;
+                        if (dl >= -bR && dl <= bR) {
+                            float *bp = band + (b0 + bl) * bss + (long long)i * brs + (long long)(bR - dl) * bos +
+                                        (long long)a * bns + cc;
+                            *reinterpret_cast<float4 *>(bp) =
+                                make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+                        }
+                        cc += 4;
+                        if (cc == bns) {
+                            cc = 0;
+                            ++ks;
+                        }
+                    }
+                }
+            }
+        }
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
+    } else if (lane == 0) {
+        // ------------------------------------------------------------- MMA issue --
+        const uint32_t idesc = tc::idesc_bf16(kTcM, TN);
+        int use = 0;
+        bool ok = true;
+        for (int k = 0; k < nt && ok; ++k) {
+            const int ab = k & 1;
+            ok = alive();
+            if (ok && k >= 2) ok = tc::wait(aempty + ab, (uint32_t)(((k - 2) >> 1) & 1));
+            if (!ok) break;
+            tc::fence_after();
+            const uint32_t tacc = tmem + (uint32_t)(ab * TN);
+            for (int ch = 0; ch < nch; ++ch, ++use) {
+                const int bb = use & 1;
+                ok = alive() && tc::wait(bfull + bb, (uint32_t)((use >> 1) & 1));
+                if (!ok) break;
+                tc::fence_after();
+                const unsigned char *Ap = Aall + (size_t)ch * NPL * kHankelBytes;
+                const unsigned char *Bp = Bbuf + bb * kBbytes;
+                for (int s = 0; s < kTcK / 16; ++s)
+#pragma unroll
+                    for (int pa = 0; pa < NPL; ++pa)
+#pragma unroll
+                        for (int pb = 0; pa + pb < NPL; ++pb)
+                            tc::mma_bf16(tacc, umma_desc_hankel(sm_u32(Ap + pa * kHankelBytes + 2 * s * 128)),
+                                         umma_desc(sm_u32(Bp + pb * 4 * kSlabB + s * kSlabB)), idesc,
+                                         (ch == 0 && s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+                tc::commit(bempty + bb);
+            }
+            if (ok) tc::commit(afull + ab);
+        }
+        if (!ok) *s_ok = 0;
+        // every MMA issued has completed before the tensor memory is released: wait for the
+        // commit of the last B buffer used (commits complete in order)
+        if (use > 0) (void)tc::wait(bempty + ((use - 1) & 1), (uint32_t)(((use - 1) >> 1) & 1));
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (!*s_ok && tid == 0) atomicOr(flag, 8u);
+    if (warp == 0) tc::tmem_free(tmem, 2 * TN);
+}
+
 // Vertex hop on the tensor cores: X[b][c][n][p] = sum_a D0_n[c][a] Y[b][a][n][p].  Per site n it is
 // a GEMM with the columns p as rows (M = 128 per tile), the output channels as N and the input
 // channels as K; D0_n is the B operand, staged once per CTA, which then loops over column tiles.
@@ -956,9 +1208,26 @@ static cudaError_t launch_tgemm_genp_d(const Geom &g, const float *taps, int P, 
                                        cudaStream_t st) {
     alignas(64) CUtensorMap tmY;
     if (!Y || bns % 4 != 0 || !hop_output_map(&tmY, Y, g.N, P, (long long)nb * g.d)) return cudaErrorNotSupported;
-    const size_t smem = tgemm_genp_smem(g.N, g.d, NPL);
     const int itiles = (g.N + kTcM - 1) / kTcM, ntiles = (P + 127) / 128;
     const long long ctas = (long long)itiles * nb * g.d;
+    const size_t smw = tgemm_genp_ws_smem<NPL>(g.N, g.d);
+    if (smw <= 227 * 1024) {
+        // one CTA per SM; column tiles per CTA: all of them when the CTAs fill the GPU twice over
+        long long cg = (2 * 152 + ctas - 1) / ctas;
+        if (cg < 1) cg = 1;
+        if (cg > ntiles) cg = ntiles;
+        dim3 grid((unsigned)cg, (unsigned)itiles, (unsigned)((long long)nb * g.d));
+        cudaError_t err =
+            cudaFuncSetAttribute(k_tgemm_genp_ws<NPL, DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+        if (err != cudaSuccess) return err;
+        {
+            ProfScope _ps("k_tgemm_tc", st);
+            k_tgemm_genp_ws<NPL, DD><<<grid, kGwThreads, smw, st>>>(g, taps, P, gtaps, gDm, dm_ss, tmY, band, bss, brs,
+                                                                    bos, bR, bns, b0, flag);
+        }
+        return cudaGetLastError();
+    }
+    const size_t smem = tgemm_genp_smem(g.N, g.d, NPL);
     // Column tiles per CTA: all of them when there are enough CTAs to fill the GPU twice over.
     long long cg = (2 * 2 * 152 + ctas - 1) / ctas;
     if (cg < 1) cg = 1;
