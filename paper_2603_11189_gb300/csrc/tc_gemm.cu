@@ -508,19 +508,19 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
 // Warp-specialised form of k_tgemm_genp (used when its shared memory fits): the operand
 // generation of the next chunk, the MMAs of the current one and the epilogue of the
 // previous column tile run at the same time instead of one after the other.
-//  * warps 0-3 generate the B operand (column pp = thread, 64 sites per chunk, NPL BF16
-//    planes) into one of two buffers;
-//  * warp 8 (one thread) issues the MMAs of a chunk once its buffer is full, into one of
+//  * warps 0-7 generate the B operand (column pp = thread mod 128, 32 of the 64 sites of a
+//    chunk each, NPL BF16 planes) into one of two buffers;
+//  * warp 12 (one thread) issues the MMAs of a chunk once its buffer is full, into one of
 //    two 128-column accumulators in tensor memory, and commits them to the buffer's empty
 //    barrier and, after the last chunk of a tile, to the accumulator's full barrier;
-//  * warps 4-7 drain an accumulator (TMEM lanes 32 (w - 4) ..): hop output through
+//  * warps 8-11 drain an accumulator (TMEM lanes 32 (w - 8) ..): hop output through
 //    per-warp double-buffered 128B-swizzled staging tiles and TMA tensor stores, band
 //    rows from registers, and release the accumulator after their last tensor-memory
 //    load.
 // The products, their order and the epilogue's values are those of k_tgemm_genp.  Every
 // wait is bounded; a wait that gives up raises bit 8 of the flag, every role leaves its
 // loop, the MMAs issued are waited for and the tensor memory is released.
-constexpr int kGwThreads = 288;
+constexpr int kGwThreads = 416;
 
 template <int NPL>
 static size_t tgemm_genp_ws_smem(int N, int d) {
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
     }
     if (tid == 0) {
         for (int j = 0; j < 2; ++j) {
-            tc::mbar_init(bfull + j, 128);
+            tc::mbar_init(bfull + j, 256);
             tc::mbar_init(bempty + j, 1);
             tc::mbar_init(afull + j, 1);
             tc::mbar_init(aempty + j, 128);
@@ -605,9 +605,9 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
     const int ntiles = (P + TN - 1) / TN;
     const int nt = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto alive = [&]() { return *((volatile int *)s_ok) != 0; };
-    if (warp < 4) {
+    if (warp < 8) {
         // ------------------------------------------------------------- B operand --
-        const int pp = tid;
+        const int pp = tid & 127, part = tid >> 7;
         int use = 0;
         bool ok = true;
         for (int k = 0; k < nt && ok; ++k) {
@@ -625,26 +625,24 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
                 }
                 unsigned char *Bp = Bbuf + bb * kBbytes;
 #pragma unroll
-                for (int part = 0; part < 2; ++part)
+                for (int kc = 0; kc < 4; ++kc) {
+                    const int base = part * 32 + kc * 8;
+                    float v[8];
 #pragma unroll
-                    for (int kc = 0; kc < 4; ++kc) {
-                        const int base = part * 32 + kc * 8;
-                        float v[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int n = n0 + base + 7 - u;
-                            v[u] = (pok && n < N) ? Dfull[n * d + cq] * Tfull[(n - kq + N - 1) * d + cq] : 0.f;
-                        }
-                        const int kk = kTcK - 8 - base;
-                        tc::stage8_planes<NPL>(Bp, 4 * kSlabB, (uint32_t)(kk >> 4) * kSlabB + tc::canon(pp, kk & 15), v);
+                    for (int u = 0; u < 8; ++u) {
+                        const int n = n0 + base + 7 - u;
+                        v[u] = (pok && n < N) ? Dfull[n * d + cq] * Tfull[(n - kq + N - 1) * d + cq] : 0.f;
                     }
+                    const int kk = kTcK - 8 - base;
+                    tc::stage8_planes<NPL>(Bp, 4 * kSlabB, (uint32_t)(kk >> 4) * kSlabB + tc::canon(pp, kk & 15), v);
+                }
                 tc::fence_async_smem();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(bfull + bb)) : "memory");
             }
         }
-    } else if (warp < 8) {
+    } else if (warp < 12) {
         // --------------------------------------------------------------- epilogue --
-        const int quad = warp - 4;
+        const int quad = warp - 8;
         const int prow0 = i0 + quad * 32, i = prow0 + lane;
         const long long zc = bl * d + a;
         int nst = 0;   // stores committed by this warp: staging tile nst & 1 is next
