@@ -514,18 +514,19 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
 //    two 128-column accumulators in tensor memory, and commits them to the buffer's empty
 //    barrier and, after the last chunk of a tile, to the accumulator's full barrier;
 //  * warps 8-11 drain an accumulator (TMEM lanes 32 (w - 8) ..): hop output through
-//    per-warp double-buffered 128B-swizzled staging tiles and TMA tensor stores, band
+//    four 128B-swizzled staging tiles per warp (TMA tensor stores in flight), band
 //    rows from registers, and release the accumulator after their last tensor-memory
 //    load.
 // The products, their order and the epilogue's values are those of k_tgemm_genp.  Every
 // wait is bounded; a wait that gives up raises bit 8 of the flag, every role leaves its
 // loop, the MMAs issued are waited for and the tensor memory is released.
 constexpr int kGwThreads = 416;
+constexpr int kGwStg = 4;   // staging tiles per epilogue warp (TMA stores in flight)
 
 template <int NPL>
 static size_t tgemm_genp_ws_smem(int N, int d) {
     const int nch = (N + kTcK - 1) / kTcK;
-    const size_t B = 2 * (size_t)NPL * 4 * 128 * 32, stg = 4 * 2 * 4096;
+    const size_t B = 2 * (size_t)NPL * 4 * 128 * 32, stg = 4 * kGwStg * 4096;
     return B + stg + (size_t)nch * NPL * kHankelBytes +
            ((size_t)((2 * N + 1) & ~1) + (size_t)N * d + ((size_t)(2 * N - 1) * d + 1) / 2 * 2) * sizeof(float) +
            8 * sizeof(uint64_t) + 16;
@@ -546,8 +547,8 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
     constexpr int d = DD;
     const int nch = (N + kTcK - 1) / kTcK;
     unsigned char *Bbuf = smgw;                                   // [2][kBbytes]
-    unsigned char *Stg = smgw + 2 * kBbytes;                      // [4 warps][2][4096]
-    unsigned char *Aall = Stg + 4 * 2 * 4096;                     // [nch][NPL][kHankelBytes]
+    unsigned char *Stg = smgw + 2 * kBbytes;                      // [4 warps][kGwStg][4096]
+    unsigned char *Aall = Stg + 4 * kGwStg * 4096;                // [nch][NPL][kHankelBytes]
     float *gx = reinterpret_cast<float *>(Aall + (size_t)nch * NPL * kHankelBytes);   // gx[r + N - 1], channel a
     float *Dfull = gx + ((2 * N + 1) & ~1);                       // [N][d]: D0_n[a][c']
     float *Tfull = Dfull + (size_t)N * d;                         // [2N - 1][d]: g_r[c'], row r + N - 1
@@ -645,7 +646,7 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
         const int quad = warp - 8;
         const int prow0 = i0 + quad * 32, i = prow0 + lane;
         const long long zc = bl * d + a;
-        int nst = 0;   // stores committed by this warp: staging tile nst & 1 is next
+        int nst = 0;   // stores committed by this warp: staging tile nst mod kGwStg is next
         for (int k = 0; k < nt; ++k) {
             const int ab = k & 1;
             bool ok = alive() && tc::wait(afull + ab, (uint32_t)((k >> 1) & 1));
@@ -670,9 +671,9 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
                 for (int j = 0; j < 32; ++j) r[j] = __uint_as_float(rr[j]);
                 const int pb = p0 + c0;
                 if (pb >= P || prow0 >= N) continue;       // warp-uniform
-                unsigned char *stg = Stg + (quad * 2 + (nst & 1)) * 4096;
-                // the store before last, which used this staging tile, has read it
-                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                unsigned char *stg = Stg + (quad * kGwStg + nst % kGwStg) * 4096;
+                // the store kGwStg back, which used this staging tile, has read it
+                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kGwStg - 1) : "memory");
                 __syncwarp();
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
