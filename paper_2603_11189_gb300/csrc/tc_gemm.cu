@@ -510,24 +510,25 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
 // previous column tile run at the same time instead of one after the other.
 //  * warps 0-7 generate the B operand (column pp = thread mod 128, 32 of the 64 sites of a
 //    chunk each, NPL BF16 planes) into one of two buffers;
-//  * warp 16 (one thread) issues the MMAs of a chunk once its buffer is full, into one of
+//  * the last warp (one thread) issues the MMAs of a chunk once its buffer is full, into one of
 //    two 128-column accumulators in tensor memory, and commits them to the buffer's empty
 //    barrier and, after the last chunk of a tile, to the accumulator's full barrier;
-//  * warps 8-15 drain an accumulator (TMEM lanes 32 (w mod 4) .., one half of the columns
-//    each): hop output through three 128B-swizzled staging tiles per warp (TMA tensor
+//  * warps 8-23 drain an accumulator (TMEM lanes 32 (w mod 4) .., a quarter of the columns
+//    each): hop output through a 128B-swizzled staging tile per warp (TMA tensor
 //    stores in flight), band
 //    rows from registers, and release the accumulator after their last tensor-memory
 //    load.
 // The products, their order and the epilogue's values are those of k_tgemm_genp.  Every
 // wait is bounded; a wait that gives up raises bit 8 of the flag, every role leaves its
 // loop, the MMAs issued are waited for and the tensor memory is released.
-constexpr int kGwThreads = 544;
-constexpr int kGwStg = 3;   // staging tiles per epilogue warp (TMA stores in flight)
+constexpr int kGwEpi = 16;  // epilogue warps: kGwEpi / 4 per tensor-memory lane quadrant
+constexpr int kGwThreads = 32 * (8 + kGwEpi + 1);
+constexpr int kGwStg = 1;   // staging tiles per epilogue warp (TMA stores in flight)
 
 template <int NPL>
 static size_t tgemm_genp_ws_smem(int N, int d) {
     const int nch = (N + kTcK - 1) / kTcK;
-    const size_t B = 2 * (size_t)NPL * 4 * 128 * 32, stg = 8 * kGwStg * 4096;
+    const size_t B = 2 * (size_t)NPL * 4 * 128 * 32, stg = (size_t)kGwEpi * kGwStg * 4096;
     return B + stg + (size_t)nch * NPL * kHankelBytes +
            ((size_t)((2 * N + 1) & ~1) + (size_t)N * d + ((size_t)(2 * N - 1) * d + 1) / 2 * 2) * sizeof(float) +
            8 * sizeof(uint64_t) + 16;
@@ -548,8 +549,8 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
     constexpr int d = DD;
     const int nch = (N + kTcK - 1) / kTcK;
     unsigned char *Bbuf = smgw;                                   // [2][kBbytes]
-    unsigned char *Stg = smgw + 2 * kBbytes;                      // [8 warps][kGwStg][4096]
-    unsigned char *Aall = Stg + 8 * kGwStg * 4096;                // [nch][NPL][kHankelBytes]
+    unsigned char *Stg = smgw + 2 * kBbytes;                      // [kGwEpi][kGwStg][4096]
+    unsigned char *Aall = Stg + kGwEpi * kGwStg * 4096;           // [nch][NPL][kHankelBytes]
     float *gx = reinterpret_cast<float *>(Aall + (size_t)nch * NPL * kHankelBytes);   // gx[r + N - 1], channel a
     float *Dfull = gx + ((2 * N + 1) & ~1);                       // [N][d]: D0_n[a][c']
     float *Tfull = Dfull + (size_t)N * d;                         // [2N - 1][d]: g_r[c'], row r + N - 1
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
             tc::mbar_init(bfull + j, 256);
             tc::mbar_init(bempty + j, 1);
             tc::mbar_init(afull + j, 1);
-            tc::mbar_init(aempty + j, 256);
+            tc::mbar_init(aempty + j, 32 * kGwEpi);
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         *s_ok = 1;
@@ -642,9 +643,10 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(bfull + bb)) : "memory");
             }
         }
-    } else if (warp < 16) {
+    } else if (warp < 8 + kGwEpi) {
         // --------------------------------------------------------------- epilogue --
-        const int quad = (warp - 8) & 3, half = (warp - 8) >> 2;   // TMEM lanes, column half
+        constexpr int kCols = TN / (kGwEpi / 4);                     // columns per epilogue warp
+        const int quad = (warp - 8) & 3, part = (warp - 8) >> 2;    // TMEM lanes, column part
         const int prow0 = i0 + quad * 32, i = prow0 + lane;
         const long long zc = bl * d + a;
         int nst = 0;   // stores committed by this warp: staging tile nst mod kGwStg is next
@@ -657,13 +659,13 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
             }
             tc::fence_after();
             const int p0 = ((int)blockIdx.x + k * (int)gridDim.x) * TN;
-            for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 32) {
+            for (int c0 = part * kCols; c0 < (part + 1) * kCols; c0 += 32) {
                 uint32_t rr[32];
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     tc::tmem_ld8_async(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * TN + c0 + 8 * q), rr + 8 * q);
                 tc::tmem_wait_ld(rr, 32);
-                if (c0 + 32 == (half + 1) * (TN / 2)) {
+                if (c0 + 32 == (part + 1) * kCols) {
                     tc::fence_before();
                     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_u32(aempty + ab)) : "memory");
                 }
