@@ -509,29 +509,30 @@ __global__ void __launch_bounds__(256, 2) k_tgemm_genp(Geom g, const float *__re
 // generation of the next chunk, the MMAs of the current one and the epilogue of the
 // previous column tile run at the same time instead of one after the other.
 //  * warps 0-7 generate the B operand (column pp = thread mod 128, 32 of the 64 sites of a
-//    chunk each, NPL BF16 planes) into one of two buffers;
+//    chunk each, NPL BF16 planes) into one of three buffers;
 //  * the last warp (one thread) issues the MMAs of a chunk once its buffer is full, into one of
-//    two 128-column accumulators in tensor memory, and commits them to the buffer's empty
+//    four 128-column accumulators in tensor memory, and commits them to the buffer's empty
 //    barrier and, after the last chunk of a tile, to the accumulator's full barrier;
 //  * warps 8-23 drain an accumulator (TMEM lanes 32 (w mod 4) .., a quarter of the columns
-//    each): hop output through a 128B-swizzled staging tile per warp (TMA tensor
-//    stores in flight), band
-//    rows from registers, and release the accumulator after their last tensor-memory
-//    load.
+//    each): hop output through a 128B-swizzled staging tile per warp and a TMA tensor
+//    store, band rows from registers; they release the accumulator after their last
+//    tensor-memory load.
 // The products, their order and the epilogue's values are those of k_tgemm_genp.  Every
 // wait is bounded; a wait that gives up raises bit 8 of the flag, every role leaves its
 // loop, the MMAs issued are waited for and the tensor memory is released.
 constexpr int kGwEpi = 16;  // epilogue warps: kGwEpi / 4 per tensor-memory lane quadrant
 constexpr int kGwThreads = 32 * (8 + kGwEpi + 1);
 constexpr int kGwStg = 1;   // staging tiles per epilogue warp (TMA stores in flight)
+constexpr int kGwB = 3;     // operand buffers
+constexpr int kGwAcc = 4;   // accumulators (128 tensor-memory columns each)
 
 template <int NPL>
 static size_t tgemm_genp_ws_smem(int N, int d) {
     const int nch = (N + kTcK - 1) / kTcK;
-    const size_t B = 2 * (size_t)NPL * 4 * 128 * 32, stg = (size_t)kGwEpi * kGwStg * 4096;
+    const size_t B = (size_t)kGwB * NPL * 4 * 128 * 32, stg = (size_t)kGwEpi * kGwStg * 4096;
     return B + stg + (size_t)nch * NPL * kHankelBytes +
            ((size_t)((2 * N + 1) & ~1) + (size_t)N * d + ((size_t)(2 * N - 1) * d + 1) / 2 * 2) * sizeof(float) +
-           8 * sizeof(uint64_t) + 16;
+           2 * (kGwB + kGwAcc) * sizeof(uint64_t) + 16;
 }
 
 template <int NPL, int DD>
@@ -548,15 +549,15 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
     const int N = g.N;
     constexpr int d = DD;
     const int nch = (N + kTcK - 1) / kTcK;
-    unsigned char *Bbuf = smgw;                                   // [2][kBbytes]
-    unsigned char *Stg = smgw + 2 * kBbytes;                      // [kGwEpi][kGwStg][4096]
+    unsigned char *Bbuf = smgw;                                   // [kGwB][kBbytes]
+    unsigned char *Stg = smgw + kGwB * kBbytes;                      // [kGwEpi][kGwStg][4096]
     unsigned char *Aall = Stg + kGwEpi * kGwStg * 4096;           // [nch][NPL][kHankelBytes]
     float *gx = reinterpret_cast<float *>(Aall + (size_t)nch * NPL * kHankelBytes);   // gx[r + N - 1], channel a
     float *Dfull = gx + ((2 * N + 1) & ~1);                       // [N][d]: D0_n[a][c']
     float *Tfull = Dfull + (size_t)N * d;                         // [2N - 1][d]: g_r[c'], row r + N - 1
     uint64_t *bar = reinterpret_cast<uint64_t *>(Tfull + ((size_t)(2 * N - 1) * d + 1) / 2 * 2);
-    uint64_t *bfull = bar, *bempty = bar + 2, *afull = bar + 4, *aempty = bar + 6;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 8);
+    uint64_t *bfull = bar, *bempty = bar + kGwB, *afull = bar + 2 * kGwB, *aempty = afull + kGwAcc;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(aempty + kGwAcc);
     int *s_ok = reinterpret_cast<int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = blockIdx.y * kTcM;
@@ -573,16 +574,18 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
         Tfull[q] = gtaps[(long long)tap_row_tc(rr - (N - 1), N, g.periodic) * d + c];
     }
     if (tid == 0) {
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < kGwB; ++j) {
             tc::mbar_init(bfull + j, 256);
             tc::mbar_init(bempty + j, 1);
+        }
+        for (int j = 0; j < kGwAcc; ++j) {
             tc::mbar_init(afull + j, 1);
             tc::mbar_init(aempty + j, 32 * kGwEpi);
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
         *s_ok = 1;
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 2 * TN);
+    if (warp == 0) tc::tmem_alloc(tslot, kGwAcc * TN);
     __syncthreads();
     // Hankel operand of every chunk (reversed K order, as in k_tgemm_tc).
     for (int ch = 0; ch < nch; ++ch) {
@@ -618,9 +621,9 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
             const bool pok = pcol < P;
             const int kq = pcol / d, cq = pcol - kq * d;
             for (int ch = 0; ch < nch; ++ch, ++use) {
-                const int bb = use & 1, n0 = ch * kTcK;
+                const int bb = use % kGwB, n0 = ch * kTcK;
                 ok = alive();
-                if (ok && use >= 2) ok = tc::wait(bempty + bb, (uint32_t)(((use - 2) >> 1) & 1));
+                if (ok && use >= kGwB) ok = tc::wait(bempty + bb, (uint32_t)(((use - kGwB) / kGwB) & 1));
                 if (!__all_sync(0xffffffffu, ok)) {
                     ok = false;
                     if (lane == 0) *s_ok = 0;
@@ -651,8 +654,8 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
         const long long zc = bl * d + a;
         int nst = 0;   // stores committed by this warp: staging tile nst mod kGwStg is next
         for (int k = 0; k < nt; ++k) {
-            const int ab = k & 1;
-            bool ok = alive() && tc::wait(afull + ab, (uint32_t)((k >> 1) & 1));
+            const int ab = k % kGwAcc;
+            bool ok = alive() && tc::wait(afull + ab, (uint32_t)((k / kGwAcc) & 1));
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) *s_ok = 0;
                 break;
@@ -723,15 +726,15 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
         int use = 0;
         bool ok = true;
         for (int k = 0; k < nt && ok; ++k) {
-            const int ab = k & 1;
+            const int ab = k % kGwAcc;
             ok = alive();
-            if (ok && k >= 2) ok = tc::wait(aempty + ab, (uint32_t)(((k - 2) >> 1) & 1));
+            if (ok && k >= kGwAcc) ok = tc::wait(aempty + ab, (uint32_t)(((k - kGwAcc) / kGwAcc) & 1));
             if (!ok) break;
             tc::fence_after();
             const uint32_t tacc = tmem + (uint32_t)(ab * TN);
             for (int ch = 0; ch < nch; ++ch, ++use) {
-                const int bb = use & 1;
-                ok = alive() && tc::wait(bfull + bb, (uint32_t)((use >> 1) & 1));
+                const int bb = use % kGwB;
+                ok = alive() && tc::wait(bfull + bb, (uint32_t)((use / kGwB) & 1));
                 if (!ok) break;
                 tc::fence_after();
                 const unsigned char *Ap = Aall + (size_t)ch * NPL * kHankelBytes;
@@ -751,12 +754,12 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
         if (!ok) *s_ok = 0;
         // every MMA issued has completed before the tensor memory is released: wait for the
         // commit of the last B buffer used (commits complete in order)
-        if (use > 0) (void)tc::wait(bempty + ((use - 1) & 1), (uint32_t)(((use - 1) >> 1) & 1));
+        if (use > 0) (void)tc::wait(bempty + ((use - 1) % kGwB), (uint32_t)(((use - 1) / kGwB) & 1));
     }
     tc::fence_before();
     __syncthreads();
     if (!*s_ok && tid == 0) atomicOr(flag, 8u);
-    if (warp == 0) tc::tmem_free(tmem, 2 * TN);
+    if (warp == 0) tc::tmem_free(tmem, kGwAcc * TN);
 }
 
 // Vertex hop on the tensor cores: X[b][c][n][p] = sum_a D0_n[c][a] Y[b][a][n][p].  Per site n it is
