@@ -13,14 +13,15 @@
 // over all N sites n, with specialised warps connected by mbarriers:
 //   - warpgroup 3: one thread brings Y[:, n, tile] (32 x 128 floats, one TMA tensor copy)
 //     and D0_n (32 x 32, one bulk copy) into a four-stage ring as stages free up; another
-//     issues, per site, the six BF16 plane products with pa + pb <= 2 (M = 128 columns,
+//     issues, per site, the five BF16 plane products with pa < 2, pa + pb <= 2 (M = 128 columns,
 //     N = 32 output channels, K = 32 input channels, FP32 accumulation into one of three
 //     tensor-memory buffers): the same products and order as the separate vertex-hop
 //     kernel;
-//   - warpgroup 0 splits every value into three BF16 planes (v = p0 + p1 + p2 + rest): the
-//     A operand (the hop output slice, row = column p) into one of three tensor-memory
-//     buffers, the B operand (D0_n) into one of three shared-memory buffers; the MMAs read
-//     A from tensor memory, which keeps the six plane products' operand reads off the
+//   - warpgroup 0 splits every value into BF16 planes (v = p0 + p1 + rest): the A operand
+//     (the hop output slice, row = column p, two planes: it carries the previous Toeplitz
+//     hop's two-plane error already) into one of three tensor-memory buffers, the B
+//     operand (D0_n, three planes) into one of three shared-memory buffers; the MMAs read
+//     A from tensor memory, which keeps the plane products' operand reads off the
 //     shared-memory port;
 //   - warpgroups 1-2 (warps 4-11) only add each site into the band sums: warp w owns
 //     TMEM lanes 32 (w & 3) .. + 31 (one source site, lane = source channel c') and
@@ -46,6 +47,7 @@ constexpr int kDbD = 32;                             // channels
 constexpr int kDbCols = 128;                         // source columns per CTA
 constexpr int kDbStages = 4;                         // depth of the input ring
 constexpr int kDbBufs = 3;                           // operand buffers and accumulators in flight
+constexpr int kDbAPl = 2;                            // BF16 planes of the A operand (the hop output)
 constexpr int kDbThreads = 512;                      // warpgroups: 0 staging, 1-2 band sums, 3 loads + MMAs
 constexpr int kDbStageRegs = 72, kDbBandRegs = 200, kDbCtlRegs = 40;   // x 128, 256, 128 threads = 512 x 128
 constexpr uint32_t kDbUBytes = kDbD * kDbCols * 4;   // Y[:, n, tile]: 16 KB
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
             tc::fence_after();
             const unsigned char *src = ring + st * kDbStage;
             // A operand (tensor memory): row p = tid of the tile, K = input channel a; each
-            // 16-wide K slab as three BF16 planes of 8 columns (element 2c in the low half).
+            // 16-wide K slab as BF16 planes of 8 columns (element 2c in the low half).
             const float *us = reinterpret_cast<const float *>(src) + tid;
             const uint32_t abase = tmem + trow + (uint32_t)(j * kDbACols);
 #pragma unroll
@@ -187,13 +189,13 @@ __global__ void __launch_bounds__(kDbThreads, 1)
 #pragma unroll
                 for (int u = 0; u < 16; ++u) r[u] = us[(a16 + u) * kDbCols];
 #pragma unroll
-                for (int pl = 0; pl < 3; ++pl) {
+                for (int pl = 0; pl < kDbAPl; ++pl) {
                     uint32_t w[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
                         w[i] = *reinterpret_cast<const uint32_t *>(&h);
-                        if (pl < 2) {
+                        if (pl < kDbAPl - 1) {
                             r[2 * i] -= __low2float(h);
                             r[2 * i + 1] -= __high2float(h);
                         }
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(kDbThreads, 1)
 #pragma unroll 1
                 for (int s = 0; s < 2; ++s)
 #pragma unroll
-                    for (int pa = 0; pa < 3; ++pa)
+                    for (int pa = 0; pa < kDbAPl; ++pa)
 #pragma unroll
                         for (int pb = 0; pa + pb < 3; ++pb)
                             mma_bf16_ta(tmem + kDbZCol0 + (uint32_t)(j * kDbD), at + (uint32_t)(pa * 16 + s * 8),

@@ -765,7 +765,8 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
 // Vertex hop on the tensor cores: X[b][c][n][p] = sum_a D0_n[c][a] Y[b][a][n][p].  Per site n it is
 // a GEMM with the columns p as rows (M = 128 per tile), the output channels as N and the input
 // channels as K; D0_n is the B operand, staged once per CTA, which then loops over column tiles.
-// Each FP32 value is split into NPL BF16 planes (3 for FP32 accuracy, 1 for BF16).
+// Each FP32 value of D0 is split into NPL BF16 planes (3 for FP32 accuracy, 1 for BF16), each
+// value of Y into 2 (FP32) or 1.
 template <int D, int NPL>
 __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__restrict__ Dm, long long dm_ss,
                                                  const float *__restrict__ Yin, float *__restrict__ Xo,
@@ -774,7 +775,10 @@ __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__re
     constexpr int ns = D / 16;
     constexpr uint32_t aslab = 128 * 32, bslab = D * 32, aplane = ns * aslab, bplane = ns * bslab;
     constexpr uint32_t cols = D < 32 ? 32 : D;
-    unsigned char *Ap = smd;                       // NPL planes: rows p, K a
+    // The input Y carries the Toeplitz hop's own error (two BF16 planes, about 2^-17
+    // relative), so two planes of it suffice: products (0,0) (0,1) (0,2) (1,0) (1,1).
+    constexpr int NPA = NPL == 3 ? 2 : NPL;
+    unsigned char *Ap = smd;                       // NPL planes (NPA used): rows p, K a
     unsigned char *Bp = Ap + NPL * aplane;         // NPL planes: rows c, K a
     uint64_t *mbar = reinterpret_cast<uint64_t *>(Bp + NPL * bplane);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
@@ -820,8 +824,8 @@ __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__re
         const bool valid = p < P;
 #pragma unroll
         for (int a16 = 0; a16 < D; a16 += 16) {
-            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 0), buf + a16);
-            tc::stage8_planes<NPL>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 8), buf + a16 + 8);
+            tc::stage8_planes<NPA>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 0), buf + a16);
+            tc::stage8_planes<NPA>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 8), buf + a16 + 8);
         }
         if (t + depth * (int)gridDim.x < ntiles) load_col(buf, t + depth * gridDim.x);
         tc::fence_async_smem();
@@ -834,7 +838,7 @@ __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__re
 #pragma unroll 1
             for (int s = 0; s < ns; ++s)
 #pragma unroll
-                for (int pa = 0; pa < NPL; ++pa)
+                for (int pa = 0; pa < NPA; ++pa)
 #pragma unroll
                     for (int pb = 0; pa + pb < NPL; ++pb)
                         tc::mma_bf16(tmem, tc::desc(tc::smem_u32(Ap + pa * aplane + s * aslab)),
