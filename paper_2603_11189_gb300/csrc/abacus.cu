@@ -455,16 +455,21 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
     long long *roff = reinterpret_cast<long long *>(smraw);   // [RT] chi offset of the row's site, or -1
     T *phT = reinterpret_cast<T *>(roff + RT);              // [dh][TS]  phi
     T *acT = phT + dh * TS;                                 // [dh][TS]  GELU(z)
-    T *W1s = acT + dh * TS;                                 // [f][e] = W1[e][f], row stride dh + 1
-    T *W2s = W1s + dh * (dh + 1);                           // [e][c] = W2[c][e], row stride d + 1
-    T *win = W2s + dh * (d + 1);                            // [RT][W] flipped spin window of the row
+    // FP32 with dh and d multiples of 4: each thread forms 4 outputs x 4 rows (16-byte weight
+    // and activation loads); otherwise 1 output x 8 rows.  Weight rows are padded to keep
+    // the 16-byte loads aligned (stride + 4) or the scalar ones off one bank (stride + 1).
+    const bool tiled = std::is_same<T, float>::value && dh % 4 == 0 && d % 4 == 0;
+    const int ws1 = tiled ? dh + 4 : dh + 1, ws2 = tiled ? d + 4 : d + 1;
+    T *W1s = acT + dh * TS;                                 // [f][e] = W1[e][f], row stride ws1
+    T *W2s = W1s + dh * ws1;                                // [e][c] = W2[c][e], row stride ws2
+    T *win = W2s + dh * ws2;                                // [RT][W] flipped spin window of the row
     const int l = blockIdx.y;
     const long long rows = (long long)a.B * N * W;
     const T *W1T = a.w.W1T + (long long)l * dh * dh, *W2T = a.w.W2T + (long long)l * dh * d;
     const T *b1 = a.w.b1 + (long long)l * dh, *b2 = a.w.b2 + (long long)l * d;
     const T *kap = a.w.kappa + (long long)l * W * dh, *beta = a.w.beta + (long long)l * dh;
-    for (int q = threadIdx.x; q < dh * dh; q += blockDim.x) W1s[(q / dh) * (dh + 1) + q % dh] = W1T[q];
-    for (int q = threadIdx.x; q < dh * d; q += blockDim.x) W2s[(q / d) * (d + 1) + q % d] = W2T[q];
+    for (int q = threadIdx.x; q < dh * dh; q += blockDim.x) W1s[(q / dh) * ws1 + q % dh] = W1T[q];
+    for (int q = threadIdx.x; q < dh * d; q += blockDim.x) W2s[(q / d) * ws2 + q % d] = W2T[q];
     for (int it = 0; it < tpb; ++it) {
         const long long r0 = ((long long)blockIdx.x * tpb + it) * RT;
         if (r0 >= rows) break;
@@ -506,40 +511,99 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
             phT[e * TS + rr] = acc;
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < dh * (RT / RG); q += blockDim.x) {
-            const int e = q % dh, t0 = (q / dh) * RG;
-            T acc[RG];
-    #pragma unroll
-            for (int u = 0; u < RG; ++u) acc[u] = b1[e];
-            for (int f = 0; f < dh; ++f) {
-                const T wv = W1s[f * (dh + 1) + e];
-                T pv[RG];
-                lds8<T>(phT + f * TS + t0, pv);
-    #pragma unroll
-                for (int u = 0; u < RG; ++u) acc[u] += wv * pv[u];
+        if (!tiled) {
+            for (int q = threadIdx.x; q < dh * (RT / RG); q += blockDim.x) {
+                const int e = q % dh, t0 = (q / dh) * RG;
+                T acc[RG];
+        #pragma unroll
+                for (int u = 0; u < RG; ++u) acc[u] = b1[e];
+                for (int f = 0; f < dh; ++f) {
+                    const T wv = W1s[f * ws1 + e];
+                    T pv[RG];
+                    lds8<T>(phT + f * TS + t0, pv);
+        #pragma unroll
+                    for (int u = 0; u < RG; ++u) acc[u] += wv * pv[u];
+                }
+        #pragma unroll
+                for (int u = 0; u < RG; ++u) acT[e * TS + t0 + u] = gelu_ab<T>(acc[u]);
             }
-    #pragma unroll
-            for (int u = 0; u < RG; ++u) acT[e * TS + t0 + u] = gelu_ab<T>(acc[u]);
-        }
-        __syncthreads();
-        for (int q = threadIdx.x; q < d * (RT / RG); q += blockDim.x) {
-            const int c = q % d, t0 = (q / d) * RG;
-            T acc[RG];
-    #pragma unroll
-            for (int u = 0; u < RG; ++u) acc[u] = b2[c];
-            for (int e = 0; e < dh; ++e) {
-                const T wv = W2s[e * (d + 1) + c];
-                T pv[RG];
-                lds8<T>(acT + e * TS + t0, pv);
-    #pragma unroll
-                for (int u = 0; u < RG; ++u) acc[u] += wv * pv[u];
+            __syncthreads();
+            for (int q = threadIdx.x; q < d * (RT / RG); q += blockDim.x) {
+                const int c = q % d, t0 = (q / d) * RG;
+                T acc[RG];
+        #pragma unroll
+                for (int u = 0; u < RG; ++u) acc[u] = b2[c];
+                for (int e = 0; e < dh; ++e) {
+                    const T wv = W2s[e * ws2 + c];
+                    T pv[RG];
+                    lds8<T>(acT + e * TS + t0, pv);
+        #pragma unroll
+                    for (int u = 0; u < RG; ++u) acc[u] += wv * pv[u];
+                }
+        #pragma unroll
+                for (int u = 0; u < RG; ++u) {
+                    const long long r = r0 + t0 + u;
+                    if (r >= rows) continue;
+                    const long long off = roff[t0 + u];
+                    DX[((long long)l * rows + r) * d + c] = off >= 0 ? acc[u] - a.chi[off + c] : (T)0;
+                }
             }
-    #pragma unroll
-            for (int u = 0; u < RG; ++u) {
-                const long long r = r0 + t0 + u;
-                if (r >= rows) continue;
-                const long long off = roff[t0 + u];
-                DX[((long long)l * rows + r) * d + c] = off >= 0 ? acc[u] - a.chi[off + c] : (T)0;
+
+        } else if constexpr (std::is_same<T, float>::value) {
+            // 4 outputs x 4 rows per thread
+            for (int q = threadIdx.x; q < (dh / 4) * (RT / 4); q += blockDim.x) {
+                const int e0 = (q % (dh / 4)) * 4, t0 = (q / (dh / 4)) * 4;
+                float acc[4][4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[j][u] = b1[e0 + j];
+#pragma unroll 4
+                for (int f = 0; f < dh; ++f) {
+                    const float4 wv = *reinterpret_cast<const float4 *>(W1s + f * ws1 + e0);
+                    const float4 pv = *reinterpret_cast<const float4 *>(phT + f * TS + t0);
+                    const float w4[4] = {wv.x, wv.y, wv.z, wv.w}, p4[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) acc[j][u] = fmaf(w4[j], p4[u], acc[j][u]);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    *reinterpret_cast<float4 *>(acT + (e0 + j) * TS + t0) =
+                        make_float4(gelu_ab<float>(acc[j][0]), gelu_ab<float>(acc[j][1]), gelu_ab<float>(acc[j][2]),
+                                    gelu_ab<float>(acc[j][3]));
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < (d / 4) * (RT / 4); q += blockDim.x) {
+                const int c0 = (q % (d / 4)) * 4, t0 = (q / (d / 4)) * 4;
+                float acc[4][4];   // [row][output]
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[u][j] = b2[c0 + j];
+#pragma unroll 4
+                for (int e = 0; e < dh; ++e) {
+                    const float4 wv = *reinterpret_cast<const float4 *>(W2s + e * ws2 + c0);
+                    const float4 pv = *reinterpret_cast<const float4 *>(acT + e * TS + t0);
+                    const float w4[4] = {wv.x, wv.y, wv.z, wv.w}, p4[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[u][j] = fmaf(w4[j], p4[u], acc[u][j]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long r = r0 + t0 + u;
+                    if (r >= rows) continue;
+                    const long long off = roff[t0 + u];
+                    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (off >= 0) {
+                        const float4 ch = *reinterpret_cast<const float4 *>(a.chi + off + c0);
+                        o = make_float4(acc[u][0] - ch.x, acc[u][1] - ch.y, acc[u][2] - ch.z, acc[u][3] - ch.w);
+                    }
+                    *reinterpret_cast<float4 *>(DX + ((long long)l * rows + r) * d + c0) = o;
+                }
             }
         }
     }
@@ -2510,7 +2574,7 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     if (g.W > kLayMaxW || g.d > 128) return cudaErrorNotSupported;
     const size_t lsm = (2 * (size_t)g.d * g.d + 8 * ((size_t)g.W * g.W * g.d + 2 * (size_t)g.W * g.d)) * sizeof(T);
     const size_t tsm = 64 * sizeof(long long) +
-                       ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1) + 2 * 68 * (size_t)g.dh + 64 * (size_t)g.W) *
+                       ((size_t)g.dh * (g.dh + 4) + (size_t)g.dh * (g.d + 4) + 2 * 68 * (size_t)g.dh + 64 * (size_t)g.W) *
                            sizeof(T);
     if (lsm > 220 * 1024 || tsm > 220 * 1024) return cudaErrorNotSupported;
     const AbArgs<T> a = ab_args<T>(m, pl, w, c);
