@@ -328,6 +328,15 @@ dn_status dn_set_fused_links(int on);
  * built after the call.  DN_EINVAL for another mode. */
 dn_status dn_set_fft_links(int mode);
 
+/* The S4 convolution of the forward pass (Eq. resolvent, Sec. "Implementation of
+ * DysonNet"): directly as a Toeplitz / circulant sum, O(N^2 d) per layer, or through
+ * DFTs of length M (the power of two >= 2N - 1 on an open chain; M = N on a ring whose N
+ * is a power of two), O(N log N d), with the tap spectra built once per (model, N).
+ * mode 1 (default): FFT for FP32 with N >= 512; 2: FFT wherever it applies (FP64 too);
+ * 0: never.  The two agree to rounding.  Process-wide; applies to forward passes (caches,
+ * full forward, recompute) launched after the call.  DN_EINVAL for another mode. */
+dn_status dn_set_fft_conv(int mode);
+
 /* Release a cache (stream-ordered on the stream of the call that built it). */
 void dn_cache_destroy(dn_cache *cache);
 

@@ -166,6 +166,8 @@ const dn::Plan<T> &ensure_plan(dn_model *m, int N, cudaStream_t st) {
     dn::Carve cv;
     const size_t o_t64 = cv.take<double>((size_t)(D.L + 1) * R * D.d), o_w64 = cv.take<double>((size_t)N * D.d),
                  o_t = cv.take<T>((size_t)D.L * R * D.d), o_w = cv.take<T>((size_t)N * D.d);
+    const size_t spec_bytes = dn::tap_spectra_bytes<T>(N, D.periodic, D.d, D.L);
+    const size_t o_s = spec_bytes ? cv.take<double>((spec_bytes + 7) / 8) : 0;
     void *blk = dn::dev_alloc(cv.off, st);
     if (!blk) throw Fail{DN_ENOMEM};
     dn::Plan<T> pl;
@@ -181,6 +183,17 @@ const dn::Plan<T> &ensure_plan(dn_model *m, int N, cudaStream_t st) {
     cudaError_t err = dn::launch_taps(m, N, pl.taps64, pl.omega64, st);
     if (err == cudaSuccess) err = dn::launch_cast<T>(pl.taps64, pl.taps, (long long)D.L * R * D.d, st);
     if (err == cudaSuccess) err = dn::launch_cast<T>(pl.omega64, pl.omega, (long long)N * D.d, st);
+    if (err == cudaSuccess && spec_bytes) {
+        // tap spectra of the FFT convolution (weights only); where the transform does not fit,
+        // the forward keeps the direct convolution
+        pl.spec = base + o_s;
+        err = dn::launch_tap_spectra<T>(N, D.periodic, D.d, D.L, R, pl.taps, pl.spec, st);
+        if (err == cudaErrorNotSupported) {
+            cudaGetLastError();
+            pl.spec = nullptr;
+            err = cudaSuccess;
+        }
+    }
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) {
         dn::dev_free(blk, cv.off, st);
@@ -229,9 +242,13 @@ void run_forward(dn_model *m, const dn::Plan<T> &pl, const dn::Weights<T> &w, in
     }
     if (prec == DN_BF16) throw Fail{DN_EUNSUPPORTED};
     dn::Fields<T> H{h, field, 0, 1}, Uf{u, field, 0, 1}, none{nullptr, 0, 0, 1};
+    const bool fft_conv = dn::use_fft_conv<T>(g, pl);
     for (int l = 1; l <= L; ++l) {
         const T *taps_l = pl.taps + (long long)(l - 1) * g.R * d;
-        ck(dn::launch_conv<T>(g, taps_l, H, l == 1 ? spins : nullptr, w.e, Uf, B, false, nullptr, nullptr, st));
+        if (fft_conv)
+            ck(dn::launch_conv_fft<T>(g, l, pl.spec, H, l == 1 ? spins : nullptr, w.e, Uf, B, st));
+        else
+            ck(dn::launch_conv<T>(g, taps_l, H, l == 1 ? spins : nullptr, w.e, Uf, B, false, nullptr, nullptr, st));
         dn::Fields<T> Y = y ? dn::Fields<T>{y + (long long)(l - 1) * field, (long long)L * field, 0, 1} : none;
         ck(dn::launch_mix<T>(g, l, w, chi, (long long)L * field, 1, 0, Uf, H, Y, pl.omega, pooled + (long long)l * d,
                              (long long)(L + 1) * d, B, false, st));

@@ -59,6 +59,7 @@ struct Plan {
     T *omega = nullptr;       // [N][d] pooling weights (1/N) sum_k g^f_{k-i}
     double *taps64 = nullptr; // [L+1][R][d]
     double *omega64 = nullptr;
+    void *spec = nullptr;     // [L][d][M/2 + 1] complex tap spectra for the FFT convolution, or null
     void *block = nullptr;
     size_t bytes = 0;
 };
@@ -258,6 +259,24 @@ cudaError_t launch_link_fft(int N, int periodic, int d, int R, const T *taps_l, 
                             long long dm_ss, T *band, long long bss, long long brs, long long bos, long long b0,
                             int nb, T *scratch, size_t scratch_elems, cudaStream_t st);
 extern int g_fft_links;
+// The forward pass's S4 convolution by FFT (link_fft.cu): conv_fft_size is the transform
+// length (0 where it does not apply: a ring whose N is not a power of two); the tap spectra
+// of all layers are built with the plan.  g_fft_conv: 0 direct, 1 FP32 with N >= 512
+// (default), 2 wherever the spectra exist.
+int conv_fft_size(int N, int periodic);
+template <typename T>
+size_t tap_spectra_bytes(int N, int periodic, int d, int L);
+template <typename T>
+cudaError_t launch_tap_spectra(int N, int periodic, int d, int L, int R, const T *taps, void *spec, cudaStream_t st);
+template <typename T>
+cudaError_t launch_conv_fft(const Geom &g, int l, const void *spec, Fields<T> in, const int8_t *spins, const T *e,
+                            Fields<T> out, long long F, cudaStream_t st);
+extern int g_fft_conv;
+template <typename T>
+inline bool use_fft_conv(const Geom &g, const Plan<T> &pl) {
+    if (!pl.spec || g_fft_conv == 0) return false;
+    return g_fft_conv == 2 || (sizeof(T) == 4 && g.N >= 512);
+}
 
 // Reverse pass for the parameter log-derivatives (grad.cu).  Operands of the per-sample
 // outer-product sums of one layer, [B][N][.] each.

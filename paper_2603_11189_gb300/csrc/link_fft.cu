@@ -274,10 +274,184 @@ template cudaError_t launch_link_fft<double>(int, int, int, int, const double *,
 
 int g_fft_links = 1;
 
+// ------------------------------------------------------------------------------------------
+// The S4 convolution of the forward pass, u = G x per channel (Eq. resolvent: the kernel is
+// applied in the frequency domain), as IDFT(G^ X^) of length M: on an open chain M is the
+// power of two >= 2N - 1 (the taps g_r, r in (-N, N), sit at circular index r mod M and
+// x is zero-padded, so the circular product is the linear convolution); on a ring M = N,
+// a power of two (the taps are circulant).  Two channels travel in one complex transform.
+
+// M of the FFT convolution, or 0 where it does not apply.
+int conv_fft_size(int N, int periodic) {
+    if (periodic) return (N >= 2 && (N & (N - 1)) == 0) ? N : 0;
+    int M = 2;
+    while (M < 2 * N - 1) M <<= 1;
+    return M;
+}
+
+namespace {
+
+// Tap spectra of every layer: spec[l][c][nu], nu = 0 .. M/2.  One CTA per (layer, channel pair).
+template <typename T>
+__global__ void __launch_bounds__(256) k_tap_spec(int N, int periodic, int d, int M, int R, const T *__restrict__ taps,
+                                                  C2<T> *__restrict__ spec) {
+    extern __shared__ __align__(16) unsigned char smt[];
+    const int logM = ilog2(M), half = M / 2, hs = half + 1;
+    C2<T> *tw = reinterpret_cast<C2<T> *>(smt);
+    C2<T> *b0 = tw + half, *b1 = b0 + M;
+    const int l = blockIdx.x, c0 = 2 * blockIdx.y;
+    fill_twiddles(tw, M);
+    const T *tl = taps + (long long)l * R * d;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        C2<T> v = {0, 0};
+        if (periodic) {
+            v = {tl[(long long)m * d + c0], tl[(long long)m * d + c0 + 1]};
+        } else {
+            const int r = m < half ? m : m - M;
+            if (r > -N && r < N) v = {tl[(long long)(r + N - 1) * d + c0], tl[(long long)(r + N - 1) * d + c0 + 1]};
+        }
+        b0[m] = v;
+    }
+    __syncthreads();
+    const C2<T> *Z = fft_block(b0, b1, tw, M, logM, 1, -1);
+    C2<T> *dst = spec + ((long long)l * d + c0) * hs;
+    for (int nu = threadIdx.x; nu < hs; nu += blockDim.x) {
+        C2<T> X, Y;
+        split_spectra(Z, M, nu, X, Y);
+        dst[nu] = X;
+        dst[hs + nu] = Y;
+    }
+}
+
+// u = G x for F fields, G channels per CTA (G / 2 complex transforms): CTA = (field, group).
+// The input is either a field [N][d] or, for the first layer, e_c s_j from the spins.
+template <typename T>
+__global__ void __launch_bounds__(256) k_conv_fft(int N, int d, int M, int G, const C2<T> *__restrict__ spec_l,
+                                                  Fields<T> in, const int8_t *__restrict__ spins,
+                                                  const T *__restrict__ e, Fields<T> out) {
+    extern __shared__ __align__(16) unsigned char smc[];
+    const int logM = ilog2(M), half = M / 2, hs = half + 1, np = G / 2;
+    C2<T> *tw = reinterpret_cast<C2<T> *>(smc);
+    C2<T> *b0 = tw + half, *b1 = b0 + (size_t)np * M;
+    const int ng = d / G;
+    const long long f = blockIdx.x / ng;
+    const int c0 = (int)(blockIdx.x % ng) * G;
+    fill_twiddles(tw, M);
+    const T *src = spins ? nullptr : in.at(f);
+    const int8_t *sp = spins ? spins + f * N : nullptr;
+    for (int q = threadIdx.x; q < np * M; q += blockDim.x) {
+        const int p = q / M, n = q - p * M, c = c0 + 2 * p;
+        C2<T> v = {0, 0};
+        if (n < N) {
+            if (sp) {
+                const T s = (T)sp[n];
+                v = {e[c] * s, e[c + 1] * s};
+            } else {
+                v = {src[(long long)n * d + c], src[(long long)n * d + c + 1]};
+            }
+        }
+        b0[q] = v;
+    }
+    __syncthreads();
+    const C2<T> *Z = fft_block(b0, b1, tw, M, logM, np, -1);
+    C2<T> *W = Z == b0 ? b1 : b0;
+    for (int q = threadIdx.x; q < np * M; q += blockDim.x) {
+        const int p = q / M, nu = q - p * M, c = c0 + 2 * p;
+        const int nh = nu <= half ? nu : M - nu;
+        C2<T> X, Y;
+        split_spectra(Z + (long long)p * M, M, nh, X, Y);
+        C2<T> w1 = cmul(X, spec_l[(long long)c * hs + nh]);
+        C2<T> w2 = cmul(Y, spec_l[(long long)(c + 1) * hs + nh]);
+        if (nu > half) {   // Hermitian extension of the two real products' spectra
+            w1.y = -w1.y;
+            w2.y = -w2.y;
+        }
+        W[q] = {w1.x - w2.y, w1.y + w2.x};      // w1 + i w2
+    }
+    __syncthreads();
+    const C2<T> *U = fft_block(W, W == b0 ? b1 : b0, tw, M, logM, np, +1);
+    T *dst = out.at(f);
+    const T scale = (T)1 / (T)M;
+    for (int q = threadIdx.x; q < np * N; q += blockDim.x) {
+        const int n = q / np, p = q - n * np, c = c0 + 2 * p;
+        const C2<T> v = U[(long long)p * M + n];
+        dst[(long long)n * d + c] = v.x * scale;
+        dst[(long long)n * d + c + 1] = v.y * scale;
+    }
+}
+
+template <typename T>
+size_t conv_fft_smem(int M, int G) {
+    return ((size_t)M / 2 + 2 * (size_t)(G / 2) * M) * sizeof(C2<T>);
+}
+
+// Channels per CTA: the largest of 8, 4, 2 dividing d whose transforms fit in 100 KB.
+template <typename T>
+int conv_fft_group(int d, int M) {
+    for (int G = 8; G >= 2; G >>= 1)
+        if (d % G == 0 && conv_fft_smem<T>(M, G) <= 100 * 1024) return G;
+    return 0;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_tap_spectra(int N, int periodic, int d, int L, int R, const T *taps, void *spec, cudaStream_t st) {
+    const int M = conv_fft_size(N, periodic);
+    if (M == 0 || d % 2 != 0) return cudaErrorNotSupported;
+    const size_t smem = ((size_t)M / 2 + 2 * (size_t)M) * sizeof(C2<T>);
+    if (smem > 200 * 1024) return cudaErrorNotSupported;
+    cudaError_t err = cudaFuncSetAttribute(k_tap_spec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_tap_spec<T><<<dim3(L, d / 2), 256, smem, st>>>(N, periodic, d, M, R, taps, static_cast<C2<T> *>(spec));
+    return cudaGetLastError();
+}
+
+template <typename T>
+size_t tap_spectra_bytes(int N, int periodic, int d, int L) {
+    const int M = conv_fft_size(N, periodic);
+    return M == 0 ? 0 : (size_t)L * d * (M / 2 + 1) * sizeof(C2<T>);
+}
+
+template <typename T>
+cudaError_t launch_conv_fft(const Geom &g, int l, const void *spec, Fields<T> in, const int8_t *spins, const T *e,
+                            Fields<T> out, long long F, cudaStream_t st) {
+    if (F <= 0) return cudaSuccess;
+    const int M = conv_fft_size(g.N, g.periodic);
+    const int G = M ? conv_fft_group<T>(g.d, M) : 0;
+    if (!spec || G == 0) return cudaErrorNotSupported;
+    const size_t smem = conv_fft_smem<T>(M, G);
+    cudaError_t err = cudaFuncSetAttribute(k_conv_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const C2<T> *spec_l = static_cast<const C2<T> *>(spec) + (long long)(l - 1) * g.d * (M / 2 + 1);
+    {
+        ProfScope _ps("k_conv_fft", st);
+        k_conv_fft<T><<<(unsigned)(F * (g.d / G)), 256, smem, st>>>(g.N, g.d, M, G, spec_l, in, spins, e, out);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tap_spectra<float>(int, int, int, int, int, const float *, void *, cudaStream_t);
+template cudaError_t launch_tap_spectra<double>(int, int, int, int, int, const double *, void *, cudaStream_t);
+template size_t tap_spectra_bytes<float>(int, int, int, int);
+template size_t tap_spectra_bytes<double>(int, int, int, int);
+template cudaError_t launch_conv_fft<float>(const Geom &, int, const void *, Fields<float>, const int8_t *,
+                                            const float *, Fields<float>, long long, cudaStream_t);
+template cudaError_t launch_conv_fft<double>(const Geom &, int, const void *, Fields<double>, const int8_t *,
+                                             const double *, Fields<double>, long long, cudaStream_t);
+
+int g_fft_conv = 1;
+
 }  // namespace dn
 
 extern "C" dn_status dn_set_fft_links(int mode) {
     if (mode < 0 || mode > 2) return DN_EINVAL;
     dn::g_fft_links = mode;
+    return DN_OK;
+}
+
+extern "C" dn_status dn_set_fft_conv(int mode) {
+    if (mode < 0 || mode > 2) return DN_EINVAL;
+    dn::g_fft_conv = mode;
     return DN_OK;
 }

@@ -100,6 +100,7 @@ def _lib():
         "dn_sampler_batch": (i32, [vp, i32, vp, i32, vp, vp, i32, dbl, i32, vp, vp, ctypes.POINTER(SamplerStats)]),
         "dn_set_fused_links": (i32, [i32]),
         "dn_set_fft_links": (i32, [i32]),
+        "dn_set_fft_conv": (i32, [i32]),
         "dn_server_set_idle_limit": (i32, [vp, dbl]),
         "dn_server_kernel_status": (i32, [vp, dbl, ctypes.POINTER(i32)]),
     }
@@ -119,7 +120,8 @@ def exported_symbols():
             "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable",
             "dn_profile_count", "dn_profile_get", "dn_server_create", "dn_server_set_chain", "dn_server_submit",
             "dn_server_wait", "dn_server_get_stats", "dn_server_destroy", "dn_model_nparams", "dn_logpsi_grad", "dn_sr_matrices", "dn_sampler_batch",
-            "dn_set_fused_links", "dn_set_fft_links", "dn_server_set_idle_limit", "dn_server_kernel_status"]
+            "dn_set_fused_links", "dn_set_fft_links", "dn_set_fft_conv", "dn_server_set_idle_limit",
+            "dn_server_kernel_status"]
 
 
 def set_fused_links(on: bool):
@@ -131,6 +133,12 @@ def set_fft_links(mode: int):
     """Band links of one-intermediate pairs: 0 direct sum, 1 FFT where it is the faster one
     (default), 2 FFT wherever the shape allows; all exact."""
     _check(_lib().dn_set_fft_links(int(mode)), "dn_set_fft_links")
+
+
+def set_fft_conv(mode: int):
+    """S4 convolution of the forward pass: 0 direct sum, 1 FFT for FP32 with N >= 512
+    (default), 2 FFT wherever it applies; all exact to rounding."""
+    _check(_lib().dn_set_fft_conv(int(mode)), "dn_set_fft_conv")
 
 
 def _check(status: int, what: str):
