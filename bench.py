@@ -235,6 +235,7 @@ def measure_n1024(dn, synth, torch, barrier, lib, chains, recompute_flips=128, L
     cache bytes the flips need, once, over the layer kernels' device time (a separate
     traced pass) and over the whole ABACUS call."""
     Nn = 1024
+    torch.cuda.empty_cache()          # the caches get fresh allocations, not the earlier workloads' pieces
     desc = synth.ModelDesc(L=L, d=64, s=64, w=2, dh=64, dout=2, periodic=0)
     params = synth.init_params(desc, 1005, a_scale=10.0)
     spins_np = synth.spins_uniform(chains, Nn, 2005)
