@@ -46,7 +46,7 @@ namespace {
 constexpr int kDbD = 32;                             // channels
 constexpr int kDbCols = 128;                         // source columns per CTA
 constexpr int kDbStages = 4;                         // depth of the input ring
-constexpr int kDbBufs = 3;                           // operand buffers and accumulators in flight
+constexpr int kDbBufs = 4;                           // operand buffers and accumulators in flight
 constexpr int kDbAPl = 2;                            // BF16 planes of the A operand (the hop output)
 constexpr int kDbThreads = 512;                      // warpgroups: 0 staging, 1-2 band sums, 3 loads + MMAs
 constexpr int kDbStageRegs = 72, kDbBandRegs = 200, kDbCtlRegs = 40;   // x 128, 256, 128 threads = 512 x 128
@@ -57,8 +57,8 @@ constexpr uint32_t kDbBSlab = kDbD * 32;
 constexpr uint32_t kDbBPlane = 2 * kDbBSlab;
 constexpr uint32_t kDbBBuf = 3 * kDbBPlane;
 constexpr uint32_t kDbFixed = kDbBufs * kDbBBuf + kDbStages * kDbStage;
-// Tensor-memory columns: A operands (3 planes x K = 32 BF16, two per column) and accumulators.
-constexpr uint32_t kDbACols = 3 * 16;
+// Tensor-memory columns: A operands (kDbAPl planes x K = 32 BF16, two per column) and accumulators.
+constexpr uint32_t kDbACols = kDbAPl * 16;
 constexpr uint32_t kDbZCol0 = kDbBufs * kDbACols;                  // accumulators after the A operands
 constexpr uint32_t kDbTmemCols = 256;                               // >= kDbZCol0 + kDbBufs * 32
 constexpr uint32_t kDbTail = (2 * kDbStages + 3 * kDbBufs) * 8 + 16;   // mbarriers, TMEM slot, status
@@ -233,61 +233,58 @@ __global__ void __launch_bounds__(kDbThreads, 1)
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[dl][c] = 0.f;
         bool good = true;
-        // Sites in pairs (m, m + 1): their tap rows overlap (row q4 + N - 1 - m + dl for site m,
-        // one lower for site m + 1), so each row is loaded once for both.  Rows go in descending
-        // order, so every accumulator still receives site m before site m + 1.
-        for (int m = 0; m < N; m += 2) {
-            const bool two = m + 1 < N;
-            const int j0 = m % kDbBufs, j1 = (m + 1) % kDbBufs;
-            bool ok = alive();
-            if (ok) ok = tc::wait(&mmad[j0], (uint32_t)((m / kDbBufs) & 1));
-            if (ok && two) ok = tc::wait(&mmad[j1], (uint32_t)(((m + 1) / kDbBufs) & 1));
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
+        // One site per step; the accumulator columns of site n + 1 are loaded (tcgen05.ld, no
+        // wait) before the band sums of site n and waited for after them, so the tensor-memory
+        // load latency hides behind the FMAs.  Sites go in ascending order, as in the band kernel.
+        auto issue = [&](int n, uint32_t (&dst)[16]) -> bool {
+            const int j = n % kDbBufs;
+            bool ok = alive() && tc::wait(&mmad[j], (uint32_t)((n / kDbBufs) & 1));
+            if (!__all_sync(0xffffffffu, ok)) return false;
+            tc::fence_after();
+            const uint32_t zc = tmem + tlane + kDbZCol0 + (uint32_t)(j * kDbD + 16 * ch);
+            tc::tmem_ld8_async(zc, dst);
+            tc::tmem_ld8_async(zc + 8, dst + 8);
+            return true;
+        };
+        auto release = [&](int n, uint32_t (&r)[16]) {
+            tc::tmem_wait_ld(r, 16);
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) arrive(&zfree[n % kDbBufs]);
+        };
+        uint32_t zc[16];
+        if (!issue(0, zc)) {
+            if (lane == 0) *s_ok = 0;
+            good = false;
+        } else {
+            release(0, zc);
+        }
+        for (int n = 0; n < N && good; ++n) {
+            uint32_t zn[16];
+            const bool nxt = n + 1 < N;
+            if (nxt && !issue(n + 1, zn)) {
                 if (lane == 0) *s_ok = 0;
                 good = false;
                 break;
             }
-            tc::fence_after();
-            // both sites' accumulator columns in four loads, then one wait
-            uint32_t zr[32];
-            const uint32_t zc0 = tmem + tlane + kDbZCol0 + (uint32_t)(j0 * kDbD + 16 * ch);
-            const uint32_t zc1 = tmem + tlane + kDbZCol0 + (uint32_t)((two ? j1 : j0) * kDbD + 16 * ch);
-            tc::tmem_ld8_async(zc0, zr);
-            tc::tmem_ld8_async(zc0 + 8, zr + 8);
-            tc::tmem_ld8_async(zc1, zr + 16);
-            tc::tmem_ld8_async(zc1 + 8, zr + 24);
-            tc::tmem_wait_ld(zr, 32);
-            float z0[16], z1[16];
+            // tap of (site n, offset dl): tap_s row q4 + N - 1 - n + dl
+            const float *tr = tap_s + (size_t)(q4 + N - 1 - n) * kDbD + 16 * ch;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                z0[c] = __uint_as_float(zr[c]);
-                z1[c] = two ? __uint_as_float(zr[16 + c]) : 0.f;
-            }
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                arrive(&zfree[j0]);
-                if (two) arrive(&zfree[j1]);
-            }
-            // row t of the pair: tap_s row q4 + N - 2 - m + t; site m uses it for dl = t - 1,
-            // site m + 1 for dl = t.
-            const float *tr = tap_s + (size_t)(q4 + N - 2 - m) * kDbD + 16 * ch;
-#pragma unroll
-            for (int t = NB; t >= 0; --t) {
-                if (t == 0 && !two) break;
-                const float4 *t4 = reinterpret_cast<const float4 *>(tr + t * kDbD);
+            for (int dl = 0; dl < NB; ++dl) {
+                const float4 *t4 = reinterpret_cast<const float4 *>(tr + dl * kDbD);
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
                     const float4 g = t4[c4];
-                    const float gv[4] = {g.x, g.y, g.z, g.w};
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int c = 4 * c4 + u;
-                        if (t >= 1) acc[t - 1][c] = fmaf(gv[u], z0[c], acc[t - 1][c]);
-                        if (t <= NB - 1 && two) acc[t][c] = fmaf(gv[u], z1[c], acc[t][c]);
-                    }
+                    acc[dl][4 * c4 + 0] = fmaf(g.x, __uint_as_float(zc[4 * c4 + 0]), acc[dl][4 * c4 + 0]);
+                    acc[dl][4 * c4 + 1] = fmaf(g.y, __uint_as_float(zc[4 * c4 + 1]), acc[dl][4 * c4 + 1]);
+                    acc[dl][4 * c4 + 2] = fmaf(g.z, __uint_as_float(zc[4 * c4 + 2]), acc[dl][4 * c4 + 2]);
+                    acc[dl][4 * c4 + 3] = fmaf(g.w, __uint_as_float(zc[4 * c4 + 3]), acc[dl][4 * c4 + 3]);
                 }
+            }
+            if (nxt) {
+                release(n + 1, zn);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) zc[c] = zn[c];
             }
         }
         const int k = k0 + q4;
