@@ -655,6 +655,7 @@ __global__ void __launch_bounds__(256) k_bandconv4g(Geom g, const float *__restr
     const int ch = (int)(blk % chunks);
     const int a = (int)((blk / chunks) % d);
     const long long bl = blk / ((long long)chunks * d);
+#pragma unroll 4
     for (int q = threadIdx.x; q < gx_len; q += blockDim.x) {
         int r = q - pad - (N - 1);
         float v = 0.f;
@@ -666,10 +667,12 @@ __global__ void __launch_bounds__(256) k_bandconv4g(Geom g, const float *__restr
         }
         gx[q] = v;
     }
+#pragma unroll 8
     for (int q = threadIdx.x; q < N * d; q += blockDim.x) {
         const int n = q / d, cc = q - n * d;
         Dsm[q] = gs.Dm[bl * gs.dm_ss + ((long long)n * d + a) * d + cc];
     }
+#pragma unroll 8
     for (int q = threadIdx.x; q < (2 * N - 1) * d; q += blockDim.x) {
         const int rr = q / d, cc = q - rr * d;
         Tsm[q] = gs.taps[(long long)tap_row(rr - (N - 1), N, g.periodic) * d + cc];

@@ -564,11 +564,14 @@ __global__ void __launch_bounds__(kGwThreads, 1) k_tgemm_genp_ws(Geom g, const f
     const long long za = blockIdx.z;
     const int a = (int)(za % d);
     const long long bl = za / d;
+#pragma unroll 4
     for (int q = tid; q < 2 * N - 1; q += blockDim.x) gx[q] = taps[(long long)tap_row_tc(q - (N - 1), N, g.periodic) * d + a];
+#pragma unroll 4
     for (int q = tid; q < N * d; q += blockDim.x) {
         const int n = q / d, c = q - n * d;
         Dfull[q] = gDm[bl * dm_ss + ((long long)n * d + a) * d + c];
     }
+#pragma unroll 4
     for (int q = tid; q < (2 * N - 1) * d; q += blockDim.x) {
         const int rr = q / d, c = q - rr * d;
         Tfull[q] = gtaps[(long long)tap_row_tc(rr - (N - 1), N, g.periodic) * d + c];
