@@ -14,6 +14,8 @@
 //  k_readout  Omega = A^T sum_l pooled_l, log psi = sum_k f(Omega_k).
 #include <math.h>
 
+#include <type_traits>
+
 #include "dn_internal.cuh"
 
 namespace dn {
@@ -159,8 +161,11 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
     T *phT = reinterpret_cast<T *>(smraw);      // [dh][kChiTS]
     T *acT = phT + dh * kChiTS;                 // [dh][kChiTS]
     T *sw = acT + dh * kChiTS;                  // [tile + 2w] spins of the tile's windows
-    T *W1s = sw + ((kChiTile + 2 * wd + 1) & ~1);   // [f][e] = W1[e][f]
-    T *W2s = W1s + dh * (dh + 1);               // [e][c] = W2[c][e]
+    // FP32 with staged weights and dh, d multiples of 4: 4 outputs x 4 sites per thread from
+    // 16-byte weight and activation loads (weight rows padded by 4); else 1 output x 8 sites.
+    const bool tiled = std::is_same<T, float>::value && stage && dh % 4 == 0 && d % 4 == 0;
+    T *W1s = sw + ((kChiTile + 2 * wd + 3) & ~3);   // [f][e] = W1[e][f]
+    T *W2s = W1s + dh * (dh + 4);               // [e][c] = W2[c][e]
     const int ntile = (N + kChiTile - 1) / kChiTile;
     const int l = blockIdx.y;
     const T *kap = w.kappa + (long long)l * W * dh;
@@ -171,12 +176,12 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
     // when they do not fit.
     const T *W1p = stage ? W1s : w.W1T + (long long)l * dh * dh;
     const T *W2p = stage ? W2s : w.W2T + (long long)l * dh * d;
-    const int s1 = stage ? dh + 1 : dh, s2 = stage ? d + 1 : d;
+    const int s1 = stage ? (tiled ? dh + 4 : dh + 1) : dh, s2 = stage ? (tiled ? d + 4 : d + 1) : d;
     if (stage) {
         for (int q = threadIdx.x; q < dh * dh; q += blockDim.x)
-            W1s[(q / dh) * (dh + 1) + q % dh] = w.W1T[(long long)l * dh * dh + q];
+            W1s[(q / dh) * s1 + q % dh] = w.W1T[(long long)l * dh * dh + q];
         for (int q = threadIdx.x; q < dh * d; q += blockDim.x)
-            W2s[(q / d) * (d + 1) + q % d] = w.W2T[(long long)l * dh * d + q];
+            W2s[(q / d) * s2 + q % d] = w.W2T[(long long)l * dh * d + q];
     }
     const long long items = (long long)B * ntile;
     for (int it = 0; it < kChiTPB; ++it) {
@@ -209,38 +214,90 @@ __global__ void __launch_bounds__(256) k_chi(Geom g, Weights<T> w, const int8_t 
             phT[e * kChiTS + t] = acc;
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < dh * (kChiTile / kChiRG); q += blockDim.x) {
-            const int e = q % dh, t0 = (q / dh) * kChiRG;
-            T acc[kChiRG];
+        if (!tiled) {
+            for (int q = threadIdx.x; q < dh * (kChiTile / kChiRG); q += blockDim.x) {
+                const int e = q % dh, t0 = (q / dh) * kChiRG;
+                T acc[kChiRG];
 #pragma unroll
-            for (int u = 0; u < kChiRG; ++u) acc[u] = b1[e];
-            for (int f = 0; f < dh; ++f) {
-                const T wv = W1p[f * s1 + e];
-                T pv[8];
-                lds8<T>(phT + f * kChiTS + t0, pv);
+                for (int u = 0; u < kChiRG; ++u) acc[u] = b1[e];
+                for (int f = 0; f < dh; ++f) {
+                    const T wv = W1p[f * s1 + e];
+                    T pv[8];
+                    lds8<T>(phT + f * kChiTS + t0, pv);
 #pragma unroll
-                for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pv[u];
+                    for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pv[u];
+                }
+#pragma unroll
+                for (int u = 0; u < kChiRG; ++u) acT[e * kChiTS + t0 + u] = gelu<T>(acc[u]);
             }
+            __syncthreads();
+            T *dst = chi + ((b * L + l) * N + i0) * d;
+            for (int q = threadIdx.x; q < d * (kChiTile / kChiRG); q += blockDim.x) {
+                const int c = q % d, t0 = (q / d) * kChiRG;
+                T acc[kChiRG];
 #pragma unroll
-            for (int u = 0; u < kChiRG; ++u) acT[e * kChiTS + t0 + u] = gelu<T>(acc[u]);
-        }
-        __syncthreads();
-        T *dst = chi + ((b * L + l) * N + i0) * d;
-        for (int q = threadIdx.x; q < d * (kChiTile / kChiRG); q += blockDim.x) {
-            const int c = q % d, t0 = (q / d) * kChiRG;
-            T acc[kChiRG];
+                for (int u = 0; u < kChiRG; ++u) acc[u] = b2[c];
+                for (int e = 0; e < dh; ++e) {
+                    const T wv = W2p[e * s2 + c];
+                    T pv[8];
+                    lds8<T>(acT + e * kChiTS + t0, pv);
 #pragma unroll
-            for (int u = 0; u < kChiRG; ++u) acc[u] = b2[c];
-            for (int e = 0; e < dh; ++e) {
-                const T wv = W2p[e * s2 + c];
-                T pv[8];
-                lds8<T>(acT + e * kChiTS + t0, pv);
+                    for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pv[u];
+                }
 #pragma unroll
-                for (int u = 0; u < kChiRG; ++u) acc[u] += wv * pv[u];
+                for (int u = 0; u < kChiRG; ++u)
+                    if (t0 + u < ns) dst[(long long)(t0 + u) * d + c] = acc[u];
             }
+
+        } else if constexpr (std::is_same<T, float>::value) {
+            for (int q = threadIdx.x; q < (dh / 4) * (kChiTile / 4); q += blockDim.x) {
+                const int e0 = (q % (dh / 4)) * 4, t0 = (q / (dh / 4)) * 4;
+                float acc[4][4];
 #pragma unroll
-            for (int u = 0; u < kChiRG; ++u)
-                if (t0 + u < ns) dst[(long long)(t0 + u) * d + c] = acc[u];
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[j][u] = b1[e0 + j];
+#pragma unroll 4
+                for (int f = 0; f < dh; ++f) {
+                    const float4 wv = *reinterpret_cast<const float4 *>(W1s + f * s1 + e0);
+                    const float4 pv = *reinterpret_cast<const float4 *>(phT + f * kChiTS + t0);
+                    const float w4[4] = {wv.x, wv.y, wv.z, wv.w}, p4[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) acc[j][u] = fmaf(w4[j], p4[u], acc[j][u]);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    *reinterpret_cast<float4 *>(acT + (e0 + j) * kChiTS + t0) =
+                        make_float4(gelu<float>(acc[j][0]), gelu<float>(acc[j][1]), gelu<float>(acc[j][2]),
+                                    gelu<float>(acc[j][3]));
+            }
+            __syncthreads();
+            float *dst = chi + ((b * L + l) * N + i0) * d;
+            for (int q = threadIdx.x; q < (d / 4) * (kChiTile / 4); q += blockDim.x) {
+                const int c0 = (q % (d / 4)) * 4, t0 = (q / (d / 4)) * 4;
+                float acc[4][4];   // [site][output]
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[u][j] = b2[c0 + j];
+#pragma unroll 4
+                for (int e = 0; e < dh; ++e) {
+                    const float4 wv = *reinterpret_cast<const float4 *>(W2s + e * s2 + c0);
+                    const float4 pv = *reinterpret_cast<const float4 *>(acT + e * kChiTS + t0);
+                    const float w4[4] = {wv.x, wv.y, wv.z, wv.w}, p4[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[u][j] = fmaf(w4[j], p4[u], acc[u][j]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (t0 + u < ns)
+                        *reinterpret_cast<float4 *>(dst + (long long)(t0 + u) * d + c0) =
+                            make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+            }
         }
     }
 }
@@ -249,8 +306,8 @@ template <typename T>
 cudaError_t launch_chi(const Geom &g, const Weights<T> &w, const int8_t *spins, int B, T *chi, cudaStream_t st) {
     const int ntile = (g.N + kChiTile - 1) / kChiTile;
     const long long groups = ((long long)B * ntile + kChiTPB - 1) / kChiTPB;
-    const size_t act = ((size_t)2 * kChiTS * g.dh + (size_t)((kChiTile + 2 * g.w + 1) & ~1)) * sizeof(T);
-    const size_t wts = ((size_t)g.dh * (g.dh + 1) + (size_t)g.dh * (g.d + 1)) * sizeof(T);
+    const size_t act = ((size_t)2 * kChiTS * g.dh + (size_t)((kChiTile + 2 * g.w + 3) & ~3)) * sizeof(T);
+    const size_t wts = ((size_t)g.dh * (g.dh + 4) + (size_t)g.dh * (g.d + 4)) * sizeof(T);
     const int stage = act + wts <= 200 * 1024 ? 1 : 0;
     const size_t smem = act + (stage ? wts : 0);
     cudaError_t err = cudaFuncSetAttribute(k_chi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
