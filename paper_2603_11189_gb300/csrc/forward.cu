@@ -484,12 +484,134 @@ __global__ void k_mix(Geom g, int l, Weights<T> w, const T *__restrict__ chi, lo
     }
 }
 
+// FP32 form of k_mix for d in {16, 32, 64, 128}: the two d x d matrices staged once per
+// CTA (rows padded by 4), rows in tiles of RT = 4096 / d, each thread forms 4 outputs x 4 rows
+// of both products from 16-byte loads (weights along the outputs, the tile's inputs stored
+// transposed along the rows).  Products and summation order per output are those of k_mix.
+__global__ void __launch_bounds__(256) k_mix_t(Geom g, int l, Weights<float> w, const float *__restrict__ chi,
+                                               long long chi_stride, long long fps, long long f0, Fields<float> in,
+                                               Fields<float> out, Fields<float> yout, const float *__restrict__ omega,
+                                               double *__restrict__ pooled, long long pooled_stride, int adjoint) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = g.N, d = g.d, RT = 4096 / d, ws = d + 4, xs = RT + 4;
+    float *M1 = reinterpret_cast<float *>(smraw);   // [bb][a] = m1t[bb d + a], row stride d + 4
+    float *M2 = M1 + d * ws;
+    float *xT = M2 + d * ws;                        // [bb][r] tile inputs, row stride RT + 4
+    float *tT = xT + d * xs;                        // [bb][r] chi . y of the tile
+    double *red = reinterpret_cast<double *>(tT + d * xs);   // [RT / 4][d] pooled partials
+    const long long f = blockIdx.x;
+    const long long b = (f0 + f) / fps;
+    const float *chib = chi + b * chi_stride + (long long)(l - 1) * N * d;
+    const long long dd = (long long)d * d, lo = (long long)(l - 1) * dd;
+    const float *m1t = adjoint ? w.U + lo : w.VT + lo;
+    const float *m2t = adjoint ? w.V + lo : w.UT + lo;
+    for (int q = threadIdx.x; q < d * d; q += blockDim.x) {
+        M1[(q / d) * ws + q % d] = m1t[q];
+        M2[(q / d) * ws + q % d] = m2t[q];
+    }
+    const float *src = in.at(f);
+    float *dst = out.at(f);
+    float *ydst = yout.base ? yout.at(f) : nullptr;
+    const int a0 = 4 * (int)(threadIdx.x % (d / 4)), r0 = 4 * (int)(threadIdx.x / (d / 4));
+    double pacc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i0 = 0; i0 < N; i0 += RT) {
+        __syncthreads();   // weights staged / the previous tile's xT and tT read
+        for (int q = threadIdx.x; q < RT * d; q += blockDim.x) {
+            const int r = q / d, bb = q % d;
+            xT[bb * xs + r] = i0 + r < N ? src[(long long)(i0 + r) * d + bb] : 0.f;
+        }
+        __syncthreads();
+        float acc[4][4];   // [row][output]
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[u][j] = 0.f;
+#pragma unroll 4
+        for (int bb = 0; bb < d; ++bb) {
+            const float4 mv = *reinterpret_cast<const float4 *>(M1 + bb * ws + a0);
+            const float4 xv = *reinterpret_cast<const float4 *>(xT + bb * xs + r0);
+            const float m4[4] = {mv.x, mv.y, mv.z, mv.w}, x4[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[u][j] = fmaf(m4[j], x4[u], acc[u][j]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + r0 + u;
+            float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < N) {
+                if (ydst) *reinterpret_cast<float4 *>(ydst + (long long)i * d + a0) =
+                              make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+                cv = *reinterpret_cast<const float4 *>(chib + (long long)i * d + a0);
+            }
+            tT[(a0 + 0) * xs + r0 + u] = cv.x * acc[u][0];
+            tT[(a0 + 1) * xs + r0 + u] = cv.y * acc[u][1];
+            tT[(a0 + 2) * xs + r0 + u] = cv.z * acc[u][2];
+            tT[(a0 + 3) * xs + r0 + u] = cv.w * acc[u][3];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[u][j] = 0.f;
+#pragma unroll 4
+        for (int bb = 0; bb < d; ++bb) {
+            const float4 mv = *reinterpret_cast<const float4 *>(M2 + bb * ws + a0);
+            const float4 tv = *reinterpret_cast<const float4 *>(tT + bb * xs + r0);
+            const float m4[4] = {mv.x, mv.y, mv.z, mv.w}, t4[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[u][j] = fmaf(m4[j], t4[u], acc[u][j]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + r0 + u;
+            if (i >= N) continue;
+            *reinterpret_cast<float4 *>(dst + (long long)i * d + a0) =
+                make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+            if (pooled) {
+                const float4 om = *reinterpret_cast<const float4 *>(omega + (long long)i * d + a0);
+                pacc[0] += (double)om.x * (double)acc[u][0];
+                pacc[1] += (double)om.y * (double)acc[u][1];
+                pacc[2] += (double)om.z * (double)acc[u][2];
+                pacc[3] += (double)om.w * (double)acc[u][3];
+            }
+        }
+    }
+    if (pooled) {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[(r0 / 4) * d + a0 + j] = pacc[j];
+        __syncthreads();
+        for (int a = threadIdx.x; a < d; a += blockDim.x) {
+            double sum = 0.0;
+            for (int q = 0; q < RT / 4; ++q) sum += red[q * d + a];
+            pooled[f * pooled_stride + a] = sum;
+        }
+    }
+}
+
 template <typename T>
 cudaError_t launch_mix(const Geom &g, int l, const Weights<T> &w, const T *chi, long long chi_stride,
                           long long fields_per_sample, long long f0, Fields<T> in, Fields<T> out, Fields<T> yout,
                           const T *omega, double *pooled, long long pooled_stride, long long F, bool adjoint,
                           cudaStream_t st) {
     if (F <= 0) return cudaSuccess;
+    if constexpr (std::is_same<T, float>::value) {
+        if (g.d == 16 || g.d == 32 || g.d == 64 || g.d == 128) {
+            const int RT = 4096 / g.d;
+            const size_t smem = (2 * (size_t)g.d * (g.d + 4) + 2 * (size_t)g.d * (RT + 4)) * sizeof(float) +
+                                (size_t)(RT / 4) * g.d * sizeof(double);
+            cudaError_t err = cudaFuncSetAttribute(k_mix_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            ProfScope _ps("k_mix", st);
+            k_mix_t<<<(unsigned)F, 256, smem, st>>>(g, l, w, chi, chi_stride, fields_per_sample, f0, in, out, yout,
+                                                    omega, pooled, pooled_stride, adjoint ? 1 : 0);
+            return cudaGetLastError();
+        }
+    }
     int TS = 256 / g.d;
     if (TS < 1) TS = 1;
     const int threads = TS * g.d;
