@@ -892,12 +892,122 @@ __global__ void __launch_bounds__(128) k_dhop_tc(int N, int P, const float *__re
     if (warp == 0) tc::tmem_free(tmem, cols);
 }
 
+// Vertex hop for a column count of at most one tile (the embedding chain, P = N <= 128): a
+// CTA loops over sites n = blockIdx.y, + gridDim.y, ... of one configuration, so the tensor
+// memory and barrier set-up are paid once, and the next site's input column is loaded into
+// registers while the current site's operands are staged, multiplied and stored.  Products,
+// planes and order as in k_dhop_tc.
+template <int D, int NPL>
+__global__ void __launch_bounds__(128) k_dhop_tc_sites(int N, int P, const float *__restrict__ Dm, long long dm_ss,
+                                                       const float *__restrict__ Yin, float *__restrict__ Xo,
+                                                       unsigned *__restrict__ flag) {
+    extern __shared__ __align__(1024) unsigned char smd[];
+    constexpr int ns = D / 16;
+    constexpr uint32_t aslab = 128 * 32, bslab = D * 32, aplane = ns * aslab, bplane = ns * bslab;
+    constexpr uint32_t cols = D < 32 ? 32 : D;
+    constexpr int NPA = NPL == 3 ? 2 : NPL;
+    unsigned char *Ap = smd;
+    unsigned char *Bp = Ap + NPL * aplane;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Bp + NPL * bplane);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    int *s_ok = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long bl = blockIdx.z;
+    if (tid == 0) {
+        tc::mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *s_ok = 1;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, cols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16(128, D);
+    const long long cs = (long long)N * P;
+    const bool valid = tid < P;
+    auto load_col = [&](float (&buf)[D], int n) {
+        const float *yg = Yin + (bl * D * N + n) * (long long)P + (valid ? tid : 0);
+#pragma unroll
+        for (int u = 0; u < D; ++u) buf[u] = valid ? yg[u * cs] : 0.f;
+    };
+    float va[D];
+    const int n0 = blockIdx.y, ng = gridDim.y;
+    if (n0 < N) load_col(va, n0);
+    uint32_t phase = 0;
+    for (int n = n0; n < N; n += ng) {
+        const float *Dn = Dm + bl * dm_ss + (long long)n * D * D;
+        for (int q = tid; q < D * (D / 8); q += blockDim.x) {
+            const int c = q / (D / 8), k8 = (q % (D / 8)) * 8;
+            tc::stage8_planes<NPL>(Bp, bplane, (uint32_t)(k8 >> 4) * bslab + tc::canon(c, k8 & 15), Dn + (long long)c * D + k8);
+        }
+#pragma unroll
+        for (int a16 = 0; a16 < D; a16 += 16) {
+            tc::stage8_planes<NPA>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 0), va + a16);
+            tc::stage8_planes<NPA>(Ap, aplane, (uint32_t)(a16 >> 4) * aslab + tc::canon(tid, 8), va + a16 + 8);
+        }
+        if (n + ng < N) load_col(va, n + ng);
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+#pragma unroll 1
+            for (int s = 0; s < ns; ++s)
+#pragma unroll
+                for (int pa = 0; pa < NPA; ++pa)
+#pragma unroll
+                    for (int pb = 0; pa + pb < NPL; ++pb)
+                        tc::mma_bf16(tmem, tc::desc(tc::smem_u32(Ap + pa * aplane + s * aslab)),
+                                     tc::desc(tc::smem_u32(Bp + pb * bplane + s * bslab)), idesc,
+                                     (s == 0 && pa == 0 && pb == 0) ? 0u : 1u);
+            tc::commit(mbar);
+        }
+        if (warp == 0 && !tc::wait(mbar, phase) && lane == 0) *s_ok = 0;
+        phase ^= 1u;
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (!*s_ok) break;
+        float *xg = Xo + (bl * D * N + n) * (long long)P + (valid ? tid : 0);
+#pragma unroll 1
+        for (int c8 = 0; c8 < D; c8 += 8, xg += 8 * cs) {
+            float f[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c8, f);
+            if (valid)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) xg[u * cs] = f[u];
+        }
+        // the next site overwrites both operands and the accumulator
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
+    if (!*s_ok && tid == 0 && flag) atomicOr(flag, 8u);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(tmem, cols);
+}
+
 template <int D, int NPL>
 static cudaError_t launch_dhop_tc_dp(int N, int P, const float *Dm, long long dm_ss, const float *Y, float *Xo, int nb,
                                      unsigned *flag, cudaStream_t st) {
     constexpr int ns = D / 16;
     const size_t smem = (size_t)NPL * ns * (128 * 32 + D * 32) + 32;
     const int ntiles = (P + 127) / 128;
+    if (ntiles == 1) {
+        // one tile per site: CTAs loop over sites, about seven per SM over the whole grid
+        long long ng = (7LL * 152 + nb - 1) / nb;
+        ng = ng < 1 ? 1 : (ng > N ? N : ng);
+        cudaError_t err =
+            cudaFuncSetAttribute(k_dhop_tc_sites<D, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        {
+            ProfScope _ps("k_dhop", st);
+            k_dhop_tc_sites<D, NPL><<<dim3(1, (unsigned)ng, (unsigned)nb), 128, smem, st>>>(N, P, Dm, dm_ss, Y, Xo, flag);
+        }
+        return cudaGetLastError();
+    }
     const int cg = ntiles < 4 ? ntiles : 4;      // column tiles split over at most 4 CTAs per site
     dim3 grid((unsigned)cg, (unsigned)N, (unsigned)nb);
     cudaError_t err = cudaFuncSetAttribute(k_dhop_tc<D, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
