@@ -484,7 +484,7 @@ __global__ void k_mix(Geom g, int l, Weights<T> w, const T *__restrict__ chi, lo
     }
 }
 
-// FP32 form of k_mix for d in {16, 32, 64, 128}: the two d x d matrices staged once per
+// FP32 form of k_mix for d in {16, 32, 64}: the two d x d matrices staged once per
 // CTA (rows padded by 4), rows in tiles of RT = 4096 / d, each thread forms 4 outputs x 4 rows
 // of both products from 16-byte loads (weights along the outputs, the tile's inputs stored
 // transposed along the rows).  Products and summation order per output are those of k_mix.
@@ -600,7 +600,7 @@ cudaError_t launch_mix(const Geom &g, int l, const Weights<T> &w, const T *chi, 
                           cudaStream_t st) {
     if (F <= 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
-        if (g.d == 16 || g.d == 32 || g.d == 64 || g.d == 128) {
+        if (g.d == 16 || g.d == 32 || g.d == 64) {
             const int RT = 4096 / g.d;
             const size_t smem = (2 * (size_t)g.d * (g.d + 4) + 2 * (size_t)g.d * (RT + 4)) * sizeof(float) +
                                 (size_t)(RT / 4) * g.d * sizeof(double);
