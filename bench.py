@@ -808,7 +808,7 @@ def read_profile(lib):
 # full-size launch's traffic is the ratio times its algorithmic units.  Valid for the
 # kernels as captured: a family whose kernel changes is reported with traffic null until
 # it is captured again.
-DRAM_PER_UNIT = {"abacus": 1.076, "links_dhop": 0.908, "links_bandconv": 0.964, "links_dband": 0.994,
+DRAM_PER_UNIT = {"abacus": 1.076, "links_dhop": 0.857, "links_bandconv": 0.964, "links_dband": 0.994,
                  "links_bandconv_gen": 0.0105, "links_tgemm_tc": 0.01665}
 
 
