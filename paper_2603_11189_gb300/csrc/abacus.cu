@@ -440,12 +440,11 @@ cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T>
 constexpr int kLayMaxW = 9;
 constexpr int kDxTPB = 8;   // most row tiles per CTA of k_dchi_table (fewer when the grid would not fill the GPU)
 
-// One CTA per (64 (flip, slot) rows, layer).  The MLP weights are staged once; the
-// activations are kept transposed ([feature][row]) so that a thread (output feature, group
-// of 8 rows) reads its 8 rows as two 16-byte broadcasts and its weight row without bank
-// conflicts (row stride dh + 1 / d + 1).  Each tile first resolves its rows once: the
-// flipped spin window of the row (W values) and the offset of the row's chi entry (-1
-// where slot site j - w + t lies off an open chain).
+// A CTA takes up to tpb consecutive tiles of 64 (flip, slot) rows of one layer and stages
+// that layer's MLP weights once for all of them.  The activations are kept transposed
+// ([feature][row]), so a thread reads its rows as 16-byte broadcasts.  Each tile first
+// resolves its rows once: the flipped spin window of the row (W values) and the offset of
+// the row's chi entry (-1 where slot site j - w + t lies off an open chain).
 template <typename T>
 __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__ DX, int tpb) {
     extern __shared__ __align__(16) unsigned char smraw[];
