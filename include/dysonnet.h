@@ -166,6 +166,23 @@ dn_status abacus_flip_ratios(const dn_cache *cache, const int32_t *sample_dev, c
  * Errors: DN_EINVAL, DN_ECUDA. */
 dn_status abacus_single_flip_ratios(const dn_cache *cache, double *dlogpsi_dev, void *stream);
 
+/* ABACUS for the pair flips {j, j + delta} of every site j of every cached
+ * configuration, for n_bonds (1 or 2) distinct separations (the connected
+ * configurations of a J1-J2 chain are the antialigned pairs at delta = 1, 2;
+ * Sec. "ABACUS", cluster flips):
+ *   bonds [n_bonds] int32, HOST memory: the separations delta,
+ *     1 <= delta <= max_cluster - 1 of the cache;
+ *   dlogpsi_dev [B][n_bonds][N] float64: entry (b, k, j) = log psi(sigma_b with
+ *     sites j and j + bonds[k] flipped) - log psi(sigma_b); on a ring j + delta
+ *     wraps, on an open chain a pair past the end gives 0.
+ * Same results as abacus_flip_ratios() on the list of these pairs; the pairs of a
+ * configuration are processed by site, both separations together, so that each
+ * link block is read from memory once per site and layer pair.
+ * Errors: DN_EINVAL (null pointers, n_bonds not 1 or 2, a separation out of
+ * range, equal separations), DN_ECUDA. */
+dn_status abacus_pair_flip_ratios(const dn_cache *cache, int n_bonds, const int32_t *bonds, double *dlogpsi_dev,
+                                  void *stream);
+
 /* Local energy E_loc(sigma) = sum_sigma' <sigma|H|sigma'> psi(sigma')/psi(sigma)
  * (Eq. local-estimator) for B configurations, every ratio by ABACUS:
  *   eloc_dev [B] float64.  Builds and frees its own caches (in chunks of

@@ -440,13 +440,30 @@ cudaError_t launch_abacus(const dn_model *m, const Plan<T> &pl, const Weights<T>
 constexpr int kLayMaxW = 9;
 constexpr int kDxTPB = 8;   // most row tiles per CTA of k_dchi_table (fewer when the grid would not fill the GPU)
 
+// The flips that the grouped kernels evaluate for every site j of every configuration:
+// for each of nb bonds the set {j, j + delta} (delta = 0: the single flip of j).  A
+// flip's slice is the W + delta sites j - w ... j + delta + w (Sec. "ABACUS", cluster
+// flips: the window grows by the extent of the cluster); its rows are padded to Wm =
+// W + the largest delta slots.  Row r = ((b N + j) nb + bond) Wm + t holds slot t (site
+// j - w + t) of the flip; slots t >= W + delta are unused.  Single flips are
+// {nb = 1, Wm = W, delta = 0}.  With anti set, only the pairs of antialigned spins are
+// evaluated (the connected configurations of an exchange coupling); the others give 0.
+struct FlipPattern {
+    int nb, Wm;
+    int bond[2];
+    int anti;
+};
+// fp.bond[k] without a dynamic index into the parameter (which would copy it to local memory)
+__device__ __forceinline__ int bond_of(const FlipPattern &fp, int k) { return k == 0 ? fp.bond[0] : fp.bond[1]; }
+
 // A CTA takes up to tpb consecutive tiles of 64 (flip, slot) rows of one layer and stages
 // that layer's MLP weights once for all of them.  The activations are kept transposed
 // ([feature][row]), so a thread reads its rows as 16-byte broadcasts.  Each tile first
 // resolves its rows once: the flipped spin window of the row (W values) and the offset of
 // the row's chi entry (-1 where slot site j - w + t lies off an open chain).
-template <typename T>
-__global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__ DX, int tpb) {
+template <typename T, bool PR>
+__global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, FlipPattern fp, T *__restrict__ DX, int tpb) {
+    if constexpr (!PR) fp = FlipPattern{1, 2 * a.g.w + 1, {0, 0}, 0};   // single flips: compile-time row layout
     extern __shared__ __align__(16) unsigned char smraw[];
     const Geom &g = a.g;
     const int N = g.N, d = g.d, dh = g.dh, L = g.L, wd = g.w, W = g.W;
@@ -463,7 +480,8 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
     T *W2s = W1s + dh * ws1;                                // [e][c] = W2[c][e], row stride ws2
     T *win = W2s + dh * ws2;                                // [RT][W] flipped spin window of the row
     const int l = blockIdx.y;
-    const long long rows = (long long)a.B * N * W;
+    const int Wm = PR ? fp.Wm : W, nb = PR ? fp.nb : 1;
+    const long long rows = (long long)a.B * N * nb * Wm;
     const T *W1T = a.w.W1T + (long long)l * dh * dh, *W2T = a.w.W2T + (long long)l * dh * d;
     const T *b1 = a.w.b1 + (long long)l * dh, *b2 = a.w.b2 + (long long)l * d;
     const T *kap = a.w.kappa + (long long)l * W * dh, *beta = a.w.beta + (long long)l * dh;
@@ -477,11 +495,17 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
             const long long r = r0 + rr;
             long long off = -1;
             if (r < rows) {
-                const int t = (int)(r % W), j = (int)((r / W) % N);
-                const long long b = r / ((long long)W * N);
+                const int t = (int)(r % Wm);
+                const long long fb = r / Wm;   // (b N + j) nb + bond
+                const int dl = PR ? bond_of(fp, (int)(fb % nb)) : 0, j = (int)((fb / nb) % N);
+                const long long b = fb / ((long long)nb * N);
                 const int8_t *sp = a.spins + b * N;
                 const int iu = j - wd + t;
-                if (g.periodic || (iu >= 0 && iu < N)) {
+                // partner of a pair (-1: none); a pair past an open end is not a flip
+                int jp = -1;
+                if (dl > 0) jp = g.periodic ? (j + dl) % N : (j + dl < N ? j + dl : -2);
+                if (PR && fp.anti && jp >= 0 && sp[j] == sp[jp]) jp = -2;
+                if (t < W + dl && jp != -2 && (g.periodic || (iu >= 0 && iu < N))) {
                     off = ((b * L + l) * N + (g.periodic ? ((iu % N) + N) % N : iu)) * d;
                     for (int o = -wd; o <= wd; ++o) {
                         int jn = iu + o;
@@ -492,7 +516,7 @@ __global__ void __launch_bounds__(256) k_dchi_table(AbArgs<T> a, T *__restrict__
                         } else {
                             v = (jn >= 0 && jn < N) ? (T)sp[jn] : (T)0;
                         }
-                        if (jn == j) v = -v;
+                        if (jn == j || jn == jp) v = -v;
                         win[rr * W + o + wd] = v;
                     }
                 }
@@ -778,6 +802,245 @@ __global__ void __launch_bounds__(256) k_ab_layer(AbArgs<T> a, int l, T *__restr
             }
             v = warp_sum<double>(v);
             if (lane == 0) PART[(((long long)b * N + jq[q]) * W + q) * dout + k] += v;
+        }
+    }
+}
+
+// Layer l of the grouped pair flips of a FlipPattern.  A CTA of nw warps takes a run of nw
+// consecutive sites i0 .. i0 + nw - 1 of one configuration, warp r the site i = i0 + r.
+// For bond delta the site is slot q of the W + delta flips j = i + w - q (pairs
+// {j, j + delta}); consecutive sites share all but one of them, so the run needs only the
+// nw + W + delta - 1 flips of a window, whose states s^(m) are staged once per CTA.  Every
+// link block K^(l,m)_{i, i+dk} (|dk| <= Wm - 1) is read once per site and applied to the
+// flips of all bonds whose slice holds site i + dk.  The terms are those of the flip-list
+// kernel with the slice [j - w, j + delta + w]: the slice Toeplitz term of the previous
+// layer's states, the embedding links of both flipped sites (Eq. Lmn with m = 0), the
+// interlayer links (Eq. recur_step), then s^(l) = U (dchi * (y + V p)) and its
+// contribution rho^(l) . s^(l) to the flip's partial dOmega.
+constexpr int kPrMaxWs = 8;   // slots per flip (W + delta)
+constexpr int kPrMaxFl = 48;  // flips per bond in a CTA's window (nw + W + delta - 1)
+
+template <typename T, int HD>
+__global__ void __launch_bounds__(256) k_ab_pairs(AbArgs<T> a, FlipPattern fp, int l, T *__restrict__ S,
+                                                  const T *__restrict__ DX, double *__restrict__ PART) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int jwin[2][kPrMaxFl];   // wrapped flip site of window entry fl, or -1 (no flip)
+    const Geom &g = a.g;
+    const int N = g.N, d = g.d, L = g.L, wd = g.w, W = g.W, dout = g.dout, nb = fp.nb, Wm = fp.Wm;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long dd = (long long)d * d;
+    const int ws0 = W + fp.bond[0], ws1 = nb > 1 ? W + fp.bond[1] : 0;
+    T *VTs = reinterpret_cast<T *>(smraw);                       // [d][d] = V^T
+    T *UTs = VTs + dd;                                           // [d][d] = U^T
+    T *Sw0 = UTs + dd;                                           // bond 0: [nw + ws0 - 1][ws0][d]
+    T *Sw1 = Sw0 + (size_t)(nw + ws0 - 1) * ws0 * d;             // bond 1: [nw + ws1 - 1][ws1][d]
+    T *pq = Sw1 + (size_t)(nw + ws1 - 1) * ws1 * d + (size_t)warp * (nb * Wm + 1) * d;   // [nb][Wm][d] of the warp
+    T *gb = pq + (size_t)nb * Wm * d;                            // [d]
+    const long long lo = l - 1;
+    const long long b = blockIdx.y;
+    const int i0 = blockIdx.x * nw, i = i0 + warp;
+    const bool active = i < N;
+    const int8_t *sp = a.spins + b * N;
+    for (int q = threadIdx.x; q < dd; q += blockDim.x) {
+        VTs[q] = a.w.VT[lo * dd + q];
+        UTs[q] = a.w.UT[lo * dd + q];
+    }
+    for (int x = threadIdx.x; x < 2 * kPrMaxFl; x += blockDim.x) {
+        const int bo = x / kPrMaxFl, fl = x % kPrMaxFl;
+        int jw = -1;
+        if (bo < nb) {
+            const int dl = bond_of(fp, bo), ws = W + dl;
+            if (fl < nw + ws - 1) {
+                const int ju = i0 + wd - ws + 1 + fl;
+                if (g.periodic) {
+                    const int j = ((ju % N) + N) % N;
+                    if (!fp.anti || sp[j] != sp[(j + dl) % N]) jw = j;
+                } else if (ju >= 0 && ju + dl < N && (!fp.anti || sp[ju] != sp[ju + dl])) {
+                    jw = ju;
+                }
+            }
+        }
+        jwin[bo][fl] = jw;
+    }
+    __syncthreads();
+    const long long rows = (long long)a.B * N * nb * Wm;
+    const long long nRk = 2 * a.Rk + 1, nRl = 2 * a.Rl + 1;
+    auto row_of = [&](int j, int bo) -> long long { return (((long long)b * N + j) * nb + bo) * Wm; };
+    auto tap = [&](int ll, int r, int c) -> T {
+        const int row = g.periodic ? ((r % N) + N) % N : r + N - 1;
+        return a.taps[((long long)(ll - 1) * g.R + row) * d + c];
+    };
+    auto site_ok = [&](int k) -> bool { return g.periodic || (k >= 0 && k < N); };
+    // flip (bond bo, slot q) of this warp's site: window entry warp + ws - 1 - q
+    auto flip_of = [&](int bo, int q) -> int {
+        const int ws = bo == 0 ? ws0 : ws1;
+        return jwin[bo][warp + ws - 1 - q];
+    };
+    unsigned valid = 0;   // bit bo * kPrMaxWs + q
+    if (active)
+        for (int bo = 0; bo < nb; ++bo)
+            for (int q = 0; q < (bo == 0 ? ws0 : ws1); ++q)
+                if (flip_of(bo, q) >= 0) valid |= 1u << (bo * kPrMaxWs + q);
+    T acc[HD][2][kPrMaxWs];
+#pragma unroll
+    for (int h = 0; h < HD; ++h)
+#pragma unroll
+        for (int bo = 0; bo < 2; ++bo)
+#pragma unroll
+            for (int q = 0; q < kPrMaxWs; ++q) acc[h][bo][q] = 0;
+    // Slice Toeplitz and embedding terms.
+#pragma unroll
+    for (int bo = 0; bo < 2; ++bo) {
+        if (bo >= nb) break;
+        const int dl = fp.bond[bo];
+#pragma unroll
+        for (int q = 0; q < kPrMaxWs; ++q) {
+            if (!((valid >> (bo * kPrMaxWs + q)) & 1u)) continue;
+            const int j = flip_of(bo, q), jp = g.periodic ? (j + dl) % N : j + dl;
+            const T ds = (T)(-2 * sp[j]), dsp = (T)(-2 * sp[jp]);
+#pragma unroll
+            for (int h = 0; h < HD; ++h) {
+                const int c = lane + 32 * h;
+                if (c >= d) continue;
+                T v;
+                if (l == 1) {
+                    v = tap(1, q - wd, c) * a.w.e[c] * ds + tap(1, q - wd - dl, c) * a.w.e[c] * dsp;
+                } else {
+                    v = 0;
+                    const T *Sp = S + (lo - 1) * rows * d + row_of(j, bo) * d + c;
+                    for (int t2 = 0; t2 < W + dl; ++t2)
+                        if (site_ok(i - q + t2)) v += tap(l, q - t2, c) * Sp[(long long)t2 * d];
+                    const T *el = a.ell + (((b * (L - 1) + (l - 2)) * N + i) * nRl) * d + c;
+                    v += ds * el[(long long)(wd - q + a.Rl) * d] + dsp * el[(long long)(wd - q + dl + a.Rl) * d];
+                }
+                acc[h][bo][q] = v;
+            }
+        }
+    }
+    // Interlayer links.
+    const bool vec = std::is_same<T, float>::value && d % 16 == 0;
+    for (int m = 1; m <= l - 2; ++m) {
+        __syncthreads();   // the previous m's window is no longer read
+        for (int bo = 0; bo < nb; ++bo) {
+            const int ws = bo == 0 ? ws0 : ws1, per = ws * d;
+            T *dst = bo == 0 ? Sw0 : Sw1;
+            const T *src = S + (long long)(m - 1) * rows * d;
+            for (int x = threadIdx.x; x < (nw + ws - 1) * per; x += blockDim.x) {
+                const int fl = x / per, rem = x % per;
+                const int j = jwin[bo][fl];
+                dst[x] = j >= 0 ? src[row_of(j, bo) * d + rem] : (T)0;
+            }
+        }
+        __syncthreads();
+        if (!active) continue;
+        const T *Kr = a.K + ((b * a.P + pair_index(l, m)) * N + i) * nRk * dd;
+        for (int dk = -(Wm - 1); dk <= Wm - 1; ++dk) {
+            if (!site_ok(i + dk)) continue;
+            const T *Kb = Kr + (long long)(dk + a.Rk) * dd;
+#pragma unroll
+            for (int h = 0; h < HD; ++h) {
+                const int c = lane + 32 * h;
+                if (c >= d) continue;
+                const T *kr = Kb + (long long)c * d;
+                for (int c2 = 0; c2 < d; c2 += 16) {
+                    T kv[16];
+                    if (vec) {
+#pragma unroll
+                        for (int u = 0; u < 16; u += 4) {
+                            const float4 k4 = __ldg(reinterpret_cast<const float4 *>(kr + c2 + u));
+                            kv[u] = (T)k4.x;
+                            kv[u + 1] = (T)k4.y;
+                            kv[u + 2] = (T)k4.z;
+                            kv[u + 3] = (T)k4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) kv[u] = (c2 + u < d) ? kr[c2 + u] : (T)0;
+                    }
+#pragma unroll
+                    for (int bo = 0; bo < 2; ++bo) {
+                        if (bo >= nb) break;
+                        const int ws = bo == 0 ? ws0 : ws1;
+                        const T *Swb = bo == 0 ? Sw0 : Sw1;
+#pragma unroll
+                        for (int q = 0; q < kPrMaxWs; ++q) {
+                            const int t2 = dk + q;
+                            if (q >= ws || t2 < 0 || t2 >= ws || !((valid >> (bo * kPrMaxWs + q)) & 1u)) continue;
+                            const T *sv = Swb + ((size_t)(warp + ws - 1 - q) * ws + t2) * d + c2;
+                            T sacc = 0;
+                            if (vec) {
+#pragma unroll
+                                for (int u = 0; u < 16; u += 4) {
+                                    const float4 s4 = *reinterpret_cast<const float4 *>(sv + u);
+                                    sacc += kv[u] * (T)s4.x + kv[u + 1] * (T)s4.y + kv[u + 2] * (T)s4.z +
+                                            kv[u + 3] * (T)s4.w;
+                                }
+                            } else {
+#pragma unroll
+                                for (int u = 0; u < 16; ++u)
+                                    if (c2 + u < d) sacc += kv[u] * sv[u];
+                            }
+                            acc[h][bo][q] += sacc;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (!active) return;
+    // s^(l) = U (dchi * (y + V p)) and its contribution to dOmega, one flip at a time.
+#pragma unroll
+    for (int bo = 0; bo < 2; ++bo) {
+        if (bo >= nb) break;
+#pragma unroll
+        for (int q = 0; q < kPrMaxWs; ++q) {
+            if (q >= Wm) break;
+#pragma unroll
+            for (int h = 0; h < HD; ++h) {
+                const int c = lane + 32 * h;
+                if (c < d) pq[(bo * Wm + q) * d + c] = acc[h][bo][q];
+            }
+        }
+    }
+    __syncwarp();
+    const T *yrow = a.y + ((b * L + lo) * N + i) * d;
+    const T *rho = a.rho + ((b * L + lo) * dout) * (long long)N * d + (long long)i * d;
+    for (int bo = 0; bo < nb; ++bo) {
+        for (int q = 0; q < (bo == 0 ? ws0 : ws1); ++q) {
+            if (!((valid >> (bo * kPrMaxWs + q)) & 1u)) continue;
+            const long long row = row_of(flip_of(bo, q), bo) + q;
+            const T *pv = pq + (bo * Wm + q) * d;
+#pragma unroll
+            for (int h = 0; h < HD; ++h) {
+                const int c = lane + 32 * h;
+                if (c >= d) continue;
+                T z = yrow[c];
+                for (int c2 = 0; c2 < d; ++c2) z += VTs[c2 * d + c] * pv[c2];
+                gb[c] = DX[(lo * rows + row) * d + c] * z;
+            }
+            __syncwarp();
+            T sv[HD];
+#pragma unroll
+            for (int h = 0; h < HD; ++h) {
+                const int c = lane + 32 * h;
+                T s = 0;
+                if (c < d) {
+                    for (int c2 = 0; c2 < d; ++c2) s += UTs[c2 * d + c] * gb[c2];
+                    if (l < L) S[(lo * rows + row) * d + c] = s;
+                }
+                sv[h] = s;
+            }
+            __syncwarp();   // gb is rewritten by the next flip
+            for (int k = 0; k < dout; ++k) {
+                double v = 0.0;
+#pragma unroll
+                for (int h = 0; h < HD; ++h) {
+                    const int c = lane + 32 * h;
+                    if (c < d) v += (double)rho[(long long)k * N * d + c] * (double)sv[h];
+                }
+                v = warp_sum<double>(v);
+                if (lane == 0) PART[row * dout + k] += v;
+            }
         }
     }
 }
@@ -2220,20 +2483,35 @@ __global__ void __launch_bounds__(32 * kLfWarps, 1) k_ab_lf64(AbArgs<float> a, i
     }
 }
 
-__global__ void k_ab_final(Geom g, int B, int f_kind, const int8_t *__restrict__ spins, const double *__restrict__ Omega,
-                           const double *__restrict__ PART, const void *__restrict__ tlink, int tsize,
-                           double *__restrict__ out) {
+// out[(b nb + bond) N + j]: the sum of a flip's slot partials and its embedding terms
+// t_j ds_j (Eq. recur_out), through the readout.  A pair past an open end gives 0.
+__global__ void k_ab_final(Geom g, FlipPattern fp, int B, int f_kind, const int8_t *__restrict__ spins,
+                           const double *__restrict__ Omega, const double *__restrict__ PART,
+                           const void *__restrict__ tlink, int tsize, double *__restrict__ out) {
     const long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int N = g.N, W = g.W, dout = g.dout;
-    if (f >= (long long)B * N) return;
-    const long long b = f / N;
-    const int j = (int)(f % N);
-    const double ds = -2.0 * spins[b * N + j];
+    const int N = g.N, W = g.W, dout = g.dout, nb = fp.nb, Wm = fp.Wm;
+    if (f >= (long long)B * nb * N) return;
+    const long long b = f / ((long long)nb * N);
+    const int bond = (int)((f / N) % nb), j = (int)(f % N);
+    const int dl = bond_of(fp, bond);
+    int jp = -1;
+    if (dl > 0) {
+        jp = g.periodic ? (j + dl) % N : j + dl;
+        if (jp >= N || (fp.anti && spins[b * N + j] == spins[b * N + jp])) {
+            out[f] = 0.0;
+            return;
+        }
+    }
+    const double ds = -2.0 * spins[b * N + j], dsp = jp >= 0 ? -2.0 * spins[b * N + jp] : 0.0;
+    const long long row0 = ((b * N + j) * nb + bond) * Wm;
+    auto tval = [&](long long ti) -> double {
+        return tsize == 8 ? static_cast<const double *>(tlink)[ti] : (double)static_cast<const float *>(tlink)[ti];
+    };
     double res = 0.0;
     for (int k = 0; k < dout; ++k) {
-        const long long ti = (b * N + j) * dout + k;
-        double s = (tsize == 8 ? static_cast<const double *>(tlink)[ti] : (double)static_cast<const float *>(tlink)[ti]) * ds;
-        for (int t = 0; t < W; ++t) s += PART[(f * W + t) * dout + k];
+        double s = tval((b * N + j) * dout + k) * ds;
+        if (jp >= 0) s += tval((b * N + jp) * dout + k) * dsp;
+        for (int t = 0; t < W + dl; ++t) s += PART[(row0 + t) * dout + k];
         const double om = Omega[b * dout + k];
         res += f_kind == 0 ? (log_cosh_ab(om + s) - log_cosh_ab(om)) : s;
     }
@@ -2577,13 +2855,14 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
                            sizeof(T);
     if (lsm > 220 * 1024 || tsm > 220 * 1024) return cudaErrorNotSupported;
     const AbArgs<T> a = ab_args<T>(m, pl, w, c);
+    const FlipPattern singles{1, g.W, {0, 0}, 0};
     const long long rows = (long long)c->B * c->N * g.W;
     T *DX = static_cast<T *>(scratch);
     T *S = DX + (size_t)g.L * rows * g.d;
     double *PART = reinterpret_cast<double *>(S + (size_t)g.L * rows * g.d);
     cudaError_t err = cudaMemsetAsync(PART, 0, (size_t)rows * g.dout * sizeof(double), st);
     if (err != cudaSuccess) return err;
-    if ((err = cudaFuncSetAttribute(k_dchi_table<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) !=
+    if ((err = cudaFuncSetAttribute(k_dchi_table<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) !=
         cudaSuccess)
         return err;
     {
@@ -2593,7 +2872,7 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
         const long long tiles = (rows + 63) / 64;
         long long tpb = (tiles * g.L + 4 * 152 - 1) / (4 * 152);
         tpb = tpb < 1 ? 1 : (tpb > kDxTPB ? kDxTPB : tpb);
-        k_dchi_table<T><<<dim3((unsigned)((tiles + tpb - 1) / tpb), g.L), 256, tsm, st>>>(a, DX, (int)tpb);
+        k_dchi_table<T, false><<<dim3((unsigned)((tiles + tpb - 1) / tpb), g.L), 256, tsm, st>>>(a, singles, DX, (int)tpb);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     const int hd = (g.d + 31) / 32;
@@ -2623,7 +2902,7 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
     {
         ProfScope _ps("k_ab_final", st);
         k_ab_final<<<(unsigned)(((long long)c->B * c->N + 255) / 256), 256, 0, st>>>(
-            g, c->B, m->desc.f_kind, c->spins, c->Omega, PART, c->t, (int)sizeof(T), out);
+            g, singles, c->B, m->desc.f_kind, c->spins, c->Omega, PART, c->t, (int)sizeof(T), out);
     }
     return cudaGetLastError();
 }
@@ -2632,6 +2911,94 @@ template cudaError_t launch_abacus_singles<double>(const dn_model *, const Plan<
                                                    const dn_cache *, void *, double *, cudaStream_t);
 template cudaError_t launch_abacus_singles<float>(const dn_model *, const Plan<float> &, const Weights<float> &,
                                                   const dn_cache *, void *, double *, cudaStream_t);
+
+static int pattern_wm(const dn_model *m, int nb, const int *bonds) {
+    int mx = 0;
+    for (int q = 0; q < nb; ++q) mx = bonds[q] > mx ? bonds[q] : mx;
+    return 2 * m->desc.w + 1 + mx;
+}
+
+size_t pairs_scratch_bytes(const dn_model *m, const dn_cache *c, int nb, const int *bonds) {
+    const size_t rows = (size_t)c->B * c->N * nb * pattern_wm(m, nb, bonds);
+    const size_t tb = c->prec == DN_FP64 ? 8 : 4;
+    return 2 * (size_t)m->desc.L * rows * m->desc.d * tb + rows * m->desc.d_out * 8 + 1024;
+}
+
+template <typename T>
+cudaError_t launch_abacus_pairs(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c, int nb,
+                                const int *bonds, bool anti, void *scratch, double *out, cudaStream_t st) {
+    const Geom g = geom_of(m, c->N);
+    if (nb < 1 || nb > 2) return cudaErrorInvalidValue;
+    FlipPattern fp{nb, pattern_wm(m, nb, bonds), {bonds[0], nb > 1 ? bonds[1] : 0}, anti ? 1 : 0};
+    for (int q = 0; q < nb; ++q)
+        if (bonds[q] < 1 || bonds[q] > c->max_cluster - 1) return cudaErrorInvalidValue;
+    if (fp.Wm > kPrMaxWs || fp.Wm > c->WF || g.d > 64 || c->B > 65535) return cudaErrorNotSupported;
+    const size_t tsm = 64 * sizeof(long long) +
+                       ((size_t)g.dh * (g.dh + 4) + (size_t)g.dh * (g.d + 4) + 2 * 68 * (size_t)g.dh + 64 * (size_t)g.W) *
+                           sizeof(T);
+    // Sites per CTA (one warp each): the most resident warps per SM for the shared flip
+    // windows and the per-warp buffers.
+    const int ws0 = g.W + fp.bond[0], ws1 = nb > 1 ? g.W + fp.bond[1] : 0;
+    auto lsm_of = [&](int nw) -> size_t {
+        return (2 * (size_t)g.d * g.d + (size_t)(nw + ws0 - 1) * ws0 * g.d + (size_t)(nw + ws1 - 1) * ws1 * g.d +
+                (size_t)nw * (nb * fp.Wm + 1) * g.d) *
+               sizeof(T);
+    };
+    const bool two = g.d > 32;
+    auto kfn = two ? k_ab_pairs<T, 2> : k_ab_pairs<T, 1>;
+    cudaError_t err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    if (err != cudaSuccess) return err;
+    int wpc = 0, best = 0;
+    for (int nw = 1; nw <= 8; ++nw) {
+        if (lsm_of(nw) > 220 * 1024) break;
+        int blocks = 0;
+        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kfn, 32 * nw, lsm_of(nw))) != cudaSuccess)
+            return err;
+        if (blocks * nw >= best && blocks > 0) {
+            best = blocks * nw;
+            wpc = nw;
+        }
+    }
+    if (wpc == 0 || tsm > 220 * 1024) return cudaErrorNotSupported;
+    const size_t lsm = lsm_of(wpc);
+    const AbArgs<T> a = ab_args<T>(m, pl, w, c);
+    const long long rows = (long long)c->B * c->N * nb * fp.Wm;
+    T *DX = static_cast<T *>(scratch);
+    T *S = DX + (size_t)g.L * rows * g.d;
+    double *PART = reinterpret_cast<double *>(S + (size_t)g.L * rows * g.d);
+    err = cudaMemsetAsync(PART, 0, (size_t)rows * g.dout * sizeof(double), st);
+    if (err != cudaSuccess) return err;
+    if ((err = cudaFuncSetAttribute(k_dchi_table<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)) !=
+        cudaSuccess)
+        return err;
+    {
+        ProfScope _ps("k_dchi_table", st);
+        const long long tiles = (rows + 63) / 64;
+        long long tpb = (tiles * g.L + 4 * 152 - 1) / (4 * 152);
+        tpb = tpb < 1 ? 1 : (tpb > kDxTPB ? kDxTPB : tpb);
+        k_dchi_table<T, true><<<dim3((unsigned)((tiles + tpb - 1) / tpb), g.L), 256, tsm, st>>>(a, fp, DX, (int)tpb);
+    }
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const dim3 grid((unsigned)((g.N + wpc - 1) / wpc), (unsigned)c->B);
+    for (int l = 1; l <= g.L; ++l) {
+        ProfScope _ps("k_ab_pairs", st);
+        kfn<<<grid, 32 * wpc, lsm, st>>>(a, fp, l, S, DX, PART);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    {
+        ProfScope _ps("k_ab_final", st);
+        k_ab_final<<<(unsigned)(((long long)c->B * nb * c->N + 255) / 256), 256, 0, st>>>(
+            g, fp, c->B, m->desc.f_kind, c->spins, c->Omega, PART, c->t, (int)sizeof(T), out);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_abacus_pairs<double>(const dn_model *, const Plan<double> &, const Weights<double> &,
+                                                 const dn_cache *, int, const int *, bool, void *, double *,
+                                                 cudaStream_t);
+template cudaError_t launch_abacus_pairs<float>(const dn_model *, const Plan<float> &, const Weights<float> &,
+                                                const dn_cache *, int, const int *, bool, void *, double *,
+                                                cudaStream_t);
 
 template cudaError_t launch_abacus<double>(const dn_model *, const Plan<double> &, const Weights<double> &,
                                            const dn_cache *, const int32_t *, const int32_t *, int, double *,
@@ -2666,6 +3033,33 @@ __global__ void k_make_flips(int kind, int N, int B, int periodic, const int8_t 
             sites[2 * f + 1] = ok ? j : -1;
         }
     }
+}
+
+__global__ void k_make_pair_flips(int N, int B, int periodic, FlipPattern fp, const int8_t *__restrict__ spins,
+                                  int32_t *__restrict__ sample, int32_t *__restrict__ sites) {
+    const long long F = (long long)B * fp.nb * N;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < F; f += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(f % N), bo = (int)((f / N) % fp.nb);
+        int jp = j + bond_of(fp, bo);
+        bool ok = true;
+        if (periodic) jp %= N;
+        else if (jp >= N) ok = false;
+        const long long b = f / ((long long)fp.nb * N);
+        if (ok && fp.anti && spins[b * N + j] == spins[b * N + jp]) ok = false;
+        sample[f] = (int32_t)b;
+        sites[2 * f] = ok ? j : -1;
+        sites[2 * f + 1] = ok ? jp : -1;
+    }
+}
+
+cudaError_t launch_make_pair_flips(int N, int B, int periodic, int nb, const int *bonds, bool anti,
+                                   const int8_t *spins, int32_t *sample, int32_t *sites, cudaStream_t st) {
+    const FlipPattern fp{nb, 0, {bonds[0], nb > 1 ? bonds[1] : 0}, anti ? 1 : 0};
+    {
+        ProfScope _ps("k_make_flips", st);
+        k_make_pair_flips<<<1024, 256, 0, st>>>(N, B, periodic, fp, spins, sample, sites);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_make_flips(int kind, int N, int B, int periodic, const int8_t *spins, int32_t *sample,

@@ -694,6 +694,48 @@ dn_status abacus_single_flip_ratios(const dn_cache *c, double *dlogpsi_dev, void
     });
 }
 
+// Pair flips grouped by site (anti: antialigned pairs only, the others 0); arguments checked.
+static dn_status pair_ratios(const dn_cache *c, int n_bonds, const int32_t *bonds, bool anti, double *dlogpsi_dev,
+                            void *stream) {
+    if (!c || !bonds || !dlogpsi_dev || n_bonds < 1 || n_bonds > 2) return DN_EINVAL;
+    for (int q = 0; q < n_bonds; ++q)
+        if (bonds[q] < 1 || bonds[q] > c->max_cluster - 1) return DN_EINVAL;
+    if (n_bonds == 2 && bonds[0] == bonds[1]) return DN_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return guard([&]() -> dn_status {
+        dn::ProfPhase phase("abacus");
+        dn_model *m = c->model;
+        const int bd[2] = {bonds[0], n_bonds > 1 ? bonds[1] : 0};
+        DevBuf scratch(dn::pairs_scratch_bytes(m, c, n_bonds, bd), st);
+        cudaError_t err = c->prec == DN_FP64
+                              ? dn::launch_abacus_pairs<double>(m, m->plan64.at(c->N), m->w64, c, n_bonds, bd,
+                                                                anti, scratch.p, dlogpsi_dev, st)
+                              : dn::launch_abacus_pairs<float>(m, m->plan32.at(c->N), m->w32, c, n_bonds, bd,
+                                                               anti, scratch.p, dlogpsi_dev, st);
+        if (err == cudaErrorNotSupported) {
+            // Shapes outside the grouped kernel: the flip-list kernel on the same pairs.
+            cudaGetLastError();
+            const long long F = (long long)c->B * n_bonds * c->N;
+            DevBuf smp((size_t)F * sizeof(int32_t), st), sts((size_t)F * 2 * sizeof(int32_t), st);
+            ck(dn::launch_make_pair_flips(c->N, c->B, m->desc.periodic, n_bonds, bd, anti, c->spins,
+                                          smp.as<int32_t>(), sts.as<int32_t>(), st));
+            if (c->prec == DN_FP64)
+                err = dn::launch_abacus<double>(m, m->plan64.at(c->N), m->w64, c, smp.as<int32_t>(), sts.as<int32_t>(),
+                                                (int)F, dlogpsi_dev, st);
+            else
+                err = dn::launch_abacus<float>(m, m->plan32.at(c->N), m->w32, c, smp.as<int32_t>(), sts.as<int32_t>(),
+                                               (int)F, dlogpsi_dev, st);
+        }
+        ck(err);
+        return DN_OK;
+    });
+}
+
+dn_status abacus_pair_flip_ratios(const dn_cache *c, int n_bonds, const int32_t *bonds, double *dlogpsi_dev,
+                                  void *stream) {
+    return pair_ratios(c, n_bonds, bonds, false, dlogpsi_dev, stream);
+}
+
 dn_status local_energy(dn_model *m, const dn_hamiltonian *H, int N, const int8_t *spins_dev, int B,
                        dn_precision prec, void *stream, double *eloc_dev) {
     if (!m || !H || !spins_dev || !eloc_dev || B < 1 || N < 1) return DN_EINVAL;
@@ -732,6 +774,11 @@ dn_status local_energy(dn_model *m, const dn_hamiltonian *H, int N, const int8_t
             cudaError_t err = cudaSuccess;
             if (H->kind == 0) {
                 s = abacus_single_flip_ratios(c, dl.as<double>(), stream);
+            } else if (H->periodic == m->desc.periodic) {
+                // the antialigned pairs (j, j+1), (j, j+2) grouped by site: entry b 2N + (bond-1) N + j,
+                // the layout k_eloc_reduce reads
+                const int32_t bonds[2] = {1, 2};
+                s = pair_ratios(c, 2, bonds, true, dl.as<double>(), stream);
             } else {
                 err = dn::launch_make_flips(H->kind, N, n, H->periodic, c->spins, smp.as<int32_t>(), sts.as<int32_t>(),
                                             st);

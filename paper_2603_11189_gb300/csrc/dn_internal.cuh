@@ -404,6 +404,19 @@ size_t singles_scratch_bytes(const dn_model *m, const dn_cache *c);
 template <typename T>
 cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c,
                                   void *scratch, double *out, cudaStream_t st);
+// The pair flips {j, j + bonds[bo]} (1 <= nb <= 2 bonds, 1 <= bonds[bo] <= max_cluster - 1)
+// of every site j of every cached configuration, out[(b nb + bo) N + j] (0 where the pair
+// runs past an open end, and with anti set where its two spins are aligned), layer by
+// layer; scratch of pairs_scratch_bytes() bytes (cudaErrorNotSupported when the shape does
+// not fit the kernels).
+size_t pairs_scratch_bytes(const dn_model *m, const dn_cache *c, int nb, const int *bonds);
+template <typename T>
+cudaError_t launch_abacus_pairs(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c, int nb,
+                                const int *bonds, bool anti, void *scratch, double *out, cudaStream_t st);
+// The same pairs as a flip list for the flip-list kernel: entry (b nb + bo) N + j (empty
+// entries where the pair runs past an open end or, with anti set, its spins are aligned).
+cudaError_t launch_make_pair_flips(int N, int B, int periodic, int nb, const int *bonds, bool anti,
+                                   const int8_t *spins, int32_t *sample, int32_t *sites, cudaStream_t st);
 cudaError_t launch_make_flips(int kind, int N, int B, int periodic, const int8_t *spins, int32_t *sample,
                               int32_t *sites, cudaStream_t st);
 cudaError_t launch_eloc_reduce(const dn_hamiltonian &H, int N, int B, const int8_t *spins, const double *coupling,

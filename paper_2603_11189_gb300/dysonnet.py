@@ -79,6 +79,7 @@ def _lib():
         "dysonnet_forward_cache": (i32, [vp, i32, vp, i32, i32, i32, vp, ctypes.POINTER(vp), vp]),
         "abacus_flip_ratios": (i32, [vp, vp, vp, i32, vp, vp]),
         "abacus_single_flip_ratios": (i32, [vp, vp, vp]),
+        "abacus_pair_flip_ratios": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int32), vp, vp]),
         "local_energy": (i32, [vp, ctypes.POINTER(Hamiltonian), i32, vp, i32, i32, vp, vp]),
         "dn_full_forward": (i32, [vp, i32, vp, i32, i32, vp, vp, vp]),
         "dn_recompute_flip_ratios": (i32, [vp, i32, vp, i32, vp, vp, i32, i32, vp, vp]),
@@ -117,7 +118,7 @@ def exported_symbols():
     return ["dn_status_string", "dn_set_allocator", "dn_model_create", "dn_model_destroy", "dn_cache_bytes",
             "dysonnet_forward_cache", "abacus_flip_ratios", "local_energy", "dn_full_forward",
             "dn_recompute_flip_ratios", "dn_cache_check", "dn_cache_info", "dn_cache_tensor", "dn_cache_destroy",
-            "dn_full_forward_noalloc", "abacus_single_flip_ratios", "dn_launch_count", "dn_profile_enable",
+            "dn_full_forward_noalloc", "abacus_single_flip_ratios", "abacus_pair_flip_ratios", "dn_launch_count", "dn_profile_enable",
             "dn_profile_count", "dn_profile_get", "dn_server_create", "dn_server_set_chain", "dn_server_submit",
             "dn_server_wait", "dn_server_get_stats", "dn_server_destroy", "dn_model_nparams", "dn_logpsi_grad", "dn_sr_matrices", "dn_sampler_batch",
             "dn_set_fused_links", "dn_set_fft_links", "dn_set_fft_conv", "dn_server_set_idle_limit",
@@ -328,6 +329,16 @@ class Cache:
         if out is None:
             out = torch.empty((self.B, self.N), dtype=torch.float64, device="cuda")
         _check(_lib().abacus_single_flip_ratios(self._h, _ptr(out), _stream(stream)), "abacus_single_flip_ratios")
+        return out
+
+    def pair_flip_ratios(self, bonds=(1, 2), stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+        """abacus_pair_flip_ratios: [B][len(bonds)][N] ratios of the pairs {j, j + bond}."""
+        nb = len(bonds)
+        arr = (ctypes.c_int32 * max(nb, 1))(*bonds)
+        if out is None:
+            out = torch.empty((self.B, nb, self.N), dtype=torch.float64, device="cuda")
+        _check(_lib().abacus_pair_flip_ratios(self._h, nb, arr, _ptr(out), _stream(stream)),
+               "abacus_pair_flip_ratios")
         return out
 
     def check(self, stream=None) -> int:
