@@ -626,6 +626,7 @@ def main():
     ap.add_argument("--no-sampler", action="store_true")
     ap.add_argument("--no-bf16-forward", action="store_true")
     ap.add_argument("--bf16-samples", type=int, default=2048)
+    ap.add_argument("--j1j2-samples", type=int, default=64)
     ap.add_argument("--grad-samples", type=int, default=4096)
     ap.add_argument("--n1024-chains", type=int, default=4)
     args = ap.parse_args()
@@ -762,7 +763,7 @@ def main():
     sampler = None if args.no_sampler else measure_sampler(dn, synth, torch, barrier)
     bf16_forward = None if args.no_bf16_forward else measure_bf16_forward(dn, synth, torch, barrier, lib,
                                                                            B=args.bf16_samples)
-    bf16_j1j2 = None if args.no_bf16_forward else measure_bf16_j1j2(dn, synth, torch, barrier, lib)
+    bf16_j1j2 = None if args.no_bf16_forward else measure_bf16_j1j2(dn, synth, torch, barrier, lib, B=args.j1j2_samples)
 
     peaks, src = _peaks()
     roof, families = roofline(prof, args.steps, desc, N, Bs, peaks, src, clocks)
