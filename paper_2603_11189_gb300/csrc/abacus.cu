@@ -820,9 +820,10 @@ __global__ void __launch_bounds__(256) k_ab_layer(AbArgs<T> a, int l, T *__restr
 constexpr int kPrMaxWs = 8;   // slots per flip (W + delta)
 constexpr int kPrMaxFl = 48;  // flips per bond in a CTA's window (nw + W + delta - 1)
 
-template <typename T, int HD>
+template <typename T, int HD, bool VEC>
 __global__ void __launch_bounds__(256) k_ab_pairs(AbArgs<T> a, FlipPattern fp, int l, T *__restrict__ S,
                                                   const T *__restrict__ DX, double *__restrict__ PART) {
+    static_assert(!VEC || std::is_same<T, float>::value, "16-byte loads of FP32 link rows (d a multiple of 16)");
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int jwin[2][kPrMaxFl];   // wrapped flip site of window entry fl, or -1 (no flip)
     const Geom &g = a.g;
@@ -917,8 +918,8 @@ __global__ void __launch_bounds__(256) k_ab_pairs(AbArgs<T> a, FlipPattern fp, i
             }
         }
     }
-    // Interlayer links.
-    const bool vec = std::is_same<T, float>::value && d % 16 == 0;
+    // Interlayer links.  Each flip's 16-term dot product runs as four partial sums, so its
+    // dependent chain is 4 + 2 deep rather than 16.
     for (int m = 1; m <= l - 2; ++m) {
         __syncthreads();   // the previous m's window is no longer read
         for (int bo = 0; bo < nb; ++bo) {
@@ -944,14 +945,14 @@ __global__ void __launch_bounds__(256) k_ab_pairs(AbArgs<T> a, FlipPattern fp, i
                 const T *kr = Kb + (long long)c * d;
                 for (int c2 = 0; c2 < d; c2 += 16) {
                     T kv[16];
-                    if (vec) {
+                    if constexpr (VEC) {
 #pragma unroll
                         for (int u = 0; u < 16; u += 4) {
                             const float4 k4 = __ldg(reinterpret_cast<const float4 *>(kr + c2 + u));
-                            kv[u] = (T)k4.x;
-                            kv[u + 1] = (T)k4.y;
-                            kv[u + 2] = (T)k4.z;
-                            kv[u + 3] = (T)k4.w;
+                            kv[u] = k4.x;
+                            kv[u + 1] = k4.y;
+                            kv[u + 2] = k4.z;
+                            kv[u + 3] = k4.w;
                         }
                     } else {
 #pragma unroll
@@ -967,20 +968,22 @@ __global__ void __launch_bounds__(256) k_ab_pairs(AbArgs<T> a, FlipPattern fp, i
                             const int t2 = dk + q;
                             if (q >= ws || t2 < 0 || t2 >= ws || !((valid >> (bo * kPrMaxWs + q)) & 1u)) continue;
                             const T *sv = Swb + ((size_t)(warp + ws - 1 - q) * ws + t2) * d + c2;
-                            T sacc = 0;
-                            if (vec) {
+                            T ps[4] = {0, 0, 0, 0};
+                            if constexpr (VEC) {
 #pragma unroll
                                 for (int u = 0; u < 16; u += 4) {
                                     const float4 s4 = *reinterpret_cast<const float4 *>(sv + u);
-                                    sacc += kv[u] * (T)s4.x + kv[u + 1] * (T)s4.y + kv[u + 2] * (T)s4.z +
-                                            kv[u + 3] * (T)s4.w;
+                                    ps[0] = fmaf(kv[u], s4.x, ps[0]);
+                                    ps[1] = fmaf(kv[u + 1], s4.y, ps[1]);
+                                    ps[2] = fmaf(kv[u + 2], s4.z, ps[2]);
+                                    ps[3] = fmaf(kv[u + 3], s4.w, ps[3]);
                                 }
                             } else {
 #pragma unroll
                                 for (int u = 0; u < 16; ++u)
-                                    if (c2 + u < d) sacc += kv[u] * sv[u];
+                                    if (c2 + u < d) ps[u & 3] += kv[u] * sv[u];
                             }
-                            acc[h][bo][q] += sacc;
+                            acc[h][bo][q] += (ps[0] + ps[1]) + (ps[2] + ps[3]);
                         }
                     }
                 }
@@ -2945,7 +2948,10 @@ cudaError_t launch_abacus_pairs(const dn_model *m, const Plan<T> &pl, const Weig
                sizeof(T);
     };
     const bool two = g.d > 32;
-    auto kfn = two ? k_ab_pairs<T, 2> : k_ab_pairs<T, 1>;
+    constexpr bool F32 = std::is_same<T, float>::value;
+    const bool vec = F32 && g.d % 16 == 0;
+    auto kfn = two ? (vec ? k_ab_pairs<T, 2, F32> : k_ab_pairs<T, 2, false>)
+                   : (vec ? k_ab_pairs<T, 1, F32> : k_ab_pairs<T, 1, false>);
     cudaError_t err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     if (err != cudaSuccess) return err;
     int wpc = 0, best = 0;
