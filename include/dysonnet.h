@@ -216,13 +216,11 @@ dn_status dn_recompute_flip_ratios(dn_model *model, int N, const int8_t *spins_d
  * exits; no cudaMalloc, cudaFree or allocator call is made.  A call needs
  * about B*N*d*(L+2)*t + B*(L+1)*d*8 bytes plus the weights and kernel taps
  * (t = 8 for DN_FP64, 4 for DN_FP32); a request that does not fit returns
- * DN_EINVAL and does nothing.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  The address is kept for the life of the process and does not
- * survive cudaDeviceReset() or another reset of the device's primary context: do
- * not call this entry point on a device after such a reset.  All calls share the
- * array and nothing in it needs clearing, but calls that overlap on the GPU (other
- * streams or threads) race on it. */
+ * DN_EINVAL and does nothing.  Every call looks up the array's device address
+ * in the current context (cudaGetSymbolAddress, a host-side query; the first one
+ * on a device loads the library's device code, so make it before any stream
+ * capture).  All calls share the array and nothing in it needs clearing, but
+ * calls that overlap on the GPU (other streams or threads) race on it. */
 dn_status dn_full_forward_noalloc(const dn_model *model, int N, const int8_t *spins_dev, int B, dn_precision prec,
                                   void *stream, double *logpsi_dev, double *Omega_dev);
 

@@ -20,7 +20,6 @@
 // call: every value a call reads is written earlier in the same call, so
 // nothing needs clearing, but two calls that overlap on the GPU (different
 // streams, or different host threads) race on it.
-#include <mutex>
 
 #include "dn_internal.cuh"
 
@@ -32,26 +31,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_na_mu;
-void *g_na_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set-up once per device).
-cudaError_t noalloc_scratch(void **out) {
-    int dev = 0;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return err;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
-        void *p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (err != cudaSuccess) return err;
-        g_na_ptr[dev] = p;
-    }
-    *out = g_na_ptr[dev];
-    return cudaSuccess;
-}
+// Device address of the scratch array in the current context.  Looked up on every call
+// (a host-side query that allocates nothing), so that a device or primary-context reset,
+// which reloads the module at a new address, never leaves a stale pointer behind.
+cudaError_t noalloc_scratch(void **out) { return cudaGetSymbolAddress(out, g_noalloc_scratch); }
 
 // Pack the layer weights of the FP64 parameter vector into the kernels' layout
 // (both orientations of every matrix) in precision T.
