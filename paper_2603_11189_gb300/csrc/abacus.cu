@@ -2921,6 +2921,11 @@ static int pattern_wm(const dn_model *m, int nb, const int *bonds) {
     return 2 * m->desc.w + 1 + mx;
 }
 
+bool pairs_grouped_fits(const dn_model *m, const dn_cache *c, int nb, const int *bonds) {
+    const int Wm = pattern_wm(m, nb, bonds);
+    return nb >= 1 && nb <= 2 && Wm <= kPrMaxWs && Wm <= c->WF && m->desc.d <= 64 && c->B <= 65535;
+}
+
 size_t pairs_scratch_bytes(const dn_model *m, const dn_cache *c, int nb, const int *bonds) {
     const size_t rows = (size_t)c->B * c->N * nb * pattern_wm(m, nb, bonds);
     const size_t tb = c->prec == DN_FP64 ? 8 : 4;
@@ -2935,7 +2940,7 @@ cudaError_t launch_abacus_pairs(const dn_model *m, const Plan<T> &pl, const Weig
     FlipPattern fp{nb, pattern_wm(m, nb, bonds), {bonds[0], nb > 1 ? bonds[1] : 0}, anti ? 1 : 0};
     for (int q = 0; q < nb; ++q)
         if (bonds[q] < 1 || bonds[q] > c->max_cluster - 1) return cudaErrorInvalidValue;
-    if (fp.Wm > kPrMaxWs || fp.Wm > c->WF || g.d > 64 || c->B > 65535) return cudaErrorNotSupported;
+    if (!pairs_grouped_fits(m, c, nb, bonds)) return cudaErrorNotSupported;
     const size_t tsm = 64 * sizeof(long long) +
                        ((size_t)g.dh * (g.dh + 4) + (size_t)g.dh * (g.d + 4) + 2 * 68 * (size_t)g.dh + 64 * (size_t)g.W) *
                            sizeof(T);

@@ -706,12 +706,14 @@ static dn_status pair_ratios(const dn_cache *c, int n_bonds, const int32_t *bond
         dn::ProfPhase phase("abacus");
         dn_model *m = c->model;
         const int bd[2] = {bonds[0], n_bonds > 1 ? bonds[1] : 0};
-        DevBuf scratch(dn::pairs_scratch_bytes(m, c, n_bonds, bd), st);
-        cudaError_t err = c->prec == DN_FP64
-                              ? dn::launch_abacus_pairs<double>(m, m->plan64.at(c->N), m->w64, c, n_bonds, bd,
-                                                                anti, scratch.p, dlogpsi_dev, st)
-                              : dn::launch_abacus_pairs<float>(m, m->plan32.at(c->N), m->w32, c, n_bonds, bd,
-                                                               anti, scratch.p, dlogpsi_dev, st);
+        cudaError_t err = cudaErrorNotSupported;
+        if (dn::pairs_grouped_fits(m, c, n_bonds, bd)) {
+            DevBuf scratch(dn::pairs_scratch_bytes(m, c, n_bonds, bd), st);
+            err = c->prec == DN_FP64 ? dn::launch_abacus_pairs<double>(m, m->plan64.at(c->N), m->w64, c, n_bonds, bd,
+                                                                      anti, scratch.p, dlogpsi_dev, st)
+                                     : dn::launch_abacus_pairs<float>(m, m->plan32.at(c->N), m->w32, c, n_bonds, bd,
+                                                                     anti, scratch.p, dlogpsi_dev, st);
+        }
         if (err == cudaErrorNotSupported) {
             // Shapes outside the grouped kernel: the flip-list kernel on the same pairs.
             cudaGetLastError();

@@ -409,6 +409,8 @@ cudaError_t launch_abacus_singles(const dn_model *m, const Plan<T> &pl, const We
 // runs past an open end, and with anti set where its two spins are aligned), layer by
 // layer; scratch of pairs_scratch_bytes() bytes (cudaErrorNotSupported when the shape does
 // not fit the kernels).
+// Whether the grouped kernels take the pattern (else the flip-list kernel serves it).
+bool pairs_grouped_fits(const dn_model *m, const dn_cache *c, int nb, const int *bonds);
 size_t pairs_scratch_bytes(const dn_model *m, const dn_cache *c, int nb, const int *bonds);
 template <typename T>
 cudaError_t launch_abacus_pairs(const dn_model *m, const Plan<T> &pl, const Weights<T> &w, const dn_cache *c, int nb,
